@@ -1,0 +1,251 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds problem descriptions and seeded random draws only: box
+slabs, conductivities, stimulus boxes, fibre angles, initial fronts, batches
+of instances and request arrival times.  It contains none of the numerical
+method (no basis, operator, ionic model, time stepping or indicators); both
+the FP64 oracle and the CUDA library read a ``Problem`` and do their own
+arithmetic on it.
+
+Units follow the monodomain problem statement of the paper (Sec. 2,
+Eq. (monodomain)): cm, ms, mS/cm, uF/cm^2, and a dimensionless transmembrane
+potential V for the Aliev-Panfilov cell model (rest 0, peak about 1).
+
+The five workloads mirror the slabs the paper measures on (Niederer slab,
+Sec. 3.1; spiral-wave square, Sec. 3.2), restated with the Aliev-Panfilov
+model because the paper's PCG model equations are not available here.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+AP_STANDARD = (8.0, 0.15, 0.002, 0.2, 0.3, 1.0)  # k, a, eps0, mu1, mu2, time_scale [ms per model unit]
+
+STATE_FE = 0
+STATE_EXP = 1
+
+
+@dataclass
+class Stimulus:
+    """Box-shaped stimulus: I_stim = -amplitude on nodes inside [lo, hi] for t in [t0, t1)."""
+    lo: Tuple[float, float, float]
+    hi: Tuple[float, float, float]
+    amplitude: float = 1.0
+    t0: float = 0.0
+    t1: float = 1.0
+
+
+@dataclass
+class Problem:
+    """One monodomain simulation on a box slab (fields mirror ``mdl_problem`` in include/mdl.h)."""
+    dim: int = 2
+    order: int = 1
+    extent: Tuple[float, float, float] = (1.0, 1.0, 1.0)
+    base: Tuple[int, int, int] = (32, 32, 1)
+    sigma_l: float = 1.0            # mS/cm along the fibre
+    sigma_t: float = 1.0            # mS/cm across the fibre
+    fibre: Tuple[float, float, float] = (1.0, 0.0, 0.0)
+    chi: float = 1400.0             # 1/cm
+    cm: float = 1.0                 # uF/cm^2
+    gamma: float = 10.0             # SIPG penalty factor
+    ionic_model: int = 0            # 0 = Aliev-Panfilov, -1 = none (pure diffusion)
+    ionic_params: Tuple[float, ...] = AP_STANDARD
+    stimuli: List[Stimulus] = field(default_factory=list)
+    dt_barrier: float = 0.01        # ms; 0 = largest 2^-k ms meeting the LTS level budget
+    max_refine: int = 0
+    n_lts_levels: int = 1
+    tau_refine: float = math.inf
+    tau_coarsen: float = -1.0
+    tau_cell: float = math.inf
+    dt_bar_cell: float = 0.0        # ms; substep length requested by the temporal indicator
+    act_threshold: float = 0.5
+    state_integrator: int = STATE_FE
+    precision: int = 64             # 32 or 64
+    amr_enabled: int = 0
+    lts_enabled: int = 0
+
+    def replace(self, **kw) -> "Problem":
+        return dataclasses.replace(self, **kw)
+
+    @property
+    def n_base(self) -> int:
+        n = self.base[0] * self.base[1]
+        return n * (self.base[2] if self.dim == 3 else 1)
+
+    @property
+    def n_p(self) -> int:
+        return (self.order + 1) ** self.dim
+
+
+def fibre_from_angle(theta: float) -> Tuple[float, float, float]:
+    return (math.cos(theta), math.sin(theta), 0.0)
+
+
+# --------------------------------------------------------------------------
+# The five workloads.
+# --------------------------------------------------------------------------
+
+def plain_2d_q1_32x32() -> Problem:
+    """Unit square, 32x32 Q1, isotropic 1.0 mS/cm, forward Euler at 0.01 ms for 20 ms, FP64."""
+    return Problem(
+        dim=2, order=1, extent=(1.0, 1.0, 1.0), base=(32, 32, 1),
+        sigma_l=1.0, sigma_t=1.0, fibre=(1.0, 0.0, 0.0), gamma=10.0,
+        stimuli=[Stimulus((0.0, 0.0, 0.0), (0.1, 0.1, 1.0), 1.0, 0.0, 1.0)],
+        dt_barrier=0.01, act_threshold=0.5, state_integrator=STATE_FE,
+        precision=64, amr_enabled=0, lts_enabled=0, n_lts_levels=1)
+
+
+PLAIN_T_END = 20.0
+
+
+def slab_2d_q1_256(seed: int = 2) -> Problem:
+    """2x2 cm, 256x256 Q1 base, quadtree AMR to depth 3, 4 LTS levels, 3:1 fibres at a seeded angle."""
+    rng = np.random.default_rng(seed)
+    theta = float(rng.uniform(0.0, math.pi))
+    return Problem(
+        dim=2, order=1, extent=(2.0, 2.0, 1.0), base=(256, 256, 1),
+        sigma_l=1.2, sigma_t=0.4, fibre=fibre_from_angle(theta), gamma=10.0,
+        stimuli=[Stimulus((0.0, 0.0, 0.0), (0.1, 0.1, 1.0), 1.0, 0.0, 1.0)],
+        dt_barrier=0.0, max_refine=3, n_lts_levels=4,
+        tau_refine=SLAB2D_TAU[0], tau_coarsen=SLAB2D_TAU[1],
+        tau_cell=0.5, dt_bar_cell=0.01,
+        act_threshold=0.5, state_integrator=STATE_EXP,
+        precision=32, amr_enabled=1, lts_enabled=1)
+
+
+# Refinement thresholds for the 2D slab, calibrated once on the oracle so that
+# a developed Aliev-Panfilov front (width ~0.01 cm) is refined to depth 3 and the
+# rest coarsens.  tau_coarsen = tau_refine / 10 is the ratio the paper uses for its
+# ventricle runs; with the indicator falling ~6x per refinement, the 1/3 ratio of
+# its slab runs would coarsen freshly refined children on the next barrier.
+SLAB2D_TAU = (3.0e-9, 3.0e-10)
+SLAB2D_T_END = 100.0
+
+
+def slab_3d_q2(seed: int = 3) -> Problem:
+    """2x0.7x0.3 cm, 128x48x20 Q2 hexes, octree AMR to depth 3, 4 LTS levels, planar x=0 stimulus."""
+    return Problem(
+        dim=3, order=2, extent=(2.0, 0.7, 0.3), base=(128, 48, 20),
+        sigma_l=1.2, sigma_t=0.3, fibre=(1.0, 0.0, 0.0), gamma=40.0,
+        stimuli=[Stimulus((0.0, 0.0, 0.0), (2.0 / 128.0, 0.7, 0.3), 1.0, 0.0, 1.0)],
+        dt_barrier=0.0, max_refine=3, n_lts_levels=4,
+        tau_refine=SLAB3D_TAU[0], tau_coarsen=SLAB3D_TAU[1],
+        tau_cell=0.5, dt_bar_cell=0.01,
+        act_threshold=0.5, state_integrator=STATE_EXP,
+        precision=32, amr_enabled=1, lts_enabled=1)
+
+
+SLAB3D_TAU = (1.0e-8, 1.0e-9)
+SLAB3D_T_END = 50.0
+
+
+def scaled(prob: Problem, base: Tuple[int, int, int]) -> Problem:
+    """Same physics on a different base grid with the extent scaled to keep h fixed."""
+    ext = tuple(prob.extent[k] * base[k] / prob.base[k] if k < prob.dim else prob.extent[k]
+                for k in range(3))
+    stims = []
+    for s in prob.stimuli:
+        stims.append(dataclasses.replace(s))
+    return prob.replace(base=tuple(base), extent=ext, stimuli=stims)
+
+
+# --------------------------------------------------------------------------
+# Seeded initial states: a developed excitation front.
+# --------------------------------------------------------------------------
+
+def front_state(points: np.ndarray, origin, radius: float, width: float,
+                tail: float = 0.0) -> Tuple[np.ndarray, np.ndarray]:
+    """Synthetic developed front: V = 1 inside a ball of ``radius`` around ``origin``
+    with a tanh edge of ``width``, and a recovery variable that rises behind the front.
+
+    ``points`` is (n, dim) physical coordinates; returns (V, v).  This shapes an
+    input state only (it stands in for the state a corner stimulus reaches after
+    several milliseconds); it is not part of the method.
+    """
+    o = np.asarray(origin[: points.shape[1]], dtype=np.float64)
+    r = np.sqrt(((points - o) ** 2).sum(axis=1))
+    V = 0.5 * (1.0 - np.tanh((r - radius) / width))
+    v = np.clip((radius - r) / max(tail, 1e-30), 0.0, 1.0) * 1.5 if tail > 0 else np.zeros_like(r)
+    return V, v
+
+
+# --------------------------------------------------------------------------
+# Batches and request streams.
+# --------------------------------------------------------------------------
+
+def batch_instances(n: int = 64, seed: int = 4, min_e: float = 1e3, max_e: float = 1e5,
+                    t_end: float = 100.0) -> List[Tuple[Problem, float]]:
+    """Heterogeneous instances: half 2D Q1, half 3D (Q1/Q2); log-uniform base element count."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        ne = float(np.exp(rng.uniform(np.log(min_e), np.log(max_e))))
+        if i < n // 2:
+            dim, order = 2, 1
+            side = max(2, int(round(math.sqrt(ne))))
+            base = (side, side, 1)
+            ext = (side * 0.0078125, side * 0.0078125, 1.0)
+        else:
+            dim = 3
+            order = 1 if i < (3 * n) // 4 else 2
+            # aspect 2 : 0.7 : 0.3
+            s = (ne / (2.0 * 0.7 * 0.3)) ** (1.0 / 3.0)
+            base = (max(2, int(round(2.0 * s))), max(2, int(round(0.7 * s))), max(2, int(round(0.3 * s))))
+            hh = 0.015625 * order
+            ext = (base[0] * hh, base[1] * hh, base[2] * hh)
+        sl = float(rng.uniform(0.5, 2.0))
+        st = float(rng.uniform(0.5, 2.0))
+        sl, st = max(sl, st), min(sl, st)
+        theta = float(rng.uniform(0.0, math.pi))
+        n_lts = int(rng.integers(1, 5))
+        corner = [float(rng.uniform(0.0, 0.8)) * ext[k] for k in range(3)]
+        size = [0.1 * ext[k] for k in range(3)]
+        stim = Stimulus(tuple(corner), tuple(corner[k] + size[k] for k in range(3)), 1.0, 0.0, 1.0)
+        p = Problem(dim=dim, order=order, extent=ext, base=base, sigma_l=sl, sigma_t=st,
+                    fibre=fibre_from_angle(theta), gamma=10.0 * order * order, stimuli=[stim],
+                    dt_barrier=0.0, max_refine=0, n_lts_levels=n_lts, tau_cell=0.5,
+                    state_integrator=STATE_EXP, precision=32, amr_enabled=0,
+                    lts_enabled=1 if n_lts > 1 else 0)
+        out.append((p, t_end))
+    return out
+
+
+def poisson_requests(rate: float = 20.0, duration: float = 60.0, seed: int = 5,
+                     min_e: float = 1e3, max_e: float = 2e5) -> List[Tuple[float, Problem, float]]:
+    """Poisson arrivals: (arrival_s, problem, horizon_ms)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= duration:
+            break
+        ne = float(np.exp(rng.uniform(np.log(min_e), np.log(max_e))))
+        dim = 2 if rng.uniform() < 0.5 else 3
+        order = 1 if rng.uniform() < 0.5 else 2
+        if dim == 2:
+            side = max(2, int(round(math.sqrt(ne))))
+            base = (side, side, 1)
+            hh = 0.0078125 * order
+            ext = (side * hh, side * hh, 1.0)
+        else:
+            s = (ne / (2.0 * 0.7 * 0.3)) ** (1.0 / 3.0)
+            base = (max(2, int(round(2.0 * s))), max(2, int(round(0.7 * s))), max(2, int(round(0.3 * s))))
+            hh = 0.015625 * order
+            ext = (base[0] * hh, base[1] * hh, base[2] * hh)
+        theta = float(rng.uniform(0.0, math.pi))
+        horizon = float(rng.uniform(100.0, 500.0))
+        corner = [0.0, 0.0, 0.0]
+        size = [0.1 * ext[k] for k in range(3)]
+        stim = Stimulus(tuple(corner), tuple(size), 1.0, 0.0, 1.0)
+        p = Problem(dim=dim, order=order, extent=ext, base=base, sigma_l=1.2, sigma_t=0.4,
+                    fibre=fibre_from_angle(theta), gamma=10.0 * order * order, stimuli=[stim],
+                    dt_barrier=0.0, max_refine=2, n_lts_levels=3, tau_cell=0.5,
+                    state_integrator=STATE_EXP, precision=32, amr_enabled=1, lts_enabled=1)
+        out.append((t, p, horizon))
+    return out
