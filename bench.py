@@ -1,0 +1,361 @@
+"""Benchmark: explicit local space-time adaptive monodomain stepping on one GB300.
+
+Workload (the 2D slab the headline metric is quoted on): 2x2 cm, 256x256 Q1 DG
+base mesh, quadtree AMR to depth 3 driven by the Kelly indicator, 4 synchronous
+LTS levels, Aliev-Panfilov, 3:1 fibres at a seeded angle, FP32 bulk arithmetic.
+The synthetic initial state is a developed excitation front (quarter circle of
+radius 1 cm around the stimulus corner, tanh edge 0.01 cm); setup barriers let
+the AMR refine it to depth 3 before warm-up.
+
+A step is one barrier step of Alg. 1: eta^s, refine/coarsen (host forest
+bookkeeping included), level assignment, all sweep ticks, eta^t, LAT, int V.
+value = DOF-updates / s over the K timed steps (device-timed with CUDA events on
+the library's stream, L2 flushed between steps by writing a 512 MiB buffer).
+
+--impl reference times the FP64 numpy oracle on the host cores instead (a
+bounded sample of the same workload, see cpu_baseline).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "DOF-updates/s"
+UNIT = "DOF-updates/s"
+FRONT = dict(origin=(0.0, 0.0, 0.0), radius=1.0, width=0.01, tail=0.3)
+SETUP_BARRIERS = 5
+# Algorithmic bytes per DOF-update of the fused sweep (Q1 2D, FP32, AP): V_old 4 + v 4 +
+# V_new 4 + v 4 = 16 B, plus per element step 2d neighbour ids + 4 B level/flags + the FP64
+# RV-T accumulator read-modify-write (36 B) over (p+1)^d = 4 DOFs.
+ALG_BYTES_PER_DOF_UPDATE = 25.0
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        finally:
+            os.unlink(self.path)
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(smax)
+            out["samples"] = len(sm)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def make_sim(prob):
+    from paper_2310_07607_gb300 import mdl
+    return mdl.Sim(prob)
+
+
+def node_coords_of(sim, prob):
+    """Physical node coordinates of the library's current mesh (leaf order)."""
+    root, level, coords, _ = sim.read_mesh()
+    n1 = prob.order + 1
+    if prob.order == 1:
+        xi = np.array([-1 / math.sqrt(3), 1 / math.sqrt(3)])
+    else:
+        xi = np.array([-math.sqrt(0.6), 0.0, math.sqrt(0.6)])
+    d = prob.dim
+    n_p = n1 ** d
+    q = np.arange(n_p)
+    a = [(q // n1 ** k) % n1 for k in range(d)]
+    X = np.empty((len(level), n_p, d))
+    for k in range(d):
+        h = prob.extent[k] / (prob.base[k] * (2.0 ** level.astype(np.float64)))
+        X[:, :, k] = coords[:, k:k + 1] * h[:, None] + (xi[a[k]][None, :] + 1.0) * 0.5 * h[:, None]
+    return X.reshape(-1, d)
+
+
+def run_ours(args, rank, world):
+    import torch
+    torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        dist.init_process_group("nccl")
+    from paper_2310_07607_gb300 import build
+    build.build()
+    prob = W.slab_2d_q1_256()
+    sim = make_sim(prob)
+    X = node_coords_of(sim, prob)
+    V0, v0 = W.front_state(X, FRONT["origin"], FRONT["radius"], FRONT["width"], FRONT["tail"])
+    sim.set_initial(V0, v0)
+    sim.step_barriers(SETUP_BARRIERS)
+    sim.step_barriers(args.warmup)
+    _, _, stream_ptr = sim.device_view(1)
+    stream = torch.cuda.ExternalStream(stream_ptr)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sim.reset_stats()
+    sim.set_timing(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = ClockSampler(torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+        evs[i][0].record(stream)
+        sim.step_barriers(1)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    st = sim.stats()
+    n_e, n_dof, _ = sim.sizes()
+    if dist:
+        t = torch.tensor([total_ms, float(st["dof_updates"])], device="cuda", dtype=torch.float64)
+        mx = t.clone()
+        dist.all_reduce(mx[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(mx[1:2], op=dist.ReduceOp.SUM)
+        total_ms_all, dof_all = mx[0].item(), mx[1].item()
+    else:
+        total_ms_all, dof_all = total_ms, float(st["dof_updates"])
+    value = dof_all / (total_ms_all / 1e3)
+    # roofline of the dominant kernel (the sweep tick kernel), from its own CUDA-event timing
+    peak, peak_kind = load_peaks()
+    sweep_s = st["sweep_ms"] / 1e3
+    alg_bytes = st["dof_updates"] * ALG_BYTES_PER_DOF_UPDATE
+    achieved = alg_bytes / sweep_s / 1e9 if sweep_s > 0 else 0.0
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+            "kernel": "k_tick<float,2,1>", "launches": st["tick_launches"],
+            "avg_launch_us": round(st["sweep_ms"] * 1e3 / max(st["tick_launches"], 1), 3),
+            "alg_bytes_per_dof_update": ALG_BYTES_PER_DOF_UPDATE}
+    # end to end through the public API with host buffers: upload state, one barrier, read back
+    e2e = run_e2e(sim, args, torch)
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "slab2d_q1_256x256_amr3_lts4_ap_fp32",
+                       "domain_cm": [2.0, 2.0], "base": [256, 256], "max_refine": 3, "n_lts_levels": 4,
+                       "dt_barrier_ms": sim.dt, "n_elements": n_e, "n_dof": n_dof,
+                       "level_counts": st["level_counts"][:4],
+                       "initial_state": "synthetic developed front, r=1.0 cm, width 0.01 cm",
+                       "l2": "512 MiB flush buffer written between timed steps",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "dof_updates_per_step": st["dof_updates"] / args.steps,
+            "breakdown_ms_per_step": {
+                "sweep": st["sweep_ms"] / args.steps, "eta_s": st["indicator_ms"] / args.steps,
+                "amr_host": st["amr_host_ms"] / args.steps, "mesh_upload_transfer": st["transfer_ms"] / args.steps},
+            "amr_rebuilds": st["amr_rebuilds"],
+            "sweep_only_dof_updates_per_s": st["dof_updates"] / sweep_s if sweep_s > 0 else None,
+            "wall_s_timed": wall1 - wall0,
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": st["kernel_launches"],
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
+def run_e2e(sim, args, torch):
+    """Same metric through the C ABI with pinned host buffers, copies inside the timed region."""
+    n = max(2, min(args.steps, 10))
+    V = torch.empty(sim.sizes()[1] * 2, dtype=torch.float64, pin_memory=True)
+    v = torch.empty_like(V, pin_memory=True)
+    Vh = sim.read_V()
+    vh = sim.read_state()
+    sim.reset_stats()
+    h2d = d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(n):
+        nd = Vh.size
+        if V.numel() < nd:
+            V = torch.empty(nd * 2, dtype=torch.float64, pin_memory=True)
+            v = torch.empty_like(V, pin_memory=True)
+        Va, va = V.numpy()[:nd], v.numpy()[:nd]
+        Va[:] = Vh
+        va[:] = vh
+        sim.set_initial(Va, va)
+        h2d += 16 * nd
+        sim.step_barriers(1)
+        Vh = sim.read_V()
+        vh = sim.read_state()
+        d2h += 16 * Vh.size
+    t1 = time.perf_counter()
+    st = sim.stats()
+    return {"value": st["dof_updates"] / (t1 - t0), "unit": UNIT, "steps": n,
+            "h2d_bytes_per_step": h2d // n, "d2h_bytes_per_step": d2h // n}
+
+
+# ---------------------------------------------------------------------------
+# The FP64 oracle on the host cores (bounded sample of the same workload).
+# ---------------------------------------------------------------------------
+
+CPU_SAMPLE = dict(base=(64, 64, 1), barriers=6)
+
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+import workloads as W
+from oracle import lts
+prob = W.scaled(W.slab_2d_q1_256(), %(base)r).replace(precision=64)
+sim = lts.Sim(prob)
+X = sim.disc.node_coords()
+V0, v0 = W.front_state(X, (0.0, 0.0, 0.0), %(radius)r, %(width)r, %(tail)r)
+sim.V, sim.v = V0, v0
+for _ in range(%(setup)d):
+    sim.barrier()
+res = []
+for _ in range(%(steps)d):
+    d0 = sim.dof_updates
+    t0 = time.perf_counter()
+    sim.barrier()
+    res.append((sim.dof_updates - d0, time.perf_counter() - t0))
+print(json.dumps(res))
+"""
+
+
+def oracle_run(base, setup, steps, radius):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET % dict(root=ROOT, base=tuple(base), radius=radius, width=FRONT["width"],
+                                 tail=FRONT["tail"] * radius / FRONT["radius"], setup=setup, steps=steps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(args):
+    base = CPU_SAMPLE["base"]
+    # same h and front width; front radius scaled with the patch so it crosses the patch
+    radius = FRONT["radius"] * base[0] / 256.0
+    res = oracle_run(base, 3, CPU_SAMPLE["barriers"], radius)
+    dofs = sum(r[0] for r in res)
+    secs = sum(r[1] for r in res)
+    return {"value": dofs / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 numpy oracle, %dx%d-root patch of the slab (same h, physics, thresholds), "
+                      "front r=%.3f cm, %d barrier steps after 3 setup barriers, %.1f s"
+                      % (base[0], base[1], radius, len(res), secs)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    base = CPU_SAMPLE["base"]
+    radius = FRONT["radius"] * base[0] / 256.0
+    res = oracle_run(base, 3 + args.warmup, args.steps, radius)
+    dofs = sum(r[0] for r in res)
+    secs = sum(r[1] for r in res)
+    value = dofs / secs
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / len(res),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "slab2d_q1_256x256_amr3_lts4_ap_fp32",
+                   "sample": "%dx%d-root patch, same h/physics/thresholds" % (base[0], base[1])},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "FP64 numpy oracle on a %dx%d-root patch of the slab, %d barrier steps"
+                                   % (base[0], base[1], len(res))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * mdl.h -- C ABI of the GB300 explicit local space-time adaptive monodomain library.
+ *
+ * The library advances the monodomain equations (Ogiermann, Balzani, Perotti,
+ * "An Explicit Local Space-Time Adaptive Framework for Monodomain Models in
+ * Cardiac Electrophysiology", Sec. 2, Eq. monodomain) on box slabs with a
+ * symmetric interior penalty DG discretisation (Eq. monodomain-primal-formulation,
+ * Eq. monodomain-numerical-flux) on GL-collocated Q1/Q2 elements (Sec. 2.1),
+ * forest-of-trees h-adaptivity (Sec. 2.2), and synchronous local time stepping
+ * (Sec. 2.3, Alg. 1).  All stepping runs in CUDA kernels for sm_103a; the host
+ * keeps the forest bookkeeping (refine/coarsen, 2:1 balance, face tables).
+ *
+ * Conventions
+ *   - Every function returns MDL_OK (0) or a negative MDL_E_* code; no C++
+ *     exception crosses the ABI.  mdl_last_error() gives a message.
+ *   - Units: cm, ms, mS/cm, uF/cm^2; V is the dimensionless Aliev-Panfilov potential.
+ *   - The library copies every input; it never keeps a caller pointer.  All
+ *     device memory is owned by the context and released by mdl_destroy().
+ *   - Host buffers passed to mdl_read_* are caller-owned; `cap` is their capacity
+ *     in elements; `*n` receives the number of elements the full answer needs
+ *     (if cap < *n nothing is written and MDL_E_ARG is returned).
+ *   - Element (leaf) order: ascending root id (x fastest over the base grid),
+ *     then Morton order of the leaf's lower corner inside its root (x bit lowest).
+ *     DOF order: element-blocked, local node index a0 + (p+1) a1 + (p+1)^2 a2.
+ *   - A failing call leaves the context as it was, except mdl_step_to(), which
+ *     stops at the last barrier that completed.
+ *   - Calls on one context must not overlap (one host thread at a time).
+ */
+#ifndef MDL_H
+#define MDL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MDL_OK            0
+#define MDL_E_ARG        -1   /* invalid argument or size */
+#define MDL_E_NOMEM      -2   /* device or host allocation failed */
+#define MDL_E_NOSPACE    -3   /* batch: footprint does not fit the HBM budget */
+#define MDL_E_CFL        -4   /* an element needs more LTS levels than n_lts_levels allows */
+#define MDL_E_NONFINITE  -5   /* V or the state became NaN/Inf */
+#define MDL_E_TIMEOUT    -6   /* a bounded wait gave up */
+#define MDL_E_CUDA       -7   /* CUDA runtime error (message in mdl_last_error) */
+#define MDL_E_STATE      -8   /* call not valid in the context's current state */
+
+#define MDL_MAX_STIM      4
+#define MDL_MAX_REFINE    7
+
+/* Box stimulus: I_stim = -amplitude at nodes inside [lo, hi] (inclusive, 1e-12
+ * slack) for t0 <= t < t1 (Sec. 2, I' = I_ion + I_stim). */
+typedef struct mdl_stim {
+    double lo[3], hi[3];
+    double amplitude, t0, t1;
+} mdl_stim;
+
+/* One simulation (Sec. 2, Eq. monodomain with the parameters of Sec. 2.1-2.3).
+ * Copied by mdl_create. */
+typedef struct mdl_problem {
+    int32_t dim;               /* 2 or 3 */
+    int32_t order;             /* polynomial order p: 1 or 2 */
+    double  extent[3];         /* slab size [cm] (extent[2] ignored in 2D) */
+    int32_t base[3];           /* root grid (base[2] ignored in 2D) */
+    double  sigma_l, sigma_t;  /* conductivity along / across the fibre [mS/cm] */
+    double  fibre[3];          /* fibre direction (normalised by the library) */
+    double  chi, cm;           /* surface-to-volume ratio [1/cm], capacitance [uF/cm^2] */
+    double  gamma;             /* SIPG penalty factor, Eq. monodomain-numerical-flux */
+    int32_t ionic_model;       /* 0 = Aliev-Panfilov, -1 = none (pure diffusion) */
+    double  ionic_params[8];   /* AP: k, a, eps0, mu1, mu2, time_scale [ms per model unit] */
+    int32_t n_stim;            /* 0 .. MDL_MAX_STIM */
+    mdl_stim stim[MDL_MAX_STIM];
+    double  dt_barrier;        /* barrier step [ms]; 0 = largest 2^-k ms such that every
+                                  admissible element class needs <= n_lts_levels-1 levels */
+    int32_t max_refine;        /* maximum refinement depth (0 .. MDL_MAX_REFINE) */
+    int32_t n_lts_levels;      /* substeps per barrier are 2^b, b < n_lts_levels */
+    double  tau_refine, tau_coarsen;   /* Alg. 1 thresholds on eta^s */
+    double  tau_cell, dt_bar_cell;     /* Eq. num-substeps thresholds on eta^t (dt_bar_cell <= 0: off) */
+    double  act_threshold;     /* activation threshold for LAT (Sec. 3.3) */
+    int32_t state_integrator;  /* 0 forward Euler, 1 exponential (Rush-Larsen analogue) */
+    int32_t precision;         /* 32 (FP32 bulk, FP64 reductions) or 64 */
+    int32_t amr_enabled;       /* 0/1 */
+    int32_t lts_enabled;       /* 0/1; 0 = every element takes one step per barrier */
+} mdl_problem;
+
+typedef struct mdl_ctx mdl_ctx;
+
+/* Per-context counters since creation (or since mdl_reset_stats). */
+typedef struct mdl_stats {
+    int64_t barriers;          /* barrier steps completed */
+    int64_t dof_updates;       /* sum over element steps of (p+1)^d ("element evaluations") */
+    int64_t element_updates;   /* element steps */
+    int64_t tick_launches;     /* sweep kernel launches */
+    int64_t kernel_launches;   /* all kernel launches of the library */
+    int64_t amr_rebuilds;      /* barriers whose mesh changed */
+    double  sweep_ms;          /* device time of the sweep kernels (CUDA events; 0 unless timing is on) */
+    double  indicator_ms;      /* device time of the eta^s kernel (timing on) */
+    double  amr_host_ms;       /* host wall time in refine/coarsen bookkeeping */
+    double  transfer_ms;       /* host wall time to upload a rebuilt mesh + device transfer */
+    double  integral_V;        /* last FP64 integral of V over the domain */
+    int64_t n_elements;        /* current leaf count */
+    int64_t level_counts[8];   /* elements per LTS level b in the last barrier */
+} mdl_stats;
+
+/* Create a context: base grid of roots, V = v = 0 (rest), t = 0.
+ * Validates the problem (MDL_E_ARG), allocates device memory (MDL_E_NOMEM) on the
+ * current CUDA device, creates a private non-blocking stream. */
+int mdl_create(const mdl_problem* prob, mdl_ctx** out);
+
+/* Replace the mesh by the given leaves (any order; the library sorts them).
+ * level[i] in 0..max_refine; coords[i*dim + k] is the leaf's integer cell
+ * coordinate on the level-level[i] grid (0 <= c < base[k] 2^level[i]);
+ * root[i] must equal the root id containing the leaf (checked).  The leaves
+ * must tile the slab and be 2:1 face balanced (else MDL_E_ARG).  Resets V and
+ * the state to 0 and the activation times to +INF; time is unchanged. */
+int mdl_upload_mesh(mdl_ctx* ctx, int64_t n_leaves, const int32_t* root, const int8_t* level,
+                    const int32_t* coords);
+
+/* Set V and the state variable at every DOF (n_dof = n_elements (p+1)^d, leaf
+ * order).  s may be NULL (state left unchanged).  Probes already above the
+ * activation threshold get the current time as activation time. */
+int mdl_set_initial(mdl_ctx* ctx, const double* V, const double* s, int64_t n_dof);
+
+/* Replay: use these substep levels b_e (0 <= b_e < n_lts_levels) for the next
+ * barrier instead of the library's own assignment (Eq. num-substeps). */
+int mdl_set_levels(mdl_ctx* ctx, const int8_t* b_e, int64_t n_e);
+
+/* Replay: use these indicators for the next barrier's refine/coarsen decision
+ * (eta_s, Eq. dg-error-estimate) and level assignment (eta_t, Eq.
+ * ratti-veroni-temporal).  Either pointer may be NULL (keep the library's own). */
+int mdl_set_indicators(mdl_ctx* ctx, const double* eta_s, const double* eta_t, int64_t n_e);
+
+/* Advance whole barrier steps until t >= t_end - 1e-9 dt (Alg. 1 per barrier). */
+int mdl_step_to(mdl_ctx* ctx, double t_end);
+
+/* Advance exactly n barrier steps. */
+int mdl_step_barriers(mdl_ctx* ctx, int64_t n);
+
+/* Current time t = barrier_tick * dt, the barrier count, and the barrier step dt. */
+int mdl_get_time(const mdl_ctx* ctx, double* t, int64_t* barrier_tick, double* dt);
+
+int mdl_get_sizes(const mdl_ctx* ctx, int64_t* n_e, int64_t* n_dof, int64_t* n_probe);
+
+/* V, resp. the AP recovery variable, at every DOF (leaf order), as FP64. */
+int mdl_read_V(mdl_ctx* ctx, double* out, int64_t cap, int64_t* n);
+int mdl_read_state(mdl_ctx* ctx, double* out, int64_t cap, int64_t* n);
+
+/* Activation time at each probe: the GL nodes of every root element, probe id =
+ * root_id (p+1)^d + local node.  +INF = not activated (Sec. 3.3 LAT). */
+int mdl_read_activation(mdl_ctx* ctx, double* out, int64_t cap, int64_t* n);
+
+/* Mesh in leaf order: root id, level, integer coords [n*dim] on the leaf's level
+ * grid, and the substep level b_e of the last barrier.  Any pointer may be NULL. */
+int mdl_read_mesh(mdl_ctx* ctx, int32_t* root, int8_t* level, int32_t* coords, int8_t* b_e,
+                  int64_t cap, int64_t* n);
+
+/* Face table in leaf order: for element e and face f = 2 axis + (side > 0),
+ * kind[e*2d+f] = 0 boundary, 1 same level, 2 coarser neighbour, 3 finer
+ * neighbours; nbr[(e*2d+f)*2^(d-1) + j] = neighbour leaf index (j = 0 for kinds
+ * 1, 2; j = tangential child bits for kind 3), -1 where unused; pos[e*2d+f] =
+ * tangential position bits of e on a coarser neighbour's face (kind 2), else 0. */
+int mdl_read_faces(mdl_ctx* ctx, int8_t* kind, int32_t* nbr, int8_t* pos, int64_t cap, int64_t* n);
+
+/* eta^s of the last barrier's adapt step and eta^t of the last completed barrier. */
+int mdl_read_indicators(mdl_ctx* ctx, double* eta_s, double* eta_t, int64_t cap, int64_t* n);
+
+/* Counters; timing=1 records CUDA events around every sweep launch (adds a little
+ * host work per launch), 0 turns it off. */
+int mdl_get_stats(const mdl_ctx* ctx, mdl_stats* out);
+int mdl_reset_stats(mdl_ctx* ctx);
+int mdl_set_timing(mdl_ctx* ctx, int on);
+
+/* Device pointer to a resident array (valid until the next mutating call) and
+ * the context's CUDA stream.  which: 0 V (current values are in slot 0 after
+ * every barrier), 1 state, 2 activation times, 3 eta_t.  *n = element count of
+ * the array. */
+int mdl_device_view(mdl_ctx* ctx, int which, void** dptr, int64_t* n, void** stream);
+
+const char* mdl_last_error(const mdl_ctx* ctx);
+void mdl_destroy(mdl_ctx* ctx);
+
+/* Library build identifier (static string). */
+const char* mdl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDL_H */

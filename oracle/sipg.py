@@ -68,6 +68,7 @@ class Disc:
         self.nodes, self.weights = basis.gauss_legendre(self.p)
         self.ne = forest.n
         self.levels = np.array([lf[0] for lf in forest.leaves], dtype=np.int64)
+        self._blocks = {}
         self._faces()
         self.M = self.mass()
 
@@ -112,6 +113,12 @@ class Disc:
     # ------------------------------------------------------------------
     def volume_block(self, level: int) -> np.ndarray:
         """A_e[i, j] = sum_q W_q grad psi_i(x_q) . D grad psi_j(x_q)."""
+        key = ('vol', int(level))
+        if key not in self._blocks:
+            self._blocks[key] = self._volume_block(level)
+        return self._blocks[key]
+
+    def _volume_block(self, level: int) -> np.ndarray:
         h = self.forest.h(level)
         xi = basis.node_points(self.dim, self.p)
         W = basis.node_weights(self.dim, self.p) * np.prod(h / 2.0)
@@ -180,6 +187,13 @@ class Disc:
         return self.gamma * 0.5 * (Dnn / hm[k] + Dnn / hp[k])
 
     def face_block(self, k: int, sig) -> np.ndarray:
+        """Cached face block (the block only depends on the axis and the signature)."""
+        key = ('face', k, sig)
+        if key not in self._blocks:
+            self._blocks[key] = self._face_block(k, sig)
+        return self._blocks[key]
+
+    def _face_block(self, k: int, sig) -> np.ndarray:
         """2 n_p x 2 n_p block of one interior (sub)face; rows/cols [minus DOFs, plus DOFs].
 
         For test psi_i on side s and trial psi_j on side t (sign + on the minus

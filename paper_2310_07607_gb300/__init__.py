@@ -1,0 +1,6 @@
+"""GB300-native explicit local space-time adaptive monodomain stepping (SIPG-DG + S-LTS + AMR).
+
+The numerical path lives in libmdl.so (CUDA for sm_103a behind the C ABI of
+include/mdl.h); this package holds its build script and a thin ctypes binding.
+"""
+from .mdl import Sim, MdlError, load, to_c, LIB_PATH  # noqa: F401

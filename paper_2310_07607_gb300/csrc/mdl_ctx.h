@@ -1,0 +1,43 @@
+// mdl_ctx.h -- abstract context behind the C ABI; one implementation per (precision, dim, order).
+#pragma once
+
+#include <string>
+
+#include "../../include/mdl.h"
+
+namespace mdl {
+
+class CtxBase {
+public:
+    virtual ~CtxBase() {}
+    virtual int create(const mdl_problem& pb) = 0;
+    virtual int upload_mesh(int64_t n, const int32_t* root, const int8_t* level, const int32_t* coords) = 0;
+    virtual int set_initial(const double* V, const double* s, int64_t n_dof) = 0;
+    virtual int set_levels(const int8_t* b, int64_t n) = 0;
+    virtual int set_indicators(const double* eta_s, const double* eta_t, int64_t n) = 0;
+    virtual int step_barriers(int64_t n) = 0;
+    virtual int step_to(double t_end) = 0;
+    virtual int get_time(double* t, int64_t* tick, double* dt) const = 0;
+    virtual int get_sizes(int64_t* ne, int64_t* ndof, int64_t* nprobe) const = 0;
+    virtual int read_field(int which, double* out, int64_t cap, int64_t* n) = 0;
+    virtual int read_activation(double* out, int64_t cap, int64_t* n) = 0;
+    virtual int read_mesh(int32_t* root, int8_t* level, int32_t* coords, int8_t* b, int64_t cap, int64_t* n) = 0;
+    virtual int read_faces(int8_t* kind, int32_t* nbr, int8_t* pos, int64_t cap, int64_t* n) = 0;
+    virtual int read_indicators(double* eta_s, double* eta_t, int64_t cap, int64_t* n) = 0;
+    virtual int get_stats(mdl_stats* s) const = 0;
+    virtual int reset_stats() = 0;
+    virtual int set_timing(int on) = 0;
+    virtual int device_view(int which, void** p, int64_t* n, void** stream) = 0;
+    std::string err;
+};
+
+CtxBase* make_ctx_f32_2_1();
+CtxBase* make_ctx_f64_2_1();
+CtxBase* make_ctx_f32_2_2();
+CtxBase* make_ctx_f64_2_2();
+CtxBase* make_ctx_f32_3_1();
+CtxBase* make_ctx_f64_3_1();
+CtxBase* make_ctx_f32_3_2();
+CtxBase* make_ctx_f64_3_2();
+
+}  // namespace mdl

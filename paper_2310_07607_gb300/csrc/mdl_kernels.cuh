@@ -1,0 +1,590 @@
+// mdl_kernels.cuh -- CUDA kernels of one barrier step (Alg. 1) for one (precision, dim, order).
+//
+// Data layout in HBM (structure of arrays, element-blocked DOFs):
+//   V0, V1  [ne * NP]  two slots of V; element e's current value is in slot
+//                      par_e ^ (updates this barrier & 1) -- a per-element ping-pong,
+//                      so a tick reads the values at its start and writes the other slot
+//   v       [ne * NP]  Aliev-Panfilov recovery variable (element-local, in place)
+//   Ia, ga  [ne * NP]  I(u_a, t_a) and g(u_a) at the barrier start (only for S_e > 1)
+//   lvl     [ne]       b_e (bits 0-2) | parity par_e (bit 3)
+//   info    [ne]       4 bits per face: kind (0 bnd, 1 same, 2 coarser, 3 finer) | pos << 2;
+//                      bits 24-27 refinement level; bit 28 in a stimulus box; bit 29 probes pending
+//   nbr     [ne * 2d]  neighbour element (same/coarser) or first hang[] index (finer)
+//   hang    [*]        2^(d-1) fine neighbours per hanging face
+//   order   [ne]       element ids sorted by b descending: tick i updates a prefix
+//   acc     [ne]       FP64 RV-T accumulator; eta_t, eta_s [ne] FP64
+//   lat     [n_probe]  FP64 activation time per probe (+INF pending)
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/mdl.h"
+#include "mdl_element.cuh"
+
+namespace mdl {
+
+constexpr uint32_t INFO_STIM = 1u << 28;
+constexpr uint32_t INFO_PENDING = 1u << 29;
+
+struct DevStatus {
+    unsigned int cnt[8];      // elements per level b
+    unsigned int changed;     // some b_e differs from the previous barrier
+    unsigned int cfl_err;     // some b_e > B
+    unsigned int nonfinite;   // NaN/Inf in V or v after the sweep
+    unsigned int n_refine;    // refine marks
+    unsigned int n_coarsen;   // coarsen candidates
+    unsigned int pad[3];
+    double integral;          // FP64 integral of V
+};
+
+template <typename R>
+struct DevArrays {
+    R* V0;
+    R* V1;
+    R* v;
+    R* Ia;
+    R* ga;
+    double* acc;
+    double* eta_t;
+    double* eta_s;
+    double* lat;
+    double* partial;
+    uint8_t* lvl;
+    const uint8_t* bcfl;
+    uint32_t* info;
+    const int32_t* nbr;
+    const int32_t* hang;
+    const int32_t* order;
+    const int32_t* root;
+    const uint32_t* loc;
+    const uint32_t* smask[MDL_MAX_STIM];
+    DevStatus* status;
+    int64_t ne;
+};
+
+struct StimArgs {
+    int n;
+    double t0[MDL_MAX_STIM], t1[MDL_MAX_STIM], amp[MDL_MAX_STIM];
+};
+
+template <typename R>
+__device__ __forceinline__ R r_exp(R x);
+template <>
+__device__ __forceinline__ float r_exp<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double r_exp<double>(double x) { return exp(x); }
+
+template <typename R>
+__device__ __forceinline__ R ap_iion(const Phys<R>& ph, R V, R w) {
+    if (ph.ionic < 0) return R(0);
+    return (ph.k * V * (V - ph.a) * (V - R(1)) + V * w) * ph.inv_ts;
+}
+
+template <typename R>
+__device__ __forceinline__ R ap_eps(const Phys<R>& ph, R V, R w) {
+    R den = V + ph.mu2;
+    den = den > R(1e-6) ? den : R(1e-6);
+    return ph.eps0 + ph.mu1 * w / den;
+}
+
+template <typename R>
+__device__ __forceinline__ R ap_g(const Phys<R>& ph, R V, R w) {
+    if (ph.ionic < 0) return R(0);
+    const R vinf = -ph.k * V * (V - ph.a - R(1));
+    return ap_eps(ph, V, w) * (vinf - w) * ph.inv_ts;
+}
+
+template <typename R>
+__device__ __forceinline__ R ap_step_state(const Phys<R>& ph, R V, R w, R dt) {
+    if (ph.ionic < 0) return w;
+    const R vinf = -ph.k * V * (V - ph.a - R(1));
+    const R eps = ap_eps(ph, V, w);
+    if (ph.integrator == 0) return w + dt * eps * (vinf - w) * ph.inv_ts;
+    return vinf + (w - vinf) * r_exp<R>(-eps * dt * ph.inv_ts);
+}
+
+// Values of element nb as seen at tick `tick`: its current value if it is due (or
+// finer), else the linear time interpolant of its last step (Alg. 1).
+template <typename R, int NP>
+__device__ __forceinline__ void load_seen(const DevArrays<R>& d, int tick, int B, int nb, R* un) {
+    const uint8_t lv = d.lvl[nb];
+    const int b = lv & 7, par = (lv >> 3) & 1;
+    const int sh = B - b;
+    const int j = tick >> sh;
+    const int rem = tick & ((1 << sh) - 1);
+    if (rem == 0) {
+        const R* src = ((par ^ (j & 1)) ? d.V1 : d.V0) + (size_t)nb * NP;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) un[q] = src[q];
+    } else {
+        const int nw = par ^ ((j + 1) & 1);
+        const R* sn = (nw ? d.V1 : d.V0) + (size_t)nb * NP;
+        const R* so = (nw ? d.V0 : d.V1) + (size_t)nb * NP;
+        const R th = R(rem) / R(1 << sh);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const R o = so[q];
+            un[q] = o + th * (sn[q] - o);
+        }
+    }
+}
+
+// Residual r = (A u)_e with the neighbours seen at tick `tick`.
+template <typename R, int DIM, int P>
+__device__ __forceinline__ void element_residual(const DevArrays<R>& d, const Tables<R>& T,
+                                                 const Phys<R>& ph, int tick, int B, int e,
+                                                 uint32_t inf, int lev, const R* u, R* r) {
+    using S = Shape<DIM, P>;
+    constexpr int NP = S::NP, NF = S::NF, NSUB = S::NSUB;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r[q] = R(0);
+    volume_term<R, DIM, P>(T, ph, lev, u, r);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const int kind = (inf >> (4 * f)) & 3;
+        if (kind == 0) continue;
+        const int k = f >> 1, s = (f & 1) ? 1 : -1;
+        const int nbi = d.nbr[(size_t)e * NF + f];
+        if (kind != 3) {
+            R un[NP];
+            load_seen<R, NP>(d, tick, B, nbi, un);
+            const int pos = (inf >> (4 * f + 2)) & 3;
+            face_term<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
+                                 kind == 1 ? -1 : pos, un, lev, r);
+        } else {
+            for (int sb = 0; sb < NSUB; ++sb) {
+                R un[NP];
+                load_seen<R, NP>(d, tick, B, d.hang[nbi + sb], un);
+                face_term<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1, r);
+            }
+        }
+    }
+}
+
+// Probe activation check for element e after a step from u (at t_old) to un (t_old + dte).
+template <typename R, int DIM, int P>
+__device__ void lat_check(const DevArrays<R>& d, const Tables<R>& T, const Phys<R>& ph, int e,
+                          uint32_t inf, int lev, const R* u, const R* un, double t_old, double dte) {
+    using S = Shape<DIM, P>;
+    constexpr int N1 = S::N1, NP = S::NP;
+    const uint32_t lc = d.loc[e];
+    const int lx[3] = {(int)(lc & 255u), (int)((lc >> 8) & 255u), (int)((lc >> 16) & 255u)};
+    const int64_t rid = d.root[e];
+    bool pending = false;
+    for (int q = 0; q < NP; ++q) {
+        bool inside = true;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) inside = inside && (T.pfl[lev][digit<N1>(q, k)] == lx[k]);
+        if (!inside) continue;
+        double* lp = d.lat + rid * NP + q;
+        if (!isinf(*lp)) continue;
+        R po = 0, pn = 0;
+        for (int j = 0; j < NP; ++j) {
+            R w = R(1);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) w *= T.pphi[lev][digit<N1>(q, k)][digit<N1>(j, k)];
+            po += w * u[j];
+            pn += w * un[j];
+        }
+        if (po <= ph.act && pn > ph.act) {
+            *lp = t_old + dte * (double)((ph.act - po) / (pn - po));
+        } else {
+            pending = true;
+        }
+    }
+    if (!pending) d.info[e] = inf & ~INFO_PENDING;
+}
+
+template <typename R>
+struct TickArgs {
+    DevArrays<R> d;
+    StimArgs stim;
+    double t_i;        // tick start time
+    double dt;         // barrier step
+    int tick, B, n_act;
+};
+
+// One tick of Alg. 1: every due element (a prefix of `order`) takes one forward
+// Euler step on V and one exponential/FE step on v, accumulates the RV-T indicator
+// and checks its probes for activation.
+template <typename R, int DIM, int P>
+__global__ void __launch_bounds__(128) k_tick(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph) {
+    using S = Shape<DIM, P>;
+    constexpr int N1 = S::N1, NP = S::NP;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.n_act) return;
+    const DevArrays<R>& d = a.d;
+    const int e = d.order[idx];
+    const uint8_t lv = d.lvl[e];
+    const int b = lv & 7, par = (lv >> 3) & 1;
+    const int ke = a.tick >> (a.B - b);
+    const int cur = par ^ (ke & 1);
+    const R* Vc = (cur ? d.V1 : d.V0) + (size_t)e * NP;
+    R* Vd = (cur ? d.V0 : d.V1) + (size_t)e * NP;
+    R* vp = d.v + (size_t)e * NP;
+    R u[NP], w[NP], r[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        u[q] = Vc[q];
+        w[q] = vp[q];
+    }
+    const uint32_t inf = d.info[e];
+    const int lev = (inf >> 24) & 15;
+    element_residual<R, DIM, P>(d, T, ph, a.tick, a.B, e, inf, lev, u, r);
+
+    const double dte_d = ldexp(a.dt, -b);
+    const R dte = (R)dte_d;
+    const double t_mid = a.t_i + 0.5 * dte_d;
+    R stim_old[NP], stim_mid[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) stim_old[q] = stim_mid[q] = R(0);
+    if (inf & INFO_STIM) {
+        for (int s = 0; s < a.stim.n; ++s) {
+            const bool on_o = (a.stim.t0[s] <= a.t_i) && (a.t_i < a.stim.t1[s]);
+            const bool on_m = (a.stim.t0[s] <= t_mid) && (t_mid < a.stim.t1[s]);
+            if (!on_o && !on_m) continue;
+            const uint32_t m = d.smask[s][e];
+            const R amp = (R)a.stim.amp[s];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                if ((m >> q) & 1u) {
+                    if (on_o) stim_old[q] -= amp;
+                    if (on_m) stim_mid[q] -= amp;
+                }
+            }
+        }
+    }
+    R Ia[NP], ga[NP];
+    if (ke == 0) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            Ia[q] = ap_iion(ph, u[q], w[q]) + stim_old[q];
+            ga[q] = ap_g(ph, u[q], w[q]);
+        }
+        if (b > 0) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                d.Ia[(size_t)e * NP + q] = Ia[q];
+                d.ga[(size_t)e * NP + q] = ga[q];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            Ia[q] = d.Ia[(size_t)e * NP + q];
+            ga[q] = d.ga[(size_t)e * NP + q];
+        }
+    }
+    R un[NP], wn[NP];
+    R term = R(0);
+    R vmax = R(0);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        R Mq = ph.Wvol[lev];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) Mq *= T.w[digit<N1>(q, k)];
+        const R I = ap_iion(ph, u[q], w[q]) + stim_old[q];
+        un[q] = u[q] + dte * (-r[q] / Mq - I);
+        wn[q] = ap_step_state(ph, u[q], w[q], dte);
+        const R Vm = R(0.5) * (u[q] + un[q]);
+        const R wm = R(0.5) * (w[q] + wn[q]);
+        const R dI = ap_iion(ph, Vm, wm) + stim_mid[q] - Ia[q];
+        const R dg = ap_g(ph, Vm, wm) - ga[q];
+        term += Mq * (dI * dI + dg * dg);
+        const R av = un[q] < R(0) ? -un[q] : un[q];
+        vmax = av > vmax ? av : vmax;
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        Vd[q] = un[q];
+        vp[q] = wn[q];
+    }
+    const double inc = dte_d * (double)term;
+    d.acc[e] = (ke == 0) ? inc : d.acc[e] + inc;
+    if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
+        lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, a.t_i, dte_d);
+}
+
+// Kelly-type spatial indicator per element (Eq. dg-error-estimate) on the barrier-start values.
+template <typename R, int DIM, int P>
+__global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> ph) {
+    using S = Shape<DIM, P>;
+    constexpr int NP = S::NP, NF = S::NF, NSUB = S::NSUB;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= d.ne) return;
+    const int par = (d.lvl[e] >> 3) & 1;
+    const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
+    R u[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) u[q] = Vc[q];
+    const uint32_t inf = d.info[e];
+    const int lev = (inf >> 24) & 15;
+    double acc = 0.0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const int kind = (inf >> (4 * f)) & 3;
+        if (kind == 0) continue;
+        const int k = f >> 1, s = (f & 1) ? 1 : -1;
+        const int nbi = d.nbr[(size_t)e * NF + f];
+        if (kind != 3) {
+            const int pn = (d.lvl[nbi] >> 3) & 1;
+            const R* src = (pn ? d.V1 : d.V0) + (size_t)nbi * NP;
+            R un[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) un[q] = src[q];
+            const int pos = (inf >> (4 * f + 2)) & 3;
+            acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
+                                         kind == 1 ? -1 : pos, un, lev);
+        } else {
+            for (int sb = 0; sb < NSUB; ++sb) {
+                const int nb = d.hang[nbi + sb];
+                const int pn = (d.lvl[nb] >> 3) & 1;
+                const R* src = (pn ? d.V1 : d.V0) + (size_t)nb * NP;
+                R un[NP];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) un[q] = src[q];
+                acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
+            }
+        }
+    }
+    d.eta_s[e] = sqrt(acc);
+}
+
+// Refine marks and coarsening candidates (Alg. 1): counts only; the host decides.
+template <typename R>
+__global__ void k_marks(const DevArrays<R> d, double tau_r, double tau_c, int L) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= d.ne) return;
+    const int lev = (d.info[e] >> 24) & 15;
+    const double eta = d.eta_s[e];
+    if (eta >= tau_r && lev < L) atomicAdd(&d.status->n_refine, 1u);
+    if (eta <= tau_c && lev > 0) atomicAdd(&d.status->n_coarsen, 1u);
+}
+
+// Substep levels b_e = max(b^CFL_e, b^cell_e) (Eq. num-substeps), or the replayed levels.
+template <typename R>
+__global__ void k_levels(const DevArrays<R> d, const int8_t* ovr, const double* eta_t, double tau_cell,
+                         int bcell, int B, int lts) {
+    __shared__ unsigned int sc[8];
+    if (threadIdx.x < 8) sc[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < d.ne) {
+        int b;
+        if (ovr) b = ovr[e];
+        else if (!lts) b = 0;
+        else {
+            b = d.bcfl[e];
+            const int bt = (eta_t[e] > tau_cell) ? bcell : 0;
+            b = bt > b ? bt : b;
+        }
+        if (b > B || b < 0) {
+            atomicOr(&d.status->cfl_err, 1u);
+            b = b < 0 ? 0 : B;
+        }
+        const uint8_t old = d.lvl[e];
+        if ((old & 7) != b) atomicOr(&d.status->changed, 1u);
+        d.lvl[e] = (uint8_t)(b | (old & 8));
+        atomicAdd(&sc[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && sc[threadIdx.x]) atomicAdd(&d.status->cnt[threadIdx.x], sc[threadIdx.x]);
+}
+
+// Barrier epilogue: eta^t = sqrt(acc)/dt, parity flip of single-step elements, non-finite
+// check, per-block partial sums of int V = sum_q M_q V_q (FP64).
+template <typename R, int DIM, int P>
+__global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const Tables<R> T,
+                                                 const Phys<R> ph, double dt) {
+    using S = Shape<DIM, P>;
+    constexpr int N1 = S::N1, NP = S::NP;
+    __shared__ double red[256];
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double loc = 0.0;
+    if (e < d.ne) {
+        d.eta_t[e] = sqrt(d.acc[e]) / dt;
+        uint8_t lv = d.lvl[e];
+        if ((lv & 7) == 0) {
+            lv ^= 8;
+            d.lvl[e] = lv;
+        }
+        const int par = (lv >> 3) & 1;
+        const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
+        const R* w = d.v + (size_t)e * NP;
+        const int lev = (d.info[e] >> 24) & 15;
+        bool bad = false;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            double Mq = (double)ph.Wvol[lev];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) Mq *= (double)T.w[digit<N1>(q, k)];
+            const R x = Vc[q];
+            loc += Mq * (double)x;
+            bad = bad || !isfinite(x) || !isfinite(w[q]);
+        }
+        if (bad) atomicOr(&d.status->nonfinite, 1u);
+    }
+    red[threadIdx.x] = loc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) d.partial[blockIdx.x] = red[0];
+}
+
+// Deterministic final sum of the epilogue partials (one block, fixed order).
+__global__ void k_reduce_partials(const double* partial, int n, double* out);
+
+// Copy V (current slot by parity) or v to an FP64 output.
+template <typename R, int NP>
+__global__ void k_gather(const DevArrays<R> d, int which, double* out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= d.ne * NP) return;
+    const int64_t e = i / NP;
+    if (which == 0) {
+        const int par = (d.lvl[e] >> 3) & 1;
+        out[i] = (double)((par ? d.V1 : d.V0)[i]);
+    } else {
+        out[i] = (double)d.v[i];
+    }
+}
+
+// Set V (into slot 0, parity reset) and optionally v from FP64 input.
+template <typename R, int NP>
+__global__ void k_scatter_initial(DevArrays<R> d, const double* V, const double* w) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= d.ne * NP) return;
+    d.V0[i] = (R)V[i];
+    if (w) d.v[i] = (R)w[i];
+    if (i % NP == 0) d.lvl[i / NP] &= 7;
+}
+
+// Activation at the current time for probes already above threshold, and the
+// per-element pending flag (any probe of the element not yet activated).
+template <typename R, int DIM, int P>
+__global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> ph, double t, int mark_now) {
+    using S = Shape<DIM, P>;
+    constexpr int N1 = S::N1, NP = S::NP;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= d.ne) return;
+    uint32_t inf = d.info[e];
+    const int lev = (inf >> 24) & 15;
+    const int par = (d.lvl[e] >> 3) & 1;
+    const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
+    R u[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) u[q] = Vc[q];
+    const uint32_t lc = d.loc[e];
+    const int lx[3] = {(int)(lc & 255u), (int)((lc >> 8) & 255u), (int)((lc >> 16) & 255u)};
+    const int64_t rid = d.root[e];
+    bool pending = false;
+    for (int q = 0; q < NP; ++q) {
+        bool inside = true;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) inside = inside && (T.pfl[lev][digit<N1>(q, k)] == lx[k]);
+        if (!inside) continue;
+        double* lp = d.lat + rid * NP + q;
+        if (!isinf(*lp)) continue;
+        if (mark_now) {
+            R pv = 0;
+            for (int j = 0; j < NP; ++j) {
+                R w = R(1);
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) w *= T.pphi[lev][digit<N1>(q, k)][digit<N1>(j, k)];
+                pv += w * u[j];
+            }
+            if (pv > ph.act) {
+                *lp = t;
+                continue;
+            }
+        }
+        pending = true;
+    }
+    inf = pending ? (inf | INFO_PENDING) : (inf & ~INFO_PENDING);
+    d.info[e] = inf;
+}
+
+// Solution transfer after adaptation (Alg. 1 adapt steps): keep, prolong (parent
+// polynomial at the child nodes) or restrict (L2 projection with the children's GL
+// rule, exact for the diagonal GL mass).  Old arrays in `o`, new in `n` (slot 0).
+template <typename R, int DIM, int P>
+__global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* pkind, const int32_t* psrc,
+                           const int8_t* pbits, const Tables<R> T) {
+    using S = Shape<DIM, P>;
+    constexpr int N1 = S::N1, NP = S::NP, NC = 1 << DIM;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n.ne) return;
+    const int kd = pkind[i];
+    const int src = psrc[i];
+    R* Vn = n.V0 + (size_t)i * NP;
+    R* wn = n.v + (size_t)i * NP;
+    if (kd == 0) {
+        const int par = (o.lvl[src] >> 3) & 1;
+        const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NP;
+        const R* wo = o.v + (size_t)src * NP;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            Vn[q] = Vo[q];
+            wn[q] = wo[q];
+        }
+        n.eta_t[i] = o.eta_t[src];
+    } else if (kd == 1) {
+        const int bits = pbits[i];
+        const int par = (o.lvl[src] >> 3) & 1;
+        const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NP;
+        const R* wo = o.v + (size_t)src * NP;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            R a = 0, c = 0;
+            for (int j = 0; j < NP; ++j) {
+                R w = R(1);
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) w *= T.Pi[(bits >> k) & 1][digit<N1>(q, k)][digit<N1>(j, k)];
+                a += w * Vo[j];
+                c += w * wo[j];
+            }
+            Vn[q] = a;
+            wn[q] = c;
+        }
+        n.eta_t[i] = o.eta_t[src];
+    } else {
+        R a[NP], c[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) a[q] = c[q] = R(0);
+        double et = 0.0;
+        for (int cb = 0; cb < NC; ++cb) {
+            const int ch = src + cb;
+            const int par = (o.lvl[ch] >> 3) & 1;
+            const R* Vo = (par ? o.V1 : o.V0) + (size_t)ch * NP;
+            const R* wo = o.v + (size_t)ch * NP;
+            et += o.eta_t[ch];
+            for (int qc = 0; qc < NP; ++qc) {
+                R wc = R(1);
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) wc *= T.w[digit<N1>(qc, k)] * R(0.5);
+                const R xv = wc * Vo[qc], xw = wc * wo[qc];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    R w = R(1);
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) w *= T.Pi[(cb >> k) & 1][digit<N1>(qc, k)][digit<N1>(q, k)];
+                    a[q] += w * xv;
+                    c[q] += w * xw;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            R wq = R(1);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) wq *= T.w[digit<N1>(q, k)];
+            Vn[q] = a[q] / wq;
+            wn[q] = c[q] / wq;
+        }
+        n.eta_t[i] = et / NC;
+    }
+    n.lvl[i] = 0;
+}
+
+}  // namespace mdl

@@ -1,0 +1,289 @@
+// mdl_mesh.cpp -- forest bookkeeping: ordering, owner grid, face tables, adaptation.
+#include "mdl_mesh.h"
+
+#include <algorithm>
+#include <numeric>
+
+namespace mdl {
+
+void Mesh::init_params(int dim_, const int* base_, int L_) {
+    dim = dim_;
+    L = L_;
+    for (int k = 0; k < 3; ++k) base[k] = (k < dim) ? base_[k] : 1;
+    for (int k = 0; k < 3; ++k) fine[k] = (int64_t)base[k] << ((k < dim) ? L : 0);
+}
+
+void Mesh::init(int dim_, const int* base_, int L_) {
+    init_params(dim_, base_, L_);
+    leaves.clear();
+    for (int z = 0; z < base[2]; ++z)
+        for (int y = 0; y < base[1]; ++y)
+            for (int x = 0; x < base[0]; ++x) leaves.push_back(Leaf{0, {x, y, z}});
+    keys.clear();
+    std::string e;
+    set_leaves(leaves, &e);
+}
+
+int64_t Mesh::root_id(const Leaf& lf) const {
+    const int l = lf.level;
+    int64_t r[3];
+    for (int k = 0; k < 3; ++k) r[k] = (k < dim) ? (lf.c[k] >> l) : 0;
+    return r[0] + (int64_t)base[0] * (r[1] + (int64_t)base[1] * r[2]);
+}
+
+uint64_t Mesh::key(const Leaf& lf) const {
+    const int l = lf.level;
+    uint64_t loc[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) {
+        const int64_t r = lf.c[k] >> l;
+        loc[k] = (uint64_t)(lf.c[k] - (r << l)) << (L - l);
+    }
+    uint64_t m = 0;
+    for (int bit = 0; bit < L; ++bit)
+        for (int k = 0; k < dim; ++k) m |= ((loc[k] >> bit) & 1ull) << (bit * dim + k);
+    return ((uint64_t)root_id(lf) << (dim * L)) | m;
+}
+
+bool Mesh::set_leaves(std::vector<Leaf> lv, std::string* err) {
+    std::vector<uint64_t> kk(lv.size());
+    for (size_t i = 0; i < lv.size(); ++i) kk[i] = key(lv[i]);
+    std::vector<int64_t> idx(lv.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return kk[a] < kk[b]; });
+    leaves.resize(lv.size());
+    keys.resize(lv.size());
+    for (size_t i = 0; i < lv.size(); ++i) {
+        leaves[i] = lv[idx[i]];
+        keys[i] = kk[idx[i]];
+    }
+    return rebuild(err);
+}
+
+bool Mesh::rebuild(std::string* err) {
+    const int64_t nf = fine[0] * fine[1] * fine[2];
+    owner.assign(nf, -1);
+    for (int64_t i = 0; i < n(); ++i) {
+        const Leaf& lf = leaves[i];
+        if (lf.level < 0 || lf.level > L) {
+            if (err) *err = "leaf level out of range";
+            return false;
+        }
+        const int sh = L - lf.level;
+        int64_t lo[3], hi[3];
+        for (int k = 0; k < 3; ++k) {
+            if (k < dim) {
+                lo[k] = (int64_t)lf.c[k] << sh;
+                hi[k] = lo[k] + ((int64_t)1 << sh);
+                if (lf.c[k] < 0 || hi[k] > fine[k]) {
+                    if (err) *err = "leaf outside the slab";
+                    return false;
+                }
+            } else {
+                lo[k] = 0;
+                hi[k] = 1;
+            }
+        }
+        for (int64_t z = lo[2]; z < hi[2]; ++z)
+            for (int64_t y = lo[1]; y < hi[1]; ++y)
+                for (int64_t x = lo[0]; x < hi[0]; ++x) {
+                    int32_t& o = owner[x + fine[0] * (y + fine[1] * z)];
+                    if (o != -1) {
+                        if (err) *err = "leaves overlap";
+                        return false;
+                    }
+                    o = (int32_t)i;
+                }
+    }
+    for (int64_t c = 0; c < nf; ++c)
+        if (owner[c] < 0) {
+            if (err) *err = "leaves do not cover the slab";
+            return false;
+        }
+    const int NF = nfaces(), NS = nsub();
+    kind.assign(n() * NF, F_BOUNDARY);
+    pos.assign(n() * NF, 0);
+    nbr.assign(n() * NF, -1);
+    hang.clear();
+    cls.assign(n(), 0);
+    int32_t sub[4];
+    for (int64_t i = 0; i < n(); ++i) {
+        uint16_t code = 0;
+        for (int f = 0; f < NF; ++f) {
+            const int axis = f / 2, side = (f & 1) ? 1 : -1;
+            int pb = 0;
+            const int kd = neighbour(i, axis, side, sub, &pb);
+            if (kd < 0) {
+                if (err) *err = "mesh is not 2:1 face balanced";
+                return false;
+            }
+            kind[i * NF + f] = (int8_t)kd;
+            pos[i * NF + f] = (int8_t)pb;
+            if (kd == F_SAME || kd == F_COARSER) {
+                nbr[i * NF + f] = sub[0];
+            } else if (kd == F_FINER) {
+                nbr[i * NF + f] = (int32_t)hang.size();
+                for (int j = 0; j < NS; ++j) hang.push_back(sub[j]);
+            }
+            code |= (uint16_t)(kd << (2 * f));
+        }
+        cls[i] = code;
+    }
+    return true;
+}
+
+int Mesh::neighbour(int64_t i, int axis, int side, int32_t* out, int* posbits) const {
+    const Leaf& lf = leaves[i];
+    const int l = lf.level, sh = L - l;
+    int64_t cn[3] = {lf.c[0], lf.c[1], lf.c[2]};
+    cn[axis] += side;
+    const int64_t ncell = (int64_t)base[axis] << l;
+    if (cn[axis] < 0 || cn[axis] >= ncell) return F_BOUNDARY;
+    // finest cell of the neighbouring level-l cell that touches this face, at its lower tangential corner
+    int64_t fc[3];
+    for (int k = 0; k < 3; ++k) fc[k] = (k < dim) ? (cn[k] << sh) : 0;
+    if (side < 0) fc[axis] = ((cn[axis] + 1) << sh) - 1;
+    const int32_t o = owner[fc[0] + fine[0] * (fc[1] + fine[1] * fc[2])];
+    const int lo = leaves[o].level;
+    int tg[2], nt = 0;
+    for (int k = 0; k < dim; ++k)
+        if (k != axis) tg[nt++] = k;
+    if (lo == l) {
+        out[0] = o;
+        *posbits = 0;
+        return F_SAME;
+    }
+    if (lo == l - 1) {
+        out[0] = o;
+        int pb = 0;
+        for (int t = 0; t < nt; ++t) pb |= (lf.c[tg[t]] & 1) << t;
+        *posbits = pb;
+        return F_COARSER;
+    }
+    if (lo != l + 1) return -1;
+    // finer: the 2^(dim-1) children of cell cn that touch this face
+    const int shc = sh - 1;
+    for (int b = 0; b < nsub(); ++b) {
+        int64_t ch[3] = {0, 0, 0};
+        ch[axis] = 2 * cn[axis] + (side > 0 ? 0 : 1);
+        for (int t = 0; t < nt; ++t) ch[tg[t]] = 2 * (int64_t)lf.c[tg[t]] + ((b >> t) & 1);
+        int64_t f2[3];
+        for (int k = 0; k < 3; ++k) f2[k] = (k < dim) ? (ch[k] << shc) : 0;
+        const int32_t oc = owner[f2[0] + fine[0] * (f2[1] + fine[1] * f2[2])];
+        if (leaves[oc].level != l + 1) return -1;
+        out[b] = oc;
+    }
+    *posbits = 0;
+    return F_FINER;
+}
+
+// ---------------------------------------------------------------------------
+bool adapt(const Mesh& m, const double* eta, double tau_r, double tau_c, Mesh* next,
+           std::vector<int8_t>* plan_kind, std::vector<int32_t>* plan_src,
+           std::vector<int8_t>* plan_bits, std::string* err) {
+    const int64_t n = m.n();
+    const int dim = m.dim, NF = m.nfaces(), NC = 1 << dim;
+    std::vector<uint8_t> ref(n, 0);
+    std::vector<int64_t> work;
+    for (int64_t i = 0; i < n; ++i)
+        if (eta[i] >= tau_r && m.leaves[i].level < m.L) {
+            ref[i] = 1;
+            work.push_back(i);
+        }
+    // 2:1 closure: a refined leaf's coarser face neighbours must refine too
+    int32_t sub[4];
+    while (!work.empty()) {
+        const int64_t i = work.back();
+        work.pop_back();
+        for (int f = 0; f < NF; ++f) {
+            int pb;
+            const int kd = m.neighbour(i, f / 2, (f & 1) ? 1 : -1, sub, &pb);
+            if (kd == F_COARSER && !ref[sub[0]]) {
+                ref[sub[0]] = 1;
+                work.push_back(sub[0]);
+            }
+        }
+    }
+    // coarsening of complete families (siblings are contiguous in child order)
+    std::vector<uint8_t> coarsen_first(n, 0), in_coarsen(n, 0);
+    for (int64_t i = 0; i + NC <= n; ++i) {
+        const Leaf& a = m.leaves[i];
+        if (a.level == 0) continue;
+        bool first = true;
+        for (int k = 0; k < dim; ++k)
+            if (a.c[k] & 1) first = false;
+        if (!first) continue;
+        bool ok = true;
+        for (int b = 0; b < NC && ok; ++b) {
+            const Leaf& s = m.leaves[i + b];
+            if (s.level != a.level) ok = false;
+            for (int k = 0; k < dim && ok; ++k)
+                if (s.c[k] != a.c[k] + ((b >> k) & 1)) ok = false;
+            if (ok && (ref[i + b] || !(eta[i + b] <= tau_c))) ok = false;
+        }
+        if (!ok) continue;
+        // every outside face neighbour must be no finer than the children after refinement
+        for (int b = 0; b < NC && ok; ++b) {
+            for (int f = 0; f < NF && ok; ++f) {
+                const int axis = f / 2, side = (f & 1) ? 1 : -1;
+                const int cb = (b >> axis) & 1;
+                if ((side > 0 && cb == 0) || (side < 0 && cb == 1)) continue;  // inside the family
+                int pb;
+                const int kd = m.neighbour(i + b, axis, side, sub, &pb);
+                if (kd == F_FINER) ok = false;
+                else if (kd == F_SAME && ref[sub[0]]) ok = false;
+            }
+        }
+        if (ok) {
+            coarsen_first[i] = 1;
+            for (int b = 0; b < NC; ++b) in_coarsen[i + b] = 1;
+        }
+    }
+    bool changed = false;
+    std::vector<Leaf> lv;
+    struct Src { int8_t kind; int32_t src; int8_t bits; };
+    std::vector<Src> src;
+    lv.reserve(n + n / 4);
+    for (int64_t i = 0; i < n; ++i) {
+        const Leaf& a = m.leaves[i];
+        if (ref[i]) {
+            changed = true;
+            for (int b = 0; b < NC; ++b) {
+                Leaf c{a.level + 1, {2 * a.c[0] + (b & 1), 2 * a.c[1] + ((b >> 1) & 1),
+                                     dim == 3 ? 2 * a.c[2] + ((b >> 2) & 1) : 0}};
+                lv.push_back(c);
+                src.push_back(Src{P_CHILD, (int32_t)i, (int8_t)b});
+            }
+        } else if (coarsen_first[i]) {
+            changed = true;
+            Leaf p{a.level - 1, {a.c[0] >> 1, a.c[1] >> 1, dim == 3 ? a.c[2] >> 1 : 0}};
+            lv.push_back(p);
+            src.push_back(Src{P_PARENT, (int32_t)i, 0});
+        } else if (!in_coarsen[i]) {
+            lv.push_back(a);
+            src.push_back(Src{P_KEEP, (int32_t)i, 0});
+        }
+    }
+    // the new order is the sorted order of lv; refined children and coarsened
+    // parents keep the relative position of their origin, so lv is already sorted
+    next->init_params(dim, m.base, m.L);
+    next->leaves = lv;
+    next->keys.resize(lv.size());
+    for (size_t i = 0; i < lv.size(); ++i) next->keys[i] = next->key(lv[i]);
+    for (size_t i = 1; i < lv.size(); ++i)
+        if (next->keys[i] <= next->keys[i - 1]) {
+            if (err) *err = "internal: adapted leaves not in order";
+            return false;
+        }
+    if (!next->rebuild(err)) return false;
+    plan_kind->resize(lv.size());
+    plan_src->resize(lv.size());
+    plan_bits->resize(lv.size());
+    for (size_t i = 0; i < lv.size(); ++i) {
+        (*plan_kind)[i] = src[i].kind;
+        (*plan_src)[i] = src[i].src;
+        (*plan_bits)[i] = src[i].bits;
+    }
+    return changed;
+}
+
+}  // namespace mdl

@@ -1,0 +1,70 @@
+// mdl_mesh.h -- host-side forest of quad/octrees on a box slab (Sec. 2.2; Alg. 1 adapt steps).
+//
+// Leaves are (level, integer cell coordinates on the level grid), ordered by
+// (root id, Morton key of the lower corner on the finest grid).  A dense owner
+// grid on the finest level maps every finest cell to its leaf, which makes face
+// neighbour queries O(1).  The mesh is kept 2:1 face balanced.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace mdl {
+
+struct Leaf {
+    int32_t level;
+    int32_t c[3];
+};
+
+// Per-element face record kinds.
+enum FaceKind { F_BOUNDARY = 0, F_SAME = 1, F_COARSER = 2, F_FINER = 3 };
+
+// Transfer plan entry for one new leaf.
+enum PlanKind { P_KEEP = 0, P_CHILD = 1, P_PARENT = 2 };
+
+struct Mesh {
+    int dim = 2;
+    int L = 0;                 // max refinement depth
+    int base[3] = {1, 1, 1};
+    int64_t fine[3] = {1, 1, 1};
+    std::vector<Leaf> leaves;
+    std::vector<uint64_t> keys;
+    std::vector<int32_t> owner;       // finest cell -> leaf index (-1 unset)
+    // face table, 2*dim faces per leaf
+    std::vector<int8_t> kind;         // FaceKind
+    std::vector<int8_t> pos;          // tangential position bits on a coarser face
+    std::vector<int32_t> nbr;         // conforming/coarser: neighbour; finer: first index into hang
+    std::vector<int32_t> hang;        // finer neighbours, 2^(dim-1) per hanging face
+    std::vector<uint16_t> cls;        // per leaf: face configuration code sum_f kind_f 4^f (CFL class, with level)
+
+    int nfaces() const { return 2 * dim; }
+    int nsub() const { return 1 << (dim - 1); }
+    int64_t n() const { return (int64_t)leaves.size(); }
+
+    void init(int dim_, const int* base_, int L_);          // base grid of roots
+    void init_params(int dim_, const int* base_, int L_);   // sizes only, no leaves
+    uint64_t key(const Leaf& lf) const;
+    int64_t root_id(const Leaf& lf) const;
+    // Replace leaves (sorted internally); returns false + message if not a balanced tiling.
+    bool set_leaves(std::vector<Leaf> lv, std::string* err);
+    // Rebuild owner grid and face tables from `leaves`.
+    bool rebuild(std::string* err);
+    // Neighbour of leaf i across face (axis, side): kind, and data (neighbour index or
+    // subface leaf list).
+    int neighbour(int64_t i, int axis, int side, int32_t* out, int* posbits) const;
+};
+
+// One refine-then-coarsen step (Alg. 1):
+//   refine leaves with eta >= tau_r (level < L), close under 2:1 balance,
+//   coarsen complete untouched families with every eta <= tau_c whose outside
+//   face neighbours are no finer than the children.
+// Fills `next` (a new mesh with rebuilt tables) and the plan for every new leaf:
+// plan_kind, plan_src (keep: old index; child: old parent; parent: old first child)
+// and plan_bits (child bits).  Returns whether anything changed.
+bool adapt(const Mesh& m, const double* eta, double tau_r, double tau_c, Mesh* next,
+           std::vector<int8_t>* plan_kind, std::vector<int32_t>* plan_src,
+           std::vector<int8_t>* plan_bits, std::string* err);
+
+}  // namespace mdl

@@ -1,0 +1,292 @@
+"""Thin ctypes binding of libmdl.so (include/mdl.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  There is no CPU fallback -- if the library is missing or the device
+is unavailable, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmdl.so")
+
+MDL_MAX_STIM = 4
+
+ERRORS = {
+    -1: "MDL_E_ARG", -2: "MDL_E_NOMEM", -3: "MDL_E_NOSPACE", -4: "MDL_E_CFL",
+    -5: "MDL_E_NONFINITE", -6: "MDL_E_TIMEOUT", -7: "MDL_E_CUDA", -8: "MDL_E_STATE",
+}
+
+
+class MdlError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class CStim(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("amplitude", C.c_double), ("t0", C.c_double), ("t1", C.c_double)]
+
+
+class CProblem(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("order", C.c_int32),
+        ("extent", C.c_double * 3), ("base", C.c_int32 * 3),
+        ("sigma_l", C.c_double), ("sigma_t", C.c_double), ("fibre", C.c_double * 3),
+        ("chi", C.c_double), ("cm", C.c_double), ("gamma", C.c_double),
+        ("ionic_model", C.c_int32), ("ionic_params", C.c_double * 8),
+        ("n_stim", C.c_int32), ("stim", CStim * MDL_MAX_STIM),
+        ("dt_barrier", C.c_double),
+        ("max_refine", C.c_int32), ("n_lts_levels", C.c_int32),
+        ("tau_refine", C.c_double), ("tau_coarsen", C.c_double),
+        ("tau_cell", C.c_double), ("dt_bar_cell", C.c_double),
+        ("act_threshold", C.c_double),
+        ("state_integrator", C.c_int32), ("precision", C.c_int32),
+        ("amr_enabled", C.c_int32), ("lts_enabled", C.c_int32),
+    ]
+
+
+class CStats(C.Structure):
+    _fields_ = [
+        ("barriers", C.c_int64), ("dof_updates", C.c_int64), ("element_updates", C.c_int64),
+        ("tick_launches", C.c_int64), ("kernel_launches", C.c_int64), ("amr_rebuilds", C.c_int64),
+        ("sweep_ms", C.c_double), ("indicator_ms", C.c_double), ("amr_host_ms", C.c_double),
+        ("transfer_ms", C.c_double), ("integral_V", C.c_double),
+        ("n_elements", C.c_int64), ("level_counts", C.c_int64 * 8),
+    ]
+
+
+EXPORTS = [
+    "mdl_create", "mdl_upload_mesh", "mdl_set_initial", "mdl_set_levels", "mdl_set_indicators",
+    "mdl_step_to", "mdl_step_barriers", "mdl_get_time", "mdl_get_sizes", "mdl_read_V",
+    "mdl_read_state", "mdl_read_activation", "mdl_read_mesh", "mdl_read_faces",
+    "mdl_read_indicators", "mdl_get_stats", "mdl_reset_stats", "mdl_set_timing",
+    "mdl_device_view", "mdl_last_error", "mdl_destroy", "mdl_version",
+]
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load libmdl.so (built by paper_2310_07607_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libmdl.so not built (%s): run __graft_entry__.build()" % p)
+    lib = C.CDLL(p)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+    dp = C.POINTER(C.c_double)
+    lib.mdl_create.argtypes = [C.POINTER(CProblem), C.POINTER(vp)]
+    lib.mdl_upload_mesh.argtypes = [vp, i64, vp, vp, vp]
+    lib.mdl_set_initial.argtypes = [vp, vp, vp, i64]
+    lib.mdl_set_levels.argtypes = [vp, vp, i64]
+    lib.mdl_set_indicators.argtypes = [vp, vp, vp, i64]
+    lib.mdl_step_to.argtypes = [vp, C.c_double]
+    lib.mdl_step_barriers.argtypes = [vp, i64]
+    lib.mdl_get_time.argtypes = [vp, dp, C.POINTER(i64), dp]
+    lib.mdl_get_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    for f in ("mdl_read_V", "mdl_read_state", "mdl_read_activation"):
+        getattr(lib, f).argtypes = [vp, vp, i64, C.POINTER(i64)]
+    lib.mdl_read_mesh.argtypes = [vp, vp, vp, vp, vp, i64, C.POINTER(i64)]
+    lib.mdl_read_faces.argtypes = [vp, vp, vp, vp, i64, C.POINTER(i64)]
+    lib.mdl_read_indicators.argtypes = [vp, vp, vp, i64, C.POINTER(i64)]
+    lib.mdl_get_stats.argtypes = [vp, C.POINTER(CStats)]
+    lib.mdl_reset_stats.argtypes = [vp]
+    lib.mdl_set_timing.argtypes = [vp, i32]
+    lib.mdl_device_view.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp)]
+    lib.mdl_last_error.argtypes = [vp]
+    lib.mdl_last_error.restype = C.c_char_p
+    lib.mdl_destroy.argtypes = [vp]
+    lib.mdl_destroy.restype = None
+    lib.mdl_version.restype = C.c_char_p
+    for f in EXPORTS:
+        if f not in ("mdl_last_error", "mdl_destroy", "mdl_version"):
+            getattr(lib, f).restype = i32
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def to_c(prob) -> CProblem:
+    """Marshal a workloads.Problem into the C struct."""
+    c = CProblem()
+    c.dim, c.order = prob.dim, prob.order
+    for k in range(3):
+        c.extent[k] = float(prob.extent[k])
+        c.base[k] = int(prob.base[k])
+        c.fibre[k] = float(prob.fibre[k])
+    c.sigma_l, c.sigma_t = prob.sigma_l, prob.sigma_t
+    c.chi, c.cm, c.gamma = prob.chi, prob.cm, prob.gamma
+    c.ionic_model = prob.ionic_model
+    ip = list(prob.ionic_params) + [0.0] * 8
+    for i in range(8):
+        c.ionic_params[i] = float(ip[i])
+    if len(prob.stimuli) > MDL_MAX_STIM:
+        raise ValueError("at most %d stimuli" % MDL_MAX_STIM)
+    c.n_stim = len(prob.stimuli)
+    for i, s in enumerate(prob.stimuli):
+        for k in range(3):
+            c.stim[i].lo[k] = float(s.lo[k])
+            c.stim[i].hi[k] = float(s.hi[k])
+        c.stim[i].amplitude, c.stim[i].t0, c.stim[i].t1 = s.amplitude, s.t0, s.t1
+    c.dt_barrier = prob.dt_barrier
+    c.max_refine, c.n_lts_levels = prob.max_refine, prob.n_lts_levels
+    c.tau_refine = prob.tau_refine if math.isfinite(prob.tau_refine) else 1e308
+    c.tau_coarsen = prob.tau_coarsen
+    c.tau_cell = prob.tau_cell if math.isfinite(prob.tau_cell) else 1e308
+    c.dt_bar_cell = prob.dt_bar_cell
+    c.act_threshold = prob.act_threshold
+    c.state_integrator, c.precision = prob.state_integrator, prob.precision
+    c.amr_enabled, c.lts_enabled = prob.amr_enabled, prob.lts_enabled
+    return c
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+class Sim:
+    """One simulation context (mdl_ctx) on the current CUDA device."""
+
+    def __init__(self, prob, lib=None):
+        self.lib = lib or load()
+        self.prob = prob
+        self._c = to_c(prob)
+        h = C.c_void_p()
+        rc = self.lib.mdl_create(C.byref(self._c), C.byref(h))
+        if rc != 0:
+            raise MdlError(rc, self.lib.mdl_last_error(None).decode())
+        self.h = h
+
+    # ---------------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise MdlError(rc, self.lib.mdl_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mdl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------
+    def upload_mesh(self, level, coords, root=None):
+        level = np.ascontiguousarray(level, dtype=np.int8)
+        coords = np.ascontiguousarray(coords, dtype=np.int32)
+        r = None if root is None else np.ascontiguousarray(root, dtype=np.int32)
+        self._check(self.lib.mdl_upload_mesh(self.h, level.size, _ptr(r), _ptr(level), _ptr(coords)))
+
+    def set_initial(self, V, s=None):
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        sv = None if s is None else np.ascontiguousarray(s, dtype=np.float64)
+        self._check(self.lib.mdl_set_initial(self.h, _ptr(V), _ptr(sv), V.size))
+
+    def set_levels(self, b):
+        b = np.ascontiguousarray(b, dtype=np.int8)
+        self._check(self.lib.mdl_set_levels(self.h, _ptr(b), b.size))
+
+    def set_indicators(self, eta_s=None, eta_t=None):
+        n = self.sizes()[0]
+        es = None if eta_s is None else np.ascontiguousarray(eta_s, dtype=np.float64)
+        et = None if eta_t is None else np.ascontiguousarray(eta_t, dtype=np.float64)
+        self._check(self.lib.mdl_set_indicators(self.h, _ptr(es), _ptr(et), n))
+
+    def step_to(self, t_end: float):
+        self._check(self.lib.mdl_step_to(self.h, float(t_end)))
+
+    def step_barriers(self, n: int):
+        self._check(self.lib.mdl_step_barriers(self.h, int(n)))
+
+    def time(self):
+        t, dt = C.c_double(), C.c_double()
+        k = C.c_int64()
+        self._check(self.lib.mdl_get_time(self.h, C.byref(t), C.byref(k), C.byref(dt)))
+        return t.value, k.value, dt.value
+
+    @property
+    def dt(self) -> float:
+        return self.time()[2]
+
+    def sizes(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self.lib.mdl_get_sizes(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def _read(self, fn, n):
+        out = np.empty(n, dtype=np.float64)
+        got = C.c_int64()
+        self._check(fn(self.h, _ptr(out), n, C.byref(got)))
+        return out
+
+    def read_V(self):
+        return self._read(self.lib.mdl_read_V, self.sizes()[1])
+
+    def read_state(self):
+        return self._read(self.lib.mdl_read_state, self.sizes()[1])
+
+    def read_activation(self):
+        return self._read(self.lib.mdl_read_activation, self.sizes()[2])
+
+    def read_mesh(self):
+        n = self.sizes()[0]
+        d = self.prob.dim
+        root = np.empty(n, np.int32)
+        level = np.empty(n, np.int8)
+        coords = np.empty(n * d, np.int32)
+        b = np.empty(n, np.int8)
+        got = C.c_int64()
+        self._check(self.lib.mdl_read_mesh(self.h, _ptr(root), _ptr(level), _ptr(coords), _ptr(b), n,
+                                           C.byref(got)))
+        return root, level, coords.reshape(n, d), b
+
+    def read_faces(self):
+        n = self.sizes()[0]
+        d = self.prob.dim
+        nf, ns = 2 * d, 1 << (d - 1)
+        kind = np.empty(n * nf, np.int8)
+        nbr = np.empty(n * nf * ns, np.int32)
+        pos = np.empty(n * nf, np.int8)
+        got = C.c_int64()
+        self._check(self.lib.mdl_read_faces(self.h, _ptr(kind), _ptr(nbr), _ptr(pos), n, C.byref(got)))
+        return kind.reshape(n, nf), nbr.reshape(n, nf, ns), pos.reshape(n, nf)
+
+    def read_indicators(self):
+        n = self.sizes()[0]
+        es = np.empty(n)
+        et = np.empty(n)
+        got = C.c_int64()
+        self._check(self.lib.mdl_read_indicators(self.h, _ptr(es), _ptr(et), n, C.byref(got)))
+        return es, et
+
+    def stats(self) -> dict:
+        s = CStats()
+        self._check(self.lib.mdl_get_stats(self.h, C.byref(s)))
+        out = {f: getattr(s, f) for f, _ in CStats._fields_ if f != "level_counts"}
+        out["level_counts"] = list(s.level_counts)
+        return out
+
+    def reset_stats(self):
+        self._check(self.lib.mdl_reset_stats(self.h))
+
+    def set_timing(self, on: bool):
+        self._check(self.lib.mdl_set_timing(self.h, 1 if on else 0))
+
+    def device_view(self, which: int):
+        p, st = C.c_void_p(), C.c_void_p()
+        n = C.c_int64()
+        self._check(self.lib.mdl_device_view(self.h, which, C.byref(p), C.byref(n), C.byref(st)))
+        return p.value, n.value, st.value

@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 builds 1e-12 relative (M-weighted L2), FP32 builds 1e-3
+relative; activation times within one finest substep; every integer result
+(face tables, levels, meshes, clocks) bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lts
+from oracle.forest import Forest
+from tests.helpers import forest_arrays, mass_rel_l2, oracle_face_table, random_forest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mdl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2310_07607_gb300 import build, mdl as M
+    build.build()
+    return M
+
+
+def lat_compare(a, b, tol):
+    """Same activated set; activation times within tol."""
+    fa, fb = np.isfinite(a), np.isfinite(b)
+    assert np.array_equal(fa, fb), (fa.sum(), fb.sum(), np.nonzero(fa != fb)[0][:10])
+    if fa.any():
+        assert np.abs(a[fa] - b[fa]).max() <= tol
+
+
+# --------------------------------------------------------------------------
+# The plain FP64 global-step workload (32x32 Q1, 20 ms) in full.
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def plain_oracle():
+    prob = W.plain_2d_q1_32x32()
+    sim = lts.Sim(prob)
+    sim.step_to(W.PLAIN_T_END)
+    return sim
+
+
+def test_plain_fp64_full_run_matches_oracle(mdl, plain_oracle):
+    prob = W.plain_2d_q1_32x32()
+    g = mdl.Sim(prob)
+    g.step_to(W.PLAIN_T_END)
+    t, nb, dt = g.time()
+    assert nb == 2000 and dt == 0.01
+    V = g.read_V()
+    assert mass_rel_l2(plain_oracle.disc.M, V, plain_oracle.V) <= 1e-12
+    s = g.read_state()
+    assert np.abs(s - plain_oracle.v).max() <= 1e-11
+    lat_compare(g.read_activation(), plain_oracle.lat, 1e-9)
+    st = g.stats()
+    assert st["dof_updates"] == 2000 * 4096
+    assert abs(st["integral_V"] - np.sum(plain_oracle.disc.M * plain_oracle.V)) <= 1e-12 * abs(st["integral_V"])
+    g.close()
+
+
+def test_plain_fp32_run_matches_oracle_within_tolerance(mdl, plain_oracle):
+    prob = W.plain_2d_q1_32x32().replace(precision=32)
+    g = mdl.Sim(prob)
+    for T in (5.0, 10.0, 15.0, W.PLAIN_T_END):
+        g.step_to(T)
+    V = g.read_V()
+    assert mass_rel_l2(plain_oracle.disc.M, V, plain_oracle.V) <= 1e-3
+    lat_compare(g.read_activation(), plain_oracle.lat, 0.01)
+    g.close()
+
+
+# --------------------------------------------------------------------------
+# Integer work: face tables, ordering, levels, barrier length.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_face_table_bit_exact_after_upload(mdl, dim):
+    f = random_forest(dim, (5, 4, 3), 3, (1.0, 0.8, 0.6), steps=3, seed=dim)
+    prob = W.Problem(dim=dim, order=1, extent=(1.0, 0.8, 0.6), base=(5, 4, 3), max_refine=3,
+                     ionic_model=-1, precision=64)
+    g = mdl.Sim(prob)
+    lv, cc, root = forest_arrays(f)
+    perm = np.random.default_rng(0).permutation(f.n)      # any order in; canonical order out
+    g.upload_mesh(lv[perm], cc[perm], root[perm])
+    r2, l2, c2, _ = g.read_mesh()
+    assert np.array_equal(l2, lv) and np.array_equal(c2, cc) and np.array_equal(r2, root)
+    k, n, p = g.read_faces()
+    ko, no, po = oracle_face_table(f)
+    assert np.array_equal(k, ko) and np.array_equal(n, no) and np.array_equal(p, po)
+    g.close()
+
+
+@pytest.mark.parametrize("which", ["slab2d", "slab3d"])
+def test_auto_barrier_step_bit_exact(mdl, which):
+    prob = W.slab_2d_q1_256() if which == "slab2d" else W.slab_3d_q2()
+    small = W.scaled(prob, (4, 4, 2)).replace(precision=64)
+    g = mdl.Sim(small)
+    o = lts.Sim(small)
+    assert g.dt == o.dt
+    g.close()
+
+
+def test_levels_from_oracle_indicators_bit_exact(mdl):
+    prob = W.scaled(W.slab_2d_q1_256(), (12, 12, 1)).replace(precision=64, amr_enabled=0,
+                                                           dt_bar_cell=0.0, tau_cell=0.5)
+    f = random_forest(2, (12, 12, 1), 3, prob.extent, steps=3, seed=11)
+    o = lts.Sim(prob, forest=f)
+    g = mdl.Sim(prob)
+    lv, cc, root = forest_arrays(f)
+    g.upload_mesh(lv, cc, root)
+    rng = np.random.default_rng(3)
+    eta_t = rng.uniform(0, 1, f.n)
+    prob2 = prob.replace(dt_bar_cell=o.dt / 4.0)
+    o2 = lts.Sim(prob2, forest=f)
+    g2 = mdl.Sim(prob2)
+    g2.upload_mesh(lv, cc, root)
+    g2.set_indicators(eta_t=eta_t)
+    g2.step_barriers(1)
+    b = g2.read_mesh()[3]
+    assert np.array_equal(b, o2.assign_levels(eta_t))
+    # without the temporal indicator: pure CFL levels
+    g.step_barriers(1)
+    assert np.array_equal(g.read_mesh()[3], o.assign_levels(np.zeros(f.n)))
+    g.close(); g2.close()
+
+
+# --------------------------------------------------------------------------
+# Multi-level LTS sweeps with hanging faces and time interpolation.
+# --------------------------------------------------------------------------
+
+def lts_case(mdl, dim, p, seed, nbar, precision):
+    prob = W.Problem(dim=dim, order=p, extent=(0.4, 0.3, 0.2), base=(4, 3, 2), sigma_l=1.2,
+                     sigma_t=0.4, fibre=(0.6, 0.8, 0.0) if dim == 2 else (0.48, 0.64, 0.6),
+                     gamma=10.0 * p * p, max_refine=2, n_lts_levels=3, lts_enabled=1,
+                     dt_barrier=0.0, state_integrator=W.STATE_EXP, precision=precision,
+                     stimuli=[W.Stimulus((0, 0, 0), (0.1, 0.1, 0.1), 1.0, 0.0, 1.0)])
+    f = random_forest(dim, prob.base, 2, prob.extent, steps=2, seed=seed, tau=0.7)
+    o = lts.Sim(prob, forest=f)
+    X = o.disc.node_coords()
+    V0, v0 = W.front_state(X, (0, 0, 0), 0.15, 0.02, tail=0.05)
+    o.V, o.v = V0.copy(), v0.copy()
+    o._lat_initial()
+    g = mdl.Sim(prob)
+    lv, cc, root = forest_arrays(f)
+    g.upload_mesh(lv, cc, root)
+    g.set_initial(V0, v0)
+    levels = []
+    for n in range(nbar):
+        lev = o.assign_levels(o.eta_t)
+        levels.append(lev)
+        o.eta_t = o.sweep(lev)
+        o.barrier_count += 1
+    g.step_barriers(nbar)
+    return prob, o, g, levels
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_lts_hanging_fp64_matches_oracle(mdl, dim, p):
+    prob, o, g, levels = lts_case(mdl, dim, p, seed=dim * 10 + p, nbar=3, precision=64)
+    assert len(set(np.concatenate(levels).tolist())) >= 2
+    assert np.array_equal(g.read_mesh()[3], levels[-1])
+    assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-12
+    assert np.abs(g.read_state() - o.v).max() <= 1e-11
+    es, et = g.read_indicators()
+    assert np.allclose(et, o.eta_t, rtol=1e-10, atol=1e-300)
+    lat_compare(g.read_activation(), o.lat, 1e-9)
+    g.close()
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (3, 1), (3, 2)])
+def test_lts_hanging_fp32_matches_oracle(mdl, dim, p):
+    prob, o, g, levels = lts_case(mdl, dim, p, seed=dim * 10 + p, nbar=3, precision=32)
+    assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-3
+    es, et = g.read_indicators()
+    assert np.allclose(et, o.eta_t, rtol=2e-3, atol=1e-12 * et.max())
+    g.close()
+
+
+# --------------------------------------------------------------------------
+# Indicators and adaptation (replay protocol).
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,p,precision", [(2, 1, 64), (2, 1, 32), (3, 1, 64), (3, 2, 64)])
+def test_eta_s_matches_oracle(mdl, dim, p, precision):
+    prob = W.Problem(dim=dim, order=p, extent=(0.4, 0.3, 0.2), base=(4, 3, 2), sigma_l=1.2,
+                     sigma_t=0.4, fibre=(0.6, 0.8, 0.0) if dim == 2 else (0.48, 0.64, 0.6),
+                     gamma=10.0 * p * p, max_refine=2, n_lts_levels=3, lts_enabled=1,
+                     amr_enabled=1, tau_refine=1e30, tau_coarsen=-1.0, dt_barrier=0.0,
+                     precision=precision)
+    f = random_forest(dim, prob.base, 2, prob.extent, steps=2, seed=5, tau=0.7)
+    o = lts.Sim(prob, forest=f)
+    X = o.disc.node_coords()
+    V0, v0 = W.front_state(X, (0, 0, 0), 0.15, 0.02, tail=0.05)
+    g = mdl.Sim(prob)
+    lv, cc, root = forest_arrays(f)
+    g.upload_mesh(lv, cc, root)
+    g.set_initial(V0, v0)
+    g.step_barriers(1)                 # eta^s is computed on the barrier-start values
+    es, _ = g.read_indicators()
+    ref = o.disc.eta_s(V0)
+    tol = 1e-10 if precision == 64 else 2e-3
+    assert np.abs(es - ref).max() <= tol * ref.max()
+    g.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_adapt_replay_bit_exact_mesh_and_transfer(mdl, dim):
+    prob = W.Problem(dim=dim, order=1, extent=(0.4, 0.3, 0.2), base=(4, 3, 2), max_refine=3,
+                     n_lts_levels=4, lts_enabled=1, amr_enabled=1, tau_refine=0.8, tau_coarsen=0.2,
+                     dt_barrier=0.0, precision=64, state_integrator=W.STATE_EXP)
+    f = random_forest(dim, prob.base, 3, prob.extent, steps=2, seed=9, tau=0.7)
+    o = lts.Sim(prob, forest=f)
+    X = o.disc.node_coords()
+    V0, v0 = W.front_state(X, (0, 0, 0), 0.15, 0.03, tail=0.05)
+    o.V, o.v = V0.copy(), v0.copy()
+    g = mdl.Sim(prob)
+    lv, cc, root = forest_arrays(f)
+    g.upload_mesh(lv, cc, root)
+    g.set_initial(V0, v0)
+    rng = np.random.default_rng(21)
+    for step in range(3):
+        eta = rng.uniform(0, 1, o.disc.ne)
+        g.set_indicators(eta_s=eta)
+        newf, plan = o.forest.adapt(eta, prob.tau_refine, prob.tau_coarsen)
+        o.transfer(newf, plan)
+        lev = o.assign_levels(o.eta_t)
+        o.eta_t = o.sweep(lev)
+        o.barrier_count += 1
+        g.step_barriers(1)
+        r2, l2, c2, b2 = g.read_mesh()
+        lvo, cco, rto = forest_arrays(o.forest)
+        assert np.array_equal(l2, lvo) and np.array_equal(c2, cco)
+        assert np.array_equal(b2, lev)
+        assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-12
+    g.close()
+
+
+# --------------------------------------------------------------------------
+# Edge cases.
+# --------------------------------------------------------------------------
+
+def test_single_element_and_no_stimulus(mdl):
+    prob = W.plain_2d_q1_32x32().replace(base=(1, 1, 1), extent=(0.05, 0.05, 1.0), stimuli=[])
+    o = lts.Sim(prob)
+    V0 = np.array([0.3, 0.31, 0.29, 0.3])
+    o.V = V0.copy()
+    o.step_to(1.0)
+    g = mdl.Sim(prob)
+    g.set_initial(V0)
+    g.step_to(1.0)
+    assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-12
+    g.close()
+
+
+def test_bad_calls_raise_and_leave_context_usable(mdl):
+    prob = W.plain_2d_q1_32x32().replace(base=(4, 4, 1), extent=(0.125, 0.125, 1.0))
+    g = mdl.Sim(prob)
+    with pytest.raises(mdl.MdlError):
+        g.set_initial(np.zeros(7))
+    with pytest.raises(mdl.MdlError):
+        g.set_levels(np.full(16, 3, np.int8))       # no LTS levels in a plain run
+    with pytest.raises(mdl.MdlError):
+        g.upload_mesh(np.zeros(3, np.int8), np.zeros((3, 2), np.int32))  # does not tile
+    g.step_to(0.05)
+    assert g.time()[1] == 5
+    g.close()
+
+
+def test_nonfinite_state_is_reported(mdl):
+    prob = W.plain_2d_q1_32x32().replace(base=(4, 4, 1), extent=(0.125, 0.125, 1.0))
+    g = mdl.Sim(prob)
+    V = np.zeros(64)
+    V[5] = np.nan
+    g.set_initial(V)
+    with pytest.raises(mdl.MdlError) as ei:
+        g.step_barriers(2)
+    assert ei.value.code == -5
+    g.close()
