@@ -373,8 +373,8 @@ class Ctx : public CtxBase {
         }
         const double* et = ovr_eta_t ? eta_t_ovr.p : sets[cs].eta_t.p;
         k_levels<R><<<grid(ne, 256), 256, 0, st>>>(arrays(cs), ovr_levels ? lvl_ovr.p : nullptr, et, tau_cell,
-        stats.kernel_launches++;
                                                     bcell, B, pb.lts_enabled);
+        stats.kernel_launches++;
         MDL_CK(cudaGetLastError());
         const bool was_ovr = ovr_levels;
         ovr_levels = false;
