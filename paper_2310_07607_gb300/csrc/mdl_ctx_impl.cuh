@@ -281,7 +281,7 @@ class Ctx : public CtxBase {
         ovr_eta_s = false;
         int rc = zero_counters();
         if (rc) return rc;
-        k_marks<R><<<grid(ne, 256), 256, 0, st>>>(arrays(cs), pb.tau_refine, pb.tau_coarsen, pb.max_refine);
+        k_marks<R, DIM><<<grid(ne, 256), 256, 0, st>>>(arrays(cs), pb.tau_refine, pb.tau_coarsen, pb.max_refine);
         stats.kernel_launches++;
         MDL_CK(cudaGetLastError());
         rc = read_status();
@@ -290,7 +290,7 @@ class Ctx : public CtxBase {
             float ms = 0;
             if (cudaEventElapsedTime(&ms, ev[2], ev[3]) == cudaSuccess) stats.indicator_ms += ms;
         }
-        const bool possible = hst->n_refine > 0 || hst->n_coarsen >= (1u << DIM);
+        const bool possible = hst->n_refine > 0 || hst->n_coarsen > 0;
         if (!possible) return MDL_OK;
         auto t0 = std::chrono::steady_clock::now();
         std::vector<double> h_eta(ne);

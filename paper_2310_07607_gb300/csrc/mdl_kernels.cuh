@@ -32,7 +32,7 @@ struct DevStatus {
     unsigned int cfl_err;     // some b_e > B
     unsigned int nonfinite;   // NaN/Inf in V or v after the sweep
     unsigned int n_refine;    // refine marks
-    unsigned int n_coarsen;   // coarsen candidates
+    unsigned int n_coarsen;   // coarsenable families
     unsigned int pad[3];
     double integral;          // FP64 integral of V
 };
@@ -350,15 +350,50 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
     d.eta_s[e] = sqrt(acc);
 }
 
-// Refine marks and coarsening candidates (Alg. 1): counts only; the host decides.
-template <typename R>
+// Refine marks and coarsenable families (Alg. 1).  A family counts when its 2^d
+// children are consecutive leaves (child 0 first), all have eta <= tau_c, none is
+// marked for refinement, and no face neighbour outside the family is finer or a
+// same-level leaf marked for refinement.  With no refine mark this is exactly the
+// host's decision, so the host is only involved when the mesh will change.
+template <typename R, int DIM>
 __global__ void k_marks(const DevArrays<R> d, double tau_r, double tau_c, int L) {
+    constexpr int NF = 2 * DIM, NC = 1 << DIM;
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= d.ne) return;
-    const int lev = (d.info[e] >> 24) & 15;
+    const uint32_t inf = d.info[e];
+    const int lev = (inf >> 24) & 15;
     const double eta = d.eta_s[e];
     if (eta >= tau_r && lev < L) atomicAdd(&d.status->n_refine, 1u);
-    if (eta <= tau_c && lev > 0) atomicAdd(&d.status->n_coarsen, 1u);
+    if (lev == 0) return;
+    const uint32_t lc = d.loc[e];
+    for (int k = 0; k < DIM; ++k)
+        if ((lc >> (8 * k)) & 1u) return;                 // not child 0
+    if (e + NC > d.ne) return;
+    const int32_t rt = d.root[e];
+    for (int b = 0; b < NC; ++b) {
+        const int64_t c = e + b;
+        const uint32_t ic = d.info[c];
+        const int lc_ = (ic >> 24) & 15;
+        if (lc_ != lev || d.root[c] != rt) return;
+        const uint32_t lcc = d.loc[c];
+        for (int k = 0; k < DIM; ++k)
+            if (((lcc >> (8 * k)) & 255u) != ((lc >> (8 * k)) & 255u) + ((b >> k) & 1)) return;
+        const double ec = d.eta_s[c];
+        if (!(ec <= tau_c) || (ec >= tau_r && lc_ < L)) return;
+        for (int f = 0; f < NF; ++f) {
+            const int axis = f >> 1, side = (f & 1) ? 1 : -1;
+            const int cb = (b >> axis) & 1;
+            if ((side > 0 && cb == 0) || (side < 0 && cb == 1)) continue;   // inside the family
+            const int kind = (ic >> (4 * f)) & 3;
+            if (kind == 3) return;
+            if (kind == 1) {
+                const int nb = d.nbr[(size_t)c * NF + f];
+                const int ln = (d.info[nb] >> 24) & 15;
+                if (d.eta_s[nb] >= tau_r && ln < L) return;
+            }
+        }
+    }
+    atomicAdd(&d.status->n_coarsen, 1u);
 }
 
 // Substep levels b_e = max(b^CFL_e, b^cell_e) (Eq. num-substeps), or the replayed levels.

@@ -282,3 +282,37 @@ def test_nonfinite_state_is_reported(mdl):
         g.step_barriers(2)
     assert ei.value.code == -5
     g.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_coarsen_only_replay_bit_exact(mdl, dim):
+    """No refine mark: the device's exact coarsenable-family count decides alone whether the
+    host adapts; the resulting meshes must equal the oracle's."""
+    prob = W.Problem(dim=dim, order=1, extent=(0.4, 0.3, 0.2), base=(4, 3, 2), max_refine=3,
+                     n_lts_levels=4, lts_enabled=1, amr_enabled=1, tau_refine=0.8, tau_coarsen=0.2,
+                     dt_barrier=0.0, precision=64, state_integrator=W.STATE_EXP)
+    f = random_forest(dim, prob.base, 3, prob.extent, steps=3, seed=13, tau=0.6)
+    o = lts.Sim(prob, forest=f)
+    g = mdl.Sim(prob)
+    lv, cc, root = forest_arrays(f)
+    g.upload_mesh(lv, cc, root)
+    rng = np.random.default_rng(4)
+    for step in range(3):
+        # below tau_refine everywhere; about half the leaves below tau_coarsen
+        eta = rng.uniform(0.0, 0.4, o.disc.ne)
+        if step == 2:
+            eta[:] = 0.5            # nothing may change
+        g.set_indicators(eta_s=eta)
+        newf, plan = o.forest.adapt(eta, prob.tau_refine, prob.tau_coarsen)
+        o.transfer(newf, plan)
+        lev = o.assign_levels(o.eta_t)
+        o.eta_t = o.sweep(lev)
+        o.barrier_count += 1
+        before = g.stats()["amr_rebuilds"]
+        g.step_barriers(1)
+        r2, l2, c2, b2 = g.read_mesh()
+        lvo, cco, rto = forest_arrays(o.forest)
+        assert np.array_equal(l2, lvo) and np.array_equal(c2, cco)
+        changed = any(pl[0] != 'keep' for pl in plan)
+        assert (g.stats()["amr_rebuilds"] - before) == (1 if changed else 0)
+    g.close()
