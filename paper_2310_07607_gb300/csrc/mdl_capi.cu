@@ -21,7 +21,8 @@ __global__ void k_fill_inf(double* p, int64_t n) {
     if (i < n) p[i] = INFINITY;
 }
 
-__global__ void k_reduce_partials(const double* partial, int n, double* out) {
+__global__ void k_reduce_partials(const double* partial, int n, DevMeta* m) {
+    if (m->err) return;
     __shared__ double red[256];
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
@@ -31,7 +32,14 @@ __global__ void k_reduce_partials(const double* partial, int n, double* out) {
         if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = red[0];
+    if (threadIdx.x == 0) {
+        m->integral = red[0];
+        m->nbar += 1;
+        if (m->nf_pending) {
+            m->err |= ERR_NONFINITE;
+            m->nf_pending = 0;
+        }
+    }
 }
 
 }  // namespace mdl

@@ -1,15 +1,17 @@
 // mdl_ctx_impl.cuh -- context implementation for one (precision R, dim, order).
 //
-// Per barrier step (Alg. 1):
-//   1. [AMR] eta^s on the device (k_eta_s), refine/coarsen mark counts (k_marks);
-//      only if a change is possible, eta^s goes to the host, the forest adapts,
-//      the new mesh tables go up and k_transfer remaps V, v and eta^t.
-//   2. levels b_e on the device (k_levels) from the class CFL level b^CFL and eta^t;
-//      the host re-sorts the element order only when some b_e changed.
-//   3. 2^B ticks of k_tick over the due prefix of the order.
-//   4. k_epilogue + k_reduce_partials: eta^t, parities, non-finite flag, int V.
-// The host crosses to the device at most twice per barrier (status reads) plus
-// the mesh upload when the forest changed.
+// A barrier step (Alg. 1) is a fixed sequence of kernel launches on the context's
+// stream; element counts, due counts per tick, the barrier counter and errors live
+// in device memory (DevMeta), so the host never waits inside a barrier:
+//   [AMR]  k_eta_s, k_amr_mark, k_amr_close x max_refine, k_amr_family, k_amr_count,
+//          k_scan_*, k_amr_emit (current set -> other set), k_commit_count,
+//          k_owner_fill, k_mesh_tables, k_transfer, k_lat_refresh
+//   levels k_levels, k_order_count / k_order_top / k_order_scatter
+//   sweep  2^B launches of k_tick (each reads its due count from DevMeta)
+//   end    k_epilogue, k_reduce_partials (eta^t, parities, int V, counters)
+// The host reads DevMeta once at the end of each stepping call.  A capacity overflow
+// makes every later kernel skip; the host then grows the buffers and resumes at the
+// failed barrier, so results do not depend on the capacity.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,11 +19,10 @@
 #include <string.h>
 
 #include <algorithm>
-#include <chrono>
 #include <string>
-#include <unordered_map>
 #include <vector>
 
+#include "mdl_amr.cuh"
 #include "mdl_ctx.h"
 #include "mdl_kernels.cuh"
 #include "mdl_mesh.h"
@@ -33,10 +34,11 @@ template <class T>
 struct DBuf {
     T* p = nullptr;
     size_t cap = 0;
+    // (Re)allocate for n elements; contents are not preserved.
     cudaError_t ensure(size_t n) {
         if (n <= cap && p) return cudaSuccess;
         release();
-        const size_t c = n + n / 4 + 64;
+        const size_t c = n > 0 ? n : 1;
         cudaError_t e = cudaMalloc((void**)&p, c * sizeof(T));
         if (e != cudaSuccess) {
             p = nullptr;
@@ -62,391 +64,353 @@ struct DBuf {
         }                                                                           \
     } while (0)
 
+#define MDL_LAUNCHED()                                                              \
+    do {                                                                            \
+        stats.kernel_launches++;                                                    \
+        MDL_CK(cudaGetLastError());                                                 \
+    } while (0)
+
 __global__ void k_fill_inf(double* p, int64_t n);
 
 template <typename R, int DIM, int P>
 class Ctx : public CtxBase {
     using S = Shape<DIM, P>;
-    static constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB;
+    static constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB, NC = 1 << DIM;
 
-    struct StateSet {
+    // One mesh with its state.
+    struct Set {
         DBuf<R> V0, V1, v;
         DBuf<double> eta_t;
-        DBuf<uint8_t> lvl;
+        DBuf<uint8_t> lvl, bcfl;
+        DBuf<int4> coord;
+        DBuf<uint32_t> info, loc;
+        DBuf<int32_t> nbr, hang, root, order;
+        DBuf<uint32_t> smask[MDL_MAX_STIM];
         void release() {
-            V0.release(); V1.release(); v.release(); eta_t.release(); lvl.release();
+            V0.release(); V1.release(); v.release(); eta_t.release(); lvl.release(); bcfl.release();
+            coord.release(); info.release(); loc.release(); nbr.release(); hang.release(); root.release();
+            order.release();
+            for (auto& m : smask) m.release();
         }
     };
 
     mdl_problem pb{};
-    Mesh mesh;
     Tables<double> Td{};
     Phys<double> phd{};
     Tables<R> T{};
     Phys<R> ph{};
+    Grid grid_{};
+    StimBoxes sboxes{};
+    StimArgs stim{};
     double dt = 0;
     int B = 0;
-    int64_t nbar = 0;
+    int nsm = 1;
+    int64_t cap = 0;          // element capacity of every per-element array
+    int64_t ne = 0;           // host copy of the element count (valid after sync)
+    int64_t nbar = 0;         // host copy of the barrier count (valid after sync)
     int64_t n_probe = 0;
     cudaStream_t st = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    StateSet sets[2];
+    Set sets[2];
     int cs = 0;
     DBuf<R> Ia, ga;
     DBuf<double> acc, eta_s, lat, partial, scratch;
-    DBuf<uint32_t> info, loc;
-    DBuf<int32_t> nbr, hang, order, root;
-    DBuf<uint8_t> bcfl;
-    DBuf<uint32_t> smask[MDL_MAX_STIM];
-    DBuf<int8_t> lvl_ovr, pkind, pbits;
-    DBuf<int32_t> psrc;
+    DBuf<uint8_t> r, c0, class_b;
+    DBuf<int32_t> cnt, owner, bcnt, psrc;
+    DBuf<int64_t> base, bsum;
+    DBuf<int8_t> pkind, pbits, lvl_ovr;
     DBuf<double> eta_t_ovr;
-    DBuf<DevStatus> status;
-    DevStatus* hst = nullptr;
-    std::vector<int32_t> h_order;
-    std::vector<uint8_t> h_lvl;
-    unsigned int cnt[8] = {0};
-    bool need_order = true;
+    DBuf<DevMeta> meta;
+    DevMeta* hmeta = nullptr;
     bool ovr_levels = false, ovr_eta_s = false, ovr_eta_t = false;
     bool timing = false;
-    std::unordered_map<uint32_t, int> bcache;
+    bool generic_tick = false;   // one thread per element for every order (parity cross-check)
+    std::vector<cudaEvent_t> evpool;
+    size_t ev_used = 0;
+    struct EvSet {
+        cudaEvent_t a, b, c, d;
+    };
+    std::vector<EvSet> pending_ev;
     mdl_stats stats{};
 
-    // ------------------------------------------------------------------
-    DevArrays<R> arrays(int set) {
+    static int div_up(int64_t n, int64_t b) { return (int)((n + b - 1) / b); }
+    int persistent_blocks(int threads) const {
+        const int64_t need = div_up(std::max<int64_t>(cap, 1), threads);
+        return (int)std::min<int64_t>(need, (int64_t)nsm * (2048 / threads));
+    }
+
+    DevArrays<R> arrays(int s) {
         DevArrays<R> d{};
-        StateSet& s = sets[set];
-        d.V0 = s.V0.p; d.V1 = s.V1.p; d.v = s.v.p; d.eta_t = s.eta_t.p; d.lvl = s.lvl.p;
+        Set& x = sets[s];
+        d.V0 = x.V0.p; d.V1 = x.V1.p; d.v = x.v.p; d.eta_t = x.eta_t.p; d.lvl = x.lvl.p;
         d.Ia = Ia.p; d.ga = ga.p; d.acc = acc.p; d.eta_s = eta_s.p; d.lat = lat.p;
-        d.partial = partial.p; d.bcfl = bcfl.p; d.info = info.p; d.nbr = nbr.p; d.hang = hang.p;
-        d.order = order.p; d.root = root.p; d.loc = loc.p;
-        for (int s2 = 0; s2 < MDL_MAX_STIM; ++s2) d.smask[s2] = smask[s2].p;
-        d.status = status.p;
-        d.ne = mesh.n();
+        d.partial = partial.p; d.bcfl = x.bcfl.p; d.info = x.info.p; d.nbr = x.nbr.p; d.hang = x.hang.p;
+        d.order = x.order.p; d.root = x.root.p; d.loc = x.loc.p;
+        for (int k = 0; k < MDL_MAX_STIM; ++k) d.smask[k] = x.smask[k].p;
+        d.meta = meta.p;
         return d;
     }
 
-    static int grid(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
-
-    int class_b(int level, unsigned cls) {
-        if (!pb.lts_enabled) return 0;
-        const uint32_t key = ((uint32_t)level << 16) | cls;
-        auto it = bcache.find(key);
-        if (it != bcache.end()) return it->second;
-        const double c = class_cfl(Td, phd, DIM, P, level, cls);
-        int b = b_from_bound(dt, c);
-        if (b < 0 || b > 15) b = 15;
-        bcache[key] = b;
-        return b;
+    // ------------------------------------------------------------------
+    // Allocation.  Growing keeps the current set's contents.
+    int alloc_set(Set& x, int64_t c) {
+        MDL_CK(x.V0.ensure((size_t)c * NP));
+        MDL_CK(x.V1.ensure((size_t)c * NP));
+        MDL_CK(x.v.ensure((size_t)c * NP));
+        MDL_CK(x.eta_t.ensure(c));
+        MDL_CK(x.lvl.ensure(c));
+        MDL_CK(x.bcfl.ensure(c));
+        MDL_CK(x.coord.ensure(c));
+        MDL_CK(x.info.ensure(c));
+        MDL_CK(x.loc.ensure(c));
+        MDL_CK(x.nbr.ensure((size_t)c * NF));
+        MDL_CK(x.hang.ensure((size_t)c * NF * NSUB));
+        MDL_CK(x.root.ensure(c));
+        MDL_CK(x.order.ensure(c));
+        for (int s = 0; s < pb.n_stim; ++s) MDL_CK(x.smask[s].ensure(c));
+        return MDL_OK;
     }
 
-    // Upload the mesh tables of `mesh` (info, neighbours, classes, probes, stimulus masks).
-    int upload_tables() {
-        const int64_t ne = mesh.n();
-        std::vector<uint32_t> h_info(ne), h_loc(ne);
-        std::vector<int32_t> h_root(ne);
-        std::vector<uint8_t> h_b(ne);
-        std::vector<std::vector<uint32_t>> h_sm(pb.n_stim, std::vector<uint32_t>(ne, 0));
-        double xi[3];
-        for (int a = 0; a < N1; ++a) xi[a] = 0;
-        {
-            // GL nodes from the tables' weights are not stored; recompute closed form
-            if (P == 1) { xi[0] = -1.0 / sqrt(3.0); xi[1] = -xi[0]; }
-            else { xi[0] = -sqrt(0.6); xi[1] = 0.0; xi[2] = sqrt(0.6); }
-        }
-        for (int64_t e = 0; e < ne; ++e) {
-            const Leaf& lf = mesh.leaves[e];
-            uint32_t inf = 0;
-            for (int f = 0; f < NF; ++f) {
-                const uint32_t kd = (uint32_t)mesh.kind[e * NF + f] & 3u;
-                const uint32_t ps = (uint32_t)mesh.pos[e * NF + f] & 3u;
-                inf |= (kd | (ps << 2)) << (4 * f);
-            }
-            inf |= (uint32_t)lf.level << 24;
-            bool stim = false;
-            for (int s = 0; s < pb.n_stim; ++s) {
-                uint32_t m = 0;
-                for (int q = 0; q < NP; ++q) {
-                    bool in = true;
-                    for (int k = 0; k < DIM; ++k) {
-                        const double h = phd.h[lf.level][k];
-                        const double x = lf.c[k] * h + (xi[digit<N1>(q, k)] + 1.0) * 0.5 * h;
-                        if (x < pb.stim[s].lo[k] - 1e-12 || x > pb.stim[s].hi[k] + 1e-12) in = false;
-                    }
-                    if (in) m |= 1u << q;
-                }
-                h_sm[s][e] = m;
-                if (m) stim = true;
-            }
-            if (stim) inf |= INFO_STIM;
-            h_info[e] = inf;
-            const int64_t rid = mesh.root_id(lf);
-            h_root[e] = (int32_t)rid;
-            uint32_t lc = (uint32_t)lf.level << 24;
-            for (int k = 0; k < DIM; ++k) {
-                const int32_t r = lf.c[k] >> lf.level;
-                lc |= (uint32_t)(lf.c[k] - (r << lf.level)) << (8 * k);
-            }
-            h_loc[e] = lc;
-            h_b[e] = (uint8_t)class_b(lf.level, mesh.cls[e]);
-        }
-        MDL_CK(info.ensure(ne));
-        MDL_CK(loc.ensure(ne));
-        MDL_CK(root.ensure(ne));
-        MDL_CK(bcfl.ensure(ne));
-        MDL_CK(order.ensure(ne));
-        MDL_CK(nbr.ensure((size_t)ne * NF));
-        MDL_CK(hang.ensure(mesh.hang.size() + 1));
-        MDL_CK(cudaMemcpyAsync(info.p, h_info.data(), ne * 4, cudaMemcpyHostToDevice, st));
-        MDL_CK(cudaMemcpyAsync(loc.p, h_loc.data(), ne * 4, cudaMemcpyHostToDevice, st));
-        MDL_CK(cudaMemcpyAsync(root.p, h_root.data(), ne * 4, cudaMemcpyHostToDevice, st));
-        MDL_CK(cudaMemcpyAsync(bcfl.p, h_b.data(), ne, cudaMemcpyHostToDevice, st));
-        MDL_CK(cudaMemcpyAsync(nbr.p, mesh.nbr.data(), (size_t)ne * NF * 4, cudaMemcpyHostToDevice, st));
-        if (!mesh.hang.empty())
-            MDL_CK(cudaMemcpyAsync(hang.p, mesh.hang.data(), mesh.hang.size() * 4, cudaMemcpyHostToDevice, st));
-        for (int s = 0; s < pb.n_stim; ++s) {
-            MDL_CK(smask[s].ensure(ne));
-            MDL_CK(cudaMemcpyAsync(smask[s].p, h_sm[s].data(), ne * 4, cudaMemcpyHostToDevice, st));
-        }
-        MDL_CK(Ia.ensure((size_t)ne * NP));
-        MDL_CK(ga.ensure((size_t)ne * NP));
-        MDL_CK(acc.ensure(ne));
-        MDL_CK(eta_s.ensure(ne));
-        MDL_CK(partial.ensure(grid(ne, 256) + 1));
-        // host copies must stay alive until the async copies ran
+    int alloc_shared(int64_t c) {
+        MDL_CK(Ia.ensure((size_t)c * NP));
+        MDL_CK(ga.ensure((size_t)c * NP));
+        MDL_CK(acc.ensure(c));
+        MDL_CK(eta_s.ensure(c));
+        MDL_CK(r.ensure(c));
+        MDL_CK(c0.ensure(c));
+        MDL_CK(cnt.ensure(c));
+        MDL_CK(base.ensure(c));
+        MDL_CK(bsum.ensure(div_up(c, SCAN_CHUNK) + 1));
+        MDL_CK(bcnt.ensure((size_t)(div_up(c, ORD_THREADS) + 1) * 8 + 8));
+        MDL_CK(pkind.ensure(c));
+        MDL_CK(pbits.ensure(c));
+        MDL_CK(psrc.ensure(c));
+        MDL_CK(partial.ensure((size_t)nsm * 16 + 1024));
+        return MDL_OK;
+    }
+
+    template <class T2>
+    int grow_copy(DBuf<T2>& b, size_t n_new, size_t n_keep) {
+        DBuf<T2> nb;
+        MDL_CK(nb.ensure(n_new));
+        if (n_keep && b.p) MDL_CK(cudaMemcpyAsync(nb.p, b.p, n_keep * sizeof(T2), cudaMemcpyDeviceToDevice, st));
         MDL_CK(cudaStreamSynchronize(st));
-        need_order = true;
+        b.release();
+        b.p = nb.p;
+        b.cap = nb.cap;
+        nb.p = nullptr;
+        nb.cap = 0;
         return MDL_OK;
     }
 
-    int ensure_set(int s, int64_t ne) {
-        StateSet& S_ = sets[s];
-        MDL_CK(S_.V0.ensure((size_t)ne * NP));
-        MDL_CK(S_.V1.ensure((size_t)ne * NP));
-        MDL_CK(S_.v.ensure((size_t)ne * NP));
-        MDL_CK(S_.eta_t.ensure(ne));
-        MDL_CK(S_.lvl.ensure(ne));
-        return MDL_OK;
-    }
-
-    int reset_state() {
-        const int64_t ne = mesh.n();
-        int rc = ensure_set(cs, ne);
-        if (rc) return rc;
-        StateSet& S_ = sets[cs];
-        MDL_CK(cudaMemsetAsync(S_.V0.p, 0, (size_t)ne * NP * sizeof(R), st));
-        MDL_CK(cudaMemsetAsync(S_.V1.p, 0, (size_t)ne * NP * sizeof(R), st));
-        MDL_CK(cudaMemsetAsync(S_.v.p, 0, (size_t)ne * NP * sizeof(R), st));
-        MDL_CK(cudaMemsetAsync(S_.eta_t.p, 0, ne * sizeof(double), st));
-        MDL_CK(cudaMemsetAsync(S_.lvl.p, 0, ne, st));
-        MDL_CK(cudaMemsetAsync(eta_s.p, 0, ne * sizeof(double), st));
-        MDL_CK(cudaMemsetAsync(status.p, 0, sizeof(DevStatus), st));
-        k_fill_inf<<<grid(n_probe, 256), 256, 0, st>>>(lat.p, n_probe);
-        stats.kernel_launches++;
-        MDL_CK(cudaGetLastError());
-        k_lat_refresh<R, DIM, P><<<grid(ne, 128), 128, 0, st>>>(arrays(cs), T, ph, time_now(), 0);
-        stats.kernel_launches++;
-        MDL_CK(cudaGetLastError());
-        MDL_CK(cudaStreamSynchronize(st));
-        return MDL_OK;
-    }
-
-    double time_now() const { return (double)nbar * dt; }
-    double tick_time(int i) const {
-        const double nt = (double)(1 << B);
-        return ((double)nbar * nt + (double)i) * dt / nt;
-    }
-
-    int read_status() {
-        MDL_CK(cudaMemcpyAsync(hst, status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-        MDL_CK(cudaStreamSynchronize(st));
-        return MDL_OK;
-    }
-    int zero_counters() {
-        MDL_CK(cudaMemsetAsync(status.p, 0, offsetof(DevStatus, nonfinite), st));
-        MDL_CK(cudaMemsetAsync((char*)status.p + offsetof(DevStatus, n_refine), 0, 2 * sizeof(unsigned int), st));
+    int grow(int64_t need) {
+        const int64_t c = std::max<int64_t>(need + need / 2, cap * 2);
+        Set& x = sets[cs];
+        int rc;
+#define MDL_GROW(buf, per) if ((rc = grow_copy(buf, (size_t)c * (per), (size_t)ne * (per)))) return rc
+        MDL_GROW(x.V0, NP); MDL_GROW(x.V1, NP); MDL_GROW(x.v, NP); MDL_GROW(x.eta_t, 1);
+        MDL_GROW(x.lvl, 1); MDL_GROW(x.bcfl, 1); MDL_GROW(x.coord, 1); MDL_GROW(x.info, 1);
+        MDL_GROW(x.loc, 1); MDL_GROW(x.nbr, NF); MDL_GROW(x.hang, NF * NSUB); MDL_GROW(x.root, 1);
+        MDL_GROW(x.order, 1);
+        for (int s = 0; s < pb.n_stim; ++s) MDL_GROW(x.smask[s], 1);
+        MDL_GROW(eta_s, 1);
+#undef MDL_GROW
+        sets[cs ^ 1].release();
+        if ((rc = alloc_set(sets[cs ^ 1], c))) return rc;
+        Ia.release(); ga.release(); acc.release(); r.release(); c0.release();
+        cnt.release(); base.release(); bsum.release(); bcnt.release(); pkind.release(); pbits.release();
+        psrc.release();
+        if ((rc = alloc_shared(c))) return rc;
+        if (lvl_ovr.p && (rc = grow_copy(lvl_ovr, (size_t)c, (size_t)ne))) return rc;
+        if (eta_t_ovr.p && (rc = grow_copy(eta_t_ovr, (size_t)c, (size_t)ne))) return rc;
+        cap = c;
         return MDL_OK;
     }
 
     // ------------------------------------------------------------------
-    int amr_step() {
-        const int64_t ne = mesh.n();
-        if (!ovr_eta_s) {
-            if (timing) MDL_CK(cudaEventRecord(ev[2], st));
-            k_eta_s<R, DIM, P><<<grid(ne, 128), 128, 0, st>>>(arrays(cs), T, ph);
-            stats.kernel_launches++;
-            MDL_CK(cudaGetLastError());
-            if (timing) MDL_CK(cudaEventRecord(ev[3], st));
-        }
-        ovr_eta_s = false;
-        int rc = zero_counters();
-        if (rc) return rc;
-        k_marks<R, DIM><<<grid(ne, 256), 256, 0, st>>>(arrays(cs), pb.tau_refine, pb.tau_coarsen, pb.max_refine);
-        stats.kernel_launches++;
-        MDL_CK(cudaGetLastError());
-        rc = read_status();
-        if (rc) return rc;
-        if (timing) {
-            float ms = 0;
-            if (cudaEventElapsedTime(&ms, ev[2], ev[3]) == cudaSuccess) stats.indicator_ms += ms;
-        }
-        const bool possible = hst->n_refine > 0 || hst->n_coarsen > 0;
-        if (!possible) return MDL_OK;
-        auto t0 = std::chrono::steady_clock::now();
-        std::vector<double> h_eta(ne);
-        MDL_CK(cudaMemcpyAsync(h_eta.data(), eta_s.p, ne * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int sync_meta() {
+        MDL_CK(cudaMemcpyAsync(hmeta, meta.p, sizeof(DevMeta), cudaMemcpyDeviceToHost, st));
         MDL_CK(cudaStreamSynchronize(st));
-        Mesh next;
-        std::vector<int8_t> pk, pbits_h;
-        std::vector<int32_t> ps;
-        std::string e2;
-        const bool changed = adapt(mesh, h_eta.data(), pb.tau_refine, pb.tau_coarsen, &next, &pk, &ps,
-                                   &pbits_h, &e2);
-        if (!e2.empty()) {
-            err = "adapt: " + e2;
+        ne = hmeta->ne;
+        nbar = hmeta->nbar;
+        cs = (int)hmeta->cur_set;
+        stats.n_elements = ne;
+        stats.integral_V = hmeta->integral;
+        stats.element_updates = hmeta->elem_updates;
+        stats.dof_updates = hmeta->elem_updates * NP;
+        stats.amr_rebuilds = hmeta->rebuilds;
+        for (int b = 0; b < 8; ++b) stats.level_counts[b] = hmeta->cnt[b];
+        return MDL_OK;
+    }
+
+    // Build the mesh tables of set s from its coordinates (device), given ne in DevMeta.
+    int build_tables(int s) {
+        Set& x = sets[s];
+        const int gb = persistent_blocks(256);
+        k_owner_fill<DIM><<<gb, 256, 0, st>>>(x.coord.p, owner.p, grid_, meta.p);
+        MDL_LAUNCHED();
+        k_mesh_tables<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(
+            x.coord.p, owner.p, grid_, x.info.p, x.nbr.p, x.hang.p, x.root.p, x.loc.p, x.bcfl.p, class_b.p,
+            x.smask[0].p, x.smask[1].p, x.smask[2].p, x.smask[3].p, sboxes, phd, meta.p);
+        MDL_LAUNCHED();
+        return MDL_OK;
+    }
+
+    // Upload a (validated, sorted) host mesh into the current set and reset the state.
+    int load_mesh(const Mesh& mh) {
+        const int64_t n = mh.n();
+        if (n > cap) {
+            const int64_t c = std::max<int64_t>(n * 2, 4096);
+            sets[0].release();
+            sets[1].release();
+            int rc = alloc_set(sets[0], c);
+            if (!rc) rc = alloc_set(sets[1], c);
+            if (!rc) rc = alloc_shared(c);
+            if (rc) return rc;
+            cap = c;
+        }
+        std::vector<int4> hc(n);
+        for (int64_t i = 0; i < n; ++i) {
+            const Leaf& lf = mh.leaves[i];
+            hc[i] = make_int4(lf.c[0], lf.c[1], DIM == 3 ? lf.c[2] : 0, lf.level);
+        }
+        Set& x = sets[cs];
+        MDL_CK(cudaMemcpyAsync(x.coord.p, hc.data(), n * sizeof(int4), cudaMemcpyHostToDevice, st));
+        DevMeta init{};
+        init.ne = n;
+        init.nbar = nbar;
+        init.cur_set = (unsigned)cs;
+        MDL_CK(cudaMemcpyAsync(meta.p, &init, sizeof(DevMeta), cudaMemcpyHostToDevice, st));
+        int rc = build_tables(cs);
+        if (rc) return rc;
+        ne = n;
+        MDL_CK(cudaMemsetAsync(x.V0.p, 0, (size_t)n * NP * sizeof(R), st));
+        MDL_CK(cudaMemsetAsync(x.V1.p, 0, (size_t)n * NP * sizeof(R), st));
+        MDL_CK(cudaMemsetAsync(x.v.p, 0, (size_t)n * NP * sizeof(R), st));
+        MDL_CK(cudaMemsetAsync(x.eta_t.p, 0, n * sizeof(double), st));
+        MDL_CK(cudaMemsetAsync(x.lvl.p, 0, n, st));
+        MDL_CK(cudaMemsetAsync(eta_s.p, 0, n * sizeof(double), st));
+        k_fill_inf<<<div_up(n_probe, 256), 256, 0, st>>>(lat.p, n_probe);
+        MDL_LAUNCHED();
+        k_lat_refresh<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(arrays(cs), T, ph, (double)nbar * dt, 0);
+        MDL_LAUNCHED();
+        rc = sync_meta();   // the host staging buffer hc must outlive the copy
+        if (rc) return rc;
+        if (hmeta->err) {
+            err = "mesh tables: inconsistent mesh";
             return MDL_E_STATE;
         }
-        auto t1 = std::chrono::steady_clock::now();
-        stats.amr_host_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
-        if (!changed) return MDL_OK;
-        // transfer into the other state set
-        const int ns = cs ^ 1;
-        const int64_t nn = next.n();
-        rc = ensure_set(ns, nn);
-        if (rc) return rc;
-        MDL_CK(pkind.ensure(nn));
-        MDL_CK(pbits.ensure(nn));
-        MDL_CK(psrc.ensure(nn));
-        MDL_CK(cudaMemcpyAsync(pkind.p, pk.data(), nn, cudaMemcpyHostToDevice, st));
-        MDL_CK(cudaMemcpyAsync(pbits.p, pbits_h.data(), nn, cudaMemcpyHostToDevice, st));
-        MDL_CK(cudaMemcpyAsync(psrc.p, ps.data(), nn * 4, cudaMemcpyHostToDevice, st));
-        DevArrays<R> od = arrays(cs);
-        std::swap(mesh, next);
-        rc = upload_tables();
-        if (rc) return rc;
-        DevArrays<R> nd = arrays(ns);
-        k_transfer<R, DIM, P><<<grid(nn, 128), 128, 0, st>>>(od, nd, pkind.p, psrc.p, pbits.p, T);
-        stats.kernel_launches++;
-        MDL_CK(cudaGetLastError());
-        cs = ns;
-        k_lat_refresh<R, DIM, P><<<grid(nn, 128), 128, 0, st>>>(arrays(cs), T, ph, time_now(), 0);
-        stats.kernel_launches++;
-        MDL_CK(cudaGetLastError());
-        MDL_CK(cudaStreamSynchronize(st));
-        auto t2 = std::chrono::steady_clock::now();
-        stats.transfer_ms += std::chrono::duration<double, std::milli>(t2 - t1).count();
-        stats.amr_rebuilds++;
         return MDL_OK;
     }
 
-    int build_order() {
-        const int64_t ne = mesh.n();
-        h_lvl.resize(ne);
-        MDL_CK(cudaMemcpyAsync(h_lvl.data(), sets[cs].lvl.p, ne, cudaMemcpyDeviceToHost, st));
-        MDL_CK(cudaStreamSynchronize(st));
-        int64_t off[9] = {0};
-        for (int b = B; b >= 0; --b) off[B - b + 1] = off[B - b] + cnt[b];
-        h_order.resize(ne);
-        int64_t pos[8];
-        for (int b = 0; b <= B; ++b) pos[b] = off[B - b];
-        for (int64_t e = 0; e < ne; ++e) h_order[pos[h_lvl[e] & 7]++] = (int32_t)e;
-        MDL_CK(cudaMemcpyAsync(order.p, h_order.data(), ne * 4, cudaMemcpyHostToDevice, st));
-        MDL_CK(cudaStreamSynchronize(st));
-        need_order = false;
-        return MDL_OK;
-    }
-
-    int barrier() {
-        int rc;
-        if (pb.amr_enabled) {
-            rc = amr_step();
-            if (rc) return rc;
+    // ------------------------------------------------------------------
+    cudaEvent_t next_event() {
+        if (ev_used == evpool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            evpool.push_back(e);
         }
-        const int64_t ne = mesh.n();
-        rc = zero_counters();
-        if (rc) return rc;
-        const double tau_cell = pb.tau_cell;
+        return evpool[ev_used++];
+    }
+
+    // Launch one barrier step; no host synchronisation.
+    int launch_barrier() {
+        const int g256 = persistent_blocks(256), g128 = persistent_blocks(128);
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
+        if (pb.amr_enabled) {
+            const int o = cs, n = cs ^ 1;
+            Set& so = sets[o];
+            Set& sn = sets[n];
+            if (!ovr_eta_s) {
+                if (timing && (e2 = next_event())) MDL_CK(cudaEventRecord(e2, st));
+                k_eta_s<R, DIM, P><<<g128, 128, 0, st>>>(arrays(o), T, ph);
+                MDL_LAUNCHED();
+                if (timing && (e3 = next_event())) MDL_CK(cudaEventRecord(e3, st));
+            }
+            k_amr_mark<DIM><<<g256, 256, 0, st>>>(so.coord.p, eta_s.p, r.p, c0.p, meta.p, pb.tau_refine,
+                                                  pb.max_refine);
+            MDL_LAUNCHED();
+            for (int i = 0; i < pb.max_refine; ++i) {
+                k_amr_close<DIM><<<g256, 256, 0, st>>>(so.info.p, so.nbr.p, r.p, meta.p);
+                MDL_LAUNCHED();
+            }
+            k_amr_family<DIM><<<g256, 256, 0, st>>>(so.coord.p, so.info.p, so.nbr.p, eta_s.p, r.p, c0.p, meta.p,
+                                                    pb.tau_coarsen);
+            MDL_LAUNCHED();
+            k_amr_count<DIM><<<g256, 256, 0, st>>>(so.coord.p, r.p, c0.p, cnt.p, meta.p);
+            MDL_LAUNCHED();
+            const int nsb = div_up(cap, SCAN_CHUNK);
+            k_scan_blocks<<<nsb, SCAN_THREADS, 0, st>>>(cnt.p, bsum.p, meta.p);
+            MDL_LAUNCHED();
+            k_scan_top<<<1, 1024, 0, st>>>(bsum.p, meta.p, cap);
+            MDL_LAUNCHED();
+            k_scan_apply<<<nsb, SCAN_THREADS, 0, st>>>(cnt.p, bsum.p, base.p, meta.p);
+            MDL_LAUNCHED();
+            k_amr_emit<DIM><<<g256, 256, 0, st>>>(so.coord.p, r.p, c0.p, cnt.p, base.p, sn.coord.p, pkind.p,
+                                                  psrc.p, pbits.p, meta.p);
+            MDL_LAUNCHED();
+            DevArrays<R> od = arrays(o);
+            k_commit_count<<<1, 1, 0, st>>>(meta.p);
+            MDL_LAUNCHED();
+            int rc = build_tables(n);
+            if (rc) return rc;
+            k_transfer<R, DIM, P><<<g128, 128, 0, st>>>(od, arrays(n), pkind.p, psrc.p, pbits.p, T);
+            MDL_LAUNCHED();
+            k_lat_refresh<R, DIM, P><<<g128, 128, 0, st>>>(arrays(n), T, ph, 0.0, 0);
+            MDL_LAUNCHED();
+            cs = n;
+        }
         int bcell = 0;
         if (pb.dt_bar_cell > 0) {
             bcell = b_from_bound(dt, pb.dt_bar_cell);
             if (bcell < 0) bcell = 15;
         }
         const double* et = ovr_eta_t ? eta_t_ovr.p : sets[cs].eta_t.p;
-        k_levels<R><<<grid(ne, 256), 256, 0, st>>>(arrays(cs), ovr_levels ? lvl_ovr.p : nullptr, et, tau_cell,
-                                                    bcell, B, pb.lts_enabled);
-        stats.kernel_launches++;
-        MDL_CK(cudaGetLastError());
-        const bool was_ovr = ovr_levels;
-        ovr_levels = false;
-        ovr_eta_t = false;
-        rc = read_status();
-        if (rc) return rc;
-        if (hst->nonfinite) {
-            err = "V or the state is not finite";
-            return MDL_E_NONFINITE;
-        }
-        if (hst->cfl_err) {
-            err = was_ovr ? "replayed level out of range" : "an element needs more LTS levels than allowed";
-            need_order = true;
-            return MDL_E_CFL;
-        }
-        for (int b = 0; b < 8; ++b) cnt[b] = hst->cnt[b];
-        if (hst->changed || need_order) {
-            rc = build_order();
-            if (rc) return rc;
-        }
-        const int nt = 1 << B;
+        k_levels<R><<<g256, 256, 0, st>>>(arrays(cs), ovr_levels ? lvl_ovr.p : nullptr, et, pb.tau_cell, bcell, B,
+                                          pb.lts_enabled);
+        MDL_LAUNCHED();
+        const int nob = div_up(cap, ORD_THREADS);
+        k_order_count<<<nob, ORD_THREADS, 0, st>>>(sets[cs].lvl.p, bcnt.p, meta.p);
+        MDL_LAUNCHED();
+        k_order_top<<<1, 1024, 0, st>>>(bcnt.p, meta.p, B);
+        MDL_LAUNCHED();
+        k_order_scatter<<<nob, ORD_THREADS, 0, st>>>(sets[cs].lvl.p, bcnt.p, sets[cs].order.p, meta.p);
+        MDL_LAUNCHED();
         TickArgs<R> ta{};
         ta.d = arrays(cs);
         ta.dt = dt;
         ta.B = B;
-        ta.stim.n = pb.n_stim;
-        for (int s = 0; s < pb.n_stim; ++s) {
-            ta.stim.t0[s] = pb.stim[s].t0;
-            ta.stim.t1[s] = pb.stim[s].t1;
-            ta.stim.amp[s] = pb.stim[s].amplitude;
-        }
-        if (timing) MDL_CK(cudaEventRecord(ev[0], st));
-        int64_t elem_upd = 0;
+        ta.stim = stim;
+        if (timing && (e0 = next_event())) MDL_CK(cudaEventRecord(e0, st));
+        const int nt = 1 << B;
         for (int i = 0; i < nt; ++i) {
-            int64_t na = 0;
-            if (i == 0) na = ne;
-            else {
-                int tz = 0;
-                while (((i >> tz) & 1) == 0) ++tz;
-                for (int b = B - tz; b <= B; ++b) na += cnt[b];
-            }
-            if (na == 0) continue;
             ta.tick = i;
-            ta.n_act = (int)na;
-            ta.t_i = tick_time(i);
-            k_tick<R, DIM, P><<<grid(na, 128), 128, 0, st>>>(ta, T, ph);
-            stats.kernel_launches++;
-            MDL_CK(cudaGetLastError());
-            elem_upd += na;
+            if (P == 1 && !generic_tick) {
+                const int gq = (int)std::min<int64_t>(div_up(std::max<int64_t>(cap, 1) * NP, 256),
+                                                      (int64_t)nsm * 8);
+                k_tick_q1<R, DIM><<<gq, 256, 0, st>>>(ta, T, ph);
+            } else {
+                k_tick<R, DIM, P><<<g128, 128, 0, st>>>(ta, T, ph);
+            }
+            MDL_LAUNCHED();
             stats.tick_launches++;
         }
-        if (timing) MDL_CK(cudaEventRecord(ev[1], st));
-        const int nb = grid(ne, 256);
-        k_epilogue<R, DIM, P><<<nb, 256, 0, st>>>(arrays(cs), T, ph, dt);
-        stats.kernel_launches++;
-        MDL_CK(cudaGetLastError());
-        k_reduce_partials<<<1, 256, 0, st>>>(partial.p, nb, &status.p->integral);
-        stats.kernel_launches++;
-        MDL_CK(cudaGetLastError());
-        if (timing) {
-            MDL_CK(cudaEventSynchronize(ev[1]));
-            float ms = 0;
-            MDL_CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
-            stats.sweep_ms += ms;
-        }
-        nbar++;
-        stats.barriers++;
-        stats.element_updates += elem_upd;
-        stats.dof_updates += elem_upd * NP;
-        for (int b = 0; b < 8; ++b) stats.level_counts[b] = cnt[b];
-        stats.n_elements = ne;
+        if (timing && (e1 = next_event())) MDL_CK(cudaEventRecord(e1, st));
+        k_epilogue<R, DIM, P><<<g256, 256, 0, st>>>(arrays(cs), T, ph, dt);
+        MDL_LAUNCHED();
+        k_reduce_partials<<<1, 256, 0, st>>>(partial.p, g256, meta.p);
+        MDL_LAUNCHED();
+        if (timing) pending_ev.push_back({e0, e1, e2, e3});
         return MDL_OK;
+    }
+
+    void collect_timing() {
+        for (auto& x : pending_ev) {
+            float ms = 0;
+            if (x.a && x.b && cudaEventElapsedTime(&ms, x.a, x.b) == cudaSuccess) stats.sweep_ms += ms;
+            if (x.c && x.d && cudaEventElapsedTime(&ms, x.c, x.d) == cudaSuccess) stats.indicator_ms += ms;
+        }
+        pending_ev.clear();
+        ev_used = 0;
     }
 
 public:
@@ -454,13 +418,11 @@ public:
         if (st) cudaStreamSynchronize(st);
         for (auto& s : sets) s.release();
         Ia.release(); ga.release(); acc.release(); eta_s.release(); lat.release(); partial.release();
-        scratch.release(); info.release(); loc.release(); nbr.release(); hang.release(); order.release();
-        root.release(); bcfl.release(); lvl_ovr.release(); pkind.release(); pbits.release(); psrc.release();
-        eta_t_ovr.release(); status.release();
-        for (auto& m : smask) m.release();
-        if (hst) cudaFreeHost(hst);
-        for (auto& e : ev)
-            if (e) cudaEventDestroy(e);
+        scratch.release(); r.release(); c0.release(); class_b.release(); cnt.release(); owner.release();
+        bcnt.release(); psrc.release(); base.release(); bsum.release(); pkind.release(); pbits.release();
+        lvl_ovr.release(); eta_t_ovr.release(); meta.release();
+        if (hmeta) cudaFreeHost(hmeta);
+        for (auto e : evpool) cudaEventDestroy(e);
         if (st) cudaStreamDestroy(st);
     }
 
@@ -472,17 +434,69 @@ public:
         convert_tables<R>(Td, &T);
         convert_phys<R>(phd, &ph);
         dt = pb.dt_barrier > 0 ? pb.dt_barrier : auto_dt_barrier(Td, phd, DIM, P, pb.max_refine, B);
+        int dev = 0;
+        MDL_CK(cudaGetDevice(&dev));
+        MDL_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         MDL_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-        for (auto& e : ev) MDL_CK(cudaEventCreate(&e));
-        MDL_CK(cudaMallocHost((void**)&hst, sizeof(DevStatus)));
-        MDL_CK(status.ensure(1));
-        MDL_CK(cudaMemsetAsync(status.p, 0, sizeof(DevStatus), st));
-        mesh.init(DIM, pb.base, pb.max_refine);
-        n_probe = (int64_t)mesh.n() * NP;
+        MDL_CK(cudaMallocHost((void**)&hmeta, sizeof(DevMeta)));
+        memset(hmeta, 0, sizeof(DevMeta));
+        MDL_CK(meta.ensure(1));
+        for (int k = 0; k < 3; ++k) {
+            grid_.base[k] = (k < DIM) ? pb.base[k] : 1;
+            grid_.fine[k] = (k < DIM) ? ((int64_t)pb.base[k] << pb.max_refine) : 1;
+        }
+        grid_.L = pb.max_refine;
+        grid_.dim = DIM;
+        MDL_CK(owner.ensure((size_t)(grid_.fine[0] * grid_.fine[1] * grid_.fine[2])));
+        // stimulus boxes (inclusion slack applied here, once) and time windows
+        sboxes.n = pb.n_stim;
+        stim.n = pb.n_stim;
+        for (int s = 0; s < pb.n_stim; ++s) {
+            for (int k = 0; k < 3; ++k) {
+                sboxes.lo[s][k] = pb.stim[s].lo[k] - 1e-12;
+                sboxes.hi[s][k] = pb.stim[s].hi[k] + 1e-12;
+            }
+            stim.t0[s] = pb.stim[s].t0;
+            stim.t1[s] = pb.stim[s].t1;
+            stim.amp[s] = pb.stim[s].amplitude;
+        }
+        if (P == 1) {
+            sboxes.xi[0] = -1.0 / sqrt(3.0);
+            sboxes.xi[1] = 1.0 / sqrt(3.0);
+        } else {
+            sboxes.xi[0] = -sqrt(0.6);
+            sboxes.xi[1] = 0.0;
+            sboxes.xi[2] = sqrt(0.6);
+        }
+        // b^CFL of every (level, face configuration) class
+        const size_t per = (size_t)1 << (2 * NF);
+        std::vector<uint8_t> hcb((size_t)(pb.max_refine + 1) * per, 0);
+        if (pb.lts_enabled) {
+            std::vector<double> vol, face;
+            for (int l = 0; l <= pb.max_refine; ++l) {
+                level_blocks(Td, phd, DIM, P, l, &vol, &face);
+                for (size_t cfg = 0; cfg < per; ++cfg) {
+                    bool valid = true;
+                    for (int f = 0; f < NF; ++f) {
+                        const unsigned kd = (cfg >> (2 * f)) & 3u;
+                        if ((kd == 2 && l == 0) || (kd == 3 && l == pb.max_refine)) valid = false;
+                    }
+                    if (!valid) continue;
+                    const double c = class_cfl_from_blocks(Td, phd, DIM, P, l, (unsigned)cfg, vol, face);
+                    int b = b_from_bound(dt, c);
+                    if (b < 0 || b > 15) b = 15;
+                    hcb[l * per + cfg] = (uint8_t)b;
+                }
+            }
+        }
+        MDL_CK(class_b.ensure(hcb.size()));
+        MDL_CK(cudaMemcpyAsync(class_b.p, hcb.data(), hcb.size(), cudaMemcpyHostToDevice, st));
+        Mesh mh;
+        mh.init(DIM, pb.base, pb.max_refine);
+        n_probe = mh.n() * NP;
         MDL_CK(lat.ensure(n_probe));
-        int rc = upload_tables();
-        if (rc) return rc;
-        return reset_state();
+        MDL_CK(cudaStreamSynchronize(st));
+        return load_mesh(mh);
     }
 
     int upload_mesh(int64_t n, const int32_t* rt, const int8_t* level, const int32_t* coords) override {
@@ -508,14 +522,10 @@ public:
             err = "upload_mesh: " + e2;
             return MDL_E_ARG;
         }
-        std::swap(mesh, m2);
-        int rc = upload_tables();
-        if (rc) return rc;
-        return reset_state();
+        return load_mesh(m2);
     }
 
     int set_initial(const double* V, const double* s, int64_t n_dof) override {
-        const int64_t ne = mesh.n();
         if (n_dof != ne * NP || !V) {
             err = "set_initial: n_dof must be n_elements * (p+1)^d";
             return MDL_E_ARG;
@@ -523,19 +533,18 @@ public:
         MDL_CK(scratch.ensure((size_t)2 * n_dof));
         MDL_CK(cudaMemcpyAsync(scratch.p, V, n_dof * 8, cudaMemcpyHostToDevice, st));
         if (s) MDL_CK(cudaMemcpyAsync(scratch.p + n_dof, s, n_dof * 8, cudaMemcpyHostToDevice, st));
-        k_scatter_initial<R, NP><<<grid(n_dof, 256), 256, 0, st>>>(arrays(cs), scratch.p, s ? scratch.p + n_dof : nullptr);
-        stats.kernel_launches++;
-        MDL_CK(cudaGetLastError());
-        MDL_CK(cudaMemsetAsync((char*)status.p + offsetof(DevStatus, nonfinite), 0, sizeof(unsigned int), st));
-        k_lat_refresh<R, DIM, P><<<grid(ne, 128), 128, 0, st>>>(arrays(cs), T, ph, time_now(), 1);
-        stats.kernel_launches++;
-        MDL_CK(cudaGetLastError());
+        k_scatter_initial<R, NP><<<div_up(n_dof, 256), 256, 0, st>>>(arrays(cs), ne, scratch.p,
+                                                                     s ? scratch.p + n_dof : nullptr);
+        MDL_LAUNCHED();
+        MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
+        k_lat_refresh<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(arrays(cs), T, ph, (double)nbar * dt, 1);
+        MDL_LAUNCHED();
         MDL_CK(cudaStreamSynchronize(st));
         return MDL_OK;
     }
 
     int set_levels(const int8_t* b, int64_t n) override {
-        if (n != mesh.n() || !b) {
+        if (n != ne || !b) {
             err = "set_levels: size mismatch";
             return MDL_E_ARG;
         }
@@ -544,7 +553,7 @@ public:
                 err = "set_levels: level outside [0, n_lts_levels)";
                 return MDL_E_ARG;
             }
-        MDL_CK(lvl_ovr.ensure(n));
+        MDL_CK(lvl_ovr.ensure(cap));
         MDL_CK(cudaMemcpyAsync(lvl_ovr.p, b, n, cudaMemcpyHostToDevice, st));
         MDL_CK(cudaStreamSynchronize(st));
         ovr_levels = true;
@@ -552,7 +561,7 @@ public:
     }
 
     int set_indicators(const double* es, const double* et, int64_t n) override {
-        if (n != mesh.n()) {
+        if (n != ne) {
             err = "set_indicators: size mismatch";
             return MDL_E_ARG;
         }
@@ -561,7 +570,7 @@ public:
             ovr_eta_s = true;
         }
         if (et) {
-            MDL_CK(eta_t_ovr.ensure(n));
+            MDL_CK(eta_t_ovr.ensure(cap));
             MDL_CK(cudaMemcpyAsync(eta_t_ovr.p, et, n * 8, cudaMemcpyHostToDevice, st));
             ovr_eta_t = true;
         }
@@ -570,59 +579,92 @@ public:
     }
 
     int step_barriers(int64_t n) override {
-        for (int64_t i = 0; i < n; ++i) {
-            int rc = barrier();
+        int64_t done = 0;
+        int retries = 0;
+        while (done < n) {
+            const int64_t start = nbar;
+            // replayed indicators/levels apply to exactly one barrier: run it alone
+            const bool ovr = ovr_levels || ovr_eta_s || ovr_eta_t;
+            const int64_t chunk = ovr ? 1 : (n - done);
+            for (int64_t i = 0; i < chunk; ++i) {
+                int rc = launch_barrier();
+                if (rc) return rc;
+            }
+            int rc = sync_meta();
             if (rc) return rc;
+            if (timing) collect_timing();
+            done += nbar - start;
+            if (nbar > start) ovr_levels = ovr_eta_s = ovr_eta_t = false;   // consumed by a completed barrier
+            const unsigned e = hmeta->err;
+            if (e & ERR_CAPACITY) {
+                if (++retries > 8) {
+                    err = "element capacity could not be grown";
+                    return MDL_E_NOMEM;
+                }
+                rc = grow(hmeta->need);
+                if (rc) return rc;
+                MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
+                MDL_CK(cudaStreamSynchronize(st));
+                hmeta->err = 0;
+                continue;
+            }
+            if (e & ERR_NONFINITE) {
+                err = "V or the state is not finite";
+                return MDL_E_NONFINITE;
+            }
+            if (e & ERR_CFL) {
+                err = "an element needs more LTS levels than n_lts_levels allows";
+                MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
+                MDL_CK(cudaStreamSynchronize(st));
+                return MDL_E_CFL;
+            }
+            if (e & ERR_MESH) {
+                err = "internal: adapted mesh is not 2:1 balanced";
+                return MDL_E_STATE;
+            }
         }
-        int rc = read_status();
-        if (rc) return rc;
-        stats.integral_V = hst->integral;
-        if (hst->nonfinite) {
-            err = "V or the state is not finite";
-            return MDL_E_NONFINITE;
-        }
+        stats.barriers = nbar;
         return MDL_OK;
     }
 
     int step_to(double t_end) override {
-        const double nn = floor((t_end - time_now()) / dt + 1e-9);
+        const double nn = floor((t_end - (double)nbar * dt) / dt + 1e-9);
         if (nn <= 0) return MDL_OK;
         return step_barriers((int64_t)nn);
     }
 
     int get_time(double* t, int64_t* tick, double* d) const override {
-        if (t) *t = time_now();
+        if (t) *t = (double)nbar * dt;
         if (tick) *tick = nbar;
         if (d) *d = dt;
         return MDL_OK;
     }
 
-    int get_sizes(int64_t* ne, int64_t* ndof, int64_t* np) const override {
-        if (ne) *ne = mesh.n();
-        if (ndof) *ndof = mesh.n() * NP;
+    int get_sizes(int64_t* n_e, int64_t* ndof, int64_t* np) const override {
+        if (n_e) *n_e = ne;
+        if (ndof) *ndof = ne * NP;
         if (np) *np = n_probe;
         return MDL_OK;
     }
 
-    int read_field(int which, double* out, int64_t cap, int64_t* n) override {
-        const int64_t nd = mesh.n() * NP;
+    int read_field(int which, double* out, int64_t cap_, int64_t* n) override {
+        const int64_t nd = ne * NP;
         if (n) *n = nd;
-        if (cap < nd || !out) {
+        if (cap_ < nd || !out) {
             err = "read: capacity too small";
             return MDL_E_ARG;
         }
         MDL_CK(scratch.ensure(2 * nd));
-        k_gather<R, NP><<<grid(nd, 256), 256, 0, st>>>(arrays(cs), which, scratch.p);
-        stats.kernel_launches++;
-        MDL_CK(cudaGetLastError());
+        k_gather<R, NP><<<div_up(nd, 256), 256, 0, st>>>(arrays(cs), ne, which, scratch.p);
+        MDL_LAUNCHED();
         MDL_CK(cudaMemcpyAsync(out, scratch.p, nd * 8, cudaMemcpyDeviceToHost, st));
         MDL_CK(cudaStreamSynchronize(st));
         return MDL_OK;
     }
 
-    int read_activation(double* out, int64_t cap, int64_t* n) override {
+    int read_activation(double* out, int64_t cap_, int64_t* n) override {
         if (n) *n = n_probe;
-        if (cap < n_probe || !out) {
+        if (cap_ < n_probe || !out) {
             err = "read_activation: capacity too small";
             return MDL_E_ARG;
         }
@@ -631,56 +673,63 @@ public:
         return MDL_OK;
     }
 
-    int read_mesh(int32_t* rt, int8_t* level, int32_t* coords, int8_t* b, int64_t cap, int64_t* n) override {
-        const int64_t ne = mesh.n();
+    int read_mesh(int32_t* rt, int8_t* level, int32_t* coords, int8_t* b, int64_t cap_, int64_t* n) override {
         if (n) *n = ne;
-        if (cap < ne) {
+        if (cap_ < ne) {
             err = "read_mesh: capacity too small";
             return MDL_E_ARG;
         }
+        std::vector<int4> hc(ne);
+        std::vector<int32_t> hr(ne);
+        std::vector<uint8_t> hl(ne);
+        MDL_CK(cudaMemcpyAsync(hc.data(), sets[cs].coord.p, ne * sizeof(int4), cudaMemcpyDeviceToHost, st));
+        MDL_CK(cudaMemcpyAsync(hr.data(), sets[cs].root.p, ne * 4, cudaMemcpyDeviceToHost, st));
+        MDL_CK(cudaMemcpyAsync(hl.data(), sets[cs].lvl.p, ne, cudaMemcpyDeviceToHost, st));
+        MDL_CK(cudaStreamSynchronize(st));
         for (int64_t i = 0; i < ne; ++i) {
-            const Leaf& lf = mesh.leaves[i];
-            if (rt) rt[i] = (int32_t)mesh.root_id(lf);
-            if (level) level[i] = (int8_t)lf.level;
-            if (coords)
-                for (int k = 0; k < DIM; ++k) coords[i * DIM + k] = lf.c[k];
-        }
-        if (b) {
-            h_lvl.resize(ne);
-            MDL_CK(cudaMemcpyAsync(h_lvl.data(), sets[cs].lvl.p, ne, cudaMemcpyDeviceToHost, st));
-            MDL_CK(cudaStreamSynchronize(st));
-            for (int64_t i = 0; i < ne; ++i) b[i] = (int8_t)(h_lvl[i] & 7);
+            if (rt) rt[i] = hr[i];
+            if (level) level[i] = (int8_t)hc[i].w;
+            if (coords) {
+                const int c[3] = {hc[i].x, hc[i].y, hc[i].z};
+                for (int k = 0; k < DIM; ++k) coords[i * DIM + k] = c[k];
+            }
+            if (b) b[i] = (int8_t)(hl[i] & 7);
         }
         return MDL_OK;
     }
 
-    int read_faces(int8_t* kind, int32_t* nb, int8_t* pos, int64_t cap, int64_t* n) override {
-        const int64_t ne = mesh.n();
+    int read_faces(int8_t* kind, int32_t* nb, int8_t* pos, int64_t cap_, int64_t* n) override {
         if (n) *n = ne;
-        if (cap < ne) {
+        if (cap_ < ne) {
             err = "read_faces: capacity too small";
             return MDL_E_ARG;
         }
+        std::vector<uint32_t> hi(ne);
+        std::vector<int32_t> hn((size_t)ne * NF), hh((size_t)ne * NF * NSUB);
+        MDL_CK(cudaMemcpyAsync(hi.data(), sets[cs].info.p, ne * 4, cudaMemcpyDeviceToHost, st));
+        MDL_CK(cudaMemcpyAsync(hn.data(), sets[cs].nbr.p, (size_t)ne * NF * 4, cudaMemcpyDeviceToHost, st));
+        MDL_CK(cudaMemcpyAsync(hh.data(), sets[cs].hang.p, (size_t)ne * NF * NSUB * 4, cudaMemcpyDeviceToHost, st));
+        MDL_CK(cudaStreamSynchronize(st));
         for (int64_t e = 0; e < ne; ++e)
             for (int f = 0; f < NF; ++f) {
                 const int64_t i = e * NF + f;
-                const int kd = mesh.kind[i];
+                const int kd = (hi[e] >> (4 * f)) & 3;
+                const int ps = (hi[e] >> (4 * f + 2)) & 3;
                 if (kind) kind[i] = (int8_t)kd;
-                if (pos) pos[i] = (kd == F_COARSER) ? mesh.pos[i] : 0;
+                if (pos) pos[i] = (kd == F_COARSER) ? (int8_t)ps : 0;
                 if (nb) {
                     for (int j = 0; j < NSUB; ++j) nb[i * NSUB + j] = -1;
-                    if (kd == F_SAME || kd == F_COARSER) nb[i * NSUB] = mesh.nbr[i];
+                    if (kd == F_SAME || kd == F_COARSER) nb[i * NSUB] = hn[i];
                     else if (kd == F_FINER)
-                        for (int j = 0; j < NSUB; ++j) nb[i * NSUB + j] = mesh.hang[mesh.nbr[i] + j];
+                        for (int j = 0; j < NSUB; ++j) nb[i * NSUB + j] = hh[hn[i] + j];
                 }
             }
         return MDL_OK;
     }
 
-    int read_indicators(double* es, double* et, int64_t cap, int64_t* n) override {
-        const int64_t ne = mesh.n();
+    int read_indicators(double* es, double* et, int64_t cap_, int64_t* n) override {
         if (n) *n = ne;
-        if (cap < ne) {
+        if (cap_ < ne) {
             err = "read_indicators: capacity too small";
             return MDL_E_ARG;
         }
@@ -695,7 +744,11 @@ public:
         return MDL_OK;
     }
     int reset_stats() override {
+        MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, elem_updates), 0, 2 * sizeof(int64_t), st));
+        MDL_CK(cudaStreamSynchronize(st));
         stats = mdl_stats{};
+        stats.n_elements = ne;
+        stats.barriers = nbar;
         return MDL_OK;
     }
     int set_timing(int on) override {
@@ -703,23 +756,20 @@ public:
         return MDL_OK;
     }
     int device_view(int which, void** p, int64_t* n, void** stream) override {
-        const int64_t ne = mesh.n();
         if (stream) *stream = (void*)st;
         switch (which) {
             case 0: {
-                // normalise: current values into slot 0
+                // normalise: current values into slot 0 with the parities reset
                 std::vector<double> tmp(ne * NP);
                 int64_t nn;
                 int rc = read_field(0, tmp.data(), ne * NP, &nn);
                 if (rc) return rc;
-                if (p) *p = sets[cs].V0.p;
-                // write back as slot 0 with parity reset
                 MDL_CK(scratch.ensure(2 * ne * NP));
                 MDL_CK(cudaMemcpyAsync(scratch.p, tmp.data(), ne * NP * 8, cudaMemcpyHostToDevice, st));
-                k_scatter_initial<R, NP><<<grid(ne * NP, 256), 256, 0, st>>>(arrays(cs), scratch.p, nullptr);
-                stats.kernel_launches++;
-                MDL_CK(cudaGetLastError());
+                k_scatter_initial<R, NP><<<div_up(ne * NP, 256), 256, 0, st>>>(arrays(cs), ne, scratch.p, nullptr);
+                MDL_LAUNCHED();
                 MDL_CK(cudaStreamSynchronize(st));
+                if (p) *p = sets[cs].V0.p;
                 if (n) *n = ne * NP;
                 return MDL_OK;
             }

@@ -26,16 +26,28 @@ namespace mdl {
 constexpr uint32_t INFO_STIM = 1u << 28;
 constexpr uint32_t INFO_PENDING = 1u << 29;
 
-struct DevStatus {
-    unsigned int cnt[8];      // elements per level b
-    unsigned int changed;     // some b_e differs from the previous barrier
-    unsigned int cfl_err;     // some b_e > B
-    unsigned int nonfinite;   // NaN/Inf in V or v after the sweep
-    unsigned int n_refine;    // refine marks
-    unsigned int n_coarsen;   // coarsenable families
-    unsigned int pad[3];
-    double integral;          // FP64 integral of V
+// Device-resident bookkeeping of one context: every kernel reads its element count
+// and the sticky error word from here, so a barrier needs no host round trip.
+struct DevMeta {
+    int64_t ne;              // elements of the current mesh
+    int64_t ne_new;          // elements after this barrier's adaptation
+    int64_t nbar;            // completed barriers
+    int64_t need;            // element capacity requested on overflow
+    unsigned int err;        // sticky: 1 non-finite, 2 CFL, 4 capacity, 8 mesh
+    unsigned int changed;    // the adaptation changed the mesh
+    unsigned int nf_pending; // non-finite values seen by this barrier's epilogue
+    unsigned int cur_set;    // index of the state/mesh set holding the current mesh
+    unsigned int cnt[8];     // elements per level b in this barrier
+    int32_t nact[128];       // due elements per tick
+    int64_t elem_updates;    // accumulated element steps
+    int64_t rebuilds;        // barriers whose mesh changed
+    double integral;         // FP64 int V after the last barrier
 };
+
+constexpr unsigned ERR_NONFINITE = 1u, ERR_CFL = 2u, ERR_CAPACITY = 4u, ERR_MESH = 8u;
+
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+__device__ __forceinline__ int64_t gtid() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }
 
 template <typename R>
 struct DevArrays {
@@ -58,8 +70,7 @@ struct DevArrays {
     const int32_t* root;
     const uint32_t* loc;
     const uint32_t* smask[MDL_MAX_STIM];
-    DevStatus* status;
-    int64_t ne;
+    DevMeta* meta;
 };
 
 struct StimArgs {
@@ -199,9 +210,8 @@ template <typename R>
 struct TickArgs {
     DevArrays<R> d;
     StimArgs stim;
-    double t_i;        // tick start time
     double dt;         // barrier step
-    int tick, B, n_act;
+    int tick, B;
 };
 
 // One tick of Alg. 1: every due element (a prefix of `order`) takes one forward
@@ -211,9 +221,12 @@ template <typename R, int DIM, int P>
 __global__ void __launch_bounds__(128) k_tick(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph) {
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= a.n_act) return;
     const DevArrays<R>& d = a.d;
+    if (d.meta->err) return;
+    const int n_act = d.meta->nact[a.tick];
+    const double nt = (double)(1 << a.B);
+    const double t_i = ((double)d.meta->nbar * nt + (double)a.tick) * a.dt / nt;
+    for (int idx = (int)gtid(); idx < n_act; idx += (int)gstride()) {
     const int e = d.order[idx];
     const uint8_t lv = d.lvl[e];
     const int b = lv & 7, par = (lv >> 3) & 1;
@@ -234,13 +247,13 @@ __global__ void __launch_bounds__(128) k_tick(const TickArgs<R> a, const Tables<
 
     const double dte_d = ldexp(a.dt, -b);
     const R dte = (R)dte_d;
-    const double t_mid = a.t_i + 0.5 * dte_d;
+    const double t_mid = t_i + 0.5 * dte_d;
     R stim_old[NP], stim_mid[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) stim_old[q] = stim_mid[q] = R(0);
     if (inf & INFO_STIM) {
         for (int s = 0; s < a.stim.n; ++s) {
-            const bool on_o = (a.stim.t0[s] <= a.t_i) && (a.t_i < a.stim.t1[s]);
+            const bool on_o = (a.stim.t0[s] <= t_i) && (t_i < a.stim.t1[s]);
             const bool on_m = (a.stim.t0[s] <= t_mid) && (t_mid < a.stim.t1[s]);
             if (!on_o && !on_m) continue;
             const uint32_t m = d.smask[s][e];
@@ -302,7 +315,8 @@ __global__ void __launch_bounds__(128) k_tick(const TickArgs<R> a, const Tables<
     const double inc = dte_d * (double)term;
     d.acc[e] = (ke == 0) ? inc : d.acc[e] + inc;
     if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
-        lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, a.t_i, dte_d);
+        lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, t_i, dte_d);
+    }
 }
 
 // Kelly-type spatial indicator per element (Eq. dg-error-estimate) on the barrier-start values.
@@ -310,8 +324,9 @@ template <typename R, int DIM, int P>
 __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> ph) {
     using S = Shape<DIM, P>;
     constexpr int NP = S::NP, NF = S::NF, NSUB = S::NSUB;
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= d.ne) return;
+    if (d.meta->err) return;
+    const int64_t ne = d.meta->ne;
+    for (int64_t e = gtid(); e < ne; e += gstride()) {
     const int par = (d.lvl[e] >> 3) & 1;
     const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
     R u[NP];
@@ -348,63 +363,16 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
         }
     }
     d.eta_s[e] = sqrt(acc);
-}
-
-// Refine marks and coarsenable families (Alg. 1).  A family counts when its 2^d
-// children are consecutive leaves (child 0 first), all have eta <= tau_c, none is
-// marked for refinement, and no face neighbour outside the family is finer or a
-// same-level leaf marked for refinement.  With no refine mark this is exactly the
-// host's decision, so the host is only involved when the mesh will change.
-template <typename R, int DIM>
-__global__ void k_marks(const DevArrays<R> d, double tau_r, double tau_c, int L) {
-    constexpr int NF = 2 * DIM, NC = 1 << DIM;
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= d.ne) return;
-    const uint32_t inf = d.info[e];
-    const int lev = (inf >> 24) & 15;
-    const double eta = d.eta_s[e];
-    if (eta >= tau_r && lev < L) atomicAdd(&d.status->n_refine, 1u);
-    if (lev == 0) return;
-    const uint32_t lc = d.loc[e];
-    for (int k = 0; k < DIM; ++k)
-        if ((lc >> (8 * k)) & 1u) return;                 // not child 0
-    if (e + NC > d.ne) return;
-    const int32_t rt = d.root[e];
-    for (int b = 0; b < NC; ++b) {
-        const int64_t c = e + b;
-        const uint32_t ic = d.info[c];
-        const int lc_ = (ic >> 24) & 15;
-        if (lc_ != lev || d.root[c] != rt) return;
-        const uint32_t lcc = d.loc[c];
-        for (int k = 0; k < DIM; ++k)
-            if (((lcc >> (8 * k)) & 255u) != ((lc >> (8 * k)) & 255u) + ((b >> k) & 1)) return;
-        const double ec = d.eta_s[c];
-        if (!(ec <= tau_c) || (ec >= tau_r && lc_ < L)) return;
-        for (int f = 0; f < NF; ++f) {
-            const int axis = f >> 1, side = (f & 1) ? 1 : -1;
-            const int cb = (b >> axis) & 1;
-            if ((side > 0 && cb == 0) || (side < 0 && cb == 1)) continue;   // inside the family
-            const int kind = (ic >> (4 * f)) & 3;
-            if (kind == 3) return;
-            if (kind == 1) {
-                const int nb = d.nbr[(size_t)c * NF + f];
-                const int ln = (d.info[nb] >> 24) & 15;
-                if (d.eta_s[nb] >= tau_r && ln < L) return;
-            }
-        }
     }
-    atomicAdd(&d.status->n_coarsen, 1u);
 }
 
 // Substep levels b_e = max(b^CFL_e, b^cell_e) (Eq. num-substeps), or the replayed levels.
 template <typename R>
 __global__ void k_levels(const DevArrays<R> d, const int8_t* ovr, const double* eta_t, double tau_cell,
                          int bcell, int B, int lts) {
-    __shared__ unsigned int sc[8];
-    if (threadIdx.x < 8) sc[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e < d.ne) {
+    if (d.meta->err) return;
+    const int64_t ne = d.meta->ne;
+    for (int64_t e = gtid(); e < ne; e += gstride()) {
         int b;
         if (ovr) b = ovr[e];
         else if (!lts) b = 0;
@@ -414,16 +382,12 @@ __global__ void k_levels(const DevArrays<R> d, const int8_t* ovr, const double* 
             b = bt > b ? bt : b;
         }
         if (b > B || b < 0) {
-            atomicOr(&d.status->cfl_err, 1u);
+            atomicOr(&d.meta->err, ERR_CFL);
             b = b < 0 ? 0 : B;
         }
         const uint8_t old = d.lvl[e];
-        if ((old & 7) != b) atomicOr(&d.status->changed, 1u);
         d.lvl[e] = (uint8_t)(b | (old & 8));
-        atomicAdd(&sc[b], 1u);
     }
-    __syncthreads();
-    if (threadIdx.x < 8 && sc[threadIdx.x]) atomicAdd(&d.status->cnt[threadIdx.x], sc[threadIdx.x]);
 }
 
 // Barrier epilogue: eta^t = sqrt(acc)/dt, parity flip of single-step elements, non-finite
@@ -434,9 +398,11 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const Ta
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
     __shared__ double red[256];
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d.meta->err) return;
+    const int64_t ne = d.meta->ne;
     double loc = 0.0;
-    if (e < d.ne) {
+    bool bad = false;
+    for (int64_t e = gtid(); e < ne; e += gstride()) {
         d.eta_t[e] = sqrt(d.acc[e]) / dt;
         uint8_t lv = d.lvl[e];
         if ((lv & 7) == 0) {
@@ -447,7 +413,6 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const Ta
         const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
         const R* w = d.v + (size_t)e * NP;
         const int lev = (d.info[e] >> 24) & 15;
-        bool bad = false;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             double Mq = (double)ph.Wvol[lev];
@@ -457,8 +422,8 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const Ta
             loc += Mq * (double)x;
             bad = bad || !isfinite(x) || !isfinite(w[q]);
         }
-        if (bad) atomicOr(&d.status->nonfinite, 1u);
     }
+    if (bad) atomicOr(&d.meta->nf_pending, 1u);
     red[threadIdx.x] = loc;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -468,14 +433,15 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const Ta
     if (threadIdx.x == 0) d.partial[blockIdx.x] = red[0];
 }
 
-// Deterministic final sum of the epilogue partials (one block, fixed order).
-__global__ void k_reduce_partials(const double* partial, int n, double* out);
+// End of a barrier: deterministic sum of the epilogue partials (one block, fixed
+// order), barrier count, non-finite flag.
+__global__ void k_reduce_partials(const double* partial, int n, DevMeta* m);
 
 // Copy V (current slot by parity) or v to an FP64 output.
 template <typename R, int NP>
-__global__ void k_gather(const DevArrays<R> d, int which, double* out) {
+__global__ void k_gather(const DevArrays<R> d, int64_t ne, int which, double* out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= d.ne * NP) return;
+    if (i >= ne * NP) return;
     const int64_t e = i / NP;
     if (which == 0) {
         const int par = (d.lvl[e] >> 3) & 1;
@@ -487,9 +453,9 @@ __global__ void k_gather(const DevArrays<R> d, int which, double* out) {
 
 // Set V (into slot 0, parity reset) and optionally v from FP64 input.
 template <typename R, int NP>
-__global__ void k_scatter_initial(DevArrays<R> d, const double* V, const double* w) {
+__global__ void k_scatter_initial(DevArrays<R> d, int64_t ne, const double* V, const double* w) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= d.ne * NP) return;
+    if (i >= ne * NP) return;
     d.V0[i] = (R)V[i];
     if (w) d.v[i] = (R)w[i];
     if (i % NP == 0) d.lvl[i / NP] &= 7;
@@ -501,8 +467,9 @@ template <typename R, int DIM, int P>
 __global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> ph, double t, int mark_now) {
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= d.ne) return;
+    if (d.meta->err) return;
+    const int64_t ne = d.meta->ne;
+    for (int64_t e = gtid(); e < ne; e += gstride()) {
     uint32_t inf = d.info[e];
     const int lev = (inf >> 24) & 15;
     const int par = (d.lvl[e] >> 3) & 1;
@@ -538,6 +505,7 @@ __global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> p
     }
     inf = pending ? (inf | INFO_PENDING) : (inf & ~INFO_PENDING);
     d.info[e] = inf;
+    }
 }
 
 // Solution transfer after adaptation (Alg. 1 adapt steps): keep, prolong (parent
@@ -548,8 +516,9 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
                            const int8_t* pbits, const Tables<R> T) {
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP, NC = 1 << DIM;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n.ne) return;
+    if (n.meta->err) return;
+    const int64_t nne = n.meta->ne;
+    for (int64_t i = gtid(); i < nne; i += gstride()) {
     const int kd = pkind[i];
     const int src = psrc[i];
     R* Vn = n.V0 + (size_t)i * NP;
@@ -620,6 +589,151 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
         n.eta_t[i] = et / NC;
     }
     n.lvl[i] = 0;
+    }
+}
+
+}  // namespace mdl
+
+namespace mdl {
+
+// --------------------------------------------------------------------------
+// Cooperative sweep tick for Q1 elements: a group of G = (p+1)^d lanes per element
+// (4 in 2D, 8 in 3D).  Lane g loads and updates DOF g; lane f < 2d gathers the
+// neighbour(s) across face f (time-interpolated) and evaluates that face's
+// contribution; the contributions are summed over the group by shuffles.  The
+// arithmetic per DOF is the one of k_tick; only the work split differs, which keeps
+// G times more warps in flight to hide the dependent neighbour loads.
+// --------------------------------------------------------------------------
+template <typename R, int DIM>
+__global__ void __launch_bounds__(256) k_tick_q1(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph) {
+    using S = Shape<DIM, 1>;
+    constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB;
+    constexpr int G = NP;  // lanes per element
+    const DevArrays<R>& d = a.d;
+    if (d.meta->err) return;
+    const int n_act = d.meta->nact[a.tick];
+    const double nt = (double)(1 << a.B);
+    const double t_i = ((double)d.meta->nbar * nt + (double)a.tick) * a.dt / nt;
+    const int lane = threadIdx.x & 31;
+    const int g = lane % G;
+    const unsigned gmask = ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)) << (lane - g);
+    const int64_t gid = gtid() / G, gstr = gstride() / G;
+    for (int64_t idx = gid; idx < n_act; idx += gstr) {
+        const int e = d.order[idx];
+        const uint8_t lv = d.lvl[e];
+        const uint32_t inf = d.info[e];
+        const int b = lv & 7, par = (lv >> 3) & 1;
+        const int ke = a.tick >> (a.B - b);
+        const int cur = par ^ (ke & 1);
+        const int lev = (inf >> 24) & 15;
+        const R* Vc = (cur ? d.V1 : d.V0) + (size_t)e * NP;
+        R* Vd = (cur ? d.V0 : d.V1) + (size_t)e * NP;
+        const R my_u = Vc[g];
+        const R my_w = d.v[(size_t)e * NP + g];
+        int my_nb = -1;
+        if (g < NF) my_nb = d.nbr[(size_t)e * NF + g];
+        R u[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) u[q] = __shfl_sync(gmask, my_u, q, G);
+        // face contribution of this lane's face
+        R rf[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) rf[q] = R(0);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            if (f != g) continue;
+            const int kind = (inf >> (4 * f)) & 3;
+            if (kind == 0) continue;
+            const int k = f >> 1, s = (f & 1) ? 1 : -1;
+            if (kind != 3) {
+                R un[NP];
+                load_seen<R, NP>(d, a.tick, a.B, my_nb, un);
+                const int pos = (inf >> (4 * f + 2)) & 3;
+                face_term<R, DIM, 1>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1, kind == 1 ? -1 : pos,
+                                     un, lev, rf);
+            } else {
+                for (int sb = 0; sb < NSUB; ++sb) {
+                    R un[NP];
+                    load_seen<R, NP>(d, a.tick, a.B, d.hang[my_nb + sb], un);
+                    face_term<R, DIM, 1>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1, rf);
+                }
+            }
+        }
+        // volume term (every lane, all rows) plus the group sum of the face terms
+        R r[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) r[q] = R(0);
+        volume_term<R, DIM, 1>(T, ph, lev, u, r);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            R x = rf[q];
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(gmask, x, o, G);
+            r[q] += x;
+        }
+        // pointwise update of DOF g
+        const double dte_d = ldexp(a.dt, -b);
+        const R dte = (R)dte_d;
+        const double t_mid = t_i + 0.5 * dte_d;
+        R stim_o = R(0), stim_m = R(0);
+        if (inf & INFO_STIM) {
+            for (int s = 0; s < a.stim.n; ++s) {
+                const bool on_o = (a.stim.t0[s] <= t_i) && (t_i < a.stim.t1[s]);
+                const bool on_m = (a.stim.t0[s] <= t_mid) && (t_mid < a.stim.t1[s]);
+                if (!on_o && !on_m) continue;
+                if ((d.smask[s][e] >> g) & 1u) {
+                    if (on_o) stim_o -= (R)a.stim.amp[s];
+                    if (on_m) stim_m -= (R)a.stim.amp[s];
+                }
+            }
+        }
+        R Iag, gag;
+        if (ke == 0) {
+            Iag = ap_iion(ph, my_u, my_w) + stim_o;
+            gag = ap_g(ph, my_u, my_w);
+            if (b > 0) {
+                d.Ia[(size_t)e * NP + g] = Iag;
+                d.ga[(size_t)e * NP + g] = gag;
+            }
+        } else {
+            Iag = d.Ia[(size_t)e * NP + g];
+            gag = d.ga[(size_t)e * NP + g];
+        }
+        R rg = r[0];
+#pragma unroll
+        for (int q = 1; q < NP; ++q)
+            if (q == g) rg = r[q];
+        R Mq = ph.Wvol[lev];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) Mq *= T.w[digit<N1>(g, k)];
+        const R I = ap_iion(ph, my_u, my_w) + stim_o;
+        const R un_g = my_u + dte * (-rg / Mq - I);
+        const R wn_g = ap_step_state(ph, my_u, my_w, dte);
+        const R Vm = R(0.5) * (my_u + un_g);
+        const R wm = R(0.5) * (my_w + wn_g);
+        const R dI = ap_iion(ph, Vm, wm) + stim_m - Iag;
+        const R dg = ap_g(ph, Vm, wm) - gag;
+        R term = Mq * (dI * dI + dg * dg);
+        R vmax = un_g < R(0) ? -un_g : un_g;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            term += __shfl_xor_sync(gmask, term, o, G);
+            const R om = __shfl_xor_sync(gmask, vmax, o, G);
+            vmax = om > vmax ? om : vmax;
+        }
+        Vd[g] = un_g;
+        d.v[(size_t)e * NP + g] = wn_g;
+        if (g == 0) {
+            const double inc = dte_d * (double)term;
+            d.acc[e] = (ke == 0) ? inc : d.acc[e] + inc;
+        }
+        if ((inf & INFO_PENDING) && vmax >= ph.lat_gate) {
+            R unv[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) unv[q] = __shfl_sync(gmask, un_g, q, G);
+            if (g == 0) lat_check<R, DIM, 1>(d, T, ph, e, inf, lev, u, unv, t_i, dte_d);
+        }
+    }
 }
 
 }  // namespace mdl

@@ -1,4 +1,4 @@
-// mdl_mesh.cpp -- forest bookkeeping: ordering, owner grid, face tables, adaptation.
+// mdl_mesh.cpp -- host-side ordering and validation of a forest of leaves.
 #include "mdl_mesh.h"
 
 #include <algorithm>
@@ -174,116 +174,6 @@ int Mesh::neighbour(int64_t i, int axis, int side, int32_t* out, int* posbits) c
     }
     *posbits = 0;
     return F_FINER;
-}
-
-// ---------------------------------------------------------------------------
-bool adapt(const Mesh& m, const double* eta, double tau_r, double tau_c, Mesh* next,
-           std::vector<int8_t>* plan_kind, std::vector<int32_t>* plan_src,
-           std::vector<int8_t>* plan_bits, std::string* err) {
-    const int64_t n = m.n();
-    const int dim = m.dim, NF = m.nfaces(), NC = 1 << dim;
-    std::vector<uint8_t> ref(n, 0);
-    std::vector<int64_t> work;
-    for (int64_t i = 0; i < n; ++i)
-        if (eta[i] >= tau_r && m.leaves[i].level < m.L) {
-            ref[i] = 1;
-            work.push_back(i);
-        }
-    // 2:1 closure: a refined leaf's coarser face neighbours must refine too
-    int32_t sub[4];
-    while (!work.empty()) {
-        const int64_t i = work.back();
-        work.pop_back();
-        for (int f = 0; f < NF; ++f) {
-            int pb;
-            const int kd = m.neighbour(i, f / 2, (f & 1) ? 1 : -1, sub, &pb);
-            if (kd == F_COARSER && !ref[sub[0]]) {
-                ref[sub[0]] = 1;
-                work.push_back(sub[0]);
-            }
-        }
-    }
-    // coarsening of complete families (siblings are contiguous in child order)
-    std::vector<uint8_t> coarsen_first(n, 0), in_coarsen(n, 0);
-    for (int64_t i = 0; i + NC <= n; ++i) {
-        const Leaf& a = m.leaves[i];
-        if (a.level == 0) continue;
-        bool first = true;
-        for (int k = 0; k < dim; ++k)
-            if (a.c[k] & 1) first = false;
-        if (!first) continue;
-        bool ok = true;
-        for (int b = 0; b < NC && ok; ++b) {
-            const Leaf& s = m.leaves[i + b];
-            if (s.level != a.level) ok = false;
-            for (int k = 0; k < dim && ok; ++k)
-                if (s.c[k] != a.c[k] + ((b >> k) & 1)) ok = false;
-            if (ok && (ref[i + b] || !(eta[i + b] <= tau_c))) ok = false;
-        }
-        if (!ok) continue;
-        // every outside face neighbour must be no finer than the children after refinement
-        for (int b = 0; b < NC && ok; ++b) {
-            for (int f = 0; f < NF && ok; ++f) {
-                const int axis = f / 2, side = (f & 1) ? 1 : -1;
-                const int cb = (b >> axis) & 1;
-                if ((side > 0 && cb == 0) || (side < 0 && cb == 1)) continue;  // inside the family
-                int pb;
-                const int kd = m.neighbour(i + b, axis, side, sub, &pb);
-                if (kd == F_FINER) ok = false;
-                else if (kd == F_SAME && ref[sub[0]]) ok = false;
-            }
-        }
-        if (ok) {
-            coarsen_first[i] = 1;
-            for (int b = 0; b < NC; ++b) in_coarsen[i + b] = 1;
-        }
-    }
-    bool changed = false;
-    std::vector<Leaf> lv;
-    struct Src { int8_t kind; int32_t src; int8_t bits; };
-    std::vector<Src> src;
-    lv.reserve(n + n / 4);
-    for (int64_t i = 0; i < n; ++i) {
-        const Leaf& a = m.leaves[i];
-        if (ref[i]) {
-            changed = true;
-            for (int b = 0; b < NC; ++b) {
-                Leaf c{a.level + 1, {2 * a.c[0] + (b & 1), 2 * a.c[1] + ((b >> 1) & 1),
-                                     dim == 3 ? 2 * a.c[2] + ((b >> 2) & 1) : 0}};
-                lv.push_back(c);
-                src.push_back(Src{P_CHILD, (int32_t)i, (int8_t)b});
-            }
-        } else if (coarsen_first[i]) {
-            changed = true;
-            Leaf p{a.level - 1, {a.c[0] >> 1, a.c[1] >> 1, dim == 3 ? a.c[2] >> 1 : 0}};
-            lv.push_back(p);
-            src.push_back(Src{P_PARENT, (int32_t)i, 0});
-        } else if (!in_coarsen[i]) {
-            lv.push_back(a);
-            src.push_back(Src{P_KEEP, (int32_t)i, 0});
-        }
-    }
-    // the new order is the sorted order of lv; refined children and coarsened
-    // parents keep the relative position of their origin, so lv is already sorted
-    next->init_params(dim, m.base, m.L);
-    next->leaves = lv;
-    next->keys.resize(lv.size());
-    for (size_t i = 0; i < lv.size(); ++i) next->keys[i] = next->key(lv[i]);
-    for (size_t i = 1; i < lv.size(); ++i)
-        if (next->keys[i] <= next->keys[i - 1]) {
-            if (err) *err = "internal: adapted leaves not in order";
-            return false;
-        }
-    if (!next->rebuild(err)) return false;
-    plan_kind->resize(lv.size());
-    plan_src->resize(lv.size());
-    plan_bits->resize(lv.size());
-    for (size_t i = 0; i < lv.size(); ++i) {
-        (*plan_kind)[i] = src[i].kind;
-        (*plan_src)[i] = src[i].src;
-        (*plan_bits)[i] = src[i].bits;
-    }
-    return changed;
 }
 
 }  // namespace mdl

@@ -1,9 +1,9 @@
-// mdl_mesh.h -- host-side forest of quad/octrees on a box slab (Sec. 2.2; Alg. 1 adapt steps).
+// mdl_mesh.h -- host-side checks of a caller-supplied forest of quad/octree leaves (Sec. 2.2).
 //
 // Leaves are (level, integer cell coordinates on the level grid), ordered by
-// (root id, Morton key of the lower corner on the finest grid).  A dense owner
-// grid on the finest level maps every finest cell to its leaf, which makes face
-// neighbour queries O(1).  The mesh is kept 2:1 face balanced.
+// (root id, Morton key of the lower corner on the finest grid).  Used to sort and
+// validate meshes given to mdl_upload_mesh (tiling, 2:1 face balance); the device
+// builds its own tables and adapts the forest itself.
 #pragma once
 
 #include <stdint.h>
@@ -20,9 +20,6 @@ struct Leaf {
 
 // Per-element face record kinds.
 enum FaceKind { F_BOUNDARY = 0, F_SAME = 1, F_COARSER = 2, F_FINER = 3 };
-
-// Transfer plan entry for one new leaf.
-enum PlanKind { P_KEEP = 0, P_CHILD = 1, P_PARENT = 2 };
 
 struct Mesh {
     int dim = 2;
@@ -55,16 +52,5 @@ struct Mesh {
     // subface leaf list).
     int neighbour(int64_t i, int axis, int side, int32_t* out, int* posbits) const;
 };
-
-// One refine-then-coarsen step (Alg. 1):
-//   refine leaves with eta >= tau_r (level < L), close under 2:1 balance,
-//   coarsen complete untouched families with every eta <= tau_c whose outside
-//   face neighbours are no finer than the children.
-// Fills `next` (a new mesh with rebuilt tables) and the plan for every new leaf:
-// plan_kind, plan_src (keep: old index; child: old parent; parent: old first child)
-// and plan_bits (child bits).  Returns whether anything changed.
-bool adapt(const Mesh& m, const double* eta, double tau_r, double tau_c, Mesh* next,
-           std::vector<int8_t>* plan_kind, std::vector<int32_t>* plan_src,
-           std::vector<int8_t>* plan_bits, std::string* err);
 
 }  // namespace mdl
