@@ -165,10 +165,10 @@ class Forest:
                 refine.add(lf)
         # balance closure: refine coarser neighbours of any too-fine child
         leafset = set(old)
-        queue = sorted(refine, key=self.key)
+        queue = list(refine)          # the closure does not depend on the processing order
         refined = set()
         while queue:
-            lf = queue.pop(0)
+            lf = queue.pop()
             if lf in refined or lf not in leafset:
                 continue
             refined.add(lf)
@@ -187,7 +187,6 @@ class Forest:
                         par = (lvl - 1, (cn[0] >> 1, cn[1] >> 1, (cn[2] >> 1) if dim == 3 else 0))
                         if par in leafset and par not in refined:
                             queue.append(par)
-            queue.sort(key=self.key)
         # coarsening of complete, untouched families
         fams: Dict[Leaf, List[Leaf]] = {}
         for lf in old:

@@ -209,29 +209,27 @@ class Sim:
         f = self.forest
         xi = basis.node_points(d, prob.order)
         n_p = xi.shape[0]
-        rows, cols, vals = [], [], []
+        lv, c = self.disc.leaf_arrays()
+        root = c >> lv[:, None]
+        loc = c - (root << lv[:, None])
+        rid = root[:, 0] + f.base[0] * (root[:, 1] + (f.base[1] * root[:, 2] if d == 3 else 0))
+        # cell of root node q at level l, per direction
+        cell = np.floor((xi[None, :, :] + 1.0) * 0.5 * (2.0 ** lv)[:, None, None]).astype(np.int64)
+        inside = np.all(cell == loc[:, None, :], axis=2)                      # (ne, n_p)
+        e_idx, q_idx = np.nonzero(inside)
+        ids = rid[e_idx] * n_p + q_idx
         owner = np.full(self.n_probe, -1, dtype=np.int64)
-        for e, lf in enumerate(f.leaves):
-            lvl, c = lf
-            root = [c[k] >> lvl for k in range(d)]
-            loc = [c[k] - (root[k] << lvl) for k in range(d)]
-            sel = [q for q in range(n_p)
-                   if all(int(math.floor((xi[q, k] + 1.0) * 0.5 * (1 << lvl))) == loc[k] for k in range(d))]
-            if not sel:
-                continue
-            rid = root[0] + f.base[0] * (root[1] + (f.base[1] * root[2] if d == 3 else 0))
-            ids = np.array([rid * n_p + q for q in sel], dtype=np.int64)
-            h = f.h(lvl)
-            xl = 2.0 * (self.probe_x[ids] - f.lower(lf)[None, :]) / h[None, :] - 1.0
-            phi, _ = basis.eval_basis(d, prob.order, xl)
-            owner[ids] = e
-            for r_, pid in enumerate(ids):
-                rows.extend([pid] * n_p)
-                cols.extend(range(e * n_p, (e + 1) * n_p))
-                vals.extend(phi[r_])
+        owner[ids] = e_idx
         assert (owner >= 0).all()
+        hs = np.array([f.h(l) for l in range(f.L + 1)])
+        h = hs[lv[e_idx]]
+        lower = c[e_idx] * h
+        xl = 2.0 * (self.probe_x[ids] - lower) / h - 1.0
+        phi, _ = basis.eval_basis(d, prob.order, xl)                          # (npr, n_p)
+        rows = np.repeat(ids, n_p)
+        cols = (e_idx[:, None] * n_p + np.arange(n_p)[None, :]).ravel()
         self.probe_owner = owner
-        self.P = sp.csr_matrix((vals, (rows, cols)), shape=(self.n_probe, f.n * n_p))
+        self.P = sp.csr_matrix((phi.ravel(), (rows, cols)), shape=(self.n_probe, f.n * n_p))
 
     def _lat_initial(self):
         th = self.prob.act_threshold
@@ -249,10 +247,13 @@ class Sim:
         cfl = self.cfl()
         b_cell_on = b_from_bound(self.dt, prob.dt_bar_cell) if prob.dt_bar_cell > 0 else 0
         out = np.empty(ne, dtype=np.int64)
+        memo = {}
         for e in range(ne):
-            bc = b_from_bound(self.dt, cfl[e])
+            c = cfl[e]
+            if c not in memo:
+                memo[c] = b_from_bound(self.dt, c)
             bt = b_cell_on if eta_t[e] > prob.tau_cell else 0
-            out[e] = max(bc, bt)
+            out[e] = max(memo[c], bt)
         if out.max(initial=0) > self.B:
             raise CFLViolation("element needs %d levels, budget %d" % (out.max(), self.B))
         return out
@@ -345,32 +346,40 @@ class Sim:
         wq = basis.node_weights(d, p)
         oldV = self.V.reshape(-1, n_p)
         oldv = self.v.reshape(-1, n_p)
-        newV = np.empty((new_forest.n, n_p))
-        newv = np.empty((new_forest.n, n_p))
-        eta_t = np.empty(new_forest.n)
-        # child b occupies [-1,0] or [0,1] per direction in parent coords
-        for i, pl in enumerate(plan):
-            if pl[0] == 'keep':
-                newV[i] = oldV[pl[1]]; newv[i] = oldv[pl[1]]
-                eta_t[i] = self.eta_t[pl[1]]
-            elif pl[0] == 'child':
-                par, bits = pl[1], pl[2]
-                off = np.array([((bits >> k) & 1) for k in range(d)], dtype=np.float64)
-                xp = (xi + 2.0 * off[None, :] - 1.0) / 2.0
-                phi, _ = basis.eval_basis(d, p, xp)
-                newV[i] = phi @ oldV[par]; newv[i] = phi @ oldv[par]
-                eta_t[i] = self.eta_t[par]
-            else:
-                kids = pl[1]
-                accV = np.zeros(n_p); accv = np.zeros(n_p)
-                for b, c in enumerate(kids):
-                    off = np.array([((b >> k) & 1) for k in range(d)], dtype=np.float64)
-                    xp = (xi + 2.0 * off[None, :] - 1.0) / 2.0
-                    phi, _ = basis.eval_basis(d, p, xp)      # parent basis at child nodes
-                    wc = wq / (2.0 ** d)                      # child weights in parent reference measure
-                    accV += phi.T @ (wc * oldV[c]); accv += phi.T @ (wc * oldv[c])
-                newV[i] = accV / wq; newv[i] = accv / wq
-                eta_t[i] = float(np.mean(self.eta_t[kids]))
+        nn = new_forest.n
+        newV = np.empty((nn, n_p))
+        newv = np.empty((nn, n_p))
+        eta_t = np.empty(nn)
+        # parent basis at the nodes of child b: child b occupies [-1,0] or [0,1] per direction
+        phis = []
+        for b in range(1 << d):
+            off = np.array([((b >> k) & 1) for k in range(d)], dtype=np.float64)
+            phi, _ = basis.eval_basis(d, p, (xi + 2.0 * off[None, :] - 1.0) / 2.0)
+            phis.append(phi)
+        kind = np.array([0 if pl[0] == 'keep' else (1 if pl[0] == 'child' else 2) for pl in plan])
+        keep = np.nonzero(kind == 0)[0]
+        src = np.array([pl[1] for pl in plan if pl[0] == 'keep'], dtype=np.int64)
+        newV[keep] = oldV[src]; newv[keep] = oldv[src]; eta_t[keep] = self.eta_t[src]
+        ch = np.nonzero(kind == 1)[0]
+        if ch.size:
+            par = np.array([plan[i][1] for i in ch], dtype=np.int64)
+            bits = np.array([plan[i][2] for i in ch], dtype=np.int64)
+            for b in range(1 << d):
+                m = bits == b
+                newV[ch[m]] = oldV[par[m]] @ phis[b].T
+                newv[ch[m]] = oldv[par[m]] @ phis[b].T
+            eta_t[ch] = self.eta_t[par]
+        pa = np.nonzero(kind == 2)[0]
+        if pa.size:
+            kids = np.array([plan[i][1] for i in pa], dtype=np.int64)         # (npar, 2^d)
+            wc = wq / (2.0 ** d)                                              # child weights in parent measure
+            accV = np.zeros((pa.size, n_p)); accv = np.zeros((pa.size, n_p))
+            for b in range(1 << d):
+                accV += (wc[None, :] * oldV[kids[:, b]]) @ phis[b]
+                accv += (wc[None, :] * oldv[kids[:, b]]) @ phis[b]
+            newV[pa] = accV / wq[None, :]
+            newv[pa] = accv / wq[None, :]
+            eta_t[pa] = self.eta_t[kids].mean(axis=1)
         self.forest = new_forest
         self._rebuild()
         self.V = newV.reshape(-1)

@@ -94,18 +94,22 @@ class Disc:
     def mass(self) -> np.ndarray:
         """Diagonal GL mass M_q = w_q det J per DOF (Sec. 2.1: collocation makes M diagonal)."""
         wq = basis.node_weights(self.dim, self.p)
-        out = np.empty((self.ne, self.n_p))
-        for i, lvl in enumerate(self.levels):
-            out[i] = wq * np.prod(self.forest.h(int(lvl)) / 2.0)
-        return out.reshape(-1)
+        detj = np.array([np.prod(self.forest.h(l) / 2.0) for l in range(self.forest.L + 1)])
+        return (detj[self.levels][:, None] * wq[None, :]).reshape(-1)
+
+    def leaf_arrays(self):
+        """(level (ne,), integer coordinates (ne, dim)) of the leaves."""
+        c = np.array([lf[1][:self.dim] for lf in self.forest.leaves], dtype=np.int64).reshape(-1, self.dim)
+        return self.levels, c
 
     def node_coords(self) -> np.ndarray:
-        """Physical coordinates of every DOF node, (ne * n_p, dim)."""
+        """Physical coordinates of every DOF node, (ne * n_p, dim): lower + (xi + 1)/2 h."""
         xi = basis.node_points(self.dim, self.p)
-        out = np.empty((self.ne, self.n_p, self.dim))
-        for i, lf in enumerate(self.forest.leaves):
-            h = self.forest.h(lf[0])
-            out[i] = self.forest.lower(lf)[None, :] + (xi + 1.0) * 0.5 * h[None, :]
+        lv, c = self.leaf_arrays()
+        hs = np.array([self.forest.h(l) for l in range(self.forest.L + 1)])   # (L+1, dim)
+        h = hs[lv]                                                            # (ne, dim)
+        lower = c * h
+        out = lower[:, None, :] + (xi[None, :, :] + 1.0) * 0.5 * h[:, None, :]
         return out.reshape(-1, self.dim)
 
     # ------------------------------------------------------------------
@@ -375,14 +379,13 @@ class Disc:
         if A is None:
             A = self.assemble()
         n_p = self.n_p
-        out = np.empty(self.ne)
-        Ad = A.tocsr()
-        for e in range(self.ne):
-            s = slice(e * n_p, (e + 1) * n_p)
-            Ke = -Ad[s, s].toarray()
-            L = Ke / self.M[s][:, None]
-            out[e] = 1.0 / np.max(np.abs(L).sum(axis=1))
-        return out
+        C = A.tocoo()
+        own = (C.row // n_p) == (C.col // n_p)
+        rows, cols, vals = C.row[own], C.col[own], C.data[own]
+        Ke = np.zeros((self.ne, n_p, n_p))
+        np.add.at(Ke, (rows // n_p, rows % n_p, cols % n_p), -vals)
+        L = Ke / self.M.reshape(self.ne, n_p)[:, :, None]
+        return 1.0 / np.max(np.abs(L).sum(axis=2), axis=1)
 
     # ------------------------------------------------------------------
     def eta_s(self, u: np.ndarray) -> np.ndarray:

@@ -99,26 +99,6 @@ __global__ void k_amr_family(const int4* coord, const uint32_t* info, const int3
     }
 }
 
-template <int DIM>
-__global__ void k_amr_count(const int4* coord, const uint8_t* r, const uint8_t* c0, int32_t* cnt, DevMeta* m) {
-    if (m->err) return;
-    constexpr int NC = 1 << DIM;
-    const int64_t ne = m->ne;
-    for (int64_t e = gtid(); e < ne; e += gstride()) {
-        int n = 1;
-        if (r[e]) n = NC;
-        else if (!c0[e]) {
-            const int4 a = coord[e];
-            if (a.w > 0) {
-                const int b = (a.x & 1) | ((a.y & 1) << 1) | (DIM == 3 ? ((a.z & 1) << 2) : 0);
-                if (b > 0 && e - b >= 0 && c0[e - b]) n = 0;
-            }
-        }
-        cnt[e] = n;
-        if (n != 1 || c0[e]) m->changed = 1;
-    }
-}
-
 // Exclusive scan of cnt[0..ne) in chunks of SCAN_CHUNK per block: block sums, a one-block
 // scan of the sums, then per-block scans with the block offset.  Writes the total to ne_new.
 constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 8, SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
@@ -149,17 +129,39 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* sh, int64
     return woff + x - v;
 }
 
-static __global__ void k_scan_blocks(const int32_t* cnt, int64_t* bsum, const DevMeta* m) {
+// New leaves per old leaf: 2^d if refined, 1 if kept or child 0 of a coarsened family
+// (which becomes the parent), 0 for the other children of a coarsened family.
+template <int DIM>
+__device__ __forceinline__ int new_count(const int4* coord, const uint8_t* r, const uint8_t* c0, int64_t e) {
+    if (r[e]) return 1 << DIM;
+    if (c0[e]) return 1;
+    const int4 a = coord[e];
+    if (a.w > 0) {
+        const int b = (a.x & 1) | ((a.y & 1) << 1) | (DIM == 3 ? ((a.z & 1) << 2) : 0);
+        if (b > 0 && e - b >= 0 && c0[e - b]) return 0;
+    }
+    return 1;
+}
+
+template <int DIM>
+__global__ void k_scan_blocks(const int4* coord, const uint8_t* r, const uint8_t* c0, int64_t* bsum,
+                              DevMeta* m) {
     if (m->err) return;
     __shared__ int64_t sh[32];
     const int64_t ne = m->ne;
     const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
     if (base >= ne) return;
     int64_t s = 0;
+    bool ch = false;
     for (int i = 0; i < SCAN_ITEMS; ++i) {
         const int64_t e = base + (int64_t)threadIdx.x * SCAN_ITEMS + i;
-        if (e < ne) s += cnt[e];
+        if (e < ne) {
+            const int n = new_count<DIM>(coord, r, c0, e);
+            s += n;
+            ch = ch || n != 1 || c0[e];
+        }
     }
+    if (ch) m->changed = 1;
     int64_t tot;
     block_excl_scan(s, sh, &tot);
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
@@ -180,48 +182,45 @@ static __global__ void k_scan_top(int64_t* bsum, DevMeta* m, int64_t cap) {
         carry += tot;
     }
     if (threadIdx.x == 0) {
-        m->ne_new = carry;
         if (carry > cap) {
             m->need = carry;
             atomicOr(&m->err, ERR_CAPACITY);
+        } else {
+            // commit: the new count becomes current, the other set becomes current
+            m->ne_new = ne;          // old count, read by the emit pass
+            m->ne = carry;
+            m->cur_set ^= 1u;
+            if (m->changed) m->rebuilds++;
         }
     }
 }
 
-static __global__ void k_scan_apply(const int32_t* cnt, const int64_t* bsum, int64_t* base_out, const DevMeta* m) {
+// Exclusive offsets of the new leaves, written directly as the new coordinates and the
+// transfer plan (0 keep, 1 child, 2 parent).  Runs after the commit: the old count is
+// in ne_new.
+template <int DIM>
+__global__ void k_scan_emit(const int4* coord, const uint8_t* r, const uint8_t* c0, const int64_t* bsum,
+                            int4* ncoord, int8_t* pkind, int32_t* psrc, int8_t* pbits, const DevMeta* m) {
     if (m->err) return;
+    constexpr int NC = 1 << DIM;
     __shared__ int64_t sh[32];
-    const int64_t ne = m->ne;
+    const int64_t ne = m->ne_new;
     const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
     if (base >= ne) return;
-    int64_t v[SCAN_ITEMS];
+    int v[SCAN_ITEMS];
     int64_t s = 0;
     for (int i = 0; i < SCAN_ITEMS; ++i) {
         const int64_t e = base + (int64_t)threadIdx.x * SCAN_ITEMS + i;
-        v[i] = e < ne ? cnt[e] : 0;
+        v[i] = e < ne ? new_count<DIM>(coord, r, c0, e) : 0;
         s += v[i];
     }
     int64_t tot;
-    int64_t ex = block_excl_scan(s, sh, &tot) + bsum[blockIdx.x];
+    int64_t o = block_excl_scan(s, sh, &tot) + bsum[blockIdx.x];
     for (int i = 0; i < SCAN_ITEMS; ++i) {
         const int64_t e = base + (int64_t)threadIdx.x * SCAN_ITEMS + i;
-        if (e < ne) base_out[e] = ex;
-        ex += v[i];
-    }
-}
-
-// New leaves and the transfer plan (0 keep, 1 child, 2 parent).
-template <int DIM>
-__global__ void k_amr_emit(const int4* coord, const uint8_t* r, const uint8_t* c0, const int32_t* cnt,
-                           const int64_t* base, int4* ncoord, int8_t* pkind, int32_t* psrc, int8_t* pbits,
-                           const DevMeta* m) {
-    if (m->err) return;
-    constexpr int NC = 1 << DIM;
-    const int64_t ne = m->ne;
-    for (int64_t e = gtid(); e < ne; e += gstride()) {
+        if (e >= ne) break;
         const int4 a = coord[e];
-        const int64_t o = base[e];
-        if (r[e]) {
+        if (v[i] == NC) {
             for (int b = 0; b < NC; ++b) {
                 ncoord[o + b] = make_int4(2 * a.x + (b & 1), 2 * a.y + ((b >> 1) & 1),
                                           DIM == 3 ? 2 * a.z + ((b >> 2) & 1) : 0, a.w + 1);
@@ -229,43 +228,42 @@ __global__ void k_amr_emit(const int4* coord, const uint8_t* r, const uint8_t* c
                 psrc[o + b] = (int32_t)e;
                 pbits[o + b] = (int8_t)b;
             }
-        } else if (c0[e]) {
-            ncoord[o] = make_int4(a.x >> 1, a.y >> 1, DIM == 3 ? a.z >> 1 : 0, a.w - 1);
-            pkind[o] = 2;
-            psrc[o] = (int32_t)e;
-            pbits[o] = 0;
-        } else if (cnt[e] == 1) {
-            ncoord[o] = a;
-            pkind[o] = 0;
+        } else if (v[i] == 1) {
+            if (c0[e]) {
+                ncoord[o] = make_int4(a.x >> 1, a.y >> 1, DIM == 3 ? a.z >> 1 : 0, a.w - 1);
+                pkind[o] = 2;
+            } else {
+                ncoord[o] = a;
+                pkind[o] = 0;
+            }
             psrc[o] = (int32_t)e;
             pbits[o] = 0;
         }
+        o += v[i];
     }
 }
 
-static __global__ void k_commit_count(DevMeta* m) {
-    if (m->err) return;
-    m->ne = m->ne_new;
-    m->cur_set ^= 1u;
-    if (m->changed) m->rebuilds++;
-}
-
 // Finest-grid owner map: every leaf writes its index into the finest cells it covers.
+// One thread per (leaf, row of finest cells along x), rows of a coarse leaf being
+// contiguous runs of 2^(L - level) cells.
 template <int DIM>
-__global__ void k_owner_fill(const int4* coord, int32_t* owner, Grid g, const DevMeta* m) {
-    if (m->err) return;
+__global__ void k_owner_fill(const int4* coord, int32_t* owner, Grid g, const DevMeta* m, int force) {
+    if (m->err || !(force || m->changed)) return;
     const int64_t ne = m->ne;
-    for (int64_t e = gtid(); e < ne; e += gstride()) {
+    const int maxrows = DIM == 3 ? (1 << (2 * g.L)) : (1 << g.L);
+    const int64_t total = ne * maxrows;
+    for (int64_t t = gtid(); t < total; t += gstride()) {
+        const int64_t e = t / maxrows;
+        const int row = (int)(t - e * maxrows);
         const int4 a = coord[e];
         const int sh = g.L - a.w;
-        const int64_t n = (int64_t)1 << sh;
-        const int64_t x0 = (int64_t)a.x << sh, y0 = (int64_t)a.y << sh, z0 = DIM == 3 ? ((int64_t)a.z << sh) : 0;
-        const int64_t nz = DIM == 3 ? n : 1;
-        for (int64_t z = 0; z < nz; ++z)
-            for (int64_t y = 0; y < n; ++y) {
-                int32_t* row = owner + x0 + g.fine[0] * ((y0 + y) + g.fine[1] * (z0 + z));
-                for (int64_t x = 0; x < n; ++x) row[x] = (int32_t)e;
-            }
+        const int n = 1 << sh;
+        const int nrows = DIM == 3 ? n * n : n;
+        if (row >= nrows) continue;
+        const int64_t y = ((int64_t)a.y << sh) + (row % n);
+        const int64_t z = DIM == 3 ? (((int64_t)a.z << sh) + row / n) : 0;
+        int32_t* dst = owner + ((int64_t)a.x << sh) + g.fine[0] * (y + g.fine[1] * z);
+        for (int x = 0; x < n; ++x) dst[x] = (int32_t)e;
     }
 }
 
@@ -276,8 +274,8 @@ template <typename R, int DIM, int P>
 __global__ void k_mesh_tables(const int4* coord, const int32_t* owner, Grid g, uint32_t* info, int32_t* nbr,
                               int32_t* hang, int32_t* root, uint32_t* loc, uint8_t* bcfl,
                               const uint8_t* class_b, uint32_t* smask0, uint32_t* smask1, uint32_t* smask2,
-                              uint32_t* smask3, StimBoxes sb, Phys<double> phd, DevMeta* m) {
-    if (m->err) return;
+                              uint32_t* smask3, StimBoxes sb, Phys<double> phd, DevMeta* m, int force) {
+    if (m->err || !(force || m->changed)) return;
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB;
     const int64_t ne = m->ne;
@@ -367,13 +365,33 @@ __global__ void k_mesh_tables(const int4* coord, const int32_t* owner, Grid g, u
 // due count of every tick (tick 0: all; tick i > 0: b >= B - ctz(i)).
 constexpr int ORD_THREADS = 256;
 
-static __global__ void k_order_count(const uint8_t* lvl, int32_t* bcnt, const DevMeta* m) {
-    if (m->err) return;
+// Substep levels b_e = max(b^CFL_e, b^cell_e) (Eq. num-substeps), or the replayed
+// levels, fused with the per-block level counts of the ordering.
+template <typename R>
+__global__ void k_levels_count(const DevArrays<R> d, const int8_t* ovr, const double* eta_t, double tau_cell,
+                               int bcell, int B, int lts, int32_t* bcnt) {
+    if (d.meta->err) return;
     __shared__ int sc[8];
     if (threadIdx.x < 8) sc[threadIdx.x] = 0;
     __syncthreads();
     const int64_t e = (int64_t)blockIdx.x * ORD_THREADS + threadIdx.x;
-    if (e < m->ne) atomicAdd(&sc[lvl[e] & 7], 1);
+    if (e < d.meta->ne) {
+        int b;
+        if (ovr) b = ovr[e];
+        else if (!lts) b = 0;
+        else {
+            b = d.bcfl[e];
+            const int bt = (eta_t[e] > tau_cell) ? bcell : 0;
+            b = bt > b ? bt : b;
+        }
+        if (b > B || b < 0) {
+            atomicOr(&d.meta->err, ERR_CFL);
+            b = b < 0 ? 0 : B;
+        }
+        const uint8_t old = d.lvl[e];
+        d.lvl[e] = (uint8_t)(b | (old & 8));
+        atomicAdd(&sc[b], 1);
+    }
     __syncthreads();
     if (threadIdx.x < 8) bcnt[(int64_t)blockIdx.x * 8 + threadIdx.x] = sc[threadIdx.x];
 }

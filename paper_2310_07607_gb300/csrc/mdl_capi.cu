@@ -21,27 +21,6 @@ __global__ void k_fill_inf(double* p, int64_t n) {
     if (i < n) p[i] = INFINITY;
 }
 
-__global__ void k_reduce_partials(const double* partial, int n, DevMeta* m) {
-    if (m->err) return;
-    __shared__ double red[256];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        m->integral = red[0];
-        m->nbar += 1;
-        if (m->nf_pending) {
-            m->err |= ERR_NONFINITE;
-            m->nf_pending = 0;
-        }
-    }
-}
-
 }  // namespace mdl
 
 namespace {

@@ -3,12 +3,15 @@
 // A barrier step (Alg. 1) is a fixed sequence of kernel launches on the context's
 // stream; element counts, due counts per tick, the barrier counter and errors live
 // in device memory (DevMeta), so the host never waits inside a barrier:
-//   [AMR]  k_eta_s, k_amr_mark, k_amr_close x max_refine, k_amr_family, k_amr_count,
-//          k_scan_*, k_amr_emit (current set -> other set), k_commit_count,
-//          k_owner_fill, k_mesh_tables, k_transfer, k_lat_refresh
-//   levels k_levels, k_order_count / k_order_top / k_order_scatter
+//   [AMR]  k_eta_s, k_amr_mark, k_amr_close x max_refine, k_amr_family, k_scan_blocks,
+//          k_scan_top (commit), k_scan_emit (coordinates into the other state set),
+//          k_owner_fill + k_mesh_tables + k_lat_refresh (in place, only if the mesh changed),
+//          k_transfer (state into the other set)
+//   levels k_levels_count, k_order_top, k_order_scatter
 //   sweep  2^B launches of k_tick (each reads its due count from DevMeta)
-//   end    k_epilogue, k_reduce_partials (eta^t, parities, int V, counters)
+//   end    k_epilogue (eta^t, parities, int V by a last-block reduction, counters)
+// The state (V slots, v, eta^t, levels, coordinates) is double-buffered across an
+// adaptation; the mesh tables are single copies rebuilt in place.
 // The host reads DevMeta once at the end of each stepping call.  A capacity overflow
 // makes every later kernel skip; the host then grows the buffers and resumes at the
 // failed barrier, so results do not depend on the capacity.
@@ -77,20 +80,14 @@ class Ctx : public CtxBase {
     using S = Shape<DIM, P>;
     static constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB, NC = 1 << DIM;
 
-    // One mesh with its state.
+    // State of one mesh (double-buffered across an adaptation).
     struct Set {
         DBuf<R> V0, V1, v;
         DBuf<double> eta_t;
-        DBuf<uint8_t> lvl, bcfl;
+        DBuf<uint8_t> lvl;
         DBuf<int4> coord;
-        DBuf<uint32_t> info, loc;
-        DBuf<int32_t> nbr, hang, root, order;
-        DBuf<uint32_t> smask[MDL_MAX_STIM];
         void release() {
-            V0.release(); V1.release(); v.release(); eta_t.release(); lvl.release(); bcfl.release();
-            coord.release(); info.release(); loc.release(); nbr.release(); hang.release(); root.release();
-            order.release();
-            for (auto& m : smask) m.release();
+            V0.release(); V1.release(); v.release(); eta_t.release(); lvl.release(); coord.release();
         }
     };
 
@@ -115,15 +112,20 @@ class Ctx : public CtxBase {
     DBuf<R> Ia, ga;
     DBuf<double> acc, eta_s, lat, partial, scratch;
     DBuf<uint8_t> r, c0, class_b;
-    DBuf<int32_t> cnt, owner, bcnt, psrc;
-    DBuf<int64_t> base, bsum;
+    DBuf<int32_t> owner, bcnt, psrc;
+    DBuf<int64_t> bsum;
+    // mesh tables (single copies)
+    DBuf<uint8_t> bcfl;
+    DBuf<uint32_t> info, loc;
+    DBuf<int32_t> nbr, hang, root, order;
+    DBuf<uint32_t> smask[MDL_MAX_STIM];
     DBuf<int8_t> pkind, pbits, lvl_ovr;
     DBuf<double> eta_t_ovr;
+    DBuf<double> mtab;   // FP64 GL mass w_q det J per (level, node)
     DBuf<DevMeta> meta;
     DevMeta* hmeta = nullptr;
     bool ovr_levels = false, ovr_eta_s = false, ovr_eta_t = false;
     bool timing = false;
-    bool generic_tick = false;   // one thread per element for every order (parity cross-check)
     std::vector<cudaEvent_t> evpool;
     size_t ev_used = 0;
     struct EvSet {
@@ -131,6 +133,11 @@ class Ctx : public CtxBase {
     };
     std::vector<EvSet> pending_ev;
     mdl_stats stats{};
+    // captured barrier graphs, one per state-set parity (a barrier with adaptation swaps sets)
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int64_t gcap[2] = {-1, -1};
+    int64_t glaunch[2] = {0, 0};
+    bool use_graphs = true;
 
     static int div_up(int64_t n, int64_t b) { return (int)((n + b - 1) / b); }
     int persistent_blocks(int threads) const {
@@ -143,9 +150,9 @@ class Ctx : public CtxBase {
         Set& x = sets[s];
         d.V0 = x.V0.p; d.V1 = x.V1.p; d.v = x.v.p; d.eta_t = x.eta_t.p; d.lvl = x.lvl.p;
         d.Ia = Ia.p; d.ga = ga.p; d.acc = acc.p; d.eta_s = eta_s.p; d.lat = lat.p;
-        d.partial = partial.p; d.bcfl = x.bcfl.p; d.info = x.info.p; d.nbr = x.nbr.p; d.hang = x.hang.p;
-        d.order = x.order.p; d.root = x.root.p; d.loc = x.loc.p;
-        for (int k = 0; k < MDL_MAX_STIM; ++k) d.smask[k] = x.smask[k].p;
+        d.partial = partial.p; d.bcfl = bcfl.p; d.info = info.p; d.nbr = nbr.p; d.hang = hang.p;
+        d.order = order.p; d.root = root.p; d.loc = loc.p;
+        for (int k = 0; k < MDL_MAX_STIM; ++k) d.smask[k] = smask[k].p;
         d.meta = meta.p;
         return d;
     }
@@ -158,15 +165,19 @@ class Ctx : public CtxBase {
         MDL_CK(x.v.ensure((size_t)c * NP));
         MDL_CK(x.eta_t.ensure(c));
         MDL_CK(x.lvl.ensure(c));
-        MDL_CK(x.bcfl.ensure(c));
         MDL_CK(x.coord.ensure(c));
-        MDL_CK(x.info.ensure(c));
-        MDL_CK(x.loc.ensure(c));
-        MDL_CK(x.nbr.ensure((size_t)c * NF));
-        MDL_CK(x.hang.ensure((size_t)c * NF * NSUB));
-        MDL_CK(x.root.ensure(c));
-        MDL_CK(x.order.ensure(c));
-        for (int s = 0; s < pb.n_stim; ++s) MDL_CK(x.smask[s].ensure(c));
+        return MDL_OK;
+    }
+
+    int alloc_tables(int64_t c) {
+        MDL_CK(bcfl.ensure(c));
+        MDL_CK(info.ensure(c));
+        MDL_CK(loc.ensure(c));
+        MDL_CK(nbr.ensure((size_t)c * NF));
+        MDL_CK(hang.ensure((size_t)c * NF * NSUB));
+        MDL_CK(root.ensure(c));
+        MDL_CK(order.ensure(c));
+        for (int s = 0; s < pb.n_stim; ++s) MDL_CK(smask[s].ensure(c));
         return MDL_OK;
     }
 
@@ -177,8 +188,6 @@ class Ctx : public CtxBase {
         MDL_CK(eta_s.ensure(c));
         MDL_CK(r.ensure(c));
         MDL_CK(c0.ensure(c));
-        MDL_CK(cnt.ensure(c));
-        MDL_CK(base.ensure(c));
         MDL_CK(bsum.ensure(div_up(c, SCAN_CHUNK) + 1));
         MDL_CK(bcnt.ensure((size_t)(div_up(c, ORD_THREADS) + 1) * 8 + 8));
         MDL_CK(pkind.ensure(c));
@@ -208,21 +217,21 @@ class Ctx : public CtxBase {
         int rc;
 #define MDL_GROW(buf, per) if ((rc = grow_copy(buf, (size_t)c * (per), (size_t)ne * (per)))) return rc
         MDL_GROW(x.V0, NP); MDL_GROW(x.V1, NP); MDL_GROW(x.v, NP); MDL_GROW(x.eta_t, 1);
-        MDL_GROW(x.lvl, 1); MDL_GROW(x.bcfl, 1); MDL_GROW(x.coord, 1); MDL_GROW(x.info, 1);
-        MDL_GROW(x.loc, 1); MDL_GROW(x.nbr, NF); MDL_GROW(x.hang, NF * NSUB); MDL_GROW(x.root, 1);
-        MDL_GROW(x.order, 1);
-        for (int s = 0; s < pb.n_stim; ++s) MDL_GROW(x.smask[s], 1);
+        MDL_GROW(x.lvl, 1); MDL_GROW(x.coord, 1);
+        MDL_GROW(bcfl, 1); MDL_GROW(info, 1); MDL_GROW(loc, 1); MDL_GROW(nbr, NF); MDL_GROW(hang, NF * NSUB);
+        MDL_GROW(root, 1); MDL_GROW(order, 1);
+        for (int s = 0; s < pb.n_stim; ++s) MDL_GROW(smask[s], 1);
         MDL_GROW(eta_s, 1);
 #undef MDL_GROW
         sets[cs ^ 1].release();
         if ((rc = alloc_set(sets[cs ^ 1], c))) return rc;
         Ia.release(); ga.release(); acc.release(); r.release(); c0.release();
-        cnt.release(); base.release(); bsum.release(); bcnt.release(); pkind.release(); pbits.release();
-        psrc.release();
+        bsum.release(); bcnt.release(); pkind.release(); pbits.release(); psrc.release();
         if ((rc = alloc_shared(c))) return rc;
         if (lvl_ovr.p && (rc = grow_copy(lvl_ovr, (size_t)c, (size_t)ne))) return rc;
         if (eta_t_ovr.p && (rc = grow_copy(eta_t_ovr, (size_t)c, (size_t)ne))) return rc;
         cap = c;
+        drop_graphs();
         return MDL_OK;
     }
 
@@ -242,15 +251,16 @@ class Ctx : public CtxBase {
         return MDL_OK;
     }
 
-    // Build the mesh tables of set s from its coordinates (device), given ne in DevMeta.
-    int build_tables(int s) {
+    // Build the mesh tables from the coordinates of set s (device), given ne in DevMeta;
+    // unless forced, only when this barrier's adaptation changed the mesh.
+    int build_tables(int s, int force) {
         Set& x = sets[s];
         const int gb = persistent_blocks(256);
-        k_owner_fill<DIM><<<gb, 256, 0, st>>>(x.coord.p, owner.p, grid_, meta.p);
+        k_owner_fill<DIM><<<nsm * 8, 256, 0, st>>>(x.coord.p, owner.p, grid_, meta.p, force);
         MDL_LAUNCHED();
         k_mesh_tables<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(
-            x.coord.p, owner.p, grid_, x.info.p, x.nbr.p, x.hang.p, x.root.p, x.loc.p, x.bcfl.p, class_b.p,
-            x.smask[0].p, x.smask[1].p, x.smask[2].p, x.smask[3].p, sboxes, phd, meta.p);
+            x.coord.p, owner.p, grid_, info.p, nbr.p, hang.p, root.p, loc.p, bcfl.p, class_b.p,
+            smask[0].p, smask[1].p, smask[2].p, smask[3].p, sboxes, phd, meta.p, force);
         MDL_LAUNCHED();
         return MDL_OK;
     }
@@ -265,8 +275,10 @@ class Ctx : public CtxBase {
             int rc = alloc_set(sets[0], c);
             if (!rc) rc = alloc_set(sets[1], c);
             if (!rc) rc = alloc_shared(c);
+            if (!rc) rc = alloc_tables(c);
             if (rc) return rc;
             cap = c;
+            drop_graphs();
         }
         std::vector<int4> hc(n);
         for (int64_t i = 0; i < n; ++i) {
@@ -280,7 +292,7 @@ class Ctx : public CtxBase {
         init.nbar = nbar;
         init.cur_set = (unsigned)cs;
         MDL_CK(cudaMemcpyAsync(meta.p, &init, sizeof(DevMeta), cudaMemcpyHostToDevice, st));
-        int rc = build_tables(cs);
+        int rc = build_tables(cs, 1);
         if (rc) return rc;
         ne = n;
         MDL_CK(cudaMemsetAsync(x.V0.p, 0, (size_t)n * NP * sizeof(R), st));
@@ -291,7 +303,7 @@ class Ctx : public CtxBase {
         MDL_CK(cudaMemsetAsync(eta_s.p, 0, n * sizeof(double), st));
         k_fill_inf<<<div_up(n_probe, 256), 256, 0, st>>>(lat.p, n_probe);
         MDL_LAUNCHED();
-        k_lat_refresh<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(arrays(cs), T, ph, (double)nbar * dt, 0);
+        k_lat_refresh<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(arrays(cs), T, ph, (double)nbar * dt, 0, 1);
         MDL_LAUNCHED();
         rc = sync_meta();   // the host staging buffer hc must outlive the copy
         if (rc) return rc;
@@ -330,32 +342,26 @@ class Ctx : public CtxBase {
                                                   pb.max_refine);
             MDL_LAUNCHED();
             for (int i = 0; i < pb.max_refine; ++i) {
-                k_amr_close<DIM><<<g256, 256, 0, st>>>(so.info.p, so.nbr.p, r.p, meta.p);
+                k_amr_close<DIM><<<g256, 256, 0, st>>>(info.p, nbr.p, r.p, meta.p);
                 MDL_LAUNCHED();
             }
-            k_amr_family<DIM><<<g256, 256, 0, st>>>(so.coord.p, so.info.p, so.nbr.p, eta_s.p, r.p, c0.p, meta.p,
+            k_amr_family<DIM><<<g256, 256, 0, st>>>(so.coord.p, info.p, nbr.p, eta_s.p, r.p, c0.p, meta.p,
                                                     pb.tau_coarsen);
             MDL_LAUNCHED();
-            k_amr_count<DIM><<<g256, 256, 0, st>>>(so.coord.p, r.p, c0.p, cnt.p, meta.p);
-            MDL_LAUNCHED();
             const int nsb = div_up(cap, SCAN_CHUNK);
-            k_scan_blocks<<<nsb, SCAN_THREADS, 0, st>>>(cnt.p, bsum.p, meta.p);
+            k_scan_blocks<DIM><<<nsb, SCAN_THREADS, 0, st>>>(so.coord.p, r.p, c0.p, bsum.p, meta.p);
             MDL_LAUNCHED();
             k_scan_top<<<1, 1024, 0, st>>>(bsum.p, meta.p, cap);
             MDL_LAUNCHED();
-            k_scan_apply<<<nsb, SCAN_THREADS, 0, st>>>(cnt.p, bsum.p, base.p, meta.p);
-            MDL_LAUNCHED();
-            k_amr_emit<DIM><<<g256, 256, 0, st>>>(so.coord.p, r.p, c0.p, cnt.p, base.p, sn.coord.p, pkind.p,
-                                                  psrc.p, pbits.p, meta.p);
+            k_scan_emit<DIM><<<nsb, SCAN_THREADS, 0, st>>>(so.coord.p, r.p, c0.p, bsum.p, sn.coord.p, pkind.p,
+                                                           psrc.p, pbits.p, meta.p);
             MDL_LAUNCHED();
             DevArrays<R> od = arrays(o);
-            k_commit_count<<<1, 1, 0, st>>>(meta.p);
-            MDL_LAUNCHED();
-            int rc = build_tables(n);
+            int rc = build_tables(n, 0);
             if (rc) return rc;
             k_transfer<R, DIM, P><<<g128, 128, 0, st>>>(od, arrays(n), pkind.p, psrc.p, pbits.p, T);
             MDL_LAUNCHED();
-            k_lat_refresh<R, DIM, P><<<g128, 128, 0, st>>>(arrays(n), T, ph, 0.0, 0);
+            k_lat_refresh<R, DIM, P><<<g128, 128, 0, st>>>(arrays(n), T, ph, 0.0, 0, 0);
             MDL_LAUNCHED();
             cs = n;
         }
@@ -365,15 +371,13 @@ class Ctx : public CtxBase {
             if (bcell < 0) bcell = 15;
         }
         const double* et = ovr_eta_t ? eta_t_ovr.p : sets[cs].eta_t.p;
-        k_levels<R><<<g256, 256, 0, st>>>(arrays(cs), ovr_levels ? lvl_ovr.p : nullptr, et, pb.tau_cell, bcell, B,
-                                          pb.lts_enabled);
-        MDL_LAUNCHED();
         const int nob = div_up(cap, ORD_THREADS);
-        k_order_count<<<nob, ORD_THREADS, 0, st>>>(sets[cs].lvl.p, bcnt.p, meta.p);
+        k_levels_count<R><<<nob, ORD_THREADS, 0, st>>>(arrays(cs), ovr_levels ? lvl_ovr.p : nullptr, et,
+                                                       pb.tau_cell, bcell, B, pb.lts_enabled, bcnt.p);
         MDL_LAUNCHED();
         k_order_top<<<1, 1024, 0, st>>>(bcnt.p, meta.p, B);
         MDL_LAUNCHED();
-        k_order_scatter<<<nob, ORD_THREADS, 0, st>>>(sets[cs].lvl.p, bcnt.p, sets[cs].order.p, meta.p);
+        k_order_scatter<<<nob, ORD_THREADS, 0, st>>>(sets[cs].lvl.p, bcnt.p, order.p, meta.p);
         MDL_LAUNCHED();
         TickArgs<R> ta{};
         ta.d = arrays(cs);
@@ -384,22 +388,58 @@ class Ctx : public CtxBase {
         const int nt = 1 << B;
         for (int i = 0; i < nt; ++i) {
             ta.tick = i;
-            if (P == 1 && !generic_tick) {
-                const int gq = (int)std::min<int64_t>(div_up(std::max<int64_t>(cap, 1) * NP, 256),
-                                                      (int64_t)nsm * 8);
-                k_tick_q1<R, DIM><<<gq, 256, 0, st>>>(ta, T, ph);
-            } else {
-                k_tick<R, DIM, P><<<g128, 128, 0, st>>>(ta, T, ph);
-            }
+            k_tick<R, DIM, P><<<g128, 128, 0, st>>>(ta, T, ph);
             MDL_LAUNCHED();
             stats.tick_launches++;
         }
         if (timing && (e1 = next_event())) MDL_CK(cudaEventRecord(e1, st));
-        k_epilogue<R, DIM, P><<<g256, 256, 0, st>>>(arrays(cs), T, ph, dt);
-        MDL_LAUNCHED();
-        k_reduce_partials<<<1, 256, 0, st>>>(partial.p, g256, meta.p);
+        k_epilogue<R, DIM, P><<<g256, 256, 0, st>>>(arrays(cs), mtab.p, dt);
         MDL_LAUNCHED();
         if (timing) pending_ev.push_back({e0, e1, e2, e3});
+        return MDL_OK;
+    }
+
+    void drop_graphs() {
+        for (int i = 0; i < 2; ++i) {
+            if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
+            gexec[i] = nullptr;
+            gcap[i] = -1;
+        }
+    }
+
+    // One barrier: replay the captured graph of the current set parity, capturing it
+    // first if needed; direct launches when inputs are replayed or per-barrier timing is on.
+    int run_barrier() {
+        const bool ovr = ovr_levels || ovr_eta_s || ovr_eta_t;
+        if (!use_graphs || timing || ovr) return launch_barrier();
+        const int key = pb.amr_enabled ? cs : 0;
+        if (!gexec[key] || gcap[key] != cap) {
+            if (gexec[key]) cudaGraphExecDestroy(gexec[key]);
+            gexec[key] = nullptr;
+            const int cs0 = cs;
+            const int64_t kl0 = stats.kernel_launches, tl0 = stats.tick_launches;
+            cudaGraph_t graph;
+            MDL_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            int rc = launch_barrier();
+            cudaError_t ec = cudaStreamEndCapture(st, &graph);
+            if (rc) {
+                if (ec == cudaSuccess) cudaGraphDestroy(graph);
+                return rc;
+            }
+            MDL_CK(ec);
+            ec = cudaGraphInstantiate(&gexec[key], graph, 0);
+            cudaGraphDestroy(graph);
+            MDL_CK(ec);
+            glaunch[key] = stats.kernel_launches - kl0;
+            stats.kernel_launches = kl0;
+            stats.tick_launches = tl0;
+            gcap[key] = cap;
+            cs = cs0;
+        }
+        MDL_CK(cudaGraphLaunch(gexec[key], st));
+        stats.kernel_launches += glaunch[key];
+        stats.tick_launches += 1 << B;
+        if (pb.amr_enabled) cs ^= 1;
         return MDL_OK;
     }
 
@@ -416,11 +456,15 @@ class Ctx : public CtxBase {
 public:
     ~Ctx() override {
         if (st) cudaStreamSynchronize(st);
+        drop_graphs();
         for (auto& s : sets) s.release();
         Ia.release(); ga.release(); acc.release(); eta_s.release(); lat.release(); partial.release();
-        scratch.release(); r.release(); c0.release(); class_b.release(); cnt.release(); owner.release();
-        bcnt.release(); psrc.release(); base.release(); bsum.release(); pkind.release(); pbits.release();
-        lvl_ovr.release(); eta_t_ovr.release(); meta.release();
+        scratch.release(); r.release(); c0.release(); class_b.release(); owner.release();
+        bcnt.release(); psrc.release(); bsum.release(); pkind.release(); pbits.release();
+        bcfl.release(); info.release(); loc.release(); nbr.release(); hang.release(); root.release();
+        order.release();
+        for (auto& m : smask) m.release();
+        lvl_ovr.release(); eta_t_ovr.release(); meta.release(); mtab.release();
         if (hmeta) cudaFreeHost(hmeta);
         for (auto e : evpool) cudaEventDestroy(e);
         if (st) cudaStreamDestroy(st);
@@ -489,6 +533,15 @@ public:
                 }
             }
         }
+        std::vector<double> hm(8 * NP);
+        for (int l = 0; l < 8; ++l)
+            for (int q = 0; q < NP; ++q) {
+                double w = phd.Wvol[l];
+                for (int k = 0; k < DIM; ++k) w *= Td.w[digit<N1>(q, k)];
+                hm[l * NP + q] = w;
+            }
+        MDL_CK(mtab.ensure(hm.size()));
+        MDL_CK(cudaMemcpyAsync(mtab.p, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         MDL_CK(class_b.ensure(hcb.size()));
         MDL_CK(cudaMemcpyAsync(class_b.p, hcb.data(), hcb.size(), cudaMemcpyHostToDevice, st));
         Mesh mh;
@@ -537,7 +590,7 @@ public:
                                                                      s ? scratch.p + n_dof : nullptr);
         MDL_LAUNCHED();
         MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
-        k_lat_refresh<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(arrays(cs), T, ph, (double)nbar * dt, 1);
+        k_lat_refresh<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(arrays(cs), T, ph, (double)nbar * dt, 1, 1);
         MDL_LAUNCHED();
         MDL_CK(cudaStreamSynchronize(st));
         return MDL_OK;
@@ -587,7 +640,7 @@ public:
             const bool ovr = ovr_levels || ovr_eta_s || ovr_eta_t;
             const int64_t chunk = ovr ? 1 : (n - done);
             for (int64_t i = 0; i < chunk; ++i) {
-                int rc = launch_barrier();
+                int rc = run_barrier();
                 if (rc) return rc;
             }
             int rc = sync_meta();
@@ -683,7 +736,7 @@ public:
         std::vector<int32_t> hr(ne);
         std::vector<uint8_t> hl(ne);
         MDL_CK(cudaMemcpyAsync(hc.data(), sets[cs].coord.p, ne * sizeof(int4), cudaMemcpyDeviceToHost, st));
-        MDL_CK(cudaMemcpyAsync(hr.data(), sets[cs].root.p, ne * 4, cudaMemcpyDeviceToHost, st));
+        MDL_CK(cudaMemcpyAsync(hr.data(), root.p, ne * 4, cudaMemcpyDeviceToHost, st));
         MDL_CK(cudaMemcpyAsync(hl.data(), sets[cs].lvl.p, ne, cudaMemcpyDeviceToHost, st));
         MDL_CK(cudaStreamSynchronize(st));
         for (int64_t i = 0; i < ne; ++i) {
@@ -706,9 +759,9 @@ public:
         }
         std::vector<uint32_t> hi(ne);
         std::vector<int32_t> hn((size_t)ne * NF), hh((size_t)ne * NF * NSUB);
-        MDL_CK(cudaMemcpyAsync(hi.data(), sets[cs].info.p, ne * 4, cudaMemcpyDeviceToHost, st));
-        MDL_CK(cudaMemcpyAsync(hn.data(), sets[cs].nbr.p, (size_t)ne * NF * 4, cudaMemcpyDeviceToHost, st));
-        MDL_CK(cudaMemcpyAsync(hh.data(), sets[cs].hang.p, (size_t)ne * NF * NSUB * 4, cudaMemcpyDeviceToHost, st));
+        MDL_CK(cudaMemcpyAsync(hi.data(), info.p, ne * 4, cudaMemcpyDeviceToHost, st));
+        MDL_CK(cudaMemcpyAsync(hn.data(), nbr.p, (size_t)ne * NF * 4, cudaMemcpyDeviceToHost, st));
+        MDL_CK(cudaMemcpyAsync(hh.data(), hang.p, (size_t)ne * NF * NSUB * 4, cudaMemcpyDeviceToHost, st));
         MDL_CK(cudaStreamSynchronize(st));
         for (int64_t e = 0; e < ne; ++e)
             for (int f = 0; f < NF; ++f) {

@@ -36,7 +36,8 @@ struct DevMeta {
     unsigned int err;        // sticky: 1 non-finite, 2 CFL, 4 capacity, 8 mesh
     unsigned int changed;    // the adaptation changed the mesh
     unsigned int nf_pending; // non-finite values seen by this barrier's epilogue
-    unsigned int cur_set;    // index of the state/mesh set holding the current mesh
+    unsigned int cur_set;    // index of the state set holding the current values
+    unsigned int done_blocks;// epilogue blocks finished (last-block reduction)
     unsigned int cnt[8];     // elements per level b in this barrier
     int32_t nact[128];       // due elements per tick
     int64_t elem_updates;    // accumulated element steps
@@ -140,7 +141,28 @@ __device__ __forceinline__ void load_seen(const DevArrays<R>& d, int tick, int B
     }
 }
 
-// Residual r = (A u)_e with the neighbours seen at tick `tick`.
+// Values of element nb as seen at tick `tick`, given its level byte (see load_seen).
+template <typename R, int NP>
+__device__ __forceinline__ void load_seen_lv(const DevArrays<R>& d, int tick, int B, int nb, uint8_t lv, R* un) {
+    const int b = lv & 7, par = (lv >> 3) & 1;
+    const int sh = B - b;
+    const int j = tick >> sh;
+    const int rem = tick & ((1 << sh) - 1);
+    const int nw = par ^ ((j + (rem ? 1 : 0)) & 1);
+    const R* sn = (nw ? d.V1 : d.V0) + (size_t)nb * NP;
+    const R* so = (nw ? d.V0 : d.V1) + (size_t)nb * NP;
+    const R th = R(rem) / R(1 << sh);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const R n = sn[q];
+        un[q] = rem ? so[q] + th * (n - so[q]) : n;
+    }
+}
+
+// Residual r = (A u)_e with the neighbours seen at tick `tick`.  All same-level and
+// coarser neighbours are gathered before any face arithmetic (their ids, then their
+// level bytes, then their values), so the dependent loads of the faces overlap;
+// hanging faces (finer neighbours) follow on a separate path.
 template <typename R, int DIM, int P>
 __device__ __forceinline__ void element_residual(const DevArrays<R>& d, const Tables<R>& T,
                                                  const Phys<R>& ph, int tick, int B, int e,
@@ -149,25 +171,65 @@ __device__ __forceinline__ void element_residual(const DevArrays<R>& d, const Ta
     constexpr int NP = S::NP, NF = S::NF, NSUB = S::NSUB;
 #pragma unroll
     for (int q = 0; q < NP; ++q) r[q] = R(0);
+    if constexpr (P > 1) {
+        // Q2: one face at a time (holding every neighbour's 27 values would spill)
+        volume_term<R, DIM, P>(T, ph, lev, u, r);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const int kind = (inf >> (4 * f)) & 3;
+            if (kind == 0) continue;
+            const int k = f >> 1, s = (f & 1) ? 1 : -1;
+            const int nbi = d.nbr[(size_t)e * NF + f];
+            if (kind != 3) {
+                R un[NP];
+                load_seen<R, NP>(d, tick, B, nbi, un);
+                const int pos = (inf >> (4 * f + 2)) & 3;
+                face_term<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
+                                     kind == 1 ? -1 : pos, un, lev, r);
+            } else {
+                for (int sb = 0; sb < NSUB; ++sb) {
+                    R un[NP];
+                    load_seen<R, NP>(d, tick, B, d.hang[nbi + sb], un);
+                    face_term<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1, r);
+                }
+            }
+        }
+        return;
+    }
+    int nbf[NF], src[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) nbf[f] = d.nbr[(size_t)e * NF + f];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const int kind = (inf >> (4 * f)) & 3;
+        src[f] = (kind == 1 || kind == 2) ? nbf[f] : e;
+    }
+    uint8_t lvn[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) lvn[f] = d.lvl[src[f]];
+    R un[NF][NP];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) load_seen_lv<R, NP>(d, tick, B, src[f], lvn[f], un[f]);
     volume_term<R, DIM, P>(T, ph, lev, u, r);
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         const int kind = (inf >> (4 * f)) & 3;
-        if (kind == 0) continue;
         const int k = f >> 1, s = (f & 1) ? 1 : -1;
-        const int nbi = d.nbr[(size_t)e * NF + f];
-        if (kind != 3) {
-            R un[NP];
-            load_seen<R, NP>(d, tick, B, nbi, un);
+        if (kind == 1 || kind == 2) {
             const int pos = (inf >> (4 * f + 2)) & 3;
             face_term<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
-                                 kind == 1 ? -1 : pos, un, lev, r);
-        } else {
-            for (int sb = 0; sb < NSUB; ++sb) {
-                R un[NP];
-                load_seen<R, NP>(d, tick, B, d.hang[nbi + sb], un);
-                face_term<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1, r);
-            }
+                                 kind == 1 ? -1 : pos, un[f], lev, r);
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const int kind = (inf >> (4 * f)) & 3;
+        if (kind != 3) continue;
+        const int k = f >> 1, s = (f & 1) ? 1 : -1;
+        for (int sb = 0; sb < NSUB; ++sb) {
+            R uh[NP];
+            load_seen<R, NP>(d, tick, B, d.hang[nbf[f] + sb], uh);
+            face_term<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, uh, lev + 1, r);
         }
     }
 }
@@ -319,7 +381,8 @@ __global__ void __launch_bounds__(128) k_tick(const TickArgs<R> a, const Tables<
     }
 }
 
-// Kelly-type spatial indicator per element (Eq. dg-error-estimate) on the barrier-start values.
+// Kelly-type spatial indicator per element (Eq. dg-error-estimate) on the barrier-start
+// values; same-level and coarser neighbours are gathered before the face arithmetic.
 template <typename R, int DIM, int P>
 __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> ph) {
     using S = Shape<DIM, P>;
@@ -327,32 +390,67 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
     if (d.meta->err) return;
     const int64_t ne = d.meta->ne;
     for (int64_t e = gtid(); e < ne; e += gstride()) {
-    const int par = (d.lvl[e] >> 3) & 1;
-    const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
-    R u[NP];
+        const uint32_t inf = d.info[e];
+        const int lev = (inf >> 24) & 15;
+        const int par = (d.lvl[e] >> 3) & 1;
+        const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
+        R u[NP];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) u[q] = Vc[q];
-    const uint32_t inf = d.info[e];
-    const int lev = (inf >> 24) & 15;
-    double acc = 0.0;
+        for (int q = 0; q < NP; ++q) u[q] = Vc[q];
+        double acc = 0.0;
+        int nbf[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        const int kind = (inf >> (4 * f)) & 3;
-        if (kind == 0) continue;
-        const int k = f >> 1, s = (f & 1) ? 1 : -1;
-        const int nbi = d.nbr[(size_t)e * NF + f];
-        if (kind != 3) {
-            const int pn = (d.lvl[nbi] >> 3) & 1;
-            const R* src = (pn ? d.V1 : d.V0) + (size_t)nbi * NP;
-            R un[NP];
+        for (int f = 0; f < NF; ++f) nbf[f] = d.nbr[(size_t)e * NF + f];
+        if constexpr (P == 1) {
+            int src[NF];
+            uint8_t lvn[NF];
 #pragma unroll
-            for (int q = 0; q < NP; ++q) un[q] = src[q];
-            const int pos = (inf >> (4 * f + 2)) & 3;
-            acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
-                                         kind == 1 ? -1 : pos, un, lev);
+            for (int f = 0; f < NF; ++f) {
+                const int kind = (inf >> (4 * f)) & 3;
+                src[f] = (kind == 1 || kind == 2) ? nbf[f] : (int)e;
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) lvn[f] = d.lvl[src[f]];
+            R un[NF][NP];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const R* srcp = (((lvn[f] >> 3) & 1) ? d.V1 : d.V0) + (size_t)src[f] * NP;
+#pragma unroll
+                for (int q = 0; q < NP; ++q) un[f][q] = srcp[q];
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const int kind = (inf >> (4 * f)) & 3;
+                if (kind != 1 && kind != 2) continue;
+                const int k = f >> 1, s = (f & 1) ? 1 : -1;
+                const int pos = (inf >> (4 * f + 2)) & 3;
+                acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
+                                             kind == 1 ? -1 : pos, un[f], lev);
+            }
         } else {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const int kind = (inf >> (4 * f)) & 3;
+                if (kind != 1 && kind != 2) continue;
+                const int k = f >> 1, s = (f & 1) ? 1 : -1;
+                const int nbi = nbf[f];
+                const int pn = (d.lvl[nbi] >> 3) & 1;
+                const R* src = (pn ? d.V1 : d.V0) + (size_t)nbi * NP;
+                R un[NP];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) un[q] = src[q];
+                const int pos = (inf >> (4 * f + 2)) & 3;
+                acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
+                                             kind == 1 ? -1 : pos, un, lev);
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const int kind = (inf >> (4 * f)) & 3;
+            if (kind != 3) continue;
+            const int k = f >> 1, s = (f & 1) ? 1 : -1;
             for (int sb = 0; sb < NSUB; ++sb) {
-                const int nb = d.hang[nbi + sb];
+                const int nb = d.hang[nbf[f] + sb];
                 const int pn = (d.lvl[nb] >> 3) & 1;
                 const R* src = (pn ? d.V1 : d.V0) + (size_t)nb * NP;
                 R un[NP];
@@ -361,40 +459,15 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
                 acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
             }
         }
-    }
-    d.eta_s[e] = sqrt(acc);
-    }
-}
-
-// Substep levels b_e = max(b^CFL_e, b^cell_e) (Eq. num-substeps), or the replayed levels.
-template <typename R>
-__global__ void k_levels(const DevArrays<R> d, const int8_t* ovr, const double* eta_t, double tau_cell,
-                         int bcell, int B, int lts) {
-    if (d.meta->err) return;
-    const int64_t ne = d.meta->ne;
-    for (int64_t e = gtid(); e < ne; e += gstride()) {
-        int b;
-        if (ovr) b = ovr[e];
-        else if (!lts) b = 0;
-        else {
-            b = d.bcfl[e];
-            const int bt = (eta_t[e] > tau_cell) ? bcell : 0;
-            b = bt > b ? bt : b;
-        }
-        if (b > B || b < 0) {
-            atomicOr(&d.meta->err, ERR_CFL);
-            b = b < 0 ? 0 : B;
-        }
-        const uint8_t old = d.lvl[e];
-        d.lvl[e] = (uint8_t)(b | (old & 8));
+        d.eta_s[e] = sqrt(acc);
     }
 }
 
 // Barrier epilogue: eta^t = sqrt(acc)/dt, parity flip of single-step elements, non-finite
 // check, per-block partial sums of int V = sum_q M_q V_q (FP64).
 template <typename R, int DIM, int P>
-__global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const Tables<R> T,
-                                                 const Phys<R> ph, double dt) {
+__global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const double* __restrict__ mtab,
+                                                 double dt) {
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
     __shared__ double red[256];
@@ -413,13 +486,11 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const Ta
         const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
         const R* w = d.v + (size_t)e * NP;
         const int lev = (d.info[e] >> 24) & 15;
+        const double* Mq = mtab + lev * NP;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            double Mq = (double)ph.Wvol[lev];
-#pragma unroll
-            for (int k = 0; k < DIM; ++k) Mq *= (double)T.w[digit<N1>(q, k)];
             const R x = Vc[q];
-            loc += Mq * (double)x;
+            loc += Mq[q] * (double)x;
             bad = bad || !isfinite(x) || !isfinite(w[q]);
         }
     }
@@ -430,12 +501,37 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const Ta
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) d.partial[blockIdx.x] = red[0];
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        d.partial[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(&d.meta->done_blocks, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last block: fixed-order sum of the partials, barrier count, non-finite flag
+    __threadfence();
+    double s2 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s2 += ((volatile double*)d.partial)[i];
+    red[threadIdx.x] = s2;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        DevMeta* m = d.meta;
+        m->integral = red[0];
+        m->nbar += 1;
+        m->done_blocks = 0;
+        if (m->nf_pending) {
+            m->err |= ERR_NONFINITE;
+            m->nf_pending = 0;
+        }
+    }
 }
 
-// End of a barrier: deterministic sum of the epilogue partials (one block, fixed
-// order), barrier count, non-finite flag.
-__global__ void k_reduce_partials(const double* partial, int n, DevMeta* m);
+
 
 // Copy V (current slot by parity) or v to an FP64 output.
 template <typename R, int NP>
@@ -464,10 +560,11 @@ __global__ void k_scatter_initial(DevArrays<R> d, int64_t ne, const double* V, c
 // Activation at the current time for probes already above threshold, and the
 // per-element pending flag (any probe of the element not yet activated).
 template <typename R, int DIM, int P>
-__global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> ph, double t, int mark_now) {
+__global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> ph, double t, int mark_now,
+                              int force) {
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
-    if (d.meta->err) return;
+    if (d.meta->err || !(force || d.meta->changed)) return;
     const int64_t ne = d.meta->ne;
     for (int64_t e = gtid(); e < ne; e += gstride()) {
     uint32_t inf = d.info[e];
@@ -594,146 +691,3 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
 
 }  // namespace mdl
 
-namespace mdl {
-
-// --------------------------------------------------------------------------
-// Cooperative sweep tick for Q1 elements: a group of G = (p+1)^d lanes per element
-// (4 in 2D, 8 in 3D).  Lane g loads and updates DOF g; lane f < 2d gathers the
-// neighbour(s) across face f (time-interpolated) and evaluates that face's
-// contribution; the contributions are summed over the group by shuffles.  The
-// arithmetic per DOF is the one of k_tick; only the work split differs, which keeps
-// G times more warps in flight to hide the dependent neighbour loads.
-// --------------------------------------------------------------------------
-template <typename R, int DIM>
-__global__ void __launch_bounds__(256) k_tick_q1(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph) {
-    using S = Shape<DIM, 1>;
-    constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB;
-    constexpr int G = NP;  // lanes per element
-    const DevArrays<R>& d = a.d;
-    if (d.meta->err) return;
-    const int n_act = d.meta->nact[a.tick];
-    const double nt = (double)(1 << a.B);
-    const double t_i = ((double)d.meta->nbar * nt + (double)a.tick) * a.dt / nt;
-    const int lane = threadIdx.x & 31;
-    const int g = lane % G;
-    const unsigned gmask = ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)) << (lane - g);
-    const int64_t gid = gtid() / G, gstr = gstride() / G;
-    for (int64_t idx = gid; idx < n_act; idx += gstr) {
-        const int e = d.order[idx];
-        const uint8_t lv = d.lvl[e];
-        const uint32_t inf = d.info[e];
-        const int b = lv & 7, par = (lv >> 3) & 1;
-        const int ke = a.tick >> (a.B - b);
-        const int cur = par ^ (ke & 1);
-        const int lev = (inf >> 24) & 15;
-        const R* Vc = (cur ? d.V1 : d.V0) + (size_t)e * NP;
-        R* Vd = (cur ? d.V0 : d.V1) + (size_t)e * NP;
-        const R my_u = Vc[g];
-        const R my_w = d.v[(size_t)e * NP + g];
-        int my_nb = -1;
-        if (g < NF) my_nb = d.nbr[(size_t)e * NF + g];
-        R u[NP];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) u[q] = __shfl_sync(gmask, my_u, q, G);
-        // face contribution of this lane's face
-        R rf[NP];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) rf[q] = R(0);
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            if (f != g) continue;
-            const int kind = (inf >> (4 * f)) & 3;
-            if (kind == 0) continue;
-            const int k = f >> 1, s = (f & 1) ? 1 : -1;
-            if (kind != 3) {
-                R un[NP];
-                load_seen<R, NP>(d, a.tick, a.B, my_nb, un);
-                const int pos = (inf >> (4 * f + 2)) & 3;
-                face_term<R, DIM, 1>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1, kind == 1 ? -1 : pos,
-                                     un, lev, rf);
-            } else {
-                for (int sb = 0; sb < NSUB; ++sb) {
-                    R un[NP];
-                    load_seen<R, NP>(d, a.tick, a.B, d.hang[my_nb + sb], un);
-                    face_term<R, DIM, 1>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1, rf);
-                }
-            }
-        }
-        // volume term (every lane, all rows) plus the group sum of the face terms
-        R r[NP];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) r[q] = R(0);
-        volume_term<R, DIM, 1>(T, ph, lev, u, r);
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            R x = rf[q];
-#pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(gmask, x, o, G);
-            r[q] += x;
-        }
-        // pointwise update of DOF g
-        const double dte_d = ldexp(a.dt, -b);
-        const R dte = (R)dte_d;
-        const double t_mid = t_i + 0.5 * dte_d;
-        R stim_o = R(0), stim_m = R(0);
-        if (inf & INFO_STIM) {
-            for (int s = 0; s < a.stim.n; ++s) {
-                const bool on_o = (a.stim.t0[s] <= t_i) && (t_i < a.stim.t1[s]);
-                const bool on_m = (a.stim.t0[s] <= t_mid) && (t_mid < a.stim.t1[s]);
-                if (!on_o && !on_m) continue;
-                if ((d.smask[s][e] >> g) & 1u) {
-                    if (on_o) stim_o -= (R)a.stim.amp[s];
-                    if (on_m) stim_m -= (R)a.stim.amp[s];
-                }
-            }
-        }
-        R Iag, gag;
-        if (ke == 0) {
-            Iag = ap_iion(ph, my_u, my_w) + stim_o;
-            gag = ap_g(ph, my_u, my_w);
-            if (b > 0) {
-                d.Ia[(size_t)e * NP + g] = Iag;
-                d.ga[(size_t)e * NP + g] = gag;
-            }
-        } else {
-            Iag = d.Ia[(size_t)e * NP + g];
-            gag = d.ga[(size_t)e * NP + g];
-        }
-        R rg = r[0];
-#pragma unroll
-        for (int q = 1; q < NP; ++q)
-            if (q == g) rg = r[q];
-        R Mq = ph.Wvol[lev];
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) Mq *= T.w[digit<N1>(g, k)];
-        const R I = ap_iion(ph, my_u, my_w) + stim_o;
-        const R un_g = my_u + dte * (-rg / Mq - I);
-        const R wn_g = ap_step_state(ph, my_u, my_w, dte);
-        const R Vm = R(0.5) * (my_u + un_g);
-        const R wm = R(0.5) * (my_w + wn_g);
-        const R dI = ap_iion(ph, Vm, wm) + stim_m - Iag;
-        const R dg = ap_g(ph, Vm, wm) - gag;
-        R term = Mq * (dI * dI + dg * dg);
-        R vmax = un_g < R(0) ? -un_g : un_g;
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            term += __shfl_xor_sync(gmask, term, o, G);
-            const R om = __shfl_xor_sync(gmask, vmax, o, G);
-            vmax = om > vmax ? om : vmax;
-        }
-        Vd[g] = un_g;
-        d.v[(size_t)e * NP + g] = wn_g;
-        if (g == 0) {
-            const double inc = dte_d * (double)term;
-            d.acc[e] = (ke == 0) ? inc : d.acc[e] + inc;
-        }
-        if ((inf & INFO_PENDING) && vmax >= ph.lat_gate) {
-            R unv[NP];
-#pragma unroll
-            for (int q = 0; q < NP; ++q) unv[q] = __shfl_sync(gmask, un_g, q, G);
-            if (g == 0) lat_check<R, DIM, 1>(d, T, ph, e, inf, lev, u, unv, t_i, dte_d);
-        }
-    }
-}
-
-}  // namespace mdl

@@ -316,3 +316,42 @@ def test_coarsen_only_replay_bit_exact(mdl, dim):
         changed = any(pl[0] != 'keep' for pl in plan)
         assert (g.stats()["amr_rebuilds"] - before) == (1 if changed else 0)
     g.close()
+
+
+def test_full_size_slab2d_replay_matches_oracle(mdl):
+    """The benchmark workload at full size (256x256 roots, AMR to depth 3, 4 LTS levels, FP32)
+    from the synthetic developed front, in the benchmark's launch configuration, with the
+    oracle's eta^s replayed: meshes and levels bit-exact, V within 1e-3, activation times
+    within one finest substep; and the device's own eta^s within FP32 error of the oracle's."""
+    prob = W.slab_2d_q1_256()
+    o = lts.Sim(prob.replace(precision=64))
+    X = o.disc.node_coords()
+    V0, v0 = W.front_state(X, (0.0, 0.0, 0.0), 1.0, 0.01, 0.3)
+    o.V, o.v = V0.copy(), v0.copy()
+    o._lat_initial()
+    g = mdl.Sim(prob)
+    g.set_initial(V0, v0)
+    assert g.dt == o.dt
+    for n in range(4):
+        es = o.disc.eta_s(o.V)
+        g.set_indicators(eta_s=es)
+        newf, plan = o.forest.adapt(es, prob.tau_refine, prob.tau_coarsen)
+        o.transfer(newf, plan)
+        lev = o.assign_levels(o.eta_t)
+        o.eta_t = o.sweep(lev)
+        o.barrier_count += 1
+        g.step_barriers(1)
+        r2, l2, c2, b2 = g.read_mesh()
+        lvo, cco, rto = forest_arrays(o.forest)
+        assert np.array_equal(l2, lvo) and np.array_equal(c2, cco)
+        assert np.array_equal(b2, lev)
+        assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-3
+    assert o.disc.ne > 100000 and len(set(lev.tolist())) >= 3
+    lat_compare(g.read_activation(), o.lat, o.dt / 8)
+    # free-running indicator: the device's own eta^s on the current state
+    es_o = o.disc.eta_s(o.V)
+    g.step_barriers(1)
+    es_g, _ = g.read_indicators()
+    big = es_o > 1e-3 * es_o.max()
+    assert np.abs(es_g[big] - es_o[big]).max() <= 5e-3 * es_o.max()
+    g.close()
