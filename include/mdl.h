@@ -161,7 +161,9 @@ int mdl_read_mesh(mdl_ctx* ctx, int32_t* root, int8_t* level, int32_t* coords, i
  * tangential position bits of e on a coarser neighbour's face (kind 2), else 0. */
 int mdl_read_faces(mdl_ctx* ctx, int8_t* kind, int32_t* nbr, int8_t* pos, int64_t cap, int64_t* n);
 
-/* eta^s of the last barrier's adapt step and eta^t of the last completed barrier. */
+/* eta^s of the last barrier's adapt step (its first n_e_before entries are valid, n_e_before
+ * being the element count before that barrier's adaptation) and eta^t of the last completed
+ * barrier on the current mesh. */
 int mdl_read_indicators(mdl_ctx* ctx, double* eta_s, double* eta_t, int64_t cap, int64_t* n);
 
 /* Counters; timing=1 records CUDA events around every sweep launch (adds a little
@@ -181,6 +183,33 @@ void mdl_destroy(mdl_ctx* ctx);
 
 /* Library build identifier (static string). */
 const char* mdl_version(void);
+
+/* ---- Allocation-free FP64 integral (the paper has no counterpart; a service for callers) ----
+ *
+ * Some callers cannot call cudaMalloc: code that runs while a stream is being captured
+ * into a CUDA graph, a real-time loop that must not allocate, or a host application whose
+ * device memory is fully pre-partitioned by its own allocator.  This entry point computes
+ * the same FP64 integral as the barrier diagnostic (mdl_stats.integral_V),
+ *   out = sum_e sum_q w_q prod_k (h_k(level_e) / 2) V[e (p+1)^d + q],
+ *   h_k(l) = extent[k] / (base[k] 2^l),
+ * of a caller-owned device field without allocating anything: its block partials live in
+ * a file-scope static device array of MDL_NOALLOC_MAX_PARTIALS doubles (32 KiB) that every
+ * GPU which loads the library keeps until the process exits.
+ *   V_dev     device pointer, n_e (p+1)^d values, float (precision 32) or double (64)
+ *   level_dev device pointer, n_e refinement levels (0..7)
+ *   out_dev   device pointer to one double, written on `stream`
+ *   stream    cudaStream_t (NULL = legacy default stream); the call is asynchronous
+ * The first call on a device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture begins.  Every
+ * call shares the one array: calls whose kernels overlap on a GPU race and give wrong
+ * results, so serialise them (one stream, or events).  n_e above MDL_NOALLOC_MAX_ELEMENTS
+ * is rejected with MDL_E_ARG; the message is in mdl_noalloc_last_error(). */
+#define MDL_NOALLOC_MAX_PARTIALS 4096
+#define MDL_NOALLOC_MAX_ELEMENTS ((int64_t)1 << 30)
+int mdl_integral_noalloc(int32_t dim, int32_t order, const double* extent, const int32_t* base,
+                         int32_t precision, const void* V_dev, const int8_t* level_dev, int64_t n_e,
+                         double* out_dev, void* stream);
+const char* mdl_noalloc_last_error(void);
 
 #ifdef __cplusplus
 }

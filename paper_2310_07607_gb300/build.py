@@ -24,6 +24,7 @@ SOURCES = [
     "mdl_inst_3_2.cu",
     "mdl_mesh.cpp",
     "mdl_tables.cpp",
+    "mdl_noalloc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

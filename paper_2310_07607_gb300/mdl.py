@@ -68,7 +68,8 @@ EXPORTS = [
     "mdl_step_to", "mdl_step_barriers", "mdl_get_time", "mdl_get_sizes", "mdl_read_V",
     "mdl_read_state", "mdl_read_activation", "mdl_read_mesh", "mdl_read_faces",
     "mdl_read_indicators", "mdl_get_stats", "mdl_reset_stats", "mdl_set_timing",
-    "mdl_device_view", "mdl_last_error", "mdl_destroy", "mdl_version",
+    "mdl_device_view", "mdl_last_error", "mdl_destroy", "mdl_version", "mdl_integral_noalloc",
+    "mdl_noalloc_last_error",
 ]
 
 _lib = None
@@ -108,8 +109,10 @@ def load(path: Optional[str] = None):
     lib.mdl_destroy.argtypes = [vp]
     lib.mdl_destroy.restype = None
     lib.mdl_version.restype = C.c_char_p
+    lib.mdl_integral_noalloc.argtypes = [C.c_int32, C.c_int32, vp, vp, C.c_int32, vp, vp, i64, vp, vp]
+    lib.mdl_noalloc_last_error.restype = C.c_char_p
     for f in EXPORTS:
-        if f not in ("mdl_last_error", "mdl_destroy", "mdl_version"):
+        if f not in ("mdl_last_error", "mdl_destroy", "mdl_version", "mdl_noalloc_last_error"):
             getattr(lib, f).restype = i32
     if path is None:
         _lib = lib
@@ -290,3 +293,19 @@ class Sim:
         n = C.c_int64()
         self._check(self.lib.mdl_device_view(self.h, which, C.byref(p), C.byref(n), C.byref(st)))
         return p.value, n.value, st.value
+
+
+def integral_noalloc(prob, V_dev: int, level_dev: int, n_e: int, out_dev: int, stream: int = 0, lib=None):
+    """FP64 integral of a device DOF field without device allocation (mdl_integral_noalloc).
+
+    V_dev, level_dev and out_dev are device addresses (e.g. torch tensor data_ptr());
+    the call is asynchronous on `stream`.
+    """
+    lib = lib or load()
+    ext = (C.c_double * 3)(*[float(x) for x in prob.extent])
+    base = (C.c_int32 * 3)(*[int(x) for x in prob.base])
+    rc = lib.mdl_integral_noalloc(prob.dim, prob.order, C.cast(ext, C.c_void_p), C.cast(base, C.c_void_p),
+                                  prob.precision, C.c_void_p(V_dev), C.c_void_p(level_dev), int(n_e),
+                                  C.c_void_p(out_dev), C.c_void_p(stream))
+    if rc != 0:
+        raise MdlError(rc, lib.mdl_noalloc_last_error().decode())
