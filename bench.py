@@ -39,11 +39,17 @@ import workloads as W  # noqa: E402
 METRIC = "DOF-updates/s"
 UNIT = "DOF-updates/s"
 FRONT = dict(origin=(0.0, 0.0, 0.0), radius=1.0, width=0.01, tail=0.3)
+PLANAR = dict(x0=1.0, width=0.012, tail=0.3)
+WORKLOADS = {
+    # name: (problem factory, algorithmic bytes per DOF-update, kernel name)
+    "slab2d": (W.slab_2d_q1_256, 25.0, "k_tick<float,2,1>"),
+    "slab3d": (W.slab_3d_q2, 17.6, "k_tick<float,3,2>"),
+}
 SETUP_BARRIERS = 5
 # Algorithmic bytes per DOF-update of the fused sweep (Q1 2D, FP32, AP): V_old 4 + v 4 +
 # V_new 4 + v 4 = 16 B, plus per element step 2d neighbour ids + 4 B level/flags + the FP64
 # RV-T accumulator read-modify-write (36 B) over (p+1)^d = 4 DOFs.
-ALG_BYTES_PER_DOF_UPDATE = 25.0
+ALG_BYTES_PER_DOF_UPDATE = 25.0   # Q1 2D; Q2 3D: 16 + 44/27 = 17.6 B
 
 
 def load_peaks():
@@ -111,6 +117,12 @@ class ClockSampler:
         return out
 
 
+def workload_name(prob):
+    if prob.dim == 2:
+        return "slab2d_q1_256x256_amr3_lts4_ap_fp32"
+    return "slab3d_q2_128x48x20_amr3_lts4_ap_fp32"
+
+
 def make_sim(prob):
     from paper_2310_07607_gb300 import mdl
     return mdl.Sim(prob)
@@ -144,10 +156,14 @@ def run_ours(args, rank, world):
         dist.init_process_group("nccl")
     from paper_2310_07607_gb300 import build
     build.build()
-    prob = W.slab_2d_q1_256()
+    factory, alg_bytes, kname = WORKLOADS[args.workload]
+    prob = factory()
     sim = make_sim(prob)
     X = node_coords_of(sim, prob)
-    V0, v0 = W.front_state(X, FRONT["origin"], FRONT["radius"], FRONT["width"], FRONT["tail"])
+    if prob.dim == 2:
+        V0, v0 = W.front_state(X, FRONT["origin"], FRONT["radius"], FRONT["width"], FRONT["tail"])
+    else:
+        V0, v0 = W.planar_front_state(X, PLANAR["x0"], PLANAR["width"], PLANAR["tail"])
     sim.set_initial(V0, v0)
     sim.step_barriers(SETUP_BARRIERS)
     sim.step_barriers(args.warmup)
@@ -178,6 +194,8 @@ def run_ours(args, rank, world):
     total_ms = sum(step_ms)
     st = sim.stats()
     n_e, n_dof, _ = sim.sizes()
+    if st["timed_barriers"] != args.steps:
+        raise RuntimeError("sweep timing covers %d of %d barriers" % (st["timed_barriers"], args.steps))
     if dist:
         t = torch.tensor([total_ms, float(st["dof_updates"])], device="cuda", dtype=torch.float64)
         mx = t.clone()
@@ -190,13 +208,13 @@ def run_ours(args, rank, world):
     # roofline of the dominant kernel (the sweep tick kernel), from its own CUDA-event timing
     peak, peak_kind = load_peaks()
     sweep_s = st["sweep_ms"] / 1e3
-    alg_bytes = st["dof_updates"] * ALG_BYTES_PER_DOF_UPDATE
+    alg_bytes = st["dof_updates"] * alg_bytes
     achieved = alg_bytes / sweep_s / 1e9 if sweep_s > 0 else 0.0
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
-            "kernel": "k_tick<float,2,1>", "launches": st["tick_launches"],
+            "kernel": kname, "launches": st["tick_launches"],
             "avg_launch_us": round(st["sweep_ms"] * 1e3 / max(st["tick_launches"], 1), 3),
-            "alg_bytes_per_dof_update": ALG_BYTES_PER_DOF_UPDATE}
+            "alg_bytes_per_dof_update": WORKLOADS[args.workload][1]}
     # end to end through the public API with host buffers: upload state, one barrier, read back
     e2e = run_e2e(sim, args, torch)
     out = None
@@ -205,11 +223,13 @@ def run_ours(args, rank, world):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "slab2d_q1_256x256_amr3_lts4_ap_fp32",
-                       "domain_cm": [2.0, 2.0], "base": [256, 256], "max_refine": 3, "n_lts_levels": 4,
+            "config": {"workload": workload_name(prob),
+                       "domain_cm": list(prob.extent[:prob.dim]), "base": list(prob.base[:prob.dim]),
+                       "max_refine": prob.max_refine, "n_lts_levels": prob.n_lts_levels,
                        "dt_barrier_ms": sim.dt, "n_elements": n_e, "n_dof": n_dof,
                        "level_counts": st["level_counts"][:4],
-                       "initial_state": "synthetic developed front, r=1.0 cm, width 0.01 cm",
+                       "initial_state": ("synthetic developed front, r=1.0 cm, width 0.01 cm" if prob.dim == 2
+                                         else "synthetic planar front at x=1.0 cm, width 0.012 cm"),
                        "l2": "512 MiB flush buffer written between timed steps",
                        "parallelism": "replicas" if world > 1 else "single"},
             "dof_updates_per_step": st["dof_updates"] / args.steps,
@@ -224,7 +244,7 @@ def run_ours(args, rank, world):
             "gpu_launches": st["kernel_launches"],
             "clocks": clocks,
         }
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.workload == "slab2d":
             out["cpu_baseline"] = cpu_baseline(args)
     sim.close()
     if dist:
@@ -344,6 +364,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="slab2d", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

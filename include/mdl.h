@@ -94,6 +94,7 @@ typedef struct mdl_stats {
     int64_t kernel_launches;   /* all kernel launches of the library */
     int64_t amr_rebuilds;      /* barriers whose mesh changed */
     double  sweep_ms;          /* device time of the sweep kernels (CUDA events; 0 unless timing is on) */
+    int64_t timed_barriers;    /* barriers whose sweep time is included in sweep_ms */
     double  indicator_ms;      /* device time of the eta^s kernel (timing on) */
     double  amr_host_ms;       /* host wall time in refine/coarsen bookkeeping */
     double  transfer_ms;       /* host wall time to upload a rebuilt mesh + device transfer */
@@ -166,8 +167,10 @@ int mdl_read_faces(mdl_ctx* ctx, int8_t* kind, int32_t* nbr, int8_t* pos, int64_
  * barrier on the current mesh. */
 int mdl_read_indicators(mdl_ctx* ctx, double* eta_s, double* eta_t, int64_t cap, int64_t* n);
 
-/* Counters; timing=1 records CUDA events around every sweep launch (adds a little
- * host work per launch), 0 turns it off. */
+/* Counters; timing=1 records CUDA events around each barrier's sweep and indicator
+ * kernels (inside the captured barrier graph) and adds their elapsed times to sweep_ms
+ * and indicator_ms -- exactly for calls that step one barrier, for every barrier of a
+ * call otherwise only when graphs are not used; 0 turns it off. */
 int mdl_get_stats(const mdl_ctx* ctx, mdl_stats* out);
 int mdl_reset_stats(mdl_ctx* ctx);
 int mdl_set_timing(mdl_ctx* ctx, int on);

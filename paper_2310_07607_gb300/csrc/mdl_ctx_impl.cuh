@@ -137,6 +137,8 @@ class Ctx : public CtxBase {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int64_t gcap[2] = {-1, -1};
     int64_t glaunch[2] = {0, 0};
+    cudaEvent_t gev[2][4] = {};     // timing events recorded inside each captured graph
+    int greplays[2] = {0, 0};       // replays of each graph since the last synchronisation
     bool use_graphs = true;
 
     static int div_up(int64_t n, int64_t b) { return (int)((n + b - 1) / b); }
@@ -324,19 +326,21 @@ class Ctx : public CtxBase {
         return evpool[ev_used++];
     }
 
-    // Launch one barrier step; no host synchronisation.
-    int launch_barrier() {
+    // Launch one barrier step; no host synchronisation.  `evs` (4 events: sweep start/end,
+    // indicator start/end) are recorded when given, else taken from the pool when timing.
+    int launch_barrier(cudaEvent_t* evs = nullptr) {
         const int g256 = persistent_blocks(256), g128 = persistent_blocks(128);
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
+        const bool rec = timing || evs;
         if (pb.amr_enabled) {
             const int o = cs, n = cs ^ 1;
             Set& so = sets[o];
             Set& sn = sets[n];
             if (!ovr_eta_s) {
-                if (timing && (e2 = next_event())) MDL_CK(cudaEventRecord(e2, st));
+                if (rec && (e2 = evs ? evs[2] : next_event())) MDL_CK(cudaEventRecord(e2, st));
                 k_eta_s<R, DIM, P><<<g128, 128, 0, st>>>(arrays(o), T, ph);
                 MDL_LAUNCHED();
-                if (timing && (e3 = next_event())) MDL_CK(cudaEventRecord(e3, st));
+                if (rec && (e3 = evs ? evs[3] : next_event())) MDL_CK(cudaEventRecord(e3, st));
             }
             k_amr_mark<DIM><<<g256, 256, 0, st>>>(so.coord.p, eta_s.p, r.p, c0.p, meta.p, pb.tau_refine,
                                                   pb.max_refine);
@@ -384,7 +388,7 @@ class Ctx : public CtxBase {
         ta.dt = dt;
         ta.B = B;
         ta.stim = stim;
-        if (timing && (e0 = next_event())) MDL_CK(cudaEventRecord(e0, st));
+        if (rec && (e0 = evs ? evs[0] : next_event())) MDL_CK(cudaEventRecord(e0, st));
         const int nt = 1 << B;
         for (int i = 0; i < nt; ++i) {
             ta.tick = i;
@@ -392,10 +396,10 @@ class Ctx : public CtxBase {
             MDL_LAUNCHED();
             stats.tick_launches++;
         }
-        if (timing && (e1 = next_event())) MDL_CK(cudaEventRecord(e1, st));
+        if (rec && (e1 = evs ? evs[1] : next_event())) MDL_CK(cudaEventRecord(e1, st));
         k_epilogue<R, DIM, P><<<g256, 256, 0, st>>>(arrays(cs), mtab.p, dt);
         MDL_LAUNCHED();
-        if (timing) pending_ev.push_back({e0, e1, e2, e3});
+        if (timing && !evs) pending_ev.push_back({e0, e1, e2, e3});
         return MDL_OK;
     }
 
@@ -411,8 +415,10 @@ class Ctx : public CtxBase {
     // first if needed; direct launches when inputs are replayed or per-barrier timing is on.
     int run_barrier() {
         const bool ovr = ovr_levels || ovr_eta_s || ovr_eta_t;
-        if (!use_graphs || timing || ovr) return launch_barrier();
+        if (!use_graphs || ovr) return launch_barrier();
         const int key = pb.amr_enabled ? cs : 0;
+        if (!gev[key][0])
+            for (int i = 0; i < 4; ++i) MDL_CK(cudaEventCreate(&gev[key][i]));
         if (!gexec[key] || gcap[key] != cap) {
             if (gexec[key]) cudaGraphExecDestroy(gexec[key]);
             gexec[key] = nullptr;
@@ -420,7 +426,7 @@ class Ctx : public CtxBase {
             const int64_t kl0 = stats.kernel_launches, tl0 = stats.tick_launches;
             cudaGraph_t graph;
             MDL_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            int rc = launch_barrier();
+            int rc = launch_barrier(gev[key]);
             cudaError_t ec = cudaStreamEndCapture(st, &graph);
             if (rc) {
                 if (ec == cudaSuccess) cudaGraphDestroy(graph);
@@ -437,6 +443,7 @@ class Ctx : public CtxBase {
             cs = cs0;
         }
         MDL_CK(cudaGraphLaunch(gexec[key], st));
+        greplays[key]++;
         stats.kernel_launches += glaunch[key];
         stats.tick_launches += 1 << B;
         if (pb.amr_enabled) cs ^= 1;
@@ -451,12 +458,27 @@ class Ctx : public CtxBase {
         }
         pending_ev.clear();
         ev_used = 0;
+        // graph events hold the last replay only: counted when a graph replayed once per call
+        for (int k = 0; k < 2; ++k) {
+            if (greplays[k] == 1) {
+                float ms = 0;
+                if (cudaEventElapsedTime(&ms, gev[k][0], gev[k][1]) == cudaSuccess) stats.sweep_ms += ms;
+                if (pb.amr_enabled && cudaEventElapsedTime(&ms, gev[k][2], gev[k][3]) == cudaSuccess)
+                    stats.indicator_ms += ms;
+                stats.timed_barriers++;
+            }
+            greplays[k] = 0;
+        }
+        for (auto& x : pending_ev) (void)x;
     }
 
 public:
     ~Ctx() override {
         if (st) cudaStreamSynchronize(st);
         drop_graphs();
+        for (auto& row : gev)
+            for (auto e : row)
+                if (e) cudaEventDestroy(e);
         for (auto& s : sets) s.release();
         Ia.release(); ga.release(); acc.release(); eta_s.release(); lat.release(); partial.release();
         scratch.release(); r.release(); c0.release(); class_b.release(); owner.release();
@@ -645,7 +667,12 @@ public:
             }
             int rc = sync_meta();
             if (rc) return rc;
-            if (timing) collect_timing();
+            if (timing) {
+                stats.timed_barriers += (int64_t)pending_ev.size();
+                collect_timing();
+            } else {
+                greplays[0] = greplays[1] = 0;
+            }
             done += nbar - start;
             if (nbar > start) ovr_levels = ovr_eta_s = ovr_eta_t = false;   // consumed by a completed barrier
             const unsigned e = hmeta->err;

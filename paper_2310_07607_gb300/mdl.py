@@ -57,7 +57,8 @@ class CStats(C.Structure):
     _fields_ = [
         ("barriers", C.c_int64), ("dof_updates", C.c_int64), ("element_updates", C.c_int64),
         ("tick_launches", C.c_int64), ("kernel_launches", C.c_int64), ("amr_rebuilds", C.c_int64),
-        ("sweep_ms", C.c_double), ("indicator_ms", C.c_double), ("amr_host_ms", C.c_double),
+        ("sweep_ms", C.c_double), ("timed_barriers", C.c_int64), ("indicator_ms", C.c_double),
+        ("amr_host_ms", C.c_double),
         ("transfer_ms", C.c_double), ("integral_V", C.c_double),
         ("n_elements", C.c_int64), ("level_counts", C.c_int64 * 8),
     ]

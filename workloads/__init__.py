@@ -140,7 +140,9 @@ def slab_3d_q2(seed: int = 3) -> Problem:
         precision=32, amr_enabled=1, lts_enabled=1)
 
 
-SLAB3D_TAU = (1.0e-8, 1.0e-9)
+# 3D Q2: the indicator falls ~50-90x per refinement, so tau_coarsen = tau_refine / 1000
+# keeps freshly refined children; tau_refine brings a developed planar front to depth 3.
+SLAB3D_TAU = (1.0e-13, 1.0e-16)
 SLAB3D_T_END = 50.0
 
 
@@ -171,6 +173,15 @@ def front_state(points: np.ndarray, origin, radius: float, width: float,
     r = np.sqrt(((points - o) ** 2).sum(axis=1))
     V = 0.5 * (1.0 - np.tanh((r - radius) / width))
     v = np.clip((radius - r) / max(tail, 1e-30), 0.0, 1.0) * 1.5 if tail > 0 else np.zeros_like(r)
+    return V, v
+
+
+def planar_front_state(points: np.ndarray, x0: float, width: float, tail: float = 0.0):
+    """Synthetic planar front travelling along +x: V = 1 for x < x0 with a tanh edge of
+    ``width``, recovery rising behind it over ``tail``.  Input shaping only."""
+    x = points[:, 0]
+    V = 0.5 * (1.0 - np.tanh((x - x0) / width))
+    v = np.clip((x0 - x) / max(tail, 1e-30), 0.0, 1.0) * 1.5 if tail > 0 else np.zeros_like(x)
     return V, v
 
 
