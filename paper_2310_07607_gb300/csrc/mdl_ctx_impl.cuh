@@ -1,8 +1,10 @@
 // mdl_ctx_impl.cuh -- context implementation for one (precision R, dim, order).
 //
 // A barrier step (Alg. 1) is a fixed sequence of kernel launches on the context's
-// stream; element counts, due counts per tick, the barrier counter and errors live
-// in device memory (DevMeta), so the host never waits inside a barrier:
+// stream, in four phases that are captured once as CUDA graphs and replayed
+// (indicator / adaptation + levels + ordering / sweep / epilogue); element counts, due
+// counts per tick, the barrier counter and errors live in device memory (DevMeta), so
+// the host never waits inside a barrier:
 //   [AMR]  k_eta_s, k_amr_mark, k_amr_close x max_refine, k_amr_family, k_scan_blocks,
 //          k_scan_top (commit), k_scan_emit (coordinates into the other state set),
 //          k_owner_fill + k_mesh_tables + k_lat_refresh (in place, only if the mesh changed),
@@ -133,12 +135,11 @@ class Ctx : public CtxBase {
     };
     std::vector<EvSet> pending_ev;
     mdl_stats stats{};
-    // captured barrier graphs, one per state-set parity (a barrier with adaptation swaps sets)
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    int64_t gcap[2] = {-1, -1};
-    int64_t glaunch[2] = {0, 0};
-    cudaEvent_t gev[2][4] = {};     // timing events recorded inside each captured graph
-    int greplays[2] = {0, 0};       // replays of each graph since the last synchronisation
+    // captured phase graphs, per phase and state set (an adapting barrier swaps sets)
+    cudaGraphExec_t gexec[4][2] = {};
+    int64_t gcap[4][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
+    int64_t glaunch[4][2] = {};
+    int64_t gticks[4][2] = {};
     bool use_graphs = true;
 
     static int div_up(int64_t n, int64_t b) { return (int)((n + b - 1) / b); }
@@ -326,128 +327,149 @@ class Ctx : public CtxBase {
         return evpool[ev_used++];
     }
 
-    // Launch one barrier step; no host synchronisation.  `evs` (4 events: sweep start/end,
-    // indicator start/end) are recorded when given, else taken from the pool when timing.
-    int launch_barrier(cudaEvent_t* evs = nullptr) {
+    // A barrier step is four phases, each launched directly or replayed from a captured graph:
+    //   0 indicator (k_eta_s), 1 adaptation + levels + ordering, 2 sweep ticks, 3 epilogue.
+    // Phase 0 only runs with adaptation and no replayed eta^s.  No host synchronisation.
+    static constexpr int NPHASE = 4;
+
+    int launch_phase(int ph_, int o) {
         const int g256 = persistent_blocks(256), g128 = persistent_blocks(128);
-        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
-        const bool rec = timing || evs;
-        if (pb.amr_enabled) {
-            const int o = cs, n = cs ^ 1;
-            Set& so = sets[o];
-            Set& sn = sets[n];
-            if (!ovr_eta_s) {
-                if (rec && (e2 = evs ? evs[2] : next_event())) MDL_CK(cudaEventRecord(e2, st));
-                k_eta_s<R, DIM, P><<<g128, 128, 0, st>>>(arrays(o), T, ph);
+        if (ph_ == 0) {
+            k_eta_s<R, DIM, P><<<g128, 128, 0, st>>>(arrays(o), T, ph);
+            MDL_LAUNCHED();
+            return MDL_OK;
+        }
+        if (ph_ == 1) {
+            int cur = o;
+            if (pb.amr_enabled) {
+                const int n = o ^ 1;
+                Set& so = sets[o];
+                Set& sn = sets[n];
+                k_amr_mark<DIM><<<g256, 256, 0, st>>>(so.coord.p, eta_s.p, r.p, c0.p, meta.p, pb.tau_refine,
+                                                      pb.max_refine);
                 MDL_LAUNCHED();
-                if (rec && (e3 = evs ? evs[3] : next_event())) MDL_CK(cudaEventRecord(e3, st));
-            }
-            k_amr_mark<DIM><<<g256, 256, 0, st>>>(so.coord.p, eta_s.p, r.p, c0.p, meta.p, pb.tau_refine,
-                                                  pb.max_refine);
-            MDL_LAUNCHED();
-            for (int i = 0; i < pb.max_refine; ++i) {
-                k_amr_close<DIM><<<g256, 256, 0, st>>>(info.p, nbr.p, r.p, meta.p);
+                for (int i = 0; i < pb.max_refine; ++i) {
+                    k_amr_close<DIM><<<g256, 256, 0, st>>>(info.p, nbr.p, r.p, meta.p);
+                    MDL_LAUNCHED();
+                }
+                k_amr_family<DIM><<<g256, 256, 0, st>>>(so.coord.p, info.p, nbr.p, eta_s.p, r.p, c0.p, meta.p,
+                                                        pb.tau_coarsen);
                 MDL_LAUNCHED();
+                const int nsb = div_up(cap, SCAN_CHUNK);
+                k_scan_blocks<DIM><<<nsb, SCAN_THREADS, 0, st>>>(so.coord.p, r.p, c0.p, bsum.p, meta.p);
+                MDL_LAUNCHED();
+                k_scan_top<<<1, 1024, 0, st>>>(bsum.p, meta.p, cap);
+                MDL_LAUNCHED();
+                k_scan_emit<DIM><<<nsb, SCAN_THREADS, 0, st>>>(so.coord.p, r.p, c0.p, bsum.p, sn.coord.p,
+                                                               pkind.p, psrc.p, pbits.p, meta.p);
+                MDL_LAUNCHED();
+                DevArrays<R> od = arrays(o);
+                int rc = build_tables(n, 0);
+                if (rc) return rc;
+                k_transfer<R, DIM, P><<<g128, 128, 0, st>>>(od, arrays(n), pkind.p, psrc.p, pbits.p, T);
+                MDL_LAUNCHED();
+                k_lat_refresh<R, DIM, P><<<g128, 128, 0, st>>>(arrays(n), T, ph, 0.0, 0, 0);
+                MDL_LAUNCHED();
+                cur = n;
             }
-            k_amr_family<DIM><<<g256, 256, 0, st>>>(so.coord.p, info.p, nbr.p, eta_s.p, r.p, c0.p, meta.p,
-                                                    pb.tau_coarsen);
+            int bcell = 0;
+            if (pb.dt_bar_cell > 0) {
+                bcell = b_from_bound(dt, pb.dt_bar_cell);
+                if (bcell < 0) bcell = 15;
+            }
+            const double* et = ovr_eta_t ? eta_t_ovr.p : sets[cur].eta_t.p;
+            const int nob = div_up(cap, ORD_THREADS);
+            k_levels_count<R><<<nob, ORD_THREADS, 0, st>>>(arrays(cur), ovr_levels ? lvl_ovr.p : nullptr, et,
+                                                           pb.tau_cell, bcell, B, pb.lts_enabled, bcnt.p);
             MDL_LAUNCHED();
-            const int nsb = div_up(cap, SCAN_CHUNK);
-            k_scan_blocks<DIM><<<nsb, SCAN_THREADS, 0, st>>>(so.coord.p, r.p, c0.p, bsum.p, meta.p);
+            k_order_top<<<1, 1024, 0, st>>>(bcnt.p, meta.p, B);
             MDL_LAUNCHED();
-            k_scan_top<<<1, 1024, 0, st>>>(bsum.p, meta.p, cap);
+            k_order_scatter<<<nob, ORD_THREADS, 0, st>>>(sets[cur].lvl.p, bcnt.p, order.p, meta.p);
             MDL_LAUNCHED();
-            k_scan_emit<DIM><<<nsb, SCAN_THREADS, 0, st>>>(so.coord.p, r.p, c0.p, bsum.p, sn.coord.p, pkind.p,
-                                                           psrc.p, pbits.p, meta.p);
-            MDL_LAUNCHED();
-            DevArrays<R> od = arrays(o);
-            int rc = build_tables(n, 0);
-            if (rc) return rc;
-            k_transfer<R, DIM, P><<<g128, 128, 0, st>>>(od, arrays(n), pkind.p, psrc.p, pbits.p, T);
-            MDL_LAUNCHED();
-            k_lat_refresh<R, DIM, P><<<g128, 128, 0, st>>>(arrays(n), T, ph, 0.0, 0, 0);
-            MDL_LAUNCHED();
-            cs = n;
+            return MDL_OK;
         }
-        int bcell = 0;
-        if (pb.dt_bar_cell > 0) {
-            bcell = b_from_bound(dt, pb.dt_bar_cell);
-            if (bcell < 0) bcell = 15;
+        if (ph_ == 2) {
+            TickArgs<R> ta{};
+            ta.d = arrays(o);
+            ta.dt = dt;
+            ta.B = B;
+            ta.stim = stim;
+            const int nt = 1 << B;
+            for (int i = 0; i < nt; ++i) {
+                ta.tick = i;
+                k_tick<R, DIM, P><<<g128, 128, 0, st>>>(ta, T, ph);
+                MDL_LAUNCHED();
+                stats.tick_launches++;
+            }
+            return MDL_OK;
         }
-        const double* et = ovr_eta_t ? eta_t_ovr.p : sets[cs].eta_t.p;
-        const int nob = div_up(cap, ORD_THREADS);
-        k_levels_count<R><<<nob, ORD_THREADS, 0, st>>>(arrays(cs), ovr_levels ? lvl_ovr.p : nullptr, et,
-                                                       pb.tau_cell, bcell, B, pb.lts_enabled, bcnt.p);
+        k_epilogue<R, DIM, P><<<g256, 256, 0, st>>>(arrays(o), mtab.p, dt);
         MDL_LAUNCHED();
-        k_order_top<<<1, 1024, 0, st>>>(bcnt.p, meta.p, B);
-        MDL_LAUNCHED();
-        k_order_scatter<<<nob, ORD_THREADS, 0, st>>>(sets[cs].lvl.p, bcnt.p, order.p, meta.p);
-        MDL_LAUNCHED();
-        TickArgs<R> ta{};
-        ta.d = arrays(cs);
-        ta.dt = dt;
-        ta.B = B;
-        ta.stim = stim;
-        if (rec && (e0 = evs ? evs[0] : next_event())) MDL_CK(cudaEventRecord(e0, st));
-        const int nt = 1 << B;
-        for (int i = 0; i < nt; ++i) {
-            ta.tick = i;
-            k_tick<R, DIM, P><<<g128, 128, 0, st>>>(ta, T, ph);
-            MDL_LAUNCHED();
-            stats.tick_launches++;
-        }
-        if (rec && (e1 = evs ? evs[1] : next_event())) MDL_CK(cudaEventRecord(e1, st));
-        k_epilogue<R, DIM, P><<<g256, 256, 0, st>>>(arrays(cs), mtab.p, dt);
-        MDL_LAUNCHED();
-        if (timing && !evs) pending_ev.push_back({e0, e1, e2, e3});
         return MDL_OK;
     }
 
-    void drop_graphs() {
-        for (int i = 0; i < 2; ++i) {
-            if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
-            gexec[i] = nullptr;
-            gcap[i] = -1;
-        }
-    }
-
-    // One barrier: replay the captured graph of the current set parity, capturing it
-    // first if needed; direct launches when inputs are replayed or per-barrier timing is on.
-    int run_barrier() {
-        const bool ovr = ovr_levels || ovr_eta_s || ovr_eta_t;
-        if (!use_graphs || ovr) return launch_barrier();
-        const int key = pb.amr_enabled ? cs : 0;
-        if (!gev[key][0])
-            for (int i = 0; i < 4; ++i) MDL_CK(cudaEventCreate(&gev[key][i]));
-        if (!gexec[key] || gcap[key] != cap) {
-            if (gexec[key]) cudaGraphExecDestroy(gexec[key]);
-            gexec[key] = nullptr;
-            const int cs0 = cs;
+    // Run phase ph_ on set o: replay its captured graph (capturing it first) unless inputs
+    // are replayed this barrier, in which case launch directly.
+    int run_phase(int ph_, int o, bool direct) {
+        if (direct || !use_graphs) return launch_phase(ph_, o);
+        cudaGraphExec_t& ge = gexec[ph_][o];
+        if (!ge || gcap[ph_][o] != cap) {
+            if (ge) cudaGraphExecDestroy(ge);
+            ge = nullptr;
             const int64_t kl0 = stats.kernel_launches, tl0 = stats.tick_launches;
             cudaGraph_t graph;
             MDL_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            int rc = launch_barrier(gev[key]);
+            int rc = launch_phase(ph_, o);
             cudaError_t ec = cudaStreamEndCapture(st, &graph);
             if (rc) {
                 if (ec == cudaSuccess) cudaGraphDestroy(graph);
                 return rc;
             }
             MDL_CK(ec);
-            ec = cudaGraphInstantiate(&gexec[key], graph, 0);
+            ec = cudaGraphInstantiate(&ge, graph, 0);
             cudaGraphDestroy(graph);
             MDL_CK(ec);
-            glaunch[key] = stats.kernel_launches - kl0;
+            glaunch[ph_][o] = stats.kernel_launches - kl0;
+            gticks[ph_][o] = stats.tick_launches - tl0;
             stats.kernel_launches = kl0;
             stats.tick_launches = tl0;
-            gcap[key] = cap;
-            cs = cs0;
+            gcap[ph_][o] = cap;
         }
-        MDL_CK(cudaGraphLaunch(gexec[key], st));
-        greplays[key]++;
-        stats.kernel_launches += glaunch[key];
-        stats.tick_launches += 1 << B;
-        if (pb.amr_enabled) cs ^= 1;
+        MDL_CK(cudaGraphLaunch(ge, st));
+        stats.kernel_launches += glaunch[ph_][o];
+        stats.tick_launches += gticks[ph_][o];
         return MDL_OK;
+    }
+
+    // One barrier step; events around the indicator and the sweep when timing.
+    int run_barrier() {
+        const bool direct = ovr_levels || ovr_eta_s || ovr_eta_t;
+        const int o = cs;
+        int rc;
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
+        if (pb.amr_enabled && !ovr_eta_s) {
+            if (timing && (e2 = next_event())) MDL_CK(cudaEventRecord(e2, st));
+            if ((rc = run_phase(0, o, direct))) return rc;
+            if (timing && (e3 = next_event())) MDL_CK(cudaEventRecord(e3, st));
+        }
+        if ((rc = run_phase(1, o, direct))) return rc;
+        const int cur = pb.amr_enabled ? (o ^ 1) : o;
+        if (timing && (e0 = next_event())) MDL_CK(cudaEventRecord(e0, st));
+        if ((rc = run_phase(2, cur, direct))) return rc;
+        if (timing && (e1 = next_event())) MDL_CK(cudaEventRecord(e1, st));
+        if ((rc = run_phase(3, cur, direct))) return rc;
+        if (timing) pending_ev.push_back({e0, e1, e2, e3});
+        cs = cur;
+        return MDL_OK;
+    }
+
+    void drop_graphs() {
+        for (int p = 0; p < NPHASE; ++p)
+            for (int i = 0; i < 2; ++i) {
+                if (gexec[p][i]) cudaGraphExecDestroy(gexec[p][i]);
+                gexec[p][i] = nullptr;
+                gcap[p][i] = -1;
+            }
     }
 
     void collect_timing() {
@@ -458,27 +480,13 @@ class Ctx : public CtxBase {
         }
         pending_ev.clear();
         ev_used = 0;
-        // graph events hold the last replay only: counted when a graph replayed once per call
-        for (int k = 0; k < 2; ++k) {
-            if (greplays[k] == 1) {
-                float ms = 0;
-                if (cudaEventElapsedTime(&ms, gev[k][0], gev[k][1]) == cudaSuccess) stats.sweep_ms += ms;
-                if (pb.amr_enabled && cudaEventElapsedTime(&ms, gev[k][2], gev[k][3]) == cudaSuccess)
-                    stats.indicator_ms += ms;
-                stats.timed_barriers++;
-            }
-            greplays[k] = 0;
-        }
-        for (auto& x : pending_ev) (void)x;
+        (void)cudaGetLastError();   // a failed elapsed-time query must not leak into later calls
     }
 
 public:
     ~Ctx() override {
         if (st) cudaStreamSynchronize(st);
         drop_graphs();
-        for (auto& row : gev)
-            for (auto e : row)
-                if (e) cudaEventDestroy(e);
         for (auto& s : sets) s.release();
         Ia.release(); ga.release(); acc.release(); eta_s.release(); lat.release(); partial.release();
         scratch.release(); r.release(); c0.release(); class_b.release(); owner.release();
@@ -670,8 +678,6 @@ public:
             if (timing) {
                 stats.timed_barriers += (int64_t)pending_ev.size();
                 collect_timing();
-            } else {
-                greplays[0] = greplays[1] = 0;
             }
             done += nbar - start;
             if (nbar > start) ovr_levels = ovr_eta_s = ovr_eta_t = false;   // consumed by a completed barrier
