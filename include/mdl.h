@@ -187,6 +187,45 @@ void mdl_destroy(mdl_ctx* ctx);
 /* Library build identifier (static string). */
 const char* mdl_version(void);
 
+/* Launch shape of the sweep kernel: threads per block in {64, 128, 256}, resident blocks
+ * per SM with threads * blocks_per_sm <= 2048.  Results do not depend on it. */
+int mdl_set_tick_shape(mdl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
+
+/* ---- Batches: many resident simulations stepped together on one GPU ----
+ * (North-star batching/serving pattern; the paper runs one simulation serially.)
+ * Each slot is a context with its own stream; mdl_batch_step launches every unfinished
+ * slot's barriers before waiting for any, so their kernels overlap on the device.
+ * Admission compares the slot's device-memory footprint estimate (mdl_batch_footprint)
+ * with the budget.  With autotune, a temporary copy of the first instance of each
+ * (precision, dim, order) class is stepped under a few sweep launch shapes and the
+ * fastest shape is used for the class; launch shapes do not change results, so an
+ * instance gives the same values alone and in a mix. */
+#define MDL_SLOT_FREE    0
+#define MDL_SLOT_RUNNING 1
+#define MDL_SLOT_DONE    2
+#define MDL_SLOT_FAILED  3
+typedef struct mdl_batch mdl_batch;
+/* hbm_budget_bytes <= 0: 90% of the current free device memory. */
+int mdl_batch_create(int64_t hbm_budget_bytes, int autotune, mdl_batch** out);
+int mdl_batch_footprint(const mdl_problem* prob, int64_t* bytes);
+/* Create a slot for prob, optionally set its initial state on the base mesh (V0/s0 with
+ * n_dof values, may be NULL), to run until t_end.  MDL_E_NOSPACE if it does not fit. */
+int mdl_batch_admit(mdl_batch* b, const mdl_problem* prob, const double* V0, const double* s0, int64_t n_dof,
+                    double t_end, int32_t* slot);
+/* Advance every running slot by up to barriers_per_slot barriers, repeating rounds until
+ * wall_budget_s seconds have passed (one round if <= 0) or nothing is left to run. */
+int mdl_batch_step(mdl_batch* b, int64_t barriers_per_slot, double wall_budget_s, int64_t* barriers_done);
+/* Slots that finished (reached t_end) or failed since the last poll. */
+int mdl_batch_poll(mdl_batch* b, int32_t* done_slots, int32_t cap, int32_t* n);
+/* The slot's context (for mdl_read_* / mdl_get_*), state (MDL_SLOT_*) and error code. */
+int mdl_batch_slot(mdl_batch* b, int32_t slot, mdl_ctx** ctx, int32_t* state, int32_t* rc);
+int mdl_batch_release(mdl_batch* b, int32_t slot);
+int mdl_batch_usage(const mdl_batch* b, int64_t* used, int64_t* budget, int32_t* resident);
+/* The autotuned sweep shape of prob's class (MDL_E_STATE if not tuned yet). */
+int mdl_batch_shape(const mdl_batch* b, const mdl_problem* prob, int32_t* threads, int32_t* blocks_per_sm);
+const char* mdl_batch_last_error(const mdl_batch* b);
+void mdl_batch_destroy(mdl_batch* b);
+
 /* ---- Allocation-free FP64 integral (the paper has no counterpart; a service for callers) ----
  *
  * Some callers cannot call cudaMalloc: code that runs while a stream is being captured

@@ -25,6 +25,7 @@ SOURCES = [
     "mdl_mesh.cpp",
     "mdl_tables.cpp",
     "mdl_noalloc.cu",
+    "mdl_batch.cpp",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -2,17 +2,13 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 
 #include "../../include/mdl.h"
 #include "mdl_ctx.h"
 #include "mdl_kernels.cuh"
-
-struct mdl_ctx {
-    mdl::CtxBase* impl = nullptr;
-    std::string err;
-};
 
 namespace mdl {
 
@@ -23,7 +19,7 @@ __global__ void k_fill_inf(double* p, int64_t n) {
 
 }  // namespace mdl
 
-namespace {
+namespace mdl {
 
 int check_problem(const mdl_problem* p, std::string* why) {
     if (!p) { *why = "problem is NULL"; return MDL_E_ARG; }
@@ -52,13 +48,47 @@ int check_problem(const mdl_problem* p, std::string* why) {
     return MDL_OK;
 }
 
-mdl::CtxBase* make(const mdl_problem* p) {
+}  // namespace mdl
+
+namespace {
+
+mdl::CtxBase* make(const mdl_problem* p) { return mdl::make_ctx(*p); }
+
+}  // namespace
+
+namespace mdl {
+
+CtxBase* make_ctx(const mdl_problem& pr) {
+    const mdl_problem* p = &pr;
     const bool f64 = p->precision == 64;
     if (p->dim == 2 && p->order == 1) return f64 ? mdl::make_ctx_f64_2_1() : mdl::make_ctx_f32_2_1();
     if (p->dim == 2 && p->order == 2) return f64 ? mdl::make_ctx_f64_2_2() : mdl::make_ctx_f32_2_2();
     if (p->dim == 3 && p->order == 1) return f64 ? mdl::make_ctx_f64_3_1() : mdl::make_ctx_f32_3_1();
     return f64 ? mdl::make_ctx_f64_3_2() : mdl::make_ctx_f32_3_2();
 }
+
+// Device bytes of a freshly created context: per-element arrays at the initial capacity
+// (twice the roots, or four times with adaptation), the finest owner map and the probes.
+int64_t estimate_footprint(const mdl_problem& p) {
+    const int d = p.dim, n1 = p.order + 1;
+    const int64_t np = d == 2 ? n1 * n1 : n1 * n1 * n1;
+    const int64_t nf = 2 * d, nsub = 1 << (d - 1);
+    int64_t roots = 1, fine = 1;
+    for (int k = 0; k < d; ++k) {
+        roots *= p.base[k];
+        fine *= (int64_t)p.base[k] << p.max_refine;
+    }
+    const int64_t cap = std::max<int64_t>(roots * (p.amr_enabled ? 4 : 2), 4096);
+    const int64_t r = p.precision == 64 ? 8 : 4;
+    const int64_t per_set = 3 * np * r + 8 + 1 + 16;
+    const int64_t shared = 2 * np * r + 8 + 8 + 1 + 1 + 8 + 1 + 1 + 4 + 4;
+    const int64_t tables = 1 + 4 + 4 + 4 * nf + 4 * nf * nsub + 4 + 4 + 4 * p.n_stim;
+    return cap * (2 * per_set + shared + tables) + fine * 4 + roots * np * 8 + (1 << 20);
+}
+
+}  // namespace mdl
+
+namespace {
 
 thread_local std::string g_create_err;
 
@@ -89,7 +119,7 @@ int mdl_create(const mdl_problem* prob, mdl_ctx** out) {
     if (!out) return MDL_E_ARG;
     *out = nullptr;
     std::string why;
-    int rc = check_problem(prob, &why);
+    int rc = mdl::check_problem(prob, &why);
     if (rc) {
         g_create_err = why;
         return rc;

@@ -28,9 +28,19 @@ public:
     virtual int reset_stats() = 0;
     virtual int set_timing(int on) = 0;
     virtual int device_view(int which, void** p, int64_t* n, void** stream) = 0;
+    // Asynchronous stepping for batches: launch up to n barriers (no host wait), then
+    // wait, handle capacity growth and errors, and report how many completed.
+    virtual int begin_barriers(int64_t n) = 0;
+    virtual int end_barriers(int64_t* completed) = 0;
+    // Launch shape of the sweep kernel (threads per block, resident blocks per SM); results
+    // do not depend on it.  Returns MDL_E_ARG for unsupported shapes.
+    virtual int set_tick_shape(int threads, int blocks_per_sm) = 0;
+    virtual int64_t device_bytes() const = 0;     // device memory held by the context
+    virtual double dt_barrier() const = 0;
     std::string err;
 };
 
+CtxBase* make_ctx(const mdl_problem& p);
 CtxBase* make_ctx_f32_2_1();
 CtxBase* make_ctx_f64_2_1();
 CtxBase* make_ctx_f32_2_2();
@@ -40,4 +50,14 @@ CtxBase* make_ctx_f64_3_1();
 CtxBase* make_ctx_f32_3_2();
 CtxBase* make_ctx_f64_3_2();
 
+// Footprint estimate (device bytes) of a problem before it is created.
+int64_t estimate_footprint(const mdl_problem& p);
+int check_problem(const mdl_problem* p, std::string* why);
+
 }  // namespace mdl
+
+// The opaque handle behind the C ABI.
+struct mdl_ctx {
+    mdl::CtxBase* impl = nullptr;
+    std::string err;
+};

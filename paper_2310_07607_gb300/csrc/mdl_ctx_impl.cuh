@@ -124,6 +124,7 @@ class Ctx : public CtxBase {
     DBuf<int8_t> pkind, pbits, lvl_ovr;
     DBuf<double> eta_t_ovr;
     DBuf<double> mtab;   // FP64 GL mass w_q det J per (level, node)
+    DBuf<R> qvol, qface, qkelly;   // Q1 class blocks
     DBuf<DevMeta> meta;
     DevMeta* hmeta = nullptr;
     bool ovr_levels = false, ovr_eta_s = false, ovr_eta_t = false;
@@ -141,6 +142,8 @@ class Ctx : public CtxBase {
     int64_t glaunch[4][2] = {};
     int64_t gticks[4][2] = {};
     bool use_graphs = true;
+    int tick_threads = 128, tick_bpsm = 16;   // sweep launch shape
+    int64_t inflight = 0, inflight_start = 0; // barriers launched by begin_barriers
 
     static int div_up(int64_t n, int64_t b) { return (int)((n + b - 1) / b); }
     int persistent_blocks(int threads) const {
@@ -157,6 +160,9 @@ class Ctx : public CtxBase {
         d.order = order.p; d.root = root.p; d.loc = loc.p;
         for (int k = 0; k < MDL_MAX_STIM; ++k) d.smask[k] = smask[k].p;
         d.meta = meta.p;
+        d.qvol = qvol.p;
+        d.qface = qface.p;
+        d.qkelly = qkelly.p;
         return d;
     }
 
@@ -395,9 +401,11 @@ class Ctx : public CtxBase {
             ta.B = B;
             ta.stim = stim;
             const int nt = 1 << B;
+            const int gt = (int)std::min<int64_t>(div_up(std::max<int64_t>(cap, 1), tick_threads),
+                                                  (int64_t)nsm * tick_bpsm);
             for (int i = 0; i < nt; ++i) {
                 ta.tick = i;
-                k_tick<R, DIM, P><<<g128, 128, 0, st>>>(ta, T, ph);
+                k_tick<R, DIM, P><<<gt, tick_threads, 0, st>>>(ta, T, ph);
                 MDL_LAUNCHED();
                 stats.tick_launches++;
             }
@@ -495,6 +503,7 @@ public:
         order.release();
         for (auto& m : smask) m.release();
         lvl_ovr.release(); eta_t_ovr.release(); meta.release(); mtab.release();
+        qvol.release(); qface.release(); qkelly.release();
         if (hmeta) cudaFreeHost(hmeta);
         for (auto e : evpool) cudaEventDestroy(e);
         if (st) cudaStreamDestroy(st);
@@ -570,6 +579,17 @@ public:
                 for (int k = 0; k < DIM; ++k) w *= Td.w[digit<N1>(q, k)];
                 hm[l * NP + q] = w;
             }
+        if (P == 1) {
+            std::vector<double> bv, bf, bk;
+            q1_blocks(Td, phd, DIM, pb.max_refine, &bv, &bf, &bk);
+            std::vector<R> rv(bv.begin(), bv.end()), rf(bf.begin(), bf.end()), rk(bk.begin(), bk.end());
+            MDL_CK(qvol.ensure(rv.size()));
+            MDL_CK(qface.ensure(rf.size()));
+            MDL_CK(qkelly.ensure(rk.size()));
+            MDL_CK(cudaMemcpy(qvol.p, rv.data(), rv.size() * sizeof(R), cudaMemcpyHostToDevice));
+            MDL_CK(cudaMemcpy(qface.p, rf.data(), rf.size() * sizeof(R), cudaMemcpyHostToDevice));
+            MDL_CK(cudaMemcpy(qkelly.p, rk.data(), rk.size() * sizeof(R), cudaMemcpyHostToDevice));
+        }
         MDL_CK(mtab.ensure(hm.size()));
         MDL_CK(cudaMemcpyAsync(mtab.p, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         MDL_CK(class_b.ensure(hcb.size()));
@@ -712,6 +732,93 @@ public:
         stats.barriers = nbar;
         return MDL_OK;
     }
+
+    int begin_barriers(int64_t n) override {
+        if (inflight) {
+            err = "begin_barriers: barriers already in flight";
+            return MDL_E_STATE;
+        }
+        inflight_start = nbar;
+        // replayed inputs apply to exactly one barrier
+        if (ovr_levels || ovr_eta_s || ovr_eta_t) n = std::min<int64_t>(n, 1);
+        for (int64_t i = 0; i < n; ++i) {
+            int rc = run_barrier();
+            if (rc) return rc;
+        }
+        inflight = n;
+        return MDL_OK;
+    }
+
+    int end_barriers(int64_t* completed) override {
+        if (completed) *completed = 0;
+        int rc = sync_meta();
+        if (rc) return rc;
+        inflight = 0;
+        if (timing) {
+            stats.timed_barriers += (int64_t)pending_ev.size();
+            collect_timing();
+        }
+        const int64_t done = nbar - inflight_start;
+        if (completed) *completed = done;
+        if (done > 0) ovr_levels = ovr_eta_s = ovr_eta_t = false;
+        stats.barriers = nbar;
+        const unsigned e = hmeta->err;
+        if (e & ERR_CAPACITY) {
+            rc = grow(hmeta->need);
+            if (rc) return rc;
+            MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
+            MDL_CK(cudaStreamSynchronize(st));
+            hmeta->err = 0;
+            return MDL_OK;   // the barriers after the overflow were skipped; the caller relaunches
+        }
+        if (e & ERR_NONFINITE) {
+            err = "V or the state is not finite";
+            return MDL_E_NONFINITE;
+        }
+        if (e & ERR_CFL) {
+            err = "an element needs more LTS levels than n_lts_levels allows";
+            MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
+            MDL_CK(cudaStreamSynchronize(st));
+            return MDL_E_CFL;
+        }
+        if (e & ERR_MESH) {
+            err = "internal: adapted mesh is not 2:1 balanced";
+            return MDL_E_STATE;
+        }
+        return MDL_OK;
+    }
+
+    int set_tick_shape(int threads, int blocks_per_sm) override {
+        if ((threads != 64 && threads != 128 && threads != 256) || blocks_per_sm < 1 || blocks_per_sm > 32 ||
+            threads * blocks_per_sm > 2048) {
+            err = "set_tick_shape: threads in {64,128,256}, threads * blocks_per_sm <= 2048";
+            return MDL_E_ARG;
+        }
+        if (threads != tick_threads || blocks_per_sm != tick_bpsm) {
+            tick_threads = threads;
+            tick_bpsm = blocks_per_sm;
+            drop_graphs();
+        }
+        return MDL_OK;
+    }
+
+    int64_t device_bytes() const override {
+        int64_t b = 0;
+        auto add = [&](size_t n, size_t sz) { b += (int64_t)(n * sz); };
+        for (const auto& x : sets) {
+            add(x.V0.cap + x.V1.cap + x.v.cap, sizeof(R));
+            add(x.eta_t.cap, 8); add(x.lvl.cap, 1); add(x.coord.cap, sizeof(int4));
+        }
+        add(Ia.cap + ga.cap, sizeof(R));
+        add(acc.cap + eta_s.cap + lat.cap + partial.cap + scratch.cap + eta_t_ovr.cap + mtab.cap, 8);
+        add(r.cap + c0.cap + class_b.cap + bcfl.cap + pkind.cap + pbits.cap + lvl_ovr.cap, 1);
+        add(owner.cap + bcnt.cap + psrc.cap + nbr.cap + hang.cap + root.cap + order.cap + info.cap + loc.cap, 4);
+        for (const auto& m : smask) add(m.cap, 4);
+        add(bsum.cap, 8);
+        return b;
+    }
+
+    double dt_barrier() const override { return dt; }
 
     int step_to(double t_end) override {
         const double nn = floor((t_end - (double)nbar * dt) / dt + 1e-9);

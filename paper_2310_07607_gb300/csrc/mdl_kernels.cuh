@@ -72,7 +72,34 @@ struct DevArrays {
     const uint32_t* loc;
     const uint32_t* smask[MDL_MAX_STIM];
     DevMeta* meta;
+    const R* qvol;      // Q1 class blocks (see q1_blocks): volume, face, Kelly
+    const R* qface;
+    const R* qkelly;
 };
+
+// j[t] += sum_q K[t][q] x[q] for a row-major NT x NP block.
+template <typename R, int NT, int NP>
+__device__ __forceinline__ void block_jump(const R* __restrict__ K, const R* x, R* j) {
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        R acc = j[t];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) acc += __ldg(K + t * NP + q) * x[q];
+        j[t] = acc;
+    }
+}
+
+// r[q] += sum_j A[q][j] x[j] for a row-major NP x NP block in global memory (read-only path).
+template <typename R, int NP>
+__device__ __forceinline__ void block_mv(const R* __restrict__ A, const R* x, R* r) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        R acc = r[q];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc += __ldg(A + q * NP + j) * x[j];
+        r[q] = acc;
+    }
+}
 
 struct StimArgs {
     int n;
@@ -210,26 +237,29 @@ __device__ __forceinline__ void element_residual(const DevArrays<R>& d, const Ta
     R un[NF][NP];
 #pragma unroll
     for (int f = 0; f < NF; ++f) load_seen_lv<R, NP>(d, tick, B, src[f], lvn[f], un[f]);
-    volume_term<R, DIM, P>(T, ph, lev, u, r);
+    // Q1: precomputed class blocks, r = A_vol u + sum_f (A_own u + A_nb u_nb)
+    constexpr int NREL = 1 + 2 * NSUB;
+    block_mv<R, NP>(d.qvol + (size_t)lev * NP * NP, u, r);
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         const int kind = (inf >> (4 * f)) & 3;
-        const int k = f >> 1, s = (f & 1) ? 1 : -1;
         if (kind == 1 || kind == 2) {
-            const int pos = (inf >> (4 * f + 2)) & 3;
-            face_term<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
-                                 kind == 1 ? -1 : pos, un[f], lev, r);
+            const int rel = kind == 1 ? 0 : 1 + ((inf >> (4 * f + 2)) & 3);
+            const R* A = d.qface + ((((size_t)f * 8 + lev) * NREL + rel) * 2) * NP * NP;
+            block_mv<R, NP>(A, u, r);
+            block_mv<R, NP>(A + NP * NP, un[f], r);
         }
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         const int kind = (inf >> (4 * f)) & 3;
         if (kind != 3) continue;
-        const int k = f >> 1, s = (f & 1) ? 1 : -1;
         for (int sb = 0; sb < NSUB; ++sb) {
             R uh[NP];
             load_seen<R, NP>(d, tick, B, d.hang[nbf[f] + sb], uh);
-            face_term<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, uh, lev + 1, r);
+            const R* A = d.qface + ((((size_t)f * 8 + lev) * NREL + 1 + NSUB + sb) * 2) * NP * NP;
+            block_mv<R, NP>(A, u, r);
+            block_mv<R, NP>(A + NP * NP, uh, r);
         }
     }
 }
@@ -280,7 +310,7 @@ struct TickArgs {
 // Euler step on V and one exponential/FE step on v, accumulates the RV-T indicator
 // and checks its probes for activation.
 template <typename R, int DIM, int P>
-__global__ void __launch_bounds__(128) k_tick(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph) {
+__global__ void __launch_bounds__(256) k_tick(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph) {
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
     const DevArrays<R>& d = a.d;
@@ -418,14 +448,22 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
 #pragma unroll
                 for (int q = 0; q < NP; ++q) un[f][q] = srcp[q];
             }
+            constexpr int NT = S::NT, NREL = 1 + 2 * NSUB;
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const int kind = (inf >> (4 * f)) & 3;
                 if (kind != 1 && kind != 2) continue;
-                const int k = f >> 1, s = (f & 1) ? 1 : -1;
-                const int pos = (inf >> (4 * f + 2)) & 3;
-                acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
-                                             kind == 1 ? -1 : pos, un[f], lev);
+                const int rel = kind == 1 ? 0 : 1 + ((inf >> (4 * f + 2)) & 3);
+                const R* K = d.qkelly + ((((size_t)f * 8 + lev) * NREL + rel) * 2) * NT * NP;
+                R j[NT];
+#pragma unroll
+                for (int t = 0; t < NT; ++t) j[t] = R(0);
+                block_jump<R, NT, NP>(K, u, j);
+                block_jump<R, NT, NP>(K + NT * NP, un[f], j);
+                R fsum = R(0);
+#pragma unroll
+                for (int t = 0; t < NT; ++t) fsum += j[t] * j[t];
+                acc += (double)fsum;
             }
         } else {
 #pragma unroll
@@ -456,7 +494,21 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
                 R un[NP];
 #pragma unroll
                 for (int q = 0; q < NP; ++q) un[q] = src[q];
-                acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
+                if constexpr (P == 1) {
+                    constexpr int NT = S::NT, NREL = 1 + 2 * NSUB;
+                    const R* K = d.qkelly + ((((size_t)f * 8 + lev) * NREL + 1 + NSUB + sb) * 2) * NT * NP;
+                    R j[NT];
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) j[t] = R(0);
+                    block_jump<R, NT, NP>(K, u, j);
+                    block_jump<R, NT, NP>(K + NT * NP, un, j);
+                    R fsum = R(0);
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) fsum += j[t] * j[t];
+                    acc += (double)fsum;
+                } else {
+                    acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
+                }
             }
         }
         d.eta_s[e] = sqrt(acc);

@@ -256,6 +256,78 @@ double class_cfl(const Tables<double>& T, const Phys<double>& ph, int dim, int p
     return class_cfl_from_blocks(T, ph, dim, p, level, cfg, vol, face);
 }
 
+namespace {
+
+template <int DIM>
+void q1_blocks_t(const Tables<double>& T, const Phys<double>& ph, int L, std::vector<double>* vol,
+                 std::vector<double>* face, std::vector<double>* kelly) {
+    using S = Shape<DIM, 1>;
+    constexpr int NP = S::NP, NF = S::NF, NSUB = S::NSUB, NT = S::NT;
+    constexpr int NREL = 1 + 2 * NSUB;
+    vol->assign((size_t)8 * NP * NP, 0.0);
+    face->assign((size_t)NF * 8 * NREL * 2 * NP * NP, 0.0);
+    kelly->assign((size_t)NF * 8 * NREL * 2 * NT * NP, 0.0);
+    double zero[NP] = {0};
+    for (int l = 0; l < 8; ++l) {
+        for (int j = 0; j < NP; ++j) {
+            double u[NP] = {0}, r[NP] = {0};
+            u[j] = 1.0;
+            volume_term<double, DIM, 1>(T, ph, l, u, r);
+            for (int q = 0; q < NP; ++q) (*vol)[((size_t)l * NP + q) * NP + j] = r[q];
+        }
+        for (int f = 0; f < NF; ++f) {
+            const int k = f / 2, s = (f & 1) ? 1 : -1;
+            for (int rel = 0; rel < NREL; ++rel) {
+                int lo = l, ln, lf, cb_own, cb_nb;
+                if (rel == 0) {
+                    ln = l; lf = l; cb_own = -1; cb_nb = -1;
+                } else if (rel <= NSUB) {
+                    if (l == 0) continue;
+                    ln = l - 1; lf = l; cb_own = -1; cb_nb = rel - 1;
+                } else {
+                    if (l >= 7) continue;
+                    ln = l + 1; lf = l + 1; cb_own = rel - 1 - NSUB; cb_nb = -1;
+                }
+                const size_t fb = (((size_t)f * 8 + l) * NREL + rel) * 2;
+                for (int side = 0; side < 2; ++side)
+                    for (int j = 0; j < NP; ++j) {
+                        double e[NP] = {0}, r[NP] = {0};
+                        e[j] = 1.0;
+                        const double* own = side == 0 ? e : zero;
+                        const double* nb = side == 0 ? zero : e;
+                        face_term<double, DIM, 1>(T, ph, k, s, lo, cb_own, own, ln, cb_nb, nb, lf, r);
+                        for (int q = 0; q < NP; ++q) (*face)[((fb + side) * NP + q) * NP + j] = r[q];
+                        // Kelly: flux jump at the face points, scaled by sqrt(h_F/(2p) W_t) W_F
+                        double vo[NT], vn[NT], go[DIM][NT], gn[DIM][NT], W[NT];
+                        face_eval<double, DIM, 1>(T, ph.h2[lo], k, s, cb_own, own, vo, go);
+                        face_eval<double, DIM, 1>(T, ph.h2[ln], k, -s, cb_nb, nb, vn, gn);
+                        face_weights<double, DIM, 1>(T, ph, lf, k, W);
+                        const double WF = ph.Wface[lf][k];
+                        const double area = WF * (double)(1 << (DIM - 1));
+                        const double hF = (DIM == 2) ? area : sqrt(area);
+                        for (int t = 0; t < NT; ++t) {
+                            double fo = 0, fn = 0;
+                            for (int m = 0; m < DIM; ++m) {
+                                fo += ph.D[k][m] * go[m][t];
+                                fn += ph.D[k][m] * gn[m][t];
+                            }
+                            const double c = sqrt(hF / 2.0 * W[t]) * WF;
+                            (*kelly)[((fb + side) * NT + t) * NP + j] = c * (fo - fn);
+                        }
+                    }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void q1_blocks(const Tables<double>& T, const Phys<double>& ph, int dim, int L, std::vector<double>* vol,
+               std::vector<double>* face, std::vector<double>* kelly) {
+    if (dim == 2) q1_blocks_t<2>(T, ph, L, vol, face, kelly);
+    else q1_blocks_t<3>(T, ph, L, vol, face, kelly);
+}
+
 int b_from_bound(double dt, double bound) {
     for (int b = 0; b <= 60; ++b)
         if (ldexp(dt, -b) <= bound) return b;

@@ -34,6 +34,16 @@ double class_cfl_from_blocks(const Tables<double>& T, const Phys<double>& ph, in
 // Smallest b >= 0 with dt 2^-b <= bound; -1 if none below 60.
 int b_from_bound(double dt, double bound);
 
+// Q1 class blocks.  Every Q1 face contribution to an element's residual is the linear
+// map r += A_own u + A_nb u_nb; it depends only on (face f, own level l, relation rel),
+// rel = 0 same level, 1 + pos coarser neighbour (pos = tangential position bits),
+// 1 + 2^(d-1) + sub finer neighbour on subface sub.  Tables (row-major NP x NP blocks):
+//   vol [8][NP][NP], face [NF][8][NREL][2][NP][NP] (0 own, 1 neighbour),
+//   kelly [NF][8][NREL][2][NT][NP]: sqrt(c_t) times the flux jump at face point t, so
+//   that a face's Kelly contribution is sum_t (K_own u + K_nb u_nb)_t^2.
+void q1_blocks(const Tables<double>& T, const Phys<double>& ph, int dim, int L, std::vector<double>* vol,
+               std::vector<double>* face, std::vector<double>* kelly);
+
 // Largest 2^-k with 2^-k 2^-B <= min over all admissible classes (levels 0..L).
 double auto_dt_barrier(const Tables<double>& T, const Phys<double>& ph, int dim, int p, int L, int B);
 

@@ -70,8 +70,12 @@ EXPORTS = [
     "mdl_read_state", "mdl_read_activation", "mdl_read_mesh", "mdl_read_faces",
     "mdl_read_indicators", "mdl_get_stats", "mdl_reset_stats", "mdl_set_timing",
     "mdl_device_view", "mdl_last_error", "mdl_destroy", "mdl_version", "mdl_integral_noalloc",
-    "mdl_noalloc_last_error",
+    "mdl_noalloc_last_error", "mdl_set_tick_shape", "mdl_batch_create", "mdl_batch_footprint",
+    "mdl_batch_admit", "mdl_batch_step", "mdl_batch_poll", "mdl_batch_slot", "mdl_batch_release",
+    "mdl_batch_usage", "mdl_batch_shape", "mdl_batch_last_error", "mdl_batch_destroy",
 ]
+
+SLOT_FREE, SLOT_RUNNING, SLOT_DONE, SLOT_FAILED = 0, 1, 2, 3
 
 _lib = None
 
@@ -112,8 +116,24 @@ def load(path: Optional[str] = None):
     lib.mdl_version.restype = C.c_char_p
     lib.mdl_integral_noalloc.argtypes = [C.c_int32, C.c_int32, vp, vp, C.c_int32, vp, vp, i64, vp, vp]
     lib.mdl_noalloc_last_error.restype = C.c_char_p
+    i32p = C.POINTER(C.c_int32)
+    lib.mdl_set_tick_shape.argtypes = [vp, C.c_int32, C.c_int32]
+    lib.mdl_batch_create.argtypes = [i64, i32, C.POINTER(vp)]
+    lib.mdl_batch_footprint.argtypes = [C.POINTER(CProblem), C.POINTER(i64)]
+    lib.mdl_batch_admit.argtypes = [vp, C.POINTER(CProblem), vp, vp, i64, C.c_double, i32p]
+    lib.mdl_batch_step.argtypes = [vp, i64, C.c_double, C.POINTER(i64)]
+    lib.mdl_batch_poll.argtypes = [vp, i32p, C.c_int32, i32p]
+    lib.mdl_batch_slot.argtypes = [vp, C.c_int32, C.POINTER(vp), i32p, i32p]
+    lib.mdl_batch_release.argtypes = [vp, C.c_int32]
+    lib.mdl_batch_usage.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), i32p]
+    lib.mdl_batch_shape.argtypes = [vp, C.POINTER(CProblem), i32p, i32p]
+    lib.mdl_batch_last_error.argtypes = [vp]
+    lib.mdl_batch_last_error.restype = C.c_char_p
+    lib.mdl_batch_destroy.argtypes = [vp]
+    lib.mdl_batch_destroy.restype = None
     for f in EXPORTS:
-        if f not in ("mdl_last_error", "mdl_destroy", "mdl_version", "mdl_noalloc_last_error"):
+        if f not in ("mdl_last_error", "mdl_destroy", "mdl_version", "mdl_noalloc_last_error",
+                     "mdl_batch_last_error", "mdl_batch_destroy"):
             getattr(lib, f).restype = i32
     if path is None:
         _lib = lib
@@ -161,10 +181,14 @@ def _ptr(a: np.ndarray):
 class Sim:
     """One simulation context (mdl_ctx) on the current CUDA device."""
 
-    def __init__(self, prob, lib=None):
+    def __init__(self, prob, lib=None, handle=None):
         self.lib = lib or load()
         self.prob = prob
         self._c = to_c(prob)
+        self._owned = handle is None
+        if handle is not None:      # a context owned by a batch slot
+            self.h = C.c_void_p(handle)
+            return
         h = C.c_void_p()
         rc = self.lib.mdl_create(C.byref(self._c), C.byref(h))
         if rc != 0:
@@ -177,9 +201,12 @@ class Sim:
             raise MdlError(rc, self.lib.mdl_last_error(self.h).decode())
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", True):
             self.lib.mdl_destroy(self.h)
-            self.h = None
+        self.h = None
+
+    def set_tick_shape(self, threads: int, blocks_per_sm: int):
+        self._check(self.lib.mdl_set_tick_shape(self.h, threads, blocks_per_sm))
 
     def __del__(self):
         try:
@@ -310,3 +337,83 @@ def integral_noalloc(prob, V_dev: int, level_dev: int, n_e: int, out_dev: int, s
                                   C.c_void_p(out_dev), C.c_void_p(stream))
     if rc != 0:
         raise MdlError(rc, lib.mdl_noalloc_last_error().decode())
+
+
+class Batch:
+    """Resident simulations stepped together (mdl_batch_*)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, autotune: bool = True, lib=None):
+        self.lib = lib or load()
+        h = C.c_void_p()
+        rc = self.lib.mdl_batch_create(int(hbm_budget_bytes), 1 if autotune else 0, C.byref(h))
+        if rc != 0:
+            raise MdlError(rc, self.lib.mdl_batch_last_error(None).decode())
+        self.h = h
+        self.problems = {}
+
+    def _check(self, rc):
+        if rc != 0:
+            raise MdlError(rc, self.lib.mdl_batch_last_error(self.h).decode())
+
+    def footprint(self, prob) -> int:
+        c = to_c(prob)
+        b = C.c_int64()
+        self._check(self.lib.mdl_batch_footprint(C.byref(c), C.byref(b)))
+        return b.value
+
+    def admit(self, prob, t_end: float, V0=None, s0=None) -> int:
+        """Admit a simulation; raises MdlError with code -3 (MDL_E_NOSPACE) when it does not fit."""
+        c = to_c(prob)
+        Va = None if V0 is None else np.ascontiguousarray(V0, dtype=np.float64)
+        sa = None if s0 is None else np.ascontiguousarray(s0, dtype=np.float64)
+        slot = C.c_int32()
+        n = 0 if Va is None else Va.size
+        self._check(self.lib.mdl_batch_admit(self.h, C.byref(c), _ptr(Va), _ptr(sa), n, float(t_end),
+                                             C.byref(slot)))
+        self.problems[slot.value] = prob
+        return slot.value
+
+    def step(self, barriers_per_slot: int = 1, wall_budget_s: float = 0.0) -> int:
+        done = C.c_int64()
+        self._check(self.lib.mdl_batch_step(self.h, int(barriers_per_slot), float(wall_budget_s), C.byref(done)))
+        return done.value
+
+    def poll(self, cap: int = 4096):
+        out = (C.c_int32 * cap)()
+        n = C.c_int32()
+        self._check(self.lib.mdl_batch_poll(self.h, out, cap, C.byref(n)))
+        return [out[i] for i in range(n.value)]
+
+    def slot(self, slot: int):
+        """(Sim view of the slot's context, state, error code)."""
+        ctx = C.c_void_p()
+        st, rc = C.c_int32(), C.c_int32()
+        self._check(self.lib.mdl_batch_slot(self.h, slot, C.byref(ctx), C.byref(st), C.byref(rc)))
+        return Sim(self.problems[slot], lib=self.lib, handle=ctx.value), st.value, rc.value
+
+    def release(self, slot: int):
+        self._check(self.lib.mdl_batch_release(self.h, slot))
+        self.problems.pop(slot, None)
+
+    def usage(self):
+        u, b = C.c_int64(), C.c_int64()
+        r = C.c_int32()
+        self._check(self.lib.mdl_batch_usage(self.h, C.byref(u), C.byref(b), C.byref(r)))
+        return u.value, b.value, r.value
+
+    def shape(self, prob):
+        c = to_c(prob)
+        t, k = C.c_int32(), C.c_int32()
+        self._check(self.lib.mdl_batch_shape(self.h, C.byref(c), C.byref(t), C.byref(k)))
+        return t.value, k.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mdl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,116 @@
+"""Batches of resident simulations (mdl_batch_*): same results alone and in a mix,
+admission by device-memory footprint, completion polling and slot release."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.helpers import forest_arrays, random_forest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mdl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2310_07607_gb300 import build, mdl as M
+    build.build()
+    return M
+
+
+def instance(dim, p, seed, precision=32, amr=1):
+    ext = (0.4, 0.3, 0.2)
+    return W.Problem(dim=dim, order=p, extent=ext, base=(4, 3, 2), sigma_l=1.2, sigma_t=0.4,
+                     fibre=(0.6, 0.8, 0.0) if dim == 2 else (0.48, 0.64, 0.6), gamma=10.0 * p * p,
+                     max_refine=2, n_lts_levels=3, lts_enabled=1, amr_enabled=amr,
+                     tau_refine=2e-9 if dim == 2 else 1e-11, tau_coarsen=2e-10 if dim == 2 else 1e-14,
+                     dt_barrier=0.0, state_integrator=W.STATE_EXP, precision=precision,
+                     stimuli=[W.Stimulus((0, 0, 0), (0.05 + 0.02 * seed, 0.1, 0.1), 1.0, 0.0, 1.0)])
+
+
+def initial(mdl, prob):
+    g = mdl.Sim(prob)
+    root, level, coords, _ = g.read_mesh()
+    g.close()
+    n1 = prob.order + 1
+    xi = np.polynomial.legendre.leggauss(n1)[0]
+    d = prob.dim
+    q = np.arange(n1 ** d)
+    X = np.empty((len(level), n1 ** d, d))
+    for k in range(d):
+        h = prob.extent[k] / (prob.base[k] * 2.0 ** level)
+        X[:, :, k] = coords[:, k:k + 1] * h[:, None] + (xi[(q // n1 ** k) % n1][None, :] + 1) * 0.5 * h[:, None]
+    return W.front_state(X.reshape(-1, d), (0, 0, 0), 0.12, 0.02, tail=0.05)
+
+
+def test_alone_equals_in_mix_bitwise(mdl):
+    probs = [instance(2, 1, 0), instance(3, 1, 1), instance(3, 2, 2), instance(2, 1, 3, precision=64),
+             instance(2, 2, 4, amr=0)]
+    nbar = 6
+    alone = []
+    for p in probs:
+        V0, v0 = initial(mdl, p)
+        g = mdl.Sim(p)
+        g.set_initial(V0, v0)
+        g.step_barriers(nbar)
+        alone.append((g.read_V(), g.read_state(), g.read_activation(), g.read_mesh()[1]))
+        g.close()
+    b = mdl.Batch(autotune=True)
+    slots = []
+    for p in probs:
+        V0, v0 = initial(mdl, p)
+        dt = mdl.Sim(p).dt
+        slots.append(b.admit(p, nbar * dt, V0, v0))
+    # uneven stepping: rounds of 2 barriers until every slot has reached its end time
+    while True:
+        done = b.step(barriers_per_slot=2)
+        if done == 0:
+            break
+    finished = sorted(b.poll())
+    assert finished == sorted(slots)
+    for s, (Va, va, la, lva) in zip(slots, alone):
+        g, state, rc = b.slot(s)
+        assert state == mdl.SLOT_DONE and rc == 0
+        assert g.time()[1] == nbar
+        assert np.array_equal(g.read_mesh()[1], lva)
+        assert np.array_equal(g.read_V(), Va)
+        assert np.array_equal(g.read_state(), va)
+        assert np.array_equal(g.read_activation(), la)
+    # every class got a tuned launch shape
+    for p in probs:
+        t, k = b.shape(p)
+        assert t in (64, 128, 256) and 1 <= k <= 32
+    for s in slots:
+        b.release(s)
+    assert b.usage()[2] == 0
+    b.close()
+
+
+def test_admission_by_footprint_and_release(mdl):
+    p = instance(2, 1, 0)
+    fp = mdl.Batch(autotune=False).footprint(p)
+    assert fp > 0
+    b = mdl.Batch(hbm_budget_bytes=int(fp * 1.5), autotune=False)
+    s0 = b.admit(p, 0.001)
+    with pytest.raises(mdl.MdlError) as ei:
+        b.admit(p, 0.001)
+    assert ei.value.code == -3
+    b.release(s0)
+    s1 = b.admit(p, 0.001)
+    assert s1 == s0
+    b.close()
+
+
+def test_slot_finishes_at_its_own_end_time(mdl):
+    b = mdl.Batch(autotune=False)
+    p = instance(2, 1, 0)
+    dt = mdl.Sim(p).dt
+    a = b.admit(p, 3 * dt)
+    c = b.admit(p, 7 * dt)
+    b.step(barriers_per_slot=4)
+    assert b.poll() == [a]
+    b.step(barriers_per_slot=4)
+    assert b.poll() == [c]
+    assert b.slot(a)[0].time()[1] == 3 and b.slot(c)[0].time()[1] == 7
+    b.close()
