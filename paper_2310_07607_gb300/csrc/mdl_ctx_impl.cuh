@@ -143,6 +143,7 @@ class Ctx : public CtxBase {
     int64_t gticks[4][2] = {};
     bool use_graphs = true;
     int tick_threads = 128, tick_bpsm = 16;   // sweep launch shape
+    bool coop_sweep = true;                   // ticks + epilogue in one cooperative launch
     int64_t inflight = 0, inflight_start = 0; // barriers launched by begin_barriers
 
     static int div_up(int64_t n, int64_t b) { return (int)((n + b - 1) / b); }
@@ -401,6 +402,25 @@ class Ctx : public CtxBase {
             ta.B = B;
             ta.stim = stim;
             const int nt = 1 << B;
+            if (coop_sweep) {
+                // all ticks + epilogue in one cooperative launch (every block resident)
+                int occ = 0;
+                MDL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep<R, DIM, P>, tick_threads, 0));
+                const int per_sm = std::max(1, std::min(occ, tick_bpsm));
+                cudaLaunchConfig_t cfg{};
+                cfg.gridDim = dim3((unsigned)(nsm * per_sm));
+                cfg.blockDim = dim3((unsigned)tick_threads);
+                cfg.stream = st;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeCooperative;
+                attr[0].val.cooperative = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                MDL_CK(cudaLaunchKernelEx(&cfg, k_sweep<R, DIM, P>, ta, T, ph, (const double*)mtab.p));
+                MDL_LAUNCHED();
+                stats.tick_launches += nt;
+                return MDL_OK;
+            }
             const int gt = (int)std::min<int64_t>(div_up(std::max<int64_t>(cap, 1), tick_threads),
                                                   (int64_t)nsm * tick_bpsm);
             for (int i = 0; i < nt; ++i) {
@@ -465,7 +485,7 @@ class Ctx : public CtxBase {
         if (timing && (e0 = next_event())) MDL_CK(cudaEventRecord(e0, st));
         if ((rc = run_phase(2, cur, direct))) return rc;
         if (timing && (e1 = next_event())) MDL_CK(cudaEventRecord(e1, st));
-        if ((rc = run_phase(3, cur, direct))) return rc;
+        if (!coop_sweep && (rc = run_phase(3, cur, direct))) return rc;
         if (timing) pending_ev.push_back({e0, e1, e2, e3});
         cs = cur;
         return MDL_OK;

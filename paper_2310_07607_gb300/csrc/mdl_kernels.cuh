@@ -16,6 +16,7 @@
 //   lat     [n_probe]  FP64 activation time per probe (+INF pending)
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "../../include/mdl.h"
@@ -310,19 +311,18 @@ struct TickArgs {
 // Euler step on V and one exponential/FE step on v, accumulates the RV-T indicator
 // and checks its probes for activation.
 template <typename R, int DIM, int P>
-__global__ void __launch_bounds__(256) k_tick(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph) {
+__device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>& T, const Phys<R>& ph, int tick) {
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
     const DevArrays<R>& d = a.d;
-    if (d.meta->err) return;
-    const int n_act = d.meta->nact[a.tick];
+    const int n_act = d.meta->nact[tick];
     const double nt = (double)(1 << a.B);
-    const double t_i = ((double)d.meta->nbar * nt + (double)a.tick) * a.dt / nt;
+    const double t_i = ((double)d.meta->nbar * nt + (double)tick) * a.dt / nt;
     for (int idx = (int)gtid(); idx < n_act; idx += (int)gstride()) {
     const int e = d.order[idx];
     const uint8_t lv = d.lvl[e];
     const int b = lv & 7, par = (lv >> 3) & 1;
-    const int ke = a.tick >> (a.B - b);
+    const int ke = tick >> (a.B - b);
     const int cur = par ^ (ke & 1);
     const R* Vc = (cur ? d.V1 : d.V0) + (size_t)e * NP;
     R* Vd = (cur ? d.V0 : d.V1) + (size_t)e * NP;
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(256) k_tick(const TickArgs<R> a, const Tables<
     }
     const uint32_t inf = d.info[e];
     const int lev = (inf >> 24) & 15;
-    element_residual<R, DIM, P>(d, T, ph, a.tick, a.B, e, inf, lev, u, r);
+    element_residual<R, DIM, P>(d, T, ph, tick, a.B, e, inf, lev, u, r);
 
     const double dte_d = ldexp(a.dt, -b);
     const R dte = (R)dte_d;
@@ -409,6 +409,12 @@ __global__ void __launch_bounds__(256) k_tick(const TickArgs<R> a, const Tables<
     if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
         lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, t_i, dte_d);
     }
+}
+
+template <typename R, int DIM, int P>
+__global__ void __launch_bounds__(256) k_tick(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph) {
+    if (a.d.meta->err) return;
+    tick_work<R, DIM, P>(a, T, ph, a.tick);
 }
 
 // Kelly-type spatial indicator per element (Eq. dg-error-estimate) on the barrier-start
@@ -584,6 +590,75 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const do
 }
 
 
+
+// The whole sweep of a barrier in one cooperative launch: every tick of Alg. 1 with a
+// grid-wide barrier between ticks (the Jacobi reading needs all of tick i before tick
+// i+1), then the epilogue with a fixed-order final reduction by block 0.  The grid is
+// sized from the occupancy API so that every block is resident.
+template <typename R, int DIM, int P>
+__global__ void __launch_bounds__(256) k_sweep(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph,
+                                              const double* __restrict__ mtab) {
+    using S = Shape<DIM, P>;
+    constexpr int NP = S::NP;
+    const DevArrays<R>& d = a.d;
+    if (d.meta->err) return;             // uniform: nothing below changes err before the end
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    const int nt = 1 << a.B;
+    for (int i = 0; i < nt; ++i) {
+        tick_work<R, DIM, P>(a, T, ph, i);
+        grid.sync();
+    }
+    __shared__ double red[256];
+    const int64_t ne = d.meta->ne;
+    double loc = 0.0;
+    bool bad = false;
+    for (int64_t e = gtid(); e < ne; e += gstride()) {
+        d.eta_t[e] = sqrt(d.acc[e]) / a.dt;
+        uint8_t lv = d.lvl[e];
+        if ((lv & 7) == 0) {
+            lv ^= 8;
+            d.lvl[e] = lv;
+        }
+        const int par = (lv >> 3) & 1;
+        const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
+        const R* w = d.v + (size_t)e * NP;
+        const int lev = (d.info[e] >> 24) & 15;
+        const double* Mq = mtab + lev * NP;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const R x = Vc[q];
+            loc += Mq[q] * (double)x;
+            bad = bad || !isfinite(x) || !isfinite(w[q]);
+        }
+    }
+    if (bad) atomicOr(&d.meta->nf_pending, 1u);
+    red[threadIdx.x] = loc;
+    __syncthreads();
+    for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+        if (threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) d.partial[blockIdx.x] = red[0];
+    grid.sync();
+    if (blockIdx.x != 0) return;
+    double s3 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s3 += d.partial[i];
+    red[threadIdx.x] = s3;
+    __syncthreads();
+    for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+        if (threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        DevMeta* m = d.meta;
+        m->integral = red[0];
+        m->nbar += 1;
+        if (m->nf_pending) {
+            m->err |= ERR_NONFINITE;
+            m->nf_pending = 0;
+        }
+    }
+}
 
 // Copy V (current slot by parity) or v to an FP64 output.
 template <typename R, int NP>
