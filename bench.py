@@ -42,8 +42,8 @@ FRONT = dict(origin=(0.0, 0.0, 0.0), radius=1.0, width=0.01, tail=0.3)
 PLANAR = dict(x0=1.0, width=0.012, tail=0.3)
 WORKLOADS = {
     # name: (problem factory, algorithmic bytes per DOF-update, kernel name)
-    "slab2d": (W.slab_2d_q1_256, 25.0, "k_tick<float,2,1>"),
-    "slab3d": (W.slab_3d_q2, 17.6, "k_tick<float,3,2>"),
+    "slab2d": (W.slab_2d_q1_256, 25.0, "<float,2,1>"),
+    "slab3d": (W.slab_3d_q2, 17.6, "<float,3,2>"),
 }
 SETUP_BARRIERS = 5
 # Algorithmic bytes per DOF-update of the fused sweep (Q1 2D, FP32, AP): V_old 4 + v 4 +
@@ -117,6 +117,13 @@ class ClockSampler:
         return out
 
 
+SWEEPS = {"thread": 0, "group": 1, "coop": 2}
+
+
+def prob_order(factory):
+    return factory().order
+
+
 def workload_name(prob):
     if prob.dim == 2:
         return "slab2d_q1_256x256_amr3_lts4_ap_fp32"
@@ -157,8 +164,13 @@ def run_ours(args, rank, world):
     from paper_2310_07607_gb300 import build
     build.build()
     factory, alg_bytes, kname = WORKLOADS[args.workload]
+    if args.sweep == "group" and prob_order(factory) == 1:
+        kname = "k_tick_group" + kname.replace(",1>", ">")
+    else:
+        kname = ("k_sweep" if args.sweep == "coop" else "k_tick") + kname
     prob = factory()
     sim = make_sim(prob)
+    sim.set_sweep_variant(SWEEPS[args.sweep])
     X = node_coords_of(sim, prob)
     if prob.dim == 2:
         V0, v0 = W.front_state(X, FRONT["origin"], FRONT["radius"], FRONT["width"], FRONT["tail"])
@@ -223,7 +235,7 @@ def run_ours(args, rank, world):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(prob),
+            "config": {"workload": workload_name(prob), "sweep": args.sweep,
                        "domain_cm": list(prob.extent[:prob.dim]), "base": list(prob.base[:prob.dim]),
                        "max_refine": prob.max_refine, "n_lts_levels": prob.n_lts_levels,
                        "dt_barrier_ms": sim.dt, "n_elements": n_e, "n_dof": n_dof,
@@ -365,6 +377,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="slab2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--sweep", default="thread", choices=sorted(SWEEPS),
+                    help="sweep kernel variant (thread per element; group: Q1 lanes per element; "
+                         "coop: one cooperative launch per barrier)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

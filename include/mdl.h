@@ -191,6 +191,19 @@ const char* mdl_version(void);
  * per SM with threads * blocks_per_sm <= 2048.  Results do not depend on it. */
 int mdl_set_tick_shape(mdl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
 
+/* Sweep kernel variant.  All follow Alg. 1 tick by tick; THREAD and COOP give identical
+ * values, GROUP sums the face terms in another order (agreement within rounding):
+ *   MDL_SWEEP_THREAD  one thread per due element, one launch per tick; the default;
+ *   MDL_SWEEP_GROUP   Q1 only: (p+1)^d lanes per element, one lane per face and per DOF,
+ *                     one launch per tick (Q2 contexts use MDL_SWEEP_THREAD);
+ *   MDL_SWEEP_COOP    every tick and the barrier epilogue in one cooperative launch with
+ *                     grid-wide barriers between ticks.
+ * Returns MDL_E_ARG for any other value. */
+#define MDL_SWEEP_THREAD 0
+#define MDL_SWEEP_GROUP 1
+#define MDL_SWEEP_COOP 2
+int mdl_set_sweep_variant(mdl_ctx* ctx, int32_t variant);
+
 /* ---- Batches: many resident simulations stepped together on one GPU ----
  * (North-star batching/serving pattern; the paper runs one simulation serially.)
  * Each slot is a context with its own stream; mdl_batch_step launches every unfinished

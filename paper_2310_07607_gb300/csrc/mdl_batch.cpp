@@ -51,9 +51,11 @@ int64_t barriers_to(double dt, double t0, double t_end) {
     return n > 0 ? (int64_t)n : 0;
 }
 
-// Time `n` barriers of the context for each candidate sweep shape and keep the fastest.
+// Time `n` barriers of the context for each candidate sweep launch shape (threads, blocks
+// per SM) of its sweep variant and keep the fastest.  The variant itself is not tuned:
+// variants round differently, and a slot must give the values it gives alone.
 int tune(mdl_ctx* c, int n, std::pair<int, int>* best) {
-    static const int cand[][2] = {{128, 16}, {64, 32}, {128, 8}, {256, 8}, {64, 16}};
+    static const int cand[][2] = {{128, 16}, {64, 32}, {256, 8}, {128, 8}, {64, 16}};
     double best_ms = 1e300;
     *best = {128, 16};
     mdl::CtxBase* x = c->impl;
@@ -307,6 +309,13 @@ void mdl_batch_destroy(mdl_batch* b) {
 int mdl_set_tick_shape(mdl_ctx* ctx, int32_t threads, int32_t blocks_per_sm) {
     if (!ctx || !ctx->impl) return MDL_E_ARG;
     const int rc = ctx->impl->set_tick_shape(threads, blocks_per_sm);
+    if (rc) ctx->err = ctx->impl->err;
+    return rc;
+}
+
+int mdl_set_sweep_variant(mdl_ctx* ctx, int32_t variant) {
+    if (!ctx || !ctx->impl) return MDL_E_ARG;
+    const int rc = ctx->impl->set_sweep_variant(variant);
     if (rc) ctx->err = ctx->impl->err;
     return rc;
 }

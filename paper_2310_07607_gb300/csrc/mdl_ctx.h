@@ -35,6 +35,7 @@ public:
     // Launch shape of the sweep kernel (threads per block, resident blocks per SM); results
     // do not depend on it.  Returns MDL_E_ARG for unsupported shapes.
     virtual int set_tick_shape(int threads, int blocks_per_sm) = 0;
+    virtual int set_sweep_variant(int variant) = 0;
     virtual int64_t device_bytes() const = 0;     // device memory held by the context
     virtual double dt_barrier() const = 0;
     std::string err;

@@ -143,7 +143,8 @@ class Ctx : public CtxBase {
     int64_t gticks[4][2] = {};
     bool use_graphs = true;
     int tick_threads = 128, tick_bpsm = 16;   // sweep launch shape
-    bool coop_sweep = true;                   // ticks + epilogue in one cooperative launch
+    bool coop_sweep = false;                  // ticks + epilogue in one cooperative launch
+    bool group_tick = false;                  // Q1: a group of (p+1)^d lanes per element
     int64_t inflight = 0, inflight_start = 0; // barriers launched by begin_barriers
 
     static int div_up(int64_t n, int64_t b) { return (int)((n + b - 1) / b); }
@@ -421,11 +422,17 @@ class Ctx : public CtxBase {
                 stats.tick_launches += nt;
                 return MDL_OK;
             }
-            const int gt = (int)std::min<int64_t>(div_up(std::max<int64_t>(cap, 1), tick_threads),
+            const int lanes = (P == 1 && group_tick) ? NP : 1;
+            const int gt = (int)std::min<int64_t>(div_up(std::max<int64_t>(cap, 1) * lanes, tick_threads),
                                                   (int64_t)nsm * tick_bpsm);
             for (int i = 0; i < nt; ++i) {
                 ta.tick = i;
-                k_tick<R, DIM, P><<<gt, tick_threads, 0, st>>>(ta, T, ph);
+                if constexpr (P == 1) {
+                    if (group_tick) k_tick_group<R, DIM><<<gt, tick_threads, 0, st>>>(ta, ph, T);
+                    else k_tick<R, DIM, P><<<gt, tick_threads, 0, st>>>(ta, T, ph);
+                } else {
+                    k_tick<R, DIM, P><<<gt, tick_threads, 0, st>>>(ta, T, ph);
+                }
                 MDL_LAUNCHED();
                 stats.tick_launches++;
             }
@@ -817,6 +824,20 @@ public:
         if (threads != tick_threads || blocks_per_sm != tick_bpsm) {
             tick_threads = threads;
             tick_bpsm = blocks_per_sm;
+            drop_graphs();
+        }
+        return MDL_OK;
+    }
+
+    int set_sweep_variant(int variant) override {
+        if (variant < MDL_SWEEP_THREAD || variant > MDL_SWEEP_COOP) {
+            err = "set_sweep_variant: variant in {0, 1, 2}";
+            return MDL_E_ARG;
+        }
+        const bool co = variant == MDL_SWEEP_COOP, gr = variant == MDL_SWEEP_GROUP;
+        if (co != coop_sweep || gr != group_tick) {
+            coop_sweep = co;
+            group_tick = gr;
             drop_graphs();
         }
         return MDL_OK;

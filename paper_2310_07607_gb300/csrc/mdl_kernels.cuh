@@ -591,6 +591,134 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const do
 
 
 
+// Q1 tick with a group of G = (p+1)^d lanes per element (4 in 2D, 8 in 3D).  With the
+// class blocks every face contribution is the same code, A_own u + A_nb u_nb, so lane f
+// gathers and applies face f while the other lanes do the same for their faces (no
+// divergence); the group sums the face terms by shuffles and lane g updates DOF g.
+// Same arithmetic per element as k_tick for Q1, G times more threads in flight.
+template <typename R, int DIM>
+__global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const Phys<R> ph, const Tables<R> T) {
+    using S = Shape<DIM, 1>;
+    constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB, NREL = 1 + 2 * NSUB;
+    constexpr int G = NP;
+    const DevArrays<R>& d = a.d;
+    if (d.meta->err) return;
+    const int tick = a.tick;
+    const int n_act = d.meta->nact[tick];
+    const double nt = (double)(1 << a.B);
+    const double t_i = ((double)d.meta->nbar * nt + (double)tick) * a.dt / nt;
+    const int lane = threadIdx.x & 31;
+    const int g = lane % G;
+    const unsigned gmask = ((1u << G) - 1u) << (lane - g);
+    const int64_t gsz = gstride() / G;
+    for (int64_t idx = gtid() / G; idx < n_act; idx += gsz) {
+        const int e = d.order[idx];
+        const uint8_t lv = d.lvl[e];
+        const uint32_t inf = d.info[e];
+        const int b = lv & 7, par = (lv >> 3) & 1;
+        const int ke = tick >> (a.B - b);
+        const int cur = par ^ (ke & 1);
+        const int lev = (inf >> 24) & 15;
+        const R my_u = ((cur ? d.V1 : d.V0) + (size_t)e * NP)[g];
+        const R my_w = d.v[(size_t)e * NP + g];
+        const int fk = g < NF ? (int)((inf >> (4 * g)) & 3) : 0;
+        const int my_nb = g < NF ? d.nbr[(size_t)e * NF + g] : 0;
+        R u[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) u[q] = __shfl_sync(gmask, my_u, q, G);
+        R rf[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) rf[q] = R(0);
+        if (fk == 1 || fk == 2) {
+            R un[NP];
+            load_seen<R, NP>(d, tick, a.B, my_nb, un);
+            const int rel = fk == 1 ? 0 : 1 + ((inf >> (4 * g + 2)) & 3);
+            const R* A = d.qface + ((((size_t)g * 8 + lev) * NREL + rel) * 2) * NP * NP;
+            block_mv<R, NP>(A, u, rf);
+            block_mv<R, NP>(A + NP * NP, un, rf);
+        } else if (fk == 3) {
+            for (int sb = 0; sb < NSUB; ++sb) {
+                R un[NP];
+                load_seen<R, NP>(d, tick, a.B, d.hang[my_nb + sb], un);
+                const R* A = d.qface + ((((size_t)g * 8 + lev) * NREL + 1 + NSUB + sb) * 2) * NP * NP;
+                block_mv<R, NP>(A, u, rf);
+                block_mv<R, NP>(A + NP * NP, un, rf);
+            }
+        }
+        // group sum of the face terms; lane g keeps row g and adds its volume row
+        R rg = R(0);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            R x = rf[q];
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(gmask, x, o, G);
+            if (q == g) rg = x;
+        }
+        {
+            const R* Av = d.qvol + ((size_t)lev * NP + g) * NP;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) rg += __ldg(Av + j) * u[j];
+        }
+        const double dte_d = ldexp(a.dt, -b);
+        const R dte = (R)dte_d;
+        const double t_mid = t_i + 0.5 * dte_d;
+        R stim_o = R(0), stim_m = R(0);
+        if (inf & INFO_STIM) {
+            for (int s = 0; s < a.stim.n; ++s) {
+                const bool on_o = (a.stim.t0[s] <= t_i) && (t_i < a.stim.t1[s]);
+                const bool on_m = (a.stim.t0[s] <= t_mid) && (t_mid < a.stim.t1[s]);
+                if (!on_o && !on_m) continue;
+                if ((d.smask[s][e] >> g) & 1u) {
+                    if (on_o) stim_o -= (R)a.stim.amp[s];
+                    if (on_m) stim_m -= (R)a.stim.amp[s];
+                }
+            }
+        }
+        R Iag, gag;
+        if (ke == 0) {
+            Iag = ap_iion(ph, my_u, my_w) + stim_o;
+            gag = ap_g(ph, my_u, my_w);
+            if (b > 0) {
+                d.Ia[(size_t)e * NP + g] = Iag;
+                d.ga[(size_t)e * NP + g] = gag;
+            }
+        } else {
+            Iag = d.Ia[(size_t)e * NP + g];
+            gag = d.ga[(size_t)e * NP + g];
+        }
+        R Mq = ph.Wvol[lev];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) Mq *= T.w[digit<N1>(g, k)];
+        const R I = ap_iion(ph, my_u, my_w) + stim_o;
+        const R un_g = my_u + dte * (-rg / Mq - I);
+        const R wn_g = ap_step_state(ph, my_u, my_w, dte);
+        const R Vm = R(0.5) * (my_u + un_g);
+        const R wm = R(0.5) * (my_w + wn_g);
+        const R dI = ap_iion(ph, Vm, wm) + stim_m - Iag;
+        const R dg = ap_g(ph, Vm, wm) - gag;
+        R term = Mq * (dI * dI + dg * dg);
+        R vmax = un_g < R(0) ? -un_g : un_g;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            term += __shfl_xor_sync(gmask, term, o, G);
+            const R om = __shfl_xor_sync(gmask, vmax, o, G);
+            vmax = om > vmax ? om : vmax;
+        }
+        ((cur ? d.V0 : d.V1) + (size_t)e * NP)[g] = un_g;
+        d.v[(size_t)e * NP + g] = wn_g;
+        if (g == 0) {
+            const double inc = dte_d * (double)term;
+            d.acc[e] = (ke == 0) ? inc : d.acc[e] + inc;
+        }
+        if ((inf & INFO_PENDING) && vmax >= ph.lat_gate) {
+            R unv[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) unv[q] = __shfl_sync(gmask, un_g, q, G);
+            if (g == 0) lat_check<R, DIM, 1>(d, T, ph, e, inf, lev, u, unv, t_i, dte_d);
+        }
+    }
+}
+
 // The whole sweep of a barrier in one cooperative launch: every tick of Alg. 1 with a
 // grid-wide barrier between ticks (the Jacobi reading needs all of tick i before tick
 // i+1), then the epilogue with a fixed-order final reduction by block 0.  The grid is

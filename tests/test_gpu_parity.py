@@ -134,7 +134,7 @@ def test_levels_from_oracle_indicators_bit_exact(mdl):
 # Multi-level LTS sweeps with hanging faces and time interpolation.
 # --------------------------------------------------------------------------
 
-def lts_case(mdl, dim, p, seed, nbar, precision):
+def lts_case(mdl, dim, p, seed, nbar, precision, variant=None):
     prob = W.Problem(dim=dim, order=p, extent=(0.4, 0.3, 0.2), base=(4, 3, 2), sigma_l=1.2,
                      sigma_t=0.4, fibre=(0.6, 0.8, 0.0) if dim == 2 else (0.48, 0.64, 0.6),
                      gamma=10.0 * p * p, max_refine=2, n_lts_levels=3, lts_enabled=1,
@@ -150,6 +150,8 @@ def lts_case(mdl, dim, p, seed, nbar, precision):
     lv, cc, root = forest_arrays(f)
     g.upload_mesh(lv, cc, root)
     g.set_initial(V0, v0)
+    if variant is not None:
+        g.set_sweep_variant(variant)
     levels = []
     for n in range(nbar):
         lev = o.assign_levels(o.eta_t)
@@ -180,6 +182,28 @@ def test_lts_hanging_fp32_matches_oracle(mdl, dim, p):
     es, et = g.read_indicators()
     assert np.allclose(et, o.eta_t, rtol=2e-3, atol=1e-12 * et.max())
     g.close()
+
+
+@pytest.mark.parametrize("variant", ["group", "coop"])
+@pytest.mark.parametrize("dim,p", [(2, 1), (3, 1), (3, 2)])
+def test_sweep_variants_match_oracle_fp64(mdl, dim, p, variant):
+    v = {"group": mdl.SWEEP_GROUP, "coop": mdl.SWEEP_COOP}[variant]
+    prob, o, g, levels = lts_case(mdl, dim, p, seed=dim * 10 + p, nbar=3, precision=64, variant=v)
+    assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-12
+    assert np.abs(g.read_state() - o.v).max() <= 1e-11
+    lat_compare(g.read_activation(), o.lat, 1e-9)
+    g.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_thread_and_coop_sweeps_identical(mdl, dim):
+    out = []
+    for v in (mdl.SWEEP_THREAD, mdl.SWEEP_COOP):
+        prob, o, g, levels = lts_case(mdl, dim, 1, seed=dim, nbar=3, precision=32, variant=v)
+        out.append((g.read_V(), g.read_state(), g.read_indicators()[1], g.read_activation()))
+        g.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
 
 
 # --------------------------------------------------------------------------

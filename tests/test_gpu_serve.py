@@ -1,0 +1,51 @@
+"""Continuous-batching request loop: requests arriving while others run are admitted as
+memory allows, all complete, and each result equals the same simulation run alone."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def small(dim, p, seed, precision=32):
+    return W.Problem(dim=dim, order=p, extent=(0.2, 0.15, 0.1), base=(4, 3, 2), sigma_l=1.2, sigma_t=0.4,
+                     fibre=(0.6, 0.8, 0.0), gamma=10.0 * p * p, max_refine=1, n_lts_levels=2,
+                     lts_enabled=1, amr_enabled=1, tau_refine=1e-10, tau_coarsen=1e-13, dt_barrier=0.0,
+                     state_integrator=W.STATE_EXP, precision=precision,
+                     stimuli=[W.Stimulus((0, 0, 0), (0.05 + 0.01 * seed, 0.05, 0.05), 1.0, 0.0, 1.0)])
+
+
+def test_serving_loop_results_equal_alone():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2310_07607_gb300 import build, mdl
+    from paper_2310_07607_gb300.serve import Request, Server
+    build.build()
+    specs = [(2, 1), (3, 1), (2, 2), (3, 2), (2, 1), (3, 1)]
+    reqs = []
+    for i, (d, p) in enumerate(specs):
+        prob = small(d, p, i)
+        dt = mdl.Sim(prob).dt
+        reqs.append(Request(rid=i, prob=prob, horizon_ms=(10 + 3 * i) * dt, arrival_s=0.02 * i))
+
+    def grab(req, g):
+        return {"V": g.read_V(), "lat": g.read_activation(), "nbar": g.time()[1]}
+
+    # a budget that holds about three of them at a time forces waiting and admission later
+    fp = max(mdl.Batch(autotune=False).footprint(r.prob) for r in reqs)
+    srv = Server(budget_bytes=int(3.2 * fp), barriers_per_round=4, on_result=grab)
+    rep = srv.run(reqs, wall_limit_s=120.0, drain=True)
+    srv.close()
+    assert rep["completed"] == len(reqs) and rep["failed"] == 0
+    assert rep["peak_resident"] <= 3
+    assert np.isfinite(rep["ttr_p50_s"]) and rep["ttr_p99_s"] >= rep["ttr_p50_s"]
+    for r in reqs:
+        g = mdl.Sim(r.prob)
+        n = int(np.floor(r.horizon_ms / g.dt + 1e-9))
+        g.step_barriers(n)
+        assert r.result["nbar"] == n
+        assert np.array_equal(r.result["V"], g.read_V())
+        assert np.array_equal(r.result["lat"], g.read_activation())
+        g.close()
