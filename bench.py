@@ -295,6 +295,139 @@ def run_e2e(sim, args, torch):
 
 
 # ---------------------------------------------------------------------------
+# Many simulations on one GPU: a batch of 64 heterogeneous instances, and a
+# continuous-batching request stream.  Both go through mdl_batch_*.
+# ---------------------------------------------------------------------------
+
+CLASS_ALG_BYTES = {(2, 1): 25.0, (3, 1): 21.5, (3, 2): 17.6, (2, 2): 16.0 + 36.0 / 9.0}
+
+
+def slot_alg_bytes(prob):
+    return CLASS_ALG_BYTES.get((prob.dim, prob.order), 16.0)
+
+
+def run_batch(args, rank, world):
+    """64 heterogeneous resident instances (32 2D Q1, 16 3D Q1, 16 3D Q2; base element counts
+    log-uniform in [1e3, 1e5], seed 4).  A step is one batch round: every instance advances
+    one barrier, all slots' work issued on their own streams before any is waited for."""
+    import torch
+    torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
+    from paper_2310_07607_gb300 import build, mdl
+    build.build()
+    inst = W.batch_instances(64, seed=4)
+    b = mdl.Batch(autotune=True)
+    t_setup = time.perf_counter()
+    slots = [b.admit(p, t_end) for p, t_end in inst]
+    t_setup = time.perf_counter() - t_setup
+    sims = {s: b.slot(s)[0] for s in slots}
+    for _ in range(args.warmup):
+        b.step(1)
+    base = {s: sims[s].stats()["dof_updates"] for s in slots}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.step(1)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    du = {s: sims[s].stats()["dof_updates"] - base[s] for s in slots}
+    total = float(sum(du.values()))
+    alg = sum(du[s] * slot_alg_bytes(p) for s, (p, _) in zip(slots, inst))
+    peak, peak_kind = load_peaks()
+    n_dof = sum(sims[s].sizes()[1] for s in slots)
+    # barriers each instance needs to reach its 100 ms horizon, and the projected batch time
+    need = [int(math.floor(t_end / sims[s].time()[2] + 1e-9)) for s, (_, t_end) in zip(slots, inst)]
+    per_round_s = secs / args.steps
+    used, budget, resident = b.usage()
+    out = {
+        "metric": METRIC, "value": total / secs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch64_mixed_2dq1_3dq1_3dq2_lts1to4_ap_fp32", "instances": len(slots),
+                   "n_dof_total": int(n_dof), "device_bytes": int(used), "resident": resident,
+                   "timing": "host clock around K batch rounds, device synchronised on both sides",
+                   "l2": "working set larger than L2 (%.0f MB of state)" % (used / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": round(alg / secs / 1e9, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(alg / secs / 1e9 / peak, 4), "traffic": None, "peak_source": peak_kind,
+                     "note": "whole batch round incl. every phase; per-class algorithmic bytes"},
+        "horizon": {"t_end_ms": inst[0][1], "barriers_max": max(need), "barriers_min": min(need),
+                    "projected_s_all_to_horizon": round(max(need) * per_round_s, 2)},
+        "setup_s_incl_autotune": round(t_setup, 2),
+        "tuned_shapes": sorted({str(b.shape(p)) for p, _ in inst}),
+    }
+    b.close()
+    return out
+
+
+def run_serve(args, rank, world):
+    """Poisson request stream (rate 20/s for 60 s, seed 5; 2D/3D, Q1/Q2, AMR + LTS, horizons
+    100-500 ms) through the continuous-batching loop for a bounded wall time, then the same
+    stream through a plain loop (one request at a time, FP64, uniform mesh at the finest
+    level, global time step) for a bounded wall time."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2310_07607_gb300 import build, mdl
+    from paper_2310_07607_gb300.serve import Request, Server
+    build.build()
+    wall = float(os.environ.get("MDL_SERVE_WALL_S", "60"))
+    reqs = [Request(rid=i, prob=p, horizon_ms=h, arrival_s=t)
+            for i, (t, p, h) in enumerate(W.poisson_requests(20.0, 60.0, seed=5))]
+    srv = Server(budget_bytes=0, barriers_per_round=args.serve_round, autotune=True)
+    rep = srv.run(reqs, wall_limit_s=wall, drain=False)
+    srv.close()
+    # plain comparator: the same arrivals served one by one without adaptivity in FP64
+    plain = run_plain_loop(mdl, reqs, wall, torch)
+    return {"metric": "sims/s", "value": rep["sims_per_s"], "unit": "sims/s", "n_gpus": 1,
+            "steps": None, "warmup": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve_poisson_rate20_60s_amr2_lts3_ap_fp32", "wall_limit_s": wall,
+                       "barriers_per_round": args.serve_round},
+            "adaptive": rep, "plain_fp64_uniform_loop": plain}
+
+
+def plain_version(prob):
+    import dataclasses
+    f = 2 ** prob.max_refine
+    base = tuple(int(x * f) if k < prob.dim else x for k, x in enumerate(prob.base))
+    return dataclasses.replace(prob, base=base, max_refine=0, amr_enabled=0, lts_enabled=0,
+                               n_lts_levels=1, precision=64, dt_barrier=0.0)
+
+
+def run_plain_loop(mdl, reqs, wall, torch):
+    """One request at a time in arrival order, FP64, uniform mesh at the adaptive run's finest
+    level, global forward Euler; bounded by `wall` seconds of serving time."""
+    t0 = time.perf_counter()
+    done, ttr, proj = 0, [], []
+    for r in sorted(reqs, key=lambda x: x.arrival_s):
+        now = time.perf_counter() - t0
+        if now >= wall:
+            break
+        if r.arrival_s > now:
+            time.sleep(r.arrival_s - now)
+        p = plain_version(r.prob)
+        g = mdl.Sim(p)
+        n = int(math.floor(r.horizon_ms / g.dt + 1e-9))
+        start = time.perf_counter() - t0
+        k = 0
+        while k < n and time.perf_counter() - t0 < wall:
+            m = min(64, n - k)
+            g.step_barriers(m)
+            k += m
+        end = time.perf_counter() - t0
+        g.close()
+        if k == n:
+            done += 1
+            ttr.append(end - r.arrival_s)
+        else:
+            rate = k / max(end - start, 1e-9)
+            proj.append((start - r.arrival_s) + n / max(rate, 1e-9))
+    from paper_2310_07607_gb300.serve import percentile
+    el = time.perf_counter() - t0
+    return {"completed": done, "sims_per_s": done / el, "wall_s": el,
+            "ttr_p50_s": percentile(ttr, 0.5), "ttr_p99_s": percentile(ttr, 0.99),
+            "projected_ttr_of_unfinished_s": proj[:4]}
+
+
+# ---------------------------------------------------------------------------
 # The FP64 oracle on the host cores (bounded sample of the same workload).
 # ---------------------------------------------------------------------------
 
@@ -376,7 +509,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="slab2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="slab2d", choices=sorted(WORKLOADS) + ["batch64", "serve"])
+    ap.add_argument("--serve-round", type=int, default=16, help="barriers per slot per serving round")
     ap.add_argument("--sweep", default="thread", choices=sorted(SWEEPS),
                     help="sweep kernel variant (thread per element; group: Q1 lanes per element; "
                          "coop: one cooperative launch per barrier)")
@@ -387,6 +521,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.workload == "batch64":
+        out = run_batch(args, rank, world)
+    elif args.workload == "serve":
+        out = run_serve(args, rank, world) if rank == 0 else None
     else:
         out = run_ours(args, rank, world)
     if rank == 0 and out is not None:

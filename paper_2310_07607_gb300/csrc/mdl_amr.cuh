@@ -42,6 +42,7 @@ struct StimBoxes {
 template <int DIM>
 __global__ void k_amr_mark(const int4* coord, const double* eta, uint8_t* r, uint8_t* c0, DevMeta* m,
                            double tau_r, int L) {
+    pdl_enter();
     if (m->err) return;
     const int64_t ne = m->ne;
     for (int64_t e = gtid(); e < ne; e += gstride()) {
@@ -53,6 +54,7 @@ __global__ void k_amr_mark(const int4* coord, const double* eta, uint8_t* r, uin
 
 template <int DIM>
 __global__ void k_amr_close(const uint32_t* info, const int32_t* nbr, uint8_t* r, DevMeta* m) {
+    pdl_enter();
     if (m->err) return;
     constexpr int NF = 2 * DIM;
     const int64_t ne = m->ne;
@@ -67,6 +69,7 @@ __global__ void k_amr_close(const uint32_t* info, const int32_t* nbr, uint8_t* r
 template <int DIM>
 __global__ void k_amr_family(const int4* coord, const uint32_t* info, const int32_t* nbr, const double* eta,
                              const uint8_t* r, uint8_t* c0, DevMeta* m, double tau_c) {
+    pdl_enter();
     if (m->err) return;
     constexpr int NF = 2 * DIM, NC = 1 << DIM;
     const int64_t ne = m->ne;
@@ -101,7 +104,7 @@ __global__ void k_amr_family(const int4* coord, const uint32_t* info, const int3
 
 // Exclusive scan of cnt[0..ne) in chunks of SCAN_CHUNK per block: block sums, a one-block
 // scan of the sums, then per-block scans with the block offset.  Writes the total to ne_new.
-constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 8, SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
+constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 2, SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
 
 __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* sh, int64_t* total) {
     // inclusive warp scans then a scan over warp totals
@@ -146,6 +149,7 @@ __device__ __forceinline__ int new_count(const int4* coord, const uint8_t* r, co
 template <int DIM>
 __global__ void k_scan_blocks(const int4* coord, const uint8_t* r, const uint8_t* c0, int64_t* bsum,
                               DevMeta* m) {
+    pdl_enter();
     if (m->err) return;
     __shared__ int64_t sh[32];
     const int64_t ne = m->ne;
@@ -168,6 +172,7 @@ __global__ void k_scan_blocks(const int4* coord, const uint8_t* r, const uint8_t
 }
 
 static __global__ void k_scan_top(int64_t* bsum, DevMeta* m, int64_t cap) {
+    pdl_enter();
     if (m->err) return;
     __shared__ int64_t sh[32];
     const int64_t ne = m->ne;
@@ -201,6 +206,7 @@ static __global__ void k_scan_top(int64_t* bsum, DevMeta* m, int64_t cap) {
 template <int DIM>
 __global__ void k_scan_emit(const int4* coord, const uint8_t* r, const uint8_t* c0, const int64_t* bsum,
                             int4* ncoord, int8_t* pkind, int32_t* psrc, int8_t* pbits, const DevMeta* m) {
+    pdl_enter();
     if (m->err) return;
     constexpr int NC = 1 << DIM;
     __shared__ int64_t sh[32];
@@ -248,6 +254,7 @@ __global__ void k_scan_emit(const int4* coord, const uint8_t* r, const uint8_t* 
 // contiguous runs of 2^(L - level) cells.
 template <int DIM>
 __global__ void k_owner_fill(const int4* coord, int32_t* owner, Grid g, const DevMeta* m, int force) {
+    pdl_enter();
     if (m->err || !(force || m->changed)) return;
     const int64_t ne = m->ne;
     const int maxrows = DIM == 3 ? (1 << (2 * g.L)) : (1 << g.L);
@@ -275,6 +282,7 @@ __global__ void k_mesh_tables(const int4* coord, const int32_t* owner, Grid g, u
                               int32_t* hang, int32_t* root, uint32_t* loc, uint8_t* bcfl,
                               const uint8_t* class_b, uint32_t* smask0, uint32_t* smask1, uint32_t* smask2,
                               uint32_t* smask3, StimBoxes sb, Phys<double> phd, DevMeta* m, int force) {
+    pdl_enter();
     if (m->err || !(force || m->changed)) return;
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB;
@@ -370,6 +378,7 @@ constexpr int ORD_THREADS = 256;
 template <typename R>
 __global__ void k_levels_count(const DevArrays<R> d, const int8_t* ovr, const double* eta_t, double tau_cell,
                                int bcell, int B, int lts, int32_t* bcnt) {
+    pdl_enter();
     if (d.meta->err) return;
     __shared__ int sc[8];
     if (threadIdx.x < 8) sc[threadIdx.x] = 0;
@@ -396,23 +405,68 @@ __global__ void k_levels_count(const DevArrays<R> d, const int8_t* ovr, const do
     if (threadIdx.x < 8) bcnt[(int64_t)blockIdx.x * 8 + threadIdx.x] = sc[threadIdx.x];
 }
 
+// Exclusive scan over blocks of the per-block level counts, all 8 levels at once (each
+// thread holds one block's 8 counts; warp scans, then a scan of the warp totals), then the
+// level base offsets (b descending) and the due counts of every tick.
 static __global__ void k_order_top(int32_t* bcnt, DevMeta* m, int B) {
+    pdl_enter();
     if (m->err) return;
-    __shared__ int64_t sh[32];
+    __shared__ int32_t ws[32][8];
     const int64_t ne = m->ne;
     const int64_t nb = (ne + ORD_THREADS - 1) / ORD_THREADS;
-    __shared__ int64_t tot[8];
-    for (int b = 0; b < 8; ++b) {
-        int64_t carry = 0;
-        for (int64_t s0 = 0; s0 < nb; s0 += blockDim.x) {
-            const int64_t i = s0 + threadIdx.x;
-            const int64_t v = i < nb ? bcnt[i * 8 + b] : 0;
-            int64_t t;
-            const int64_t ex = block_excl_scan(v, sh, &t);
-            if (i < nb) bcnt[i * 8 + b] = (int32_t)(carry + ex);
-            carry += t;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int32_t carry[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) carry[b] = 0;
+    for (int64_t s0 = 0; s0 < nb; s0 += blockDim.x) {
+        const int64_t i = s0 + threadIdx.x;
+        int32_t v[8];
+        if (i < nb) {
+            const int4 lo = reinterpret_cast<const int4*>(bcnt)[2 * i];
+            const int4 hi = reinterpret_cast<const int4*>(bcnt)[2 * i + 1];
+            v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+            v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+        } else {
+#pragma unroll
+            for (int b = 0; b < 8; ++b) v[b] = 0;
         }
-        if (threadIdx.x == 0) tot[b] = carry;
+        int32_t x[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) x[b] = v[b];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, x[b], o);
+                if (lane >= o) x[b] += y;
+            }
+        }
+        if (lane == 31) {
+#pragma unroll
+            for (int b = 0; b < 8; ++b) ws[w][b] = x[b];
+        }
+        __syncthreads();
+        if (w == 0) {
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                int32_t t = lane < nw ? ws[lane][b] : 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                    if (lane >= o) t += y;
+                }
+                if (lane < nw) ws[lane][b] = t;
+            }
+        }
+        __syncthreads();
+        int32_t ex[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) ex[b] = carry[b] + (w > 0 ? ws[w - 1][b] : 0) + x[b] - v[b];
+        if (i < nb) {
+            reinterpret_cast<int4*>(bcnt)[2 * i] = make_int4(ex[0], ex[1], ex[2], ex[3]);
+            reinterpret_cast<int4*>(bcnt)[2 * i + 1] = make_int4(ex[4], ex[5], ex[6], ex[7]);
+        }
+#pragma unroll
+        for (int b = 0; b < 8; ++b) carry[b] += ws[nw - 1][b];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -421,8 +475,8 @@ static __global__ void k_order_top(int32_t* bcnt, DevMeta* m, int B) {
         int32_t* lo = bcnt + nb * 8;
         for (int b = 7; b >= 0; --b) {
             lo[b] = (int32_t)off;
-            off += tot[b];
-            m->cnt[b] = (unsigned)tot[b];
+            off += carry[b];
+            m->cnt[b] = (unsigned)carry[b];
         }
         const int nt = 1 << B;
         int64_t eu = 0;
@@ -431,7 +485,7 @@ static __global__ void k_order_top(int32_t* bcnt, DevMeta* m, int B) {
             if (i == 0) na = ne;
             else {
                 const int tz = __ffs(i) - 1;
-                for (int b = B - tz; b <= B; ++b) na += tot[b];
+                for (int b = B - tz; b <= B; ++b) na += carry[b];
             }
             m->nact[i] = (int32_t)na;
             eu += na;
@@ -441,6 +495,7 @@ static __global__ void k_order_top(int32_t* bcnt, DevMeta* m, int B) {
 }
 
 static __global__ void k_order_scatter(const uint8_t* lvl, const int32_t* bcnt, int32_t* order, const DevMeta* m) {
+    pdl_enter();
     if (m->err) return;
     __shared__ int wc[ORD_THREADS / 32][8];
     const int64_t ne = m->ne;

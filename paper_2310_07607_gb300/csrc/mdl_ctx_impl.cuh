@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mdl_amr.cuh"
@@ -145,9 +146,29 @@ class Ctx : public CtxBase {
     int tick_threads = 128, tick_bpsm = 16;   // sweep launch shape
     bool coop_sweep = false;                  // ticks + epilogue in one cooperative launch
     bool group_tick = false;                  // Q1: a group of (p+1)^d lanes per element
+    bool pdl = true;                          // programmatic dependent launch between kernels
     int64_t inflight = 0, inflight_start = 0; // barriers launched by begin_barriers
 
     static int div_up(int64_t n, int64_t b) { return (int)((n + b - 1) / b); }
+    // Launch a barrier-step kernel on the context's stream.  With pdl set, the launch
+    // allows programmatic dependent launch: the kernel's blocks may be scheduled while
+    // its predecessor drains, and every such kernel starts with pdl_enter(), which waits
+    // for the predecessor to complete (its writes visible) before touching any data.
+    template <typename... KP, typename... Args>
+    cudaError_t launch_k(void (*k)(KP...), int grid, int block, Args&&... args) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3((unsigned)block);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+    }
+
     int persistent_blocks(int threads) const {
         const int64_t need = div_up(std::max<int64_t>(cap, 1), threads);
         return (int)std::min<int64_t>(need, (int64_t)nsm * (2048 / threads));
@@ -267,11 +288,11 @@ class Ctx : public CtxBase {
     int build_tables(int s, int force) {
         Set& x = sets[s];
         const int gb = persistent_blocks(256);
-        k_owner_fill<DIM><<<nsm * 8, 256, 0, st>>>(x.coord.p, owner.p, grid_, meta.p, force);
+        MDL_CK(launch_k((k_owner_fill<DIM>), nsm * 8, 256, x.coord.p, owner.p, grid_, meta.p, force));
         MDL_LAUNCHED();
-        k_mesh_tables<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(
+        MDL_CK(launch_k((k_mesh_tables<R, DIM, P>), persistent_blocks(128), 128, 
             x.coord.p, owner.p, grid_, info.p, nbr.p, hang.p, root.p, loc.p, bcfl.p, class_b.p,
-            smask[0].p, smask[1].p, smask[2].p, smask[3].p, sboxes, phd, meta.p, force);
+            smask[0].p, smask[1].p, smask[2].p, smask[3].p, sboxes, phd, meta.p, force));
         MDL_LAUNCHED();
         return MDL_OK;
     }
@@ -343,7 +364,7 @@ class Ctx : public CtxBase {
     int launch_phase(int ph_, int o) {
         const int g256 = persistent_blocks(256), g128 = persistent_blocks(128);
         if (ph_ == 0) {
-            k_eta_s<R, DIM, P><<<g128, 128, 0, st>>>(arrays(o), T, ph);
+            MDL_CK(launch_k((k_eta_s<R, DIM, P>), g128, 128, arrays(o), T, ph));
             MDL_LAUNCHED();
             return MDL_OK;
         }
@@ -353,30 +374,30 @@ class Ctx : public CtxBase {
                 const int n = o ^ 1;
                 Set& so = sets[o];
                 Set& sn = sets[n];
-                k_amr_mark<DIM><<<g256, 256, 0, st>>>(so.coord.p, eta_s.p, r.p, c0.p, meta.p, pb.tau_refine,
-                                                      pb.max_refine);
+                MDL_CK(launch_k((k_amr_mark<DIM>), g256, 256, so.coord.p, eta_s.p, r.p, c0.p, meta.p, pb.tau_refine,
+                                                      pb.max_refine));
                 MDL_LAUNCHED();
                 for (int i = 0; i < pb.max_refine; ++i) {
-                    k_amr_close<DIM><<<g256, 256, 0, st>>>(info.p, nbr.p, r.p, meta.p);
+                    MDL_CK(launch_k((k_amr_close<DIM>), g256, 256, info.p, nbr.p, r.p, meta.p));
                     MDL_LAUNCHED();
                 }
-                k_amr_family<DIM><<<g256, 256, 0, st>>>(so.coord.p, info.p, nbr.p, eta_s.p, r.p, c0.p, meta.p,
-                                                        pb.tau_coarsen);
+                MDL_CK(launch_k((k_amr_family<DIM>), g256, 256, so.coord.p, info.p, nbr.p, eta_s.p, r.p, c0.p, meta.p,
+                                                        pb.tau_coarsen));
                 MDL_LAUNCHED();
                 const int nsb = div_up(cap, SCAN_CHUNK);
-                k_scan_blocks<DIM><<<nsb, SCAN_THREADS, 0, st>>>(so.coord.p, r.p, c0.p, bsum.p, meta.p);
+                MDL_CK(launch_k((k_scan_blocks<DIM>), nsb, SCAN_THREADS, so.coord.p, r.p, c0.p, bsum.p, meta.p));
                 MDL_LAUNCHED();
-                k_scan_top<<<1, 1024, 0, st>>>(bsum.p, meta.p, cap);
+                MDL_CK(launch_k((k_scan_top), 1, 1024, bsum.p, meta.p, cap));
                 MDL_LAUNCHED();
-                k_scan_emit<DIM><<<nsb, SCAN_THREADS, 0, st>>>(so.coord.p, r.p, c0.p, bsum.p, sn.coord.p,
-                                                               pkind.p, psrc.p, pbits.p, meta.p);
+                MDL_CK(launch_k((k_scan_emit<DIM>), nsb, SCAN_THREADS, so.coord.p, r.p, c0.p, bsum.p, sn.coord.p,
+                                                               pkind.p, psrc.p, pbits.p, meta.p));
                 MDL_LAUNCHED();
                 DevArrays<R> od = arrays(o);
                 int rc = build_tables(n, 0);
                 if (rc) return rc;
-                k_transfer<R, DIM, P><<<g128, 128, 0, st>>>(od, arrays(n), pkind.p, psrc.p, pbits.p, T);
+                MDL_CK(launch_k((k_transfer<R, DIM, P>), g128, 128, od, arrays(n), pkind.p, psrc.p, pbits.p, T));
                 MDL_LAUNCHED();
-                k_lat_refresh<R, DIM, P><<<g128, 128, 0, st>>>(arrays(n), T, ph, 0.0, 0, 0);
+                MDL_CK(launch_k((k_lat_refresh<R, DIM, P>), g128, 128, arrays(n), T, ph, 0.0, 0, 0));
                 MDL_LAUNCHED();
                 cur = n;
             }
@@ -387,12 +408,12 @@ class Ctx : public CtxBase {
             }
             const double* et = ovr_eta_t ? eta_t_ovr.p : sets[cur].eta_t.p;
             const int nob = div_up(cap, ORD_THREADS);
-            k_levels_count<R><<<nob, ORD_THREADS, 0, st>>>(arrays(cur), ovr_levels ? lvl_ovr.p : nullptr, et,
-                                                           pb.tau_cell, bcell, B, pb.lts_enabled, bcnt.p);
+            MDL_CK(launch_k((k_levels_count<R>), nob, ORD_THREADS, arrays(cur), ovr_levels ? lvl_ovr.p : nullptr, et,
+                                                           pb.tau_cell, bcell, B, pb.lts_enabled, bcnt.p));
             MDL_LAUNCHED();
-            k_order_top<<<1, 1024, 0, st>>>(bcnt.p, meta.p, B);
+            MDL_CK(launch_k((k_order_top), 1, 1024, bcnt.p, meta.p, B));
             MDL_LAUNCHED();
-            k_order_scatter<<<nob, ORD_THREADS, 0, st>>>(sets[cur].lvl.p, bcnt.p, order.p, meta.p);
+            MDL_CK(launch_k((k_order_scatter), nob, ORD_THREADS, sets[cur].lvl.p, bcnt.p, order.p, meta.p));
             MDL_LAUNCHED();
             return MDL_OK;
         }
@@ -401,6 +422,11 @@ class Ctx : public CtxBase {
             ta.d = arrays(o);
             ta.dt = dt;
             ta.B = B;
+            ta.tscale = ldexp(dt, -B);
+            for (int b = 0; b < 8; ++b) {
+                ta.dte[b] = ldexp(dt, -b);
+                ta.dteR[b] = (R)ta.dte[b];
+            }
             ta.stim = stim;
             const int nt = 1 << B;
             if (coop_sweep) {
@@ -428,17 +454,17 @@ class Ctx : public CtxBase {
             for (int i = 0; i < nt; ++i) {
                 ta.tick = i;
                 if constexpr (P == 1) {
-                    if (group_tick) k_tick_group<R, DIM><<<gt, tick_threads, 0, st>>>(ta, ph, T);
-                    else k_tick<R, DIM, P><<<gt, tick_threads, 0, st>>>(ta, T, ph);
+                    if (group_tick) MDL_CK(launch_k((k_tick_group<R, DIM>), gt, tick_threads, ta, ph, T));
+                    else MDL_CK(launch_k((k_tick<R, DIM, P>), gt, tick_threads, ta, T, ph));
                 } else {
-                    k_tick<R, DIM, P><<<gt, tick_threads, 0, st>>>(ta, T, ph);
+                    MDL_CK(launch_k((k_tick<R, DIM, P>), gt, tick_threads, ta, T, ph));
                 }
                 MDL_LAUNCHED();
                 stats.tick_launches++;
             }
             return MDL_OK;
         }
-        k_epilogue<R, DIM, P><<<g256, 256, 0, st>>>(arrays(o), mtab.p, dt);
+        MDL_CK(launch_k((k_epilogue<R, DIM, P>), g256, 256, arrays(o), mtab.p, dt, (float)(1.0 / dt)));
         MDL_LAUNCHED();
         return MDL_OK;
     }

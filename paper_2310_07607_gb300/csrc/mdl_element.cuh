@@ -67,6 +67,7 @@ struct Phys {
     R h2[8][3];        // 2 / h
     R Wvol[8];         // prod_k h_k / 2
     R Wface[8][3];     // prod_{l != k} h_l / 2  (face Jacobian of a normal-k face)
+    R Minv[8][27];     // inverse diagonal GL mass 1 / (Wvol prod_k w_{a_k}) per level and node
     // Aliev-Panfilov
     R k, a, eps0, mu1, mu2, inv_ts;
     int32_t ionic;     // 0 AP, -1 none

@@ -48,6 +48,14 @@ struct DevMeta {
 
 constexpr unsigned ERR_NONFINITE = 1u, ERR_CFL = 2u, ERR_CAPACITY = 4u, ERR_MESH = 8u;
 
+// Programmatic dependent launch: wait until the preceding grid on the stream has completed
+// and its writes are visible, then let the following grid be scheduled.  Each kernel of a
+// barrier step calls this first; launched without the attribute it returns at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
 __device__ __forceinline__ int64_t gtid() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }
 
@@ -78,14 +86,81 @@ struct DevArrays {
     const R* qkelly;
 };
 
-// j[t] += sum_q K[t][q] x[q] for a row-major NT x NP block.
+// Vector width for rows of NP values of type R: 16-byte loads when a row is a whole number
+// of them (every table block and element vector below starts on a 16-byte boundary).
+template <typename R, int NP>
+struct Vec {
+    static constexpr int W = (16 / (int)sizeof(R));
+    static constexpr bool ok = (NP % W) == 0;
+};
+
+// out[0..n) = p[0..n), 16-byte loads where the width allows (p 16-byte aligned then).
+template <typename R, int N>
+__device__ __forceinline__ void ld_row(const R* __restrict__ p, R* out) {
+    if constexpr (Vec<R, N>::ok && sizeof(R) == 4) {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
+            out[4 * i] = v.x; out[4 * i + 1] = v.y; out[4 * i + 2] = v.z; out[4 * i + 3] = v.w;
+        }
+    } else if constexpr (Vec<R, N>::ok && sizeof(R) == 8) {
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const double2 v = __ldg(reinterpret_cast<const double2*>(p) + i);
+            out[2 * i] = v.x; out[2 * i + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = __ldg(p + i);
+    }
+}
+
+// Plain (coherent) vector load / store of an element's N values.
+template <typename R, int N>
+__device__ __forceinline__ void ld_vec(const R* p, R* out) {
+    if constexpr (Vec<R, N>::ok && sizeof(R) == 4) {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            const float4 v = reinterpret_cast<const float4*>(p)[i];
+            out[4 * i] = v.x; out[4 * i + 1] = v.y; out[4 * i + 2] = v.z; out[4 * i + 3] = v.w;
+        }
+    } else if constexpr (Vec<R, N>::ok && sizeof(R) == 8) {
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const double2 v = reinterpret_cast<const double2*>(p)[i];
+            out[2 * i] = v.x; out[2 * i + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = p[i];
+    }
+}
+
+template <typename R, int N>
+__device__ __forceinline__ void st_vec(R* p, const R* x) {
+    if constexpr (Vec<R, N>::ok && sizeof(R) == 4) {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i)
+            reinterpret_cast<float4*>(p)[i] = make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
+    } else if constexpr (Vec<R, N>::ok && sizeof(R) == 8) {
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) reinterpret_cast<double2*>(p)[i] = make_double2(x[2 * i], x[2 * i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) p[i] = x[i];
+    }
+}
+
+// j[t] += sum_q K[t][q] x[q] for a row-major NT x NP block (read-only path).
 template <typename R, int NT, int NP>
 __device__ __forceinline__ void block_jump(const R* __restrict__ K, const R* x, R* j) {
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
+        R row[NP];
+        ld_row<R, NP>(K + t * NP, row);
         R acc = j[t];
 #pragma unroll
-        for (int q = 0; q < NP; ++q) acc += __ldg(K + t * NP + q) * x[q];
+        for (int q = 0; q < NP; ++q) acc += row[q] * x[q];
         j[t] = acc;
     }
 }
@@ -95,11 +170,23 @@ template <typename R, int NP>
 __device__ __forceinline__ void block_mv(const R* __restrict__ A, const R* x, R* r) {
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
+        R row[NP];
+        ld_row<R, NP>(A + q * NP, row);
         R acc = r[q];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc += __ldg(A + q * NP + j) * x[j];
+        for (int j = 0; j < NP; ++j) acc += row[j] * x[j];
         r[q] = acc;
     }
+}
+
+// 2^-sh exactly, for 0 <= sh < 64 (built from the IEEE-754 exponent field).
+template <typename R>
+__device__ __forceinline__ R pow2_neg(int sh);
+template <>
+__device__ __forceinline__ float pow2_neg<float>(int sh) { return __int_as_float((127 - sh) << 23); }
+template <>
+__device__ __forceinline__ double pow2_neg<double>(int sh) {
+    return __longlong_as_double((long long)(1023 - sh) << 52);
 }
 
 struct StimArgs {
@@ -143,33 +230,8 @@ __device__ __forceinline__ R ap_step_state(const Phys<R>& ph, R V, R w, R dt) {
     return vinf + (w - vinf) * r_exp<R>(-eps * dt * ph.inv_ts);
 }
 
-// Values of element nb as seen at tick `tick`: its current value if it is due (or
-// finer), else the linear time interpolant of its last step (Alg. 1).
-template <typename R, int NP>
-__device__ __forceinline__ void load_seen(const DevArrays<R>& d, int tick, int B, int nb, R* un) {
-    const uint8_t lv = d.lvl[nb];
-    const int b = lv & 7, par = (lv >> 3) & 1;
-    const int sh = B - b;
-    const int j = tick >> sh;
-    const int rem = tick & ((1 << sh) - 1);
-    if (rem == 0) {
-        const R* src = ((par ^ (j & 1)) ? d.V1 : d.V0) + (size_t)nb * NP;
-#pragma unroll
-        for (int q = 0; q < NP; ++q) un[q] = src[q];
-    } else {
-        const int nw = par ^ ((j + 1) & 1);
-        const R* sn = (nw ? d.V1 : d.V0) + (size_t)nb * NP;
-        const R* so = (nw ? d.V0 : d.V1) + (size_t)nb * NP;
-        const R th = R(rem) / R(1 << sh);
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const R o = so[q];
-            un[q] = o + th * (sn[q] - o);
-        }
-    }
-}
-
-// Values of element nb as seen at tick `tick`, given its level byte (see load_seen).
+// Values of element nb as seen at tick `tick`, given its level byte: its current value if
+// it is due (or finer), else the linear time interpolant of its last step (Alg. 1).
 template <typename R, int NP>
 __device__ __forceinline__ void load_seen_lv(const DevArrays<R>& d, int tick, int B, int nb, uint8_t lv, R* un) {
     const int b = lv & 7, par = (lv >> 3) & 1;
@@ -177,14 +239,19 @@ __device__ __forceinline__ void load_seen_lv(const DevArrays<R>& d, int tick, in
     const int j = tick >> sh;
     const int rem = tick & ((1 << sh) - 1);
     const int nw = par ^ ((j + (rem ? 1 : 0)) & 1);
-    const R* sn = (nw ? d.V1 : d.V0) + (size_t)nb * NP;
-    const R* so = (nw ? d.V0 : d.V1) + (size_t)nb * NP;
-    const R th = R(rem) / R(1 << sh);
+    ld_vec<R, NP>((nw ? d.V1 : d.V0) + (size_t)nb * NP, un);
+    if (rem) {
+        R so[NP];
+        ld_vec<R, NP>((nw ? d.V0 : d.V1) + (size_t)nb * NP, so);
+        const R th = R(rem) * pow2_neg<R>(sh);
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        const R n = sn[q];
-        un[q] = rem ? so[q] + th * (n - so[q]) : n;
+        for (int q = 0; q < NP; ++q) un[q] = so[q] + th * (un[q] - so[q]);
     }
+}
+
+template <typename R, int NP>
+__device__ __forceinline__ void load_seen(const DevArrays<R>& d, int tick, int B, int nb, R* un) {
+    load_seen_lv<R, NP>(d, tick, B, nb, d.lvl[nb], un);
 }
 
 // Residual r = (A u)_e with the neighbours seen at tick `tick`.  All same-level and
@@ -304,8 +371,19 @@ struct TickArgs {
     DevArrays<R> d;
     StimArgs stim;
     double dt;         // barrier step
+    double tscale;     // dt * 2^-B: t at tick i of barrier n is (n 2^B + i) * tscale (exact)
+    double dte[8];     // dt * 2^-b per level b (exact), and the same rounded to R
+    R dteR[8];
     int tick, B;
 };
+
+// Canonical time of tick `tick` in the current barrier, ((n 2^B + i) dt) / 2^B (the
+// division by 2^B is exact, so scaling dt first gives the same value).  Evaluated only
+// where a time is needed (stimulus windows, activation times): FP64 is slow on this part.
+template <typename R>
+__device__ __forceinline__ double tick_time(const TickArgs<R>& a, int tick) {
+    return ((double)a.d.meta->nbar * (double)(1 << a.B) + (double)tick) * a.tscale;
+}
 
 // One tick of Alg. 1: every due element (a prefix of `order`) takes one forward
 // Euler step on V and one exponential/FE step on v, accumulates the RV-T indicator
@@ -316,8 +394,6 @@ __device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>&
     constexpr int N1 = S::N1, NP = S::NP;
     const DevArrays<R>& d = a.d;
     const int n_act = d.meta->nact[tick];
-    const double nt = (double)(1 << a.B);
-    const double t_i = ((double)d.meta->nbar * nt + (double)tick) * a.dt / nt;
     for (int idx = (int)gtid(); idx < n_act; idx += (int)gstride()) {
     const int e = d.order[idx];
     const uint8_t lv = d.lvl[e];
@@ -328,22 +404,20 @@ __device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>&
     R* Vd = (cur ? d.V0 : d.V1) + (size_t)e * NP;
     R* vp = d.v + (size_t)e * NP;
     R u[NP], w[NP], r[NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        u[q] = Vc[q];
-        w[q] = vp[q];
-    }
+    ld_vec<R, NP>(Vc, u);
+    ld_vec<R, NP>(vp, w);
     const uint32_t inf = d.info[e];
     const int lev = (inf >> 24) & 15;
     element_residual<R, DIM, P>(d, T, ph, tick, a.B, e, inf, lev, u, r);
 
-    const double dte_d = ldexp(a.dt, -b);
-    const R dte = (R)dte_d;
-    const double t_mid = t_i + 0.5 * dte_d;
+    const double dte_d = a.dte[b];
+    const R dte = a.dteR[b];
     R stim_old[NP], stim_mid[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) stim_old[q] = stim_mid[q] = R(0);
     if (inf & INFO_STIM) {
+        const double t_i = tick_time(a, tick);
+        const double t_mid = t_i + 0.5 * dte_d;
         for (int s = 0; s < a.stim.n; ++s) {
             const bool on_o = (a.stim.t0[s] <= t_i) && (t_i < a.stim.t1[s]);
             const bool on_m = (a.stim.t0[s] <= t_mid) && (t_mid < a.stim.t1[s]);
@@ -367,18 +441,12 @@ __device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>&
             ga[q] = ap_g(ph, u[q], w[q]);
         }
         if (b > 0) {
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                d.Ia[(size_t)e * NP + q] = Ia[q];
-                d.ga[(size_t)e * NP + q] = ga[q];
-            }
+            st_vec<R, NP>(d.Ia + (size_t)e * NP, Ia);
+            st_vec<R, NP>(d.ga + (size_t)e * NP, ga);
         }
     } else {
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            Ia[q] = d.Ia[(size_t)e * NP + q];
-            ga[q] = d.ga[(size_t)e * NP + q];
-        }
+        ld_vec<R, NP>(d.Ia + (size_t)e * NP, Ia);
+        ld_vec<R, NP>(d.ga + (size_t)e * NP, ga);
     }
     R un[NP], wn[NP];
     R term = R(0);
@@ -389,7 +457,7 @@ __device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>&
 #pragma unroll
         for (int k = 0; k < DIM; ++k) Mq *= T.w[digit<N1>(q, k)];
         const R I = ap_iion(ph, u[q], w[q]) + stim_old[q];
-        un[q] = u[q] + dte * (-r[q] / Mq - I);
+        un[q] = u[q] + dte * (-r[q] * ph.Minv[lev][q] - I);
         wn[q] = ap_step_state(ph, u[q], w[q], dte);
         const R Vm = R(0.5) * (u[q] + un[q]);
         const R wm = R(0.5) * (w[q] + wn[q]);
@@ -399,20 +467,18 @@ __device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>&
         const R av = un[q] < R(0) ? -un[q] : un[q];
         vmax = av > vmax ? av : vmax;
     }
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        Vd[q] = un[q];
-        vp[q] = wn[q];
-    }
+    st_vec<R, NP>(Vd, un);
+    st_vec<R, NP>(vp, wn);
     const double inc = dte_d * (double)term;
     d.acc[e] = (ke == 0) ? inc : d.acc[e] + inc;
     if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
-        lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, t_i, dte_d);
+        lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, tick_time(a, tick), dte_d);
     }
 }
 
 template <typename R, int DIM, int P>
 __global__ void __launch_bounds__(256) k_tick(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph) {
+    pdl_enter();
     if (a.d.meta->err) return;
     tick_work<R, DIM, P>(a, T, ph, a.tick);
 }
@@ -421,6 +487,7 @@ __global__ void __launch_bounds__(256) k_tick(const TickArgs<R> a, const Tables<
 // values; same-level and coarser neighbours are gathered before the face arithmetic.
 template <typename R, int DIM, int P>
 __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> ph) {
+    pdl_enter();
     using S = Shape<DIM, P>;
     constexpr int NP = S::NP, NF = S::NF, NSUB = S::NSUB;
     if (d.meta->err) return;
@@ -431,9 +498,9 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
         const int par = (d.lvl[e] >> 3) & 1;
         const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
         R u[NP];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) u[q] = Vc[q];
-        double acc = 0.0;
+        ld_vec<R, NP>(Vc, u);
+        // sum of the squared face jumps in the working precision (FP64 runs in FP64)
+        R acc = R(0);
         int nbf[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) nbf[f] = d.nbr[(size_t)e * NF + f];
@@ -451,8 +518,7 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const R* srcp = (((lvn[f] >> 3) & 1) ? d.V1 : d.V0) + (size_t)src[f] * NP;
-#pragma unroll
-                for (int q = 0; q < NP; ++q) un[f][q] = srcp[q];
+                ld_vec<R, NP>(srcp, un[f]);
             }
             constexpr int NT = S::NT, NREL = 1 + 2 * NSUB;
 #pragma unroll
@@ -469,7 +535,7 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
                 R fsum = R(0);
 #pragma unroll
                 for (int t = 0; t < NT; ++t) fsum += j[t] * j[t];
-                acc += (double)fsum;
+                acc += fsum;
             }
         } else {
 #pragma unroll
@@ -484,7 +550,7 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
 #pragma unroll
                 for (int q = 0; q < NP; ++q) un[q] = src[q];
                 const int pos = (inf >> (4 * f + 2)) & 3;
-                acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
+                acc += (R)face_kelly<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
                                              kind == 1 ? -1 : pos, un, lev);
             }
         }
@@ -511,13 +577,13 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
                     R fsum = R(0);
 #pragma unroll
                     for (int t = 0; t < NT; ++t) fsum += j[t] * j[t];
-                    acc += (double)fsum;
+                    acc += fsum;
                 } else {
-                    acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
+                    acc += (R)face_kelly<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
                 }
             }
         }
-        d.eta_s[e] = sqrt(acc);
+        d.eta_s[e] = (double)sqrt(acc);
     }
 }
 
@@ -525,7 +591,8 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
 // check, per-block partial sums of int V = sum_q M_q V_q (FP64).
 template <typename R, int DIM, int P>
 __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const double* __restrict__ mtab,
-                                                 double dt) {
+                                                 double dt, float inv_dtf) {
+    pdl_enter();
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
     __shared__ double red[256];
@@ -534,7 +601,9 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const do
     double loc = 0.0;
     bool bad = false;
     for (int64_t e = gtid(); e < ne; e += gstride()) {
-        d.eta_t[e] = sqrt(d.acc[e]) / dt;
+        // eta^t = sqrt(acc) / dt; FP32 runs take the root in FP32 (FP64 is slow on this part)
+        if constexpr (sizeof(R) == 4) d.eta_t[e] = (double)(sqrtf((float)d.acc[e]) * inv_dtf);
+        else d.eta_t[e] = sqrt(d.acc[e]) / dt;
         uint8_t lv = d.lvl[e];
         if ((lv & 7) == 0) {
             lv ^= 8;
@@ -598,6 +667,7 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const do
 // Same arithmetic per element as k_tick for Q1, G times more threads in flight.
 template <typename R, int DIM>
 __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const Phys<R> ph, const Tables<R> T) {
+    pdl_enter();
     using S = Shape<DIM, 1>;
     constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB, NREL = 1 + 2 * NSUB;
     constexpr int G = NP;
@@ -605,8 +675,6 @@ __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const P
     if (d.meta->err) return;
     const int tick = a.tick;
     const int n_act = d.meta->nact[tick];
-    const double nt = (double)(1 << a.B);
-    const double t_i = ((double)d.meta->nbar * nt + (double)tick) * a.dt / nt;
     const int lane = threadIdx.x & 31;
     const int g = lane % G;
     const unsigned gmask = ((1u << G) - 1u) << (lane - g);
@@ -659,11 +727,12 @@ __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const P
 #pragma unroll
             for (int j = 0; j < NP; ++j) rg += __ldg(Av + j) * u[j];
         }
-        const double dte_d = ldexp(a.dt, -b);
-        const R dte = (R)dte_d;
-        const double t_mid = t_i + 0.5 * dte_d;
+        const double dte_d = a.dte[b];
+        const R dte = a.dteR[b];
         R stim_o = R(0), stim_m = R(0);
         if (inf & INFO_STIM) {
+            const double t_i = tick_time(a, tick);
+            const double t_mid = t_i + 0.5 * dte_d;
             for (int s = 0; s < a.stim.n; ++s) {
                 const bool on_o = (a.stim.t0[s] <= t_i) && (t_i < a.stim.t1[s]);
                 const bool on_m = (a.stim.t0[s] <= t_mid) && (t_mid < a.stim.t1[s]);
@@ -690,7 +759,7 @@ __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const P
 #pragma unroll
         for (int k = 0; k < DIM; ++k) Mq *= T.w[digit<N1>(g, k)];
         const R I = ap_iion(ph, my_u, my_w) + stim_o;
-        const R un_g = my_u + dte * (-rg / Mq - I);
+        const R un_g = my_u + dte * (-rg * ph.Minv[lev][g] - I);
         const R wn_g = ap_step_state(ph, my_u, my_w, dte);
         const R Vm = R(0.5) * (my_u + un_g);
         const R wm = R(0.5) * (my_w + wn_g);
@@ -714,7 +783,7 @@ __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const P
             R unv[NP];
 #pragma unroll
             for (int q = 0; q < NP; ++q) unv[q] = __shfl_sync(gmask, un_g, q, G);
-            if (g == 0) lat_check<R, DIM, 1>(d, T, ph, e, inf, lev, u, unv, t_i, dte_d);
+            if (g == 0) lat_check<R, DIM, 1>(d, T, ph, e, inf, lev, u, unv, tick_time(a, tick), dte_d);
         }
     }
 }
@@ -741,7 +810,8 @@ __global__ void __launch_bounds__(256) k_sweep(const TickArgs<R> a, const Tables
     double loc = 0.0;
     bool bad = false;
     for (int64_t e = gtid(); e < ne; e += gstride()) {
-        d.eta_t[e] = sqrt(d.acc[e]) / a.dt;
+        if constexpr (sizeof(R) == 4) d.eta_t[e] = (double)(sqrtf((float)d.acc[e]) * (float)(1.0 / a.dt));
+        else d.eta_t[e] = sqrt(d.acc[e]) / a.dt;
         uint8_t lv = d.lvl[e];
         if ((lv & 7) == 0) {
             lv ^= 8;
@@ -817,6 +887,7 @@ __global__ void k_scatter_initial(DevArrays<R> d, int64_t ne, const double* V, c
 template <typename R, int DIM, int P>
 __global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> ph, double t, int mark_now,
                               int force) {
+    pdl_enter();
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
     if (d.meta->err || !(force || d.meta->changed)) return;
@@ -866,6 +937,7 @@ __global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> p
 template <typename R, int DIM, int P>
 __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* pkind, const int32_t* psrc,
                            const int8_t* pbits, const Tables<R> T) {
+    pdl_enter();
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP, NC = 1 << DIM;
     if (n.meta->err) return;

@@ -111,6 +111,14 @@ void make_phys(const mdl_problem& pb, const Tables<double>& T, Phys<double>* ph)
             ph->Wface[l][k] = wf;
         }
     }
+    const int n1 = pb.order + 1;
+    for (int l = 0; l < 8; ++l)
+        for (int q = 0; q < 27; ++q) {
+            double m = ph->Wvol[l];
+            int r = q;
+            for (int k = 0; k < d; ++k, r /= n1) m *= T.w[r % n1];
+            ph->Minv[l][q] = 1.0 / m;
+        }
     ph->ionic = pb.ionic_model;
     ph->integrator = pb.state_integrator;
     ph->k = pb.ionic_params[0];
@@ -160,6 +168,7 @@ void convert_phys(const Phys<double>& a, Phys<R>* b) {
     b->gamma = (R)a.gamma;
     for (int l = 0; l < 8; ++l) {
         b->Wvol[l] = (R)a.Wvol[l];
+        for (int q = 0; q < 27; ++q) b->Minv[l][q] = (R)a.Minv[l][q];
         for (int k = 0; k < 3; ++k) {
             b->h[l][k] = (R)a.h[l][k];
             b->h2[l][k] = (R)a.h2[l][k];
