@@ -171,6 +171,9 @@ def run_ours(args, rank, world):
     prob = factory()
     sim = make_sim(prob)
     sim.set_sweep_variant(SWEEPS[args.sweep])
+    if args.tick_shape:
+        t, k = (int(x) for x in args.tick_shape.split(","))
+        sim.set_tick_shape(t, k)
     X = node_coords_of(sim, prob)
     if prob.dim == 2:
         V0, v0 = W.front_state(X, FRONT["origin"], FRONT["radius"], FRONT["width"], FRONT["tail"])
@@ -236,6 +239,7 @@ def run_ours(args, rank, world):
             "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(prob), "sweep": args.sweep,
+                       "tick_shape": args.tick_shape or "128,16",
                        "domain_cm": list(prob.extent[:prob.dim]), "base": list(prob.base[:prob.dim]),
                        "max_refine": prob.max_refine, "n_lts_levels": prob.n_lts_levels,
                        "dt_barrier_ms": sim.dt, "n_elements": n_e, "n_dof": n_dof,
@@ -511,6 +515,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="slab2d", choices=sorted(WORKLOADS) + ["batch64", "serve"])
     ap.add_argument("--serve-round", type=int, default=16, help="barriers per slot per serving round")
+    ap.add_argument("--tick-shape", default="", help="sweep launch shape 'threads,blocks_per_sm'")
     ap.add_argument("--sweep", default="thread", choices=sorted(SWEEPS),
                     help="sweep kernel variant (thread per element; group: Q1 lanes per element; "
                          "coop: one cooperative launch per barrier)")

@@ -156,6 +156,11 @@ class Ctx : public CtxBase {
     // for the predecessor to complete (its writes visible) before touching any data.
     template <typename... KP, typename... Args>
     cudaError_t launch_k(void (*k)(KP...), int grid, int block, Args&&... args) {
+        return launch_kx(pdl, k, grid, block, std::forward<Args>(args)...);
+    }
+
+    template <typename... KP, typename... Args>
+    cudaError_t launch_kx(bool overlap, void (*k)(KP...), int grid, int block, Args&&... args) {
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3((unsigned)grid);
         cfg.blockDim = dim3((unsigned)block);
@@ -163,7 +168,7 @@ class Ctx : public CtxBase {
         cfg.stream = st;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+        at[0].val.programmaticStreamSerializationAllowed = overlap ? 1 : 0;
         cfg.attrs = at;
         cfg.numAttrs = 1;
         return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
@@ -455,16 +460,21 @@ class Ctx : public CtxBase {
                 ta.tick = i;
                 if constexpr (P == 1) {
                     if (group_tick) MDL_CK(launch_k((k_tick_group<R, DIM>), gt, tick_threads, ta, ph, T));
-                    else MDL_CK(launch_k((k_tick<R, DIM, P>), gt, tick_threads, ta, T, ph));
+                    else MDL_CK(launch_kx(pdl && i > 0, (k_tick<R, DIM, P>), gt, tick_threads, ta, T, ph));
                 } else {
-                    MDL_CK(launch_k((k_tick<R, DIM, P>), gt, tick_threads, ta, T, ph));
+                    MDL_CK(launch_kx(pdl && i > 0, (k_tick<R, DIM, P>), gt, tick_threads, ta, T, ph));
                 }
                 MDL_LAUNCHED();
                 stats.tick_launches++;
             }
             return MDL_OK;
         }
-        MDL_CK(launch_k((k_epilogue<R, DIM, P>), g256, 256, arrays(o), mtab.p, dt, (float)(1.0 / dt)));
+        {
+            int ex = 0;
+            const double fr = frexp(dt, &ex);
+            MDL_CK(launch_k((k_epilogue<R, DIM, P>), g256, 256, arrays(o), mtab.p, dt, 1.0 / dt,
+                            fr == 0.5 ? 1 : 0));
+        }
         MDL_LAUNCHED();
         return MDL_OK;
     }

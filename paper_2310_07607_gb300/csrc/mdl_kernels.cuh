@@ -385,30 +385,134 @@ __device__ __forceinline__ double tick_time(const TickArgs<R>& a, int tick) {
     return ((double)a.d.meta->nbar * (double)(1 << a.B) + (double)tick) * a.tscale;
 }
 
-// One tick of Alg. 1: every due element (a prefix of `order`) takes one forward
-// Euler step on V and one exponential/FE step on v, accumulates the RV-T indicator
-// and checks its probes for activation.
+// Per-element data that stays fixed during a sweep: the element, its level byte and face
+// info, its face neighbours and (Q1) their level bytes.  A tick reads it before waiting for
+// the previous tick (programmatic dependent launch), so after the wait only the values are
+// loaded, all at once.  (info's probe-pending bit may be cleared by an earlier tick of the
+// sweep; a stale bit only repeats a probe check that finds nothing left to do.)
+template <int NF, bool NB>
+struct TickMeta {
+    int e;
+    uint32_t inf;
+    uint8_t lv;
+    int nbf[NF];
+    uint8_t lvn[NF];
+};
+// Q2: the neighbours are read face by face inside the residual (holding them would spill)
+template <int NF>
+struct TickMeta<NF, false> {
+    int e;
+    uint32_t inf;
+    uint8_t lv;
+};
+template <int DIM, int P>
+using TickMetaT = TickMeta<2 * DIM, P == 1>;
+
 template <typename R, int DIM, int P>
-__device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>& T, const Phys<R>& ph, int tick) {
+__device__ __forceinline__ void tick_fetch(const DevArrays<R>& d, int idx, TickMetaT<DIM, P>& m) {
+    constexpr int NF = 2 * DIM;
+    m.e = d.order[idx];
+    m.lv = d.lvl[m.e];
+    m.inf = d.info[m.e];
+    if constexpr (P != 1) {
+    } else if constexpr (DIM == 2) {
+        const int4 n = *reinterpret_cast<const int4*>(d.nbr + (size_t)m.e * 4);
+        m.nbf[0] = n.x; m.nbf[1] = n.y; m.nbf[2] = n.z; m.nbf[3] = n.w;
+    } else {
+#pragma unroll
+        for (int f = 0; f < NF; f += 2) {
+            const int2 n = *reinterpret_cast<const int2*>(d.nbr + (size_t)m.e * NF + f);
+            m.nbf[f] = n.x;
+            m.nbf[f + 1] = n.y;
+        }
+    }
+    if constexpr (P == 1) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const int kind = (m.inf >> (4 * f)) & 3;
+            m.lvn[f] = d.lvl[(kind == 1 || kind == 2) ? m.nbf[f] : m.e];
+        }
+    }
+}
+
+// Q1 residual r = (A u)_e from the class blocks, with the face neighbours and their level
+// bytes already known: r = A_vol u + sum_f (A_own u + A_nb u_nb); hanging faces after.
+template <typename R, int DIM>
+__device__ __forceinline__ void residual_q1(const DevArrays<R>& d, int tick, int B, const TickMetaT<DIM, 1>& m,
+                                            int lev, const R* u, R* r) {
+    using S = Shape<DIM, 1>;
+    constexpr int NP = S::NP, NF = S::NF, NSUB = S::NSUB, NREL = 1 + 2 * NSUB;
+    R un[NF][NP];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const int kind = (m.inf >> (4 * f)) & 3;
+        load_seen_lv<R, NP>(d, tick, B, (kind == 1 || kind == 2) ? m.nbf[f] : m.e, m.lvn[f], un[f]);
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r[q] = R(0);
+    block_mv<R, NP>(d.qvol + (size_t)lev * NP * NP, u, r);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const int kind = (m.inf >> (4 * f)) & 3;
+        if (kind == 1 || kind == 2) {
+            const int rel = kind == 1 ? 0 : 1 + ((m.inf >> (4 * f + 2)) & 3);
+            const R* A = d.qface + ((((size_t)f * 8 + lev) * NREL + rel) * 2) * NP * NP;
+            block_mv<R, NP>(A, u, r);
+            block_mv<R, NP>(A + NP * NP, un[f], r);
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const int kind = (m.inf >> (4 * f)) & 3;
+        if (kind != 3) continue;
+        for (int sb = 0; sb < NSUB; ++sb) {
+            R uh[NP];
+            load_seen<R, NP>(d, tick, B, d.hang[m.nbf[f] + sb], uh);
+            const R* A = d.qface + ((((size_t)f * 8 + lev) * NREL + 1 + NSUB + sb) * 2) * NP * NP;
+            block_mv<R, NP>(A, u, r);
+            block_mv<R, NP>(A + NP * NP, uh, r);
+        }
+    }
+}
+
+// One element step of Alg. 1 at tick `tick`: forward Euler on V, exponential/FE step on
+// v, the RV-T accumulation and the element's probe check.
+template <typename R, int DIM, int P>
+__device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>& T, const Phys<R>& ph, int tick,
+                                          const TickMetaT<DIM, P>& m) {
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
     const DevArrays<R>& d = a.d;
-    const int n_act = d.meta->nact[tick];
-    for (int idx = (int)gtid(); idx < n_act; idx += (int)gstride()) {
-    const int e = d.order[idx];
-    const uint8_t lv = d.lvl[e];
-    const int b = lv & 7, par = (lv >> 3) & 1;
+    const int e = m.e;
+    const uint32_t inf = m.inf;
+    const int b = m.lv & 7, par = (m.lv >> 3) & 1;
     const int ke = tick >> (a.B - b);
     const int cur = par ^ (ke & 1);
+    const int lev = (inf >> 24) & 15;
     const R* Vc = (cur ? d.V1 : d.V0) + (size_t)e * NP;
     R* Vd = (cur ? d.V0 : d.V1) + (size_t)e * NP;
     R* vp = d.v + (size_t)e * NP;
-    R u[NP], w[NP], r[NP];
+    // every value this step needs is addressed by now: issue the loads together
+    R u[NP], w[NP], r[NP], Ia[NP], ga[NP];
     ld_vec<R, NP>(Vc, u);
     ld_vec<R, NP>(vp, w);
-    const uint32_t inf = d.info[e];
-    const int lev = (inf >> 24) & 15;
-    element_residual<R, DIM, P>(d, T, ph, tick, a.B, e, inf, lev, u, r);
+    double acc0 = 0.0;
+    if constexpr (P == 1) {
+        if (ke != 0) {
+            ld_vec<R, NP>(d.Ia + (size_t)e * NP, Ia);
+            ld_vec<R, NP>(d.ga + (size_t)e * NP, ga);
+            acc0 = d.acc[e];
+        }
+        residual_q1<R, DIM>(d, tick, a.B, m, lev, u, r);
+    } else {
+        // Q2: the barrier-start terms are loaded after the residual (register pressure)
+        element_residual<R, DIM, P>(d, T, ph, tick, a.B, e, inf, lev, u, r);
+        if (ke != 0) {
+            ld_vec<R, NP>(d.Ia + (size_t)e * NP, Ia);
+            ld_vec<R, NP>(d.ga + (size_t)e * NP, ga);
+            acc0 = d.acc[e];
+        }
+    }
 
     const double dte_d = a.dte[b];
     const R dte = a.dteR[b];
@@ -422,18 +526,17 @@ __device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>&
             const bool on_o = (a.stim.t0[s] <= t_i) && (t_i < a.stim.t1[s]);
             const bool on_m = (a.stim.t0[s] <= t_mid) && (t_mid < a.stim.t1[s]);
             if (!on_o && !on_m) continue;
-            const uint32_t m = d.smask[s][e];
+            const uint32_t msk = d.smask[s][e];
             const R amp = (R)a.stim.amp[s];
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                if ((m >> q) & 1u) {
+                if ((msk >> q) & 1u) {
                     if (on_o) stim_old[q] -= amp;
                     if (on_m) stim_mid[q] -= amp;
                 }
             }
         }
     }
-    R Ia[NP], ga[NP];
     if (ke == 0) {
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
@@ -444,9 +547,6 @@ __device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>&
             st_vec<R, NP>(d.Ia + (size_t)e * NP, Ia);
             st_vec<R, NP>(d.ga + (size_t)e * NP, ga);
         }
-    } else {
-        ld_vec<R, NP>(d.Ia + (size_t)e * NP, Ia);
-        ld_vec<R, NP>(d.ga + (size_t)e * NP, ga);
     }
     R un[NP], wn[NP];
     R term = R(0);
@@ -469,18 +569,38 @@ __device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>&
     }
     st_vec<R, NP>(Vd, un);
     st_vec<R, NP>(vp, wn);
-    const double inc = dte_d * (double)term;
-    d.acc[e] = (ke == 0) ? inc : d.acc[e] + inc;
+    d.acc[e] = acc0 + dte_d * (double)term;
     if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
         lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, tick_time(a, tick), dte_d);
+}
+
+// One tick of Alg. 1 over the due elements (a prefix of `order`), for callers that
+// already waited for the previous tick.
+template <typename R, int DIM, int P>
+__device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>& T, const Phys<R>& ph, int tick) {
+    const int n_act = a.d.meta->nact[tick];
+    for (int idx = (int)gtid(); idx < n_act; idx += (int)gstride()) {
+        TickMetaT<DIM, P> m;
+        tick_fetch<R, DIM, P>(a.d, idx, m);
+        tick_elem<R, DIM, P>(a, T, ph, tick, m);
     }
 }
 
 template <typename R, int DIM, int P>
 __global__ void __launch_bounds__(256) k_tick(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph) {
+    // the due count and the first element's metadata are fixed during the sweep: read them
+    // while the previous tick drains, then wait for its values (the first tick of a sweep
+    // is launched without overlap, after the ordering that writes them)
+    const int n_act = a.d.meta->nact[a.tick];
+    const int idx0 = (int)gtid();
+    TickMetaT<DIM, P> m;
+    if (idx0 < n_act) tick_fetch<R, DIM, P>(a.d, idx0, m);
     pdl_enter();
     if (a.d.meta->err) return;
-    tick_work<R, DIM, P>(a, T, ph, a.tick);
+    for (int idx = idx0; idx < n_act; idx += (int)gstride()) {
+        if (idx != idx0) tick_fetch<R, DIM, P>(a.d, idx, m);
+        tick_elem<R, DIM, P>(a, T, ph, a.tick, m);
+    }
 }
 
 // Kelly-type spatial indicator per element (Eq. dg-error-estimate) on the barrier-start
@@ -499,8 +619,9 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
         const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
         R u[NP];
         ld_vec<R, NP>(Vc, u);
-        // sum of the squared face jumps in the working precision (FP64 runs in FP64)
-        R acc = R(0);
+        // squared face jumps in the working precision, summed in FP64 (the indicator decides
+        // refinement, so its reduction keeps FP64 as on the host)
+        double acc = 0.0;
         int nbf[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) nbf[f] = d.nbr[(size_t)e * NF + f];
@@ -535,7 +656,7 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
                 R fsum = R(0);
 #pragma unroll
                 for (int t = 0; t < NT; ++t) fsum += j[t] * j[t];
-                acc += fsum;
+                acc += (double)fsum;
             }
         } else {
 #pragma unroll
@@ -550,7 +671,7 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
 #pragma unroll
                 for (int q = 0; q < NP; ++q) un[q] = src[q];
                 const int pos = (inf >> (4 * f + 2)) & 3;
-                acc += (R)face_kelly<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
+                acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
                                              kind == 1 ? -1 : pos, un, lev);
             }
         }
@@ -577,13 +698,13 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
                     R fsum = R(0);
 #pragma unroll
                     for (int t = 0; t < NT; ++t) fsum += j[t] * j[t];
-                    acc += fsum;
+                    acc += (double)fsum;
                 } else {
-                    acc += (R)face_kelly<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
+                    acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
                 }
             }
         }
-        d.eta_s[e] = (double)sqrt(acc);
+        d.eta_s[e] = sqrt(acc);
     }
 }
 
@@ -591,7 +712,7 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
 // check, per-block partial sums of int V = sum_q M_q V_q (FP64).
 template <typename R, int DIM, int P>
 __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const double* __restrict__ mtab,
-                                                 double dt, float inv_dtf) {
+                                                 double dt, double inv_dt, int inv_dt_exact) {
     pdl_enter();
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
@@ -601,9 +722,9 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const do
     double loc = 0.0;
     bool bad = false;
     for (int64_t e = gtid(); e < ne; e += gstride()) {
-        // eta^t = sqrt(acc) / dt; FP32 runs take the root in FP32 (FP64 is slow on this part)
-        if constexpr (sizeof(R) == 4) d.eta_t[e] = (double)(sqrtf((float)d.acc[e]) * inv_dtf);
-        else d.eta_t[e] = sqrt(d.acc[e]) / dt;
+        // eta^t = sqrt(acc) / dt in FP64 (it sets b^cell); the product with 1/dt equals the
+        // quotient whenever dt is a power of two, as the automatic barrier step is
+        d.eta_t[e] = inv_dt_exact ? sqrt(d.acc[e]) * inv_dt : sqrt(d.acc[e]) / dt;
         uint8_t lv = d.lvl[e];
         if ((lv & 7) == 0) {
             lv ^= 8;
@@ -810,8 +931,7 @@ __global__ void __launch_bounds__(256) k_sweep(const TickArgs<R> a, const Tables
     double loc = 0.0;
     bool bad = false;
     for (int64_t e = gtid(); e < ne; e += gstride()) {
-        if constexpr (sizeof(R) == 4) d.eta_t[e] = (double)(sqrtf((float)d.acc[e]) * (float)(1.0 / a.dt));
-        else d.eta_t[e] = sqrt(d.acc[e]) / a.dt;
+        d.eta_t[e] = sqrt(d.acc[e]) / a.dt;
         uint8_t lv = d.lvl[e];
         if ((lv & 7) == 0) {
             lv ^= 8;
