@@ -333,3 +333,52 @@ def test_eta_s_kink_closed_form(dim):
         cx = lf[1][0]
         expect = ref if cx in (n // 2 - 1, n // 2) else 0.0
         assert abs(es[e] - expect) <= 1e-12 * ref + 1e-18
+
+
+# --------------------------------------------------------------------------
+# Statements of the paper (tests/golden/paper_statements.json).
+# --------------------------------------------------------------------------
+
+def paper_statements():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_statements.json")) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2), (3, 1)])
+def test_refinement_divides_cfl_by_four(dim, p):
+    """Sec. 2.3: one refinement divides the stable step by about 4 (CFL_e ~ h^2 on box meshes)."""
+    g = paper_statements()["cfl_refinement_ratio"]
+    prob = make_prob(dim, p, (3, 3, 3), (1.0, 1.0, 1.0), D_iso=1.0)
+    f = Forest(dim, prob.base, 3, prob.extent)
+    # the interior element of the base grid, and of the uniformly refined grid
+    c0 = Disc(prob, f).cfl()
+    f1, _ = f.adapt(np.ones(f.n), 0.5, -1.0)
+    c1 = Disc(prob, f1).cfl()
+    ratio = c0.min() / c1.min()
+    assert abs(ratio - g["value"]) <= g["rel_tol"] * g["value"]
+
+
+def test_larger_penalty_lowers_cfl_bound():
+    """Sec. 3.3: gamma = 8 decreases the CFL bound relative to gamma = 4."""
+    g = paper_statements()["penalty_reference"]["value"]
+    cfls = []
+    for gamma in (g, 2 * g):
+        prob = make_prob(2, 1, (4, 4, 1), (1.0, 1.0, 1.0), gamma=gamma)
+        cfls.append(Disc(prob, Forest(2, prob.base, 3, prob.extent)).cfl().min())
+    assert cfls[1] < cfls[0]
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2)])
+def test_small_penalty_loses_semidefiniteness(dim, p):
+    """Sec. 3.3: penalties << 4 are unstable; the SIPG operator then has a negative eigenvalue,
+    while at gamma = 4 it is positive semi-definite."""
+    st = paper_statements()["penalty_unstable_below"]
+    lam = {}
+    for gamma in (st["value"], st["factor"] * st["value"]):
+        prob = make_prob(dim, p, (3, 3, 1), (1.0, 1.0, 1.0), gamma=gamma)
+        A = Disc(prob, Forest(dim, prob.base, 3, prob.extent)).assemble().toarray()
+        lam[gamma] = np.linalg.eigvalsh(0.5 * (A + A.T)).min() / np.abs(A).max()
+    assert lam[st["value"]] >= -1e-12
+    assert lam[st["factor"] * st["value"]] < -1e-6
