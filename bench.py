@@ -46,6 +46,14 @@ WORKLOADS = {
     "slab3d": (W.slab_3d_q2, 17.6, "<float,3,2>"),
 }
 SETUP_BARRIERS = 5
+# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum)
+# from one ncu capture of the same build, averaged over the launches of a barrier step in
+# their proportion (tick 0 once, the finer ticks 7 times).  ncu replays each launch with
+# cold caches, so this is an upper bound on the live traffic.  Set to None whenever the
+# kernel changes until it is captured again.
+TRAFFIC_PER_LAUNCH = {
+    "k_tick<float,2,1>": (7.776768e6 + 7 * 5.551104e6) / 8.0,
+}
 # Algorithmic bytes per DOF-update of the fused sweep (Q1 2D, FP32, AP): V_old 4 + v 4 +
 # V_new 4 + v 4 = 16 B, plus per element step 2d neighbour ids + 4 B level/flags + the FP64
 # RV-T accumulator read-modify-write (36 B) over (p+1)^d = 4 DOFs.
@@ -225,8 +233,10 @@ def run_ours(args, rank, world):
     sweep_s = st["sweep_ms"] / 1e3
     alg_bytes = st["dof_updates"] * alg_bytes
     achieved = alg_bytes / sweep_s / 1e9 if sweep_s > 0 else 0.0
+    traffic = TRAFFIC_PER_LAUNCH.get(kname) if args.sweep == "thread" and not args.tick_shape else None
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+            "alg_bytes_per_launch": round(alg_bytes / max(st["tick_launches"], 1), 1),
             "kernel": kname, "launches": st["tick_launches"],
             "avg_launch_us": round(st["sweep_ms"] * 1e3 / max(st["tick_launches"], 1), 3),
             "alg_bytes_per_dof_update": WORKLOADS[args.workload][1]}
