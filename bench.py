@@ -125,7 +125,7 @@ class ClockSampler:
         return out
 
 
-SWEEPS = {"thread": 0, "group": 1, "coop": 2}
+SWEEPS = {"thread": 0, "group": 1, "coop": 2, "tensor": 3}
 
 
 def prob_order(factory):
@@ -133,9 +133,10 @@ def prob_order(factory):
 
 
 def workload_name(prob):
+    b = prob.base
     if prob.dim == 2:
-        return "slab2d_q1_256x256_amr3_lts4_ap_fp32"
-    return "slab3d_q2_128x48x20_amr3_lts4_ap_fp32"
+        return "slab2d_q1_%dx%d_amr3_lts4_ap_fp32" % (b[0], b[1])
+    return "slab3d_q2_%dx%dx%d_amr3_lts4_ap_fp32" % (b[0], b[1], b[2])
 
 
 def make_sim(prob):
@@ -174,19 +175,26 @@ def run_ours(args, rank, world):
     factory, alg_bytes, kname = WORKLOADS[args.workload]
     if args.sweep == "group" and prob_order(factory) == 1:
         kname = "k_tick_group" + kname.replace(",1>", ">")
+    elif args.sweep == "tensor" or (args.sweep == "default" and factory().order == 2 and factory().dim == 3):
+        kname = "k_tick_tc<3,2>"
     else:
         kname = ("k_sweep" if args.sweep == "coop" else "k_tick") + kname
     prob = factory()
+    if args.base:
+        prob = W.scaled(prob, tuple(int(x) for x in args.base.split(",")) + ((1,) if prob.dim == 2 else ()))
     sim = make_sim(prob)
-    sim.set_sweep_variant(SWEEPS[args.sweep])
+    if args.sweep != "default":
+        sim.set_sweep_variant(SWEEPS[args.sweep])
     if args.tick_shape:
         t, k = (int(x) for x in args.tick_shape.split(","))
         sim.set_tick_shape(t, k)
     X = node_coords_of(sim, prob)
     if prob.dim == 2:
-        V0, v0 = W.front_state(X, FRONT["origin"], FRONT["radius"], FRONT["width"], FRONT["tail"])
+        # a scaled base keeps the front at the same fraction of the domain
+        V0, v0 = W.front_state(X, FRONT["origin"], FRONT["radius"] * prob.extent[0] / 2.0, FRONT["width"],
+                               FRONT["tail"])
     else:
-        V0, v0 = W.planar_front_state(X, PLANAR["x0"], PLANAR["width"], PLANAR["tail"])
+        V0, v0 = W.planar_front_state(X, PLANAR["x0"] * prob.extent[0] / 2.0, PLANAR["width"], PLANAR["tail"])
     sim.set_initial(V0, v0)
     sim.step_barriers(SETUP_BARRIERS)
     sim.step_barriers(args.warmup)
@@ -233,7 +241,7 @@ def run_ours(args, rank, world):
     sweep_s = st["sweep_ms"] / 1e3
     alg_bytes = st["dof_updates"] * alg_bytes
     achieved = alg_bytes / sweep_s / 1e9 if sweep_s > 0 else 0.0
-    traffic = TRAFFIC_PER_LAUNCH.get(kname) if args.sweep == "thread" and not args.tick_shape else None
+    traffic = TRAFFIC_PER_LAUNCH.get(kname) if args.sweep in ("default", "thread") and not args.tick_shape else None
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
             "alg_bytes_per_launch": round(alg_bytes / max(st["tick_launches"], 1), 1),
@@ -248,7 +256,8 @@ def run_ours(args, rank, world):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(prob), "sweep": args.sweep,
+            "config": {"workload": workload_name(prob),
+                       "sweep": args.sweep if args.sweep != "default" else ("tensor" if "k_tick_tc" in kname else "thread"),
                        "tick_shape": args.tick_shape or "128,16",
                        "domain_cm": list(prob.extent[:prob.dim]), "base": list(prob.base[:prob.dim]),
                        "max_refine": prob.max_refine, "n_lts_levels": prob.n_lts_levels,
@@ -526,9 +535,11 @@ def main():
     ap.add_argument("--workload", default="slab2d", choices=sorted(WORKLOADS) + ["batch64", "serve"])
     ap.add_argument("--serve-round", type=int, default=16, help="barriers per slot per serving round")
     ap.add_argument("--tick-shape", default="", help="sweep launch shape 'threads,blocks_per_sm'")
-    ap.add_argument("--sweep", default="thread", choices=sorted(SWEEPS),
-                    help="sweep kernel variant (thread per element; group: Q1 lanes per element; "
-                         "coop: one cooperative launch per barrier)")
+    ap.add_argument("--base", default="", help="base grid 'nx,ny[,nz]' at the workload's element size")
+    ap.add_argument("--sweep", default="default", choices=["default"] + sorted(SWEEPS),
+                    help="sweep kernel variant (default: the library's choice, tensor for Q2 3D FP32 and "
+                         "thread otherwise; thread per element; group: Q1 lanes per element; coop: one "
+                         "cooperative launch per barrier; tensor: tcgen05 residual, Q2 3D FP32)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -193,19 +193,31 @@ int mdl_set_tick_shape(mdl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
 
 /* Sweep kernel variant.  All follow Alg. 1 tick by tick; THREAD and COOP give identical
  * values, GROUP sums the face terms in another order (agreement within rounding):
- *   MDL_SWEEP_THREAD  one thread per due element, one launch per tick; the default;
+ *   MDL_SWEEP_THREAD  one thread per due element, one launch per tick; the default except
+ *                     for Q2 3D FP32 contexts, whose default is MDL_SWEEP_TENSOR;
  *   MDL_SWEEP_GROUP   Q1 only: (p+1)^d lanes per element, one lane per face and per DOF,
  *                     one launch per tick (Q2 contexts use MDL_SWEEP_THREAD);
  *   MDL_SWEEP_COOP    every tick and the barrier epilogue in one cooperative launch with
- *                     grid-wide barriers between ticks.
- * Returns MDL_E_ARG for any other value. */
+ *                     grid-wide barriers between ticks;
+ *   MDL_SWEEP_TENSOR  Q2 3D FP32 contexts only: per tile of 128 due elements the SIPG
+ *                     residual of elements with same-level neighbours is one TF32
+ *                     tensor-core product (tcgen05) of the gathered element and face-
+ *                     neighbour values with the level-0 operator (Sec. 2.1: box elements,
+ *                     so every level is a power-of-two multiple of it), on values shifted
+ *                     by the element mean and with the operator split into TF32 hi and lo
+ *                     parts; other faces are added on the CUDA cores.  Agrees with THREAD
+ *                     within the FP32 tolerance, not bit for bit.  A bounded device wait
+ *                     that gives up makes the stepping call return MDL_E_TIMEOUT.
+ * Returns MDL_E_ARG for any other value, or for TENSOR on another kind of context. */
 #define MDL_SWEEP_THREAD 0
 #define MDL_SWEEP_GROUP 1
 #define MDL_SWEEP_COOP 2
+#define MDL_SWEEP_TENSOR 3
 int mdl_set_sweep_variant(mdl_ctx* ctx, int32_t variant);
 
 /* ---- Batches: many resident simulations stepped together on one GPU ----
- * (North-star batching/serving pattern; the paper runs one simulation serially.)
+ * (The paper runs one simulation at a time on one CPU core, Sec. 3; batching many
+ * resident simulations is this library's addition.)
  * Each slot is a context with its own stream; mdl_batch_step launches every unfinished
  * slot's barriers before waiting for any, so their kernels overlap on the device.
  * Admission compares the slot's device-memory footprint estimate (mdl_batch_footprint)

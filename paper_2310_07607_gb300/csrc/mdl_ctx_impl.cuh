@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <string>
 #include <utility>
+#include <type_traits>
 #include <vector>
 
 #include "mdl_amr.cuh"
@@ -33,6 +34,7 @@
 #include "mdl_kernels.cuh"
 #include "mdl_mesh.h"
 #include "mdl_tables.h"
+#include "mdl_tc.cuh"
 
 namespace mdl {
 
@@ -126,6 +128,9 @@ class Ctx : public CtxBase {
     DBuf<double> eta_t_ovr;
     DBuf<double> mtab;   // FP64 GL mass w_q det J per (level, node)
     DBuf<R> qvol, qface, qkelly;   // Q1 class blocks
+    DBuf<uint16_t> tcB;            // Q2 3D FP32: level-0 operator of the tensor-core sweep (FP16 hi/lo)
+    float tc_unscale = 1.0f;       // 2^-t: undoes the scaling of the operator by 2^t
+    DBuf<float> tcC;               // Q2 3D FP32: level-0 correction blocks of non-regular faces
     DBuf<DevMeta> meta;
     DevMeta* hmeta = nullptr;
     bool ovr_levels = false, ovr_eta_s = false, ovr_eta_t = false;
@@ -146,6 +151,7 @@ class Ctx : public CtxBase {
     int tick_threads = 128, tick_bpsm = 16;   // sweep launch shape
     bool coop_sweep = false;                  // ticks + epilogue in one cooperative launch
     bool group_tick = false;                  // Q1: a group of (p+1)^d lanes per element
+    bool tensor_tick = false;                 // Q2 3D FP32: element residual on the tensor cores
     bool pdl = true;                          // programmatic dependent launch between kernels
     int64_t inflight = 0, inflight_start = 0; // barriers launched by begin_barriers
 
@@ -161,10 +167,15 @@ class Ctx : public CtxBase {
 
     template <typename... KP, typename... Args>
     cudaError_t launch_kx(bool overlap, void (*k)(KP...), int grid, int block, Args&&... args) {
+        return launch_kxs(overlap, 0, k, grid, block, std::forward<Args>(args)...);
+    }
+
+    template <typename... KP, typename... Args>
+    cudaError_t launch_kxs(bool overlap, size_t dyn_smem, void (*k)(KP...), int grid, int block, Args&&... args) {
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3((unsigned)grid);
         cfg.blockDim = dim3((unsigned)block);
-        cfg.dynamicSmemBytes = 0;
+        cfg.dynamicSmemBytes = dyn_smem;
         cfg.stream = st;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -178,6 +189,8 @@ class Ctx : public CtxBase {
         const int64_t need = div_up(std::max<int64_t>(cap, 1), threads);
         return (int)std::min<int64_t>(need, (int64_t)nsm * (2048 / threads));
     }
+
+    static constexpr bool tensor_capable = std::is_same<R, float>::value && DIM == 3 && P == 2;
 
     DevArrays<R> arrays(int s) {
         DevArrays<R> d{};
@@ -456,6 +469,19 @@ class Ctx : public CtxBase {
             const int lanes = (P == 1 && group_tick) ? NP : 1;
             const int gt = (int)std::min<int64_t>(div_up(std::max<int64_t>(cap, 1) * lanes, tick_threads),
                                                   (int64_t)nsm * tick_bpsm);
+            if constexpr (tensor_capable) {
+                if (tensor_tick) {
+                    // persistent: two CTAs per SM walk the tiles of 64 due elements
+                    for (int i = 0; i < nt; ++i) {
+                        ta.tick = i;
+                        MDL_CK(launch_kxs(pdl && i > 0, (size_t)tc::SMEM_BYTES, (k_tick_tc<DIM, P>), 2 * nsm, tc::THREADS,
+                                          ta, T, ph, (const uint16_t*)tcB.p, tc_unscale, (const float*)tcC.p));
+                        MDL_LAUNCHED();
+                        stats.tick_launches++;
+                    }
+                    return MDL_OK;
+                }
+            }
             for (int i = 0; i < nt; ++i) {
                 ta.tick = i;
                 if constexpr (P == 1) {
@@ -566,7 +592,7 @@ public:
         order.release();
         for (auto& m : smask) m.release();
         lvl_ovr.release(); eta_t_ovr.release(); meta.release(); mtab.release();
-        qvol.release(); qface.release(); qkelly.release();
+        qvol.release(); qface.release(); qkelly.release(); tcB.release(); tcC.release();
         if (hmeta) cudaFreeHost(hmeta);
         for (auto e : evpool) cudaEventDestroy(e);
         if (st) cudaStreamDestroy(st);
@@ -574,6 +600,7 @@ public:
 
     int create(const mdl_problem& p) override {
         pb = p;
+        tensor_tick = tensor_capable;   // Q2 3D FP32: the tensor-core sweep is the default
         B = pb.lts_enabled ? pb.n_lts_levels - 1 : 0;
         make_tables(P, &Td);
         make_phys(pb, Td, &phd);
@@ -652,6 +679,19 @@ public:
             MDL_CK(cudaMemcpy(qvol.p, rv.data(), rv.size() * sizeof(R), cudaMemcpyHostToDevice));
             MDL_CK(cudaMemcpy(qface.p, rf.data(), rf.size() * sizeof(R), cudaMemcpyHostToDevice));
             MDL_CK(cudaMemcpy(qkelly.p, rk.data(), rk.size() * sizeof(R), cudaMemcpyHostToDevice));
+        }
+        if constexpr (tensor_capable) {
+            std::vector<uint16_t> hb;
+            const int t = q2_tensor_blocks(Td, phd, &hb);
+            tc_unscale = (float)ldexp(1.0, -t);
+            MDL_CK(tcB.ensure(hb.size()));
+            MDL_CK(cudaMemcpy(tcB.p, hb.data(), hb.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+            std::vector<float> hc;
+            q2_correction_blocks(Td, phd, &hc);
+            MDL_CK(tcC.ensure(hc.size()));
+            MDL_CK(cudaMemcpy(tcC.p, hc.data(), hc.size() * sizeof(float), cudaMemcpyHostToDevice));
+            MDL_CK(cudaFuncSetAttribute((k_tick_tc<DIM, P>), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        tc::SMEM_BYTES));
         }
         MDL_CK(mtab.ensure(hm.size()));
         MDL_CK(cudaMemcpyAsync(mtab.p, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -787,6 +827,10 @@ public:
                 MDL_CK(cudaStreamSynchronize(st));
                 return MDL_E_CFL;
             }
+            if (e & tc::ERR_TIMEOUT) {
+                err = "a bounded wait of the tensor-core sweep gave up";
+                return MDL_E_TIMEOUT;
+            }
             if (e & ERR_MESH) {
                 err = "internal: adapted mesh is not 2:1 balanced";
                 return MDL_E_STATE;
@@ -844,6 +888,10 @@ public:
             MDL_CK(cudaStreamSynchronize(st));
             return MDL_E_CFL;
         }
+        if (e & tc::ERR_TIMEOUT) {
+            err = "a bounded wait of the tensor-core sweep gave up";
+            return MDL_E_TIMEOUT;
+        }
         if (e & ERR_MESH) {
             err = "internal: adapted mesh is not 2:1 balanced";
             return MDL_E_STATE;
@@ -866,14 +914,19 @@ public:
     }
 
     int set_sweep_variant(int variant) override {
-        if (variant < MDL_SWEEP_THREAD || variant > MDL_SWEEP_COOP) {
-            err = "set_sweep_variant: variant in {0, 1, 2}";
+        if (variant < MDL_SWEEP_THREAD || variant > MDL_SWEEP_TENSOR) {
+            err = "set_sweep_variant: variant in {0, 1, 2, 3}";
             return MDL_E_ARG;
         }
-        const bool co = variant == MDL_SWEEP_COOP, gr = variant == MDL_SWEEP_GROUP;
-        if (co != coop_sweep || gr != group_tick) {
+        if (variant == MDL_SWEEP_TENSOR && !tensor_capable) {
+            err = "set_sweep_variant: the tensor-core sweep needs a Q2 3D FP32 context";
+            return MDL_E_ARG;
+        }
+        const bool co = variant == MDL_SWEEP_COOP, gr = variant == MDL_SWEEP_GROUP, tn = variant == MDL_SWEEP_TENSOR;
+        if (co != coop_sweep || gr != group_tick || tn != tensor_tick) {
             coop_sweep = co;
             group_tick = gr;
+            tensor_tick = tn;
             drop_graphs();
         }
         return MDL_OK;

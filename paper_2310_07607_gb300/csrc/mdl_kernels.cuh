@@ -201,6 +201,22 @@ __device__ __forceinline__ float r_exp<float>(float x) { return expf(x); }
 template <>
 __device__ __forceinline__ double r_exp<double>(double x) { return exp(x); }
 
+// a / b: FP32 through the fast reciprocal (within 2 ulp; b >= 1e-6 here), FP64 exact.
+template <typename R>
+__device__ __forceinline__ R r_div(R a, R b);
+template <>
+__device__ __forceinline__ float r_div<float>(float a, float b) { return __fdividef(a, b); }
+template <>
+__device__ __forceinline__ double r_div<double>(double a, double b) { return a / b; }
+
+// e^x - 1 in FP32 without the cancellation of expf(x) - 1: for |x| < 1/16 the Taylor series
+// of the exponential through x^6 (truncation below 1e-12 relative), else expf(x) - 1.
+__device__ __forceinline__ float expm1_f32(float x) {
+    if (fabsf(x) < 0.0625f)
+        return x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f + x * (1.0f / 720.0f))))));
+    return expf(x) - 1.0f;
+}
+
 template <typename R>
 __device__ __forceinline__ R ap_iion(const Phys<R>& ph, R V, R w) {
     if (ph.ionic < 0) return R(0);
@@ -211,7 +227,7 @@ template <typename R>
 __device__ __forceinline__ R ap_eps(const Phys<R>& ph, R V, R w) {
     R den = V + ph.mu2;
     den = den > R(1e-6) ? den : R(1e-6);
-    return ph.eps0 + ph.mu1 * w / den;
+    return ph.eps0 + r_div<R>(ph.mu1 * w, den);
 }
 
 template <typename R>
@@ -221,12 +237,18 @@ __device__ __forceinline__ R ap_g(const Phys<R>& ph, R V, R w) {
     return ap_eps(ph, V, w) * (vinf - w) * ph.inv_ts;
 }
 
+// One step of the state: forward Euler, or the exponential step v_inf + (v - v_inf) e^(-eps dt)
+// with eps and v_inf frozen at the step start.  In FP32 the exponential step is evaluated as
+// v + (v - v_inf) (e^(-eps dt) - 1): on explicit substeps eps dt is far below 1 (about
+// 1e-8 .. 1e-4 for substeps of 1e-6 .. 1e-2 ms), where e^(-eps dt) rounded to FP32 would
+// lose most of the increment.
 template <typename R>
 __device__ __forceinline__ R ap_step_state(const Phys<R>& ph, R V, R w, R dt) {
     if (ph.ionic < 0) return w;
     const R vinf = -ph.k * V * (V - ph.a - R(1));
     const R eps = ap_eps(ph, V, w);
     if (ph.integrator == 0) return w + dt * eps * (vinf - w) * ph.inv_ts;
+    if constexpr (sizeof(R) == 4) return w + (w - vinf) * expm1_f32(-eps * dt * ph.inv_ts);
     return vinf + (w - vinf) * r_exp<R>(-eps * dt * ph.inv_ts);
 }
 
@@ -333,29 +355,62 @@ __device__ __forceinline__ void element_residual(const DevArrays<R>& d, const Ta
 }
 
 // Probe activation check for element e after a step from u (at t_old) to un (t_old + dte).
+// The probes inside the leaf are the root GL nodes a with pfl[lev][a_k] == the leaf's cell
+// in every direction k; a pending probe's values before and after the step are the leaf
+// polynomial at its position, evaluated by sum factorisation.
 template <typename R, int DIM, int P>
 __device__ void lat_check(const DevArrays<R>& d, const Tables<R>& T, const Phys<R>& ph, int e,
                           uint32_t inf, int lev, const R* u, const R* un, double t_old, double dte) {
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
     const uint32_t lc = d.loc[e];
-    const int lx[3] = {(int)(lc & 255u), (int)((lc >> 8) & 255u), (int)((lc >> 16) & 255u)};
     const int64_t rid = d.root[e];
-    bool pending = false;
-    for (int q = 0; q < NP; ++q) {
-        bool inside = true;
+    const int lx[3] = {(int)(lc & 255u), (int)((lc >> 8) & 255u), (int)((lc >> 16) & 255u)};
+    unsigned inside_k[3] = {1u, 1u, 1u};
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) inside = inside && (T.pfl[lev][digit<N1>(q, k)] == lx[k]);
-        if (!inside) continue;
+    for (int k = 0; k < DIM; ++k) {
+        inside_k[k] = 0u;
+#pragma unroll
+        for (int a = 0; a < N1; ++a)
+            if (T.pfl[lev][a] == lx[k]) inside_k[k] |= 1u << a;
+    }
+    uint32_t im = 0u;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        bool in = true;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) in = in && ((inside_k[k] >> digit<N1>(q, k)) & 1u);
+        if (in) im |= 1u << q;
+    }
+    bool pending = false;
+    while (im) {
+        const int q = __ffs(im) - 1;
+        im &= im - 1u;
         double* lp = d.lat + rid * NP + q;
         if (!isinf(*lp)) continue;
-        R po = 0, pn = 0;
-        for (int j = 0; j < NP; ++j) {
-            R w = R(1);
+        R Pk[3][3];
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) w *= T.pphi[lev][digit<N1>(q, k)][digit<N1>(j, k)];
-            po += w * u[j];
-            pn += w * un[j];
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < N1; ++j) Pk[k][j] = (k < DIM) ? T.pphi[lev][digit<N1>(q, k)][j] : R(1);
+        R po = 0, pn = 0;
+#pragma unroll
+        for (int j2 = 0; j2 < (DIM == 3 ? N1 : 1); ++j2) {
+            R t1o = 0, t1n = 0;
+#pragma unroll
+            for (int j1 = 0; j1 < N1; ++j1) {
+                R t0o = 0, t0n = 0;
+#pragma unroll
+                for (int j0 = 0; j0 < N1; ++j0) {
+                    const int idx = j0 + N1 * j1 + N1 * N1 * j2;
+                    t0o += Pk[0][j0] * u[idx];
+                    t0n += Pk[0][j0] * un[idx];
+                }
+                t1o += Pk[1][j1] * t0o;
+                t1n += Pk[1][j1] * t0n;
+            }
+            po += Pk[2][j2] * t1o;
+            pn += Pk[2][j2] * t1n;
         }
         if (po <= ph.act && pn > ph.act) {
             *lp = t_old + dte * (double)((ph.act - po) / (pn - po));
@@ -475,13 +530,86 @@ __device__ __forceinline__ void residual_q1(const DevArrays<R>& d, int tick, int
     }
 }
 
+// Stimulus currents of DOF q of element e at the step start (so) and at the step midpoint
+// (sm): -amplitude for every stimulus box holding the node whose window [t0, t1) holds the
+// time (the midpoint value enters the RV-T term).
+template <typename R>
+__device__ __forceinline__ void dof_stim(const TickArgs<R>& a, int e, int tick, double dte_d, int q, R& so, R& sm) {
+    so = sm = R(0);
+    const double t_i = tick_time(a, tick);
+    const double t_mid = t_i + 0.5 * dte_d;
+    for (int s = 0; s < a.stim.n; ++s) {
+        const bool on_o = (a.stim.t0[s] <= t_i) && (t_i < a.stim.t1[s]);
+        const bool on_m = (a.stim.t0[s] <= t_mid) && (t_mid < a.stim.t1[s]);
+        if (!on_o && !on_m) continue;
+        if (!((a.d.smask[s][e] >> q) & 1u)) continue;
+        const R amp = (R)a.stim.amp[s];
+        if (on_o) so -= amp;
+        if (on_m) sm -= amp;
+    }
+}
+
+// Update of one DOF given its residual r = (A u)_q, its GL mass Mq = w_q det J and the
+// inverse Minv: forward Euler on V, the exponential/FE step on v, and the DOF's share
+// Mq [dI^2 + dg^2] of the RV-T midpoint term (returned).  At the element's first step of
+// the barrier (ke == 0), Ia/ga receive I and g at the barrier start.
+template <typename R>
+__device__ __forceinline__ R dof_update(const Phys<R>& ph, R Mq, R Minv, int ke, R dte, R so, R sm, R u, R w, R r,
+                                        R& Ia, R& ga, R& un, R& wn) {
+    if (ke == 0) {
+        Ia = ap_iion(ph, u, w) + so;
+        ga = ap_g(ph, u, w);
+    }
+    const R I = ap_iion(ph, u, w) + so;
+    un = u + dte * (-r * Minv - I);
+    wn = ap_step_state(ph, u, w, dte);
+    const R Vm = R(0.5) * (u + un);
+    const R wm = R(0.5) * (w + wn);
+    const R dI = ap_iion(ph, Vm, wm) + sm - Ia;
+    const R dg = ap_g(ph, Vm, wm) - ga;
+    return Mq * (dI * dI + dg * dg);
+}
+
+// dof_update for DOF q of an element of refinement level lev (mass from the tables).
+template <typename R, int DIM, int P>
+__device__ __forceinline__ R dof_step(const Tables<R>& T, const Phys<R>& ph, int lev, int q, int ke, R dte, R so,
+                                      R sm, R u, R w, R r, R& Ia, R& ga, R& un, R& wn) {
+    constexpr int N1 = P + 1;
+    R Mq = ph.Wvol[lev];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) Mq *= T.w[digit<N1>(q, k)];
+    return dof_update<R>(ph, Mq, ph.Minv[lev][q], ke, dte, so, sm, u, w, r, Ia, ga, un, wn);
+}
+
+// Pointwise part of one element step (Alg. 1) given the residual r = (A u)_e (dof_step for
+// every DOF); returns the element's RV-T term, vmax = max_q |V_new|.
+template <typename R, int DIM, int P>
+__device__ __forceinline__ R elem_pointwise(const TickArgs<R>& a, const Tables<R>& T, const Phys<R>& ph, int tick,
+                                            int e, uint32_t inf, int b, int ke, int lev, const R* u, const R* w,
+                                            const R* r, R* Ia, R* ga, R* un, R* wn, R& vmax) {
+    constexpr int NP = Shape<DIM, P>::NP;
+    const double dte_d = a.dte[b];
+    const R dte = a.dteR[b];
+    R term = R(0);
+    vmax = R(0);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        R so = R(0), sm = R(0);
+        if (inf & INFO_STIM) dof_stim<R>(a, e, tick, dte_d, q, so, sm);
+        term += dof_step<R, DIM, P>(T, ph, lev, q, ke, dte, so, sm, u[q], w[q], r[q], Ia[q], ga[q], un[q], wn[q]);
+        const R av = un[q] < R(0) ? -un[q] : un[q];
+        vmax = av > vmax ? av : vmax;
+    }
+    return term;
+}
+
 // One element step of Alg. 1 at tick `tick`: forward Euler on V, exponential/FE step on
 // v, the RV-T accumulation and the element's probe check.
 template <typename R, int DIM, int P>
 __device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>& T, const Phys<R>& ph, int tick,
                                           const TickMetaT<DIM, P>& m) {
     using S = Shape<DIM, P>;
-    constexpr int N1 = S::N1, NP = S::NP;
+    constexpr int NP = S::NP;
     const DevArrays<R>& d = a.d;
     const int e = m.e;
     const uint32_t inf = m.inf;
@@ -514,58 +642,12 @@ __device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>&
         }
     }
 
+    R un[NP], wn[NP], vmax;
+    const R term = elem_pointwise<R, DIM, P>(a, T, ph, tick, e, inf, b, ke, lev, u, w, r, Ia, ga, un, wn, vmax);
     const double dte_d = a.dte[b];
-    const R dte = a.dteR[b];
-    R stim_old[NP], stim_mid[NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) stim_old[q] = stim_mid[q] = R(0);
-    if (inf & INFO_STIM) {
-        const double t_i = tick_time(a, tick);
-        const double t_mid = t_i + 0.5 * dte_d;
-        for (int s = 0; s < a.stim.n; ++s) {
-            const bool on_o = (a.stim.t0[s] <= t_i) && (t_i < a.stim.t1[s]);
-            const bool on_m = (a.stim.t0[s] <= t_mid) && (t_mid < a.stim.t1[s]);
-            if (!on_o && !on_m) continue;
-            const uint32_t msk = d.smask[s][e];
-            const R amp = (R)a.stim.amp[s];
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                if ((msk >> q) & 1u) {
-                    if (on_o) stim_old[q] -= amp;
-                    if (on_m) stim_mid[q] -= amp;
-                }
-            }
-        }
-    }
-    if (ke == 0) {
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            Ia[q] = ap_iion(ph, u[q], w[q]) + stim_old[q];
-            ga[q] = ap_g(ph, u[q], w[q]);
-        }
-        if (b > 0) {
-            st_vec<R, NP>(d.Ia + (size_t)e * NP, Ia);
-            st_vec<R, NP>(d.ga + (size_t)e * NP, ga);
-        }
-    }
-    R un[NP], wn[NP];
-    R term = R(0);
-    R vmax = R(0);
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        R Mq = ph.Wvol[lev];
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) Mq *= T.w[digit<N1>(q, k)];
-        const R I = ap_iion(ph, u[q], w[q]) + stim_old[q];
-        un[q] = u[q] + dte * (-r[q] * ph.Minv[lev][q] - I);
-        wn[q] = ap_step_state(ph, u[q], w[q], dte);
-        const R Vm = R(0.5) * (u[q] + un[q]);
-        const R wm = R(0.5) * (w[q] + wn[q]);
-        const R dI = ap_iion(ph, Vm, wm) + stim_mid[q] - Ia[q];
-        const R dg = ap_g(ph, Vm, wm) - ga[q];
-        term += Mq * (dI * dI + dg * dg);
-        const R av = un[q] < R(0) ? -un[q] : un[q];
-        vmax = av > vmax ? av : vmax;
+    if (ke == 0 && b > 0) {
+        st_vec<R, NP>(d.Ia + (size_t)e * NP, Ia);
+        st_vec<R, NP>(d.ga + (size_t)e * NP, ga);
     }
     st_vec<R, NP>(Vd, un);
     st_vec<R, NP>(vp, wn);

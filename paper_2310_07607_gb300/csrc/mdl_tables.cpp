@@ -2,6 +2,8 @@
 #include "mdl_tables.h"
 
 #include <math.h>
+
+#include <cmath>
 #include <string.h>
 
 #include <vector>
@@ -335,6 +337,115 @@ void q1_blocks(const Tables<double>& T, const Phys<double>& ph, int dim, int L, 
                std::vector<double>* face, std::vector<double>* kelly) {
     if (dim == 2) q1_blocks_t<2>(T, ph, L, vol, face, kelly);
     else q1_blocks_t<3>(T, ph, L, vol, face, kelly);
+}
+
+namespace {
+
+// x rounded to the nearest FP16 value (11-bit significand, subnormal spacing 2^-24),
+// ties to even; |x| must stay below 65520.
+double round_half(double x) {
+    if (x == 0.0) return 0.0;
+    int ex = 0;
+    frexp(x, &ex);                           // |x| in [2^(ex-1), 2^ex)
+    const int e = ex - 1 < -14 ? -14 : ex - 1;   // exponent of the FP16 binade (normal or subnormal)
+    return ldexp(nearbyint(ldexp(x, 10 - e)), e - 10);
+}
+
+// IEEE binary16 bit pattern of an FP16-representable value.
+uint16_t half_bits(double x) {
+    uint16_t sign = 0;
+    if (x < 0) {
+        sign = 0x8000;
+        x = -x;
+    }
+    if (x == 0.0) return sign;
+    int ex = 0;
+    frexp(x, &ex);
+    const int e = ex - 1;
+    if (e < -14) return (uint16_t)(sign | (uint16_t)ldexp(x, 24));   // subnormal: x / 2^-24
+    const uint16_t frac = (uint16_t)(ldexp(x, 10 - e) - 1024.0);
+    return (uint16_t)(sign | (uint16_t)((e + 15) << 10) | frac);
+}
+
+}  // namespace
+
+int q2_tensor_blocks(const Tables<double>& T, const Phys<double>& ph, std::vector<uint16_t>* out) {
+    constexpr int NP = 27, NN = 32, KK = 192;
+    std::vector<double> full((size_t)NN * KK, 0.0);
+    double zero[NP] = {0};
+    for (int j = 0; j < NP; ++j) {
+        double u[NP] = {0};
+        u[j] = 1.0;
+        double r[NP] = {0};
+        volume_term<double, 3, 2>(T, ph, 0, u, r);
+        for (int f = 0; f < 6; ++f) {
+            const int k = f / 2, s = (f & 1) ? 1 : -1;
+            face_term<double, 3, 2>(T, ph, k, s, 0, -1, u, 0, -1, zero, 0, r);
+        }
+        for (int q = 0; q < NP; ++q) full[(size_t)q * KK + j] = r[q];
+        for (int f = 0; f < 6; ++f) {
+            const int k = f / 2, s = (f & 1) ? 1 : -1;
+            double rn[NP] = {0};
+            face_term<double, 3, 2>(T, ph, k, s, 0, -1, zero, 0, -1, u, 0, rn);
+            for (int q = 0; q < NP; ++q) full[(size_t)q * KK + NP * (f + 1) + j] = rn[q];
+        }
+    }
+    double mx = 0.0;
+    for (double x : full) mx = fmax(mx, fabs(x));
+    int ex = 0;
+    if (mx > 0) frexp(mx, &ex);
+    const int t = 15 - ex;                   // max |B| 2^t in [2^14, 2^15)
+    out->assign((size_t)2 * NN * KK, 0);
+    for (size_t i = 0; i < full.size(); ++i) {
+        const double x = ldexp(full[i], t);
+        const double hi = round_half(x);
+        (*out)[i] = half_bits(hi);
+        (*out)[full.size() + i] = half_bits(round_half(x - hi));
+    }
+    return t;
+}
+
+void q2_correction_blocks(const Tables<double>& T, const Phys<double>& ph, std::vector<float>* out) {
+    constexpr int NP = 27, RS = 28, NB = 14;
+    out->assign((size_t)6 * NB * NP * RS, 0.0f);
+    double zero[NP] = {0};
+    for (int f = 0; f < 6; ++f) {
+        const int k = f / 2, s = (f & 1) ? 1 : -1;
+        for (int j = 0; j < NP; ++j) {
+            double u[NP] = {0};
+            u[j] = 1.0;
+            double blk[NB][NP] = {{0}};
+            double own0[NP] = {0}, own1[NP] = {0};
+            // same-level own blocks at levels 0 and 1
+            face_term<double, 3, 2>(T, ph, k, s, 0, -1, u, 0, -1, zero, 0, own0);
+            face_term<double, 3, 2>(T, ph, k, s, 1, -1, u, 1, -1, zero, 1, own1);
+            for (int q = 0; q < NP; ++q) blk[0][q] = -own0[q];
+            // coarser neighbour (own level 1, neighbour level 0), tangential position p;
+            // blocks of level l are 2^-(l-1) times these, so 2x gives the level-0 equivalent
+            for (int p = 0; p < 4; ++p) {
+                double ro[NP] = {0}, rn[NP] = {0};
+                face_term<double, 3, 2>(T, ph, k, s, 1, -1, u, 0, p, zero, 1, ro);
+                face_term<double, 3, 2>(T, ph, k, s, 1, -1, zero, 0, p, u, 1, rn);
+                for (int q = 0; q < NP; ++q) {
+                    blk[1 + p][q] = 2.0 * (ro[q] - own1[q]);
+                    blk[5 + p][q] = 2.0 * rn[q];
+                }
+            }
+            // finer neighbours (own level 0, neighbours level 1) on subfaces sb
+            for (int sb = 0; sb < 4; ++sb) {
+                double ro[NP] = {0}, rn[NP] = {0};
+                face_term<double, 3, 2>(T, ph, k, s, 0, sb, u, 1, -1, zero, 1, ro);
+                face_term<double, 3, 2>(T, ph, k, s, 0, sb, zero, 1, -1, u, 1, rn);
+                for (int q = 0; q < NP; ++q) {
+                    blk[9][q] += ro[q];
+                    blk[10 + sb][q] = rn[q];
+                }
+            }
+            for (int q = 0; q < NP; ++q) blk[9][q] -= own0[q];
+            for (int b = 0; b < NB; ++b)
+                for (int q = 0; q < NP; ++q) (*out)[(((size_t)f * NB + b) * NP + q) * RS + j] = (float)blk[b][q];
+        }
+    }
 }
 
 int b_from_bound(double dt, double bound) {

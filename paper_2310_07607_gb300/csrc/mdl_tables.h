@@ -1,6 +1,8 @@
 // mdl_tables.h -- host construction of basis tables, physics constants and CFL classes.
 #pragma once
 
+#include <stdint.h>
+
 #include <vector>
 
 #include "../../include/mdl.h"
@@ -43,6 +45,20 @@ int b_from_bound(double dt, double bound);
 //   that a face's Kelly contribution is sum_t (K_own u + K_nb u_nb)_t^2.
 void q1_blocks(const Tables<double>& T, const Phys<double>& ph, int dim, int L, std::vector<double>* vol,
                std::vector<double>* face, std::vector<double>* kelly);
+
+// Q2 3D level-0 operator of the tensor-core sweep as two FP16 terms (binary16 bit
+// patterns, out = [hi | lo], each 32 x 192 row-major), scaled by 2^t with t returned:
+// row q = output DOF (27 used), columns 27 s + j: s = 0 the own block A_vol + sum_f A_own,f
+// (same-level neighbours on all six faces), s = 1 + f the same-level neighbour block of
+// face f.  Blocks of level l are 2^-l times these (box elements).
+int q2_tensor_blocks(const Tables<double>& T, const Phys<double>& ph, std::vector<uint16_t>* out);
+
+// Q2 3D blocks that turn the tensor product of an element with non-regular faces into its
+// exact residual, FP32 [6 faces][14][27 rows][28 (27 used)], level-0 equivalents (level l:
+// 2^-l times these): 0 boundary face (-A_own,same); 1+p coarser neighbour at tangential
+// position p: own block minus A_own,same; 5+p its neighbour block; 9 finer neighbours: the
+// own blocks of the four subfaces minus A_own,same; 10+sb neighbour block of subface sb.
+void q2_correction_blocks(const Tables<double>& T, const Phys<double>& ph, std::vector<float>* out);
 
 // Largest 2^-k with 2^-k 2^-B <= min over all admissible classes (levels 0..L).
 double auto_dt_barrier(const Tables<double>& T, const Phys<double>& ph, int dim, int p, int L, int B);

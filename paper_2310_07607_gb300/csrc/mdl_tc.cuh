@@ -1,0 +1,645 @@
+// mdl_tc.cuh -- tensor-core (tcgen05) element residual for the Q2 3D FP32 sweep.
+//
+// For an element whose six faces all have a same-level neighbour, the SIPG residual
+// (Eq. monodomain-primal-formulation with the flux of Eq. monodomain-numerical-flux) is
+//   r_e = A_self(l) u_e + sum_f A_nb,f(l) u_nb,f,   A_self = A_vol + sum_f A_own,f,
+// and on box elements every one of these blocks scales with the level as
+// A(l) = 2^((2-d) l) A(0) (volume: (2/h)^2 h^d; faces: h^(d-1) (1/h)), so a single set of
+// level-0 blocks serves every element up to an exact power-of-two row scale.  A tile of
+// 64 due elements is one tcgen05 MMA problem
+//   D[64 x 32] = U[64 x 192] B^T,   U row i = [u_e | u_nb,1 | ... | u_nb,6] (7 x 27 values),
+//   B[32 x 192] = [A_self(0) | A_nb,1(0) | ... | A_nb,6(0)],
+// with D in tensor memory (one TMEM lane per element, one column per output DOF).
+//
+// Precision.  A has zero row sums (A 1 = 0), so r_e is unchanged when the element mean c of
+// u_e is subtracted from every gathered value: the operand is y = x - c, whose size is the
+// local variation of V.  Both operands are split into two FP16 terms (y = y_hi + y_lo,
+// B = B_hi + B_lo, each term with an 11-bit significand; B scaled by 2^t, each row of U by
+// its own power of two that brings max |y| to [2^13, 2^14)) and the product is
+// U_hi B_hi + U_hi B_lo + U_lo B_hi with FP32 accumulation: about 22 significant bits
+// relative to the row's variation, as FP32 arithmetic on the CUDA cores.  (One TF32 term per
+// operand loses ~2^-11 of y per step; the temporal indicator, a sum of squared small
+// differences, then drifts by up to ~10% on a front.  Two TF32 terms of U would need
+// 192 KB of shared memory per tile; FP16 terms of the same significand take half.)
+//
+// Faces that are not same-level interior faces (boundary, coarser or finer neighbours) are
+// zero slots in U; their exact contribution minus the same-level own block that A_self
+// assumed is added on the CUDA cores in FP32 from precomputed level-0 correction blocks
+// (same power-of-two level scaling), on the same mean-shifted values.
+//
+// Shared-memory operands use the 128-byte swizzled K-major layout: 8-row x 128-byte atoms
+// (64 FP16 values per row), atoms of one 64-value K block stacked over the rows, K blocks
+// outermost.  The MMA of K step j (16 values) starts 32 j bytes into its atom.  With M = 64
+// the accumulator row 16 w + t sits in TMEM lane 32 w + t (w = 0..3).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "mdl_kernels.cuh"
+
+namespace mdl {
+namespace tc {
+
+constexpr int M = 64;           // elements per tile (M = 64 MMA: row 16 w + t in TMEM lane 32 w + t)
+constexpr int N = 32;           // output DOFs per element (27 used)
+constexpr int K = 192;          // 7 slots x 27 input DOFs (189 used, 3 zero)
+constexpr int KU = 189;         // used K
+constexpr int NP = 27;
+constexpr int SLOTS = 7;
+constexpr int THREADS = 256;    // 8 warps; two CTAs per SM overlap each other's latencies
+constexpr int RST = 29;         // row stride of the residual staging array (odd: no bank conflicts)
+constexpr uint32_t TMEM_COLS = 32;
+constexpr int KSTEP = 16;       // K per kind::f16 MMA
+
+// Shared-memory plan (bytes from a 1024-aligned base).
+constexpr int B_BYTES = N * K * 2;                    // one FP16 term of B
+constexpr int U_BYTES = M * K * 2;                    // one FP16 term of U
+constexpr int OFF_BHI = 0;
+constexpr int OFF_BLO = OFF_BHI + B_BYTES;
+constexpr int OFF_UHI = OFF_BLO + B_BYTES;
+constexpr int OFF_ULO = OFF_UHI + U_BYTES;
+constexpr int OFF_R = OFF_ULO + U_BYTES;              // float [M][RST] scaled residual
+constexpr int OFF_SCR = OFF_R + M * RST * 4;          // float [8 warps][2][32] per-warp scratch
+constexpr int OFF_PTR = OFF_SCR + 8 * 2 * 32 * 4;     // const float* [M][8]: row of slot s (seen value)
+constexpr int OFF_PTRO = OFF_PTR + M * 8 * 8;         // const float* [M][8]: other V slot (interpolation)
+constexpr int OFF_E = OFF_PTRO + M * 8 * 8;           // int32 element id (-1: padding row)
+constexpr int OFF_INF = OFF_E + M * 4;                // uint32 face info
+constexpr int OFF_NB = OFF_INF + M * 4;               // int32 [M][6] face neighbours
+constexpr int OFF_TH = OFF_NB + M * 6 * 4;            // float [M][8] time-interpolation weight
+constexpr int OFF_RS = OFF_TH + M * 8 * 4;            // float 2^-sc: undoes the row's operand scale
+constexpr int OFF_C = OFF_RS + M * 4;                 // float operand mean c of the row
+constexpr int OFF_LV = OFF_C + M * 4;                 // uint8 level byte
+constexpr int OFF_LIVE = OFF_LV + M;                  // uint8 bit s: slot s holds values
+constexpr int OFF_INTP = OFF_LIVE + M;                // uint8 bit s: slot s is interpolated in time
+constexpr int OFF_IRR = OFF_INTP + M;                 // uint8 element has a non-regular face
+constexpr int OFF_CORR = ((OFF_IRR + M + 15) / 16) * 16;  // float [M][RST] residual corrections
+constexpr int OFF_NX = OFF_CORR + M * RST * 4;        // next tile: int32 [M][8] = info, nbr[6], lvl | lvn[f] << 8 (f < 3)
+constexpr int OFF_NX2 = OFF_NX + M * 8 * 4;           // next tile: uint32 [M] lvn[f] for f >= 3
+constexpr int OFF_MTAB = OFF_NX2 + M * 4;             // float [8][27] GL mass, then [8][27] inverse
+constexpr int OFF_MBAR = ((OFF_MTAB + 2 * 8 * NP * 4 + 7) / 8) * 8;
+constexpr int OFF_FLAG = OFF_MBAR + 8;
+constexpr int OFF_TMEM = OFF_FLAG + 8;
+constexpr int SMEM_BYTES = OFF_TMEM + 16 + 1024;      // + alignment slack of the dynamic base
+static_assert(OFF_UHI % 1024 == 0 && OFF_ULO % 1024 == 0 && OFF_BLO % 1024 == 0, "operand alignment");
+static_assert(2 * (SMEM_BYTES + 1024) <= 228 * 1024, "two CTAs per SM");
+
+constexpr unsigned ERR_TIMEOUT = 16u;                 // a bounded wait of the sweep gave up
+constexpr uint32_t WAIT_LIMIT = 1u << 26;             // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Byte offset of FP16 element (row, k) in a 128-byte swizzled K-major operand of `rows` rows.
+__device__ __forceinline__ uint32_t sw128h(int row, int k, int rows) {
+    return (uint32_t)((k >> 6) * rows * 128 + (row >> 3) * 1024 + (row & 7) * 128 +
+                      ((((k >> 3) & 7) ^ (row & 7)) << 4) + ((k & 7) << 1));
+}
+
+// Shared-memory matrix descriptor: 128-byte swizzle, 1024-byte stride between 8-row groups,
+// start address in 16-byte units; bits 46-48 hold the descriptor version (1).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B FP16, both K-major, M x N shape.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes become visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// arrive on the mbarrier once every MMA issued so far by this thread has completed
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(mbar))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+    for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
+        if (mbar_test(mbar, parity)) return true;
+    return false;
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane (32x32b shape: warp w reads
+// lanes 32 (w % 4) .. + 31); the wait is in the same asm so no use precedes it.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// y (already scaled) as two FP16 terms: hi = fp16(y), lo = fp16(y - hi).
+__device__ __forceinline__ void split_half(float y, __half& hi, __half& lo) {
+    hi = __float2half_rn(y);
+    lo = __float2half_rn(y - __half2float(hi));
+}
+
+// Issue the 3 x 12 MMAs of one tile (U_hi B_hi, U_hi B_lo, U_lo B_hi per K step) and
+// commit to mbar.
+__device__ __forceinline__ void issue_tile_mma(uint32_t tmem, uint32_t sUhi, uint32_t sUlo, uint32_t sBhi,
+                                               uint32_t sBlo, uint64_t* mbar) {
+    constexpr uint32_t idesc = idesc_f16(M, N);
+#pragma unroll 1
+    for (int ks = 0; ks < K / KSTEP; ++ks) {
+        const int k0 = ks * KSTEP;
+        const uint32_t offA = (uint32_t)((k0 >> 6) * M * 128 + (k0 & 63) * 2);
+        const uint32_t offB = (uint32_t)((k0 >> 6) * N * 128 + (k0 & 63) * 2);
+        const uint64_t ahi = sdesc(sUhi + offA), bhi = sdesc(sBhi + offB);
+        mma_f16(tmem, ahi, bhi, idesc, ks > 0 ? 1u : 0u);
+        mma_f16(tmem, ahi, sdesc(sBlo + offB), idesc, 1u);
+        mma_f16(tmem, sdesc(sUlo + offA), bhi, idesc, 1u);
+    }
+    mma_commit(mbar);
+}
+
+}  // namespace tc
+
+// Values of DOF q of element nb as seen at tick `tick` (Alg. 1): its current value if due,
+// else the linear time interpolant of its last step.
+__device__ __forceinline__ float seen_dof(const DevArrays<float>& d, int tick, int B, int nb, int q) {
+    const int lv = d.lvl[nb], sh = B - (lv & 7), par = (lv >> 3) & 1;
+    const int j = tick >> sh, rem = tick & ((1 << sh) - 1);
+    const int nw = par ^ ((j + (rem ? 1 : 0)) & 1);
+    const size_t o = (size_t)nb * 27 + q;
+    const float x = (nw ? d.V1 : d.V0)[o];
+    if (!rem) return x;
+    const float xo = (nw ? d.V0 : d.V1)[o];
+    return xo + (float)rem * pow2_neg<float>(sh) * (x - xo);
+}
+
+// Row q of a 27 x 28 correction block (16-byte aligned) times the 27 values in s.
+__device__ __forceinline__ float block_row_dot(const float* __restrict__ row, const float* s) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+        const float4 r4 = __ldg(reinterpret_cast<const float4*>(row) + m);
+        acc += r4.x * s[4 * m] + r4.y * s[4 * m + 1] + r4.z * s[4 * m + 2] + r4.w * s[4 * m + 3];
+    }
+    acc += __ldg(row + 24) * s[24] + __ldg(row + 25) * s[25] + __ldg(row + 26) * s[26];
+    return acc;
+}
+
+// One tick of Alg. 1 for a Q2 3D FP32 context with the element residual on the tensor
+// cores.  Persistent, two CTAs per SM (each hides the other's memory latency), each CTA
+// walking tiles of 64 due elements:
+//   0  threads 0..63: metadata of the tile's elements and, per operand slot, the row that
+//      holds the value the element sees (Alg. 1: a coarser LTS neighbour mid-interval is
+//      seen through the linear interpolant of its last step); next tile's ids prefetched
+//   1  warp w = 8-row group w, lane = 4 ii + kk: row ii, columns k = kk + 4 jj; all loads
+//      issued at once, then the row mean c, y = x - c, the row's power-of-two scale and
+//      the FP16 hi/lo terms in the swizzled operand layout
+//   2  one thread issues the MMAs and commits to an mbarrier
+//   3  while they run: corrections of non-regular faces (warp per element, lane = row) and
+//      the loads of the pointwise step, item by item (element, DOF)
+//   4  warps 0-3: D row -> scaled residual in shared memory
+//   5  the pointwise step (dof_update) of every item with coalesced stores
+//   6  per element: the RV-T accumulation and the probe checks
+// unscale = 2^-t undoes the scaling of B by 2^t; each row's scale of y is undone by 2^-sc.
+template <int DIM, int P>
+__global__ void __launch_bounds__(tc::THREADS, 2)
+    k_tick_tc(const TickArgs<float> a, const Tables<float> T, const Phys<float> ph,
+              const uint16_t* __restrict__ Bg, const float unscale, const float* __restrict__ Cg) {
+    static_assert(DIM == 3 && P == 2, "tensor-core sweep: Q2 3D only");
+    using namespace tc;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    float* sR = reinterpret_cast<float*>(sm + OFF_R);
+    float* sScr = reinterpret_cast<float*>(sm + OFF_SCR);
+    const float** sPtr = reinterpret_cast<const float**>(sm + OFF_PTR);
+    const float** sPtrO = reinterpret_cast<const float**>(sm + OFF_PTRO);
+    int* sE = reinterpret_cast<int*>(sm + OFF_E);
+    uint32_t* sInf = reinterpret_cast<uint32_t*>(sm + OFF_INF);
+    int* sNb = reinterpret_cast<int*>(sm + OFF_NB);
+    float* sTh = reinterpret_cast<float*>(sm + OFF_TH);
+    float* sRs = reinterpret_cast<float*>(sm + OFF_RS);
+    float* sC = reinterpret_cast<float*>(sm + OFF_C);
+    uint8_t* sLv = sm + OFF_LV;
+    uint8_t* sLive = sm + OFF_LIVE;
+    uint8_t* sIntp = sm + OFF_INTP;
+    uint8_t* sIrr = sm + OFF_IRR;
+    float* sCorr = reinterpret_cast<float*>(sm + OFF_CORR);
+    int* sNx = reinterpret_cast<int*>(sm + OFF_NX);
+    uint32_t* sNx2 = reinterpret_cast<uint32_t*>(sm + OFF_NX2);
+    float* sMq = reinterpret_cast<float*>(sm + OFF_MTAB);
+    float* sMinv = sMq + 8 * NP;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + OFF_MBAR);
+    unsigned* sFlag = reinterpret_cast<unsigned*>(sm + OFF_FLAG);
+    uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + OFF_TMEM);
+
+    const DevArrays<float>& d = a.d;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tick = a.tick, B = a.B;
+
+    // --- set-up that reads nothing the previous tick writes (before the dependent wait)
+    for (int i = tid; i < 2 * N * K; i += THREADS) {
+        const int part = i / (N * K), rem = i - part * (N * K), n = rem / K, k = rem - n * K;
+        *reinterpret_cast<uint16_t*>(sm + (part ? OFF_BLO : OFF_BHI) + sw128h(n, k, N)) = Bg[i];
+    }
+    // per (level, node) GL mass and its inverse: lanes read different nodes, which kernel-
+    // parameter arrays would serve one address at a time
+    for (int i = tid; i < 8 * NP; i += THREADS) {
+        const int l = i / NP, q = i - l * NP;
+        sMq[i] = ph.Wvol[l] * T.w[q % 3] * T.w[(q / 3) % 3] * T.w[q / 9];
+        sMinv[i] = ph.Minv[l][q];
+    }
+    if (warp == 0) tmem_alloc(sTmem, TMEM_COLS);
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        *sFlag = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *sTmem;
+    // due count and element order are fixed during the sweep
+    const int n_act = d.meta->nact[tick];
+    const int ntiles = (n_act + M - 1) / M;
+    int e_next = -1;
+    if (tid < M && (int)blockIdx.x * M + tid < n_act) e_next = d.order[blockIdx.x * M + tid];
+    pdl_enter();
+    uint32_t parity = 0;
+    bool ok = d.meta->err == 0;
+    double acc0 = 0.0;   // threads 0..63: RV-T accumulator of the tile's element tid
+    // Metadata of a tile's element (threads 0..63) is fetched one tile ahead: the ids when a
+    // tile starts, their level bytes, face info and neighbours while its gather runs, the
+    // neighbours' level bytes while its pointwise step runs (kept in sNx / sNx2).
+    auto fetch_raw = [&](int e, int* nx) {
+        const int es = e >= 0 ? e : 0;
+        nx[0] = e >= 0 ? (int)d.info[es] : 0;
+#pragma unroll
+        for (int f = 0; f < 6; f += 2) {
+            const int2 n2 = *reinterpret_cast<const int2*>(d.nbr + (size_t)es * 6 + f);
+            nx[1 + f] = n2.x;
+            nx[2 + f] = n2.y;
+        }
+        nx[7] = e >= 0 ? (int)d.lvl[es] : 0;
+    };
+    auto fetch_lvn = [&](int e, const int* nx, uint32_t& lo, uint32_t& hi) {
+        const int es = e >= 0 ? e : 0;
+        lo = 0u;
+        hi = 0u;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const uint32_t v = d.lvl[(((nx[0] >> (4 * f)) & 3) == 1) ? nx[1 + f] : es];
+            if (f < 3) lo |= v << (8 * f);
+            else hi |= v << (8 * (f - 3));
+        }
+    };
+    if (tid < M && (int)blockIdx.x < ntiles) {
+        int nx[8];
+        fetch_raw(e_next, nx);
+        uint32_t lo, hi;
+        fetch_lvn(e_next, nx, lo, hi);
+        nx[7] |= (int)(lo << 8);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sNx[tid * 8 + k] = nx[k];
+        sNx2[tid] = hi;
+    }
+    int nxr[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // threads 0..63: next tile's raw metadata in flight
+    uint32_t nlo = 0u, nhi = 0u;
+
+    for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+        // ---- 0: metadata (threads 0..63, one element each)
+        if (tid < M) {
+            const int e = e_next;
+            const int idx_n = (t + (int)gridDim.x) * M + tid;
+            e_next = idx_n < n_act ? d.order[idx_n] : -1;
+            const int es = e >= 0 ? e : 0;                    // any valid row for padding slots
+            uint8_t live = 0, intp = 0;
+            const uint32_t inf = (uint32_t)sNx[tid * 8];
+            int nbf[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) nbf[f] = sNx[tid * 8 + 1 + f];
+            const uint32_t w7 = (uint32_t)sNx[tid * 8 + 7], w8 = sNx2[tid];
+            const uint8_t lv = (uint8_t)(w7 & 255u);
+            uint8_t lvn[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) lvn[f] = (uint8_t)((f < 3 ? (w7 >> (8 * (f + 1))) : (w8 >> (8 * (f - 3)))) & 255u);
+            const int b = lv & 7, par = (lv >> 3) & 1;
+            const int cur = par ^ ((tick >> (B - b)) & 1);
+            sPtr[tid * 8] = (cur ? d.V1 : d.V0) + (size_t)es * NP;
+            sPtrO[tid * 8] = sPtr[tid * 8];
+            sTh[tid * 8] = 0.0f;
+            if (e >= 0) live = 1;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                const bool same = e >= 0 && ((inf >> (4 * f)) & 3) == 1;
+                const int sh = B - (lvn[f] & 7), pn = (lvn[f] >> 3) & 1;
+                const int j = tick >> sh, rem = same ? (tick & ((1 << sh) - 1)) : 0;
+                const int nw = pn ^ ((j + (rem ? 1 : 0)) & 1);
+                const size_t o = (size_t)(same ? nbf[f] : es) * NP;
+                sPtr[tid * 8 + 1 + f] = (nw ? d.V1 : d.V0) + o;
+                sPtrO[tid * 8 + 1 + f] = (nw ? d.V0 : d.V1) + o;
+                sTh[tid * 8 + 1 + f] = rem ? (float)rem * pow2_neg<float>(sh) : 0.0f;
+                if (same) live |= (uint8_t)(2u << f);
+                if (rem) intp |= (uint8_t)(2u << f);
+            }
+            bool irr = false;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) irr = irr || (((inf >> (4 * f)) & 3) != 1);
+            // the element's RV-T accumulator, needed at the end of the tile (ke != 0)
+            acc0 = (e >= 0 && (tick >> (B - b)) != 0) ? d.acc[e] : 0.0;
+            sE[tid] = e;
+            sInf[tid] = inf;
+            sLv[tid] = lv;
+            sLive[tid] = live;
+            sIntp[tid] = intp;
+            sIrr[tid] = (e >= 0 && irr) ? 1 : 0;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) sNb[tid * 6 + f] = nbf[f];
+        }
+        __syncthreads();
+
+        // ---- 1: gather, mean shift, FP16 split (warp w: rows 8 w .. 8 w + 7; lane = 4 ii + kk:
+        //      row ii, column pairs k = 2 kk + 8 jj + {0, 1})
+        {
+            const int ii = lane >> 2, kk = lane & 3, i = warp * 8 + ii;
+            const float* pr[SLOTS];
+#pragma unroll
+            for (int s = 0; s < SLOTS; ++s) pr[s] = sPtr[i * 8 + s];
+            const unsigned live = sLive[i], intp = sIntp[i];
+            float x[48];
+            // column k lies in slot s0 = floor(8 jj / 27) or the next one
+#pragma unroll
+            for (int jj = 0; jj < 24; ++jj) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int s0 = (8 * jj) / NP, s1 = s0 + 1 < SLOTS ? s0 + 1 : s0;
+                    const int k = 2 * kk + 8 * jj + h;
+                    const bool nxt = k >= NP * (s0 + 1) && s1 != s0;
+                    const int q = (k < KU ? k : KU - 1) - NP * (nxt ? s1 : s0);
+                    x[2 * jj + h] = __ldg((nxt ? pr[s1] : pr[s0]) + q);
+                }
+            }
+            if (intp) {
+                // coarser LTS neighbours mid-interval: linear interpolant in time (Alg. 1)
+#pragma unroll
+                for (int m = 0; m < 48; ++m) {
+                    const int k = 2 * kk + 8 * (m >> 1) + (m & 1);
+                    const int s = (k < KU ? k : KU - 1) / NP;
+                    if (k < KU && ((intp >> s) & 1u)) {
+                        const float xo = __ldg(sPtrO[i * 8 + s] + (k - NP * s));
+                        x[m] = xo + sTh[i * 8 + s] * (x[m] - xo);
+                    }
+                }
+            }
+            float cs = 0.0f;
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if (2 * kk + 8 * (m >> 1) + (m & 1) < NP) cs += x[m];
+            cs += __shfl_xor_sync(0xffffffffu, cs, 1);
+            cs += __shfl_xor_sync(0xffffffffu, cs, 2);
+            const float c = cs * (1.0f / NP);
+            float mx = 0.0f;
+#pragma unroll
+            for (int m = 0; m < 48; ++m) {
+                const int k = 2 * kk + 8 * (m >> 1) + (m & 1);
+                const int s = (k < KU ? k : KU - 1) / NP;
+                x[m] = (k < KU && ((live >> s) & 1u)) ? x[m] - c : 0.0f;
+                mx = fmaxf(mx, fabsf(x[m]));
+            }
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+            // row scale 2^sc with max |y| 2^sc in [2^13, 2^14): the FP16 terms keep 22 bits
+            // relative to the row's own variation (exact power of two, undone after the MMA)
+            const int ex = (mx > 0.0f) ? (int)((__float_as_uint(mx) >> 23) & 255u) - 126 : 14;
+            const int sc = min(max(14 - ex, -100), 100);
+            const float up = __int_as_float((127 + sc) << 23);
+            if (kk == 0) {
+                sRs[i] = __int_as_float((127 - sc) << 23);
+                sC[i] = c;
+            }
+#pragma unroll
+            for (int jj = 0; jj < 24; ++jj) {
+                const int k = 2 * kk + 8 * jj;
+                const float a0 = x[2 * jj] * up, a1 = x[2 * jj + 1] * up;
+                const __half2 hi = __floats2half2_rn(a0, a1);
+                const __half2 lo = __floats2half2_rn(a0 - __low2float(hi), a1 - __high2float(hi));
+                *reinterpret_cast<__half2*>(sm + OFF_UHI + sw128h(i, k, M)) = hi;
+                *reinterpret_cast<__half2*>(sm + OFF_ULO + sw128h(i, k, M)) = lo;
+            }
+        }
+        fence_async_smem();
+        __syncthreads();
+
+        // ---- 2: MMAs (the tensor cores run while the corrections and the item loads below run)
+        if (tid == 0) {
+            fence_after();
+            issue_tile_mma(tmem, smem_u32(sm + OFF_UHI), smem_u32(sm + OFF_ULO), smem_u32(sm + OFF_BHI),
+                           smem_u32(sm + OFF_BLO), mbar);
+        }
+
+        if (tid < M) fetch_raw(e_next, nxr);
+
+        // ---- 3: non-regular faces (boundary, coarser, finer neighbours): exact face terms minus
+        //      the same-level own blocks the tensor product assumed, from level-0 correction
+        //      blocks; warp w takes elements 8 w .. 8 w + 7, lane q = row q, on the operand's
+        //      mean-shifted values (the same c as the MMA)
+        {
+            const int q = lane < NP ? lane : NP - 1;
+            float* su = sScr + warp * 64;
+            float* sn = su + 32;
+#pragma unroll 1
+            for (int j = 0; j < 8; ++j) {
+                const int i = warp * 8 + j;
+                if (!sIrr[i]) continue;
+                const uint32_t inf = sInf[i];
+                const float c = sC[i];
+                su[lane] = __ldg(sPtr[i * 8] + q) - c;
+                __syncwarp();
+                float corr = 0.0f;
+                for (int f = 0; f < 6; ++f) {
+                    const int kind = (inf >> (4 * f)) & 3;
+                    if (kind == 1) continue;
+                    const float* Bf = Cg + (size_t)f * 14 * NP * 28 + (size_t)q * 28;
+                    if (kind == 0) {
+                        corr += block_row_dot(Bf, su);
+                    } else if (kind == 2) {
+                        const int pos = (inf >> (4 * f + 2)) & 3;
+                        corr += block_row_dot(Bf + (1 + pos) * NP * 28, su);
+                        sn[lane] = seen_dof(d, tick, B, sNb[i * 6 + f], q) - c;
+                        __syncwarp();
+                        corr += block_row_dot(Bf + (5 + pos) * NP * 28, sn);
+                        __syncwarp();
+                    } else {
+                        corr += block_row_dot(Bf + 9 * NP * 28, su);
+                        for (int sb = 0; sb < 4; ++sb) {
+                            sn[lane] = seen_dof(d, tick, B, d.hang[sNb[i * 6 + f] + sb], q) - c;
+                            __syncwarp();
+                            corr += block_row_dot(Bf + (10 + sb) * NP * 28, sn);
+                            __syncwarp();
+                        }
+                    }
+                }
+                if (lane < NP) sCorr[i * RST + q] = corr * pow2_neg<float>((DIM - 2) * ((inf >> 24) & 15));
+                __syncwarp();
+            }
+        }
+
+        // item = (element i, DOF q), i = it / 27: the loads of every item of the thread
+        constexpr int NIT = (M * NP + THREADS - 1) / THREADS;
+        float u[NIT], w[NIT], Ia[NIT], ga[NIT];
+#pragma unroll
+        for (int m = 0; m < NIT; ++m) {
+            const int it = tid + m * THREADS;
+            const int i = min(it / NP, M - 1), q = it - (it / NP) * NP;
+            const int e = sE[i], es = e >= 0 ? e : 0;
+            const int ke = tick >> (B - (sLv[i] & 7));
+            const bool need = it < M * NP && e >= 0 && ke != 0;
+            u[m] = __ldg(sPtr[i * 8] + q);
+            w[m] = d.v[(size_t)es * NP + q];
+            Ia[m] = need ? d.Ia[(size_t)es * NP + q] : 0.0f;
+            ga[m] = need ? d.ga[(size_t)es * NP + q] : 0.0f;
+        }
+
+        // ---- 4: residual rows (warps 0-3; thread t < 16 of warp w holds row 16 w + t)
+        if (warp < 4) {
+            const bool done = mbar_wait(mbar, parity);
+            fence_after();
+            float acc[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), acc);
+            if (!done) {
+                atomicOr(sFlag, 1u);
+            } else if (lane < 16) {
+                const int i = warp * 16 + lane;
+                const float scale = unscale * sRs[i] * pow2_neg<float>((DIM - 2) * ((sInf[i] >> 24) & 15));
+#pragma unroll
+                for (int q = 0; q < NP; ++q) sR[i * RST + q] = acc[q] * scale;
+            }
+        }
+        parity ^= 1u;
+        fence_before();
+        __syncthreads();
+        if (*sFlag) {
+            ok = false;
+            if (tid == 0) atomicOr(&d.meta->err, ERR_TIMEOUT);
+            break;
+        }
+
+        if (tid < M) {
+#pragma unroll
+            for (int k = 0; k < 7; ++k) sNx[tid * 8 + k] = nxr[k];
+            fetch_lvn(e_next, nxr, nlo, nhi);
+        }
+
+        // ---- 5: item updates (dof_update) with coalesced stores; the RV-T terms and both
+        //      values go to shared memory (the operand bytes, free once the MMA completed)
+        {
+            float* sT = reinterpret_cast<float*>(sm + OFF_UHI);
+            float* sUo = sT + M * NP;
+            float* sUn = sUo + M * NP;
+#pragma unroll
+            for (int m = 0; m < NIT; ++m) {
+                const int it = tid + m * THREADS;
+                if (it >= M * NP) continue;
+                const int i = it / NP, q = it - i * NP;
+                const int e = sE[i];
+                float term = 0.0f, un = 0.0f;
+                if (e >= 0) {
+                    const uint32_t inf = sInf[i];
+                    const int b = sLv[i] & 7, ke = tick >> (B - b), lev = (inf >> 24) & 15;
+                    float so = 0.0f, smd = 0.0f;
+                    if (inf & INFO_STIM) dof_stim<float>(a, e, tick, a.dte[b], q, so, smd);
+                    const float r = sR[i * RST + q] + (sIrr[i] ? sCorr[i * RST + q] : 0.0f);
+                    float wn;
+                    term = dof_update<float>(ph, sMq[lev * NP + q], sMinv[lev * NP + q], ke, a.dteR[b], so, smd, u[m],
+                                             w[m], r, Ia[m], ga[m], un, wn);
+                    const size_t o = (size_t)e * NP + q;
+                    const bool cur1 = sPtr[i * 8] == d.V1 + (size_t)e * NP;
+                    (cur1 ? d.V0 : d.V1)[o] = un;
+                    d.v[o] = wn;
+                    if (ke == 0 && b > 0) {
+                        d.Ia[o] = Ia[m];
+                        d.ga[o] = ga[m];
+                    }
+                }
+                sT[it] = term;
+                sUo[it] = u[m];
+                sUn[it] = un;
+            }
+        }
+        __syncthreads();
+        if (tid < M) {
+            // ---- 6: per element: RV-T accumulation (terms summed in DOF order), probe checks
+            sNx[tid * 8 + 7] = nxr[7] | (int)(nlo << 8);
+            sNx2[tid] = nhi;
+            const int i = tid, e = sE[i];
+            if (e >= 0) {
+                const float* sT = reinterpret_cast<const float*>(sm + OFF_UHI);
+                const float* sUo = sT + M * NP;
+                const float* sUn = sUo + M * NP;
+                const uint32_t inf = sInf[i];
+                const int b = sLv[i] & 7;
+                float term = 0.0f, vmax = 0.0f;
+                for (int q = 0; q < NP; ++q) {
+                    term += sT[i * NP + q];
+                    vmax = fmaxf(vmax, fabsf(sUn[i * NP + q]));
+                }
+                d.acc[e] = acc0 + a.dte[b] * (double)term;
+                if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
+                    lat_check<float, DIM, P>(d, T, ph, e, inf, (inf >> 24) & 15, sUo + i * NP, sUn + i * NP,
+                                             tick_time(a, tick), a.dte[b]);
+            }
+        }
+        __syncthreads();
+    }
+    if (*sFlag) {
+        // a wait gave up: give the MMAs in flight one more bounded wait before freeing TMEM
+        if (tid == 0) mbar_wait(mbar, parity ^ 1u);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+}  // namespace mdl

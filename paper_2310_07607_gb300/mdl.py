@@ -76,7 +76,7 @@ EXPORTS = [
 ]
 
 SLOT_FREE, SLOT_RUNNING, SLOT_DONE, SLOT_FAILED = 0, 1, 2, 3
-SWEEP_THREAD, SWEEP_GROUP, SWEEP_COOP = 0, 1, 2
+SWEEP_THREAD, SWEEP_GROUP, SWEEP_COOP, SWEEP_TENSOR = 0, 1, 2, 3
 
 _lib = None
 
@@ -211,7 +211,7 @@ class Sim:
         self._check(self.lib.mdl_set_tick_shape(self.h, threads, blocks_per_sm))
 
     def set_sweep_variant(self, variant: int):
-        """SWEEP_THREAD (the default), SWEEP_GROUP (Q1) or SWEEP_COOP."""
+        """SWEEP_THREAD (the default), SWEEP_GROUP (Q1), SWEEP_COOP or SWEEP_TENSOR (Q2 3D FP32)."""
         self._check(self.lib.mdl_set_sweep_variant(self.h, variant))
 
     def __del__(self):
