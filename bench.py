@@ -51,9 +51,7 @@ SETUP_BARRIERS = 5
 # their proportion (tick 0 once, the finer ticks 7 times).  ncu replays each launch with
 # cold caches, so this is an upper bound on the live traffic.  Set to None whenever the
 # kernel changes until it is captured again.
-TRAFFIC_PER_LAUNCH = {
-    "k_tick<float,2,1>": (7.776768e6 + 7 * 5.551104e6) / 8.0,
-}
+TRAFFIC_PER_LAUNCH = {}
 # Algorithmic bytes per DOF-update of the fused sweep (Q1 2D, FP32, AP): V_old 4 + v 4 +
 # V_new 4 + v 4 = 16 B, plus per element step 2d neighbour ids + 4 B level/flags + the FP64
 # RV-T accumulator read-modify-write (36 B) over (p+1)^d = 4 DOFs.
@@ -294,6 +292,9 @@ def run_e2e(sim, args, torch):
     v = torch.empty_like(V, pin_memory=True)
     Vh = sim.read_V()
     vh = sim.read_state()
+    # results come back into pinned buffers too (ping-pong with the input buffers)
+    Vo = torch.empty_like(V, pin_memory=True)
+    vo = torch.empty_like(V, pin_memory=True)
     sim.reset_stats()
     h2d = d2h = 0
     t0 = time.perf_counter()
@@ -302,14 +303,19 @@ def run_e2e(sim, args, torch):
         if V.numel() < nd:
             V = torch.empty(nd * 2, dtype=torch.float64, pin_memory=True)
             v = torch.empty_like(V, pin_memory=True)
+            Vo = torch.empty_like(V, pin_memory=True)
+            vo = torch.empty_like(V, pin_memory=True)
         Va, va = V.numpy()[:nd], v.numpy()[:nd]
-        Va[:] = Vh
-        va[:] = vh
+        if Va.ctypes.data != Vh.ctypes.data:
+            Va[:] = Vh
+            va[:] = vh
         sim.set_initial(Va, va)
         h2d += 16 * nd
         sim.step_barriers(1)
-        Vh = sim.read_V()
-        vh = sim.read_state()
+        # the mesh may have changed size: read into the other pinned pair, then swap
+        Vh = sim.read_V(Vo.numpy())
+        vh = sim.read_state(vo.numpy())
+        V, Vo, v, vo = Vo, V, vo, v
         d2h += 16 * Vh.size
     t1 = time.perf_counter()
     st = sim.stats()

@@ -263,17 +263,22 @@ class Sim:
         self._check(self.lib.mdl_get_sizes(self.h, C.byref(a), C.byref(b), C.byref(c)))
         return a.value, b.value, c.value
 
-    def _read(self, fn, n):
-        out = np.empty(n, dtype=np.float64)
+    def _read(self, fn, n, out=None):
+        if out is None:
+            out = np.empty(n, dtype=np.float64)
+        elif out.dtype != np.float64 or not out.flags.c_contiguous or out.size < n:
+            raise ValueError("out must be a contiguous float64 array of at least %d values" % n)
         got = C.c_int64()
-        self._check(fn(self.h, _ptr(out), n, C.byref(got)))
-        return out
+        self._check(fn(self.h, _ptr(out), out.size, C.byref(got)))
+        return out[:n]
 
-    def read_V(self):
-        return self._read(self.lib.mdl_read_V, self.sizes()[1])
+    def read_V(self, out=None):
+        """V in leaf order (FP64); `out` may be a caller buffer (e.g. pinned) to fill."""
+        return self._read(self.lib.mdl_read_V, self.sizes()[1], out)
 
-    def read_state(self):
-        return self._read(self.lib.mdl_read_state, self.sizes()[1])
+    def read_state(self, out=None):
+        """Recovery variable in leaf order (FP64); `out` as for read_V."""
+        return self._read(self.lib.mdl_read_state, self.sizes()[1], out)
 
     def read_activation(self):
         return self._read(self.lib.mdl_read_activation, self.sizes()[2])
