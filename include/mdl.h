@@ -191,8 +191,9 @@ const char* mdl_version(void);
  * per SM with threads * blocks_per_sm <= 2048.  Results do not depend on it. */
 int mdl_set_tick_shape(mdl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
 
-/* Sweep kernel variant.  All follow Alg. 1 tick by tick; THREAD and COOP give identical
- * values, GROUP sums the face terms in another order (agreement within rounding):
+/* Sweep kernel variant.  All follow Alg. 1 tick by tick; THREAD and COOP run the same
+ * per-element arithmetic, GROUP sums the face terms in another order; they agree to the
+ * working precision's rounding:
  *   MDL_SWEEP_THREAD  one thread per due element, one launch per tick; the default except
  *                     for Q2 3D FP32 contexts, whose default is MDL_SWEEP_TENSOR;
  *   MDL_SWEEP_GROUP   Q1 only: (p+1)^d lanes per element, one lane per face and per DOF,

@@ -358,13 +358,12 @@ __device__ __forceinline__ void element_residual(const DevArrays<R>& d, const Ta
 // The probes inside the leaf are the root GL nodes a with pfl[lev][a_k] == the leaf's cell
 // in every direction k; a pending probe's values before and after the step are the leaf
 // polynomial at its position, evaluated by sum factorisation.
+// lc, rid: the leaf's cell in its root and the root id (loc[e], root[e]).
 template <typename R, int DIM, int P>
-__device__ void lat_check(const DevArrays<R>& d, const Tables<R>& T, const Phys<R>& ph, int e,
-                          uint32_t inf, int lev, const R* u, const R* un, double t_old, double dte) {
+__device__ void lat_check_at(const DevArrays<R>& d, const Tables<R>& T, const Phys<R>& ph, int e, uint32_t inf,
+                             int lev, uint32_t lc, int64_t rid, const R* u, const R* un, double t_old, double dte) {
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
-    const uint32_t lc = d.loc[e];
-    const int64_t rid = d.root[e];
     const int lx[3] = {(int)(lc & 255u), (int)((lc >> 8) & 255u), (int)((lc >> 16) & 255u)};
     unsigned inside_k[3] = {1u, 1u, 1u};
 #pragma unroll
@@ -421,6 +420,12 @@ __device__ void lat_check(const DevArrays<R>& d, const Tables<R>& T, const Phys<
     if (!pending) d.info[e] = inf & ~INFO_PENDING;
 }
 
+template <typename R, int DIM, int P>
+__device__ void lat_check(const DevArrays<R>& d, const Tables<R>& T, const Phys<R>& ph, int e,
+                          uint32_t inf, int lev, const R* u, const R* un, double t_old, double dte) {
+    lat_check_at<R, DIM, P>(d, T, ph, e, inf, lev, d.loc[e], (int64_t)d.root[e], u, un, t_old, dte);
+}
+
 template <typename R>
 struct TickArgs {
     DevArrays<R> d;
@@ -447,11 +452,16 @@ __device__ __forceinline__ double tick_time(const TickArgs<R>& a, int tick) {
 // sweep; a stale bit only repeats a probe check that finds nothing left to do.)
 template <int NF, bool NB>
 struct TickMeta {
+    static constexpr bool HP = NF == 4;   // 2D: the finer neighbours of hanging faces too
     int e;
     uint32_t inf;
     uint8_t lv;
     int nbf[NF];
     uint8_t lvn[NF];
+    int hg[HP ? NF : 1][2];               // fine neighbours of a hanging face and their level bytes
+    uint8_t hgl[HP ? NF : 1][2];
+    uint32_t lc;                          // probe lookup: cell in the root, root id
+    int rid;
 };
 // Q2: the neighbours are read face by face inside the residual (holding them would spill)
 template <int NF>
@@ -482,6 +492,19 @@ __device__ __forceinline__ void tick_fetch(const DevArrays<R>& d, int idx, TickM
         }
     }
     if constexpr (P == 1) {
+        m.lc = d.loc[m.e];
+        m.rid = d.root[m.e];
+        if constexpr (TickMetaT<DIM, P>::HP) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const bool hanging = ((m.inf >> (4 * f)) & 3) == 3;
+#pragma unroll
+                for (int sb = 0; sb < 2; ++sb) {
+                    m.hg[f][sb] = hanging ? d.hang[m.nbf[f] + sb] : m.e;
+                    m.hgl[f][sb] = d.lvl[m.hg[f][sb]];
+                }
+            }
+        }
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             const int kind = (m.inf >> (4 * f)) & 3;
@@ -522,7 +545,8 @@ __device__ __forceinline__ void residual_q1(const DevArrays<R>& d, int tick, int
         if (kind != 3) continue;
         for (int sb = 0; sb < NSUB; ++sb) {
             R uh[NP];
-            load_seen<R, NP>(d, tick, B, d.hang[m.nbf[f] + sb], uh);
+            if constexpr (TickMetaT<DIM, 1>::HP) load_seen_lv<R, NP>(d, tick, B, m.hg[f][sb], m.hgl[f][sb], uh);
+            else load_seen<R, NP>(d, tick, B, d.hang[m.nbf[f] + sb], uh);
             const R* A = d.qface + ((((size_t)f * 8 + lev) * NREL + 1 + NSUB + sb) * 2) * NP * NP;
             block_mv<R, NP>(A, u, r);
             block_mv<R, NP>(A + NP * NP, uh, r);
@@ -607,7 +631,7 @@ __device__ __forceinline__ R elem_pointwise(const TickArgs<R>& a, const Tables<R
 // v, the RV-T accumulation and the element's probe check.
 template <typename R, int DIM, int P>
 __device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>& T, const Phys<R>& ph, int tick,
-                                          const TickMetaT<DIM, P>& m) {
+                                          const TickMetaT<DIM, P>& m, double t_tick) {
     using S = Shape<DIM, P>;
     constexpr int NP = S::NP;
     const DevArrays<R>& d = a.d;
@@ -653,7 +677,10 @@ __device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>&
     st_vec<R, NP>(vp, wn);
     d.acc[e] = acc0 + dte_d * (double)term;
     if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
-        lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, tick_time(a, tick), dte_d);
+    {
+        if constexpr (P == 1) lat_check_at<R, DIM, P>(d, T, ph, e, inf, lev, m.lc, m.rid, u, un, t_tick, dte_d);
+        else lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, t_tick, dte_d);
+    }
 }
 
 // One tick of Alg. 1 over the due elements (a prefix of `order`), for callers that
@@ -661,10 +688,11 @@ __device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>&
 template <typename R, int DIM, int P>
 __device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>& T, const Phys<R>& ph, int tick) {
     const int n_act = a.d.meta->nact[tick];
+    const double t_tick = tick_time(a, tick);
     for (int idx = (int)gtid(); idx < n_act; idx += (int)gstride()) {
         TickMetaT<DIM, P> m;
         tick_fetch<R, DIM, P>(a.d, idx, m);
-        tick_elem<R, DIM, P>(a, T, ph, tick, m);
+        tick_elem<R, DIM, P>(a, T, ph, tick, m, t_tick);
     }
 }
 
@@ -673,15 +701,18 @@ __global__ void __launch_bounds__(256) k_tick(const TickArgs<R> a, const Tables<
     // the due count and the first element's metadata are fixed during the sweep: read them
     // while the previous tick drains, then wait for its values (the first tick of a sweep
     // is launched without overlap, after the ordering that writes them)
+    // (so are the tick's time and the error word: ticks do not set errors)
     const int n_act = a.d.meta->nact[a.tick];
+    const bool bad = a.d.meta->err != 0;
+    const double t_tick = tick_time(a, a.tick);
     const int idx0 = (int)gtid();
     TickMetaT<DIM, P> m;
     if (idx0 < n_act) tick_fetch<R, DIM, P>(a.d, idx0, m);
     pdl_enter();
-    if (a.d.meta->err) return;
+    if (bad) return;
     for (int idx = idx0; idx < n_act; idx += (int)gstride()) {
         if (idx != idx0) tick_fetch<R, DIM, P>(a.d, idx, m);
-        tick_elem<R, DIM, P>(a, T, ph, a.tick, m);
+        tick_elem<R, DIM, P>(a, T, ph, a.tick, m, t_tick);
     }
 }
 
@@ -863,112 +894,159 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const do
 
 
 
-// Q1 tick with a group of G = (p+1)^d lanes per element (4 in 2D, 8 in 3D).  With the
-// class blocks every face contribution is the same code, A_own u + A_nb u_nb, so lane f
-// gathers and applies face f while the other lanes do the same for their faces (no
-// divergence); the group sums the face terms by shuffles and lane g updates DOF g.
-// Same arithmetic per element as k_tick for Q1, G times more threads in flight.
+// Q1 tick with a group of G = (p+1)^d lanes per element (4 in 2D, 8 in 3D), lane g owning
+// DOF g: it computes row g of the residual from the class blocks (r_g = A_vol[g] u +
+// sum_f A_own,f[g] u + A_nb,f[g] u_nb,f) and the pointwise step of DOF g, so G times more
+// threads are in flight than with a thread per element and each runs a short chain.
+// Everything fixed during the sweep -- the element, its level byte and face info, its
+// neighbours and their level bytes, and in 2D the block rows -- is read before waiting for
+// the previous tick; after the wait every value load is issued at once.
+template <typename R, int DIM>
+struct GroupMeta {
+    static constexpr int NP = Shape<DIM, 1>::NP, NF = 2 * DIM;
+    static constexpr bool ROWS = DIM == 2;     // block rows held in registers (2D only)
+    int e;
+    uint32_t inf;
+    uint8_t lv;
+    int nbf[NF];
+    uint8_t lvn[NF];
+    R vrow[NP];
+    R orow[ROWS ? NF : 1][NP];
+    R nrow[ROWS ? NF : 1][NP];
+};
+
+template <typename R, int DIM>
+__device__ __forceinline__ void group_fetch(const DevArrays<R>& d, int64_t idx, int g, GroupMeta<R, DIM>& m) {
+    using M = GroupMeta<R, DIM>;
+    constexpr int NP = M::NP, NF = M::NF, NREL = 1 + 2 * Shape<DIM, 1>::NSUB;
+    m.e = d.order[idx];
+    m.lv = d.lvl[m.e];
+    m.inf = d.info[m.e];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) m.nbf[f] = d.nbr[(size_t)m.e * NF + f];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const int kind = (m.inf >> (4 * f)) & 3;
+        m.lvn[f] = d.lvl[(kind == 1 || kind == 2) ? m.nbf[f] : m.e];
+    }
+    const int lev = (m.inf >> 24) & 15;
+    ld_row<R, NP>(d.qvol + ((size_t)lev * NP + g) * NP, m.vrow);
+    if constexpr (M::ROWS) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const int kind = (m.inf >> (4 * f)) & 3;
+            const int rel = kind == 2 ? 1 + ((m.inf >> (4 * f + 2)) & 3) : 0;
+            const R* A = d.qface + ((((size_t)f * 8 + lev) * NREL + rel) * 2) * NP * NP;
+            ld_row<R, NP>(A + g * NP, m.orow[f]);
+            ld_row<R, NP>(A + NP * NP + g * NP, m.nrow[f]);
+        }
+    }
+}
+
 template <typename R, int DIM>
 __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const Phys<R> ph, const Tables<R> T) {
-    pdl_enter();
     using S = Shape<DIM, 1>;
+    using M = GroupMeta<R, DIM>;
     constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB, NREL = 1 + 2 * NSUB;
     constexpr int G = NP;
     const DevArrays<R>& d = a.d;
-    if (d.meta->err) return;
-    const int tick = a.tick;
-    const int n_act = d.meta->nact[tick];
+    const int tick = a.tick, B = a.B;
     const int lane = threadIdx.x & 31;
     const int g = lane % G;
     const unsigned gmask = ((1u << G) - 1u) << (lane - g);
     const int64_t gsz = gstride() / G;
-    for (int64_t idx = gtid() / G; idx < n_act; idx += gsz) {
-        const int e = d.order[idx];
-        const uint8_t lv = d.lvl[e];
-        const uint32_t inf = d.info[e];
-        const int b = lv & 7, par = (lv >> 3) & 1;
-        const int ke = tick >> (a.B - b);
+    // per (level, node) GL mass and inverse in shared memory (lanes read different nodes)
+    __shared__ R sMq[8 * NP], sMinv[8 * NP];
+    for (int i = threadIdx.x; i < 8 * NP; i += blockDim.x) {
+        const int l = i / NP, q = i - l * NP;
+        R w = ph.Wvol[l];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) w *= T.w[digit<N1>(q, k)];
+        sMq[i] = w;
+        sMinv[i] = ph.Minv[l][q];
+    }
+    // the due count, the element order and the error word do not change during a sweep
+    // (the first tick of a sweep is launched without overlap, after the ordering)
+    const int n_act = d.meta->nact[tick];
+    const bool bad = d.meta->err != 0;
+    int64_t idx = gtid() / G;
+    M m;
+    if (idx < n_act) group_fetch<R, DIM>(d, idx, g, m);
+    __syncthreads();
+    pdl_enter();
+    if (bad) return;
+    for (bool first = true; idx < n_act; idx += gsz, first = false) {
+        if (!first) group_fetch<R, DIM>(d, idx, g, m);
+        const int e = m.e;
+        const uint32_t inf = m.inf;
+        const int b = m.lv & 7, par = (m.lv >> 3) & 1;
+        const int ke = tick >> (B - b);
         const int cur = par ^ (ke & 1);
         const int lev = (inf >> 24) & 15;
-        const R my_u = ((cur ? d.V1 : d.V0) + (size_t)e * NP)[g];
-        const R my_w = d.v[(size_t)e * NP + g];
-        const int fk = g < NF ? (int)((inf >> (4 * g)) & 3) : 0;
-        const int my_nb = g < NF ? d.nbr[(size_t)e * NF + g] : 0;
+        // every value this step needs: own row, neighbours as seen, state, barrier-start terms
         R u[NP];
+        ld_vec<R, NP>((cur ? d.V1 : d.V0) + (size_t)e * NP, u);
+        const R w = d.v[(size_t)e * NP + g];
+        R un[NF][NP];
 #pragma unroll
-        for (int q = 0; q < NP; ++q) u[q] = __shfl_sync(gmask, my_u, q, G);
-        R rf[NP];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) rf[q] = R(0);
-        if (fk == 1 || fk == 2) {
-            R un[NP];
-            load_seen<R, NP>(d, tick, a.B, my_nb, un);
-            const int rel = fk == 1 ? 0 : 1 + ((inf >> (4 * g + 2)) & 3);
-            const R* A = d.qface + ((((size_t)g * 8 + lev) * NREL + rel) * 2) * NP * NP;
-            block_mv<R, NP>(A, u, rf);
-            block_mv<R, NP>(A + NP * NP, un, rf);
-        } else if (fk == 3) {
-            for (int sb = 0; sb < NSUB; ++sb) {
-                R un[NP];
-                load_seen<R, NP>(d, tick, a.B, d.hang[my_nb + sb], un);
-                const R* A = d.qface + ((((size_t)g * 8 + lev) * NREL + 1 + NSUB + sb) * 2) * NP * NP;
-                block_mv<R, NP>(A, u, rf);
-                block_mv<R, NP>(A + NP * NP, un, rf);
-            }
+        for (int f = 0; f < NF; ++f) {
+            const int kind = (inf >> (4 * f)) & 3;
+            load_seen_lv<R, NP>(d, tick, B, (kind == 1 || kind == 2) ? m.nbf[f] : e, m.lvn[f], un[f]);
         }
-        // group sum of the face terms; lane g keeps row g and adds its volume row
+        R Ia = R(0), ga = R(0);
+        double acc0 = 0.0;
+        if (ke != 0) {
+            Ia = d.Ia[(size_t)e * NP + g];
+            ga = d.ga[(size_t)e * NP + g];
+            if (g == 0) acc0 = d.acc[e];
+        }
+        // row g of the residual
         R rg = R(0);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            R x = rf[q];
+        for (int j = 0; j < NP; ++j) rg += m.vrow[j] * u[j];
 #pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(gmask, x, o, G);
-            if (q == g) rg = x;
-        }
-        {
-            const R* Av = d.qvol + ((size_t)lev * NP + g) * NP;
+        for (int f = 0; f < NF; ++f) {
+            const int kind = (inf >> (4 * f)) & 3;
+            if (kind == 1 || kind == 2) {
+                if constexpr (M::ROWS) {
 #pragma unroll
-            for (int j = 0; j < NP; ++j) rg += __ldg(Av + j) * u[j];
-        }
-        const double dte_d = a.dte[b];
-        const R dte = a.dteR[b];
-        R stim_o = R(0), stim_m = R(0);
-        if (inf & INFO_STIM) {
-            const double t_i = tick_time(a, tick);
-            const double t_mid = t_i + 0.5 * dte_d;
-            for (int s = 0; s < a.stim.n; ++s) {
-                const bool on_o = (a.stim.t0[s] <= t_i) && (t_i < a.stim.t1[s]);
-                const bool on_m = (a.stim.t0[s] <= t_mid) && (t_mid < a.stim.t1[s]);
-                if (!on_o && !on_m) continue;
-                if ((d.smask[s][e] >> g) & 1u) {
-                    if (on_o) stim_o -= (R)a.stim.amp[s];
-                    if (on_m) stim_m -= (R)a.stim.amp[s];
+                    for (int j = 0; j < NP; ++j) rg += m.orow[f][j] * u[j] + m.nrow[f][j] * un[f][j];
+                } else {
+                    const int rel = kind == 2 ? 1 + ((inf >> (4 * f + 2)) & 3) : 0;
+                    const R* A = d.qface + ((((size_t)f * 8 + lev) * NREL + rel) * 2) * NP * NP;
+                    R ro[NP], rn[NP];
+                    ld_row<R, NP>(A + g * NP, ro);
+                    ld_row<R, NP>(A + NP * NP + g * NP, rn);
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) rg += ro[j] * u[j] + rn[j] * un[f][j];
                 }
             }
         }
-        R Iag, gag;
-        if (ke == 0) {
-            Iag = ap_iion(ph, my_u, my_w) + stim_o;
-            gag = ap_g(ph, my_u, my_w);
-            if (b > 0) {
-                d.Ia[(size_t)e * NP + g] = Iag;
-                d.ga[(size_t)e * NP + g] = gag;
-            }
-        } else {
-            Iag = d.Ia[(size_t)e * NP + g];
-            gag = d.ga[(size_t)e * NP + g];
-        }
-        R Mq = ph.Wvol[lev];
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) Mq *= T.w[digit<N1>(g, k)];
-        const R I = ap_iion(ph, my_u, my_w) + stim_o;
-        const R un_g = my_u + dte * (-rg * ph.Minv[lev][g] - I);
-        const R wn_g = ap_step_state(ph, my_u, my_w, dte);
-        const R Vm = R(0.5) * (my_u + un_g);
-        const R wm = R(0.5) * (my_w + wn_g);
-        const R dI = ap_iion(ph, Vm, wm) + stim_m - Iag;
-        const R dg = ap_g(ph, Vm, wm) - gag;
-        R term = Mq * (dI * dI + dg * dg);
+        for (int f = 0; f < NF; ++f) {
+            const int kind = (inf >> (4 * f)) & 3;
+            if (kind != 3) continue;
+            for (int sb = 0; sb < NSUB; ++sb) {
+                R uh[NP], ro[NP], rn[NP];
+                load_seen<R, NP>(d, tick, B, d.hang[m.nbf[f] + sb], uh);
+                const R* A = d.qface + ((((size_t)f * 8 + lev) * NREL + 1 + NSUB + sb) * 2) * NP * NP;
+                ld_row<R, NP>(A + g * NP, ro);
+                ld_row<R, NP>(A + NP * NP + g * NP, rn);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) rg += ro[j] * u[j] + rn[j] * uh[j];
+            }
+        }
+        // pointwise step of DOF g
+        const double dte_d = a.dte[b];
+        R so = R(0), smd = R(0);
+        if (inf & INFO_STIM) dof_stim<R>(a, e, tick, dte_d, g, so, smd);
+        R my_u = u[0];
+#pragma unroll
+        for (int q = 1; q < NP; ++q)
+            if (q == g) my_u = u[q];
+        R un_g, wn_g;
+        R term = dof_update<R>(ph, sMq[lev * NP + g], sMinv[lev * NP + g], ke, a.dteR[b], so, smd, my_u, w, rg, Ia,
+                               ga, un_g, wn_g);
         R vmax = un_g < R(0) ? -un_g : un_g;
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
@@ -978,10 +1056,11 @@ __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const P
         }
         ((cur ? d.V0 : d.V1) + (size_t)e * NP)[g] = un_g;
         d.v[(size_t)e * NP + g] = wn_g;
-        if (g == 0) {
-            const double inc = dte_d * (double)term;
-            d.acc[e] = (ke == 0) ? inc : d.acc[e] + inc;
+        if (ke == 0 && b > 0) {
+            d.Ia[(size_t)e * NP + g] = Ia;
+            d.ga[(size_t)e * NP + g] = ga;
         }
+        if (g == 0) d.acc[e] = acc0 + dte_d * (double)term;
         if ((inf & INFO_PENDING) && vmax >= ph.lat_gate) {
             R unv[NP];
 #pragma unroll
