@@ -359,9 +359,12 @@ __device__ __forceinline__ void element_residual(const DevArrays<R>& d, const Ta
 // in every direction k; a pending probe's values before and after the step are the leaf
 // polynomial at its position, evaluated by sum factorisation.
 // lc, rid: the leaf's cell in its root and the root id (loc[e], root[e]).
+// pend: bit q set if probe q of the root may still be pending (from a read of lat before
+// the step; a probe it marks that has meanwhile activated fails the crossing test below).
 template <typename R, int DIM, int P>
 __device__ void lat_check_at(const DevArrays<R>& d, const Tables<R>& T, const Phys<R>& ph, int e, uint32_t inf,
-                             int lev, uint32_t lc, int64_t rid, const R* u, const R* un, double t_old, double dte) {
+                             int lev, uint32_t lc, int64_t rid, const R* u, const R* un, double t_old, double dte,
+                             uint32_t pend = 0xffffffffu, bool known = false) {
     using S = Shape<DIM, P>;
     constexpr int N1 = S::N1, NP = S::NP;
     const int lx[3] = {(int)(lc & 255u), (int)((lc >> 8) & 255u), (int)((lc >> 16) & 255u)};
@@ -382,11 +385,12 @@ __device__ void lat_check_at(const DevArrays<R>& d, const Tables<R>& T, const Ph
         if (in) im |= 1u << q;
     }
     bool pending = false;
+    im &= pend;
     while (im) {
         const int q = __ffs(im) - 1;
         im &= im - 1u;
         double* lp = d.lat + rid * NP + q;
-        if (!isinf(*lp)) continue;
+        if (!known && !isinf(*lp)) continue;
         R Pk[3][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
@@ -462,6 +466,7 @@ struct TickMeta {
     uint8_t hgl[HP ? NF : 1][2];
     uint32_t lc;                          // probe lookup: cell in the root, root id
     int rid;
+    uint32_t pend;                        // probes of the root with no activation time yet
 };
 // Q2: the neighbours are read face by face inside the residual (holding them would spill)
 template <int NF>
@@ -494,6 +499,15 @@ __device__ __forceinline__ void tick_fetch(const DevArrays<R>& d, int idx, TickM
     if constexpr (P == 1) {
         m.lc = d.loc[m.e];
         m.rid = d.root[m.e];
+        // activation times of the root's probes (only this leaf writes those inside it, at its
+        // own steps; a value read before the previous tick's write only repeats a check)
+        m.pend = 0u;
+        if (m.inf & INFO_PENDING) {
+            constexpr int NP = Shape<DIM, P>::NP;
+#pragma unroll
+            for (int q = 0; q < NP; ++q)
+                if (isinf(d.lat[(int64_t)m.rid * NP + q])) m.pend |= 1u << q;
+        }
         if constexpr (TickMetaT<DIM, P>::HP) {
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -678,7 +692,8 @@ __device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>&
     d.acc[e] = acc0 + dte_d * (double)term;
     if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
     {
-        if constexpr (P == 1) lat_check_at<R, DIM, P>(d, T, ph, e, inf, lev, m.lc, m.rid, u, un, t_tick, dte_d);
+        if constexpr (P == 1)
+            lat_check_at<R, DIM, P>(d, T, ph, e, inf, lev, m.lc, m.rid, u, un, t_tick, dte_d, m.pend, true);
         else lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, t_tick, dte_d);
     }
 }
