@@ -692,9 +692,10 @@ __device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>&
     d.acc[e] = acc0 + dte_d * (double)term;
     if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
     {
+        const double tt = t_tick >= 0.0 ? t_tick : tick_time(a, tick);
         if constexpr (P == 1)
-            lat_check_at<R, DIM, P>(d, T, ph, e, inf, lev, m.lc, m.rid, u, un, t_tick, dte_d, m.pend, true);
-        else lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, t_tick, dte_d);
+            lat_check_at<R, DIM, P>(d, T, ph, e, inf, lev, m.lc, m.rid, u, un, tt, dte_d, m.pend, true);
+        else lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, tt, dte_d);
     }
 }
 
@@ -703,7 +704,7 @@ __device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>&
 template <typename R, int DIM, int P>
 __device__ __forceinline__ void tick_work(const TickArgs<R>& a, const Tables<R>& T, const Phys<R>& ph, int tick) {
     const int n_act = a.d.meta->nact[tick];
-    const double t_tick = tick_time(a, tick);
+    const double t_tick = -1.0;   // computed where a probe check needs it
     for (int idx = (int)gtid(); idx < n_act; idx += (int)gstride()) {
         TickMetaT<DIM, P> m;
         tick_fetch<R, DIM, P>(a.d, idx, m);
@@ -719,10 +720,11 @@ __global__ void __launch_bounds__(256) k_tick(const TickArgs<R> a, const Tables<
     // (so are the tick's time and the error word: ticks do not set errors)
     const int n_act = a.d.meta->nact[a.tick];
     const bool bad = a.d.meta->err != 0;
-    const double t_tick = tick_time(a, a.tick);
     const int idx0 = (int)gtid();
     TickMetaT<DIM, P> m;
     if (idx0 < n_act) tick_fetch<R, DIM, P>(a.d, idx0, m);
+    // the tick's time (FP64, a slow pipe here) only where a probe check may need it
+    const double t_tick = (idx0 < n_act && (m.inf & INFO_PENDING)) ? tick_time(a, a.tick) : -1.0;
     pdl_enter();
     if (bad) return;
     for (int idx = idx0; idx < n_act; idx += (int)gstride()) {
