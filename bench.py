@@ -44,6 +44,7 @@ WORKLOADS = {
     # name: (problem factory, algorithmic bytes per DOF-update, kernel name)
     "slab2d": (W.slab_2d_q1_256, 25.0, "<float,2,1>"),
     "slab3d": (W.slab_3d_q2, 17.6, "<float,3,2>"),
+    "spiral2d": (W.spiral_2d_q1, 25.0, "<float,2,1>"),
 }
 SETUP_BARRIERS = 5
 # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum)
@@ -132,6 +133,8 @@ def prob_order(factory):
 
 def workload_name(prob):
     b = prob.base
+    if prob.dim == 2 and not prob.amr_enabled:
+        return "spiral2d_q1_%dx%d_lts%d_taucell_ap_fp32" % (b[0], b[1], prob.n_lts_levels)
     if prob.dim == 2:
         return "slab2d_q1_%dx%d_amr3_lts4_ap_fp32" % (b[0], b[1])
     return "slab3d_q2_%dx%dx%d_amr3_lts4_ap_fp32" % (b[0], b[1], b[2])
@@ -187,7 +190,9 @@ def run_ours(args, rank, world):
         t, k = (int(x) for x in args.tick_shape.split(","))
         sim.set_tick_shape(t, k)
     X = node_coords_of(sim, prob)
-    if prob.dim == 2:
+    if args.workload == "spiral2d":
+        V0, v0 = W.spiral_state(X, prob.extent[0])
+    elif prob.dim == 2:
         # a scaled base keeps the front at the same fraction of the domain
         V0, v0 = W.front_state(X, FRONT["origin"], FRONT["radius"] * prob.extent[0] / 2.0, FRONT["width"],
                                FRONT["tail"])
@@ -260,9 +265,12 @@ def run_ours(args, rank, world):
                        "domain_cm": list(prob.extent[:prob.dim]), "base": list(prob.base[:prob.dim]),
                        "max_refine": prob.max_refine, "n_lts_levels": prob.n_lts_levels,
                        "dt_barrier_ms": sim.dt, "n_elements": n_e, "n_dof": n_dof,
-                       "level_counts": st["level_counts"][:4],
-                       "initial_state": ("synthetic developed front, r=1.0 cm, width 0.01 cm" if prob.dim == 2
-                                         else "synthetic planar front at x=1.0 cm, width 0.012 cm"),
+                       "level_counts": st["level_counts"][:prob.n_lts_levels],
+                       "initial_state": ("synthetic broken planar wave (spiral onset), band x < 1/4 side"
+                                         if args.workload == "spiral2d" else
+                                         "synthetic developed front, r=%.2f cm, width 0.01 cm" % (prob.extent[0] / 2.0)
+                                         if prob.dim == 2 else
+                                         "synthetic planar front at x=%.2f cm, width 0.012 cm" % (prob.extent[0] / 2.0)),
                        "l2": "512 MiB flush buffer written between timed steps",
                        "parallelism": "replicas" if world > 1 else "single"},
             "dof_updates_per_step": st["dof_updates"] / args.steps,

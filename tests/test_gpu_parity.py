@@ -384,3 +384,53 @@ def test_full_size_slab2d_replay_matches_oracle(mdl):
     big = es_o > 1e-3 * es_o.max()
     assert np.abs(es_g[big] - es_o[big]).max() <= 5e-3 * es_o.max()
     g.close()
+
+
+# --------------------------------------------------------------------------
+# Temporal adaptivity: the cell-model substep b^cell (Eq. num-substeps) set free-running
+# from the element's own temporal indicator, on the spiral-wave workload (broken wave).
+# --------------------------------------------------------------------------
+
+def spiral_case(mdl, precision):
+    prob = W.spiral_2d_q1(12).replace(precision=precision)
+    o = lts.Sim(prob)
+    X = o.disc.node_coords()
+    V0, v0 = W.spiral_state(X, prob.extent[0])
+    o.V, o.v = V0.copy(), v0.copy()
+    o._lat_initial()
+    g = mdl.Sim(prob)
+    g.set_initial(V0, v0)
+    bcfl = np.array([lts.b_from_bound(o.dt, c) for c in o.cfl()])
+    return prob, o, g, bcfl
+
+
+def test_spiral_cell_substeps_fp64_free_running(mdl):
+    """FP64: levels (b^CFL and b^cell from the GPU's own eta^t) bit-exact every barrier,
+    b^cell raising some elements above their CFL level, V and eta^t at 1e-12 / 1e-10."""
+    prob, o, g, bcfl = spiral_case(mdl, 64)
+    raised = 0
+    for n in range(6):
+        lev = o.assign_levels(o.eta_t)
+        raised += int(np.sum(lev > bcfl))
+        o.eta_t = o.sweep(lev)
+        o.barrier_count += 1
+        g.step_barriers(1)
+        assert np.array_equal(g.read_mesh()[3], lev), n
+    assert raised > 0
+    assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-12
+    assert np.allclose(g.read_indicators()[1], o.eta_t, rtol=1e-10, atol=1e-300)
+    lat_compare(g.read_activation(), o.lat, 1e-9)
+    g.close()
+
+
+def test_spiral_cell_substeps_fp32_replay(mdl):
+    """FP32 with the oracle's levels replayed each barrier: V within 1e-3."""
+    prob, o, g, bcfl = spiral_case(mdl, 32)
+    for n in range(6):
+        lev = o.assign_levels(o.eta_t)
+        o.eta_t = o.sweep(lev)
+        o.barrier_count += 1
+        g.set_levels(lev.astype(np.int8))
+        g.step_barriers(1)
+    assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-3
+    g.close()
