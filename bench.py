@@ -52,7 +52,9 @@ SETUP_BARRIERS = 5
 # their proportion (tick 0 once, the finer ticks 7 times).  ncu replays each launch with
 # cold caches, so this is an upper bound on the live traffic.  Set to None whenever the
 # kernel changes until it is captured again.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    "k_tick<float,2,1>": (10.348288e6 + 7 * 5.934080e6) / 8.0,
+}
 # Algorithmic bytes per DOF-update of the fused sweep (Q1 2D, FP32, AP): V_old 4 + v 4 +
 # V_new 4 + v 4 = 16 B, plus per element step 2d neighbour ids + 4 B level/flags + the FP64
 # RV-T accumulator read-modify-write (36 B) over (p+1)^d = 4 DOFs.
