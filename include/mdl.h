@@ -146,6 +146,14 @@ int mdl_get_sizes(const mdl_ctx* ctx, int64_t* n_e, int64_t* n_dof, int64_t* n_p
 int mdl_read_V(mdl_ctx* ctx, double* out, int64_t cap, int64_t* n);
 int mdl_read_state(mdl_ctx* ctx, double* out, int64_t cap, int64_t* n);
 
+/* FP32 transfers of the fields, for callers that stage them in FP32 (the working
+ * precision of FP32 contexts; half the bytes of the FP64 calls).  mdl_set_initial_f32
+ * behaves as mdl_set_initial.  mdl_read_fields_f32 writes V and the state variable (either
+ * pointer may be NULL) at every DOF in leaf order with one gather and one synchronisation;
+ * cap and *n are counted in DOFs per field. */
+int mdl_set_initial_f32(mdl_ctx* ctx, const float* V, const float* s, int64_t n_dof);
+int mdl_read_fields_f32(mdl_ctx* ctx, float* V, float* s, int64_t cap, int64_t* n);
+
 /* Activation time at each probe: the GL nodes of every root element, probe id =
  * root_id (p+1)^d + local node.  +INF = not activated (Sec. 3.3 LAT). */
 int mdl_read_activation(mdl_ctx* ctx, double* out, int64_t cap, int64_t* n);

@@ -177,6 +177,12 @@ int mdl_get_sizes(const mdl_ctx* ctx, int64_t* n_e, int64_t* n_dof, int64_t* n_p
     return ctx->impl->get_sizes(n_e, n_dof, n_probe);
 }
 
+int mdl_set_initial_f32(mdl_ctx* ctx, const float* V, const float* s, int64_t n_dof) {
+    MDL_CALL(ctx, set_initial_f32(V, s, n_dof));
+}
+int mdl_read_fields_f32(mdl_ctx* ctx, float* V, float* s, int64_t cap, int64_t* n) {
+    MDL_CALL(ctx, read_fields_f32(V, s, cap, n));
+}
 int mdl_read_V(mdl_ctx* ctx, double* out, int64_t cap, int64_t* n) { MDL_CALL(ctx, read_field(0, out, cap, n)); }
 int mdl_read_state(mdl_ctx* ctx, double* out, int64_t cap, int64_t* n) { MDL_CALL(ctx, read_field(1, out, cap, n)); }
 int mdl_read_activation(mdl_ctx* ctx, double* out, int64_t cap, int64_t* n) {

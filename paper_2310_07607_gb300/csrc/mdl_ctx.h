@@ -20,6 +20,8 @@ public:
     virtual int get_time(double* t, int64_t* tick, double* dt) const = 0;
     virtual int get_sizes(int64_t* ne, int64_t* ndof, int64_t* nprobe) const = 0;
     virtual int read_field(int which, double* out, int64_t cap, int64_t* n) = 0;
+    virtual int set_initial_f32(const float* V, const float* s, int64_t n_dof) = 0;
+    virtual int read_fields_f32(float* V, float* s, int64_t cap, int64_t* n) = 0;
     virtual int read_activation(double* out, int64_t cap, int64_t* n) = 0;
     virtual int read_mesh(int32_t* root, int8_t* level, int32_t* coords, int8_t* b, int64_t cap, int64_t* n) = 0;
     virtual int read_faces(int8_t* kind, int32_t* nbr, int8_t* pos, int64_t cap, int64_t* n) = 0;

@@ -116,6 +116,7 @@ class Ctx : public CtxBase {
     int cs = 0;
     DBuf<R> Ia, ga;
     DBuf<double> acc, eta_s, lat, partial, scratch;
+    DBuf<float> fscratch;   // FP32 field transfers
     DBuf<uint8_t> r, c0, class_b;
     DBuf<int32_t> owner, bcnt, psrc;
     DBuf<int64_t> bsum;
@@ -586,7 +587,7 @@ public:
         drop_graphs();
         for (auto& s : sets) s.release();
         Ia.release(); ga.release(); acc.release(); eta_s.release(); lat.release(); partial.release();
-        scratch.release(); r.release(); c0.release(); class_b.release(); owner.release();
+        scratch.release(); fscratch.release(); r.release(); c0.release(); class_b.release(); owner.release();
         bcnt.release(); psrc.release(); bsum.release(); pkind.release(); pbits.release();
         bcfl.release(); info.release(); loc.release(); nbr.release(); hang.release(); root.release();
         order.release();
@@ -739,7 +740,7 @@ public:
         MDL_CK(scratch.ensure((size_t)2 * n_dof));
         MDL_CK(cudaMemcpyAsync(scratch.p, V, n_dof * 8, cudaMemcpyHostToDevice, st));
         if (s) MDL_CK(cudaMemcpyAsync(scratch.p + n_dof, s, n_dof * 8, cudaMemcpyHostToDevice, st));
-        k_scatter_initial<R, NP><<<div_up(n_dof, 256), 256, 0, st>>>(arrays(cs), ne, scratch.p,
+        k_scatter_initial<R, NP, double><<<div_up(n_dof, 256), 256, 0, st>>>(arrays(cs), ne, scratch.p,
                                                                      s ? scratch.p + n_dof : nullptr);
         MDL_LAUNCHED();
         MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
@@ -941,6 +942,7 @@ public:
         }
         add(Ia.cap + ga.cap, sizeof(R));
         add(acc.cap + eta_s.cap + lat.cap + partial.cap + scratch.cap + eta_t_ovr.cap + mtab.cap, 8);
+        add(fscratch.cap, 4);
         add(r.cap + c0.cap + class_b.cap + bcfl.cap + pkind.cap + pbits.cap + lvl_ovr.cap, 1);
         add(owner.cap + bcnt.cap + psrc.cap + nbr.cap + hang.cap + root.cap + order.cap + info.cap + loc.cap, 4);
         for (const auto& m : smask) add(m.cap, 4);
@@ -981,6 +983,40 @@ public:
         k_gather<R, NP><<<div_up(nd, 256), 256, 0, st>>>(arrays(cs), ne, which, scratch.p);
         MDL_LAUNCHED();
         MDL_CK(cudaMemcpyAsync(out, scratch.p, nd * 8, cudaMemcpyDeviceToHost, st));
+        MDL_CK(cudaStreamSynchronize(st));
+        return MDL_OK;
+    }
+
+    int set_initial_f32(const float* V, const float* s, int64_t n_dof) override {
+        if (n_dof != ne * NP || !V) {
+            err = "set_initial_f32: n_dof must be n_elements * (p+1)^d";
+            return MDL_E_ARG;
+        }
+        MDL_CK(fscratch.ensure((size_t)2 * n_dof));
+        MDL_CK(cudaMemcpyAsync(fscratch.p, V, n_dof * sizeof(float), cudaMemcpyHostToDevice, st));
+        if (s) MDL_CK(cudaMemcpyAsync(fscratch.p + n_dof, s, n_dof * sizeof(float), cudaMemcpyHostToDevice, st));
+        k_scatter_initial<R, NP, float><<<div_up(n_dof, 256), 256, 0, st>>>(arrays(cs), ne, fscratch.p,
+                                                                            s ? fscratch.p + n_dof : nullptr);
+        MDL_LAUNCHED();
+        MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
+        k_lat_refresh<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(arrays(cs), T, ph, (double)nbar * dt, 1, 1);
+        MDL_LAUNCHED();
+        MDL_CK(cudaStreamSynchronize(st));
+        return MDL_OK;
+    }
+
+    int read_fields_f32(float* V, float* s, int64_t cap_, int64_t* n) override {
+        const int64_t nd = ne * NP;
+        if (n) *n = nd;
+        if (cap_ < nd || (!V && !s)) {
+            err = "read_fields_f32: capacity too small";
+            return MDL_E_ARG;
+        }
+        MDL_CK(fscratch.ensure((size_t)2 * nd));
+        k_gather_f32<R, NP><<<div_up(nd, 256), 256, 0, st>>>(arrays(cs), ne, fscratch.p);
+        MDL_LAUNCHED();
+        if (V) MDL_CK(cudaMemcpyAsync(V, fscratch.p, nd * sizeof(float), cudaMemcpyDeviceToHost, st));
+        if (s) MDL_CK(cudaMemcpyAsync(s, fscratch.p + nd, nd * sizeof(float), cudaMemcpyDeviceToHost, st));
         MDL_CK(cudaStreamSynchronize(st));
         return MDL_OK;
     }
@@ -1089,7 +1125,7 @@ public:
                 if (rc) return rc;
                 MDL_CK(scratch.ensure(2 * ne * NP));
                 MDL_CK(cudaMemcpyAsync(scratch.p, tmp.data(), ne * NP * 8, cudaMemcpyHostToDevice, st));
-                k_scatter_initial<R, NP><<<div_up(ne * NP, 256), 256, 0, st>>>(arrays(cs), ne, scratch.p, nullptr);
+                k_scatter_initial<R, NP, double><<<div_up(ne * NP, 256), 256, 0, st>>>(arrays(cs), ne, scratch.p, (const double*)nullptr);
                 MDL_LAUNCHED();
                 MDL_CK(cudaStreamSynchronize(st));
                 if (p) *p = sets[cs].V0.p;

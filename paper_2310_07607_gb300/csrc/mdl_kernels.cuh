@@ -1170,9 +1170,19 @@ __global__ void k_gather(const DevArrays<R> d, int64_t ne, int which, double* ou
     }
 }
 
-// Set V (into slot 0, parity reset) and optionally v from FP64 input.
+// V (current slot) and the state variable into one FP32 buffer [V | v].
 template <typename R, int NP>
-__global__ void k_scatter_initial(DevArrays<R> d, int64_t ne, const double* V, const double* w) {
+__global__ void k_gather_f32(const DevArrays<R> d, int64_t ne, float* out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ne * NP) return;
+    const int par = (d.lvl[i / NP] >> 3) & 1;
+    out[i] = (float)((par ? d.V1 : d.V0)[i]);
+    out[ne * NP + i] = (float)d.v[i];
+}
+
+// Set V (into slot 0, parity reset) and optionally v from FP64 or FP32 input.
+template <typename R, int NP, typename In>
+__global__ void k_scatter_initial(DevArrays<R> d, int64_t ne, const In* V, const In* w) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= ne * NP) return;
     d.V0[i] = (R)V[i];

@@ -73,6 +73,7 @@ EXPORTS = [
     "mdl_noalloc_last_error", "mdl_set_tick_shape", "mdl_set_sweep_variant", "mdl_batch_create", "mdl_batch_footprint",
     "mdl_batch_admit", "mdl_batch_step", "mdl_batch_poll", "mdl_batch_slot", "mdl_batch_release",
     "mdl_batch_usage", "mdl_batch_shape", "mdl_batch_last_error", "mdl_batch_destroy",
+    "mdl_set_initial_f32", "mdl_read_fields_f32",
 ]
 
 SLOT_FREE, SLOT_RUNNING, SLOT_DONE, SLOT_FAILED = 0, 1, 2, 3
@@ -100,6 +101,9 @@ def load(path: Optional[str] = None):
     lib.mdl_step_to.argtypes = [vp, C.c_double]
     lib.mdl_step_barriers.argtypes = [vp, i64]
     lib.mdl_get_time.argtypes = [vp, dp, C.POINTER(i64), dp]
+    fp = C.POINTER(C.c_float)
+    lib.mdl_set_initial_f32.argtypes = [vp, fp, fp, i64]
+    lib.mdl_read_fields_f32.argtypes = [vp, fp, fp, i64, C.POINTER(i64)]
     lib.mdl_get_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     for f in ("mdl_read_V", "mdl_read_state", "mdl_read_activation"):
         getattr(lib, f).argtypes = [vp, vp, i64, C.POINTER(i64)]
@@ -231,6 +235,29 @@ class Sim:
         V = np.ascontiguousarray(V, dtype=np.float64)
         sv = None if s is None else np.ascontiguousarray(s, dtype=np.float64)
         self._check(self.lib.mdl_set_initial(self.h, _ptr(V), _ptr(sv), V.size))
+
+    def set_initial_f32(self, V, s=None):
+        """set_initial from FP32 arrays (half the transfer of the FP64 call)."""
+        V = np.ascontiguousarray(V, dtype=np.float32)
+        sv = None if s is None else np.ascontiguousarray(s, dtype=np.float32)
+        f = C.POINTER(C.c_float)
+        self._check(self.lib.mdl_set_initial_f32(self.h, V.ctypes.data_as(f),
+                                                 None if sv is None else sv.ctypes.data_as(f), V.size))
+
+    def read_fields_f32(self, V=None, s=None):
+        """(V, state) in FP32 with one gather and one copy each; V, s may be caller buffers
+        (e.g. pinned) of at least n_dof float32 values."""
+        n = self.sizes()[1]
+        V = np.empty(n, np.float32) if V is None else V
+        s = np.empty(n, np.float32) if s is None else s
+        for a in (V, s):
+            if a.dtype != np.float32 or not a.flags.c_contiguous or a.size < n:
+                raise ValueError("buffers must be contiguous float32 arrays of at least %d values" % n)
+        got = C.c_int64()
+        f = C.POINTER(C.c_float)
+        self._check(self.lib.mdl_read_fields_f32(self.h, V.ctypes.data_as(f), s.ctypes.data_as(f),
+                                                 min(V.size, s.size), C.byref(got)))
+        return V[:n], s[:n]
 
     def set_levels(self, b):
         b = np.ascontiguousarray(b, dtype=np.int8)

@@ -434,3 +434,22 @@ def test_spiral_cell_substeps_fp32_replay(mdl):
         g.step_barriers(1)
     assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-3
     g.close()
+
+
+def test_fp32_field_transfers_match_fp64_calls(mdl):
+    """set_initial_f32 / read_fields_f32 against the FP64 calls on an FP32 context: the same
+    stored values (FP32 either way), bit for bit, also after a step."""
+    prob = W.slab_2d_q1_256().replace(base=(24, 20, 1), extent=(24 * 2.0 / 256, 20 * 2.0 / 256, 1.0))
+    a, b = mdl.Sim(prob), mdl.Sim(prob)
+    X = lts.Sim(prob.replace(amr_enabled=0)).disc.node_coords()   # base grid, leaf order
+    V, s = W.front_state(X, (0, 0, 0), 0.1, 0.01, tail=0.3)
+    assert V.size == a.sizes()[1]
+    a.set_initial(V, s)
+    b.set_initial_f32(V.astype(np.float32), s.astype(np.float32))
+    for sim_steps in (0, 2):
+        a.step_barriers(sim_steps)
+        b.step_barriers(sim_steps)
+        Vb, sb = b.read_fields_f32()
+        assert np.array_equal(a.read_V(), Vb.astype(np.float64))
+        assert np.array_equal(a.read_state(), sb.astype(np.float64))
+    a.close(); b.close()
