@@ -139,3 +139,46 @@ def test_tensor_variant_rejected_elsewhere(mdl):
             g.set_sweep_variant(mdl.SWEEP_TENSOR)
         g.step_barriers(1)
         g.close()
+
+
+def test_full_size_slab3d_tensor_matches_thread(mdl):
+    """The 3D slab at full size (128x48x20 roots, AMR to depth 3, 4 LTS levels, 2.7M
+    elements), in the benchmark's launch configuration: from one state on one refined mesh,
+    one barrier step with the tensor-core sweep and one with the thread-per-element CUDA-core
+    sweep (an independent evaluation of the same SIPG residual) agree to FP32 rounding in V,
+    the state and eta^t, with identical meshes, levels and activation sets.  (The oracle is
+    checked against both on small meshes; at this size it cannot run.)"""
+    import bench as B
+    prob = W.slab_3d_q2()
+    a = mdl.Sim(prob)
+    a.set_sweep_variant(mdl.SWEEP_THREAD)
+    X = B.node_coords_of(a, prob)
+    V0, v0 = W.planar_front_state(X, B.PLANAR["x0"], B.PLANAR["width"], B.PLANAR["tail"])
+    a.set_initial(V0, v0)
+    a.step_barriers(4)                      # AMR refines the front to depth 3
+    root, level, coords, _ = a.read_mesh()
+    V1, s1 = a.read_V(), a.read_state()
+    assert level.max() == 3 and level.size > 2_000_000
+    b = mdl.Sim(prob)
+    b.set_sweep_variant(mdl.SWEEP_TENSOR)
+    b.upload_mesh(level, coords.reshape(-1), root)
+    b.set_initial(V1, s1)
+    a.upload_mesh(level, coords.reshape(-1), root)
+    a.set_initial(V1, s1)
+    a.step_barriers(1)
+    b.step_barriers(1)
+    ma, mb = a.read_mesh(), b.read_mesh()
+    for x, y in zip(ma, mb):
+        assert np.array_equal(x, y)
+    assert len(set(mb[3].tolist())) >= 3
+    Va, Vb = a.read_V(), b.read_V()
+    rel = np.linalg.norm(Vb - Va) / np.linalg.norm(Va)
+    assert rel <= 1e-5, rel
+    sa, sb = a.read_state(), b.read_state()
+    assert np.linalg.norm(sb - sa) <= 1e-5 * np.linalg.norm(sa)
+    ea, eb = a.read_indicators()[1], b.read_indicators()[1]
+    big = ea > 1e-6 * ea.max()
+    assert np.max(np.abs(eb[big] - ea[big]) / ea[big]) <= 1e-2
+    la, lb = a.read_activation(), b.read_activation()
+    assert np.array_equal(np.isfinite(la), np.isfinite(lb))
+    a.close(); b.close()
