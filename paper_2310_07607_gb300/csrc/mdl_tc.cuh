@@ -236,11 +236,11 @@ __device__ __forceinline__ float block_row_dot(const float* __restrict__ row, co
 //      issued at once, then the row mean c, y = x - c, the row's power-of-two scale and
 //      the FP16 hi/lo terms in the swizzled operand layout
 //   2  one thread issues the MMAs and commits to an mbarrier
-//   3  while they run: corrections of non-regular faces (warp per element, lane = row) and
-//      the loads of the pointwise step, item by item (element, DOF)
+//   3  while they run: corrections of non-regular faces (warps 1-7, warp per element, lane =
+//      row) and the loads of the pointwise step, item by item (element, DOF)
 //   4  warps 0-3: D row -> scaled residual in shared memory
 //   5  the pointwise step (dof_update) of every item with coalesced stores
-//   6  per element: the RV-T accumulation and the probe checks
+//   6  per element (four threads each): the RV-T accumulation and the probe checks
 // unscale = 2^-t undoes the scaling of B by 2^t; each row's scale of y is undone by 2^-sc.
 template <int DIM, int P>
 __global__ void __launch_bounds__(tc::THREADS, 2)
@@ -308,7 +308,6 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
     pdl_enter();
     uint32_t parity = 0;
     bool ok = d.meta->err == 0;
-    double acc0 = 0.0;   // threads 0..63: RV-T accumulator of the tile's element tid
     // Metadata of a tile's element (threads 0..63) is fetched one tile ahead: the ids when a
     // tile starts, their level bytes, face info and neighbours while its gather runs, the
     // neighbours' level bytes while its pointwise step runs (kept in sNx / sNx2).
@@ -386,8 +385,6 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             bool irr = false;
 #pragma unroll
             for (int f = 0; f < 6; ++f) irr = irr || (((inf >> (4 * f)) & 3) != 1);
-            // the element's RV-T accumulator, needed at the end of the tile (ke != 0)
-            acc0 = (e >= 0 && (tick >> (B - b)) != 0) ? d.acc[e] : 0.0;
             sE[tid] = e;
             sInf[tid] = inf;
             sLv[tid] = lv;
@@ -482,15 +479,14 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
 
         // ---- 3: non-regular faces (boundary, coarser, finer neighbours): exact face terms minus
         //      the same-level own blocks the tensor product assumed, from level-0 correction
-        //      blocks; warp w takes elements 8 w .. 8 w + 7, lane q = row q, on the operand's
-        //      mean-shifted values (the same c as the MMA)
+        //      blocks; warp w >= 1 takes elements w - 1, w + 6, ... (warp 0 issues the MMAs),
+        //      lane q = row q, on the operand's mean-shifted values (the same c as the MMA)
         {
             const int q = lane < NP ? lane : NP - 1;
             float* su = sScr + warp * 64;
             float* sn = su + 32;
 #pragma unroll 1
-            for (int j = 0; j < 8; ++j) {
-                const int i = warp * 8 + j;
+            for (int i = warp - 1; warp > 0 && i < M; i += 7) {
                 if (!sIrr[i]) continue;
                 const uint32_t inf = sInf[i];
                 const float c = sC[i];
@@ -539,6 +535,12 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             w[m] = d.v[(size_t)es * NP + q];
             Ia[m] = need ? d.Ia[(size_t)es * NP + q] : 0.0f;
             ga[m] = need ? d.ga[(size_t)es * NP + q] : 0.0f;
+        }
+        // thread 4 i: the RV-T accumulator of element i, needed at the end of the tile (ke != 0)
+        double acc0 = 0.0;
+        if ((tid & 3) == 0) {
+            const int e = sE[tid >> 2];
+            if (e >= 0 && (tick >> (B - (sLv[tid >> 2] & 7))) != 0) acc0 = d.acc[e];
         }
 
         // ---- 4: residual rows (warps 0-3; thread t < 16 of warp w holds row 16 w + t)
@@ -609,21 +611,28 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
         }
         __syncthreads();
         if (tid < M) {
-            // ---- 6: per element: RV-T accumulation (terms summed in DOF order), probe checks
             sNx[tid * 8 + 7] = nxr[7] | (int)(nlo << 8);
             sNx2[tid] = nhi;
-            const int i = tid, e = sE[i];
-            if (e >= 0) {
-                const float* sT = reinterpret_cast<const float*>(sm + OFF_UHI);
-                const float* sUo = sT + M * NP;
-                const float* sUn = sUo + M * NP;
+        }
+        {
+            // ---- 6: per element i (threads 4 i .. 4 i + 3, DOFs q = p mod 4): RV-T sum and
+            //      max |V_new|, the accumulation and the probe checks
+            const int i = tid >> 2, p = tid & 3, e = sE[i];
+            const float* sT = reinterpret_cast<const float*>(sm + OFF_UHI);
+            const float* sUo = sT + M * NP;
+            const float* sUn = sUo + M * NP;
+            float term = 0.0f, vmax = 0.0f;
+            for (int q = p; q < NP; q += 4) {
+                term += sT[i * NP + q];
+                vmax = fmaxf(vmax, fabsf(sUn[i * NP + q]));
+            }
+            term += __shfl_xor_sync(0xffffffffu, term, 1);
+            vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 1));
+            term += __shfl_xor_sync(0xffffffffu, term, 2);
+            vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 2));
+            if (p == 0 && e >= 0) {
                 const uint32_t inf = sInf[i];
                 const int b = sLv[i] & 7;
-                float term = 0.0f, vmax = 0.0f;
-                for (int q = 0; q < NP; ++q) {
-                    term += sT[i * NP + q];
-                    vmax = fmaxf(vmax, fabsf(sUn[i * NP + q]));
-                }
                 d.acc[e] = acc0 + a.dte[b] * (double)term;
                 if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
                     lat_check<float, DIM, P>(d, T, ph, e, inf, (inf >> 24) & 15, sUo + i * NP, sUn + i * NP,
