@@ -76,8 +76,8 @@ constexpr int OFF_IRR = OFF_INTP + M;                 // uint8 element has a non
 constexpr int OFF_CORR = ((OFF_IRR + M + 15) / 16) * 16;  // float [M][RST] residual corrections
 constexpr int OFF_NX = OFF_CORR + M * RST * 4;        // next tile: int32 [M][8] = info, nbr[6], lvl | lvn[f] << 8 (f < 3)
 constexpr int OFF_NX2 = OFF_NX + M * 8 * 4;           // next tile: uint32 [M] lvn[f] for f >= 3
-constexpr int OFF_MTAB = OFF_NX2 + M * 4;             // float [8][27] GL mass, then [8][27] inverse
-constexpr int OFF_MBAR = ((OFF_MTAB + 2 * 8 * NP * 4 + 7) / 8) * 8;
+constexpr int OFF_MTAB = OFF_NX2 + M * 4;             // float [8][27] GL mass, [8][27] inverse, [8] dt_e
+constexpr int OFF_MBAR = ((OFF_MTAB + (2 * 8 * NP + 8) * 4 + 7) / 8) * 8;
 constexpr int OFF_FLAG = OFF_MBAR + 8;
 constexpr int OFF_TMEM = OFF_FLAG + 8;
 constexpr int SMEM_BYTES = OFF_TMEM + 16 + 1024;      // + alignment slack of the dynamic base
@@ -199,6 +199,32 @@ __device__ __forceinline__ void issue_tile_mma(uint32_t tmem, uint32_t sUhi, uin
     mma_commit(mbar);
 }
 
+// dof_update for an element past its first step of the barrier (ke != 0), without stimulus,
+// under the Aliev-Panfilov model (ionic 0) with the exponential state step (integrator 1):
+// the same expressions as ap_iion, ap_g and ap_step_state without their model and
+// integrator branches, and e^x - 1 as a select of both forms, so that the code is
+// straight-line and the items of a thread can interleave.
+__device__ __forceinline__ float dof_update_ap(const Phys<float>& ph, float Mq, float Minv, float dte, float u, float w,
+                                               float r, float Ia, float ga, float& un, float& wn) {
+    const float I = (ph.k * u * (u - ph.a) * (u - 1.0f) + u * w) * ph.inv_ts;
+    un = u + dte * (-r * Minv - I);
+    const float vinf = -ph.k * u * (u - ph.a - 1.0f);
+    const float den = fmaxf(u + ph.mu2, 1e-6f);
+    const float eps = ph.eps0 + __fdividef(ph.mu1 * w, den);
+    const float x = -eps * dte * ph.inv_ts;
+    const float em1_t =
+        x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f + x * (1.0f / 720.0f))))));
+    const float em1_e = expf(x) - 1.0f;
+    wn = w + (w - vinf) * (fabsf(x) < 0.0625f ? em1_t : em1_e);
+    const float Vm = 0.5f * (u + un);
+    const float wm = 0.5f * (w + wn);
+    const float dI = (ph.k * Vm * (Vm - ph.a) * (Vm - 1.0f) + Vm * wm) * ph.inv_ts - Ia;
+    const float vinf_m = -ph.k * Vm * (Vm - ph.a - 1.0f);
+    const float den_m = fmaxf(Vm + ph.mu2, 1e-6f);
+    const float dg = (ph.eps0 + __fdividef(ph.mu1 * wm, den_m)) * (vinf_m - wm) * ph.inv_ts - ga;
+    return Mq * (dI * dI + dg * dg);
+}
+
 }  // namespace tc
 
 // Values of DOF q of element nb as seen at tick `tick` (Alg. 1): its current value if due,
@@ -269,6 +295,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
     uint32_t* sNx2 = reinterpret_cast<uint32_t*>(sm + OFF_NX2);
     float* sMq = reinterpret_cast<float*>(sm + OFF_MTAB);
     float* sMinv = sMq + 8 * NP;
+    float* sDte = sMinv + 8 * NP;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + OFF_MBAR);
     unsigned* sFlag = reinterpret_cast<unsigned*>(sm + OFF_FLAG);
     uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + OFF_TMEM);
@@ -289,6 +316,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
         sMq[i] = ph.Wvol[l] * T.w[q % 3] * T.w[(q / 3) % 3] * T.w[q / 9];
         sMinv[i] = ph.Minv[l][q];
     }
+    if (tid < 8) sDte[tid] = a.dteR[tid];
     if (warp == 0) tmem_alloc(sTmem, TMEM_COLS);
     if (tid == 0) {
         mbar_init(mbar, 1);
@@ -348,6 +376,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
 
     for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
         // ---- 0: metadata (threads 0..63, one element each)
+        bool slow = false;   // the element needs the general pointwise step (see phase 5)
         if (tid < M) {
             const int e = e_next;
             const int idx_n = (t + (int)gridDim.x) * M + tid;
@@ -366,7 +395,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             const int b = lv & 7, par = (lv >> 3) & 1;
             const int cur = par ^ ((tick >> (B - b)) & 1);
             sPtr[tid * 8] = (cur ? d.V1 : d.V0) + (size_t)es * NP;
-            sPtrO[tid * 8] = sPtr[tid * 8];
+            sPtrO[tid * 8] = (cur ? d.V0 : d.V1) + (size_t)es * NP;   // slot 0: the row the step writes
             sTh[tid * 8] = 0.0f;
             if (e >= 0) live = 1;
 #pragma unroll
@@ -393,8 +422,9 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             sIrr[tid] = (e >= 0 && irr) ? 1 : 0;
 #pragma unroll
             for (int f = 0; f < 6; ++f) sNb[tid * 6 + f] = nbf[f];
+            slow = e < 0 || (inf & INFO_STIM) || (tick >> (B - b)) == 0;
         }
-        __syncthreads();
+        const bool fast = !__syncthreads_or(slow) && ph.ionic == 0 && ph.integrator == 1;
 
         // ---- 1: gather, mean shift, FP16 split (warp w: rows 8 w .. 8 w + 7; lane = 4 ii + kk:
         //      row ii, column pairs k = 2 kk + 8 jj + {0, 1})
@@ -575,7 +605,35 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
 
         // ---- 5: item updates (dof_update) with coalesced stores; the RV-T terms and both
         //      values go to shared memory (the operand bytes, free once the MMA completed)
-        {
+        //      A tile whose elements are all past their first step of the barrier, without
+        //      stimulus and without padding rows, under the Aliev-Panfilov model with the
+        //      exponential state step, takes the straight-line form (dof_update_ap), so that
+        //      the items of a thread interleave; any other tile the general one.
+        if (fast) {
+            float* sT = reinterpret_cast<float*>(sm + OFF_UHI);
+            float* sUo = sT + M * NP;
+            float* sUn = sUo + M * NP;
+#pragma unroll
+            for (int m = 0; m < NIT; ++m) {
+                const int it0 = tid + m * THREADS;
+                const bool in = it0 < M * NP;
+                const int it = in ? it0 : M * NP - 1;
+                const int i = it / NP, q = it - i * NP;
+                const int lev = (sInf[i] >> 24) & 15;
+                const float cr = sCorr[i * RST + q];
+                const float r = sR[i * RST + q] + (sIrr[i] ? cr : 0.0f);
+                float un, wn;
+                const float term = dof_update_ap(ph, sMq[lev * NP + q], sMinv[lev * NP + q], sDte[sLv[i] & 7], u[m],
+                                                 w[m], r, Ia[m], ga[m], un, wn);
+                if (in) {
+                    const_cast<float*>(sPtrO[i * 8])[q] = un;
+                    d.v[(size_t)sE[i] * NP + q] = wn;
+                    sT[it] = term;
+                    sUo[it] = u[m];
+                    sUn[it] = un;
+                }
+            }
+        } else {
             float* sT = reinterpret_cast<float*>(sm + OFF_UHI);
             float* sUo = sT + M * NP;
             float* sUn = sUo + M * NP;
@@ -596,8 +654,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
                     term = dof_update<float>(ph, sMq[lev * NP + q], sMinv[lev * NP + q], ke, a.dteR[b], so, smd, u[m],
                                              w[m], r, Ia[m], ga[m], un, wn);
                     const size_t o = (size_t)e * NP + q;
-                    const bool cur1 = sPtr[i * 8] == d.V1 + (size_t)e * NP;
-                    (cur1 ? d.V0 : d.V1)[o] = un;
+                    const_cast<float*>(sPtrO[i * 8])[q] = un;
                     d.v[o] = wn;
                     if (ke == 0 && b > 0) {
                         d.Ia[o] = Ia[m];
