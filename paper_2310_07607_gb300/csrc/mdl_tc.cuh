@@ -77,7 +77,8 @@ constexpr int OFF_CORR = ((OFF_IRR + M + 15) / 16) * 16;  // float [M][RST] resi
 constexpr int OFF_NX = OFF_CORR + M * RST * 4;        // next tile: int32 [M][8] = info, nbr[6], lvl | lvn[f] << 8 (f < 3)
 constexpr int OFF_NX2 = OFF_NX + M * 8 * 4;           // next tile: uint32 [M] lvn[f] for f >= 3
 constexpr int OFF_MTAB = OFF_NX2 + M * 4;             // float [8][27] GL mass, [8][27] inverse, [8] dt_e
-constexpr int OFF_MBAR = ((OFF_MTAB + (2 * 8 * NP + 8) * 4 + 7) / 8) * 8;
+constexpr int OFF_CHK = OFF_MTAB + (2 * 8 * NP + 8) * 4;   // int32 [3][M]: probe checks deferred to the next tile
+constexpr int OFF_MBAR = ((OFF_CHK + 3 * M * 4 + 7) / 8) * 8;
 constexpr int OFF_FLAG = OFF_MBAR + 8;
 constexpr int OFF_TMEM = OFF_FLAG + 8;
 constexpr int SMEM_BYTES = OFF_TMEM + 16 + 1024;      // + alignment slack of the dynamic base
@@ -266,7 +267,8 @@ __device__ __forceinline__ float block_row_dot(const float* __restrict__ row, co
 //      row) and the loads of the pointwise step, item by item (element, DOF)
 //   4  warps 0-3: D row -> scaled residual in shared memory
 //   5  the pointwise step (dof_update) of every item with coalesced stores
-//   6  per element (four threads each): the RV-T accumulation and the probe checks
+//   6  per element (four threads each): the RV-T accumulation; a due probe check is recorded
+//      and run by threads 64..127 during the next tile's metadata step (or after the last)
 // unscale = 2^-t undoes the scaling of B by 2^t; each row's scale of y is undone by 2^-sc.
 template <int DIM, int P>
 __global__ void __launch_bounds__(tc::THREADS, 2)
@@ -296,6 +298,9 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
     float* sMq = reinterpret_cast<float*>(sm + OFF_MTAB);
     float* sMinv = sMq + 8 * NP;
     float* sDte = sMinv + 8 * NP;
+    int* sChkE = reinterpret_cast<int*>(sm + OFF_CHK);      // element whose probe check is due, or -1
+    uint32_t* sChkInf = reinterpret_cast<uint32_t*>(sChkE + M);
+    int* sChkB = sChkE + 2 * M;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + OFF_MBAR);
     unsigned* sFlag = reinterpret_cast<unsigned*>(sm + OFF_FLAG);
     uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + OFF_TMEM);
@@ -317,6 +322,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
         sMinv[i] = ph.Minv[l][q];
     }
     if (tid < 8) sDte[tid] = a.dteR[tid];
+    if (tid < M) sChkE[tid] = -1;
     if (warp == 0) tmem_alloc(sTmem, TMEM_COLS);
     if (tid == 0) {
         mbar_init(mbar, 1);
@@ -371,10 +377,27 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
         for (int k = 0; k < 8; ++k) sNx[tid * 8 + k] = nx[k];
         sNx2[tid] = hi;
     }
+    const double t_tick = tick_time(a, tick);
+    auto run_checks = [&]() {
+        if (tid >= M && tid < 2 * M) {
+            const int i = tid - M, e = sChkE[i];
+            if (e >= 0) {
+                const float* sUo = reinterpret_cast<const float*>(sm + OFF_UHI) + M * NP;
+                const uint32_t inf = sChkInf[i];
+                lat_check<float, DIM, P>(d, T, ph, e, inf, (inf >> 24) & 15, sUo + i * NP, sUo + M * NP + i * NP,
+                                         t_tick, a.dte[sChkB[i]]);
+                sChkE[i] = -1;
+            }
+        }
+    };
     int nxr[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // threads 0..63: next tile's raw metadata in flight
     uint32_t nlo = 0u, nhi = 0u;
 
     for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+        // the previous tile's probe checks (threads 64..127, element tid - 64) run while threads
+        // 0..63 fetch this tile's metadata: they read only the check records and the values
+        // before and after the step, which phase 1 overwrites after the barrier below
+        run_checks();
         // ---- 0: metadata (threads 0..63, one element each)
         bool slow = false;   // the element needs the general pointwise step (see phase 5)
         if (tid < M) {
@@ -673,7 +696,8 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
         }
         {
             // ---- 6: per element i (threads 4 i .. 4 i + 3, DOFs q = p mod 4): RV-T sum and
-            //      max |V_new|, the accumulation and the probe checks
+            //      max |V_new|, the accumulation, and the record of a due probe check (run with
+            //      the next tile's metadata)
             const int i = tid >> 2, p = tid & 3, e = sE[i];
             const float* sT = reinterpret_cast<const float*>(sm + OFF_UHI);
             const float* sUo = sT + M * NP;
@@ -687,17 +711,18 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 1));
             term += __shfl_xor_sync(0xffffffffu, term, 2);
             vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 2));
-            if (p == 0 && e >= 0) {
+            if (p == 0) {
                 const uint32_t inf = sInf[i];
                 const int b = sLv[i] & 7;
-                d.acc[e] = acc0 + a.dte[b] * (double)term;
-                if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
-                    lat_check<float, DIM, P>(d, T, ph, e, inf, (inf >> 24) & 15, sUo + i * NP, sUn + i * NP,
-                                             tick_time(a, tick), a.dte[b]);
+                if (e >= 0) d.acc[e] = acc0 + a.dte[b] * (double)term;
+                sChkE[i] = (e >= 0 && (inf & INFO_PENDING) && vmax >= ph.lat_gate) ? e : -1;
+                sChkInf[i] = inf;
+                sChkB[i] = b;
             }
         }
         __syncthreads();
     }
+    if (ok) run_checks();   // the last tile's
     if (*sFlag) {
         // a wait gave up: give the MMAs in flight one more bounded wait before freeing TMEM
         if (tid == 0) mbar_wait(mbar, parity ^ 1u);
