@@ -67,6 +67,7 @@ struct Phys {
     R h2[8][3];        // 2 / h
     R Wvol[8];         // prod_k h_k / 2
     R Wface[8][3];     // prod_{l != k} h_l / 2  (face Jacobian of a normal-k face)
+    double kfac[8][3]; // h_F / (2p) W_F^2 of a normal-k (sub)face whose finer side has level l
     R Minv[8][27];     // inverse diagonal GL mass 1 / (Wvol prod_k w_{a_k}) per level and node
     // Aliev-Panfilov
     R k, a, eps0, mu1, mu2, inv_ts;
@@ -363,6 +364,33 @@ MDL_HD double face_kelly(const Tables<R>& T, const Phys<R>& ph, int k, int s, in
         acc += (double)W[t] * j * j;
     }
     return hF / (2.0 * P) * acc;
+}
+
+// face_kelly without its FP64 factor: sum_t W_t (D grad phi . n jump)^2 in the working
+// precision (FP32 on the device, where FP64 runs at a small fraction of the FP32 rate); the
+// caller multiplies by kfac = h_F/(2p) W_F^2 and accumulates the faces in FP64.
+template <typename R, int DIM, int P>
+MDL_HD R face_kelly_sum(const Tables<R>& T, const Phys<R>& ph, int k, int s, int lo, int cb_own, const R* own,
+                        int ln, int cb_nb, const R* nb, int lf) {
+    using S = Shape<DIM, P>;
+    constexpr int NT = S::NT;
+    R vo[NT], vn[NT], go[DIM][NT], gn[DIM][NT], W[NT];
+    face_eval<R, DIM, P>(T, ph.h2[lo], k, s, cb_own, own, vo, go);
+    face_eval<R, DIM, P>(T, ph.h2[ln], k, -s, cb_nb, nb, vn, gn);
+    face_weights<R, DIM, P>(T, ph, lf, k, W);
+    R acc = 0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        R fo = 0, fn = 0;
+#pragma unroll
+        for (int l = 0; l < DIM; ++l) {
+            fo += ph.D[k][l] * go[l][t];
+            fn += ph.D[k][l] * gn[l][t];
+        }
+        const R j = fo - fn;
+        acc += W[t] * j * j;
+    }
+    return acc;
 }
 
 }  // namespace mdl

@@ -734,7 +734,9 @@ __global__ void __launch_bounds__(256) k_tick(const TickArgs<R> a, const Tables<
 }
 
 // Kelly-type spatial indicator per element (Eq. dg-error-estimate) on the barrier-start
-// values; same-level and coarser neighbours are gathered before the face arithmetic.
+// values; same-level and coarser neighbours are gathered before the face arithmetic.  In
+// FP32 the face-point sums are FP32 and the faces accumulate in FP64 (FP64 arithmetic per
+// face point would bound the kernel by the FP64 pipe).
 template <typename R, int DIM, int P>
 __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> ph) {
     pdl_enter();
@@ -801,8 +803,13 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
 #pragma unroll
                 for (int q = 0; q < NP; ++q) un[q] = src[q];
                 const int pos = (inf >> (4 * f + 2)) & 3;
-                acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
-                                             kind == 1 ? -1 : pos, un, lev);
+                if constexpr (sizeof(R) == 4)
+                    acc += ph.kfac[lev][k] * (double)face_kelly_sum<R, DIM, P>(T, ph, k, s, lev, -1, u,
+                                                                             kind == 1 ? lev : lev - 1,
+                                                                             kind == 1 ? -1 : pos, un, lev);
+                else
+                    acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
+                                                 kind == 1 ? -1 : pos, un, lev);
             }
         }
 #pragma unroll
@@ -829,6 +836,9 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
 #pragma unroll
                     for (int t = 0; t < NT; ++t) fsum += j[t] * j[t];
                     acc += (double)fsum;
+                } else if constexpr (sizeof(R) == 4) {
+                    acc += ph.kfac[lev + 1][k] *
+                           (double)face_kelly_sum<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
                 } else {
                     acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
                 }
@@ -1241,7 +1251,9 @@ __global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> p
 
 // Solution transfer after adaptation (Alg. 1 adapt steps): keep, prolong (parent
 // polynomial at the child nodes) or restrict (L2 projection with the children's GL
-// rule, exact for the diagonal GL mass).  Old arrays in `o`, new in `n` (slot 0).
+// rule, exact for the diagonal GL mass).  Old arrays in `o`, new in `n` (slot 0).  Kept
+// elements (most of them) are copied one value per thread, so that a warp moves whole
+// consecutive rows; refined and coarsened ones take a thread each.
 template <typename R, int DIM, int P>
 __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* pkind, const int32_t* psrc,
                            const int8_t* pbits, const Tables<R> T) {
@@ -1250,22 +1262,26 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
     constexpr int N1 = S::N1, NP = S::NP, NC = 1 << DIM;
     if (n.meta->err) return;
     const int64_t nne = n.meta->ne;
+    for (int64_t it = gtid(); it < nne * NP; it += gstride()) {
+        const int64_t i = it / NP;
+        const int q = (int)(it - i * NP);
+        if (pkind[i] != 0) continue;
+        const int src = psrc[i];
+        const int par = (o.lvl[src] >> 3) & 1;
+        n.V0[it] = (par ? o.V1 : o.V0)[(size_t)src * NP + q];
+        n.v[it] = o.v[(size_t)src * NP + q];
+        if (q == 0) {
+            n.eta_t[i] = o.eta_t[src];
+            n.lvl[i] = 0;
+        }
+    }
     for (int64_t i = gtid(); i < nne; i += gstride()) {
     const int kd = pkind[i];
+    if (kd == 0) continue;
     const int src = psrc[i];
     R* Vn = n.V0 + (size_t)i * NP;
     R* wn = n.v + (size_t)i * NP;
-    if (kd == 0) {
-        const int par = (o.lvl[src] >> 3) & 1;
-        const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NP;
-        const R* wo = o.v + (size_t)src * NP;
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            Vn[q] = Vo[q];
-            wn[q] = wo[q];
-        }
-        n.eta_t[i] = o.eta_t[src];
-    } else if (kd == 1) {
+    if (kd == 1) {
         const int bits = pbits[i];
         const int par = (o.lvl[src] >> 3) & 1;
         const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NP;

@@ -111,6 +111,9 @@ void make_phys(const mdl_problem& pb, const Tables<double>& T, Phys<double>* ph)
             for (int m = 0; m < d; ++m)
                 if (m != k) wf *= ph->h[l][m] * 0.5;
             ph->Wface[l][k] = wf;
+            const double area = wf * (double)(1 << (d - 1));
+            const double hF = (d == 2) ? area : std::sqrt(area);
+            ph->kfac[l][k] = hF / (2.0 * pb.order) * wf * wf;
         }
     }
     const int n1 = pb.order + 1;
@@ -175,6 +178,7 @@ void convert_phys(const Phys<double>& a, Phys<R>* b) {
             b->h[l][k] = (R)a.h[l][k];
             b->h2[l][k] = (R)a.h2[l][k];
             b->Wface[l][k] = (R)a.Wface[l][k];
+            b->kfac[l][k] = a.kfac[l][k];
         }
     }
     b->k = (R)a.k; b->a = (R)a.a; b->eps0 = (R)a.eps0; b->mu1 = (R)a.mu1; b->mu2 = (R)a.mu2;
