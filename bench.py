@@ -52,8 +52,14 @@ SETUP_BARRIERS = 5
 # their proportion (tick 0 once, the finer ticks 7 times).  ncu replays each launch with
 # cold caches, so this is an upper bound on the live traffic.  Set to None whenever the
 # kernel changes until it is captured again.
+# Keyed by (workload, kernel) at the workload's own base grid.  3D slab: captured on the same
+# slab at a quarter of its x extent (base 32x48x20: the same 2,457,600 finest elements due at
+# ticks 1-7, the same level-1 and level-3 elements at tick 4), tick 0 scaled to the full slab's
+# 2,736,960 elements by the elements due.
 TRAFFIC_PER_LAUNCH = {
-    "k_tick<float,2,1>": (10.348288e6 + 7 * 5.934080e6) / 8.0,
+    ("slab2d", "k_tick<float,2,1>"): (10.348288e6 + 7 * 5.934080e6) / 8.0,
+    ("slab3d", "k_tick_tc<3,2>"): ((728.019968e6 + 1101.996032e6) * 2736960 / 2644800
+                                   + 6 * (1222.4e6 + 515.9e6) + (1319.646976e6 + 553.46176e6)) / 8.0,
 }
 # Algorithmic bytes per DOF-update of the fused sweep (Q1 2D, FP32, AP): V_old 4 + v 4 +
 # V_new 4 + v 4 = 16 B, plus per element step 2d neighbour ids + 4 B level/flags + the FP64
@@ -246,7 +252,8 @@ def run_ours(args, rank, world):
     sweep_s = st["sweep_ms"] / 1e3
     alg_bytes = st["dof_updates"] * alg_bytes
     achieved = alg_bytes / sweep_s / 1e9 if sweep_s > 0 else 0.0
-    traffic = TRAFFIC_PER_LAUNCH.get(kname) if args.sweep in ("default", "thread") and not args.tick_shape else None
+    traffic = (TRAFFIC_PER_LAUNCH.get((args.workload, kname))
+               if args.sweep == "default" and not args.tick_shape and not args.base else None)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
             "alg_bytes_per_launch": round(alg_bytes / max(st["tick_launches"], 1), 1),

@@ -1251,9 +1251,7 @@ __global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> p
 
 // Solution transfer after adaptation (Alg. 1 adapt steps): keep, prolong (parent
 // polynomial at the child nodes) or restrict (L2 projection with the children's GL
-// rule, exact for the diagonal GL mass).  Old arrays in `o`, new in `n` (slot 0).  Kept
-// elements (most of them) are copied one value per thread, so that a warp moves whole
-// consecutive rows; refined and coarsened ones take a thread each.
+// rule, exact for the diagonal GL mass).  Old arrays in `o`, new in `n` (slot 0).
 template <typename R, int DIM, int P>
 __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* pkind, const int32_t* psrc,
                            const int8_t* pbits, const Tables<R> T) {
@@ -1262,26 +1260,22 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
     constexpr int N1 = S::N1, NP = S::NP, NC = 1 << DIM;
     if (n.meta->err) return;
     const int64_t nne = n.meta->ne;
-    for (int64_t it = gtid(); it < nne * NP; it += gstride()) {
-        const int64_t i = it / NP;
-        const int q = (int)(it - i * NP);
-        if (pkind[i] != 0) continue;
-        const int src = psrc[i];
-        const int par = (o.lvl[src] >> 3) & 1;
-        n.V0[it] = (par ? o.V1 : o.V0)[(size_t)src * NP + q];
-        n.v[it] = o.v[(size_t)src * NP + q];
-        if (q == 0) {
-            n.eta_t[i] = o.eta_t[src];
-            n.lvl[i] = 0;
-        }
-    }
     for (int64_t i = gtid(); i < nne; i += gstride()) {
     const int kd = pkind[i];
-    if (kd == 0) continue;
     const int src = psrc[i];
     R* Vn = n.V0 + (size_t)i * NP;
     R* wn = n.v + (size_t)i * NP;
-    if (kd == 1) {
+    if (kd == 0) {
+        const int par = (o.lvl[src] >> 3) & 1;
+        const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NP;
+        const R* wo = o.v + (size_t)src * NP;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            Vn[q] = Vo[q];
+            wn[q] = wo[q];
+        }
+        n.eta_t[i] = o.eta_t[src];
+    } else if (kd == 1) {
         const int bits = pbits[i];
         const int par = (o.lvl[src] >> 3) & 1;
         const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NP;
