@@ -282,6 +282,10 @@ __global__ void k_mesh_tables(const int4* coord, const int32_t* owner, Grid g, u
                               int32_t* hang, int32_t* root, uint32_t* loc, uint8_t* bcfl,
                               const uint8_t* class_b, uint32_t* smask0, uint32_t* smask1, uint32_t* smask2,
                               uint32_t* smask3, StimBoxes sb, Phys<double> phd, DevMeta* m, int force) {
+    // element extents per level in FP32 for the stimulus-box pre-test below
+    __shared__ float hf[8][3];
+    if (threadIdx.x < 24) hf[threadIdx.x / 3][threadIdx.x % 3] = (float)phd.h[threadIdx.x / 3][threadIdx.x % 3];
+    __syncthreads();
     pdl_enter();
     if (m->err || !(force || m->changed)) return;
     using S = Shape<DIM, P>;
@@ -346,11 +350,19 @@ __global__ void k_mesh_tables(const int4* coord, const int32_t* owner, Grid g, u
         root[e] = rt[0] + g.base[0] * (rt[1] + g.base[1] * rt[2]);
         loc[e] = lc;
         bcfl[e] = class_b[(size_t)l * (1u << (2 * NF)) + cfg];
-        // stimulus masks: node coordinates in FP64 without contraction (same bits as the host)
+        // stimulus masks: node coordinates in FP64 without contraction (same bits as the host).
+        // GL nodes lie at least 0.11 h inside the element along each axis, so an element whose
+        // extent misses the box by 0.05 h (FP32 test: its rounding is below 1e-4 h) holds no
+        // node of the box and skips the FP64 evaluation (a slow pipe on this part).
         bool any = false;
         for (int s = 0; s < sb.n; ++s) {
             uint32_t msk = 0;
-            for (int q = 0; q < NP; ++q) {
+            bool may = true;
+            for (int k = 0; k < DIM; ++k) {
+                const float h = hf[l][k], x0 = (float)c[k] * h;
+                if (x0 + h < (float)sb.lo[s][k] - 0.05f * h || x0 > (float)sb.hi[s][k] + 0.05f * h) may = false;
+            }
+            for (int q = 0; may && q < NP; ++q) {
                 bool in = true;
                 for (int k = 0; k < DIM; ++k) {
                     const double h = phd.h[l][k];

@@ -1251,7 +1251,10 @@ __global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> p
 
 // Solution transfer after adaptation (Alg. 1 adapt steps): keep, prolong (parent
 // polynomial at the child nodes) or restrict (L2 projection with the children's GL
-// rule, exact for the diagonal GL mass).  Old arrays in `o`, new in `n` (slot 0).
+// rule, exact for the diagonal GL mass).  Old arrays in `o`, new in `n` (slot 0).  Kept
+// elements (most of them) are copied by whole warps: a warp takes 32 consecutive new
+// elements and copies their rows lane-parallel over the values, the old row of each element
+// broadcast from its lane; refined and coarsened elements take a thread each.
 template <typename R, int DIM, int P>
 __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* pkind, const int32_t* psrc,
                            const int8_t* pbits, const Tables<R> T) {
@@ -1260,22 +1263,45 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
     constexpr int N1 = S::N1, NP = S::NP, NC = 1 << DIM;
     if (n.meta->err) return;
     const int64_t nne = n.meta->ne;
+    {
+        const int lane = threadIdx.x & 31;
+        const int64_t nwarp = gstride() >> 5;
+        for (int64_t base = (gtid() >> 5) * 32; base < nne; base += nwarp * 32) {
+            const int64_t i = base + lane;
+            long long vrow = 0, wrow = 0;   // old rows of a kept element (0: not kept)
+            if (i < nne && pkind[i] == 0) {
+                const int src = psrc[i];
+                const int par = (o.lvl[src] >> 3) & 1;
+                vrow = (long long)((par ? o.V1 : o.V0) + (size_t)src * NP);
+                wrow = (long long)(o.v + (size_t)src * NP);
+                n.eta_t[i] = o.eta_t[src];
+                n.lvl[i] = 0;
+            }
+            // value idx = lane + 32 j of the warp's block: row r = idx / NP, column q
+            int r = lane / NP, q = lane - (lane / NP) * NP;
+            for (int j = 0; j < NP; ++j) {
+                const long long vr = __shfl_sync(0xffffffffu, vrow, r);
+                const long long wr = __shfl_sync(0xffffffffu, wrow, r);
+                if (vr) {
+                    n.V0[(size_t)(base + r) * NP + q] = reinterpret_cast<const R*>(vr)[q];
+                    n.v[(size_t)(base + r) * NP + q] = reinterpret_cast<const R*>(wr)[q];
+                }
+                q += 32 % NP;
+                r += 32 / NP;
+                if (q >= NP) {
+                    q -= NP;
+                    ++r;
+                }
+            }
+        }
+    }
     for (int64_t i = gtid(); i < nne; i += gstride()) {
     const int kd = pkind[i];
+    if (kd == 0) continue;
     const int src = psrc[i];
     R* Vn = n.V0 + (size_t)i * NP;
     R* wn = n.v + (size_t)i * NP;
-    if (kd == 0) {
-        const int par = (o.lvl[src] >> 3) & 1;
-        const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NP;
-        const R* wo = o.v + (size_t)src * NP;
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            Vn[q] = Vo[q];
-            wn[q] = wo[q];
-        }
-        n.eta_t[i] = o.eta_t[src];
-    } else if (kd == 1) {
+    if (kd == 1) {
         const int bits = pbits[i];
         const int par = (o.lvl[src] >> 3) & 1;
         const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NP;
