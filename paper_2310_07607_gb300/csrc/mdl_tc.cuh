@@ -61,12 +61,12 @@ constexpr int OFF_UHI = OFF_BLO + B_BYTES;
 constexpr int OFF_ULO = OFF_UHI + U_BYTES;
 constexpr int OFF_R = OFF_ULO + U_BYTES;              // float [M][RST] scaled residual
 constexpr int OFF_SCR = OFF_R + M * RST * 4;          // float [8 warps][2][32] per-warp scratch
-constexpr int OFF_PTR = OFF_SCR + 8 * 2 * 32 * 4;     // const float* [M][8]: row of slot s (seen value)
-constexpr int OFF_PTRO = OFF_PTR + M * 8 * 8;         // const float* [M][8]: other V slot (interpolation)
+constexpr int OFF_PTR = OFF_SCR + 8 * 2 * 32 * 4;     // const float* [8][M]: row of slot s (seen value)
+constexpr int OFF_PTRO = OFF_PTR + M * 8 * 8;         // const float* [8][M]: other V slot (interpolation)
 constexpr int OFF_E = OFF_PTRO + M * 8 * 8;           // int32 element id (-1: padding row)
 constexpr int OFF_INF = OFF_E + M * 4;                // uint32 face info
-constexpr int OFF_NB = OFF_INF + M * 4;               // int32 [M][6] face neighbours
-constexpr int OFF_TH = OFF_NB + M * 6 * 4;            // float [M][8] time-interpolation weight
+constexpr int OFF_NB = OFF_INF + M * 4;               // int32 [6][M] face neighbours
+constexpr int OFF_TH = OFF_NB + M * 6 * 4;            // float [8][M] time-interpolation weight
 constexpr int OFF_RS = OFF_TH + M * 8 * 4;            // float 2^-sc: undoes the row's operand scale
 constexpr int OFF_C = OFF_RS + M * 4;                 // float operand mean c of the row
 constexpr int OFF_LV = OFF_C + M * 4;                 // uint8 level byte
@@ -74,7 +74,7 @@ constexpr int OFF_LIVE = OFF_LV + M;                  // uint8 bit s: slot s hol
 constexpr int OFF_INTP = OFF_LIVE + M;                // uint8 bit s: slot s is interpolated in time
 constexpr int OFF_IRR = OFF_INTP + M;                 // uint8 element has a non-regular face
 constexpr int OFF_CORR = ((OFF_IRR + M + 15) / 16) * 16;  // float [M][RST] residual corrections
-constexpr int OFF_NX = OFF_CORR + M * RST * 4;        // next tile: int32 [M][8] = info, nbr[6], lvl | lvn[f] << 8 (f < 3)
+constexpr int OFF_NX = OFF_CORR + M * RST * 4;        // next tile: int32 [8][M] = info, nbr[6], lvl | lvn[f] << 8 (f < 3)
 constexpr int OFF_NX2 = OFF_NX + M * 8 * 4;           // next tile: uint32 [M] lvn[f] for f >= 3
 constexpr int OFF_MTAB = OFF_NX2 + M * 4;             // float [8][27] GL mass, [8][27] inverse, [8] dt_e
 constexpr int OFF_CHK = OFF_MTAB + (2 * 8 * NP + 8) * 4;   // int32 [3][M]: probe checks deferred to the next tile
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
         fetch_lvn(e_next, nx, lo, hi);
         nx[7] |= (int)(lo << 8);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) sNx[tid * 8 + k] = nx[k];
+        for (int k = 0; k < 8; ++k) sNx[k * M + tid] = nx[k];
         sNx2[tid] = hi;
     }
     const double t_tick = tick_time(a, tick);
@@ -406,20 +406,20 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             e_next = idx_n < n_act ? d.order[idx_n] : -1;
             const int es = e >= 0 ? e : 0;                    // any valid row for padding slots
             uint8_t live = 0, intp = 0;
-            const uint32_t inf = (uint32_t)sNx[tid * 8];
+            const uint32_t inf = (uint32_t)sNx[tid];
             int nbf[6];
 #pragma unroll
-            for (int f = 0; f < 6; ++f) nbf[f] = sNx[tid * 8 + 1 + f];
-            const uint32_t w7 = (uint32_t)sNx[tid * 8 + 7], w8 = sNx2[tid];
+            for (int f = 0; f < 6; ++f) nbf[f] = sNx[(1 + f) * M + tid];
+            const uint32_t w7 = (uint32_t)sNx[7 * M + tid], w8 = sNx2[tid];
             const uint8_t lv = (uint8_t)(w7 & 255u);
             uint8_t lvn[6];
 #pragma unroll
             for (int f = 0; f < 6; ++f) lvn[f] = (uint8_t)((f < 3 ? (w7 >> (8 * (f + 1))) : (w8 >> (8 * (f - 3)))) & 255u);
             const int b = lv & 7, par = (lv >> 3) & 1;
             const int cur = par ^ ((tick >> (B - b)) & 1);
-            sPtr[tid * 8] = (cur ? d.V1 : d.V0) + (size_t)es * NP;
-            sPtrO[tid * 8] = (cur ? d.V0 : d.V1) + (size_t)es * NP;   // slot 0: the row the step writes
-            sTh[tid * 8] = 0.0f;
+            sPtr[tid] = (cur ? d.V1 : d.V0) + (size_t)es * NP;
+            sPtrO[tid] = (cur ? d.V0 : d.V1) + (size_t)es * NP;   // slot 0: the row the step writes
+            sTh[tid] = 0.0f;
             if (e >= 0) live = 1;
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
@@ -428,9 +428,9 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
                 const int j = tick >> sh, rem = same ? (tick & ((1 << sh) - 1)) : 0;
                 const int nw = pn ^ ((j + (rem ? 1 : 0)) & 1);
                 const size_t o = (size_t)(same ? nbf[f] : es) * NP;
-                sPtr[tid * 8 + 1 + f] = (nw ? d.V1 : d.V0) + o;
-                sPtrO[tid * 8 + 1 + f] = (nw ? d.V0 : d.V1) + o;
-                sTh[tid * 8 + 1 + f] = rem ? (float)rem * pow2_neg<float>(sh) : 0.0f;
+                sPtr[(1 + f) * M + tid] = (nw ? d.V1 : d.V0) + o;
+                sPtrO[(1 + f) * M + tid] = (nw ? d.V0 : d.V1) + o;
+                sTh[(1 + f) * M + tid] = rem ? (float)rem * pow2_neg<float>(sh) : 0.0f;
                 if (same) live |= (uint8_t)(2u << f);
                 if (rem) intp |= (uint8_t)(2u << f);
             }
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             sIntp[tid] = intp;
             sIrr[tid] = (e >= 0 && irr) ? 1 : 0;
 #pragma unroll
-            for (int f = 0; f < 6; ++f) sNb[tid * 6 + f] = nbf[f];
+            for (int f = 0; f < 6; ++f) sNb[f * M + tid] = nbf[f];
             slow = e < 0 || (inf & INFO_STIM) || (tick >> (B - b)) == 0;
         }
         const bool fast = !__syncthreads_or(slow) && ph.ionic == 0 && ph.integrator == 1;
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             const int ii = lane >> 2, kk = lane & 3, i = warp * 8 + ii;
             const float* pr[SLOTS];
 #pragma unroll
-            for (int s = 0; s < SLOTS; ++s) pr[s] = sPtr[i * 8 + s];
+            for (int s = 0; s < SLOTS; ++s) pr[s] = sPtr[s * M + i];
             const unsigned live = sLive[i], intp = sIntp[i];
             float x[48];
             // column k lies in slot s0 = floor(8 jj / 27) or the next one
@@ -477,8 +477,8 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
                     const int k = 2 * kk + 8 * (m >> 1) + (m & 1);
                     const int s = (k < KU ? k : KU - 1) / NP;
                     if (k < KU && ((intp >> s) & 1u)) {
-                        const float xo = __ldg(sPtrO[i * 8 + s] + (k - NP * s));
-                        x[m] = xo + sTh[i * 8 + s] * (x[m] - xo);
+                        const float xo = __ldg(sPtrO[s * M + i] + (k - NP * s));
+                        x[m] = xo + sTh[s * M + i] * (x[m] - xo);
                     }
                 }
             }
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
                 if (!sIrr[i]) continue;
                 const uint32_t inf = sInf[i];
                 const float c = sC[i];
-                su[lane] = __ldg(sPtr[i * 8] + q) - c;
+                su[lane] = __ldg(sPtr[i] + q) - c;
                 __syncwarp();
                 float corr = 0.0f;
                 for (int f = 0; f < 6; ++f) {
@@ -555,14 +555,14 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
                     } else if (kind == 2) {
                         const int pos = (inf >> (4 * f + 2)) & 3;
                         corr += block_row_dot(Bf + (1 + pos) * NP * 28, su);
-                        sn[lane] = seen_dof(d, tick, B, sNb[i * 6 + f], q) - c;
+                        sn[lane] = seen_dof(d, tick, B, sNb[f * M + i], q) - c;
                         __syncwarp();
                         corr += block_row_dot(Bf + (5 + pos) * NP * 28, sn);
                         __syncwarp();
                     } else {
                         corr += block_row_dot(Bf + 9 * NP * 28, su);
                         for (int sb = 0; sb < 4; ++sb) {
-                            sn[lane] = seen_dof(d, tick, B, d.hang[sNb[i * 6 + f] + sb], q) - c;
+                            sn[lane] = seen_dof(d, tick, B, d.hang[sNb[f * M + i] + sb], q) - c;
                             __syncwarp();
                             corr += block_row_dot(Bf + (10 + sb) * NP * 28, sn);
                             __syncwarp();
@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             const int e = sE[i], es = e >= 0 ? e : 0;
             const int ke = tick >> (B - (sLv[i] & 7));
             const bool need = it < M * NP && e >= 0 && ke != 0;
-            u[m] = __ldg(sPtr[i * 8] + q);
+            u[m] = __ldg(sPtr[i] + q);
             w[m] = d.v[(size_t)es * NP + q];
             Ia[m] = need ? d.Ia[(size_t)es * NP + q] : 0.0f;
             ga[m] = need ? d.ga[(size_t)es * NP + q] : 0.0f;
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
 
         if (tid < M) {
 #pragma unroll
-            for (int k = 0; k < 7; ++k) sNx[tid * 8 + k] = nxr[k];
+            for (int k = 0; k < 7; ++k) sNx[k * M + tid] = nxr[k];
             fetch_lvn(e_next, nxr, nlo, nhi);
         }
 
@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
                 const float term = dof_update_ap(ph, sMq[lev * NP + q], sMinv[lev * NP + q], sDte[sLv[i] & 7], u[m],
                                                  w[m], r, Ia[m], ga[m], un, wn);
                 if (in) {
-                    const_cast<float*>(sPtrO[i * 8])[q] = un;
+                    const_cast<float*>(sPtrO[i])[q] = un;
                     d.v[(size_t)sE[i] * NP + q] = wn;
                     sT[it] = term;
                     sUo[it] = u[m];
@@ -677,7 +677,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
                     term = dof_update<float>(ph, sMq[lev * NP + q], sMinv[lev * NP + q], ke, a.dteR[b], so, smd, u[m],
                                              w[m], r, Ia[m], ga[m], un, wn);
                     const size_t o = (size_t)e * NP + q;
-                    const_cast<float*>(sPtrO[i * 8])[q] = un;
+                    const_cast<float*>(sPtrO[i])[q] = un;
                     d.v[o] = wn;
                     if (ke == 0 && b > 0) {
                         d.Ia[o] = Ia[m];
@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
         }
         __syncthreads();
         if (tid < M) {
-            sNx[tid * 8 + 7] = nxr[7] | (int)(nlo << 8);
+            sNx[7 * M + tid] = nxr[7] | (int)(nlo << 8);
             sNx2[tid] = nhi;
         }
         {
@@ -703,9 +703,13 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             const float* sUo = sT + M * NP;
             const float* sUn = sUo + M * NP;
             float term = 0.0f, vmax = 0.0f;
-            for (int q = p; q < NP; q += 4) {
-                term += sT[i * NP + q];
-                vmax = fmaxf(vmax, fabsf(sUn[i * NP + q]));
+#pragma unroll
+            for (int j = 0; j < (NP + 3) / 4; ++j) {
+                const int q = p + 4 * j;
+                if (q < NP) {
+                    term += sT[i * NP + q];
+                    vmax = fmaxf(vmax, fabsf(sUn[i * NP + q]));
+                }
             }
             term += __shfl_xor_sync(0xffffffffu, term, 1);
             vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 1));
