@@ -250,27 +250,24 @@ __global__ void k_scan_emit(const int4* coord, const uint8_t* r, const uint8_t* 
 }
 
 // Finest-grid owner map: every leaf writes its index into the finest cells it covers.
-// One thread per (leaf, row of finest cells along x), rows of a coarse leaf being
-// contiguous runs of 2^(L - level) cells.
+// One thread per leaf: its rows of finest cells along x are contiguous runs of
+// 2^(L - level) cells (a leaf at the finest level writes one cell).
 template <int DIM>
 __global__ void k_owner_fill(const int4* coord, int32_t* owner, Grid g, const DevMeta* m, int force) {
     pdl_enter();
     if (m->err || !(force || m->changed)) return;
     const int64_t ne = m->ne;
-    const int maxrows = DIM == 3 ? (1 << (2 * g.L)) : (1 << g.L);
-    const int64_t total = ne * maxrows;
-    for (int64_t t = gtid(); t < total; t += gstride()) {
-        const int64_t e = t / maxrows;
-        const int row = (int)(t - e * maxrows);
+    for (int64_t e = gtid(); e < ne; e += gstride()) {
         const int4 a = coord[e];
         const int sh = g.L - a.w;
         const int n = 1 << sh;
         const int nrows = DIM == 3 ? n * n : n;
-        if (row >= nrows) continue;
-        const int64_t y = ((int64_t)a.y << sh) + (row % n);
-        const int64_t z = DIM == 3 ? (((int64_t)a.z << sh) + row / n) : 0;
-        int32_t* dst = owner + ((int64_t)a.x << sh) + g.fine[0] * (y + g.fine[1] * z);
-        for (int x = 0; x < n; ++x) dst[x] = (int32_t)e;
+        for (int row = 0; row < nrows; ++row) {
+            const int64_t y = ((int64_t)a.y << sh) + (row % n);
+            const int64_t z = DIM == 3 ? (((int64_t)a.z << sh) + row / n) : 0;
+            int32_t* dst = owner + ((int64_t)a.x << sh) + g.fine[0] * (y + g.fine[1] * z);
+            for (int x = 0; x < n; ++x) dst[x] = (int32_t)e;
+        }
     }
 }
 
