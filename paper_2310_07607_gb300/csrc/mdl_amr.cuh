@@ -250,13 +250,29 @@ __global__ void k_scan_emit(const int4* coord, const uint8_t* r, const uint8_t* 
 }
 
 // Finest-grid owner map: every leaf writes its index into the finest cells it covers.
-// One thread per leaf: its rows of finest cells along x are contiguous runs of
-// 2^(L - level) cells (a leaf at the finest level writes one cell).
+// 3D: one thread per leaf (of up to 4^L rows per leaf most would be skipped); its rows of
+// finest cells along x are contiguous runs of 2^(L - level) cells (a leaf at the finest
+// level writes one cell).
 template <int DIM>
 __global__ void k_owner_fill(const int4* coord, int32_t* owner, Grid g, const DevMeta* m, int force) {
     pdl_enter();
     if (m->err || !(force || m->changed)) return;
     const int64_t ne = m->ne;
+    if constexpr (DIM == 2) {
+        // 2D: one thread per (leaf, row); at most 2^L rows per leaf, few of them skipped
+        const int maxrows = 1 << g.L;
+        for (int64_t t = gtid(); t < ne * maxrows; t += gstride()) {
+            const int64_t e = t / maxrows;
+            const int row = (int)(t - e * maxrows);
+            const int4 a = coord[e];
+            const int sh = g.L - a.w;
+            const int n = 1 << sh;
+            if (row >= n) continue;
+            int32_t* dst = owner + ((int64_t)a.x << sh) + g.fine[0] * (((int64_t)a.y << sh) + row);
+            for (int x = 0; x < n; ++x) dst[x] = (int32_t)e;
+        }
+        return;
+    }
     for (int64_t e = gtid(); e < ne; e += gstride()) {
         const int4 a = coord[e];
         const int sh = g.L - a.w;

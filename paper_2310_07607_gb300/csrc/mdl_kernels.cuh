@@ -1252,9 +1252,10 @@ __global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> p
 // Solution transfer after adaptation (Alg. 1 adapt steps): keep, prolong (parent
 // polynomial at the child nodes) or restrict (L2 projection with the children's GL
 // rule, exact for the diagonal GL mass).  Old arrays in `o`, new in `n` (slot 0).  Kept
-// elements (most of them) are copied by whole warps: a warp takes 32 consecutive new
-// elements and copies their rows lane-parallel over the values, the old row of each element
-// broadcast from its lane; refined and coarsened elements take a thread each.
+// elements (most of them) with rows of 27 values are copied by whole warps: a warp takes 32
+// consecutive new elements and copies their rows lane-parallel over the values, the old row
+// of each element broadcast from its lane; shorter rows, refined and coarsened elements take
+// a thread each.
 template <typename R, int DIM, int P>
 __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* pkind, const int32_t* psrc,
                            const int8_t* pbits, const Tables<R> T) {
@@ -1263,7 +1264,23 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
     constexpr int N1 = S::N1, NP = S::NP, NC = 1 << DIM;
     if (n.meta->err) return;
     const int64_t nne = n.meta->ne;
-    {
+    if constexpr (NP < 27) {
+        // short rows (Q1, 2D Q2): a thread per kept element
+        for (int64_t i = gtid(); i < nne; i += gstride()) {
+            if (pkind[i] != 0) continue;
+            const int src = psrc[i];
+            const int par = (o.lvl[src] >> 3) & 1;
+            const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NP;
+            const R* wo = o.v + (size_t)src * NP;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                n.V0[(size_t)i * NP + q] = Vo[q];
+                n.v[(size_t)i * NP + q] = wo[q];
+            }
+            n.eta_t[i] = o.eta_t[src];
+            n.lvl[i] = 0;
+        }
+    } else {
         const int lane = threadIdx.x & 31;
         const int64_t nwarp = gstride() >> 5;
         for (int64_t base = (gtid() >> 5) * 32; base < nne; base += nwarp * 32) {
