@@ -791,12 +791,17 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
                 acc += (double)fsum;
             }
         } else {
+            // Q2: the axis unrolled, the side a loop (half the code of a fully unrolled face
+            // loop; the kernel's size bounded it by instruction fetch)
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
+            for (int k = 0; k < DIM; ++k)
+#pragma unroll 1
+            for (int side = 0; side < 2; ++side) {
+                const int f = 2 * k + side;
                 const int kind = (inf >> (4 * f)) & 3;
                 if (kind != 1 && kind != 2) continue;
-                const int k = f >> 1, s = (f & 1) ? 1 : -1;
-                const int nbi = nbf[f];
+                const int s = side ? 1 : -1;
+                const int nbi = d.nbr[(size_t)e * NF + f];
                 const int pn = (d.lvl[nbi] >> 3) & 1;
                 const R* src = (pn ? d.V1 : d.V0) + (size_t)nbi * NP;
                 R un[NP];
@@ -812,19 +817,18 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
                                                  kind == 1 ? -1 : pos, un, lev);
             }
         }
+        if constexpr (P == 1) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            const int kind = (inf >> (4 * f)) & 3;
-            if (kind != 3) continue;
-            const int k = f >> 1, s = (f & 1) ? 1 : -1;
-            for (int sb = 0; sb < NSUB; ++sb) {
-                const int nb = d.hang[nbf[f] + sb];
-                const int pn = (d.lvl[nb] >> 3) & 1;
-                const R* src = (pn ? d.V1 : d.V0) + (size_t)nb * NP;
-                R un[NP];
+            for (int f = 0; f < NF; ++f) {
+                const int kind = (inf >> (4 * f)) & 3;
+                if (kind != 3) continue;
+                for (int sb = 0; sb < NSUB; ++sb) {
+                    const int nb = d.hang[nbf[f] + sb];
+                    const int pn = (d.lvl[nb] >> 3) & 1;
+                    const R* src = (pn ? d.V1 : d.V0) + (size_t)nb * NP;
+                    R un[NP];
 #pragma unroll
-                for (int q = 0; q < NP; ++q) un[q] = src[q];
-                if constexpr (P == 1) {
+                    for (int q = 0; q < NP; ++q) un[q] = src[q];
                     constexpr int NT = S::NT, NREL = 1 + 2 * NSUB;
                     const R* K = d.qkelly + ((((size_t)f * 8 + lev) * NREL + 1 + NSUB + sb) * 2) * NT * NP;
                     R j[NT];
@@ -836,11 +840,30 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
 #pragma unroll
                     for (int t = 0; t < NT; ++t) fsum += j[t] * j[t];
                     acc += (double)fsum;
-                } else if constexpr (sizeof(R) == 4) {
-                    acc += ph.kfac[lev + 1][k] *
-                           (double)face_kelly_sum<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
-                } else {
-                    acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k)
+#pragma unroll 1
+            for (int side = 0; side < 2; ++side) {
+                const int f = 2 * k + side;
+                const int kind = (inf >> (4 * f)) & 3;
+                if (kind != 3) continue;
+                const int s = side ? 1 : -1;
+                const int h0 = d.nbr[(size_t)e * NF + f];
+                for (int sb = 0; sb < NSUB; ++sb) {
+                    const int nb = d.hang[h0 + sb];
+                    const int pn = (d.lvl[nb] >> 3) & 1;
+                    const R* src = (pn ? d.V1 : d.V0) + (size_t)nb * NP;
+                    R un[NP];
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) un[q] = src[q];
+                    if constexpr (sizeof(R) == 4)
+                        acc += ph.kfac[lev + 1][k] *
+                               (double)face_kelly_sum<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
+                    else
+                        acc += face_kelly<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
                 }
             }
         }
@@ -1294,20 +1317,31 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
                 n.eta_t[i] = o.eta_t[src];
                 n.lvl[i] = 0;
             }
-            // value idx = lane + 32 j of the warp's block: row r = idx / NP, column q
+            // value idx = lane + 32 j of the warp's block: row r = idx / NP, column q; every
+            // load of the block is issued before the first store
+            R xv[NP], xw[NP];
+            bool keep[NP];
             int r = lane / NP, q = lane - (lane / NP) * NP;
+#pragma unroll
             for (int j = 0; j < NP; ++j) {
                 const long long vr = __shfl_sync(0xffffffffu, vrow, r);
                 const long long wr = __shfl_sync(0xffffffffu, wrow, r);
-                if (vr) {
-                    n.V0[(size_t)(base + r) * NP + q] = reinterpret_cast<const R*>(vr)[q];
-                    n.v[(size_t)(base + r) * NP + q] = reinterpret_cast<const R*>(wr)[q];
-                }
+                keep[j] = vr != 0;
+                xv[j] = keep[j] ? reinterpret_cast<const R*>(vr)[q] : R(0);
+                xw[j] = keep[j] ? reinterpret_cast<const R*>(wr)[q] : R(0);
                 q += 32 % NP;
                 r += 32 / NP;
                 if (q >= NP) {
                     q -= NP;
                     ++r;
+                }
+            }
+            const size_t o0 = (size_t)base * NP + lane;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                if (keep[j]) {
+                    n.V0[o0 + 32 * j] = xv[j];
+                    n.v[o0 + 32 * j] = xw[j];
                 }
             }
         }
