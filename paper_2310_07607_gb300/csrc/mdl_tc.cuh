@@ -36,6 +36,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "mdl_kernels.cuh"
 
 namespace mdl {
@@ -200,18 +202,24 @@ __device__ __forceinline__ void issue_tile_mma(uint32_t tmem, uint32_t sUhi, uin
     mma_commit(mbar);
 }
 
-// dof_update for an element past its first step of the barrier (ke != 0), without stimulus,
-// under the Aliev-Panfilov model (ionic 0) with the exponential state step (integrator 1):
-// the same expressions as ap_iion, ap_g and ap_step_state without their model and
-// integrator branches, and e^x - 1 as a select of both forms, so that the code is
-// straight-line and the items of a thread can interleave.
+// dof_update for an element without stimulus under the Aliev-Panfilov model (ionic 0) with
+// the exponential state step (integrator 1): the same expressions as ap_iion, ap_g and
+// ap_step_state without their model and integrator branches, and e^x - 1 as a select of both
+// forms, so that the code is straight-line and the items of a thread can interleave.  FIRST:
+// the element's first step of the barrier (ke == 0), which sets Ia and ga to I and g at the
+// step start; otherwise they are inputs.
+template <bool FIRST>
 __device__ __forceinline__ float dof_update_ap(const Phys<float>& ph, float Mq, float Minv, float dte, float u, float w,
-                                               float r, float Ia, float ga, float& un, float& wn) {
+                                               float r, float& Ia, float& ga, float& un, float& wn) {
     const float I = (ph.k * u * (u - ph.a) * (u - 1.0f) + u * w) * ph.inv_ts;
     un = u + dte * (-r * Minv - I);
     const float vinf = -ph.k * u * (u - ph.a - 1.0f);
     const float den = fmaxf(u + ph.mu2, 1e-6f);
     const float eps = ph.eps0 + __fdividef(ph.mu1 * w, den);
+    if (FIRST) {
+        Ia = I;
+        ga = eps * (vinf - w) * ph.inv_ts;
+    }
     const float x = -eps * dte * ph.inv_ts;
     const float em1_t =
         x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f + x * (1.0f / 720.0f))))));
@@ -445,7 +453,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             sIrr[tid] = (e >= 0 && irr) ? 1 : 0;
 #pragma unroll
             for (int f = 0; f < 6; ++f) sNb[f * M + tid] = nbf[f];
-            slow = e < 0 || (inf & INFO_STIM) || (tick >> (B - b)) == 0;
+            slow = e < 0 || (inf & INFO_STIM);
         }
         const bool fast = !__syncthreads_or(slow) && ph.ionic == 0 && ph.integrator == 1;
 
@@ -628,11 +636,12 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
 
         // ---- 5: item updates (dof_update) with coalesced stores; the RV-T terms and both
         //      values go to shared memory (the operand bytes, free once the MMA completed)
-        //      A tile whose elements are all past their first step of the barrier, without
-        //      stimulus and without padding rows, under the Aliev-Panfilov model with the
-        //      exponential state step, takes the straight-line form (dof_update_ap), so that
-        //      the items of a thread interleave; any other tile the general one.
-        if (fast) {
+        //      A tile without stimulus and without padding rows, under the Aliev-Panfilov model
+        //      with the exponential state step, takes the straight-line form (dof_update_ap),
+        //      so that the items of a thread interleave; any other tile the general one.  Every
+        //      element is at its first step of the barrier exactly at tick 0.
+        auto fast_items = [&](auto first) {
+            constexpr bool FIRST = decltype(first)::value;
             float* sT = reinterpret_cast<float*>(sm + OFF_UHI);
             float* sUo = sT + M * NP;
             float* sUn = sUo + M * NP;
@@ -646,16 +655,24 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
                 const float cr = sCorr[i * RST + q];
                 const float r = sR[i * RST + q] + (sIrr[i] ? cr : 0.0f);
                 float un, wn;
-                const float term = dof_update_ap(ph, sMq[lev * NP + q], sMinv[lev * NP + q], sDte[sLv[i] & 7], u[m],
-                                                 w[m], r, Ia[m], ga[m], un, wn);
+                const float term = dof_update_ap<FIRST>(ph, sMq[lev * NP + q], sMinv[lev * NP + q],
+                                                        sDte[sLv[i] & 7], u[m], w[m], r, Ia[m], ga[m], un, wn);
                 if (in) {
                     const_cast<float*>(sPtrO[i])[q] = un;
                     d.v[(size_t)sE[i] * NP + q] = wn;
+                    if (FIRST && (sLv[i] & 7) > 0) {
+                        d.Ia[(size_t)sE[i] * NP + q] = Ia[m];
+                        d.ga[(size_t)sE[i] * NP + q] = ga[m];
+                    }
                     sT[it] = term;
                     sUo[it] = u[m];
                     sUn[it] = un;
                 }
             }
+        };
+        if (fast) {
+            if (tick == 0) fast_items(std::true_type{});
+            else fast_items(std::false_type{});
         } else {
             float* sT = reinterpret_cast<float*>(sm + OFF_UHI);
             float* sUo = sT + M * NP;
