@@ -58,10 +58,10 @@ SETUP_BARRIERS = 5
 # 2,736,960 elements by the elements due.
 TRAFFIC_PER_LAUNCH = {
     ("slab2d", "k_tick<float,2,1>"): (10.348288e6 + 7 * 5.934080e6) / 8.0,
-    ("slab3d", "k_tick_tc<3,2>"): ((729.893e6 + 1101.857e6) * 2736960 / 2644800
-                                   + (1222.453e6 + 515.861e6) + (1225.104e6 + 516.877e6) + (1221.931e6 + 516.425e6)
-                                   + (1320.383e6 + 553.861e6)
-                                   + (1222.743e6 + 516.109e6) + (1225.131e6 + 516.844e6) + (1222.177e6 + 516.414e6)) / 8.0,
+    ("slab3d", "k_tick_tc<3,2>"): ((737.793e6 + 1101.906e6) * 2736960 / 2644800
+                                   + (1226.609e6 + 516.864e6) + (1226.647e6 + 517.287e6) + (1226.482e6 + 516.999e6)
+                                   + (1323.997e6 + 553.389e6)
+                                   + (1226.882e6 + 517.236e6) + (1227.125e6 + 517.592e6) + (1226.219e6 + 516.737e6)) / 8.0,
 }
 # Algorithmic bytes per DOF-update of the fused sweep (Q1 2D, FP32, AP): V_old 4 + v 4 +
 # V_new 4 + v 4 = 16 B, plus per element step 2d neighbour ids + 4 B level/flags + the FP64
