@@ -19,6 +19,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "../../include/mdl.h"
 #include "mdl_element.cuh"
 
@@ -608,6 +610,38 @@ __device__ __forceinline__ R dof_update(const Phys<R>& ph, R Mq, R Minv, int ke,
     return Mq * (dI * dI + dg * dg);
 }
 
+// dof_update for an element without stimulus under the Aliev-Panfilov model (ionic 0) with
+// the exponential state step (integrator 1): the same expressions as ap_iion, ap_g and
+// ap_step_state without their model and integrator branches, and e^x - 1 as a select of both
+// forms, so that the code is straight-line and the items of a thread can interleave.  FIRST:
+// the element's first step of the barrier (ke == 0), which sets Ia and ga to I and g at the
+// step start; otherwise they are inputs.
+template <bool FIRST>
+__device__ __forceinline__ float dof_update_ap(const Phys<float>& ph, float Mq, float Minv, float dte, float u, float w,
+                                               float r, float& Ia, float& ga, float& un, float& wn) {
+    const float I = (ph.k * u * (u - ph.a) * (u - 1.0f) + u * w) * ph.inv_ts;
+    un = u + dte * (-r * Minv - I);
+    const float vinf = -ph.k * u * (u - ph.a - 1.0f);
+    const float den = fmaxf(u + ph.mu2, 1e-6f);
+    const float eps = ph.eps0 + __fdividef(ph.mu1 * w, den);
+    if (FIRST) {
+        Ia = I;
+        ga = eps * (vinf - w) * ph.inv_ts;
+    }
+    const float x = -eps * dte * ph.inv_ts;
+    const float em1_t =
+        x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f + x * (1.0f / 720.0f))))));
+    const float em1_e = expf(x) - 1.0f;
+    wn = w + (w - vinf) * (fabsf(x) < 0.0625f ? em1_t : em1_e);
+    const float Vm = 0.5f * (u + un);
+    const float wm = 0.5f * (w + wn);
+    const float dI = (ph.k * Vm * (Vm - ph.a) * (Vm - 1.0f) + Vm * wm) * ph.inv_ts - Ia;
+    const float vinf_m = -ph.k * Vm * (Vm - ph.a - 1.0f);
+    const float den_m = fmaxf(Vm + ph.mu2, 1e-6f);
+    const float dg = (ph.eps0 + __fdividef(ph.mu1 * wm, den_m)) * (vinf_m - wm) * ph.inv_ts - ga;
+    return Mq * (dI * dI + dg * dg);
+}
+
 // dof_update for DOF q of an element of refinement level lev (mass from the tables).
 template <typename R, int DIM, int P>
 __device__ __forceinline__ R dof_step(const Tables<R>& T, const Phys<R>& ph, int lev, int q, int ke, R dte, R so,
@@ -630,6 +664,29 @@ __device__ __forceinline__ R elem_pointwise(const TickArgs<R>& a, const Tables<R
     const R dte = a.dteR[b];
     R term = R(0);
     vmax = R(0);
+    if constexpr (sizeof(R) == 4) {
+        // no stimulus, Aliev-Panfilov, exponential state step: the straight-line update, so
+        // that the element's DOFs interleave
+        if (!(inf & INFO_STIM) && ph.ionic == 0 && ph.integrator == 1) {
+            auto run = [&](auto first) {
+                constexpr bool FIRST = decltype(first)::value;
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    constexpr int N1 = P + 1;
+                    R Mq = ph.Wvol[lev];
+#pragma unroll
+                    for (int kk = 0; kk < DIM; ++kk) Mq *= T.w[digit<N1>(q, kk)];
+                    term += dof_update_ap<FIRST>(ph, Mq, ph.Minv[lev][q], dte, u[q], w[q], r[q], Ia[q], ga[q], un[q],
+                                                 wn[q]);
+                    const R av = un[q] < R(0) ? -un[q] : un[q];
+                    vmax = av > vmax ? av : vmax;
+                }
+            };
+            if (ke == 0) run(std::true_type{});
+            else run(std::false_type{});
+            return term;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         R so = R(0), sm = R(0);

@@ -202,37 +202,6 @@ __device__ __forceinline__ void issue_tile_mma(uint32_t tmem, uint32_t sUhi, uin
     mma_commit(mbar);
 }
 
-// dof_update for an element without stimulus under the Aliev-Panfilov model (ionic 0) with
-// the exponential state step (integrator 1): the same expressions as ap_iion, ap_g and
-// ap_step_state without their model and integrator branches, and e^x - 1 as a select of both
-// forms, so that the code is straight-line and the items of a thread can interleave.  FIRST:
-// the element's first step of the barrier (ke == 0), which sets Ia and ga to I and g at the
-// step start; otherwise they are inputs.
-template <bool FIRST>
-__device__ __forceinline__ float dof_update_ap(const Phys<float>& ph, float Mq, float Minv, float dte, float u, float w,
-                                               float r, float& Ia, float& ga, float& un, float& wn) {
-    const float I = (ph.k * u * (u - ph.a) * (u - 1.0f) + u * w) * ph.inv_ts;
-    un = u + dte * (-r * Minv - I);
-    const float vinf = -ph.k * u * (u - ph.a - 1.0f);
-    const float den = fmaxf(u + ph.mu2, 1e-6f);
-    const float eps = ph.eps0 + __fdividef(ph.mu1 * w, den);
-    if (FIRST) {
-        Ia = I;
-        ga = eps * (vinf - w) * ph.inv_ts;
-    }
-    const float x = -eps * dte * ph.inv_ts;
-    const float em1_t =
-        x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f + x * (1.0f / 720.0f))))));
-    const float em1_e = expf(x) - 1.0f;
-    wn = w + (w - vinf) * (fabsf(x) < 0.0625f ? em1_t : em1_e);
-    const float Vm = 0.5f * (u + un);
-    const float wm = 0.5f * (w + wn);
-    const float dI = (ph.k * Vm * (Vm - ph.a) * (Vm - 1.0f) + Vm * wm) * ph.inv_ts - Ia;
-    const float vinf_m = -ph.k * Vm * (Vm - ph.a - 1.0f);
-    const float den_m = fmaxf(Vm + ph.mu2, 1e-6f);
-    const float dg = (ph.eps0 + __fdividef(ph.mu1 * wm, den_m)) * (vinf_m - wm) * ph.inv_ts - ga;
-    return Mq * (dI * dI + dg * dg);
-}
 
 }  // namespace tc
 
