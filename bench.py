@@ -57,7 +57,7 @@ SETUP_BARRIERS = 5
 # ticks 1-7, the same level-1 and level-3 elements at tick 4), tick 0 scaled to the full slab's
 # 2,736,960 elements by the elements due.
 TRAFFIC_PER_LAUNCH = {
-    ("slab2d", "k_tick<float,2,1>"): (10.348288e6 + 7 * 5.934080e6) / 8.0,
+    ("slab2d", "k_tick<float,2,1>"): (10.354432e6 + 7 * (5.937920e6 + 5.938176e6) / 2.0) / 8.0,
     ("slab3d", "k_tick_tc<3,2>"): ((737.793e6 + 1101.906e6) * 2736960 / 2644800
                                    + (1226.609e6 + 516.864e6) + (1226.647e6 + 517.287e6) + (1226.482e6 + 516.999e6)
                                    + (1323.997e6 + 553.389e6)
