@@ -236,14 +236,15 @@ __device__ __forceinline__ float block_row_dot(const float* __restrict__ row, co
 //   0  threads 0..63: metadata of the tile's elements and, per operand slot, the row that
 //      holds the value the element sees (Alg. 1: a coarser LTS neighbour mid-interval is
 //      seen through the linear interpolant of its last step); next tile's ids prefetched
-//   1  warp w = 8-row group w, lane = 4 ii + kk: row ii, columns k = kk + 4 jj; all loads
-//      issued at once, then the row mean c, y = x - c, the row's power-of-two scale and
-//      the FP16 hi/lo terms in the swizzled operand layout
-//   2  one thread issues the MMAs and commits to an mbarrier
+//   1  warp w = 8-row group w, lane = 4 ii + kk: row ii, column pairs k = 2 kk + 8 jj +
+//      {0, 1}; all loads issued at once, then the row mean c, y = x - c, the row's
+//      power-of-two scale and the FP16 hi/lo terms in the swizzled operand layout
+//   2  one thread of warp 0 issues the MMAs and commits to an mbarrier
 //   3  while they run: corrections of non-regular faces (warps 1-7, warp per element, lane =
 //      row) and the loads of the pointwise step, item by item (element, DOF)
 //   4  warps 0-3: D row -> scaled residual in shared memory
-//   5  the pointwise step (dof_update) of every item with coalesced stores
+//   5  the pointwise step of every item with coalesced stores: straight-line
+//      (dof_update_ap) for a tile without stimulus or padding rows, else dof_update
 //   6  per element (four threads each): the RV-T accumulation; a due probe check is recorded
 //      and run by threads 64..127 during the next tile's metadata step (or after the last)
 // unscale = 2^-t undoes the scaling of B by 2^t; each row's scale of y is undone by 2^-sc.
