@@ -182,3 +182,43 @@ def test_full_size_slab3d_tensor_matches_thread(mdl):
     la, lb = a.read_activation(), b.read_activation()
     assert np.array_equal(np.isfinite(la), np.isfinite(lb))
     a.close(); b.close()
+
+
+def test_full_size_slab3d_tensor_conserves_integral_pure_diffusion(mdl):
+    """A property that holds at any size, checked on the full 3D slab mesh (2.7M elements
+    after the AMR reaches depth 3, hanging and boundary faces, the tensor-core sweep and its
+    correction blocks): without ionic current and stimulus, a global forward Euler step
+    changes int V = sum_q M_q V_q by -dt 1^T A u, and 1^T A = 0 for the symmetric SIPG
+    operator with zero-flux boundaries.  In FP32 the residual of int V after 20 steps is set
+    by the per-(level, node) rounding of M_q M_q^-1 (~1e-7) and by unbiased roundings, far
+    below 1e-3 of the mass-weighted change of V; a dropped or doubled face term leaves the
+    flux it carries, of the order of that change."""
+    import bench as B
+    prob = W.slab_3d_q2()
+    a = mdl.Sim(prob)
+    X = B.node_coords_of(a, prob)
+    V0, v0 = W.planar_front_state(X, B.PLANAR["x0"], B.PLANAR["width"], B.PLANAR["tail"])
+    a.set_initial(V0, v0)
+    a.step_barriers(4)                      # AMR refines the front to depth 3
+    root, level, coords, _ = a.read_mesh()
+    V1, s1 = a.read_V(), a.read_state()
+    a.close()
+    assert level.max() == 3 and level.size > 2_000_000
+    diff = prob.replace(ionic_model=-1, stimuli=[], amr_enabled=0, lts_enabled=0, n_lts_levels=1,
+                        dt_barrier=0.0)
+    g = mdl.Sim(diff)
+    g.upload_mesh(level, coords.reshape(-1), root)
+    g.set_initial(V1, s1)
+    # int V of the uploaded FP32 state: M_q = prod_k (h_k / 2) w_{a_k}, h_k = extent_k / (base_k 2^l)
+    w = np.array([5.0, 8.0, 5.0]) / 9.0
+    wq = (w[None, None, :] * w[None, :, None] * w[:, None, None]).reshape(-1)
+    h = np.array(diff.extent)[None, :] / (np.array(diff.base)[None, :] * (2.0 ** level.astype(np.float64))[:, None])
+    Mq = np.prod(h / 2.0, axis=1)[:, None] * wq[None, :]
+    I0 = float(np.sum(Mq * V1.reshape(level.size, 27)))
+    g.step_barriers(20)
+    I1 = g.stats()["integral_V"]
+    Vn = g.read_V()
+    g.close()
+    change = float(np.sum(Mq * np.abs(Vn - V1).reshape(level.size, 27)))
+    assert change > 0.0
+    assert abs(I1 - I0) <= 1e-3 * change, (I0, I1, change)
