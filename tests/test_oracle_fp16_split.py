@@ -98,3 +98,26 @@ def test_fp16_hi_lo_split_reaches_fp32_accuracy():
     assert worst_split <= 3 * 189 * 2.0 ** -24 + 4 * 2.0 ** -22, worst_split
     assert worst_tf32 >= 30 * worst_split, (worst_tf32, worst_split)
     assert worst_noshift >= 30 * worst_split, (worst_noshift, worst_split)
+
+
+def test_level_blocks_scale_by_power_of_two():
+    """On box elements every SIPG block of level l is 2^((2-d) l) times its level-0 block
+    (volume: (2/h)^2 h^d; faces: h^(d-1) / h), the exact row scale that lets one level-0
+    operator serve every level of the tensor-core residual."""
+    prob = _problem()
+    disc = Disc(prob, Forest(3, prob.base, 3, prob.extent))
+    for level in (1, 2, 3):
+        scale = 2.0 ** ((2 - 3) * level)
+        V0, Vl = disc.volume_block(0), disc.volume_block(level)
+        assert np.allclose(Vl, scale * V0, rtol=1e-13, atol=1e-15 * np.abs(V0).max())
+        for k in range(3):
+            F0, Fl = disc.face_block(k, (0, 0, ())), disc.face_block(k, (level, level, ()))
+            assert np.allclose(Fl, scale * F0, rtol=1e-13, atol=1e-15 * np.abs(F0).max())
+    # the same relation with one level of refinement across the face (coarse side at level l)
+    for level in (0, 1, 2):
+        scale = 2.0 ** ((2 - 3) * level)
+        for k in range(3):
+            for pos in ((0, 0), (1, 0), (0, 1), (1, 1)):
+                H0 = disc.face_block(k, (0, 1, pos))
+                Hl = disc.face_block(k, (level, level + 1, pos))
+                assert np.allclose(Hl, scale * H0, rtol=1e-13, atol=1e-15 * np.abs(H0).max())
