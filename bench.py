@@ -174,6 +174,18 @@ def node_coords_of(sim, prob):
     return X.reshape(-1, d)
 
 
+def reduce_over_ranks(total_ms, dof_updates, dist, device):
+    """Whole-job figures of a multi-rank run: the slowest rank's timed milliseconds and the
+    DOF-updates of all ranks (each rank runs its own replica)."""
+    import torch
+    t = torch.tensor([float(total_ms), float(dof_updates)], device=device, dtype=torch.float64)
+    ms = t[0:1].clone()
+    dof = t[1:2].clone()
+    dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    dist.all_reduce(dof, op=dist.ReduceOp.SUM)
+    return ms.item(), dof.item()
+
+
 def run_ours(args, rank, world):
     import torch
     torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
@@ -241,11 +253,7 @@ def run_ours(args, rank, world):
     if st["timed_barriers"] != args.steps:
         raise RuntimeError("sweep timing covers %d of %d barriers" % (st["timed_barriers"], args.steps))
     if dist:
-        t = torch.tensor([total_ms, float(st["dof_updates"])], device="cuda", dtype=torch.float64)
-        mx = t.clone()
-        dist.all_reduce(mx[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(mx[1:2], op=dist.ReduceOp.SUM)
-        total_ms_all, dof_all = mx[0].item(), mx[1].item()
+        total_ms_all, dof_all = reduce_over_ranks(total_ms, st["dof_updates"], dist, "cuda")
     else:
         total_ms_all, dof_all = total_ms, float(st["dof_updates"])
     value = dof_all / (total_ms_all / 1e3)
