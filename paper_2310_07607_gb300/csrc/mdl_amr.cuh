@@ -271,18 +271,17 @@ __global__ void k_owner_fill(const int4* coord, int32_t* owner, Grid g, const De
             int32_t* dst = owner + ((int64_t)a.x << sh) + g.fine[0] * (((int64_t)a.y << sh) + row);
             for (int x = 0; x < n; ++x) dst[x] = (int32_t)e;
         }
-        return;
-    }
-    for (int64_t e = gtid(); e < ne; e += gstride()) {
-        const int4 a = coord[e];
-        const int sh = g.L - a.w;
-        const int n = 1 << sh;
-        const int nrows = DIM == 3 ? n * n : n;
-        for (int row = 0; row < nrows; ++row) {
-            const int64_t y = ((int64_t)a.y << sh) + (row % n);
-            const int64_t z = DIM == 3 ? (((int64_t)a.z << sh) + row / n) : 0;
-            int32_t* dst = owner + ((int64_t)a.x << sh) + g.fine[0] * (y + g.fine[1] * z);
-            for (int x = 0; x < n; ++x) dst[x] = (int32_t)e;
+    } else {
+        for (int64_t e = gtid(); e < ne; e += gstride()) {
+            const int4 a = coord[e];
+            const int sh = g.L - a.w;
+            const int n = 1 << sh;
+            for (int row = 0; row < n * n; ++row) {
+                const int64_t y = ((int64_t)a.y << sh) + (row % n);
+                const int64_t z = ((int64_t)a.z << sh) + row / n;
+                int32_t* dst = owner + ((int64_t)a.x << sh) + g.fine[0] * (y + g.fine[1] * z);
+                for (int x = 0; x < n; ++x) dst[x] = (int32_t)e;
+            }
         }
     }
 }

@@ -935,7 +935,7 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const do
                                                  double dt, double inv_dt, int inv_dt_exact) {
     pdl_enter();
     using S = Shape<DIM, P>;
-    constexpr int N1 = S::N1, NP = S::NP;
+    constexpr int NP = S::NP;
     __shared__ double red[256];
     if (d.meta->err) return;
     const int64_t ne = d.meta->ne;
