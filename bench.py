@@ -363,9 +363,12 @@ def slot_alg_bytes(prob):
 def run_batch(args, rank, world):
     """64 heterogeneous resident instances (32 2D Q1, 16 3D Q1, 16 3D Q2; base element counts
     log-uniform in [1e3, 1e5], seed 4).  A step is one batch round: every instance advances
-    one barrier, all slots' work issued on their own streams before any is waited for."""
+    one barrier, all slots' work issued on their own streams before any is waited for.  One GPU:
+    under a multi-rank launch it stops with an error instead of reporting one rank's rate."""
+    if world > 1:
+        raise SystemExit("bench.py --workload batch64 runs on one GPU (got WORLD_SIZE=%d)" % world)
     import torch
-    torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
+    torch.cuda.set_device(0)
     from paper_2310_07607_gb300 import build, mdl
     build.build()
     inst = W.batch_instances(64, seed=4)

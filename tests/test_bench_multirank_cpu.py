@@ -1,6 +1,7 @@
 """The multi-rank path of bench.py on the host with the gloo backend, world size 2: the
-whole-job figures take the slowest rank's time and the DOF-updates of all ranks, and the
-reference arm launched by torchrun prints one line from rank 0 while the other rank exits 0."""
+whole-job figures take the slowest rank's time and the DOF-updates of all ranks, the
+reference arm launched by torchrun prints one line from rank 0 while the other rank exits 0,
+and the one-GPU batch workload refuses a multi-rank launch."""
 import json
 import os
 import socket
@@ -54,3 +55,12 @@ def test_reference_arm_under_torchrun_world2():
     assert len(lines) == 1
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["value"] > 0
+
+
+def test_batch_workload_refuses_multirank():
+    env = dict(os.environ, WORLD_SIZE="2", RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "batch64"],
+                       capture_output=True, text=True, cwd=ROOT, env=env, timeout=300)
+    assert r.returncode != 0
+    assert "one GPU" in r.stderr
+    assert not any(ln.strip().startswith("{") for ln in r.stdout.splitlines())
