@@ -1,19 +1,21 @@
 """Benchmark: explicit local space-time adaptive monodomain stepping on one GB300.
 
-Workload (the 2D slab the headline metric is quoted on): 2x2 cm, 256x256 Q1 DG
-base mesh, quadtree AMR to depth 3 driven by the Kelly indicator, 4 synchronous
-LTS levels, Aliev-Panfilov, 3:1 fibres at a seeded angle, FP32 bulk arithmetic.
-The synthetic initial state is a developed excitation front (quarter circle of
-radius 1 cm around the stimulus corner, tanh edge 0.01 cm); setup barriers let
-the AMR refine it to depth 3 before warm-up.
+Default workload (the largest single-GPU configuration, HBM-resident): the 3D slab
+2 x 0.7 x 0.3 cm, 128x48x20 Q2 DG hexes, octree AMR to depth 3 driven by the Kelly
+indicator, 4 synchronous LTS levels, Aliev-Panfilov, transversely isotropic conductivity
+(1.2 / 0.3 mS/cm along x), FP32 bulk arithmetic with the element residual on the tcgen05
+tensor cores.  The synthetic initial state is a planar excitation front at mid-slab;
+setup barriers let the AMR refine it to depth 3 (2.8M elements) before warm-up.
+`--workload slab2d` runs the 2D slab (2x2 cm, 256x256 Q1, AMR 3, LTS 4), `spiral2d` the
+temporal-adaptivity workload, `batch64` and `serve` the many-simulation workloads.
 
-A step is one barrier step of Alg. 1: eta^s, refine/coarsen (host forest
-bookkeeping included), level assignment, all sweep ticks, eta^t, LAT, int V.
-value = DOF-updates / s over the K timed steps (device-timed with CUDA events on
-the library's stream, L2 flushed between steps by writing a 512 MiB buffer).
+A step is one barrier step of Alg. 1: eta^s, refine/coarsen (device forest bookkeeping),
+level assignment, all sweep ticks, eta^t, LAT, int V.  value = DOF-updates / s over the K
+timed steps (device-timed with CUDA events on the library's stream, L2 flushed between
+steps by writing a 512 MiB buffer).
 
---impl reference times the FP64 numpy oracle on the host cores instead (a
-bounded sample of the same workload, see cpu_baseline).
+--impl reference times the FP64 numpy oracle on the host cores instead (a bounded sample
+of the same workload, see cpu_baseline).
 """
 from __future__ import annotations
 
@@ -298,13 +300,15 @@ def run_ours(args, rank, world):
                 "amr_host": st["amr_host_ms"] / args.steps, "mesh_upload_transfer": st["transfer_ms"] / args.steps},
             "amr_rebuilds": st["amr_rebuilds"],
             "sweep_only_dof_updates_per_s": st["dof_updates"] / sweep_s if sweep_s > 0 else None,
-            "wall_s_timed": wall1 - wall0,
+            # host clock around the same K steps: each step also holds the L2 flush and the
+            # library's end-of-call synchronisation (one read of the device bookkeeping)
+            "host_wall": {"s": wall1 - wall0, "ms_per_step": (wall1 - wall0) * 1e3 / args.steps},
             "roofline": roof,
             "e2e": e2e,
             "gpu_launches": st["kernel_launches"],
             "clocks": clocks,
         }
-        if world == 1 and not args.no_cpu_baseline and args.workload == "slab2d":
+        if world == 1 and not args.no_cpu_baseline and args.workload in CPU_SAMPLE:
             out["cpu_baseline"] = cpu_baseline(args)
     sim.close()
     if dist:
@@ -488,7 +492,15 @@ def run_plain_loop(mdl, reqs, wall, torch):
 # The FP64 oracle on the host cores (bounded sample of the same workload).
 # ---------------------------------------------------------------------------
 
-CPU_SAMPLE = dict(base=(64, 64, 1), barriers=6)
+# Bounded samples of each workload for the oracle: a patch of roots with the workload's h,
+# physics and thresholds, `setup` barriers (the AMR reaching depth 3 on the front) before
+# `barriers` timed barrier steps.
+CPU_SAMPLE = {
+    "slab2d": dict(base=(64, 64, 1), setup=3, barriers=6),
+    "slab3d": dict(base=(4, 2, 2), setup=3, barriers=10),
+}
+# peak host memory of one oracle process on the sample (its assembled sparse operator)
+CPU_SAMPLE_BYTES = {"slab2d": 2.5e9, "slab3d": 4.0e9}
 
 ORACLE_SNIPPET = r"""
 import json, sys, time
@@ -496,10 +508,17 @@ sys.path.insert(0, %(root)r)
 import numpy as np
 import workloads as W
 from oracle import lts
-prob = W.scaled(W.slab_2d_q1_256(), %(base)r).replace(precision=64)
+wl = %(workload)r
+if wl == "slab2d":
+    prob = W.scaled(W.slab_2d_q1_256(), %(base)r).replace(precision=64)
+else:
+    prob = W.scaled(W.slab_3d_q2(), %(base)r).replace(precision=64)
 sim = lts.Sim(prob)
 X = sim.disc.node_coords()
-V0, v0 = W.front_state(X, (0.0, 0.0, 0.0), %(radius)r, %(width)r, %(tail)r)
+if wl == "slab2d":
+    V0, v0 = W.front_state(X, (0.0, 0.0, 0.0), %(radius)r, %(width)r, %(tail)r)
+else:
+    V0, v0 = W.planar_front_state(X, %(x0)r, %(width)r, %(tail)r)
 sim.V, sim.v = V0, v0
 for _ in range(%(setup)d):
     sim.barrier()
@@ -513,48 +532,126 @@ print(json.dumps(res))
 """
 
 
-def oracle_run(base, setup, steps, radius):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET % dict(root=ROOT, base=tuple(base), radius=radius, width=FRONT["width"],
-                                 tail=FRONT["tail"] * radius / FRONT["radius"], setup=setup, steps=steps)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+def _oracle_code(workload, setup, steps):
+    smp = CPU_SAMPLE[workload]
+    base = smp["base"]
+    if workload == "slab2d":
+        # same h and front width; front radius scaled with the patch so it crosses the patch
+        radius = FRONT["radius"] * base[0] / 256.0
+        geo = dict(radius=radius, x0=0.0, width=FRONT["width"], tail=FRONT["tail"] * radius / FRONT["radius"])
+    else:
+        # the planar front at the middle of the patch, as on the full slab
+        x0 = PLANAR["x0"] * base[0] / 128.0
+        geo = dict(radius=0.0, x0=x0, width=PLANAR["width"], tail=PLANAR["tail"])
+    return ORACLE_SNIPPET % dict(root=ROOT, workload=workload, base=tuple(base), setup=setup, steps=steps, **geo)
+
+
+def _oracle_env():
+    return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+
+def oracle_run(workload, setup, steps):
+    """One single-threaded oracle process on the workload's sample: [(DOF-updates, seconds)]."""
+    r = subprocess.run([sys.executable, "-c", _oracle_code(workload, setup, steps)], capture_output=True,
+                       text=True, env=_oracle_env(), timeout=1800)
     if r.returncode != 0:
         raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def host_cores():
+    """Cores this process may run on (the affinity mask, as nproc reports)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def mem_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def oracle_run_all_cores(workload, setup, steps, n):
+    """n single-threaded oracle processes at once, one per host core, each on its own copy of
+    the sample: the host's aggregate rate is their DOF-updates over the slowest one's time."""
+    code = _oracle_code(workload, setup, steps)
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                              text=True, env=_oracle_env()) for _ in range(n)]
+    dofs, secs, failed = 0, 0.0, None
+    try:
+        for p in procs:
+            out, err = p.communicate(timeout=3600)
+            if p.returncode != 0:
+                failed = "oracle process exited %d: %s" % (p.returncode, err[-500:])
+                break
+            res = json.loads(out.strip().splitlines()[-1])
+            dofs += sum(r[0] for r in res)
+            secs = max(secs, sum(r[1] for r in res))
+    finally:
+        for p in procs:
+            if p.poll() is None:
+                p.kill()
+                p.wait()
+    if failed:
+        raise RuntimeError(failed)
+    return dofs, secs
+
+
+def _sample_text(workload, n_steps):
+    smp = CPU_SAMPLE[workload]
+    b = smp["base"][:2] if workload == "slab2d" else smp["base"]
+    return ("FP64 numpy oracle on a %s-root patch of the %s (same h, physics and thresholds), "
+            "%d barrier steps after %d setup barriers that refine the front to depth 3"
+            % ("x".join(str(x) for x in b), "2D slab" if workload == "slab2d" else "3D slab", n_steps,
+               smp["setup"]))
+
+
 def cpu_baseline(args):
-    base = CPU_SAMPLE["base"]
-    # same h and front width; front radius scaled with the patch so it crosses the patch
-    radius = FRONT["radius"] * base[0] / 256.0
-    res = oracle_run(base, 3, CPU_SAMPLE["barriers"], radius)
-    dofs = sum(r[0] for r in res)
-    secs = sum(r[1] for r in res)
-    return {"value": dofs / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "FP64 numpy oracle, %dx%d-root patch of the slab (same h, physics, thresholds), "
-                      "front r=%.3f cm, %d barrier steps after 3 setup barriers, %.1f s"
-                      % (base[0], base[1], radius, len(res), secs)}
+    smp = CPU_SAMPLE[args.workload]
+    res = oracle_run(args.workload, smp["setup"], smp["barriers"])
+    d1 = sum(r[0] for r in res)
+    s1 = sum(r[1] for r in res)
+    nproc = host_cores()
+    single = {"value": d1 / s1, "unit": UNIT, "cores": 1, "seconds": round(s1, 2)}
+    # one process per core, as many as the host memory holds (each keeps its own operator)
+    avail = mem_available()
+    n = nproc if avail is None else max(1, min(nproc, int(0.6 * avail / CPU_SAMPLE_BYTES[args.workload])))
+    try:
+        dall, sall = oracle_run_all_cores(args.workload, smp["setup"], smp["barriers"], n)
+    except Exception as ex:  # report the single-core figure rather than no baseline
+        return {"value": single["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "nproc": nproc,
+                "sample": _sample_text(args.workload, len(res)), "all_cores_failed": str(ex)[:300]}
+    return {"value": dall / sall, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": _sample_text(args.workload, len(res)) + "; %d processes at once, one per host core" % n,
+            "nproc": nproc, "single_core": single}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    base = CPU_SAMPLE["base"]
-    radius = FRONT["radius"] * base[0] / 256.0
-    res = oracle_run(base, 3 + args.warmup, args.steps, radius)
+    workload = args.workload if args.workload in CPU_SAMPLE else "slab3d"
+    smp = CPU_SAMPLE[workload]
+    res = oracle_run(workload, smp["setup"] + args.warmup, args.steps)
     dofs = sum(r[0] for r in res)
     secs = sum(r[1] for r in res)
     value = dofs / secs
+    factory = WORKLOADS[workload][0]
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / len(res),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "slab2d_q1_256x256_amr3_lts4_ap_fp32",
-                   "sample": "%dx%d-root patch, same h/physics/thresholds" % (base[0], base[1])},
+        "config": {"workload": workload_name(factory()),
+                   "sample": "%s-root patch, same h/physics/thresholds" % "x".join(str(x) for x in smp["base"])},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "FP64 numpy oracle on a %dx%d-root patch of the slab, %d barrier steps"
-                                   % (base[0], base[1], len(res))},
+                         "sample": _sample_text(workload, len(res))},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -566,7 +663,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="slab2d", choices=sorted(WORKLOADS) + ["batch64", "serve"])
+    ap.add_argument("--workload", default="slab3d", choices=sorted(WORKLOADS) + ["batch64", "serve"])
     ap.add_argument("--serve-round", type=int, default=16, help="barriers per slot per serving round")
     ap.add_argument("--tick-shape", default="", help="sweep launch shape 'threads,blocks_per_sm'")
     ap.add_argument("--base", default="", help="base grid 'nx,ny[,nz]' at the workload's element size")

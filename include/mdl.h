@@ -7,8 +7,11 @@
  * symmetric interior penalty DG discretisation (Eq. monodomain-primal-formulation,
  * Eq. monodomain-numerical-flux) on GL-collocated Q1/Q2 elements (Sec. 2.1),
  * forest-of-trees h-adaptivity (Sec. 2.2), and synchronous local time stepping
- * (Sec. 2.3, Alg. 1).  All stepping runs in CUDA kernels for sm_103a; the host
- * keeps the forest bookkeeping (refine/coarsen, 2:1 balance, face tables).
+ * (Sec. 2.3, Alg. 1).  Every part of a barrier step runs in CUDA kernels for sm_103a:
+ * the sweep, both indicators, the level assignment and the forest adaptation
+ * (refine/coarsen marks, 2:1 closure, coarsenable families, the new leaf list, face
+ * tables and the solution transfer).  The host only validates uploads and reads
+ * results.
  *
  * Conventions
  *   - Every function returns MDL_OK (0) or a negative MDL_E_* code; no C++
@@ -96,8 +99,8 @@ typedef struct mdl_stats {
     double  sweep_ms;          /* device time of the sweep kernels (CUDA events; 0 unless timing is on) */
     int64_t timed_barriers;    /* barriers whose sweep time is included in sweep_ms */
     double  indicator_ms;      /* device time of the eta^s kernel (timing on) */
-    double  amr_host_ms;       /* host wall time in refine/coarsen bookkeeping */
-    double  transfer_ms;       /* host wall time to upload a rebuilt mesh + device transfer */
+    double  amr_host_ms;       /* always 0: the adaptation runs on the device (kept for layout) */
+    double  transfer_ms;       /* always 0: the solution transfer runs on the device (kept for layout) */
     double  integral_V;        /* last FP64 integral of V over the domain */
     int64_t n_elements;        /* current leaf count */
     int64_t level_counts[8];   /* elements per LTS level b in the last barrier */
@@ -272,14 +275,17 @@ void mdl_batch_destroy(mdl_batch* b);
  * a file-scope static device array of MDL_NOALLOC_MAX_PARTIALS doubles (32 KiB) that every
  * GPU which loads the library keeps until the process exits.
  *   V_dev     device pointer, n_e (p+1)^d values, float (precision 32) or double (64)
- *   level_dev device pointer, n_e refinement levels (0..7)
+ *   level_dev device pointer, n_e refinement levels (0..7); a level outside that range makes
+ *             the result NaN (the levels are device data: they are checked by the kernel)
  *   out_dev   device pointer to one double, written on `stream`
  *   stream    cudaStream_t (NULL = legacy default stream); the call is asynchronous
  * The first call on a device looks up the array's device address (once per device, with
  * that device current); make that first call before any stream capture begins.  Every
  * call shares the one array: calls whose kernels overlap on a GPU race and give wrong
  * results, so serialise them (one stream, or events).  n_e above MDL_NOALLOC_MAX_ELEMENTS
- * is rejected with MDL_E_ARG; the message is in mdl_noalloc_last_error(). */
+ * is rejected with MDL_E_ARG; the message is in mdl_noalloc_last_error().  A CUDA error
+ * already pending on the calling thread when the call starts is not cleared: the call
+ * returns MDL_E_CUDA at once, with its own message, and launches nothing. */
 #define MDL_NOALLOC_MAX_PARTIALS 4096
 #define MDL_NOALLOC_MAX_ELEMENTS ((int64_t)1 << 30)
 int mdl_integral_noalloc(int32_t dim, int32_t order, const double* extent, const int32_t* base,

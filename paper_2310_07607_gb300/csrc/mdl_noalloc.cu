@@ -34,7 +34,11 @@ __global__ void k_integral_partials(const R* __restrict__ V, const int8_t* __res
     double s = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_e;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int l = level[e] & 7;
+        const int l = level[e];
+        if (l < 0 || l > 7) {
+            s += __longlong_as_double(0x7ff8000000000000ll);   // a level outside 0..7: NaN result
+            continue;
+        }
         for (int q = 0; q < n_p; ++q) s += mt.m[l][q] * (double)V[e * n_p + q];
     }
     red[threadIdx.x] = s;
@@ -108,6 +112,11 @@ extern "C" int mdl_integral_noalloc(int32_t dim, int32_t order, const double* ex
         cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double), st);
         return e == cudaSuccess ? MDL_OK : fail(MDL_E_CUDA, cudaGetErrorString(e));
     }
+    // an error left pending by the caller's own CUDA work is reported as such (and left in
+    // place) instead of being taken for a failure of this call's launches
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess)
+        return fail(MDL_E_CUDA, "a CUDA error from earlier work was pending before this call");
     double* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc) return rc;

@@ -34,7 +34,7 @@ def test_reference_arm_prints_one_contract_line():
     assert out["cpu_baseline"]["cores"] >= 1
     assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0,
                           "d2h_bytes_per_step": 0}
-    assert out["config"]["workload"].startswith("slab2d_q1_256x256")
+    assert out["config"]["workload"].startswith("slab3d_q2_128x48x20")
 
 
 def test_gpu_arm_fails_without_a_gpu():

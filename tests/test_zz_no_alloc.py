@@ -56,3 +56,41 @@ def test_integral_noalloc_matches_barrier_diagnostic(precision):
         mdl.integral_noalloc(prob, vptr, lev.data_ptr(), (1 << 30) + 1, out.data_ptr(), stream)
     assert ei.value.code == -1
     g.close()
+
+
+@pytest.mark.parametrize("dim,order", [(2, 1), (3, 2)])
+def test_integral_noalloc_levels_up_to_seven_and_out_of_range(dim, order):
+    """Levels span the whole documented range 0..7 (a synthetic field, not a mesh); a level
+    outside it turns the result into NaN instead of wrapping to another level's mass."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from oracle import basis
+    from paper_2310_07607_gb300 import build, mdl
+    build.build()
+    prob = W.Problem(dim=dim, order=order, extent=(0.4, 0.3, 0.2), base=(4, 3, 2), precision=64)
+    n_p = (order + 1) ** dim
+    rng = np.random.default_rng(11)
+    n_e = 3000
+    level = rng.integers(0, 8, n_e).astype(np.int8)
+    level[:8] = np.arange(8)
+    V = rng.standard_normal(n_e * n_p)
+    wq = basis.node_weights(dim, order)
+    h = np.array([[prob.extent[k] / (prob.base[k] * 2.0 ** l) for k in range(dim)] for l in range(8)])
+    m = np.prod(h / 2.0, axis=1)[level][:, None] * wq[None, :]
+    ref = float(np.sum(m.reshape(-1) * V))
+    Vd = torch.tensor(V, dtype=torch.float64, device="cuda")
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        lev = torch.tensor(level, dtype=torch.int8, device="cuda")
+        torch.cuda.synchronize()
+        mdl.integral_noalloc(prob, Vd.data_ptr(), lev.data_ptr(), n_e, out.data_ptr(), 0)
+        torch.cuda.synchronize()
+        assert abs(out.item() - ref) <= 1e-12 * np.sum(np.abs(m.reshape(-1) * V)), (out.item(), ref)
+    bad = level.copy()
+    bad[17] = 8
+    lev = torch.tensor(bad, dtype=torch.int8, device="cuda")
+    torch.cuda.synchronize()
+    mdl.integral_noalloc(prob, Vd.data_ptr(), lev.data_ptr(), n_e, out.data_ptr(), 0)
+    torch.cuda.synchronize()
+    assert np.isnan(out.item())
