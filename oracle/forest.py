@@ -225,6 +225,9 @@ class Forest:
                     break
             if ok:
                 coarsen.append((par, members))
+        if not refined and not coarsen:
+            # nothing changes: the same leaves in the same order, every one kept
+            return self, [('keep', i) for i in range(self.n)]
         for par, members in coarsen:
             for m in members:
                 leafset.discard(m)

@@ -388,6 +388,26 @@ class Disc:
         return 1.0 / np.max(np.abs(L).sum(axis=2), axis=1)
 
     # ------------------------------------------------------------------
+    def _eta_s_groups(self):
+        """The faces grouped by (axis, signature) with each group's face data: the flux rows
+        D grad psi . e_k of both sides at the face points, the weights, h_F and W_F (fixed
+        for a mesh: built once per Disc)."""
+        if getattr(self, "_eta_groups", None) is None:
+            groups: Dict[Tuple, List[Tuple[int, int]]] = {}
+            for (m, p, k, sig) in self.faces:
+                groups.setdefault((k, sig), []).append((m, p))
+            out = []
+            for (k, sig), pairs in groups.items():
+                X, W, (phim, gm, hm), (phip, gp, hp), hf = self._face_points(k, sig)
+                fm = np.einsum('l,qjl->qj', self.D[k], gm)
+                fp = np.einsum('l,qjl->qj', self.D[k], gp)
+                area = np.prod([hf[l] for l in range(self.dim) if l != k])
+                hF = area ** (1.0 / (self.dim - 1))
+                WF = area / 2.0 ** (self.dim - 1)
+                out.append((np.array(pairs, dtype=np.int64), fm, fp, W, hF, WF))
+            self._eta_groups = out
+        return self._eta_groups
+
     def eta_s(self, u: np.ndarray) -> np.ndarray:
         """Kelly-type spatial indicator (Eq. dg-error-estimate).
 
@@ -399,18 +419,8 @@ class Disc:
         n_p = self.n_p
         U = np.asarray(u, dtype=np.float64).reshape(self.ne, n_p)
         acc = np.zeros(self.ne)
-        groups: Dict[Tuple, List[Tuple[int, int]]] = {}
-        for (m, p, k, sig) in self.faces:
-            groups.setdefault((k, sig), []).append((m, p))
-        for (k, sig), pairs in groups.items():
-            pairs = np.array(pairs, dtype=np.int64)
-            X, W, (phim, gm, hm), (phip, gp, hp), hf = self._face_points(k, sig)
-            fm = np.einsum('l,qjl->qj', self.D[k], gm)
-            fp = np.einsum('l,qjl->qj', self.D[k], gp)
+        for pairs, fm, fp, W, hF, WF in self._eta_s_groups():
             J = U[pairs[:, 0]] @ fm.T - U[pairs[:, 1]] @ fp.T      # (nf, pts)
-            area = np.prod([hf[l] for l in range(self.dim) if l != k])
-            hF = area ** (1.0 / (self.dim - 1))
-            WF = area / 2.0 ** (self.dim - 1)
             c = hF / (2.0 * self.p) * ((WF * J) ** 2 * W[None, :]).sum(axis=1)
             np.add.at(acc, pairs[:, 0], c)
             np.add.at(acc, pairs[:, 1], c)

@@ -181,6 +181,8 @@ def test_lts_hanging_fp32_matches_oracle(mdl, dim, p):
     assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-3
     es, et = g.read_indicators()
     assert np.allclose(et, o.eta_t, rtol=2e-3, atol=1e-12 * et.max())
+    # activation times within one finest substep of the barrier
+    lat_compare(g.read_activation(), o.lat, o.dt / 2 ** (prob.n_lts_levels - 1))
     g.close()
 
 
@@ -383,6 +385,60 @@ def test_full_size_slab2d_replay_matches_oracle(mdl):
     es_g = es_g[:es_o.size]       # eta^s lives on the mesh before this barrier's adaptation
     big = es_o > 1e-3 * es_o.max()
     assert np.abs(es_g[big] - es_o[big]).max() <= 5e-3 * es_o.max()
+    g.close()
+
+
+def test_long_horizon_fp32_amr_lts_replay_matches_oracle(mdl):
+    """FP32 AMR + 4 LTS levels on an 8x8-root patch of the 2D slab (the slab's h, physics and
+    thresholds; the developed front scaled to the patch) over 4096 barrier steps (0.25 ms),
+    with the oracle's eta^s replayed every barrier: meshes and levels bit-exact, V within
+    1e-3 (M-weighted) at every checkpoint, the same probes activated, and activation times
+    within the FP32 crossing-time tolerance, including the probes the front reaches after
+    t = 0.  That tolerance is max(one finest substep, 4e-5 ms): the finest substep here is
+    7.6e-6 ms, below what FP32 resolves -- V drifts from the FP64 oracle by ~1e-5..4e-5 at
+    the front over 10^3..10^4 steps, and divided by the upstroke slope (dV/dt ~ 1..3 per ms)
+    that moves a threshold crossing by ~1e-5 ms."""
+    prob = W.scaled(W.slab_2d_q1_256(), (8, 8, 1))
+    o = lts.Sim(prob.replace(precision=64))
+    X = o.disc.node_coords()
+    r = 1.0 * 8 / 256
+    V0, v0 = W.front_state(X, (0.0, 0.0, 0.0), r, 0.01, 0.3 * r)
+    o.V, o.v = V0.copy(), v0.copy()
+    o._lat_initial()
+    initially = np.isfinite(o.lat).copy()
+    g = mdl.Sim(prob)
+    g.set_initial(V0, v0)
+    assert g.dt == o.dt
+    fine = max(o.dt / 8, 4e-5)
+    n_bar, checks, rebuilds = 4096, 0, 0
+    for n in range(n_bar):
+        es = o.disc.eta_s(o.V)
+        g.set_indicators(eta_s=es)
+        newf, plan = o.forest.adapt(es, prob.tau_refine, prob.tau_coarsen)
+        if any(pl[0] != 'keep' for pl in plan) or newf.n != o.forest.n:
+            o.transfer(newf, plan)
+            rebuilds += 1
+        lev = o.assign_levels(o.eta_t)
+        o.eta_t = o.sweep(lev)
+        o.barrier_count += 1
+        g.step_barriers(1)
+        if (n + 1) % 512 == 0:
+            r2, l2, c2, b2 = g.read_mesh()
+            lvo, cco, rto = forest_arrays(o.forest)
+            assert np.array_equal(l2, lvo) and np.array_equal(c2, cco), n
+            assert np.array_equal(b2, lev), n
+            rel = mass_rel_l2(o.disc.M, g.read_V(), o.V)
+            la = g.read_activation()
+            both = np.isfinite(la) & np.isfinite(o.lat)
+            print("barrier %d: V rel %.2e, LAT max diff %.2e ms over %d probes"
+                  % (n + 1, rel, np.abs(la[both] - o.lat[both]).max() if both.any() else 0.0, both.sum()))
+            assert rel <= 1e-3, (n, rel)
+            lat_compare(la, o.lat, fine)
+            checks += 1
+    assert checks == 8 and rebuilds >= 10 and len(set(lev.tolist())) >= 3
+    crossed = np.isfinite(o.lat) & ~initially
+    assert crossed.sum() >= 8, crossed.sum()
+    assert np.all(o.lat[crossed] > 0.0)
     g.close()
 
 

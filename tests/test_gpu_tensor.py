@@ -1,12 +1,15 @@
-"""GPU parity of the tensor-core (tcgen05, TF32) Q2 3D sweep.
+"""GPU parity of the tensor-core (tcgen05) Q2 3D FP32 sweep.
 
 The tensor-core sweep computes the SIPG residual of elements whose faces all have
-same-level neighbours as one TF32 product per tile of 128 due elements (operator split
-into TF32 hi and lo parts, values shifted by the element mean); other faces are added on
-the CUDA cores.  It is compared with the FP64 oracle (relative M-weighted L2 error of V at
-most 1e-3, as every FP32 result) and with the CUDA-core FP32 sweep on the same inputs, on
+same-level neighbours as one tensor-core product per tile of 64 due elements: the gathered
+element and face-neighbour values, shifted by the element mean and split into two FP16
+terms, times the level-0 operator, also split into two FP16 terms, with FP32 accumulation
+in tensor memory; other faces are added on the CUDA cores.  It is compared with the FP64
+oracle (relative M-weighted L2 error of V at most 1e-3, as every FP32 result; activation
+times within one finest substep) and with the CUDA-core FP32 sweep on the same inputs, on
 meshes that span several tiles with a ragged last tile, with hanging faces, boundary faces,
-multi-level LTS with time interpolation, and an anisotropic fibre direction.
+multi-level LTS with time interpolation, an anisotropic fibre direction, and with the
+persistent blocks capped so that each block walks many tiles.
 """
 import numpy as np
 import pytest
@@ -36,7 +39,7 @@ def q2_problem(base, extent, fibre, sigma=(1.2, 0.3), max_refine=2, n_lts=3, sti
                      stimuli=[W.Stimulus((0, 0, 0), stim_hi, 1.0, 0.0, 1.0)])
 
 
-def run_pair(mdl, prob, forest, nbar, origin=(0, 0, 0), radius=0.15, width=0.02):
+def run_pair(mdl, prob, forest, nbar, origin=(0, 0, 0), radius=0.15, width=0.02, blocks=0):
     """Oracle, CUDA-core FP32 sweep and tensor-core sweep over nbar barriers (levels from
     the oracle's own indicators each barrier, mesh fixed)."""
     o = lts.Sim(prob, forest=forest)
@@ -51,6 +54,8 @@ def run_pair(mdl, prob, forest, nbar, origin=(0, 0, 0), radius=0.15, width=0.02)
         g.upload_mesh(lv, cc, root)
         g.set_initial(V0, v0)
         g.set_sweep_variant(variant)
+        if variant == mdl.SWEEP_TENSOR and blocks:
+            g.set_sweep_blocks(blocks)
         sims.append(g)
     levels = []
     for _ in range(nbar):
@@ -86,6 +91,12 @@ def check(o, gt, gx, levels, tol_pair=1e-4):
     assert np.abs(st - o.v).max() <= 1e-3 * max(np.abs(o.v).max(), 1e-3)
     # the FP32 CUDA-core sweep itself reaches ~4e-3 on the refined patch
     assert err_x <= max(2e-3, 2.0 * err_t), (err_x, err_t)
+    # activation times: the same activated probes, times within one finest substep
+    la, lo = gx.read_activation(), o.lat
+    fa, fo = np.isfinite(la), np.isfinite(lo)
+    assert np.array_equal(fa, fo), (fa.sum(), fo.sum())
+    if fa.any():
+        assert np.abs(la[fa] - lo[fa]).max() <= o.dt / 2 ** (o.prob.n_lts_levels - 1)
 
 
 def test_tensor_uniform_mesh_two_tiles(mdl):
@@ -126,6 +137,26 @@ def test_tensor_many_tiles_refined_patch(mdl):
     f, _ = f.adapt(eta, 0.5, -1.0)
     assert f.n > 3 * 128
     o, gt, gx, levels = run_pair(mdl, prob, f, 4, origin=(5 * h, 0, 0), radius=2 * h, width=h)
+    check(o, gt, gx, levels)
+    gt.close(); gx.close()
+
+
+@pytest.mark.parametrize("blocks", [1, 3])
+def test_tensor_few_blocks_walk_many_tiles(mdl, blocks):
+    """The refined patch with the persistent sweep capped at `blocks` thread blocks, so that
+    every block walks many tiles of 64 due elements back to back (metadata and operands of
+    the next tile staged while the current one is computed): V, v, eta^t and activation
+    times against the oracle, 6 barrier steps with levels from the oracle's indicators."""
+    base = (10, 8, 4)
+    h = 2.0 / 128
+    prob = q2_problem(base, (base[0] * h, base[1] * h, base[2] * h), (1.0, 0.0, 0.0), max_refine=1, n_lts=3)
+    f = Forest(3, base, 1, prob.extent)
+    eta = np.zeros(f.n)
+    X = np.array([[(lf[1][k] + 0.5) * h for k in range(3)] for lf in f.leaves])
+    eta[(X[:, 0] > 3 * h) & (X[:, 0] < 7 * h)] = 1.0
+    f, _ = f.adapt(eta, 0.5, -1.0)
+    assert f.n >= 12 * 64
+    o, gt, gx, levels = run_pair(mdl, prob, f, 6, origin=(5 * h, 0, 0), radius=2 * h, width=h, blocks=blocks)
     check(o, gt, gx, levels)
     gt.close(); gx.close()
 
