@@ -227,6 +227,13 @@ int mdl_set_tick_shape(mdl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
 #define MDL_SWEEP_TENSOR 3
 int mdl_set_sweep_variant(mdl_ctx* ctx, int32_t variant);
 
+/* Upper bound on the number of thread blocks of the persistent tensor-core sweep
+ * (MDL_SWEEP_TENSOR); 0 restores the library's default (one block per SM).  Results do
+ * not depend on it: with a small bound every block walks many tiles of due elements, which
+ * is how the tests exercise the kernel's tile-to-tile pipeline on meshes the FP64 oracle
+ * can still run.  MDL_E_ARG if max_blocks < 0. */
+int mdl_set_sweep_blocks(mdl_ctx* ctx, int32_t max_blocks);
+
 /* ---- Batches: many resident simulations stepped together on one GPU ----
  * (The paper runs one simulation at a time on one CPU core, Sec. 3; batching many
  * resident simulations is this library's addition.)

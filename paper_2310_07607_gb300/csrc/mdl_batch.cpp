@@ -320,4 +320,11 @@ int mdl_set_sweep_variant(mdl_ctx* ctx, int32_t variant) {
     return rc;
 }
 
+int mdl_set_sweep_blocks(mdl_ctx* ctx, int32_t max_blocks) {
+    if (!ctx || !ctx->impl) return MDL_E_ARG;
+    const int rc = ctx->impl->set_sweep_blocks(max_blocks);
+    if (rc) ctx->err = ctx->impl->err;
+    return rc;
+}
+
 }  // extern "C"

@@ -38,6 +38,8 @@ public:
     // do not depend on it.  Returns MDL_E_ARG for unsupported shapes.
     virtual int set_tick_shape(int threads, int blocks_per_sm) = 0;
     virtual int set_sweep_variant(int variant) = 0;
+    // Upper bound on the blocks of the persistent tensor-core sweep (0: the default).
+    virtual int set_sweep_blocks(int max_blocks) = 0;
     virtual int64_t device_bytes() const = 0;     // device memory held by the context
     virtual double dt_barrier() const = 0;
     std::string err;

@@ -153,6 +153,7 @@ class Ctx : public CtxBase {
     bool coop_sweep = false;                  // ticks + epilogue in one cooperative launch
     bool group_tick = false;                  // Q1: a group of (p+1)^d lanes per element
     bool tensor_tick = false;                 // Q2 3D FP32: element residual on the tensor cores
+    int sweep_blocks = 0;                     // bound on the tensor sweep's blocks (0: default)
     bool pdl = true;                          // programmatic dependent launch between kernels
     int64_t inflight = 0, inflight_start = 0; // barriers launched by begin_barriers
 
@@ -473,9 +474,10 @@ class Ctx : public CtxBase {
             if constexpr (tensor_capable) {
                 if (tensor_tick) {
                     // persistent: two CTAs per SM walk the tiles of 64 due elements
+                    const int nblk = sweep_blocks > 0 ? std::min(sweep_blocks, 2 * nsm) : 2 * nsm;
                     for (int i = 0; i < nt; ++i) {
                         ta.tick = i;
-                        MDL_CK(launch_kxs(pdl && i > 0, (size_t)tc::SMEM_BYTES, (k_tick_tc<DIM, P>), 2 * nsm, tc::THREADS,
+                        MDL_CK(launch_kxs(pdl && i > 0, (size_t)tc::SMEM_BYTES, (k_tick_tc<DIM, P>), nblk, tc::THREADS,
                                           ta, T, ph, (const uint16_t*)tcB.p, tc_unscale, (const float*)tcC.p));
                         MDL_LAUNCHED();
                         stats.tick_launches++;
@@ -928,6 +930,18 @@ public:
             coop_sweep = co;
             group_tick = gr;
             tensor_tick = tn;
+            drop_graphs();
+        }
+        return MDL_OK;
+    }
+
+    int set_sweep_blocks(int max_blocks) override {
+        if (max_blocks < 0) {
+            err = "set_sweep_blocks: max_blocks must be >= 0";
+            return MDL_E_ARG;
+        }
+        if (max_blocks != sweep_blocks) {
+            sweep_blocks = max_blocks;
             drop_graphs();
         }
         return MDL_OK;

@@ -70,7 +70,7 @@ EXPORTS = [
     "mdl_read_state", "mdl_read_activation", "mdl_read_mesh", "mdl_read_faces",
     "mdl_read_indicators", "mdl_get_stats", "mdl_reset_stats", "mdl_set_timing",
     "mdl_device_view", "mdl_last_error", "mdl_destroy", "mdl_version", "mdl_integral_noalloc",
-    "mdl_noalloc_last_error", "mdl_set_tick_shape", "mdl_set_sweep_variant", "mdl_batch_create", "mdl_batch_footprint",
+    "mdl_noalloc_last_error", "mdl_set_tick_shape", "mdl_set_sweep_variant", "mdl_set_sweep_blocks", "mdl_batch_create", "mdl_batch_footprint",
     "mdl_batch_admit", "mdl_batch_step", "mdl_batch_poll", "mdl_batch_slot", "mdl_batch_release",
     "mdl_batch_usage", "mdl_batch_shape", "mdl_batch_last_error", "mdl_batch_destroy",
     "mdl_set_initial_f32", "mdl_read_fields_f32",
@@ -124,6 +124,7 @@ def load(path: Optional[str] = None):
     i32p = C.POINTER(C.c_int32)
     lib.mdl_set_tick_shape.argtypes = [vp, C.c_int32, C.c_int32]
     lib.mdl_set_sweep_variant.argtypes = [vp, C.c_int32]
+    lib.mdl_set_sweep_blocks.argtypes = [vp, C.c_int32]
     lib.mdl_batch_create.argtypes = [i64, i32, C.POINTER(vp)]
     lib.mdl_batch_footprint.argtypes = [C.POINTER(CProblem), C.POINTER(i64)]
     lib.mdl_batch_admit.argtypes = [vp, C.POINTER(CProblem), vp, vp, i64, C.c_double, i32p]
@@ -217,6 +218,10 @@ class Sim:
     def set_sweep_variant(self, variant: int):
         """SWEEP_THREAD (the default), SWEEP_GROUP (Q1), SWEEP_COOP or SWEEP_TENSOR (Q2 3D FP32)."""
         self._check(self.lib.mdl_set_sweep_variant(self.h, variant))
+
+    def set_sweep_blocks(self, max_blocks: int):
+        """Upper bound on the persistent tensor-core sweep's blocks (0: one per SM)."""
+        self._check(self.lib.mdl_set_sweep_blocks(self.h, max_blocks))
 
     def __del__(self):
         try:
