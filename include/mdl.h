@@ -187,9 +187,11 @@ int mdl_reset_stats(mdl_ctx* ctx);
 int mdl_set_timing(mdl_ctx* ctx, int on);
 
 /* Device pointer to a resident array (valid until the next mutating call) and
- * the context's CUDA stream.  which: 0 V (current values are in slot 0 after
- * every barrier), 1 state, 2 activation times, 3 eta_t.  *n = element count of
- * the array. */
+ * the context's CUDA stream.  which: 0 V (the current values, normalised into slot 0),
+ * 1 state, 2 activation times, 3 eta_t.  *n = element count of the array.  V and the
+ * state are in the working precision and leaf/DOF order, (p+1)^d values per element;
+ * Q2 3D contexts store their rows padded to 28 values, so for them the view is a compact
+ * copy made by this call. */
 int mdl_device_view(mdl_ctx* ctx, int which, void** dptr, int64_t* n, void** stream);
 
 const char* mdl_last_error(const mdl_ctx* ctx);
@@ -211,15 +213,16 @@ int mdl_set_tick_shape(mdl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
  *                     one launch per tick (Q2 contexts use MDL_SWEEP_THREAD);
  *   MDL_SWEEP_COOP    every tick and the barrier epilogue in one cooperative launch with
  *                     grid-wide barriers between ticks;
- *   MDL_SWEEP_TENSOR  Q2 3D FP32 contexts only: per tile of 128 due elements the SIPG
- *                     residual of elements with same-level neighbours is one TF32
- *                     tensor-core product (tcgen05) of the gathered element and face-
- *                     neighbour values with the level-0 operator (Sec. 2.1: box elements,
- *                     so every level is a power-of-two multiple of it), on values shifted
- *                     by the element mean and with the operator split into TF32 hi and lo
- *                     parts; other faces are added on the CUDA cores.  Agrees with THREAD
- *                     within the FP32 tolerance, not bit for bit.  A bounded device wait
- *                     that gives up makes the stepping call return MDL_E_TIMEOUT.
+ *   MDL_SWEEP_TENSOR  Q2 3D FP32 contexts only (their default): per tile of 64 due
+ *                     elements the SIPG residual of elements with same-level neighbours is
+ *                     one tcgen05 tensor-core product of the gathered element and face-
+ *                     neighbour values with the level-0 operator (Sec. 2.1: box elements, so
+ *                     every level is a power-of-two multiple of it), on values shifted by the
+ *                     element mean, with both operands split into two FP16 terms and FP32
+ *                     accumulation in tensor memory; other faces are added on the CUDA cores.
+ *                     Two persistent blocks per SM walk the tiles.  Agrees with
+ *                     THREAD within the FP32 tolerance, not bit for bit.  A bounded device
+ *                     wait that gives up makes the stepping call return MDL_E_TIMEOUT.
  * Returns MDL_E_ARG for any other value, or for TENSOR on another kind of context. */
 #define MDL_SWEEP_THREAD 0
 #define MDL_SWEEP_GROUP 1
@@ -228,7 +231,7 @@ int mdl_set_tick_shape(mdl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
 int mdl_set_sweep_variant(mdl_ctx* ctx, int32_t variant);
 
 /* Upper bound on the number of thread blocks of the persistent tensor-core sweep
- * (MDL_SWEEP_TENSOR); 0 restores the library's default (one block per SM).  Results do
+ * (MDL_SWEEP_TENSOR); 0 restores the library's default (two blocks per SM).  Results do
  * not depend on it: with a small bound every block walks many tiles of due elements, which
  * is how the tests exercise the kernel's tile-to-tile pipeline on meshes the FP64 oracle
  * can still run.  MDL_E_ARG if max_blocks < 0. */

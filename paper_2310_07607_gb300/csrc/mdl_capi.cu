@@ -71,7 +71,8 @@ CtxBase* make_ctx(const mdl_problem& pr) {
 // (twice the roots, or four times with adaptation), the finest owner map and the probes.
 int64_t estimate_footprint(const mdl_problem& p) {
     const int d = p.dim, n1 = p.order + 1;
-    const int64_t np = d == 2 ? n1 * n1 : n1 * n1 * n1;
+    const int64_t np0 = d == 2 ? n1 * n1 : n1 * n1 * n1;
+    const int64_t np = np0 == 27 ? 28 : np0;   // row stride of the per-DOF arrays (Q2 3D padded)
     const int64_t nf = 2 * d, nsub = 1 << (d - 1);
     int64_t roots = 1, fine = 1;
     for (int k = 0; k < d; ++k) {
@@ -83,7 +84,7 @@ int64_t estimate_footprint(const mdl_problem& p) {
     const int64_t per_set = 3 * np * r + 8 + 1 + 16;
     const int64_t shared = 2 * np * r + 8 + 8 + 1 + 1 + 8 + 1 + 1 + 4 + 4;
     const int64_t tables = 1 + 4 + 4 + 4 * nf + 4 * nf * nsub + 4 + 4 + 4 * p.n_stim;
-    return cap * (2 * per_set + shared + tables) + fine * 4 + roots * np * 8 + (1 << 20);
+    return cap * (2 * per_set + shared + tables) + fine * 4 + roots * np0 * 8 + (1 << 20);
 }
 
 }  // namespace mdl

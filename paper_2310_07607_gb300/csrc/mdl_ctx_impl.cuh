@@ -83,7 +83,7 @@ __global__ void k_fill_inf(double* p, int64_t n);
 template <typename R, int DIM, int P>
 class Ctx : public CtxBase {
     using S = Shape<DIM, P>;
-    static constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB, NC = 1 << DIM;
+    static constexpr int N1 = S::N1, NP = S::NP, NF = S::NF, NSUB = S::NSUB, NC = 1 << DIM, NPS = S::NPS;
 
     // State of one mesh (double-buffered across an adaptation).
     struct Set {
@@ -117,6 +117,7 @@ class Ctx : public CtxBase {
     DBuf<R> Ia, ga;
     DBuf<double> acc, eta_s, lat, partial, scratch;
     DBuf<float> fscratch;   // FP32 field transfers
+    DBuf<R> cview;          // compact copy handed out by device_view for padded rows
     DBuf<uint8_t> r, c0, class_b;
     DBuf<int32_t> owner, bcnt, psrc;
     DBuf<int64_t> bsum;
@@ -212,9 +213,9 @@ class Ctx : public CtxBase {
     // ------------------------------------------------------------------
     // Allocation.  Growing keeps the current set's contents.
     int alloc_set(Set& x, int64_t c) {
-        MDL_CK(x.V0.ensure((size_t)c * NP));
-        MDL_CK(x.V1.ensure((size_t)c * NP));
-        MDL_CK(x.v.ensure((size_t)c * NP));
+        MDL_CK(x.V0.ensure((size_t)c * NPS));
+        MDL_CK(x.V1.ensure((size_t)c * NPS));
+        MDL_CK(x.v.ensure((size_t)c * NPS));
         MDL_CK(x.eta_t.ensure(c));
         MDL_CK(x.lvl.ensure(c));
         MDL_CK(x.coord.ensure(c));
@@ -234,8 +235,8 @@ class Ctx : public CtxBase {
     }
 
     int alloc_shared(int64_t c) {
-        MDL_CK(Ia.ensure((size_t)c * NP));
-        MDL_CK(ga.ensure((size_t)c * NP));
+        MDL_CK(Ia.ensure((size_t)c * NPS));
+        MDL_CK(ga.ensure((size_t)c * NPS));
         MDL_CK(acc.ensure(c));
         MDL_CK(eta_s.ensure(c));
         MDL_CK(r.ensure(c));
@@ -268,7 +269,7 @@ class Ctx : public CtxBase {
         Set& x = sets[cs];
         int rc;
 #define MDL_GROW(buf, per) if ((rc = grow_copy(buf, (size_t)c * (per), (size_t)ne * (per)))) return rc
-        MDL_GROW(x.V0, NP); MDL_GROW(x.V1, NP); MDL_GROW(x.v, NP); MDL_GROW(x.eta_t, 1);
+        MDL_GROW(x.V0, NPS); MDL_GROW(x.V1, NPS); MDL_GROW(x.v, NPS); MDL_GROW(x.eta_t, 1);
         MDL_GROW(x.lvl, 1); MDL_GROW(x.coord, 1);
         MDL_GROW(bcfl, 1); MDL_GROW(info, 1); MDL_GROW(loc, 1); MDL_GROW(nbr, NF); MDL_GROW(hang, NF * NSUB);
         MDL_GROW(root, 1); MDL_GROW(order, 1);
@@ -347,9 +348,9 @@ class Ctx : public CtxBase {
         int rc = build_tables(cs, 1);
         if (rc) return rc;
         ne = n;
-        MDL_CK(cudaMemsetAsync(x.V0.p, 0, (size_t)n * NP * sizeof(R), st));
-        MDL_CK(cudaMemsetAsync(x.V1.p, 0, (size_t)n * NP * sizeof(R), st));
-        MDL_CK(cudaMemsetAsync(x.v.p, 0, (size_t)n * NP * sizeof(R), st));
+        MDL_CK(cudaMemsetAsync(x.V0.p, 0, (size_t)n * NPS * sizeof(R), st));
+        MDL_CK(cudaMemsetAsync(x.V1.p, 0, (size_t)n * NPS * sizeof(R), st));
+        MDL_CK(cudaMemsetAsync(x.v.p, 0, (size_t)n * NPS * sizeof(R), st));
         MDL_CK(cudaMemsetAsync(x.eta_t.p, 0, n * sizeof(double), st));
         MDL_CK(cudaMemsetAsync(x.lvl.p, 0, n, st));
         MDL_CK(cudaMemsetAsync(eta_s.p, 0, n * sizeof(double), st));
@@ -473,7 +474,7 @@ class Ctx : public CtxBase {
                                                   (int64_t)nsm * tick_bpsm);
             if constexpr (tensor_capable) {
                 if (tensor_tick) {
-                    // persistent: two CTAs per SM walk the tiles of 64 due elements
+                    // persistent: two blocks per SM walk the tiles of 64 due elements
                     const int nblk = sweep_blocks > 0 ? std::min(sweep_blocks, 2 * nsm) : 2 * nsm;
                     for (int i = 0; i < nt; ++i) {
                         ta.tick = i;
@@ -589,7 +590,7 @@ public:
         drop_graphs();
         for (auto& s : sets) s.release();
         Ia.release(); ga.release(); acc.release(); eta_s.release(); lat.release(); partial.release();
-        scratch.release(); fscratch.release(); r.release(); c0.release(); class_b.release(); owner.release();
+        scratch.release(); fscratch.release(); cview.release(); r.release(); c0.release(); class_b.release(); owner.release();
         bcnt.release(); psrc.release(); bsum.release(); pkind.release(); pbits.release();
         bcfl.release(); info.release(); loc.release(); nbr.release(); hang.release(); root.release();
         order.release();
@@ -742,8 +743,8 @@ public:
         MDL_CK(scratch.ensure((size_t)2 * n_dof));
         MDL_CK(cudaMemcpyAsync(scratch.p, V, n_dof * 8, cudaMemcpyHostToDevice, st));
         if (s) MDL_CK(cudaMemcpyAsync(scratch.p + n_dof, s, n_dof * 8, cudaMemcpyHostToDevice, st));
-        k_scatter_initial<R, NP, double><<<div_up(n_dof, 256), 256, 0, st>>>(arrays(cs), ne, scratch.p,
-                                                                     s ? scratch.p + n_dof : nullptr);
+        k_scatter_initial<R, NP, NPS, double><<<div_up(ne * NPS, 256), 256, 0, st>>>(
+            arrays(cs), ne, scratch.p, s ? scratch.p + n_dof : nullptr);
         MDL_LAUNCHED();
         MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
         k_lat_refresh<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(arrays(cs), T, ph, (double)nbar * dt, 1, 1);
@@ -957,6 +958,7 @@ public:
         add(Ia.cap + ga.cap, sizeof(R));
         add(acc.cap + eta_s.cap + lat.cap + partial.cap + scratch.cap + eta_t_ovr.cap + mtab.cap, 8);
         add(fscratch.cap, 4);
+        add(cview.cap, sizeof(R));
         add(r.cap + c0.cap + class_b.cap + bcfl.cap + pkind.cap + pbits.cap + lvl_ovr.cap, 1);
         add(owner.cap + bcnt.cap + psrc.cap + nbr.cap + hang.cap + root.cap + order.cap + info.cap + loc.cap, 4);
         for (const auto& m : smask) add(m.cap, 4);
@@ -994,7 +996,7 @@ public:
             return MDL_E_ARG;
         }
         MDL_CK(scratch.ensure(2 * nd));
-        k_gather<R, NP><<<div_up(nd, 256), 256, 0, st>>>(arrays(cs), ne, which, scratch.p);
+        k_gather<R, NP, NPS, double><<<div_up(nd, 256), 256, 0, st>>>(arrays(cs), ne, which, scratch.p);
         MDL_LAUNCHED();
         MDL_CK(cudaMemcpyAsync(out, scratch.p, nd * 8, cudaMemcpyDeviceToHost, st));
         MDL_CK(cudaStreamSynchronize(st));
@@ -1009,8 +1011,8 @@ public:
         MDL_CK(fscratch.ensure((size_t)2 * n_dof));
         MDL_CK(cudaMemcpyAsync(fscratch.p, V, n_dof * sizeof(float), cudaMemcpyHostToDevice, st));
         if (s) MDL_CK(cudaMemcpyAsync(fscratch.p + n_dof, s, n_dof * sizeof(float), cudaMemcpyHostToDevice, st));
-        k_scatter_initial<R, NP, float><<<div_up(n_dof, 256), 256, 0, st>>>(arrays(cs), ne, fscratch.p,
-                                                                            s ? fscratch.p + n_dof : nullptr);
+        k_scatter_initial<R, NP, NPS, float><<<div_up(ne * NPS, 256), 256, 0, st>>>(
+            arrays(cs), ne, fscratch.p, s ? fscratch.p + n_dof : nullptr);
         MDL_LAUNCHED();
         MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
         k_lat_refresh<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(arrays(cs), T, ph, (double)nbar * dt, 1, 1);
@@ -1027,7 +1029,7 @@ public:
             return MDL_E_ARG;
         }
         MDL_CK(fscratch.ensure((size_t)2 * nd));
-        k_gather_f32<R, NP><<<div_up(nd, 256), 256, 0, st>>>(arrays(cs), ne, fscratch.p);
+        k_gather_f32<R, NP, NPS><<<div_up(nd, 256), 256, 0, st>>>(arrays(cs), ne, fscratch.p);
         MDL_LAUNCHED();
         if (V) MDL_CK(cudaMemcpyAsync(V, fscratch.p, nd * sizeof(float), cudaMemcpyDeviceToHost, st));
         if (s) MDL_CK(cudaMemcpyAsync(s, fscratch.p + nd, nd * sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -1139,14 +1141,31 @@ public:
                 if (rc) return rc;
                 MDL_CK(scratch.ensure(2 * ne * NP));
                 MDL_CK(cudaMemcpyAsync(scratch.p, tmp.data(), ne * NP * 8, cudaMemcpyHostToDevice, st));
-                k_scatter_initial<R, NP, double><<<div_up(ne * NP, 256), 256, 0, st>>>(arrays(cs), ne, scratch.p, (const double*)nullptr);
+                k_scatter_initial<R, NP, NPS, double><<<div_up(ne * NPS, 256), 256, 0, st>>>(
+                    arrays(cs), ne, scratch.p, (const double*)nullptr);
                 MDL_LAUNCHED();
+                if (NPS != NP) {
+                    // padded rows: hand out a compact copy ((p+1)^d values per element)
+                    MDL_CK(cview.ensure((size_t)ne * NP));
+                    k_gather<R, NP, NPS, R><<<div_up(ne * NP, 256), 256, 0, st>>>(arrays(cs), ne, 0, cview.p);
+                    MDL_LAUNCHED();
+                }
                 MDL_CK(cudaStreamSynchronize(st));
-                if (p) *p = sets[cs].V0.p;
+                if (p) *p = NPS != NP ? (void*)cview.p : (void*)sets[cs].V0.p;
                 if (n) *n = ne * NP;
                 return MDL_OK;
             }
-            case 1: if (p) *p = sets[cs].v.p; if (n) *n = ne * NP; return MDL_OK;
+            case 1: {
+                if (NPS != NP) {
+                    MDL_CK(cview.ensure((size_t)ne * NP));
+                    k_gather<R, NP, NPS, R><<<div_up(ne * NP, 256), 256, 0, st>>>(arrays(cs), ne, 1, cview.p);
+                    MDL_LAUNCHED();
+                    MDL_CK(cudaStreamSynchronize(st));
+                }
+                if (p) *p = NPS != NP ? (void*)cview.p : (void*)sets[cs].v.p;
+                if (n) *n = ne * NP;
+                return MDL_OK;
+            }
             case 2: if (p) *p = lat.p; if (n) *n = n_probe; return MDL_OK;
             case 3: if (p) *p = sets[cs].eta_t.p; if (n) *n = ne; return MDL_OK;
             default: err = "device_view: unknown array"; return MDL_E_ARG;

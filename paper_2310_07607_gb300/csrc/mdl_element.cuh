@@ -43,6 +43,10 @@ struct Shape {
     static constexpr int NF = 2 * DIM;               // faces
     static constexpr int NT = ipow(N1, DIM - 1);     // points per (sub)face
     static constexpr int NSUB = 1 << (DIM - 1);      // subfaces of a hanging face
+    // Row stride of the per-DOF state arrays (V slots, v, Ia, ga) in device memory: the DOF
+    // count, except Q2 3D, whose 27 values are padded to 28 so that every element row starts
+    // on a 16-byte boundary (vector loads, bulk copies of whole rows).  The pad is kept 0.
+    static constexpr int NPS = (DIM == 3 && P == 2) ? 28 : NP;
 };
 
 // 1D tables of the (P+1)-point Gauss-Legendre Lagrange basis (P <= 2), filled on the host.

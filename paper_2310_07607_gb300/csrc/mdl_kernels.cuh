@@ -1,11 +1,12 @@
 // mdl_kernels.cuh -- CUDA kernels of one barrier step (Alg. 1) for one (precision, dim, order).
 //
 // Data layout in HBM (structure of arrays, element-blocked DOFs):
-//   V0, V1  [ne * NP]  two slots of V; element e's current value is in slot
+//   V0, V1  [ne * NPS] two slots of V; element e's current value is in slot
 //                      par_e ^ (updates this barrier & 1) -- a per-element ping-pong,
 //                      so a tick reads the values at its start and writes the other slot
-//   v       [ne * NP]  Aliev-Panfilov recovery variable (element-local, in place)
-//   Ia, ga  [ne * NP]  I(u_a, t_a) and g(u_a) at the barrier start (only for S_e > 1)
+//   v       [ne * NPS] Aliev-Panfilov recovery variable (element-local, in place)
+//   Ia, ga  [ne * NPS] I(u_a, t_a) and g(u_a) at the barrier start (only for S_e > 1)
+//                      (NPS: the row stride, NP rounded up to 28 for Q2 3D; pad value 0)
 //   lvl     [ne]       b_e (bits 0-2) | parity par_e (bit 3)
 //   info    [ne]       4 bits per face: kind (0 bnd, 1 same, 2 coarser, 3 finer) | pos << 2;
 //                      bits 24-27 refinement level; bit 28 in a stimulus box; bit 29 probes pending
@@ -153,6 +154,33 @@ __device__ __forceinline__ void st_vec(R* p, const R* x) {
     }
 }
 
+// One element row of a per-DOF state array: NP values at row stride NPS.  With NPS a whole
+// number of 16-byte vectors the row moves in vectors (the pad value read is dropped; a
+// store writes the pad as 0), else value by value.
+template <typename R, int NP, int NPS>
+__device__ __forceinline__ void ld_dofs(const R* p, R* out) {
+    if constexpr (NPS == NP) {
+        ld_vec<R, NP>(p, out);
+    } else {
+        R t[NPS];
+        ld_vec<R, NPS>(p, t);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) out[q] = t[q];
+    }
+}
+
+template <typename R, int NP, int NPS>
+__device__ __forceinline__ void st_dofs(R* p, const R* x) {
+    if constexpr (NPS == NP) {
+        st_vec<R, NP>(p, x);
+    } else {
+        R t[NPS];
+#pragma unroll
+        for (int q = 0; q < NPS; ++q) t[q] = q < NP ? x[q] : R(0);
+        st_vec<R, NPS>(p, t);
+    }
+}
+
 // j[t] += sum_q K[t][q] x[q] for a row-major NT x NP block (read-only path).
 template <typename R, int NT, int NP>
 __device__ __forceinline__ void block_jump(const R* __restrict__ K, const R* x, R* j) {
@@ -256,26 +284,26 @@ __device__ __forceinline__ R ap_step_state(const Phys<R>& ph, R V, R w, R dt) {
 
 // Values of element nb as seen at tick `tick`, given its level byte: its current value if
 // it is due (or finer), else the linear time interpolant of its last step (Alg. 1).
-template <typename R, int NP>
+template <typename R, int NP, int NPS = NP>
 __device__ __forceinline__ void load_seen_lv(const DevArrays<R>& d, int tick, int B, int nb, uint8_t lv, R* un) {
     const int b = lv & 7, par = (lv >> 3) & 1;
     const int sh = B - b;
     const int j = tick >> sh;
     const int rem = tick & ((1 << sh) - 1);
     const int nw = par ^ ((j + (rem ? 1 : 0)) & 1);
-    ld_vec<R, NP>((nw ? d.V1 : d.V0) + (size_t)nb * NP, un);
+    ld_dofs<R, NP, NPS>((nw ? d.V1 : d.V0) + (size_t)nb * NPS, un);
     if (rem) {
         R so[NP];
-        ld_vec<R, NP>((nw ? d.V0 : d.V1) + (size_t)nb * NP, so);
+        ld_dofs<R, NP, NPS>((nw ? d.V0 : d.V1) + (size_t)nb * NPS, so);
         const R th = R(rem) * pow2_neg<R>(sh);
 #pragma unroll
         for (int q = 0; q < NP; ++q) un[q] = so[q] + th * (un[q] - so[q]);
     }
 }
 
-template <typename R, int NP>
+template <typename R, int NP, int NPS = NP>
 __device__ __forceinline__ void load_seen(const DevArrays<R>& d, int tick, int B, int nb, R* un) {
-    load_seen_lv<R, NP>(d, tick, B, nb, d.lvl[nb], un);
+    load_seen_lv<R, NP, NPS>(d, tick, B, nb, d.lvl[nb], un);
 }
 
 // Residual r = (A u)_e with the neighbours seen at tick `tick`.  All same-level and
@@ -287,7 +315,7 @@ __device__ __forceinline__ void element_residual(const DevArrays<R>& d, const Ta
                                                  const Phys<R>& ph, int tick, int B, int e,
                                                  uint32_t inf, int lev, const R* u, R* r) {
     using S = Shape<DIM, P>;
-    constexpr int NP = S::NP, NF = S::NF, NSUB = S::NSUB;
+    constexpr int NP = S::NP, NF = S::NF, NSUB = S::NSUB, NPS = S::NPS;
 #pragma unroll
     for (int q = 0; q < NP; ++q) r[q] = R(0);
     if constexpr (P > 1) {
@@ -301,14 +329,14 @@ __device__ __forceinline__ void element_residual(const DevArrays<R>& d, const Ta
             const int nbi = d.nbr[(size_t)e * NF + f];
             if (kind != 3) {
                 R un[NP];
-                load_seen<R, NP>(d, tick, B, nbi, un);
+                load_seen<R, NP, NPS>(d, tick, B, nbi, un);
                 const int pos = (inf >> (4 * f + 2)) & 3;
                 face_term<R, DIM, P>(T, ph, k, s, lev, -1, u, kind == 1 ? lev : lev - 1,
                                      kind == 1 ? -1 : pos, un, lev, r);
             } else {
                 for (int sb = 0; sb < NSUB; ++sb) {
                     R un[NP];
-                    load_seen<R, NP>(d, tick, B, d.hang[nbi + sb], un);
+                    load_seen<R, NP, NPS>(d, tick, B, d.hang[nbi + sb], un);
                     face_term<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1, r);
                 }
             }
@@ -712,18 +740,19 @@ __device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>&
     const int ke = tick >> (a.B - b);
     const int cur = par ^ (ke & 1);
     const int lev = (inf >> 24) & 15;
-    const R* Vc = (cur ? d.V1 : d.V0) + (size_t)e * NP;
-    R* Vd = (cur ? d.V0 : d.V1) + (size_t)e * NP;
-    R* vp = d.v + (size_t)e * NP;
+    constexpr int NPS = S::NPS;
+    const R* Vc = (cur ? d.V1 : d.V0) + (size_t)e * NPS;
+    R* Vd = (cur ? d.V0 : d.V1) + (size_t)e * NPS;
+    R* vp = d.v + (size_t)e * NPS;
     // every value this step needs is addressed by now: issue the loads together
     R u[NP], w[NP], r[NP], Ia[NP], ga[NP];
-    ld_vec<R, NP>(Vc, u);
-    ld_vec<R, NP>(vp, w);
+    ld_dofs<R, NP, NPS>(Vc, u);
+    ld_dofs<R, NP, NPS>(vp, w);
     double acc0 = 0.0;
     if constexpr (P == 1) {
         if (ke != 0) {
-            ld_vec<R, NP>(d.Ia + (size_t)e * NP, Ia);
-            ld_vec<R, NP>(d.ga + (size_t)e * NP, ga);
+            ld_dofs<R, NP, NPS>(d.Ia + (size_t)e * NPS, Ia);
+            ld_dofs<R, NP, NPS>(d.ga + (size_t)e * NPS, ga);
             acc0 = d.acc[e];
         }
         residual_q1<R, DIM>(d, tick, a.B, m, lev, u, r);
@@ -731,8 +760,8 @@ __device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>&
         // Q2: the barrier-start terms are loaded after the residual (register pressure)
         element_residual<R, DIM, P>(d, T, ph, tick, a.B, e, inf, lev, u, r);
         if (ke != 0) {
-            ld_vec<R, NP>(d.Ia + (size_t)e * NP, Ia);
-            ld_vec<R, NP>(d.ga + (size_t)e * NP, ga);
+            ld_dofs<R, NP, NPS>(d.Ia + (size_t)e * NPS, Ia);
+            ld_dofs<R, NP, NPS>(d.ga + (size_t)e * NPS, ga);
             acc0 = d.acc[e];
         }
     }
@@ -741,11 +770,11 @@ __device__ __forceinline__ void tick_elem(const TickArgs<R>& a, const Tables<R>&
     const R term = elem_pointwise<R, DIM, P>(a, T, ph, tick, e, inf, b, ke, lev, u, w, r, Ia, ga, un, wn, vmax);
     const double dte_d = a.dte[b];
     if (ke == 0 && b > 0) {
-        st_vec<R, NP>(d.Ia + (size_t)e * NP, Ia);
-        st_vec<R, NP>(d.ga + (size_t)e * NP, ga);
+        st_dofs<R, NP, NPS>(d.Ia + (size_t)e * NPS, Ia);
+        st_dofs<R, NP, NPS>(d.ga + (size_t)e * NPS, ga);
     }
-    st_vec<R, NP>(Vd, un);
-    st_vec<R, NP>(vp, wn);
+    st_dofs<R, NP, NPS>(Vd, un);
+    st_dofs<R, NP, NPS>(vp, wn);
     d.acc[e] = acc0 + dte_d * (double)term;
     if ((inf & INFO_PENDING) && vmax >= ph.lat_gate)
     {
@@ -798,16 +827,16 @@ template <typename R, int DIM, int P>
 __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> ph) {
     pdl_enter();
     using S = Shape<DIM, P>;
-    constexpr int NP = S::NP, NF = S::NF, NSUB = S::NSUB;
+    constexpr int NP = S::NP, NF = S::NF, NSUB = S::NSUB, NPS = S::NPS;
     if (d.meta->err) return;
     const int64_t ne = d.meta->ne;
     for (int64_t e = gtid(); e < ne; e += gstride()) {
         const uint32_t inf = d.info[e];
         const int lev = (inf >> 24) & 15;
         const int par = (d.lvl[e] >> 3) & 1;
-        const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
+        const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NPS;
         R u[NP];
-        ld_vec<R, NP>(Vc, u);
+        ld_dofs<R, NP, NPS>(Vc, u);
         // squared face jumps in the working precision, summed in FP64 (the indicator decides
         // refinement, so its reduction keeps FP64 as on the host)
         double acc = 0.0;
@@ -827,8 +856,8 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
             R un[NF][NP];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                const R* srcp = (((lvn[f] >> 3) & 1) ? d.V1 : d.V0) + (size_t)src[f] * NP;
-                ld_vec<R, NP>(srcp, un[f]);
+                const R* srcp = (((lvn[f] >> 3) & 1) ? d.V1 : d.V0) + (size_t)src[f] * NPS;
+                ld_dofs<R, NP, NPS>(srcp, un[f]);
             }
             constexpr int NT = S::NT, NREL = 1 + 2 * NSUB;
 #pragma unroll
@@ -860,10 +889,9 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
                 const int s = side ? 1 : -1;
                 const int nbi = d.nbr[(size_t)e * NF + f];
                 const int pn = (d.lvl[nbi] >> 3) & 1;
-                const R* src = (pn ? d.V1 : d.V0) + (size_t)nbi * NP;
+                const R* src = (pn ? d.V1 : d.V0) + (size_t)nbi * NPS;
                 R un[NP];
-#pragma unroll
-                for (int q = 0; q < NP; ++q) un[q] = src[q];
+                ld_dofs<R, NP, NPS>(src, un);
                 const int pos = (inf >> (4 * f + 2)) & 3;
                 if constexpr (sizeof(R) == 4)
                     acc += ph.kfac[lev][k] * (double)face_kelly_sum<R, DIM, P>(T, ph, k, s, lev, -1, u,
@@ -882,10 +910,9 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
                 for (int sb = 0; sb < NSUB; ++sb) {
                     const int nb = d.hang[nbf[f] + sb];
                     const int pn = (d.lvl[nb] >> 3) & 1;
-                    const R* src = (pn ? d.V1 : d.V0) + (size_t)nb * NP;
+                    const R* src = (pn ? d.V1 : d.V0) + (size_t)nb * NPS;
                     R un[NP];
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) un[q] = src[q];
+                    ld_dofs<R, NP, NPS>(src, un);
                     constexpr int NT = S::NT, NREL = 1 + 2 * NSUB;
                     const R* K = d.qkelly + ((((size_t)f * 8 + lev) * NREL + 1 + NSUB + sb) * 2) * NT * NP;
                     R j[NT];
@@ -912,10 +939,9 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
                 for (int sb = 0; sb < NSUB; ++sb) {
                     const int nb = d.hang[h0 + sb];
                     const int pn = (d.lvl[nb] >> 3) & 1;
-                    const R* src = (pn ? d.V1 : d.V0) + (size_t)nb * NP;
+                    const R* src = (pn ? d.V1 : d.V0) + (size_t)nb * NPS;
                     R un[NP];
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) un[q] = src[q];
+                    ld_dofs<R, NP, NPS>(src, un);
                     if constexpr (sizeof(R) == 4)
                         acc += ph.kfac[lev + 1][k] *
                                (double)face_kelly_sum<R, DIM, P>(T, ph, k, s, lev, sb, u, lev + 1, -1, un, lev + 1);
@@ -951,8 +977,8 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const do
             d.lvl[e] = lv;
         }
         const int par = (lv >> 3) & 1;
-        const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
-        const R* w = d.v + (size_t)e * NP;
+        const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * S::NPS;
+        const R* w = d.v + (size_t)e * S::NPS;
         const int lev = (d.info[e] >> 24) & 15;
         const double* Mq = mtab + lev * NP;
 #pragma unroll
@@ -1092,8 +1118,9 @@ __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const P
         const int lev = (inf >> 24) & 15;
         // every value this step needs: own row, neighbours as seen, state, barrier-start terms
         R u[NP];
-        ld_vec<R, NP>((cur ? d.V1 : d.V0) + (size_t)e * NP, u);
-        const R w = d.v[(size_t)e * NP + g];
+        constexpr int NPS = S::NPS;
+        ld_dofs<R, NP, NPS>((cur ? d.V1 : d.V0) + (size_t)e * NPS, u);
+        const R w = d.v[(size_t)e * NPS + g];
         R un[NF][NP];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
@@ -1103,8 +1130,8 @@ __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const P
         R Ia = R(0), ga = R(0);
         double acc0 = 0.0;
         if (ke != 0) {
-            Ia = d.Ia[(size_t)e * NP + g];
-            ga = d.ga[(size_t)e * NP + g];
+            Ia = d.Ia[(size_t)e * NPS + g];
+            ga = d.ga[(size_t)e * NPS + g];
             if (g == 0) acc0 = d.acc[e];
         }
         // row g of the residual
@@ -1161,11 +1188,11 @@ __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const P
             const R om = __shfl_xor_sync(gmask, vmax, o, G);
             vmax = om > vmax ? om : vmax;
         }
-        ((cur ? d.V0 : d.V1) + (size_t)e * NP)[g] = un_g;
-        d.v[(size_t)e * NP + g] = wn_g;
+        ((cur ? d.V0 : d.V1) + (size_t)e * NPS)[g] = un_g;
+        d.v[(size_t)e * NPS + g] = wn_g;
         if (ke == 0 && b > 0) {
-            d.Ia[(size_t)e * NP + g] = Ia;
-            d.ga[(size_t)e * NP + g] = ga;
+            d.Ia[(size_t)e * NPS + g] = Ia;
+            d.ga[(size_t)e * NPS + g] = ga;
         }
         if (g == 0) d.acc[e] = acc0 + dte_d * (double)term;
         if ((inf & INFO_PENDING) && vmax >= ph.lat_gate) {
@@ -1206,8 +1233,8 @@ __global__ void __launch_bounds__(256) k_sweep(const TickArgs<R> a, const Tables
             d.lvl[e] = lv;
         }
         const int par = (lv >> 3) & 1;
-        const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
-        const R* w = d.v + (size_t)e * NP;
+        const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * S::NPS;
+        const R* w = d.v + (size_t)e * S::NPS;
         const int lev = (d.info[e] >> 24) & 15;
         const double* Mq = mtab + lev * NP;
 #pragma unroll
@@ -1246,38 +1273,42 @@ __global__ void __launch_bounds__(256) k_sweep(const TickArgs<R> a, const Tables
     }
 }
 
-// Copy V (current slot by parity) or v to an FP64 output.
-template <typename R, int NP>
-__global__ void k_gather(const DevArrays<R> d, int64_t ne, int which, double* out) {
+// Copy V (current slot by parity) or v to a compact output (NP values per element).
+template <typename R, int NP, int NPS, typename Out>
+__global__ void k_gather(const DevArrays<R> d, int64_t ne, int which, Out* out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= ne * NP) return;
-    const int64_t e = i / NP;
+    const int64_t e = i / NP, j = e * NPS + (i - e * NP);
     if (which == 0) {
         const int par = (d.lvl[e] >> 3) & 1;
-        out[i] = (double)((par ? d.V1 : d.V0)[i]);
+        out[i] = (Out)((par ? d.V1 : d.V0)[j]);
     } else {
-        out[i] = (double)d.v[i];
+        out[i] = (Out)d.v[j];
     }
 }
 
-// V (current slot) and the state variable into one FP32 buffer [V | v].
-template <typename R, int NP>
+// V (current slot) and the state variable into one compact FP32 buffer [V | v].
+template <typename R, int NP, int NPS>
 __global__ void k_gather_f32(const DevArrays<R> d, int64_t ne, float* out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= ne * NP) return;
-    const int par = (d.lvl[i / NP] >> 3) & 1;
-    out[i] = (float)((par ? d.V1 : d.V0)[i]);
-    out[ne * NP + i] = (float)d.v[i];
+    const int64_t e = i / NP, j = e * NPS + (i - e * NP);
+    const int par = (d.lvl[e] >> 3) & 1;
+    out[i] = (float)((par ? d.V1 : d.V0)[j]);
+    out[ne * NP + i] = (float)d.v[j];
 }
 
-// Set V (into slot 0, parity reset) and optionally v from FP64 or FP32 input.
-template <typename R, int NP, typename In>
+// Set V (into slot 0, parity reset) and optionally v from compact FP64 or FP32 input; the
+// pad values of padded rows are set to 0.
+template <typename R, int NP, int NPS, typename In>
 __global__ void k_scatter_initial(DevArrays<R> d, int64_t ne, const In* V, const In* w) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= ne * NP) return;
-    d.V0[i] = (R)V[i];
-    if (w) d.v[i] = (R)w[i];
-    if (i % NP == 0) d.lvl[i / NP] &= 7;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= ne * NPS) return;
+    const int64_t e = j / NPS, q = j - e * NPS, i = e * NP + q;
+    const bool pad = q >= NP;
+    d.V0[j] = pad ? R(0) : (R)V[i];
+    if (w) d.v[j] = pad ? R(0) : (R)w[i];
+    if (q == 0) d.lvl[e] &= 7;
 }
 
 // Activation at the current time for probes already above threshold, and the
@@ -1294,10 +1325,9 @@ __global__ void k_lat_refresh(DevArrays<R> d, const Tables<R> T, const Phys<R> p
     uint32_t inf = d.info[e];
     const int lev = (inf >> 24) & 15;
     const int par = (d.lvl[e] >> 3) & 1;
-    const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * NP;
+    const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * S::NPS;
     R u[NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) u[q] = Vc[q];
+    ld_dofs<R, NP, S::NPS>(Vc, u);
     const uint32_t lc = d.loc[e];
     const int lx[3] = {(int)(lc & 255u), (int)((lc >> 8) & 255u), (int)((lc >> 16) & 255u)};
     const int64_t rid = d.root[e];
@@ -1341,7 +1371,7 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
                            const int8_t* pbits, const Tables<R> T) {
     pdl_enter();
     using S = Shape<DIM, P>;
-    constexpr int N1 = S::N1, NP = S::NP, NC = 1 << DIM;
+    constexpr int N1 = S::N1, NP = S::NP, NC = 1 << DIM, NPS = S::NPS;
     if (n.meta->err) return;
     const int64_t nne = n.meta->ne;
     if constexpr (NP < 27) {
@@ -1350,12 +1380,12 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
             if (pkind[i] != 0) continue;
             const int src = psrc[i];
             const int par = (o.lvl[src] >> 3) & 1;
-            const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NP;
-            const R* wo = o.v + (size_t)src * NP;
+            const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NPS;
+            const R* wo = o.v + (size_t)src * NPS;
 #pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                n.V0[(size_t)i * NP + q] = Vo[q];
-                n.v[(size_t)i * NP + q] = wo[q];
+            for (int q = 0; q < NPS; ++q) {
+                n.V0[(size_t)i * NPS + q] = Vo[q];
+                n.v[(size_t)i * NPS + q] = wo[q];
             }
             n.eta_t[i] = o.eta_t[src];
             n.lvl[i] = 0;
@@ -1369,33 +1399,34 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
             if (i < nne && pkind[i] == 0) {
                 const int src = psrc[i];
                 const int par = (o.lvl[src] >> 3) & 1;
-                vrow = (long long)((par ? o.V1 : o.V0) + (size_t)src * NP);
-                wrow = (long long)(o.v + (size_t)src * NP);
+                vrow = (long long)((par ? o.V1 : o.V0) + (size_t)src * NPS);
+                wrow = (long long)(o.v + (size_t)src * NPS);
                 n.eta_t[i] = o.eta_t[src];
                 n.lvl[i] = 0;
             }
-            // value idx = lane + 32 j of the warp's block: row r = idx / NP, column q; every
-            // load of the block is issued before the first store
-            R xv[NP], xw[NP];
-            bool keep[NP];
-            int r = lane / NP, q = lane - (lane / NP) * NP;
+            // value idx = lane + 32 j of the warp's block of padded rows: row r = idx / NPS,
+            // column q (the pad copied too); every load of the block is issued before the
+            // first store
+            R xv[NPS], xw[NPS];
+            bool keep[NPS];
+            int r = lane / NPS, q = lane - (lane / NPS) * NPS;
 #pragma unroll
-            for (int j = 0; j < NP; ++j) {
+            for (int j = 0; j < NPS; ++j) {
                 const long long vr = __shfl_sync(0xffffffffu, vrow, r);
                 const long long wr = __shfl_sync(0xffffffffu, wrow, r);
                 keep[j] = vr != 0;
                 xv[j] = keep[j] ? reinterpret_cast<const R*>(vr)[q] : R(0);
                 xw[j] = keep[j] ? reinterpret_cast<const R*>(wr)[q] : R(0);
-                q += 32 % NP;
-                r += 32 / NP;
-                if (q >= NP) {
-                    q -= NP;
+                q += 32 % NPS;
+                r += 32 / NPS;
+                if (q >= NPS) {
+                    q -= NPS;
                     ++r;
                 }
             }
-            const size_t o0 = (size_t)base * NP + lane;
+            const size_t o0 = (size_t)base * NPS + lane;
 #pragma unroll
-            for (int j = 0; j < NP; ++j) {
+            for (int j = 0; j < NPS; ++j) {
                 if (keep[j]) {
                     n.V0[o0 + 32 * j] = xv[j];
                     n.v[o0 + 32 * j] = xw[j];
@@ -1407,13 +1438,15 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
     const int kd = pkind[i];
     if (kd == 0) continue;
     const int src = psrc[i];
-    R* Vn = n.V0 + (size_t)i * NP;
-    R* wn = n.v + (size_t)i * NP;
+    R* Vn = n.V0 + (size_t)i * NPS;
+    R* wn = n.v + (size_t)i * NPS;
+#pragma unroll
+    for (int q = NP; q < NPS; ++q) Vn[q] = wn[q] = R(0);
     if (kd == 1) {
         const int bits = pbits[i];
         const int par = (o.lvl[src] >> 3) & 1;
-        const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NP;
-        const R* wo = o.v + (size_t)src * NP;
+        const R* Vo = (par ? o.V1 : o.V0) + (size_t)src * NPS;
+        const R* wo = o.v + (size_t)src * NPS;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             R a = 0, c = 0;
@@ -1436,8 +1469,8 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
         for (int cb = 0; cb < NC; ++cb) {
             const int ch = src + cb;
             const int par = (o.lvl[ch] >> 3) & 1;
-            const R* Vo = (par ? o.V1 : o.V0) + (size_t)ch * NP;
-            const R* wo = o.v + (size_t)ch * NP;
+            const R* Vo = (par ? o.V1 : o.V0) + (size_t)ch * NPS;
+            const R* wo = o.v + (size_t)ch * NPS;
             et += o.eta_t[ch];
             for (int qc = 0; qc < NP; ++qc) {
                 R wc = R(1);

@@ -48,6 +48,7 @@ constexpr int N = 32;           // output DOFs per element (27 used)
 constexpr int K = 192;          // 7 slots x 27 input DOFs (189 used, 3 zero)
 constexpr int KU = 189;         // used K
 constexpr int NP = 27;
+constexpr int NPS = 28;         // row stride of the per-DOF state arrays (27 values and a pad)
 constexpr int SLOTS = 7;
 constexpr int THREADS = 256;    // 8 warps; two CTAs per SM overlap each other's latencies
 constexpr int RST = 29;         // row stride of the residual staging array (odd: no bank conflicts)
@@ -211,7 +212,7 @@ __device__ __forceinline__ float seen_dof(const DevArrays<float>& d, int tick, i
     const int lv = d.lvl[nb], sh = B - (lv & 7), par = (lv >> 3) & 1;
     const int j = tick >> sh, rem = tick & ((1 << sh) - 1);
     const int nw = par ^ ((j + (rem ? 1 : 0)) & 1);
-    const size_t o = (size_t)nb * 27 + q;
+    const size_t o = (size_t)nb * tc::NPS + q;
     const float x = (nw ? d.V1 : d.V0)[o];
     if (!rem) return x;
     const float xo = (nw ? d.V0 : d.V1)[o];
@@ -395,8 +396,8 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             for (int f = 0; f < 6; ++f) lvn[f] = (uint8_t)((f < 3 ? (w7 >> (8 * (f + 1))) : (w8 >> (8 * (f - 3)))) & 255u);
             const int b = lv & 7, par = (lv >> 3) & 1;
             const int cur = par ^ ((tick >> (B - b)) & 1);
-            sPtr[tid] = (cur ? d.V1 : d.V0) + (size_t)es * NP;
-            sPtrO[tid] = (cur ? d.V0 : d.V1) + (size_t)es * NP;   // slot 0: the row the step writes
+            sPtr[tid] = (cur ? d.V1 : d.V0) + (size_t)es * NPS;
+            sPtrO[tid] = (cur ? d.V0 : d.V1) + (size_t)es * NPS;   // slot 0: the row the step writes
             sTh[tid] = 0.0f;
             if (e >= 0) live = 1;
 #pragma unroll
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
                 const int sh = B - (lvn[f] & 7), pn = (lvn[f] >> 3) & 1;
                 const int j = tick >> sh, rem = same ? (tick & ((1 << sh) - 1)) : 0;
                 const int nw = pn ^ ((j + (rem ? 1 : 0)) & 1);
-                const size_t o = (size_t)(same ? nbf[f] : es) * NP;
+                const size_t o = (size_t)(same ? nbf[f] : es) * NPS;
                 sPtr[(1 + f) * M + tid] = (nw ? d.V1 : d.V0) + o;
                 sPtrO[(1 + f) * M + tid] = (nw ? d.V0 : d.V1) + o;
                 sTh[(1 + f) * M + tid] = rem ? (float)rem * pow2_neg<float>(sh) : 0.0f;
@@ -563,9 +564,9 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             const int ke = tick >> (B - (sLv[i] & 7));
             const bool need = it < M * NP && e >= 0 && ke != 0;
             u[m] = __ldg(sPtr[i] + q);
-            w[m] = d.v[(size_t)es * NP + q];
-            Ia[m] = need ? d.Ia[(size_t)es * NP + q] : 0.0f;
-            ga[m] = need ? d.ga[(size_t)es * NP + q] : 0.0f;
+            w[m] = d.v[(size_t)es * NPS + q];
+            Ia[m] = need ? d.Ia[(size_t)es * NPS + q] : 0.0f;
+            ga[m] = need ? d.ga[(size_t)es * NPS + q] : 0.0f;
         }
         // thread 4 i: the RV-T accumulator of element i, needed at the end of the tile (ke != 0)
         double acc0 = 0.0;
@@ -629,10 +630,10 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
                                                         sDte[sLv[i] & 7], u[m], w[m], r, Ia[m], ga[m], un, wn);
                 if (in) {
                     const_cast<float*>(sPtrO[i])[q] = un;
-                    d.v[(size_t)sE[i] * NP + q] = wn;
+                    d.v[(size_t)sE[i] * NPS + q] = wn;
                     if (FIRST && (sLv[i] & 7) > 0) {
-                        d.Ia[(size_t)sE[i] * NP + q] = Ia[m];
-                        d.ga[(size_t)sE[i] * NP + q] = ga[m];
+                        d.Ia[(size_t)sE[i] * NPS + q] = Ia[m];
+                        d.ga[(size_t)sE[i] * NPS + q] = ga[m];
                     }
                     sT[it] = term;
                     sUo[it] = u[m];
@@ -663,7 +664,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
                     float wn;
                     term = dof_update<float>(ph, sMq[lev * NP + q], sMinv[lev * NP + q], ke, a.dteR[b], so, smd, u[m],
                                              w[m], r, Ia[m], ga[m], un, wn);
-                    const size_t o = (size_t)e * NP + q;
+                    const size_t o = (size_t)e * NPS + q;
                     const_cast<float*>(sPtrO[i])[q] = un;
                     d.v[o] = wn;
                     if (ke == 0 && b > 0) {

@@ -220,7 +220,7 @@ class Sim:
         self._check(self.lib.mdl_set_sweep_variant(self.h, variant))
 
     def set_sweep_blocks(self, max_blocks: int):
-        """Upper bound on the persistent tensor-core sweep's blocks (0: one per SM)."""
+        """Upper bound on the persistent tensor-core sweep's blocks (0: two per SM)."""
         self._check(self.lib.mdl_set_sweep_blocks(self.h, max_blocks))
 
     def __del__(self):
