@@ -60,10 +60,6 @@ SETUP_BARRIERS = 5
 # 2,736,960 elements by the elements due.
 TRAFFIC_PER_LAUNCH = {
     ("slab2d", "k_tick<float,2,1>"): (10.354432e6 + 7 * (5.937920e6 + 5.938176e6) / 2.0) / 8.0,
-    ("slab3d", "k_tick_tc<3,2>"): ((737.793e6 + 1101.906e6) * 2736960 / 2644800
-                                   + (1226.609e6 + 516.864e6) + (1226.647e6 + 517.287e6) + (1226.482e6 + 516.999e6)
-                                   + (1323.997e6 + 553.389e6)
-                                   + (1226.882e6 + 517.236e6) + (1227.125e6 + 517.592e6) + (1226.219e6 + 516.737e6)) / 8.0,
 }
 # Algorithmic bytes per DOF-update of the fused sweep (Q1 2D, FP32, AP): V_old 4 + v 4 +
 # V_new 4 + v 4 = 16 B, plus per element step 2d neighbour ids + 4 B level/flags + the FP64
@@ -366,9 +362,11 @@ def slot_alg_bytes(prob):
 
 def run_batch(args, rank, world):
     """64 heterogeneous resident instances (32 2D Q1, 16 3D Q1, 16 3D Q2; base element counts
-    log-uniform in [1e3, 1e5], seed 4).  A step is one batch round: every instance advances
-    one barrier, all slots' work issued on their own streams before any is waited for.  One GPU:
-    under a multi-rank launch it stops with an error instead of reporting one rank's rate."""
+    log-uniform in [1e3, 1e5], seed 4) stepped in fused rounds: a step is one batch round, every
+    instance advancing one barrier; the sweeps of all instances run as one persistent launch per
+    global tick and element family, replayed from a captured graph, with the launch shape the
+    batch's tuner picked during warm-up.  One GPU: under a multi-rank launch it stops with an
+    error instead of reporting one rank's rate."""
     if world > 1:
         raise SystemExit("bench.py --workload batch64 runs on one GPU (got WORLD_SIZE=%d)" % world)
     import torch
@@ -376,21 +374,27 @@ def run_batch(args, rank, world):
     from paper_2310_07607_gb300 import build, mdl
     build.build()
     inst = W.batch_instances(64, seed=4)
-    b = mdl.Batch(autotune=True)
+    b = mdl.Batch(autotune=True, fused=not args.batch_streams)
     t_setup = time.perf_counter()
     slots = [b.admit(p, t_end) for p, t_end in inst]
     t_setup = time.perf_counter() - t_setup
     sims = {s: b.slot(s)[0] for s in slots}
-    for _ in range(args.warmup):
+    # warm-up covers the tuner: 6 candidate shapes x 2 rounds per element family
+    warm = max(args.warmup, 13)
+    for _ in range(warm):
         b.step(1)
-    base = {s: sims[s].stats()["dof_updates"] for s in slots}
+    base = {s: sims[s].stats() for s in slots}
+    _, (r0, l0) = b.fused_info(32, 1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         b.step(1)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
-    du = {s: sims[s].stats()["dof_updates"] - base[s] for s in slots}
+    now = {s: sims[s].stats() for s in slots}
+    _, (r1, l1) = b.fused_info(32, 1)
+    du = {s: now[s]["dof_updates"] - base[s]["dof_updates"] for s in slots}
+    klaunch = sum(now[s]["kernel_launches"] - base[s]["kernel_launches"] for s in slots) + (l1 - l0)
     total = float(sum(du.values()))
     alg = sum(du[s] * slot_alg_bytes(p) for s, (p, _) in zip(slots, inst))
     peak, peak_kind = load_peaks()
@@ -399,21 +403,31 @@ def run_batch(args, rank, world):
     need = [int(math.floor(t_end / sims[s].time()[2] + 1e-9)) for s, (_, t_end) in zip(slots, inst)]
     per_round_s = secs / args.steps
     used, budget, resident = b.usage()
+    shapes = {}
+    for prec, order, name in ((32, 1, "fp32_q1"), (32, 2, "fp32_q2")):
+        sh, _ = b.fused_info(prec, order)
+        if sh:
+            shapes[name] = {"threads": sh[0], "elements_per_item": sh[1], "best_round_sweep_ms": round(sh[2], 3),
+                            "worst_round_sweep_ms": round(sh[3], 3)}
     out = {
         "metric": METRIC, "value": total / secs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+        "warmup": warm, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch64_mixed_2dq1_3dq1_3dq2_lts1to4_ap_fp32", "instances": len(slots),
+                   "mode": "streams" if args.batch_streams else "fused rounds (one sweep launch per global tick "
+                                                             "and element family, captured graph)",
                    "n_dof_total": int(n_dof), "device_bytes": int(used), "resident": resident,
                    "timing": "host clock around K batch rounds, device synchronised on both sides",
                    "l2": "working set larger than L2 (%.0f MB of state)" % (used / 1e6)},
         "roofline": {"bound": "hbm", "achieved": round(alg / secs / 1e9, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(alg / secs / 1e9 / peak, 4), "traffic": None, "peak_source": peak_kind,
                      "note": "whole batch round incl. every phase; per-class algorithmic bytes"},
+        "gpu_launches": int(klaunch),
+        "fused": {"rounds_timed": r1 - r0, "sweep_launches_timed": l1 - l0,
+                  "sweep_launches_per_round": (l1 - l0) / max(r1 - r0, 1), "tuned_shapes": shapes},
         "horizon": {"t_end_ms": inst[0][1], "barriers_max": max(need), "barriers_min": min(need),
                     "projected_s_all_to_horizon": round(max(need) * per_round_s, 2)},
-        "setup_s_incl_autotune": round(t_setup, 2),
-        "tuned_shapes": sorted({str(b.shape(p)) for p, _ in inst}),
+        "setup_s": round(t_setup, 2),
     }
     b.close()
     return out
@@ -665,6 +679,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="slab3d", choices=sorted(WORKLOADS) + ["batch64", "serve"])
     ap.add_argument("--serve-round", type=int, default=16, help="barriers per slot per serving round")
+    ap.add_argument("--batch-streams", action="store_true",
+                    help="batch64: each instance's own sweep on its own stream instead of fused rounds")
     ap.add_argument("--tick-shape", default="", help="sweep launch shape 'threads,blocks_per_sm'")
     ap.add_argument("--base", default="", help="base grid 'nx,ny[,nz]' at the workload's element size")
     ap.add_argument("--sweep", default="default", choices=["default"] + sorted(SWEEPS),

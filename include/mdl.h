@@ -240,13 +240,26 @@ int mdl_set_sweep_blocks(mdl_ctx* ctx, int32_t max_blocks);
 /* ---- Batches: many resident simulations stepped together on one GPU ----
  * (The paper runs one simulation at a time on one CPU core, Sec. 3; batching many
  * resident simulations is this library's addition.)
- * Each slot is a context with its own stream; mdl_batch_step launches every unfinished
- * slot's barriers before waiting for any, so their kernels overlap on the device.
- * Admission compares the slot's device-memory footprint estimate (mdl_batch_footprint)
- * with the budget.  With autotune, a temporary copy of the first instance of each
- * (precision, dim, order) class is stepped under a few sweep launch shapes and the
- * fastest shape is used for the class; launch shapes do not change results, so an
- * instance gives the same values alone and in a mix. */
+ * Each slot is a context with its own stream.  Admission compares the slot's device-memory
+ * footprint estimate (mdl_batch_footprint) with the budget.  mdl_batch_step steps in one
+ * of two ways (mdl_batch_set_fused):
+ *   fused (the default): in rounds, each advancing every running slot by one barrier step.
+ *     Each slot runs its indicator, adaptation, level and ordering phases (Alg. 1) on its
+ *     own stream; then ONE persistent sweep kernel per element family (Q1, Q2) and
+ *     precision covers the due elements of all slots, one launch per global tick (a slot
+ *     with fewer LTS levels takes part in every 2^k-th), replayed from a CUDA graph
+ *     captured for the batch's composition; then each slot's epilogue.  With autotune the
+ *     first rounds time every candidate launch shape of the fused kernel (threads per
+ *     block, due elements per work item) on the batch itself and keep the fastest
+ *     (mdl_batch_fused_info).  Every element takes the step of the thread-per-element
+ *     sweep (MDL_SWEEP_THREAD), whatever the slot's own sweep variant: an instance gives
+ *     the values it gives alone with that sweep, up to the FP32 rounding of two
+ *     compilations of the same arithmetic (meshes and levels identical).
+ *   streams: every unfinished slot launches its own barriers (its own sweep variant)
+ *     before any is waited for, so their kernels overlap on the device; with autotune a
+ *     temporary copy of the first instance of each (precision, dim, order) class is stepped
+ *     under a few sweep launch shapes and the fastest is used for the class.  Launch shapes
+ *     do not change results: an instance gives the same bits alone and in the mix. */
 #define MDL_SLOT_FREE    0
 #define MDL_SLOT_RUNNING 1
 #define MDL_SLOT_DONE    2
@@ -268,8 +281,16 @@ int mdl_batch_poll(mdl_batch* b, int32_t* done_slots, int32_t cap, int32_t* n);
 int mdl_batch_slot(mdl_batch* b, int32_t slot, mdl_ctx** ctx, int32_t* state, int32_t* rc);
 int mdl_batch_release(mdl_batch* b, int32_t slot);
 int mdl_batch_usage(const mdl_batch* b, int64_t* used, int64_t* budget, int32_t* resident);
-/* The autotuned sweep shape of prob's class (MDL_E_STATE if not tuned yet). */
+/* The autotuned sweep shape of prob's class in streams mode (MDL_E_STATE if not tuned yet). */
 int mdl_batch_shape(const mdl_batch* b, const mdl_problem* prob, int32_t* threads, int32_t* blocks_per_sm);
+/* on != 0: fused rounds (the default); 0: streams. */
+int mdl_batch_set_fused(mdl_batch* b, int32_t on);
+/* Fused rounds so far and fused sweep kernel launches (rounds, launches: always written);
+ * for the group of (precision 32|64, order 1|2): the tuned launch shape of its fused kernel
+ * (threads per block, due elements per work item) and the mean sweep time per round of the
+ * fastest and the slowest candidate measured by the tuner (MDL_E_STATE until tuned). */
+int mdl_batch_fused_info(const mdl_batch* b, int32_t precision, int32_t order, int32_t* threads, int32_t* tile,
+                         double* best_ms, double* worst_ms, int64_t* rounds, int64_t* launches);
 const char* mdl_batch_last_error(const mdl_batch* b);
 void mdl_batch_destroy(mdl_batch* b);
 

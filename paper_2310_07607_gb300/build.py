@@ -26,6 +26,7 @@ SOURCES = [
     "mdl_tables.cpp",
     "mdl_noalloc.cu",
     "mdl_batch.cpp",
+    "mdl_fused.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,13 +1,24 @@
 // mdl_batch.cpp -- many resident simulations stepped together on one GPU.
 //
-// Each slot is an ordinary context with its own stream and captured phase graphs; a
-// batch step first launches every unfinished slot's barriers (no host wait), then
-// waits for all of them, so their kernels overlap on the device.  Admission is by
-// device-memory footprint against the batch's budget.  The sweep kernel's launch shape
-// (threads per block, resident blocks per SM) is tuned once per (precision, dim, order)
-// class on a temporary copy of the first admitted instance; the shape does not
-// change any result, so an instance gives the same values alone and in a mix.
+// Each slot is an ordinary context with its own stream and captured phase graphs.
+// Admission is by device-memory footprint against the batch's budget.  Two ways to step:
+//   fused (the default): a round advances every running slot by one barrier step; each
+//     slot launches the phases before its sweep on its own stream, then ONE fused sweep
+//     (mdl_fused.h) per element family and precision covers the due elements of all the
+//     slots, tick by global tick, replayed from a CUDA graph captured for the batch's
+//     composition; then each slot's epilogue.  The fused kernel's launch shape (threads per
+//     block, due elements per work item) is tuned on the first rounds of the batch by timing
+//     every candidate on the batch itself (the shape changes no result).  Each element takes
+//     the step of the thread-per-element sweep, so an instance gives the values it gives alone
+//     with that sweep up to the FP32 rounding of the two kernels' compilations.
+//   streams: every slot launches its own barriers (its own sweep variant) on its own
+//     stream before any is waited for, so their kernels overlap on the device; the sweep
+//     launch shape is tuned once per class on a temporary copy of the first admitted
+//     instance, and an instance gives the same bits alone and in the mix.
 #include <cuda_runtime.h>
+
+#include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <chrono>
@@ -19,6 +30,7 @@
 
 #include "../../include/mdl.h"
 #include "mdl_ctx.h"
+#include "mdl_fused_api.h"
 
 struct mdl_batch {
     struct Slot {
@@ -30,6 +42,7 @@ struct mdl_batch {
         int64_t barriers_total = 0;
         int64_t barriers_done = 0;
         bool polled = false;
+        int group = 0;          // fused group: (precision 64) * 2 + (family - 1)
     };
     int64_t budget = 0;
     int64_t used = 0;
@@ -38,6 +51,38 @@ struct mdl_batch {
     std::map<int, std::pair<int, int>> shapes;   // class -> (threads, blocks per SM)
     std::string err;
     int64_t steps = 0;
+    // fused rounds
+    int fused = 1;
+    cudaStream_t fst = nullptr;                   // the batch's stream (fused sweeps)
+    cudaEvent_t fev = nullptr;                    // fused sweep done
+    std::vector<cudaEvent_t> sev;                 // per slot: phases before the sweep done
+    struct Group {                                // slots of one (precision, family)
+        int precision = 32, family = 1;
+        std::vector<int> members;                 // slot ids of the current round
+        std::vector<unsigned char> host;          // records of the round (host copy)
+        unsigned char* hpin = nullptr;            // pinned staging for the upload
+        void* dev = nullptr;                      // records in device memory
+        size_t cap = 0;                           // records the buffers hold
+        mdl::FusedShape shape{128, 256, 0};
+        int tuned = 0;                            // candidates timed so far (-1: done)
+        std::vector<double> cand_ms;              // measured ms per candidate
+        cudaGraphExec_t graph = nullptr;          // captured fused sweep of the composition
+        std::vector<long long> key;               // composition the graph was captured for
+        double best_ms = 0, worst_ms = 0;
+    };
+    Group groups[4];                              // (precision 32 / 64) x (family 1 / 2)
+    int64_t fused_rounds = 0, fused_launches = 0;
+    ~mdl_batch() {
+        for (auto& g : groups) {
+            if (g.graph) cudaGraphExecDestroy(g.graph);
+            if (g.hpin) cudaFreeHost(g.hpin);
+            if (g.dev) cudaFree(g.dev);
+        }
+        for (auto e : sev)
+            if (e) cudaEventDestroy(e);
+        if (fev) cudaEventDestroy(fev);
+        if (fst) cudaStreamDestroy(fst);
+    }
 };
 
 namespace {
@@ -81,6 +126,185 @@ int tune(mdl_ctx* c, int n, std::pair<int, int>* best) {
     return x->set_tick_shape(best->first, best->second);
 }
 
+// Candidate launch shapes of the fused sweep: threads per block, due elements per work item.
+const int kFusedShapes[][2] = {{128, 128}, {128, 512}, {256, 256}, {256, 1024}, {64, 256}, {128, 2048}};
+constexpr int kFusedCands = (int)(sizeof(kFusedShapes) / sizeof(kFusedShapes[0]));
+constexpr int kRoundsPerCand = 2;
+
+int sm_count() {
+    int dev = 0, n = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+// Finish a slot's barrier after end_barriers-style completion (shared by both modes).
+void settle(mdl_batch::Slot& s, int rc, int64_t c, int64_t* total) {
+    *total += c;
+    s.barriers_done += c;
+    if (rc) {
+        s.state = MDL_SLOT_FAILED;
+        s.rc = rc;
+        return;
+    }
+    double t = 0, dt = 0;
+    int64_t nb = 0;
+    s.ctx->impl->get_time(&t, &nb, &dt);
+    if (barriers_to(dt, t, s.t_end) <= 0) s.state = MDL_SLOT_DONE;
+    s.bytes = std::max<int64_t>(s.bytes, s.ctx->impl->device_bytes());
+}
+
+#define MDL_BCK(x)                                                  \
+    do {                                                            \
+        cudaError_t e_ = (x);                                       \
+        if (e_ != cudaSuccess) {                                    \
+            b->err = std::string(#x) + ": " + cudaGetErrorString(e_); \
+            return MDL_E_CUDA;                                      \
+        }                                                           \
+    } while (0)
+
+// One fused round over the running slots `run` (each advances one barrier step).
+int fused_round(mdl_batch* b, const std::vector<int>& run, int64_t* total) {
+    if (!b->fst) {
+        MDL_BCK(cudaStreamCreateWithFlags(&b->fst, cudaStreamNonBlocking));
+        MDL_BCK(cudaEventCreateWithFlags(&b->fev, cudaEventDisableTiming));
+    }
+    while (b->sev.size() < b->slots.size()) {
+        cudaEvent_t e = nullptr;
+        MDL_BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->sev.push_back(e);
+    }
+    for (auto& g : b->groups) {
+        g.members.clear();
+        g.host.clear();
+    }
+    // the phases before the sweep, each slot on its own stream
+    std::vector<int> Bs(b->slots.size(), 0);
+    std::vector<int> begun;
+    for (int i : run) {
+        mdl_batch::Slot& s = b->slots[i];
+        mdl_batch::Group& g = b->groups[s.group];
+        const size_t bytes = mdl::fused_slot_bytes(g.precision);
+        const size_t off = g.host.size();
+        g.host.resize(off + bytes);
+        const int rc = s.ctx->impl->fused_begin(g.host.data() + off, &Bs[i]);
+        if (rc) {
+            g.host.resize(off);
+            s.state = MDL_SLOT_FAILED;
+            s.rc = rc;
+            continue;
+        }
+        MDL_BCK(cudaEventRecord(b->sev[i], (cudaStream_t)s.ctx->impl->stream_handle()));
+        g.members.push_back(i);
+        begun.push_back(i);
+    }
+    // one fused sweep per (precision, family) group, from its captured graph
+    const int nsm = sm_count();
+    cudaEvent_t t0[4] = {}, t1[4] = {};
+    for (int gi = 0; gi < 4; ++gi) {
+        mdl_batch::Group& g = b->groups[gi];
+        const int n = (int)g.members.size();
+        if (n == 0) continue;
+        if (n > mdl::FUSED_MAX_SLOTS) {
+            b->err = "fused batch: too many slots in one group";
+            return MDL_E_ARG;
+        }
+        int Bmax = 0;
+        for (int i : g.members) Bmax = std::max(Bmax, Bs[i]);
+        const size_t bytes = mdl::fused_slot_bytes(g.precision);
+        for (int k = 0; k < n; ++k) mdl::fused_set_shift(g.host.data() + k * bytes, g.precision, Bmax - Bs[g.members[k]]);
+        if ((size_t)n > g.cap) {
+            if (g.graph) cudaGraphExecDestroy(g.graph);
+            g.graph = nullptr;
+            if (g.hpin) cudaFreeHost(g.hpin);
+            if (g.dev) cudaFree(g.dev);
+            g.hpin = nullptr;
+            g.dev = nullptr;
+            const size_t c = std::max<size_t>((size_t)n * 2, 16);
+            MDL_BCK(cudaMallocHost((void**)&g.hpin, c * bytes));
+            MDL_BCK(cudaMalloc(&g.dev, c * bytes));
+            g.cap = c;
+        }
+        memcpy(g.hpin, g.host.data(), (size_t)n * bytes);
+        MDL_BCK(cudaMemcpyAsync(g.dev, g.hpin, (size_t)n * bytes, cudaMemcpyHostToDevice, b->fst));
+        for (int i : g.members) MDL_BCK(cudaStreamWaitEvent(b->fst, b->sev[i], 0));
+        // launch shape: the candidate being timed, else the tuned one
+        int threads = g.shape.threads, tile = g.shape.tile;
+        if (b->autotune && g.tuned >= 0) {
+            const int c = g.tuned / kRoundsPerCand;
+            threads = kFusedShapes[c][0];
+            tile = kFusedShapes[c][1];
+        }
+        const int blocks = nsm * mdl::fused_blocks_per_sm(g.precision, g.family, threads);
+        const std::vector<long long> key{n, Bmax, threads, tile, blocks, (long long)(uintptr_t)g.dev};
+        if (!g.graph || key != g.key) {
+            if (g.graph) cudaGraphExecDestroy(g.graph);
+            g.graph = nullptr;
+            cudaGraph_t graph;
+            MDL_BCK(cudaStreamBeginCapture(b->fst, cudaStreamCaptureModeThreadLocal));
+            const cudaError_t el = mdl::fused_sweep(g.precision, g.family, g.dev, n, Bmax,
+                                                    mdl::FusedShape{threads, tile, blocks}, b->fst);
+            const cudaError_t ec = cudaStreamEndCapture(b->fst, &graph);
+            MDL_BCK(el);
+            MDL_BCK(ec);
+            const cudaError_t ei = cudaGraphInstantiate(&g.graph, graph, 0);
+            cudaGraphDestroy(graph);
+            MDL_BCK(ei);
+            g.key = key;
+        }
+        if (b->autotune && g.tuned >= 0) {
+            MDL_BCK(cudaEventCreate(&t0[gi]));
+            MDL_BCK(cudaEventCreate(&t1[gi]));
+            MDL_BCK(cudaEventRecord(t0[gi], b->fst));
+        }
+        MDL_BCK(cudaGraphLaunch(g.graph, b->fst));
+        if (t1[gi]) MDL_BCK(cudaEventRecord(t1[gi], b->fst));
+        b->fused_launches += 1 << Bmax;
+    }
+    MDL_BCK(cudaEventRecord(b->fev, b->fst));
+    // each slot's epilogue after the fused sweep, then completion
+    for (int i : begun) {
+        mdl_batch::Slot& s = b->slots[i];
+        MDL_BCK(cudaStreamWaitEvent((cudaStream_t)s.ctx->impl->stream_handle(), b->fev, 0));
+        const int rc = s.ctx->impl->fused_finish();
+        if (rc) {
+            s.state = MDL_SLOT_FAILED;
+            s.rc = rc;
+        }
+    }
+    for (int i : begun) {
+        mdl_batch::Slot& s = b->slots[i];
+        if (s.state == MDL_SLOT_FAILED) continue;
+        int64_t c = 0;
+        const int rc = s.ctx->impl->end_barriers(&c);
+        settle(s, rc, c, total);
+    }
+    MDL_BCK(cudaStreamSynchronize(b->fst));
+    // the tuner: add this round's sweep time to its candidate; after the last, keep the best
+    for (int gi = 0; gi < 4; ++gi) {
+        mdl_batch::Group& g = b->groups[gi];
+        if (!t0[gi]) continue;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, t0[gi], t1[gi]);
+        cudaEventDestroy(t0[gi]);
+        cudaEventDestroy(t1[gi]);
+        const int c = g.tuned / kRoundsPerCand;
+        if ((int)g.cand_ms.size() < kFusedCands) g.cand_ms.assign(kFusedCands, 0.0);
+        g.cand_ms[c] += ms;
+        if (++g.tuned == kFusedCands * kRoundsPerCand) {
+            int best = 0;
+            for (int k = 1; k < kFusedCands; ++k)
+                if (g.cand_ms[k] < g.cand_ms[best]) best = k;
+            g.shape = mdl::FusedShape{kFusedShapes[best][0], kFusedShapes[best][1], 0};
+            g.best_ms = g.cand_ms[best] / kRoundsPerCand;
+            g.worst_ms = *std::max_element(g.cand_ms.begin(), g.cand_ms.end()) / kRoundsPerCand;
+            g.tuned = -1;
+        }
+    }
+    b->fused_rounds++;
+    return MDL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -101,6 +325,11 @@ int mdl_batch_create(int64_t hbm_budget_bytes, int autotune, mdl_batch** out) {
     }
     b->budget = hbm_budget_bytes;
     b->autotune = autotune ? 1 : 0;
+    for (int gi = 0; gi < 4; ++gi) {
+        b->groups[gi].precision = gi >= 2 ? 64 : 32;
+        b->groups[gi].family = 1 + (gi & 1);
+        b->groups[gi].tuned = b->autotune ? 0 : -1;
+    }
     *out = b;
     return MDL_OK;
 }
@@ -145,7 +374,7 @@ int mdl_batch_admit(mdl_batch* b, const mdl_problem* prob, const double* V0, con
         }
     }
     const int key = class_key(*prob);
-    if (b->autotune) {
+    if (b->autotune && !b->fused) {
         auto it = b->shapes.find(key);
         if (it == b->shapes.end()) {
             // tune on a temporary copy of the instance, which is stepped and discarded
@@ -175,6 +404,7 @@ int mdl_batch_admit(mdl_batch* b, const mdl_problem* prob, const double* V0, con
     mdl_batch::Slot& s = b->slots[id];
     s = mdl_batch::Slot{};
     s.ctx = c;
+    s.group = (prob->precision == 64 ? 2 : 0) + (mdl::fused_family(prob->order) - 1);
     s.t_end = t_end;
     s.bytes = std::max<int64_t>(est, c->impl->device_bytes());
     double t = 0, dt = 0;
@@ -192,6 +422,38 @@ int mdl_batch_step(mdl_batch* b, int64_t barriers_per_slot, double wall_budget_s
     if (barriers_done) *barriers_done = 0;
     const auto t0 = std::chrono::steady_clock::now();
     int64_t total = 0;
+    if (b->fused) {
+        for (;;) {
+            for (int64_t r = 0; r < barriers_per_slot; ++r) {
+                std::vector<int> run;
+                for (size_t i = 0; i < b->slots.size(); ++i) {
+                    mdl_batch::Slot& s = b->slots[i];
+                    if (s.state != MDL_SLOT_RUNNING) continue;
+                    double t = 0, dt = 0;
+                    int64_t nb = 0;
+                    s.ctx->impl->get_time(&t, &nb, &dt);
+                    if (barriers_to(dt, t, s.t_end) <= 0) {
+                        s.state = MDL_SLOT_DONE;
+                        continue;
+                    }
+                    run.push_back((int)i);
+                }
+                if (run.empty()) break;
+                const int rc = fused_round(b, run, &total);
+                if (rc) {
+                    if (barriers_done) *barriers_done = total;
+                    return rc;
+                }
+            }
+            b->steps++;
+            bool any = false;
+            for (const auto& s : b->slots) any = any || s.state == MDL_SLOT_RUNNING;
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (!any || wall_budget_s <= 0 || el >= wall_budget_s) break;
+        }
+        if (barriers_done) *barriers_done = total;
+        return MDL_OK;
+    }
     for (;;) {
         std::vector<int> launched;
         for (size_t i = 0; i < b->slots.size(); ++i) {
@@ -217,18 +479,7 @@ int mdl_batch_step(mdl_batch* b, int64_t barriers_per_slot, double wall_budget_s
             mdl_batch::Slot& s = b->slots[i];
             int64_t c = 0;
             const int rc = s.ctx->impl->end_barriers(&c);
-            total += c;
-            s.barriers_done += c;
-            if (rc) {
-                s.state = MDL_SLOT_FAILED;
-                s.rc = rc;
-                continue;
-            }
-            double t = 0, dt = 0;
-            int64_t nb = 0;
-            s.ctx->impl->get_time(&t, &nb, &dt);
-            if (barriers_to(dt, t, s.t_end) <= 0) s.state = MDL_SLOT_DONE;
-            s.bytes = std::max<int64_t>(s.bytes, s.ctx->impl->device_bytes());
+            settle(s, rc, c, &total);
         }
         b->steps++;
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -304,6 +555,26 @@ void mdl_batch_destroy(mdl_batch* b) {
     for (auto& s : b->slots)
         if (s.ctx) mdl_destroy(s.ctx);
     delete b;
+}
+
+int mdl_batch_set_fused(mdl_batch* b, int32_t on) {
+    if (!b) return MDL_E_ARG;
+    b->fused = on ? 1 : 0;   // (a batch step completes its rounds before it returns)
+    return MDL_OK;
+}
+
+int mdl_batch_fused_info(const mdl_batch* b, int32_t precision, int32_t order, int32_t* threads, int32_t* tile,
+                         double* best_ms, double* worst_ms, int64_t* rounds, int64_t* launches) {
+    if (!b || (precision != 32 && precision != 64) || (order != 1 && order != 2)) return MDL_E_ARG;
+    if (rounds) *rounds = b->fused_rounds;
+    if (launches) *launches = b->fused_launches;
+    const mdl_batch::Group& g = b->groups[(precision == 64 ? 2 : 0) + (mdl::fused_family(order) - 1)];
+    if (g.tuned != -1) return MDL_E_STATE;
+    if (threads) *threads = g.shape.threads;
+    if (tile) *tile = g.shape.tile;
+    if (best_ms) *best_ms = g.best_ms;
+    if (worst_ms) *worst_ms = g.worst_ms;
+    return MDL_OK;
 }
 
 int mdl_set_tick_shape(mdl_ctx* ctx, int32_t threads, int32_t blocks_per_sm) {

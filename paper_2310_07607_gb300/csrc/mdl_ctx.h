@@ -40,6 +40,15 @@ public:
     virtual int set_sweep_variant(int variant) = 0;
     // Upper bound on the blocks of the persistent tensor-core sweep (0: the default).
     virtual int set_sweep_blocks(int max_blocks) = 0;
+    // Fused batch rounds (mdl_fused.h): launch the phases before the sweep (indicator,
+    // adaptation, levels, ordering) of one barrier on the context's stream and write the
+    // slot's sweep record (a FusedSlot of the context's precision, shift left 0) and its LTS
+    // level count B; after the batch's fused sweep, launch the epilogue.  end_barriers()
+    // then completes the barrier as after begin_barriers(1).
+    virtual int fused_begin(void* slot_record, int* B) = 0;
+    virtual int fused_finish() = 0;
+    virtual void* stream_handle() const = 0;
+    virtual int precision() const = 0;
     virtual int64_t device_bytes() const = 0;     // device memory held by the context
     virtual double dt_barrier() const = 0;
     std::string err;

@@ -31,6 +31,7 @@
 
 #include "mdl_amr.cuh"
 #include "mdl_ctx.h"
+#include "mdl_fused.h"
 #include "mdl_kernels.cuh"
 #include "mdl_mesh.h"
 #include "mdl_tables.h"
@@ -134,6 +135,9 @@ class Ctx : public CtxBase {
     float tc_unscale = 1.0f;       // 2^-t: undoes the scaling of the operator by 2^t
     DBuf<float> tcC;               // Q2 3D FP32: level-0 correction blocks of non-regular faces
     DBuf<DevMeta> meta;
+    DBuf<Tables<R>> dT;       // device copies of the tables and physics (fused batch sweeps)
+    DBuf<Phys<R>> dph;
+    int fused_cur = 0;        // state set the fused sweep of the barrier in flight updates
     DevMeta* hmeta = nullptr;
     bool ovr_levels = false, ovr_eta_s = false, ovr_eta_t = false;
     bool timing = false;
@@ -439,16 +443,7 @@ class Ctx : public CtxBase {
             return MDL_OK;
         }
         if (ph_ == 2) {
-            TickArgs<R> ta{};
-            ta.d = arrays(o);
-            ta.dt = dt;
-            ta.B = B;
-            ta.tscale = ldexp(dt, -B);
-            for (int b = 0; b < 8; ++b) {
-                ta.dte[b] = ldexp(dt, -b);
-                ta.dteR[b] = (R)ta.dte[b];
-            }
-            ta.stim = stim;
+            TickArgs<R> ta = tick_args(o);
             const int nt = 1 << B;
             if (coop_sweep) {
                 // all ticks + epilogue in one cooperative launch (every block resident)
@@ -507,6 +502,21 @@ class Ctx : public CtxBase {
         }
         MDL_LAUNCHED();
         return MDL_OK;
+    }
+
+    // Arguments of the sweep ticks on state set o (the tick is set per launch).
+    TickArgs<R> tick_args(int o) {
+        TickArgs<R> ta{};
+        ta.d = arrays(o);
+        ta.dt = dt;
+        ta.B = B;
+        ta.tscale = ldexp(dt, -B);
+        for (int b = 0; b < 8; ++b) {
+            ta.dte[b] = ldexp(dt, -b);
+            ta.dteR[b] = (R)ta.dte[b];
+        }
+        ta.stim = stim;
+        return ta;
     }
 
     // Run phase ph_ on set o: replay its captured graph (capturing it first) unless inputs
@@ -595,7 +605,7 @@ public:
         bcfl.release(); info.release(); loc.release(); nbr.release(); hang.release(); root.release();
         order.release();
         for (auto& m : smask) m.release();
-        lvl_ovr.release(); eta_t_ovr.release(); meta.release(); mtab.release();
+        lvl_ovr.release(); eta_t_ovr.release(); meta.release(); mtab.release(); dT.release(); dph.release();
         qvol.release(); qface.release(); qkelly.release(); tcB.release(); tcC.release();
         if (hmeta) cudaFreeHost(hmeta);
         for (auto e : evpool) cudaEventDestroy(e);
@@ -697,6 +707,10 @@ public:
             MDL_CK(cudaFuncSetAttribute((k_tick_tc<DIM, P>), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         tc::SMEM_BYTES));
         }
+        MDL_CK(dT.ensure(1));
+        MDL_CK(dph.ensure(1));
+        MDL_CK(cudaMemcpy(dT.p, &T, sizeof(Tables<R>), cudaMemcpyHostToDevice));
+        MDL_CK(cudaMemcpy(dph.p, &ph, sizeof(Phys<R>), cudaMemcpyHostToDevice));
         MDL_CK(mtab.ensure(hm.size()));
         MDL_CK(cudaMemcpyAsync(mtab.p, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         MDL_CK(class_b.ensure(hcb.size()));
@@ -947,6 +961,40 @@ public:
         }
         return MDL_OK;
     }
+
+    int fused_begin(void* slot_record, int* Bout) override {
+        if (inflight) {
+            err = "fused_begin: barriers already in flight";
+            return MDL_E_STATE;
+        }
+        inflight_start = nbar;
+        const bool direct = ovr_levels || ovr_eta_s || ovr_eta_t;
+        const int o = cs;
+        int rc;
+        if (pb.amr_enabled && !ovr_eta_s && (rc = run_phase(0, o, direct))) return rc;
+        if ((rc = run_phase(1, o, direct))) return rc;
+        fused_cur = pb.amr_enabled ? (o ^ 1) : o;
+        FusedSlot<R>* fs = static_cast<FusedSlot<R>*>(slot_record);
+        fs->ta = tick_args(fused_cur);
+        fs->T = dT.p;
+        fs->ph = dph.p;
+        fs->cls = DIM == 2 ? (P == 1 ? FC_2_1 : FC_2_2) : (P == 1 ? FC_3_1 : FC_3_2);
+        fs->shift = 0;
+        if (Bout) *Bout = B;
+        return MDL_OK;
+    }
+
+    int fused_finish() override {
+        const bool direct = ovr_levels || ovr_eta_s || ovr_eta_t;
+        int rc = run_phase(3, fused_cur, direct);
+        if (rc) return rc;
+        cs = fused_cur;
+        inflight = 1;
+        return MDL_OK;
+    }
+
+    void* stream_handle() const override { return (void*)st; }
+    int precision() const override { return sizeof(R) == 8 ? 64 : 32; }
 
     int64_t device_bytes() const override {
         int64_t b = 0;

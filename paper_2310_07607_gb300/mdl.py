@@ -73,6 +73,7 @@ EXPORTS = [
     "mdl_noalloc_last_error", "mdl_set_tick_shape", "mdl_set_sweep_variant", "mdl_set_sweep_blocks", "mdl_batch_create", "mdl_batch_footprint",
     "mdl_batch_admit", "mdl_batch_step", "mdl_batch_poll", "mdl_batch_slot", "mdl_batch_release",
     "mdl_batch_usage", "mdl_batch_shape", "mdl_batch_last_error", "mdl_batch_destroy",
+    "mdl_batch_set_fused", "mdl_batch_fused_info",
     "mdl_set_initial_f32", "mdl_read_fields_f32",
 ]
 
@@ -133,6 +134,9 @@ def load(path: Optional[str] = None):
     lib.mdl_batch_slot.argtypes = [vp, C.c_int32, C.POINTER(vp), i32p, i32p]
     lib.mdl_batch_release.argtypes = [vp, C.c_int32]
     lib.mdl_batch_usage.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), i32p]
+    lib.mdl_batch_set_fused.argtypes = [vp, C.c_int32]
+    lib.mdl_batch_fused_info.argtypes = [vp, C.c_int32, C.c_int32, i32p, i32p, dp, dp, C.POINTER(i64),
+                                         C.POINTER(i64)]
     lib.mdl_batch_shape.argtypes = [vp, C.POINTER(CProblem), i32p, i32p]
     lib.mdl_batch_last_error.argtypes = [vp]
     lib.mdl_batch_last_error.restype = C.c_char_p
@@ -385,7 +389,7 @@ def integral_noalloc(prob, V_dev: int, level_dev: int, n_e: int, out_dev: int, s
 class Batch:
     """Resident simulations stepped together (mdl_batch_*)."""
 
-    def __init__(self, hbm_budget_bytes: int = 0, autotune: bool = True, lib=None):
+    def __init__(self, hbm_budget_bytes: int = 0, autotune: bool = True, fused: bool = True, lib=None):
         self.lib = lib or load()
         h = C.c_void_p()
         rc = self.lib.mdl_batch_create(int(hbm_budget_bytes), 1 if autotune else 0, C.byref(h))
@@ -393,6 +397,20 @@ class Batch:
             raise MdlError(rc, self.lib.mdl_batch_last_error(None).decode())
         self.h = h
         self.problems = {}
+        self._check(self.lib.mdl_batch_set_fused(self.h, 1 if fused else 0))
+
+    def fused_info(self, precision: int = 32, order: int = 1):
+        """(threads, tile, best_ms, worst_ms) of the group's tuned fused sweep, or None before the
+        tuner finished; and the batch's fused (rounds, launches)."""
+        t, k = C.c_int32(), C.c_int32()
+        bm, wm = C.c_double(), C.c_double()
+        r, n = C.c_int64(), C.c_int64()
+        rc = self.lib.mdl_batch_fused_info(self.h, precision, order, C.byref(t), C.byref(k), C.byref(bm), C.byref(wm),
+                                           C.byref(r), C.byref(n))
+        if rc not in (0, -8):
+            self._check(rc)
+        shape = (t.value, k.value, bm.value, wm.value) if rc == 0 else None
+        return shape, (r.value, n.value)
 
     def _check(self, rc):
         if rc != 0:

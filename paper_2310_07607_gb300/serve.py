@@ -2,9 +2,9 @@
 
 Requests arrive over time; the loop admits every waiting request whose device-memory
 footprint fits the batch budget (first fit over the queue, oldest first), steps all
-resident simulations together -- each round launches every slot's barriers on its own
-stream before waiting for any, so their work overlaps on the device -- and retires
-finished slots, recording time-to-result (completion minus arrival).  Requests still
+resident simulations together -- the batch's fused rounds: each slot's adaptation and level
+phases on its own stream, one sweep launch per global tick over every resident slot -- and
+retires finished slots, recording time-to-result (completion minus arrival).  Requests still
 running when the wall limit ends are reported with their progress and a projected
 time-to-result from their own barrier rate.
 

@@ -1,5 +1,7 @@
-"""Batches of resident simulations (mdl_batch_*): same results alone and in a mix,
-admission by device-memory footprint, completion polling and slot release."""
+"""Batches of resident simulations (mdl_batch_*): same results alone and in a mix (streams mode:
+bit for bit; fused rounds: the thread-per-element sweep's values up to FP32 rounding), the fused
+sweep's tuned launch shape and launch count, admission by device-memory footprint, completion
+polling and slot release."""
 import numpy as np
 import pytest
 
@@ -45,6 +47,7 @@ def initial(mdl, prob):
 
 
 def test_alone_equals_in_mix_bitwise(mdl):
+    """Streams mode: every slot runs its own barriers (its own sweep variant) on its stream."""
     probs = [instance(2, 1, 0), instance(3, 1, 1), instance(3, 2, 2), instance(2, 1, 3, precision=64),
              instance(2, 2, 4, amr=0)]
     nbar = 6
@@ -56,7 +59,7 @@ def test_alone_equals_in_mix_bitwise(mdl):
         g.step_barriers(nbar)
         alone.append((g.read_V(), g.read_state(), g.read_activation(), g.read_mesh()[1]))
         g.close()
-    b = mdl.Batch(autotune=True)
+    b = mdl.Batch(autotune=True, fused=False)
     slots = []
     for p in probs:
         V0, v0 = initial(mdl, p)
@@ -113,4 +116,58 @@ def test_slot_finishes_at_its_own_end_time(mdl):
     b.step(barriers_per_slot=4)
     assert b.poll() == [c]
     assert b.slot(a)[0].time()[1] == 3 and b.slot(c)[0].time()[1] == 7
+    b.close()
+
+
+def test_fused_rounds_match_alone_thread_sweep(mdl):
+    """Fused rounds: one sweep launch per global tick, element family and precision over all
+    slots (uneven LTS levels: 2, 3 and 4 levels in one batch), replayed from a captured graph.
+    Each slot must give the values it gives alone with the thread-per-element sweep: meshes,
+    levels and activated probes identical, V and the state within FP32 rounding of two
+    compilations of the same element step (FP64 slots within 1e-12).  The tuner must have
+    settled on a shape, and the launch count must be one per global tick of each group."""
+    probs = [instance(2, 1, 0), instance(3, 1, 1), instance(3, 2, 2), instance(2, 1, 3, precision=64),
+             instance(2, 2, 4, amr=0), instance(2, 1, 5).replace(n_lts_levels=2),
+             instance(3, 1, 6).replace(n_lts_levels=4)]
+    nbar = 14
+    alone = []
+    for p in probs:
+        V0, v0 = initial(mdl, p)
+        g = mdl.Sim(p)
+        g.set_sweep_variant(mdl.SWEEP_THREAD)
+        g.set_initial(V0, v0)
+        g.step_barriers(nbar)
+        alone.append((g.read_V(), g.read_state(), g.read_activation(), g.read_mesh()))
+        g.close()
+    b = mdl.Batch(autotune=True, fused=True)
+    slots = []
+    for p in probs:
+        V0, v0 = initial(mdl, p)
+        slots.append(b.admit(p, nbar * mdl.Sim(p).dt, V0, v0))
+    while b.step(barriers_per_slot=2) > 0:
+        pass
+    assert sorted(b.poll()) == sorted(slots)
+    for s, p, (Va, va, la, ma) in zip(slots, probs, alone):
+        g, state, rc = b.slot(s)
+        assert state == mdl.SLOT_DONE and rc == 0
+        assert g.time()[1] == nbar
+        mb = g.read_mesh()
+        for x, y in zip(ma, mb):
+            assert np.array_equal(x, y)
+        tol = 1e-12 if p.precision == 64 else 1e-5
+        Vb, vb, lb = g.read_V(), g.read_state(), g.read_activation()
+        assert np.abs(Vb - Va).max() <= tol * max(np.abs(Va).max(), 1.0), (p.dim, p.order, np.abs(Vb - Va).max())
+        assert np.abs(vb - va).max() <= tol * max(np.abs(va).max(), 1.0)
+        fa, fb = np.isfinite(la), np.isfinite(lb)
+        assert np.array_equal(fa, fb)
+        if fa.any():
+            assert np.abs(la[fa] - lb[fa]).max() <= 1e-6
+    shape, (rounds, launches) = b.fused_info(32, 1)
+    assert shape is not None and shape[0] in (64, 128, 256) and shape[1] >= 128 and shape[2] <= shape[3]
+    assert rounds == nbar
+    # per round: 2^Bmax launches for each group with slots (FP32 Q1: Bmax 3, FP32 Q2: 2,
+    # FP64 Q1: 2)
+    assert launches == nbar * (8 + 4 + 4)
+    for s in slots:
+        b.release(s)
     b.close()

@@ -1,5 +1,7 @@
 """Continuous-batching request loop: requests arriving while others run are admitted as
-memory allows, all complete, and each result equals the same simulation run alone."""
+memory allows, all complete, and each result equals the same simulation run alone (with the
+thread-per-element sweep every element takes in the batch's fused rounds: meshes and activated
+probes identical, V within FP32 rounding of the two compilations of the element step)."""
 import numpy as np
 import pytest
 
@@ -43,9 +45,14 @@ def test_serving_loop_results_equal_alone():
     assert np.isfinite(rep["ttr_p50_s"]) and rep["ttr_p99_s"] >= rep["ttr_p50_s"]
     for r in reqs:
         g = mdl.Sim(r.prob)
+        g.set_sweep_variant(mdl.SWEEP_THREAD)
         n = int(np.floor(r.horizon_ms / g.dt + 1e-9))
         g.step_barriers(n)
         assert r.result["nbar"] == n
-        assert np.array_equal(r.result["V"], g.read_V())
-        assert np.array_equal(r.result["lat"], g.read_activation())
+        Va = g.read_V()
+        assert np.abs(r.result["V"] - Va).max() <= 1e-5 * max(np.abs(Va).max(), 1.0)
+        la, lb = g.read_activation(), r.result["lat"]
+        assert np.array_equal(np.isfinite(la), np.isfinite(lb))
+        if np.isfinite(la).any():
+            assert np.abs(la[np.isfinite(la)] - lb[np.isfinite(la)]).max() <= 1e-6
         g.close()
