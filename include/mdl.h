@@ -245,16 +245,19 @@ int mdl_set_sweep_blocks(mdl_ctx* ctx, int32_t max_blocks);
  * of two ways (mdl_batch_set_fused):
  *   fused (the default): in rounds, each advancing every running slot by one barrier step.
  *     Each slot runs its indicator, adaptation, level and ordering phases (Alg. 1) on its
- *     own stream; then ONE persistent sweep kernel per element family (Q1, Q2) and
- *     precision covers the due elements of all slots, one launch per global tick (a slot
- *     with fewer LTS levels takes part in every 2^k-th), replayed from a CUDA graph
- *     captured for the batch's composition; then each slot's epilogue.  With autotune the
- *     first rounds time every candidate launch shape of the fused kernel (threads per
- *     block, due elements per work item) on the batch itself and keep the fastest
- *     (mdl_batch_fused_info).  Every element takes the step of the thread-per-element
- *     sweep (MDL_SWEEP_THREAD), whatever the slot's own sweep variant: an instance gives
- *     the values it gives alone with that sweep, up to the FP32 rounding of two
- *     compilations of the same arithmetic (meshes and levels identical).
+ *     own stream; then ONE persistent sweep kernel per element class (2D/3D, Q1/Q2) and
+ *     precision covers the due elements of all slots of the class, one launch per global
+ *     tick (a slot with fewer LTS levels takes part in every 2^k-th), replayed from a CUDA
+ *     graph captured for the batch's composition; then each slot's epilogue.  The rounds of
+ *     one mdl_batch_step are issued back to back and waited for once.  With autotune the
+ *     first rounds (one at a time) time, per class, every candidate launch shape of the
+ *     fused kernel (threads per block, due elements per work item) and "own sweeps" (each
+ *     slot's own sweep variant on its own stream) on the batch itself, and keep the fastest
+ *     (mdl_batch_fused_info); without autotune the fused kernel runs at 128 threads and 256
+ *     due elements per work item.  A fused element takes the step of the thread-per-element
+ *     sweep (MDL_SWEEP_THREAD): an instance gives the values it gives alone with that sweep,
+ *     up to the FP32 rounding of two compilations of the same arithmetic (meshes and levels
+ *     identical); with own sweeps it gives the bits it gives alone.
  *   streams: every unfinished slot launches its own barriers (its own sweep variant)
  *     before any is waited for, so their kernels overlap on the device; with autotune a
  *     temporary copy of the first instance of each (precision, dim, order) class is stepped
@@ -286,11 +289,14 @@ int mdl_batch_shape(const mdl_batch* b, const mdl_problem* prob, int32_t* thread
 /* on != 0: fused rounds (the default); 0: streams. */
 int mdl_batch_set_fused(mdl_batch* b, int32_t on);
 /* Fused rounds so far and fused sweep kernel launches (rounds, launches: always written);
- * for the group of (precision 32|64, order 1|2): the tuned launch shape of its fused kernel
- * (threads per block, due elements per work item) and the mean sweep time per round of the
- * fastest and the slowest candidate measured by the tuner (MDL_E_STATE until tuned). */
-int mdl_batch_fused_info(const mdl_batch* b, int32_t precision, int32_t order, int32_t* threads, int32_t* tile,
-                         double* best_ms, double* worst_ms, int64_t* rounds, int64_t* launches);
+ * for the group of (precision 32|64, dim 2|3, order 1|2): own = 1 if the tuner chose each
+ * slot's own sweep, else the tuned launch shape of the fused kernel (threads per block, due
+ * elements per work item); the mean sweep time per round of the fastest and the slowest
+ * candidate and of own sweeps, as the tuner measured them (MDL_E_STATE until tuned).  Any
+ * output pointer may be NULL. */
+int mdl_batch_fused_info(const mdl_batch* b, int32_t precision, int32_t dim, int32_t order, int32_t* own,
+                         int32_t* threads, int32_t* tile, double* best_ms, double* worst_ms, double* own_ms,
+                         int64_t* rounds, int64_t* launches);
 const char* mdl_batch_last_error(const mdl_batch* b);
 void mdl_batch_destroy(mdl_batch* b);
 

@@ -9,7 +9,8 @@
 //                  none refined, no outside face neighbour finer or refined -> coarsen
 //   k_amr_count    new leaves per old leaf (2^d, 1 or 0), then an exclusive scan
 //   k_amr_emit     new leaf coordinates in (root, Morton) order and the transfer plan
-//   k_owner_fill   finest-grid owner map of the new mesh
+//   k_leaf_keys    sort key of every leaf of the new mesh (its lower corner on the finest
+//                  grid: root id, then Morton index inside the root) for neighbour search
 //   k_mesh_tables  face kinds/positions, neighbours, hanging lists, levels, probe and
 //                  stimulus data, CFL class levels of the new mesh
 // and the level ordering (a stable multi-split by b descending) with the due counts
@@ -23,7 +24,7 @@
 
 namespace mdl {
 
-// Geometry of the base grid and finest owner map.
+// Geometry of the base grid and the finest grid.
 struct Grid {
     int32_t base[3];
     int64_t fine[3];
@@ -249,48 +250,84 @@ __global__ void k_scan_emit(const int4* coord, const uint8_t* r, const uint8_t* 
     }
 }
 
-// Finest-grid owner map: every leaf writes its index into the finest cells it covers.
-// 3D: one thread per leaf (of up to 4^L rows per leaf most would be skipped); its rows of
-// finest cells along x are contiguous runs of 2^(L - level) cells (a leaf at the finest
-// level writes one cell).
+// Sort key of a finest-grid cell: its root's id (x fastest over the base grid) above the
+// Morton index of the cell inside the root (x bit lowest).  Leaves are stored in this order
+// (their lower corner's key), so the leaf holding a cell is the last leaf whose key does not
+// exceed the cell's: a search over 8 bytes per leaf instead of an owner map of 4 bytes per
+// finest cell (2^(d L) per root).
 template <int DIM>
-__global__ void k_owner_fill(const int4* coord, int32_t* owner, Grid g, const DevMeta* m, int force) {
+__device__ __forceinline__ uint64_t cell_key(const Grid& g, int64_t fx, int64_t fy, int64_t fz) {
+    const int L = g.L;
+    const int64_t rx = fx >> L, ry = fy >> L, rz = DIM == 3 ? (fz >> L) : 0;
+    const uint64_t rid = (uint64_t)(rx + g.base[0] * (ry + (int64_t)g.base[1] * rz));
+    const uint32_t lx = (uint32_t)(fx - (rx << L)), ly = (uint32_t)(fy - (ry << L)),
+                   lz = DIM == 3 ? (uint32_t)(fz - (rz << L)) : 0u;
+    uint64_t mort = 0;
+    for (int b = 0; b < L; ++b) {
+        mort |= (uint64_t)((lx >> b) & 1u) << (DIM * b);
+        mort |= (uint64_t)((ly >> b) & 1u) << (DIM * b + 1);
+        if (DIM == 3) mort |= (uint64_t)((lz >> b) & 1u) << (DIM * b + 2);
+    }
+    return (rid << (DIM * L)) | mort;
+}
+
+template <int DIM>
+__global__ void k_leaf_keys(const int4* coord, uint64_t* lkey, Grid g, const DevMeta* m, int force) {
     pdl_enter();
     if (m->err || !(force || m->changed)) return;
     const int64_t ne = m->ne;
-    if constexpr (DIM == 2) {
-        // 2D: one thread per (leaf, row); at most 2^L rows per leaf, few of them skipped
-        const int maxrows = 1 << g.L;
-        for (int64_t t = gtid(); t < ne * maxrows; t += gstride()) {
-            const int64_t e = t / maxrows;
-            const int row = (int)(t - e * maxrows);
-            const int4 a = coord[e];
-            const int sh = g.L - a.w;
-            const int n = 1 << sh;
-            if (row >= n) continue;
-            int32_t* dst = owner + ((int64_t)a.x << sh) + g.fine[0] * (((int64_t)a.y << sh) + row);
-            for (int x = 0; x < n; ++x) dst[x] = (int32_t)e;
-        }
-    } else {
-        for (int64_t e = gtid(); e < ne; e += gstride()) {
-            const int4 a = coord[e];
-            const int sh = g.L - a.w;
-            const int n = 1 << sh;
-            for (int row = 0; row < n * n; ++row) {
-                const int64_t y = ((int64_t)a.y << sh) + (row % n);
-                const int64_t z = ((int64_t)a.z << sh) + row / n;
-                int32_t* dst = owner + ((int64_t)a.x << sh) + g.fine[0] * (y + g.fine[1] * z);
-                for (int x = 0; x < n; ++x) dst[x] = (int32_t)e;
-            }
-        }
+    for (int64_t e = gtid(); e < ne; e += gstride()) {
+        const int4 a = coord[e];
+        const int sh = g.L - a.w;
+        lkey[e] = cell_key<DIM>(g, (int64_t)a.x << sh, (int64_t)a.y << sh, (int64_t)a.z << sh);
     }
 }
 
-// Face tables of the mesh in `coord` from the owner map (same rules as the forest
+// The leaf holding the cell of key k: the last e with lkey[e] <= k (lkey[0] = 0), found by a
+// galloping search from `hint` (face neighbours are mostly near in the Morton order), then
+// bisection.
+__device__ __forceinline__ int32_t find_leaf(const uint64_t* __restrict__ lkey, int64_t ne, int64_t hint,
+                                             uint64_t k) {
+    int64_t lo, hi;   // lkey[lo] <= k < lkey[hi] (hi == ne: past the end)
+    if (lkey[hint] <= k) {
+        lo = hint;
+        hi = ne;
+        for (int64_t step = 1;; step <<= 1) {
+            const int64_t j = lo + step;
+            if (j >= ne) break;
+            if (lkey[j] <= k) {
+                lo = j;
+            } else {
+                hi = j;
+                break;
+            }
+        }
+    } else {
+        hi = hint;
+        lo = 0;
+        for (int64_t step = 1;; step <<= 1) {
+            const int64_t j = hi - step;
+            if (j <= 0) break;
+            if (lkey[j] <= k) {
+                lo = j;
+                break;
+            }
+            hi = j;
+        }
+    }
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (lkey[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    return (int32_t)lo;
+}
+
+// Face tables of the mesh in `coord` from the leaf keys (same rules as the forest
 // bookkeeping: neighbour at the same level, one coarser with the tangential position
 // bits, or the 2^(d-1) finer children touching the face).
 template <typename R, int DIM, int P>
-__global__ void k_mesh_tables(const int4* coord, const int32_t* owner, Grid g, uint32_t* info, int32_t* nbr,
+__global__ void k_mesh_tables(const int4* coord, const uint64_t* lkey, Grid g, uint32_t* info, int32_t* nbr,
                               int32_t* hang, int32_t* root, uint32_t* loc, uint8_t* bcfl,
                               const uint8_t* class_b, uint32_t* smask0, uint32_t* smask1, uint32_t* smask2,
                               uint32_t* smask3, StimBoxes sb, Phys<double> phd, DevMeta* m, int force) {
@@ -321,7 +358,7 @@ __global__ void k_mesh_tables(const int4* coord, const int32_t* owner, Grid g, u
                 int64_t fc[3];
                 for (int k = 0; k < 3; ++k) fc[k] = (k < DIM) ? (cn[k] << sh) : 0;
                 if (side < 0) fc[axis] = ((cn[axis] + 1) << sh) - 1;
-                const int32_t o = owner[fc[0] + g.fine[0] * (fc[1] + g.fine[1] * fc[2])];
+                const int32_t o = find_leaf(lkey, ne, e, cell_key<DIM>(g, fc[0], fc[1], fc[2]));
                 const int lo = coord[o].w;
                 int tg[2] = {0, 0}, nt = 0;
                 for (int k = 0; k < DIM; ++k)
@@ -344,7 +381,7 @@ __global__ void k_mesh_tables(const int4* coord, const int32_t* owner, Grid g, u
                         for (int t = 0; t < nt; ++t) ch[tg[t]] = 2 * (int64_t)c[tg[t]] + ((b >> t) & 1);
                         int64_t f2[3];
                         for (int k = 0; k < 3; ++k) f2[k] = (k < DIM) ? (ch[k] << (sh - 1)) : 0;
-                        hang[nb + b] = owner[f2[0] + g.fine[0] * (f2[1] + g.fine[1] * f2[2])];
+                        hang[nb + b] = find_leaf(lkey, ne, o, cell_key<DIM>(g, f2[0], f2[1], f2[2]));
                     }
                 }
             }

@@ -4,13 +4,17 @@
 // Admission is by device-memory footprint against the batch's budget.  Two ways to step:
 //   fused (the default): a round advances every running slot by one barrier step; each
 //     slot launches the phases before its sweep on its own stream, then ONE fused sweep
-//     (mdl_fused.h) per element family and precision covers the due elements of all the
-//     slots, tick by global tick, replayed from a CUDA graph captured for the batch's
-//     composition; then each slot's epilogue.  The fused kernel's launch shape (threads per
-//     block, due elements per work item) is tuned on the first rounds of the batch by timing
-//     every candidate on the batch itself (the shape changes no result).  Each element takes
-//     the step of the thread-per-element sweep, so an instance gives the values it gives alone
-//     with that sweep up to the FP32 rounding of the two kernels' compilations.
+//     (mdl_fused.h) per element class and precision covers the due elements of all the
+//     slots of that class, tick by global tick, replayed from a CUDA graph captured for the
+//     batch's composition; then each slot's epilogue.  The rounds of one mdl_batch_step run
+//     back to back: the host waits for the device once, after the last.  Per class, the
+//     first rounds of the batch time every candidate on the batch itself -- launch shapes of
+//     the fused kernel (threads per block, due elements per work item) and "own sweeps"
+//     (each slot's own sweep variant on its own stream, e.g. the tensor-core sweep of a Q2
+//     3D FP32 slot) -- and keep the fastest.  A fused element takes the step of the
+//     thread-per-element sweep, so an instance gives the values it gives alone with that
+//     sweep up to the FP32 rounding of the two kernels' compilations; with own sweeps it
+//     gives the bits it gives alone.
 //   streams: every slot launches its own barriers (its own sweep variant) on its own
 //     stream before any is waited for, so their kernels overlap on the device; the sweep
 //     launch shape is tuned once per class on a temporary copy of the first admitted
@@ -42,7 +46,8 @@ struct mdl_batch {
         int64_t barriers_total = 0;
         int64_t barriers_done = 0;
         bool polled = false;
-        int group = 0;          // fused group: (precision 64) * 2 + (family - 1)
+        int group = 0;          // fused group: (precision 64) * 4 + element class
+        bool own = false;       // this round's sweep: the slot's own (not the fused kernel)
     };
     int64_t budget = 0;
     int64_t used = 0;
@@ -56,27 +61,41 @@ struct mdl_batch {
     cudaStream_t fst = nullptr;                   // the batch's stream (fused sweeps)
     cudaEvent_t fev = nullptr;                    // fused sweep done
     std::vector<cudaEvent_t> sev;                 // per slot: phases before the sweep done
-    struct Group {                                // slots of one (precision, family)
-        int precision = 32, family = 1;
+    struct Group {                                // slots of one (precision, element class)
+        int precision = 32, cls = 0;
         std::vector<int> members;                 // slot ids of the current round
         std::vector<unsigned char> host;          // records of the round (host copy)
-        unsigned char* hpin = nullptr;            // pinned staging for the upload
-        void* dev = nullptr;                      // records in device memory
-        size_t cap = 0;                           // records the buffers hold
+        unsigned char* hpin = nullptr;            // pinned staging for uploads
+        size_t pin_cap = 0;
+        // Uploaded records with the sweep graph captured for them.  Records change only when
+        // a slot's state set or capacity does; two entries hold an adapting batch's two sets.
+        struct Entry {
+            std::vector<unsigned char> bytes;
+            void* dev = nullptr;
+            size_t cap = 0;
+            cudaGraphExec_t graph = nullptr;
+            std::vector<long long> key;
+            int64_t last = -1;
+        } entry[2];
         mdl::FusedShape shape{128, 256, 0};
-        int tuned = 0;                            // candidates timed so far (-1: done)
+        bool own = false;                         // tuned: each slot's own sweep
+        int tuned = 0;                            // candidate rounds timed so far (-1: done)
         std::vector<double> cand_ms;              // measured ms per candidate
-        cudaGraphExec_t graph = nullptr;          // captured fused sweep of the composition
-        std::vector<long long> key;               // composition the graph was captured for
-        double best_ms = 0, worst_ms = 0;
+        cudaEvent_t t0 = nullptr, t1 = nullptr;   // tuner timing of the current round
+        bool timed = false;
+        double best_ms = 0, worst_ms = 0, own_ms = 0;
     };
-    Group groups[4];                              // (precision 32 / 64) x (family 1 / 2)
+    Group groups[8];                              // (precision 32 / 64) x element class
     int64_t fused_rounds = 0, fused_launches = 0;
     ~mdl_batch() {
         for (auto& g : groups) {
-            if (g.graph) cudaGraphExecDestroy(g.graph);
+            for (auto& e : g.entry) {
+                if (e.graph) cudaGraphExecDestroy(e.graph);
+                if (e.dev) cudaFree(e.dev);
+            }
             if (g.hpin) cudaFreeHost(g.hpin);
-            if (g.dev) cudaFree(g.dev);
+            if (g.t0) cudaEventDestroy(g.t0);
+            if (g.t1) cudaEventDestroy(g.t1);
         }
         for (auto e : sev)
             if (e) cudaEventDestroy(e);
@@ -126,9 +145,12 @@ int tune(mdl_ctx* c, int n, std::pair<int, int>* best) {
     return x->set_tick_shape(best->first, best->second);
 }
 
-// Candidate launch shapes of the fused sweep: threads per block, due elements per work item.
+// Candidate launch shapes of the fused sweep: threads per block, due elements per work
+// item.  One more candidate follows them: each slot's own sweep on its own stream.
 const int kFusedShapes[][2] = {{128, 128}, {128, 512}, {256, 256}, {256, 1024}, {64, 256}, {128, 2048}};
 constexpr int kFusedCands = (int)(sizeof(kFusedShapes) / sizeof(kFusedShapes[0]));
+constexpr int kOwnCand = kFusedCands;
+constexpr int kCands = kFusedCands + 1;
 constexpr int kRoundsPerCand = 2;
 
 int sm_count() {
@@ -138,7 +160,7 @@ int sm_count() {
     return n;
 }
 
-// Finish a slot's barrier after end_barriers-style completion (shared by both modes).
+// Finish a slot's barriers after end_barriers-style completion (shared by both modes).
 void settle(mdl_batch::Slot& s, int rc, int64_t c, int64_t* total) {
     *total += c;
     s.barriers_done += c;
@@ -163,8 +185,78 @@ void settle(mdl_batch::Slot& s, int rc, int64_t c, int64_t* total) {
         }                                                           \
     } while (0)
 
-// One fused round over the running slots `run` (each advances one barrier step).
-int fused_round(mdl_batch* b, const std::vector<int>& run, int64_t* total) {
+bool tuning(const mdl_batch* b) {
+    if (!b->autotune) return false;
+    for (const auto& g : b->groups)
+        if (g.tuned >= 0 && !g.members.empty()) return true;
+    return false;
+}
+
+// The candidate a group runs this round (-1: its tuned choice).
+int candidate(const mdl_batch* b, const mdl_batch::Group& g) {
+    return b->autotune && g.tuned >= 0 ? g.tuned / kRoundsPerCand : -1;
+}
+
+// The group's fused sweep of this round from its captured graph (uploading the records
+// and capturing first when they or the launch shape changed).
+int fused_group_sweep(mdl_batch* b, mdl_batch::Group& g, int n, int Bmax, int threads, int tile, int nsm) {
+    const size_t bytes = mdl::fused_slot_bytes(g.precision);
+    const size_t nb = (size_t)n * bytes;
+    mdl_batch::Group::Entry* E = nullptr;
+    for (auto& e : g.entry)
+        if (e.dev && e.bytes == g.host) E = &e;
+    if (!E) {
+        E = g.entry[0].last <= g.entry[1].last ? &g.entry[0] : &g.entry[1];
+        // the entry's buffer and the staging are idle once the batch stream is
+        MDL_BCK(cudaStreamSynchronize(b->fst));
+        if (nb > E->cap) {
+            if (E->graph) cudaGraphExecDestroy(E->graph);
+            E->graph = nullptr;
+            if (E->dev) cudaFree(E->dev);
+            E->dev = nullptr;
+            E->cap = 0;
+            const size_t c = std::max<size_t>(nb * 2, 16 * bytes);
+            MDL_BCK(cudaMalloc(&E->dev, c));
+            E->cap = c;
+        }
+        if (nb > g.pin_cap) {
+            if (g.hpin) cudaFreeHost(g.hpin);
+            g.hpin = nullptr;
+            g.pin_cap = 0;
+            const size_t c = std::max<size_t>(nb * 2, 16 * bytes);
+            MDL_BCK(cudaMallocHost((void**)&g.hpin, c));
+            g.pin_cap = c;
+        }
+        memcpy(g.hpin, g.host.data(), nb);
+        MDL_BCK(cudaMemcpyAsync(E->dev, g.hpin, nb, cudaMemcpyHostToDevice, b->fst));
+        E->bytes = g.host;
+    }
+    E->last = b->fused_rounds;
+    const int blocks = nsm * mdl::fused_blocks_per_sm(g.precision, g.cls, threads);
+    const std::vector<long long> key{n, Bmax, threads, tile, blocks, (long long)(uintptr_t)E->dev};
+    if (!E->graph || key != E->key) {
+        if (E->graph) cudaGraphExecDestroy(E->graph);
+        E->graph = nullptr;
+        cudaGraph_t graph;
+        MDL_BCK(cudaStreamBeginCapture(b->fst, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t el = mdl::fused_sweep(g.precision, g.cls, E->dev, n, Bmax,
+                                                mdl::FusedShape{threads, tile, blocks}, b->fst);
+        const cudaError_t ec = cudaStreamEndCapture(b->fst, &graph);
+        MDL_BCK(el);
+        MDL_BCK(ec);
+        const cudaError_t ei = cudaGraphInstantiate(&E->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        MDL_BCK(ei);
+        E->key = key;
+    }
+    MDL_BCK(cudaGraphLaunch(E->graph, b->fst));
+    b->fused_launches += 1 << Bmax;
+    return MDL_OK;
+}
+
+// Issue one fused round over the running slots `run` (each advances one barrier step);
+// completion is left to fused_complete().
+int fused_issue(mdl_batch* b, const std::vector<int>& run) {
     if (!b->fst) {
         MDL_BCK(cudaStreamCreateWithFlags(&b->fst, cudaStreamNonBlocking));
         MDL_BCK(cudaEventCreateWithFlags(&b->fev, cudaEventDisableTiming));
@@ -177,17 +269,22 @@ int fused_round(mdl_batch* b, const std::vector<int>& run, int64_t* total) {
     for (auto& g : b->groups) {
         g.members.clear();
         g.host.clear();
+        g.timed = false;
     }
-    // the phases before the sweep, each slot on its own stream
+    // the phases before the sweep, each slot on its own stream; a slot of a group tuned to
+    // own sweeps goes straight on with its sweep
     std::vector<int> Bs(b->slots.size(), 0);
     std::vector<int> begun;
     for (int i : run) {
         mdl_batch::Slot& s = b->slots[i];
         mdl_batch::Group& g = b->groups[s.group];
+        const int c = candidate(b, g);
+        s.own = c >= 0 ? c == kOwnCand : g.own;
         const size_t bytes = mdl::fused_slot_bytes(g.precision);
         const size_t off = g.host.size();
         g.host.resize(off + bytes);
-        const int rc = s.ctx->impl->fused_begin(g.host.data() + off, &Bs[i]);
+        int rc = s.ctx->impl->fused_begin(g.host.data() + off, &Bs[i]);
+        if (!rc && s.own && c < 0) rc = s.ctx->impl->fused_own_sweep();
         if (rc) {
             g.host.resize(off);
             s.state = MDL_SLOT_FAILED;
@@ -198,110 +295,149 @@ int fused_round(mdl_batch* b, const std::vector<int>& run, int64_t* total) {
         g.members.push_back(i);
         begun.push_back(i);
     }
-    // one fused sweep per (precision, family) group, from its captured graph
+    // per (precision, class) group: one fused sweep from its captured graph, or (timed
+    // while tuning) the slots' own sweeps
     const int nsm = sm_count();
-    cudaEvent_t t0[4] = {}, t1[4] = {};
-    for (int gi = 0; gi < 4; ++gi) {
-        mdl_batch::Group& g = b->groups[gi];
+    for (auto& g : b->groups) {
         const int n = (int)g.members.size();
         if (n == 0) continue;
+        const int c = candidate(b, g);
+        if (c < 0 && g.own) continue;
         if (n > mdl::FUSED_MAX_SLOTS) {
             b->err = "fused batch: too many slots in one group";
             return MDL_E_ARG;
         }
-        int Bmax = 0;
-        for (int i : g.members) Bmax = std::max(Bmax, Bs[i]);
-        const size_t bytes = mdl::fused_slot_bytes(g.precision);
-        for (int k = 0; k < n; ++k) mdl::fused_set_shift(g.host.data() + k * bytes, g.precision, Bmax - Bs[g.members[k]]);
-        if ((size_t)n > g.cap) {
-            if (g.graph) cudaGraphExecDestroy(g.graph);
-            g.graph = nullptr;
-            if (g.hpin) cudaFreeHost(g.hpin);
-            if (g.dev) cudaFree(g.dev);
-            g.hpin = nullptr;
-            g.dev = nullptr;
-            const size_t c = std::max<size_t>((size_t)n * 2, 16);
-            MDL_BCK(cudaMallocHost((void**)&g.hpin, c * bytes));
-            MDL_BCK(cudaMalloc(&g.dev, c * bytes));
-            g.cap = c;
-        }
-        memcpy(g.hpin, g.host.data(), (size_t)n * bytes);
-        MDL_BCK(cudaMemcpyAsync(g.dev, g.hpin, (size_t)n * bytes, cudaMemcpyHostToDevice, b->fst));
         for (int i : g.members) MDL_BCK(cudaStreamWaitEvent(b->fst, b->sev[i], 0));
-        // launch shape: the candidate being timed, else the tuned one
-        int threads = g.shape.threads, tile = g.shape.tile;
-        if (b->autotune && g.tuned >= 0) {
-            const int c = g.tuned / kRoundsPerCand;
-            threads = kFusedShapes[c][0];
-            tile = kFusedShapes[c][1];
+        if (c >= 0) {
+            if (!g.t0) {
+                MDL_BCK(cudaEventCreate(&g.t0));
+                MDL_BCK(cudaEventCreate(&g.t1));
+            }
+            MDL_BCK(cudaEventRecord(g.t0, b->fst));
+            g.timed = true;
         }
-        const int blocks = nsm * mdl::fused_blocks_per_sm(g.precision, g.family, threads);
-        const std::vector<long long> key{n, Bmax, threads, tile, blocks, (long long)(uintptr_t)g.dev};
-        if (!g.graph || key != g.key) {
-            if (g.graph) cudaGraphExecDestroy(g.graph);
-            g.graph = nullptr;
-            cudaGraph_t graph;
-            MDL_BCK(cudaStreamBeginCapture(b->fst, cudaStreamCaptureModeThreadLocal));
-            const cudaError_t el = mdl::fused_sweep(g.precision, g.family, g.dev, n, Bmax,
-                                                    mdl::FusedShape{threads, tile, blocks}, b->fst);
-            const cudaError_t ec = cudaStreamEndCapture(b->fst, &graph);
-            MDL_BCK(el);
-            MDL_BCK(ec);
-            const cudaError_t ei = cudaGraphInstantiate(&g.graph, graph, 0);
-            cudaGraphDestroy(graph);
-            MDL_BCK(ei);
-            g.key = key;
+        if (c == kOwnCand) {
+            for (int i : g.members) {
+                mdl_batch::Slot& s = b->slots[i];
+                cudaStream_t ss = (cudaStream_t)s.ctx->impl->stream_handle();
+                MDL_BCK(cudaStreamWaitEvent(ss, g.t0, 0));
+                const int rc = s.ctx->impl->fused_own_sweep();
+                if (rc) {
+                    s.state = MDL_SLOT_FAILED;
+                    s.rc = rc;
+                }
+                MDL_BCK(cudaEventRecord(b->sev[i], ss));
+                MDL_BCK(cudaStreamWaitEvent(b->fst, b->sev[i], 0));
+            }
+        } else {
+            int Bmax = 0;
+            for (int i : g.members) Bmax = std::max(Bmax, Bs[i]);
+            const size_t bytes = mdl::fused_slot_bytes(g.precision);
+            for (int k = 0; k < n; ++k)
+                mdl::fused_set_shift(g.host.data() + k * bytes, g.precision, Bmax - Bs[g.members[k]]);
+            const int threads = c >= 0 ? kFusedShapes[c][0] : g.shape.threads;
+            const int tile = c >= 0 ? kFusedShapes[c][1] : g.shape.tile;
+            const int rc = fused_group_sweep(b, g, n, Bmax, threads, tile, nsm);
+            if (rc) return rc;
         }
-        if (b->autotune && g.tuned >= 0) {
-            MDL_BCK(cudaEventCreate(&t0[gi]));
-            MDL_BCK(cudaEventCreate(&t1[gi]));
-            MDL_BCK(cudaEventRecord(t0[gi], b->fst));
-        }
-        MDL_BCK(cudaGraphLaunch(g.graph, b->fst));
-        if (t1[gi]) MDL_BCK(cudaEventRecord(t1[gi], b->fst));
-        b->fused_launches += 1 << Bmax;
+        if (c >= 0) MDL_BCK(cudaEventRecord(g.t1, b->fst));
     }
     MDL_BCK(cudaEventRecord(b->fev, b->fst));
-    // each slot's epilogue after the fused sweep, then completion
+    // each slot's epilogue after its sweep
     for (int i : begun) {
         mdl_batch::Slot& s = b->slots[i];
-        MDL_BCK(cudaStreamWaitEvent((cudaStream_t)s.ctx->impl->stream_handle(), b->fev, 0));
+        if (s.state == MDL_SLOT_FAILED) continue;
+        if (!s.own) MDL_BCK(cudaStreamWaitEvent((cudaStream_t)s.ctx->impl->stream_handle(), b->fev, 0));
         const int rc = s.ctx->impl->fused_finish();
         if (rc) {
             s.state = MDL_SLOT_FAILED;
             s.rc = rc;
         }
     }
-    for (int i : begun) {
+    b->fused_rounds++;
+    return MDL_OK;
+}
+
+// Wait for the rounds issued since the last completion: complete every slot that took part
+// and, while tuning, add the round's timings to the candidates (after the last, keep the best).
+int fused_complete(mdl_batch* b, const std::vector<char>& took_part, int64_t* total) {
+    for (size_t i = 0; i < b->slots.size(); ++i) {
         mdl_batch::Slot& s = b->slots[i];
-        if (s.state == MDL_SLOT_FAILED) continue;
+        if (!took_part[i] || s.state == MDL_SLOT_FAILED) continue;
         int64_t c = 0;
         const int rc = s.ctx->impl->end_barriers(&c);
         settle(s, rc, c, total);
     }
-    MDL_BCK(cudaStreamSynchronize(b->fst));
-    // the tuner: add this round's sweep time to its candidate; after the last, keep the best
-    for (int gi = 0; gi < 4; ++gi) {
-        mdl_batch::Group& g = b->groups[gi];
-        if (!t0[gi]) continue;
+    if (b->fst) MDL_BCK(cudaStreamSynchronize(b->fst));
+    for (auto& g : b->groups) {
+        if (!g.timed) continue;
+        g.timed = false;
         float ms = 0;
-        cudaEventElapsedTime(&ms, t0[gi], t1[gi]);
-        cudaEventDestroy(t0[gi]);
-        cudaEventDestroy(t1[gi]);
+        MDL_BCK(cudaEventElapsedTime(&ms, g.t0, g.t1));
         const int c = g.tuned / kRoundsPerCand;
-        if ((int)g.cand_ms.size() < kFusedCands) g.cand_ms.assign(kFusedCands, 0.0);
+        if ((int)g.cand_ms.size() < kCands) g.cand_ms.assign(kCands, 0.0);
         g.cand_ms[c] += ms;
-        if (++g.tuned == kFusedCands * kRoundsPerCand) {
+        if (++g.tuned == kCands * kRoundsPerCand) {
             int best = 0;
-            for (int k = 1; k < kFusedCands; ++k)
+            for (int k = 1; k < kCands; ++k)
                 if (g.cand_ms[k] < g.cand_ms[best]) best = k;
-            g.shape = mdl::FusedShape{kFusedShapes[best][0], kFusedShapes[best][1], 0};
+            g.own = best == kOwnCand;
+            if (!g.own) g.shape = mdl::FusedShape{kFusedShapes[best][0], kFusedShapes[best][1], 0};
             g.best_ms = g.cand_ms[best] / kRoundsPerCand;
             g.worst_ms = *std::max_element(g.cand_ms.begin(), g.cand_ms.end()) / kRoundsPerCand;
+            g.own_ms = g.cand_ms[kOwnCand] / kRoundsPerCand;
             g.tuned = -1;
         }
     }
-    b->fused_rounds++;
+    return MDL_OK;
+}
+
+// `rounds` fused rounds (fewer for slots that reach their horizon), issued back to back and
+// completed once; while a group is still tuning, each round is completed on its own.
+int fused_step(mdl_batch* b, int64_t rounds, int64_t* total) {
+    std::vector<int64_t> left(b->slots.size(), 0);
+    for (size_t i = 0; i < b->slots.size(); ++i) {
+        mdl_batch::Slot& s = b->slots[i];
+        if (s.state != MDL_SLOT_RUNNING) continue;
+        double t = 0, dt = 0;
+        int64_t nb = 0;
+        s.ctx->impl->get_time(&t, &nb, &dt);
+        left[i] = std::min(rounds, barriers_to(dt, t, s.t_end));
+        if (left[i] <= 0) s.state = MDL_SLOT_DONE;
+    }
+    std::vector<char> took(b->slots.size(), 0);
+    bool pending = false;
+    for (int64_t r = 0; r < rounds; ++r) {
+        std::vector<int> run;
+        for (size_t i = 0; i < b->slots.size(); ++i) {
+            mdl_batch::Slot& s = b->slots[i];
+            if (s.state != MDL_SLOT_RUNNING || left[i] <= 0) continue;
+            // replayed inputs hold for one barrier: such a slot takes one round per completion
+            if (took[i] && s.ctx->impl->replaying()) continue;
+            run.push_back((int)i);
+        }
+        if (run.empty()) break;
+        const bool sync_each = tuning(b);
+        int rc = fused_issue(b, run);
+        for (int i : run) {
+            took[i] = 1;
+            --left[i];
+        }
+        pending = true;
+        if (rc) {
+            fused_complete(b, took, total);
+            return rc;
+        }
+        if (sync_each || tuning(b)) {
+            if ((rc = fused_complete(b, took, total))) return rc;
+            std::fill(took.begin(), took.end(), 0);
+            pending = false;
+            // horizons and failures as of this completion
+            for (size_t i = 0; i < b->slots.size(); ++i)
+                if (b->slots[i].state != MDL_SLOT_RUNNING) left[i] = 0;
+        }
+    }
+    if (pending) return fused_complete(b, took, total);
     return MDL_OK;
 }
 
@@ -325,9 +461,9 @@ int mdl_batch_create(int64_t hbm_budget_bytes, int autotune, mdl_batch** out) {
     }
     b->budget = hbm_budget_bytes;
     b->autotune = autotune ? 1 : 0;
-    for (int gi = 0; gi < 4; ++gi) {
-        b->groups[gi].precision = gi >= 2 ? 64 : 32;
-        b->groups[gi].family = 1 + (gi & 1);
+    for (int gi = 0; gi < 8; ++gi) {
+        b->groups[gi].precision = gi >= 4 ? 64 : 32;
+        b->groups[gi].cls = gi & 3;
         b->groups[gi].tuned = b->autotune ? 0 : -1;
     }
     *out = b;
@@ -404,7 +540,7 @@ int mdl_batch_admit(mdl_batch* b, const mdl_problem* prob, const double* V0, con
     mdl_batch::Slot& s = b->slots[id];
     s = mdl_batch::Slot{};
     s.ctx = c;
-    s.group = (prob->precision == 64 ? 2 : 0) + (mdl::fused_family(prob->order) - 1);
+    s.group = (prob->precision == 64 ? 4 : 0) + mdl::fused_class(prob->dim, prob->order);
     s.t_end = t_end;
     s.bytes = std::max<int64_t>(est, c->impl->device_bytes());
     double t = 0, dt = 0;
@@ -424,26 +560,10 @@ int mdl_batch_step(mdl_batch* b, int64_t barriers_per_slot, double wall_budget_s
     int64_t total = 0;
     if (b->fused) {
         for (;;) {
-            for (int64_t r = 0; r < barriers_per_slot; ++r) {
-                std::vector<int> run;
-                for (size_t i = 0; i < b->slots.size(); ++i) {
-                    mdl_batch::Slot& s = b->slots[i];
-                    if (s.state != MDL_SLOT_RUNNING) continue;
-                    double t = 0, dt = 0;
-                    int64_t nb = 0;
-                    s.ctx->impl->get_time(&t, &nb, &dt);
-                    if (barriers_to(dt, t, s.t_end) <= 0) {
-                        s.state = MDL_SLOT_DONE;
-                        continue;
-                    }
-                    run.push_back((int)i);
-                }
-                if (run.empty()) break;
-                const int rc = fused_round(b, run, &total);
-                if (rc) {
-                    if (barriers_done) *barriers_done = total;
-                    return rc;
-                }
+            const int rc = fused_step(b, barriers_per_slot, &total);
+            if (rc) {
+                if (barriers_done) *barriers_done = total;
+                return rc;
             }
             b->steps++;
             bool any = false;
@@ -563,17 +683,21 @@ int mdl_batch_set_fused(mdl_batch* b, int32_t on) {
     return MDL_OK;
 }
 
-int mdl_batch_fused_info(const mdl_batch* b, int32_t precision, int32_t order, int32_t* threads, int32_t* tile,
-                         double* best_ms, double* worst_ms, int64_t* rounds, int64_t* launches) {
-    if (!b || (precision != 32 && precision != 64) || (order != 1 && order != 2)) return MDL_E_ARG;
+int mdl_batch_fused_info(const mdl_batch* b, int32_t precision, int32_t dim, int32_t order, int32_t* own,
+                         int32_t* threads, int32_t* tile, double* best_ms, double* worst_ms, double* own_ms,
+                         int64_t* rounds, int64_t* launches) {
+    if (!b || (precision != 32 && precision != 64) || (dim != 2 && dim != 3) || (order != 1 && order != 2))
+        return MDL_E_ARG;
     if (rounds) *rounds = b->fused_rounds;
     if (launches) *launches = b->fused_launches;
-    const mdl_batch::Group& g = b->groups[(precision == 64 ? 2 : 0) + (mdl::fused_family(order) - 1)];
+    const mdl_batch::Group& g = b->groups[(precision == 64 ? 4 : 0) + mdl::fused_class(dim, order)];
     if (g.tuned != -1) return MDL_E_STATE;
+    if (own) *own = g.own ? 1 : 0;
     if (threads) *threads = g.shape.threads;
     if (tile) *tile = g.shape.tile;
     if (best_ms) *best_ms = g.best_ms;
     if (worst_ms) *worst_ms = g.worst_ms;
+    if (own_ms) *own_ms = g.own_ms;
     return MDL_OK;
 }
 

@@ -39,9 +39,6 @@ int check_problem(const mdl_problem* p, std::string* why) {
     if (!(p->dt_barrier >= 0)) { *why = "dt_barrier must be >= 0"; return MDL_E_ARG; }
     if (p->precision != 32 && p->precision != 64) { *why = "precision must be 32 or 64"; return MDL_E_ARG; }
     if (p->state_integrator != 0 && p->state_integrator != 1) { *why = "state_integrator must be 0 or 1"; return MDL_E_ARG; }
-    double cells = 1.0;
-    for (int k = 0; k < p->dim; ++k) cells *= (double)p->base[k] * (double)(1 << p->max_refine);
-    if (cells > 1.5e9) { *why = "finest grid too large for the owner map"; return MDL_E_ARG; }
     double roots = 1.0;
     for (int k = 0; k < p->dim; ++k) roots *= p->base[k];
     if (roots * 27.0 > 2.0e9) { *why = "too many roots"; return MDL_E_ARG; }
@@ -68,23 +65,21 @@ CtxBase* make_ctx(const mdl_problem& pr) {
 }
 
 // Device bytes of a freshly created context: per-element arrays at the initial capacity
-// (twice the roots, or four times with adaptation), the finest owner map and the probes.
+// (twice the roots, or four times with adaptation, each with its 8-byte leaf key) and the
+// probes.
 int64_t estimate_footprint(const mdl_problem& p) {
     const int d = p.dim, n1 = p.order + 1;
     const int64_t np0 = d == 2 ? n1 * n1 : n1 * n1 * n1;
     const int64_t np = np0 == 27 ? 28 : np0;   // row stride of the per-DOF arrays (Q2 3D padded)
     const int64_t nf = 2 * d, nsub = 1 << (d - 1);
-    int64_t roots = 1, fine = 1;
-    for (int k = 0; k < d; ++k) {
-        roots *= p.base[k];
-        fine *= (int64_t)p.base[k] << p.max_refine;
-    }
+    int64_t roots = 1;
+    for (int k = 0; k < d; ++k) roots *= p.base[k];
     const int64_t cap = std::max<int64_t>(roots * (p.amr_enabled ? 4 : 2), 4096);
     const int64_t r = p.precision == 64 ? 8 : 4;
     const int64_t per_set = 3 * np * r + 8 + 1 + 16;
     const int64_t shared = 2 * np * r + 8 + 8 + 1 + 1 + 8 + 1 + 1 + 4 + 4;
-    const int64_t tables = 1 + 4 + 4 + 4 * nf + 4 * nf * nsub + 4 + 4 + 4 * p.n_stim;
-    return cap * (2 * per_set + shared + tables) + fine * 4 + roots * np0 * 8 + (1 << 20);
+    const int64_t tables = 1 + 4 + 4 + 4 * nf + 4 * nf * nsub + 4 + 4 + 4 * p.n_stim + 8;
+    return cap * (2 * per_set + shared + tables) + roots * np0 * 8 + (1 << 20);
 }
 
 }  // namespace mdl

@@ -43,10 +43,15 @@ public:
     // Fused batch rounds (mdl_fused.h): launch the phases before the sweep (indicator,
     // adaptation, levels, ordering) of one barrier on the context's stream and write the
     // slot's sweep record (a FusedSlot of the context's precision, shift left 0) and its LTS
-    // level count B; after the batch's fused sweep, launch the epilogue.  end_barriers()
-    // then completes the barrier as after begin_barriers(1).
+    // level count B; after the batch's fused sweep (or after fused_own_sweep(), the
+    // context's own sweep variant on its own stream), launch the epilogue.  Several rounds
+    // may be issued before end_barriers(), which then completes them as after
+    // begin_barriers(rounds).  A context with replayed inputs (set_levels, set_indicators)
+    // takes one round per end_barriers(); replaying() says so.
     virtual int fused_begin(void* slot_record, int* B) = 0;
+    virtual int fused_own_sweep() = 0;
     virtual int fused_finish() = 0;
+    virtual bool replaying() const = 0;
     virtual void* stream_handle() const = 0;
     virtual int precision() const = 0;
     virtual int64_t device_bytes() const = 0;     // device memory held by the context

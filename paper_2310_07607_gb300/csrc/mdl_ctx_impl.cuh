@@ -7,7 +7,7 @@
 // the host never waits inside a barrier:
 //   [AMR]  k_eta_s, k_amr_mark, k_amr_close x max_refine, k_amr_family, k_scan_blocks,
 //          k_scan_top (commit), k_scan_emit (coordinates into the other state set),
-//          k_owner_fill + k_mesh_tables + k_lat_refresh (in place, only if the mesh changed),
+//          k_leaf_keys + k_mesh_tables + k_lat_refresh (in place, only if the mesh changed),
 //          k_transfer (state into the other set)
 //   levels k_levels_count, k_order_top, k_order_scatter
 //   sweep  2^B launches of k_tick (each reads its due count from DevMeta)
@@ -120,7 +120,8 @@ class Ctx : public CtxBase {
     DBuf<float> fscratch;   // FP32 field transfers
     DBuf<R> cview;          // compact copy handed out by device_view for padded rows
     DBuf<uint8_t> r, c0, class_b;
-    DBuf<int32_t> owner, bcnt, psrc;
+    DBuf<int32_t> bcnt, psrc;
+    DBuf<uint64_t> lkey;      // sort key of every leaf (neighbour search of the mesh tables)
     DBuf<int64_t> bsum;
     // mesh tables (single copies)
     DBuf<uint8_t> bcfl;
@@ -138,6 +139,7 @@ class Ctx : public CtxBase {
     DBuf<Tables<R>> dT;       // device copies of the tables and physics (fused batch sweeps)
     DBuf<Phys<R>> dph;
     int fused_cur = 0;        // state set the fused sweep of the barrier in flight updates
+    bool fused_own = false;   // this round's sweep is the context's own (fused_own_sweep)
     DevMeta* hmeta = nullptr;
     bool ovr_levels = false, ovr_eta_s = false, ovr_eta_t = false;
     bool timing = false;
@@ -234,6 +236,7 @@ class Ctx : public CtxBase {
         MDL_CK(hang.ensure((size_t)c * NF * NSUB));
         MDL_CK(root.ensure(c));
         MDL_CK(order.ensure(c));
+        MDL_CK(lkey.ensure(c));
         for (int s = 0; s < pb.n_stim; ++s) MDL_CK(smask[s].ensure(c));
         return MDL_OK;
     }
@@ -276,7 +279,7 @@ class Ctx : public CtxBase {
         MDL_GROW(x.V0, NPS); MDL_GROW(x.V1, NPS); MDL_GROW(x.v, NPS); MDL_GROW(x.eta_t, 1);
         MDL_GROW(x.lvl, 1); MDL_GROW(x.coord, 1);
         MDL_GROW(bcfl, 1); MDL_GROW(info, 1); MDL_GROW(loc, 1); MDL_GROW(nbr, NF); MDL_GROW(hang, NF * NSUB);
-        MDL_GROW(root, 1); MDL_GROW(order, 1);
+        MDL_GROW(root, 1); MDL_GROW(order, 1); MDL_GROW(lkey, 1);
         for (int s = 0; s < pb.n_stim; ++s) MDL_GROW(smask[s], 1);
         MDL_GROW(eta_s, 1);
 #undef MDL_GROW
@@ -313,10 +316,10 @@ class Ctx : public CtxBase {
     int build_tables(int s, int force) {
         Set& x = sets[s];
         const int gb = persistent_blocks(256);
-        MDL_CK(launch_k((k_owner_fill<DIM>), nsm * 8, 256, x.coord.p, owner.p, grid_, meta.p, force));
+        MDL_CK(launch_k((k_leaf_keys<DIM>), persistent_blocks(256), 256, x.coord.p, lkey.p, grid_, meta.p, force));
         MDL_LAUNCHED();
         MDL_CK(launch_k((k_mesh_tables<R, DIM, P>), persistent_blocks(128), 128, 
-            x.coord.p, owner.p, grid_, info.p, nbr.p, hang.p, root.p, loc.p, bcfl.p, class_b.p,
+            x.coord.p, lkey.p, grid_, info.p, nbr.p, hang.p, root.p, loc.p, bcfl.p, class_b.p,
             smask[0].p, smask[1].p, smask[2].p, smask[3].p, sboxes, phd, meta.p, force));
         MDL_LAUNCHED();
         return MDL_OK;
@@ -600,7 +603,7 @@ public:
         drop_graphs();
         for (auto& s : sets) s.release();
         Ia.release(); ga.release(); acc.release(); eta_s.release(); lat.release(); partial.release();
-        scratch.release(); fscratch.release(); cview.release(); r.release(); c0.release(); class_b.release(); owner.release();
+        scratch.release(); fscratch.release(); cview.release(); r.release(); c0.release(); class_b.release(); lkey.release();
         bcnt.release(); psrc.release(); bsum.release(); pkind.release(); pbits.release();
         bcfl.release(); info.release(); loc.release(); nbr.release(); hang.release(); root.release();
         order.release();
@@ -634,7 +637,6 @@ public:
         }
         grid_.L = pb.max_refine;
         grid_.dim = DIM;
-        MDL_CK(owner.ensure((size_t)(grid_.fine[0] * grid_.fine[1] * grid_.fine[2])));
         // stimulus boxes (inclusion slack applied here, once) and time windows
         sboxes.n = pb.n_stim;
         stim.n = pb.n_stim;
@@ -963,12 +965,13 @@ public:
     }
 
     int fused_begin(void* slot_record, int* Bout) override {
-        if (inflight) {
-            err = "fused_begin: barriers already in flight";
+        const bool direct = ovr_levels || ovr_eta_s || ovr_eta_t;
+        if (inflight && direct) {
+            err = "fused_begin: replayed inputs apply to one barrier per completion";
             return MDL_E_STATE;
         }
-        inflight_start = nbar;
-        const bool direct = ovr_levels || ovr_eta_s || ovr_eta_t;
+        if (!inflight) inflight_start = nbar;
+        fused_own = false;
         const int o = cs;
         int rc;
         if (pb.amr_enabled && !ovr_eta_s && (rc = run_phase(0, o, direct))) return rc;
@@ -984,14 +987,27 @@ public:
         return MDL_OK;
     }
 
-    int fused_finish() override {
+    int fused_own_sweep() override {
         const bool direct = ovr_levels || ovr_eta_s || ovr_eta_t;
-        int rc = run_phase(3, fused_cur, direct);
+        int rc = run_phase(2, fused_cur, direct);
         if (rc) return rc;
-        cs = fused_cur;
-        inflight = 1;
+        fused_own = true;
         return MDL_OK;
     }
+
+    int fused_finish() override {
+        const bool direct = ovr_levels || ovr_eta_s || ovr_eta_t;
+        // the cooperative sweep runs the epilogue itself
+        if (!(fused_own && coop_sweep)) {
+            int rc = run_phase(3, fused_cur, direct);
+            if (rc) return rc;
+        }
+        cs = fused_cur;
+        inflight += 1;
+        return MDL_OK;
+    }
+
+    bool replaying() const override { return ovr_levels || ovr_eta_s || ovr_eta_t; }
 
     void* stream_handle() const override { return (void*)st; }
     int precision() const override { return sizeof(R) == 8 ? 64 : 32; }
@@ -1008,7 +1024,8 @@ public:
         add(fscratch.cap, 4);
         add(cview.cap, sizeof(R));
         add(r.cap + c0.cap + class_b.cap + bcfl.cap + pkind.cap + pbits.cap + lvl_ovr.cap, 1);
-        add(owner.cap + bcnt.cap + psrc.cap + nbr.cap + hang.cap + root.cap + order.cap + info.cap + loc.cap, 4);
+        add(bcnt.cap + psrc.cap + nbr.cap + hang.cap + root.cap + order.cap + info.cap + loc.cap, 4);
+        add(lkey.cap, 8);
         for (const auto& m : smask) add(m.cap, 4);
         add(bsum.cap, 8);
         return b;

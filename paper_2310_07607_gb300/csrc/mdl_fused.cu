@@ -20,7 +20,7 @@ __device__ __forceinline__ void fused_range(const FusedSlot<R>& fs, int tick, in
 // of the slot's ticks, its tick there and its due count (fixed during the sweep: written by
 // the slot's ordering phase before the round's first tick), and the prefix sums of the work
 // items; then walks work items t = block, block + grid, ...
-template <typename R, int FAM>
+template <typename R, int CLS>
 __global__ void __launch_bounds__(256) k_tick_fused(const FusedSlot<R>* __restrict__ slots, int nslot, int g,
                                                    int tile) {
     __shared__ int sOff[FUSED_MAX_SLOTS + 1];
@@ -55,20 +55,15 @@ __global__ void __launch_bounds__(256) k_tick_fused(const FusedSlot<R>* __restri
             else hi = mid;
         }
         const int s = lo;
-        const FusedSlot<R>& fs = slots[s];
         const int e0 = (t - sOff[s]) * tile;
         const int e1 = min(e0 + tile, sCnt[s]);
-        if constexpr (FAM == 1) {
-            if (fs.cls == FC_2_1) fused_range<R, 2, 1>(fs, sTick[s], e0, e1);
-            else fused_range<R, 3, 1>(fs, sTick[s], e0, e1);
-        } else {
-            if (fs.cls == FC_2_2) fused_range<R, 2, 2>(fs, sTick[s], e0, e1);
-            else fused_range<R, 3, 2>(fs, sTick[s], e0, e1);
-        }
+        constexpr int DIM = (CLS == FC_3_1 || CLS == FC_3_2) ? 3 : 2;
+        constexpr int P = (CLS == FC_2_2 || CLS == FC_3_2) ? 2 : 1;
+        fused_range<R, DIM, P>(slots[s], sTick[s], e0, e1);
     }
 }
 
-template <typename R, int FAM>
+template <typename R, int CLS>
 cudaError_t launch_round(const void* d_slots, int nslot, int Bmax, FusedShape sh, cudaStream_t st) {
     const FusedSlot<R>* p = static_cast<const FusedSlot<R>*>(d_slots);
     for (int g = 0; g < (1 << Bmax); ++g) {
@@ -81,7 +76,7 @@ cudaError_t launch_round(const void* d_slots, int nslot, int Bmax, FusedShape sh
         at[0].val.programmaticStreamSerializationAllowed = g > 0 ? 1 : 0;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, k_tick_fused<R, FAM>, p, nslot, g, sh.tile);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_tick_fused<R, CLS>, p, nslot, g, sh.tile);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -98,30 +93,50 @@ void fused_set_shift(void* record, int precision, int shift) {
     else static_cast<FusedSlot<float>*>(record)->shift = shift;
 }
 
-int fused_family(int order) { return order == 1 ? 1 : 2; }
+int fused_class(int dim, int order) {
+    return dim == 2 ? (order == 1 ? FC_2_1 : FC_2_2) : (order == 1 ? FC_3_1 : FC_3_2);
+}
 
-int fused_blocks_per_sm(int precision, int family, int threads) {
+namespace {
+
+template <typename R>
+int blocks_per_sm(int cls, int threads) {
     int n = 0;
-    cudaError_t e;
-    if (precision == 64)
-        e = family == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tick_fused<double, 1>, threads, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tick_fused<double, 2>, threads, 0);
-    else
-        e = family == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tick_fused<float, 1>, threads, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tick_fused<float, 2>, threads, 0);
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (cls) {
+        case FC_2_1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tick_fused<R, FC_2_1>, threads, 0); break;
+        case FC_2_2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tick_fused<R, FC_2_2>, threads, 0); break;
+        case FC_3_1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tick_fused<R, FC_3_1>, threads, 0); break;
+        case FC_3_2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tick_fused<R, FC_3_2>, threads, 0); break;
+        default: break;
+    }
     return e == cudaSuccess && n > 0 ? n : 1;
 }
 
-cudaError_t fused_sweep(int precision, int family, const void* d_slots, int nslot, int Bmax, FusedShape shape,
+template <typename R>
+cudaError_t sweep(int cls, const void* d_slots, int nslot, int Bmax, FusedShape sh, cudaStream_t st) {
+    switch (cls) {
+        case FC_2_1: return launch_round<R, FC_2_1>(d_slots, nslot, Bmax, sh, st);
+        case FC_2_2: return launch_round<R, FC_2_2>(d_slots, nslot, Bmax, sh, st);
+        case FC_3_1: return launch_round<R, FC_3_1>(d_slots, nslot, Bmax, sh, st);
+        case FC_3_2: return launch_round<R, FC_3_2>(d_slots, nslot, Bmax, sh, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+int fused_blocks_per_sm(int precision, int cls, int threads) {
+    return precision == 64 ? blocks_per_sm<double>(cls, threads) : blocks_per_sm<float>(cls, threads);
+}
+
+cudaError_t fused_sweep(int precision, int cls, const void* d_slots, int nslot, int Bmax, FusedShape shape,
                         cudaStream_t st) {
     if (nslot <= 0 || nslot > FUSED_MAX_SLOTS || Bmax < 0 || Bmax > 7 || shape.threads <= 0 ||
-        shape.threads > 256 || shape.tile <= 0 || shape.blocks <= 0 || (family != 1 && family != 2))
+        shape.threads > 256 || shape.tile <= 0 || shape.blocks <= 0 || cls < FC_2_1 || cls > FC_3_2)
         return cudaErrorInvalidValue;
-    if (precision == 64)
-        return family == 1 ? launch_round<double, 1>(d_slots, nslot, Bmax, shape, st)
-                           : launch_round<double, 2>(d_slots, nslot, Bmax, shape, st);
-    return family == 1 ? launch_round<float, 1>(d_slots, nslot, Bmax, shape, st)
-                       : launch_round<float, 2>(d_slots, nslot, Bmax, shape, st);
+    return precision == 64 ? sweep<double>(cls, d_slots, nslot, Bmax, shape, st)
+                           : sweep<float>(cls, d_slots, nslot, Bmax, shape, st);
 }
 
 }  // namespace mdl

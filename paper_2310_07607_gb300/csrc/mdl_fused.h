@@ -3,8 +3,8 @@
 // A batch round advances every running slot by one barrier step (Alg. 1).  Each slot runs
 // its own indicator, adaptation, level and ordering phases and its own epilogue on its own
 // stream; the sweep between them is fused: for every global tick g = 0 .. 2^Bmax - 1 one
-// persistent kernel launch per element family (Q1, Q2) and precision covers the due
-// elements of every slot whose tick grid contains g
+// persistent kernel launch per element class (2D/3D, Q1/Q2) and precision covers the due
+// elements of every slot of that class whose tick grid contains g
 // (a slot with B LTS levels above level 0 takes its tick g 2^(B - Bmax) when 2^(Bmax - B)
 // divides g), walking work items of `tile` consecutive due elements of one slot.  Each
 // element takes the same element step as the slot's own thread-per-element sweep.

@@ -20,16 +20,16 @@ struct FusedShape {
 size_t fused_slot_bytes(int precision);
 // Write the record's shift (Bmax - B: the slot takes part in global ticks divisible by 2^shift).
 void fused_set_shift(void* record, int precision, int shift);
-// Element family of an order: 1 (Q1, 2D and 3D) or 2 (Q2).  One fused kernel serves each
-// family: one kernel for all four element classes would take the register budget of the Q2
-// element step (255 registers, spilling) for the Q1 elements too.
-int fused_family(int order);
-// Resident blocks per SM of the family's fused kernel at `threads` per block (occupancy API).
-int fused_blocks_per_sm(int precision, int family, int threads);
-// Launch the 2^Bmax global ticks of one fused round of a family on `st` (d_slots: nslot
-// records of that family in device memory).  Returns a CUDA error code; each slot's own
+// Element class of a (dimension, order): 0 (2D Q1), 1 (2D Q2), 2 (3D Q1), 3 (3D Q2).  One
+// fused kernel serves each class, so each compiles with its own element step's register
+// budget (the 3D Q2 step takes 255 registers; the 2D Q1 step about half of that).
+int fused_class(int dim, int order);
+// Resident blocks per SM of the class's fused kernel at `threads` per block (occupancy API).
+int fused_blocks_per_sm(int precision, int cls, int threads);
+// Launch the 2^Bmax global ticks of one fused round of a class on `st` (d_slots: nslot
+// records of that class in device memory).  Returns a CUDA error code; each slot's own
 // errors stay in its device bookkeeping.
-cudaError_t fused_sweep(int precision, int family, const void* d_slots, int nslot, int Bmax, FusedShape shape,
+cudaError_t fused_sweep(int precision, int cls, const void* d_slots, int nslot, int Bmax, FusedShape shape,
                         cudaStream_t st);
 
 }  // namespace mdl

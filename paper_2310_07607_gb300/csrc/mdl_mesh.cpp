@@ -59,46 +59,60 @@ bool Mesh::set_leaves(std::vector<Leaf> lv, std::string* err) {
     return rebuild(err);
 }
 
+uint64_t Mesh::cell_key(const int64_t* fc) const {
+    uint64_t loc[3] = {0, 0, 0};
+    int64_t r[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) {
+        r[k] = fc[k] >> L;
+        loc[k] = (uint64_t)(fc[k] - (r[k] << L));
+    }
+    uint64_t m = 0;
+    for (int bit = 0; bit < L; ++bit)
+        for (int k = 0; k < dim; ++k) m |= ((loc[k] >> bit) & 1ull) << (bit * dim + k);
+    const uint64_t rid = (uint64_t)(r[0] + (int64_t)base[0] * (r[1] + (int64_t)base[1] * r[2]));
+    return (rid << (dim * L)) | m;
+}
+
+int32_t Mesh::leaf_of(const int64_t* fc) const {
+    const uint64_t k = cell_key(fc);
+    return (int32_t)(std::upper_bound(keys.begin(), keys.end(), k) - keys.begin()) - 1;
+}
+
 bool Mesh::rebuild(std::string* err) {
-    const int64_t nf = fine[0] * fine[1] * fine[2];
-    owner.assign(nf, -1);
+    // The leaves, sorted by key, tile the slab exactly when each one starts where the one
+    // before it ends (a leaf of level l spans 2^(d (L - l)) consecutive finest-cell keys)
+    // and together they span every root.
     for (int64_t i = 0; i < n(); ++i) {
         const Leaf& lf = leaves[i];
         if (lf.level < 0 || lf.level > L) {
             if (err) *err = "leaf level out of range";
             return false;
         }
-        const int sh = L - lf.level;
-        int64_t lo[3], hi[3];
-        for (int k = 0; k < 3; ++k) {
-            if (k < dim) {
-                lo[k] = (int64_t)lf.c[k] << sh;
-                hi[k] = lo[k] + ((int64_t)1 << sh);
-                if (lf.c[k] < 0 || hi[k] > fine[k]) {
-                    if (err) *err = "leaf outside the slab";
-                    return false;
-                }
-            } else {
-                lo[k] = 0;
-                hi[k] = 1;
+        for (int k = 0; k < dim; ++k)
+            if (lf.c[k] < 0 || lf.c[k] >= ((int64_t)base[k] << lf.level)) {
+                if (err) *err = "leaf outside the slab";
+                return false;
             }
-        }
-        for (int64_t z = lo[2]; z < hi[2]; ++z)
-            for (int64_t y = lo[1]; y < hi[1]; ++y)
-                for (int64_t x = lo[0]; x < hi[0]; ++x) {
-                    int32_t& o = owner[x + fine[0] * (y + fine[1] * z)];
-                    if (o != -1) {
-                        if (err) *err = "leaves overlap";
-                        return false;
-                    }
-                    o = (int32_t)i;
-                }
     }
-    for (int64_t c = 0; c < nf; ++c)
-        if (owner[c] < 0) {
+    uint64_t next = 0;
+    for (int64_t i = 0; i < n(); ++i) {
+        const Leaf& lf = leaves[i];
+        if (keys[i] < next) {
+            if (err) *err = "leaves overlap";
+            return false;
+        }
+        if (keys[i] > next) {
             if (err) *err = "leaves do not cover the slab";
             return false;
         }
+        next = keys[i] + (1ull << (dim * (L - lf.level)));
+    }
+    int64_t nroots = 1;
+    for (int k = 0; k < dim; ++k) nroots *= base[k];
+    if (next != ((uint64_t)nroots << (dim * L))) {
+        if (err) *err = "leaves do not cover the slab";
+        return false;
+    }
     const int NF = nfaces(), NS = nsub();
     kind.assign(n() * NF, F_BOUNDARY);
     pos.assign(n() * NF, 0);
@@ -142,7 +156,7 @@ int Mesh::neighbour(int64_t i, int axis, int side, int32_t* out, int* posbits) c
     int64_t fc[3];
     for (int k = 0; k < 3; ++k) fc[k] = (k < dim) ? (cn[k] << sh) : 0;
     if (side < 0) fc[axis] = ((cn[axis] + 1) << sh) - 1;
-    const int32_t o = owner[fc[0] + fine[0] * (fc[1] + fine[1] * fc[2])];
+    const int32_t o = leaf_of(fc);
     const int lo = leaves[o].level;
     int tg[2], nt = 0;
     for (int k = 0; k < dim; ++k)
@@ -168,7 +182,7 @@ int Mesh::neighbour(int64_t i, int axis, int side, int32_t* out, int* posbits) c
         for (int t = 0; t < nt; ++t) ch[tg[t]] = 2 * (int64_t)lf.c[tg[t]] + ((b >> t) & 1);
         int64_t f2[3];
         for (int k = 0; k < 3; ++k) f2[k] = (k < dim) ? (ch[k] << shc) : 0;
-        const int32_t oc = owner[f2[0] + fine[0] * (f2[1] + fine[1] * f2[2])];
+        const int32_t oc = leaf_of(f2);
         if (leaves[oc].level != l + 1) return -1;
         out[b] = oc;
     }

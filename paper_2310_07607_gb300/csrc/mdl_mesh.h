@@ -27,8 +27,7 @@ struct Mesh {
     int base[3] = {1, 1, 1};
     int64_t fine[3] = {1, 1, 1};
     std::vector<Leaf> leaves;
-    std::vector<uint64_t> keys;
-    std::vector<int32_t> owner;       // finest cell -> leaf index (-1 unset)
+    std::vector<uint64_t> keys;       // sort key of each leaf: root id, Morton index of its lower corner
     // face table, 2*dim faces per leaf
     std::vector<int8_t> kind;         // FaceKind
     std::vector<int8_t> pos;          // tangential position bits on a coarser face
@@ -46,8 +45,11 @@ struct Mesh {
     int64_t root_id(const Leaf& lf) const;
     // Replace leaves (sorted internally); returns false + message if not a balanced tiling.
     bool set_leaves(std::vector<Leaf> lv, std::string* err);
-    // Rebuild owner grid and face tables from `leaves`.
+    // Check the tiling and rebuild the face tables from `leaves` and `keys`.
     bool rebuild(std::string* err);
+    // Key of the finest cell at fc, and the leaf that holds it (leaves must tile the slab).
+    uint64_t cell_key(const int64_t* fc) const;
+    int32_t leaf_of(const int64_t* fc) const;
     // Neighbour of leaf i across face (axis, side): kind, and data (neighbour index or
     // subface leaf list).
     int neighbour(int64_t i, int axis, int side, int32_t* out, int* posbits) const;

@@ -135,8 +135,8 @@ def load(path: Optional[str] = None):
     lib.mdl_batch_release.argtypes = [vp, C.c_int32]
     lib.mdl_batch_usage.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), i32p]
     lib.mdl_batch_set_fused.argtypes = [vp, C.c_int32]
-    lib.mdl_batch_fused_info.argtypes = [vp, C.c_int32, C.c_int32, i32p, i32p, dp, dp, C.POINTER(i64),
-                                         C.POINTER(i64)]
+    lib.mdl_batch_fused_info.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, i32p, i32p, i32p, dp, dp, dp,
+                                         C.POINTER(i64), C.POINTER(i64)]
     lib.mdl_batch_shape.argtypes = [vp, C.POINTER(CProblem), i32p, i32p]
     lib.mdl_batch_last_error.argtypes = [vp]
     lib.mdl_batch_last_error.restype = C.c_char_p
@@ -399,18 +399,24 @@ class Batch:
         self.problems = {}
         self._check(self.lib.mdl_batch_set_fused(self.h, 1 if fused else 0))
 
-    def fused_info(self, precision: int = 32, order: int = 1):
-        """(threads, tile, best_ms, worst_ms) of the group's tuned fused sweep, or None before the
-        tuner finished; and the batch's fused (rounds, launches)."""
-        t, k = C.c_int32(), C.c_int32()
-        bm, wm = C.c_double(), C.c_double()
+    def fused_info(self, precision: int = 32, dim: int = 2, order: int = 1):
+        """The tuner's choice for the (precision, dim, order) group -- a dict with "own" (each
+        slot's own sweep) or the fused kernel's "threads" and "tile", and the measured
+        "best_ms", "worst_ms" and "own_ms" per round -- or None before the tuner finished;
+        and the batch's fused (rounds, launches)."""
+        own, t, k = C.c_int32(), C.c_int32(), C.c_int32()
+        bm, wm, om = C.c_double(), C.c_double(), C.c_double()
         r, n = C.c_int64(), C.c_int64()
-        rc = self.lib.mdl_batch_fused_info(self.h, precision, order, C.byref(t), C.byref(k), C.byref(bm), C.byref(wm),
-                                           C.byref(r), C.byref(n))
+        rc = self.lib.mdl_batch_fused_info(self.h, precision, dim, order, C.byref(own), C.byref(t), C.byref(k),
+                                           C.byref(bm), C.byref(wm), C.byref(om), C.byref(r), C.byref(n))
         if rc not in (0, -8):
             self._check(rc)
-        shape = (t.value, k.value, bm.value, wm.value) if rc == 0 else None
-        return shape, (r.value, n.value)
+        info = None
+        if rc == 0:
+            info = {"own": bool(own.value), "best_ms": bm.value, "worst_ms": wm.value, "own_ms": om.value}
+            if not own.value:
+                info.update(threads=t.value, tile=k.value)
+        return info, (r.value, n.value)
 
     def _check(self, rc):
         if rc != 0:

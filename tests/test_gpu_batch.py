@@ -119,32 +119,43 @@ def test_slot_finishes_at_its_own_end_time(mdl):
     b.close()
 
 
-def test_fused_rounds_match_alone_thread_sweep(mdl):
-    """Fused rounds: one sweep launch per global tick, element family and precision over all
-    slots (uneven LTS levels: 2, 3 and 4 levels in one batch), replayed from a captured graph.
-    Each slot must give the values it gives alone with the thread-per-element sweep: meshes,
-    levels and activated probes identical, V and the state within FP32 rounding of two
-    compilations of the same element step (FP64 slots within 1e-12).  The tuner must have
-    settled on a shape, and the launch count must be one per global tick of each group."""
-    probs = [instance(2, 1, 0), instance(3, 1, 1), instance(3, 2, 2), instance(2, 1, 3, precision=64),
-             instance(2, 2, 4, amr=0), instance(2, 1, 5).replace(n_lts_levels=2),
-             instance(3, 1, 6).replace(n_lts_levels=4)]
-    nbar = 14
-    alone = []
+def fused_probs():
+    return [instance(2, 1, 0), instance(3, 1, 1), instance(3, 2, 2), instance(2, 1, 3, precision=64),
+            instance(2, 2, 4, amr=0), instance(2, 1, 5).replace(n_lts_levels=2),
+            instance(3, 1, 6).replace(n_lts_levels=4)]
+
+
+def run_alone(mdl, probs, nbar, variant=None):
+    out = []
     for p in probs:
         V0, v0 = initial(mdl, p)
         g = mdl.Sim(p)
-        g.set_sweep_variant(mdl.SWEEP_THREAD)
+        if variant is not None:
+            g.set_sweep_variant(variant)
         g.set_initial(V0, v0)
         g.step_barriers(nbar)
-        alone.append((g.read_V(), g.read_state(), g.read_activation(), g.read_mesh()))
+        out.append((g.read_V(), g.read_state(), g.read_activation(), g.read_mesh()))
         g.close()
-    b = mdl.Batch(autotune=True, fused=True)
+    return out
+
+
+def test_fused_rounds_match_alone_thread_sweep(mdl):
+    """Fused rounds: one sweep launch per global tick, element class and precision over all
+    slots of the class (uneven LTS levels: 2, 3 and 4 levels in one batch), replayed from a
+    captured graph, several rounds per step issued back to back.  Each slot must give the
+    values it gives alone with the thread-per-element sweep: meshes, levels and activated
+    probes identical, V and the state within FP32 rounding of two compilations of the same
+    element step (FP64 slots within 1e-12).  The launch count must be one per global tick of
+    each group."""
+    probs = fused_probs()
+    nbar = 14
+    alone = run_alone(mdl, probs, nbar, mdl.SWEEP_THREAD)
+    b = mdl.Batch(autotune=False, fused=True)
     slots = []
     for p in probs:
         V0, v0 = initial(mdl, p)
         slots.append(b.admit(p, nbar * mdl.Sim(p).dt, V0, v0))
-    while b.step(barriers_per_slot=2) > 0:
+    while b.step(barriers_per_slot=4) > 0:
         pass
     assert sorted(b.poll()) == sorted(slots)
     for s, p, (Va, va, la, ma) in zip(slots, probs, alone):
@@ -162,12 +173,53 @@ def test_fused_rounds_match_alone_thread_sweep(mdl):
         assert np.array_equal(fa, fb)
         if fa.any():
             assert np.abs(la[fa] - lb[fa]).max() <= 1e-6
-    shape, (rounds, launches) = b.fused_info(32, 1)
-    assert shape is not None and shape[0] in (64, 128, 256) and shape[1] >= 128 and shape[2] <= shape[3]
+    info, (rounds, launches) = b.fused_info(32, 2, 1)
     assert rounds == nbar
-    # per round: 2^Bmax launches for each group with slots (FP32 Q1: Bmax 3, FP32 Q2: 2,
-    # FP64 Q1: 2)
-    assert launches == nbar * (8 + 4 + 4)
+    # per round, 2^Bmax launches for each (precision, class) group: FP32 2D Q1 (levels 3 and
+    # 2: Bmax 2), FP32 3D Q1 (3 and 4: 3), FP32 3D Q2 (2), FP64 2D Q1 (2), FP32 2D Q2 (2)
+    assert launches == nbar * (4 + 8 + 4 + 4 + 4)
+    for s in slots:
+        b.release(s)
+    b.close()
+
+
+def test_fused_tuner_picks_per_class_and_slots_finish(mdl):
+    """With autotune, the first rounds time every fused launch shape and the slots' own sweeps
+    per (precision, class) group, one round at a time, and keep the fastest; the later rounds
+    run back to back.  A slot's rounds may then mix the fused (thread-per-element) step and its
+    own sweep variant (the tensor-core sweep for Q2 3D FP32), so each slot is held to the
+    FP32 tolerance against its run alone (FP64 slots: 1e-12), and every group present must
+    report its choice with the fastest candidate no slower than the slowest."""
+    probs = fused_probs()
+    # the Q2 3D slot without adaptation: an indicator within rounding of its threshold could
+    # otherwise adapt differently under the two sweep variants
+    probs[2] = probs[2].replace(amr_enabled=0)
+    nbar = 20                     # 7 candidates x 2 rounds of tuning, then 6 back to back
+    alone = run_alone(mdl, probs, nbar)
+    b = mdl.Batch(autotune=True, fused=True)
+    slots = []
+    for p in probs:
+        V0, v0 = initial(mdl, p)
+        slots.append(b.admit(p, nbar * mdl.Sim(p).dt, V0, v0))
+    while b.step(barriers_per_slot=3) > 0:
+        pass
+    assert sorted(b.poll()) == sorted(slots)
+    for s, p, (Va, va, la, ma) in zip(slots, probs, alone):
+        g, state, rc = b.slot(s)
+        assert state == mdl.SLOT_DONE and rc == 0
+        assert g.time()[1] == nbar
+        Vb = g.read_V()
+        tol = 1e-12 if p.precision == 64 else 1e-3
+        assert np.linalg.norm(Vb - Va) <= tol * np.linalg.norm(Va), (p.dim, p.order)
+    for prec, dim, order in [(32, 2, 1), (32, 3, 1), (32, 3, 2), (64, 2, 1), (32, 2, 2)]:
+        info, (rounds, _) = b.fused_info(prec, dim, order)
+        assert info is not None, (prec, dim, order)
+        assert info["best_ms"] <= info["worst_ms"] and info["own_ms"] > 0
+        if not info["own"]:
+            assert info["threads"] in (64, 128, 256) and info["tile"] >= 128
+    assert rounds == nbar
+    # a class never admitted has no choice
+    assert b.fused_info(64, 3, 2)[0] is None
     for s in slots:
         b.release(s)
     b.close()

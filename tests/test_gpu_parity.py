@@ -348,6 +348,64 @@ def test_coarsen_only_replay_bit_exact(mdl, dim):
     g.close()
 
 
+@pytest.mark.parametrize("dim,base,seed,tau", [(2, (3, 2, 1), 5, 0.75), (3, (2, 2, 1), 1, 0.7)])
+def test_depth_seven_forest_faces_and_adapt_bit_exact(mdl, dim, base, seed, tau):
+    """Leaves down to the deepest level (7): face tables after an upload and the meshes of two
+    adaptations equal the oracle's (the device finds neighbours by a search over the leaves'
+    sort keys, so a forest this deep must resolve neighbours across many levels of keys)."""
+    prob = W.Problem(dim=dim, order=1, extent=(0.3, 0.2, 0.1), base=base, max_refine=7,
+                     n_lts_levels=1, lts_enabled=0, amr_enabled=1, tau_refine=0.8, tau_coarsen=0.2,
+                     dt_barrier=1e-4, precision=32, ionic_model=-1)
+    f = random_forest(dim, base, 7, prob.extent, steps=7, seed=seed, tau=tau)
+    assert max(lf[0] for lf in f.leaves) == 7
+    g = mdl.Sim(prob)
+    lv, cc, root = forest_arrays(f)
+    g.upload_mesh(lv, cc, root)
+    k, n, p = g.read_faces()
+    ko, no, po = oracle_face_table(f)
+    assert np.array_equal(k, ko) and np.array_equal(n, no) and np.array_equal(p, po)
+    rng = np.random.default_rng(seed)
+    for step in range(2):
+        eta = rng.uniform(0, 1, f.n)
+        g.set_indicators(eta_s=eta)
+        f, _ = f.adapt(eta, prob.tau_refine, prob.tau_coarsen)
+        g.step_barriers(1)
+        r2, l2, c2, _ = g.read_mesh()
+        lvo, cco, rto = forest_arrays(f)
+        assert np.array_equal(l2, lvo) and np.array_equal(c2, cco) and np.array_equal(r2, rto)
+    k, n, p = g.read_faces()
+    ko, no, po = oracle_face_table(f)
+    assert np.array_equal(k, ko) and np.array_equal(n, no) and np.array_equal(p, po)
+    g.close()
+
+
+def test_finest_grid_larger_than_a_dense_cell_map(mdl):
+    """512 x 512 roots with 7 refinement levels: 4.3e9 finest cells, far more than a map of
+    4 bytes per finest cell could hold; the context needs memory per leaf only.  The uniform
+    root mesh has the closed-form face table of a Cartesian grid."""
+    prob = W.Problem(dim=2, order=1, extent=(1.0, 1.0, 1.0), base=(512, 512, 1), max_refine=7,
+                     n_lts_levels=1, lts_enabled=0, amr_enabled=1, tau_refine=0.8, tau_coarsen=0.2,
+                     dt_barrier=1e-3, precision=32, ionic_model=-1)
+    g = mdl.Sim(prob)
+    k, n, _ = g.read_faces()
+    nx = ny = 512
+    e = np.arange(nx * ny)
+    x, y = e % nx, e // nx
+    want_k = np.ones((nx * ny, 4), np.int8)
+    want_n = np.stack([e - 1, e + 1, e - nx, e + nx], axis=1).astype(np.int32)
+    for f, edge in enumerate([x == 0, x == nx - 1, y == 0, y == ny - 1]):
+        want_k[edge, f] = 0
+        want_n[edge, f] = -1
+    assert np.array_equal(k, want_k) and np.array_equal(n[:, :, 0], want_n)
+    # refine the corner leaf at the origin down to the deepest level
+    for step in range(7):
+        g.set_indicators(eta_s=np.where(np.arange(g.sizes()[0]) == 0, 1.0, 0.5))
+        g.step_barriers(1)
+    r2, l2, c2, _ = g.read_mesh()
+    assert l2.max() == 7 and l2[0] == 7 and np.array_equal(c2[0], [0, 0])
+    g.close()
+
+
 def test_full_size_slab2d_replay_matches_oracle(mdl):
     """The benchmark workload at full size (256x256 roots, AMR to depth 3, 4 LTS levels, FP32)
     from the synthetic developed front, in the benchmark's launch configuration, with the
