@@ -445,7 +445,9 @@ def run_serve(args, rank, world):
     """Poisson request stream (rate 20/s for 60 s, seed 5; 2D/3D, Q1/Q2, AMR + LTS, horizons
     100-500 ms) through the continuous-batching loop for a bounded wall time, then the same
     stream through a plain loop (one request at a time, FP64, uniform mesh at the finest
-    level, global time step) for a bounded wall time."""
+    level, global time step) for a bounded wall time.  No request of that stream can finish
+    inside the window (1e5-1e6 barrier steps each), so an added measurement follows on
+    requests that do: completed_window()."""
     import torch
     torch.cuda.set_device(0)
     from paper_2310_07607_gb300 import build, mdl
@@ -458,13 +460,133 @@ def run_serve(args, rank, world):
     rep = srv.run(reqs, wall_limit_s=wall, drain=False)
     srv.close()
     # plain comparator: the same arrivals served one by one without adaptivity in FP64
-    plain = run_plain_loop(mdl, reqs, wall, torch)
+    plain = run_plain_loop(mdl, reqs, wall)
+    done = completed_window(mdl, Request, Server, args)
     return {"metric": "sims/s", "value": rep["sims_per_s"], "unit": "sims/s", "n_gpus": 1,
             "steps": None, "warmup": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serve_poisson_rate20_60s_amr2_lts3_ap_fp32", "wall_limit_s": wall,
                        "barriers_per_round": args.serve_round},
-            "adaptive": rep, "plain_fp64_uniform_loop": plain}
+            "adaptive": rep, "plain_fp64_uniform_loop": plain, "completed_window": done}
+
+
+def probe_points(prob):
+    """Coordinates of the activation-time probes: the Gauss-Legendre nodes of every root
+    element (roots with axis 0 fastest, the nodes of a root with axis 0 fastest)."""
+    d, n1 = prob.dim, prob.order + 1
+    xi = np.polynomial.legendre.leggauss(n1)[0]
+    h = [prob.extent[k] / prob.base[k] for k in range(d)]
+    q = np.arange(n1 ** d)
+    loc = np.stack([(xi[(q // n1 ** k) % n1] + 1.0) * 0.5 * h[k] for k in range(d)], axis=1)
+    e = np.arange(int(np.prod(prob.base[:d])))
+    lo = []
+    for k in range(d):
+        lo.append((e % prob.base[k]) * h[k])
+        e = e // prob.base[k]
+    lo = np.stack(lo, axis=1)
+    return (lo[:, None, :] + loc[None, :, :]).reshape(-1, d)
+
+
+def lat_interpolator(prob, lat):
+    """The activation times of a uniform-grid run (probes on the Gauss-Legendre nodes of every
+    element) as a piecewise-multilinear function on the tensor grid of those nodes; NaN where
+    a neighbouring probe never activated."""
+    from scipy.interpolate import RegularGridInterpolator
+    d, n1 = prob.dim, prob.order + 1
+    xi = np.polynomial.legendre.leggauss(n1)[0]
+    axes = [((np.arange(prob.base[k])[:, None] + (xi[None, :] + 1.0) * 0.5) * (prob.extent[k] / prob.base[k])).ravel()
+            for k in range(d)]
+    b = [prob.base[k] for k in range(d)]
+    v = np.where(np.isfinite(lat), lat, np.nan)
+    if d == 2:
+        grid = v.reshape(b[1], b[0], n1, n1).transpose(0, 2, 1, 3).reshape(b[1] * n1, b[0] * n1)
+    else:
+        grid = v.reshape(b[2], b[1], b[0], n1, n1, n1).transpose(0, 3, 1, 4, 2, 5).reshape(
+            b[2] * n1, b[1] * n1, b[0] * n1)
+    f = RegularGridInterpolator(tuple(axes[::-1]), grid, method="linear", bounds_error=False, fill_value=np.nan)
+    return lambda pts: f(pts[:, ::-1])
+
+
+def lat_difference(prob_a, lat_a, prob_p, lat_p):
+    """Activation times of an adaptive run at its probes against the plain uniform-grid run
+    interpolated there: probes compared (active in both), active in one only, and the mean and
+    largest absolute difference (ms)."""
+    ref = lat_interpolator(prob_p, lat_p)(probe_points(prob_a))
+    fa, fr = np.isfinite(lat_a), np.isfinite(ref)
+    both = fa & fr
+    diff = np.abs(lat_a[both] - ref[both])
+    return {"probes": int(both.sum()), "adaptive_only": int((fa & ~fr).sum()),
+            "plain_only": int((~fa & fr).sum()),
+            "mean_ms": float(diff.mean()) if diff.size else None,
+            "max_ms": float(diff.max()) if diff.size else None}
+
+
+def completed_window(mdl, Request, Server, args, rate=3.0, arrivals_s=20.0, cap_s=240.0):
+    """Added measurement on requests that finish: the generator above with smaller, coarser
+    meshes and 5-20 ms horizons (workloads.completed_requests, 3 arrivals/s for 20 s, seed 6),
+    served to completion by the adaptive FP32 batch loop and by the plain FP64 loop (uniform
+    mesh at the finest level, global step), each bounded by cap_s.  Accuracy: every request's
+    activation times in the adaptive run against the plain run's, interpolated to the same
+    probes; and, on a sample, the adaptive FP32 run against the same run in FP64."""
+    gen = W.completed_requests(rate, arrivals_s, seed=6)
+    mk = lambda: [Request(rid=i, prob=p, horizon_ms=h, arrival_s=t) for i, (t, p, h) in enumerate(gen)]
+    lat_a = {}
+
+    def grab(req, g):
+        lat_a[req.rid] = g.read_activation()
+        return None
+
+    srv = Server(budget_bytes=0, barriers_per_round=args.serve_round, autotune=True, on_result=grab)
+    reqs = mk()
+    rep = srv.run(reqs, wall_limit_s=cap_s, drain=False)
+    srv.close()
+    lat_p = {}
+    plain = run_plain_loop(mdl, mk(), cap_s, keep=lat_p)
+    per = []
+    for i, (t, p, h) in enumerate(gen):
+        if i in lat_a and i in lat_p:
+            per.append(lat_difference(p, lat_a[i], plain_version(p), lat_p[i]))
+    means = [x["mean_ms"] for x in per if x["mean_ms"] is not None]
+    maxes = [x["max_ms"] for x in per if x["max_ms"] is not None]
+    # FP32 against FP64 on a sample: the first completed request of each (dim, order)
+    fp = []
+    seen = set()
+    for i, (t, p, h) in enumerate(gen):
+        key = (p.dim, p.order)
+        if i not in lat_a or key in seen:
+            continue
+        seen.add(key)
+        g = mdl.Sim(p.replace(precision=64))
+        g.step_barriers(int(math.floor(h / g.dt + 1e-9)))
+        l64 = g.read_activation()
+        g.close()
+        f32, f64 = np.isfinite(lat_a[i]), np.isfinite(l64)
+        both = f32 & f64
+        fp.append({"dim": p.dim, "order": p.order, "probes": int(both.sum()),
+                   "active_in_one_only": int((f32 != f64).sum()),
+                   "max_ms": float(np.abs(lat_a[i][both] - l64[both]).max()) if both.any() else None})
+    keep = ("completed", "failed", "wall_s", "sims_per_s", "ttr_p50_s", "ttr_p99_s", "peak_resident",
+            "busy_fraction", "queue_mean")
+    return {
+        "label": "added measurement: requests that finish inside the window (100-2000 base elements, "
+                 "base elements 8x (2D) / 4x (3D) larger than the stream above, horizons 5-20 ms); "
+                 "the stream above is unchanged",
+        "requests": len(gen), "arrivals_per_s": rate, "arrivals_s": arrivals_s, "cap_s": cap_s,
+        "adaptive_fp32_batch": {k: rep[k] for k in keep},
+        "plain_fp64_uniform_loop": {k: plain[k] for k in ("completed", "wall_s", "sims_per_s", "ttr_p50_s",
+                                                          "ttr_p99_s")},
+        "sims_per_s_ratio_adaptive_over_plain": (rep["sims_per_s"] / plain["sims_per_s"]
+                                                 if plain["sims_per_s"] > 0 else None),
+        "accuracy": {
+            "lat_adaptive_vs_plain_ms": {"requests": len(per), "median_of_mean": statistics.median(means)
+                                         if means else None, "max_of_max": max(maxes) if maxes else None,
+                                         "probes": int(sum(x["probes"] for x in per)),
+                                         "active_in_one_only": int(sum(x["adaptive_only"] + x["plain_only"]
+                                                                       for x in per))},
+            "lat_fp32_vs_fp64_adaptive_ms": fp,
+            "parity": "the FP64 paths (adaptive and plain) equal the FP64 oracle to 1e-12 in the GPU tests",
+        },
+    }
 
 
 def plain_version(prob):
@@ -475,9 +597,10 @@ def plain_version(prob):
                                n_lts_levels=1, precision=64, dt_barrier=0.0)
 
 
-def run_plain_loop(mdl, reqs, wall, torch):
+def run_plain_loop(mdl, reqs, wall, keep=None):
     """One request at a time in arrival order, FP64, uniform mesh at the adaptive run's finest
-    level, global forward Euler; bounded by `wall` seconds of serving time."""
+    level, global forward Euler; bounded by `wall` seconds of serving time.  keep: a dict that
+    receives the activation times of each completed request by rid."""
     t0 = time.perf_counter()
     done, ttr, proj = 0, [], []
     for r in sorted(reqs, key=lambda x: x.arrival_s):
@@ -496,13 +619,15 @@ def run_plain_loop(mdl, reqs, wall, torch):
             g.step_barriers(m)
             k += m
         end = time.perf_counter() - t0
-        g.close()
         if k == n:
             done += 1
             ttr.append(end - r.arrival_s)
+            if keep is not None:
+                keep[r.rid] = g.read_activation()
         else:
             rate = k / max(end - start, 1e-9)
             proj.append((start - r.arrival_s) + n / max(rate, 1e-9))
+        g.close()
     from paper_2310_07607_gb300.serve import percentile
     el = time.perf_counter() - t0
     return {"completed": done, "sims_per_s": done / el, "wall_s": el,

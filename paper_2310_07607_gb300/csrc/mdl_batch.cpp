@@ -6,7 +6,8 @@
 //     slot launches the phases before its sweep on its own stream, then ONE fused sweep
 //     (mdl_fused.h) per element class and precision covers the due elements of all the
 //     slots of that class, tick by global tick, replayed from a CUDA graph captured for the
-//     batch's composition; then each slot's epilogue.  The rounds of one mdl_batch_step run
+//     batch's composition (each class on its own stream, so the classes' sweeps overlap);
+//     then each slot's epilogue.  The rounds of one mdl_batch_step run
 //     back to back: the host waits for the device once, after the last.  Per class, the
 //     first rounds of the batch time every candidate on the batch itself -- launch shapes of
 //     the fused kernel (threads per block, due elements per work item) and "own sweeps"
@@ -58,8 +59,6 @@ struct mdl_batch {
     int64_t steps = 0;
     // fused rounds
     int fused = 1;
-    cudaStream_t fst = nullptr;                   // the batch's stream (fused sweeps)
-    cudaEvent_t fev = nullptr;                    // fused sweep done
     std::vector<cudaEvent_t> sev;                 // per slot: phases before the sweep done
     struct Group {                                // slots of one (precision, element class)
         int precision = 32, cls = 0;
@@ -81,6 +80,8 @@ struct mdl_batch {
         bool own = false;                         // tuned: each slot's own sweep
         int tuned = 0;                            // candidate rounds timed so far (-1: done)
         std::vector<double> cand_ms;              // measured ms per candidate
+        cudaStream_t st = nullptr;                // the group's stream: its fused sweeps
+        cudaEvent_t done = nullptr;               // the group's sweep of the round done
         cudaEvent_t t0 = nullptr, t1 = nullptr;   // tuner timing of the current round
         bool timed = false;
         double best_ms = 0, worst_ms = 0, own_ms = 0;
@@ -96,11 +97,11 @@ struct mdl_batch {
             if (g.hpin) cudaFreeHost(g.hpin);
             if (g.t0) cudaEventDestroy(g.t0);
             if (g.t1) cudaEventDestroy(g.t1);
+            if (g.done) cudaEventDestroy(g.done);
+            if (g.st) cudaStreamDestroy(g.st);
         }
         for (auto e : sev)
             if (e) cudaEventDestroy(e);
-        if (fev) cudaEventDestroy(fev);
-        if (fst) cudaStreamDestroy(fst);
     }
 };
 
@@ -207,8 +208,8 @@ int fused_group_sweep(mdl_batch* b, mdl_batch::Group& g, int n, int Bmax, int th
         if (e.dev && e.bytes == g.host) E = &e;
     if (!E) {
         E = g.entry[0].last <= g.entry[1].last ? &g.entry[0] : &g.entry[1];
-        // the entry's buffer and the staging are idle once the batch stream is
-        MDL_BCK(cudaStreamSynchronize(b->fst));
+        // the entry's buffer and the staging are idle once the group's stream is
+        MDL_BCK(cudaStreamSynchronize(g.st));
         if (nb > E->cap) {
             if (E->graph) cudaGraphExecDestroy(E->graph);
             E->graph = nullptr;
@@ -228,7 +229,7 @@ int fused_group_sweep(mdl_batch* b, mdl_batch::Group& g, int n, int Bmax, int th
             g.pin_cap = c;
         }
         memcpy(g.hpin, g.host.data(), nb);
-        MDL_BCK(cudaMemcpyAsync(E->dev, g.hpin, nb, cudaMemcpyHostToDevice, b->fst));
+        MDL_BCK(cudaMemcpyAsync(E->dev, g.hpin, nb, cudaMemcpyHostToDevice, g.st));
         E->bytes = g.host;
     }
     E->last = b->fused_rounds;
@@ -238,10 +239,10 @@ int fused_group_sweep(mdl_batch* b, mdl_batch::Group& g, int n, int Bmax, int th
         if (E->graph) cudaGraphExecDestroy(E->graph);
         E->graph = nullptr;
         cudaGraph_t graph;
-        MDL_BCK(cudaStreamBeginCapture(b->fst, cudaStreamCaptureModeThreadLocal));
+        MDL_BCK(cudaStreamBeginCapture(g.st, cudaStreamCaptureModeThreadLocal));
         const cudaError_t el = mdl::fused_sweep(g.precision, g.cls, E->dev, n, Bmax,
-                                                mdl::FusedShape{threads, tile, blocks}, b->fst);
-        const cudaError_t ec = cudaStreamEndCapture(b->fst, &graph);
+                                                mdl::FusedShape{threads, tile, blocks}, g.st);
+        const cudaError_t ec = cudaStreamEndCapture(g.st, &graph);
         MDL_BCK(el);
         MDL_BCK(ec);
         const cudaError_t ei = cudaGraphInstantiate(&E->graph, graph, 0);
@@ -249,7 +250,7 @@ int fused_group_sweep(mdl_batch* b, mdl_batch::Group& g, int n, int Bmax, int th
         MDL_BCK(ei);
         E->key = key;
     }
-    MDL_BCK(cudaGraphLaunch(E->graph, b->fst));
+    MDL_BCK(cudaGraphLaunch(E->graph, g.st));
     b->fused_launches += 1 << Bmax;
     return MDL_OK;
 }
@@ -257,10 +258,6 @@ int fused_group_sweep(mdl_batch* b, mdl_batch::Group& g, int n, int Bmax, int th
 // Issue one fused round over the running slots `run` (each advances one barrier step);
 // completion is left to fused_complete().
 int fused_issue(mdl_batch* b, const std::vector<int>& run) {
-    if (!b->fst) {
-        MDL_BCK(cudaStreamCreateWithFlags(&b->fst, cudaStreamNonBlocking));
-        MDL_BCK(cudaEventCreateWithFlags(&b->fev, cudaEventDisableTiming));
-    }
     while (b->sev.size() < b->slots.size()) {
         cudaEvent_t e = nullptr;
         MDL_BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -295,9 +292,12 @@ int fused_issue(mdl_batch* b, const std::vector<int>& run) {
         g.members.push_back(i);
         begun.push_back(i);
     }
-    // per (precision, class) group: one fused sweep from its captured graph, or (timed
-    // while tuning) the slots' own sweeps
+    // per (precision, class) group, on the group's own stream (the groups' sweeps overlap):
+    // one fused sweep from its captured graph, or (timed while tuning) the slots' own sweeps.
+    // While tuning, the groups' sweeps run one after another so that each is timed alone.
     const int nsm = sm_count();
+    const bool serial = tuning(b);
+    cudaEvent_t prev = nullptr;
     for (auto& g : b->groups) {
         const int n = (int)g.members.size();
         if (n == 0) continue;
@@ -307,13 +307,18 @@ int fused_issue(mdl_batch* b, const std::vector<int>& run) {
             b->err = "fused batch: too many slots in one group";
             return MDL_E_ARG;
         }
-        for (int i : g.members) MDL_BCK(cudaStreamWaitEvent(b->fst, b->sev[i], 0));
+        if (!g.st) {
+            MDL_BCK(cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking));
+            MDL_BCK(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+        }
+        for (int i : g.members) MDL_BCK(cudaStreamWaitEvent(g.st, b->sev[i], 0));
+        if (serial && prev) MDL_BCK(cudaStreamWaitEvent(g.st, prev, 0));
         if (c >= 0) {
             if (!g.t0) {
                 MDL_BCK(cudaEventCreate(&g.t0));
                 MDL_BCK(cudaEventCreate(&g.t1));
             }
-            MDL_BCK(cudaEventRecord(g.t0, b->fst));
+            MDL_BCK(cudaEventRecord(g.t0, g.st));
             g.timed = true;
         }
         if (c == kOwnCand) {
@@ -327,7 +332,7 @@ int fused_issue(mdl_batch* b, const std::vector<int>& run) {
                     s.rc = rc;
                 }
                 MDL_BCK(cudaEventRecord(b->sev[i], ss));
-                MDL_BCK(cudaStreamWaitEvent(b->fst, b->sev[i], 0));
+                MDL_BCK(cudaStreamWaitEvent(g.st, b->sev[i], 0));
             }
         } else {
             int Bmax = 0;
@@ -340,14 +345,15 @@ int fused_issue(mdl_batch* b, const std::vector<int>& run) {
             const int rc = fused_group_sweep(b, g, n, Bmax, threads, tile, nsm);
             if (rc) return rc;
         }
-        if (c >= 0) MDL_BCK(cudaEventRecord(g.t1, b->fst));
+        if (c >= 0) MDL_BCK(cudaEventRecord(g.t1, g.st));
+        MDL_BCK(cudaEventRecord(g.done, g.st));
+        prev = g.done;
     }
-    MDL_BCK(cudaEventRecord(b->fev, b->fst));
     // each slot's epilogue after its sweep
     for (int i : begun) {
         mdl_batch::Slot& s = b->slots[i];
         if (s.state == MDL_SLOT_FAILED) continue;
-        if (!s.own) MDL_BCK(cudaStreamWaitEvent((cudaStream_t)s.ctx->impl->stream_handle(), b->fev, 0));
+        if (!s.own) MDL_BCK(cudaStreamWaitEvent((cudaStream_t)s.ctx->impl->stream_handle(), b->groups[s.group].done, 0));
         const int rc = s.ctx->impl->fused_finish();
         if (rc) {
             s.state = MDL_SLOT_FAILED;
@@ -368,7 +374,8 @@ int fused_complete(mdl_batch* b, const std::vector<char>& took_part, int64_t* to
         const int rc = s.ctx->impl->end_barriers(&c);
         settle(s, rc, c, total);
     }
-    if (b->fst) MDL_BCK(cudaStreamSynchronize(b->fst));
+    for (auto& g : b->groups)
+        if (g.st) MDL_BCK(cudaStreamSynchronize(g.st));
     for (auto& g : b->groups) {
         if (!g.timed) continue;
         g.timed = false;

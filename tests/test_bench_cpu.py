@@ -44,3 +44,30 @@ def test_gpu_arm_fails_without_a_gpu():
     r = _run("--steps", "1", "--warmup", "3", "--no-cpu-baseline", timeout=300)
     assert r.returncode != 0
     assert not any(ln.strip().startswith("{") for ln in r.stdout.splitlines())
+
+
+@pytest.mark.parametrize("dim,order", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_lat_difference_is_zero_for_an_affine_activation_field(dim, order):
+    """The serving accuracy measure interpolates the plain run's activation times (Gauss-Legendre
+    nodes of its uniform fine grid) to the adaptive run's probes: an affine field is
+    reproduced exactly, probes where a neighbouring plain probe never activated are left out,
+    and a shift of the adaptive times by c shows up as a difference of c."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import workloads as W
+    prob = W.Problem(dim=dim, order=order, extent=(0.5, 0.3, 0.2), base=(5, 3, 2), max_refine=2)
+    plain = bench.plain_version(prob)
+    g = np.array([3.0, -2.0, 1.5][:dim])
+    lat_p = bench.probe_points(plain) @ g + 7.0
+    pts = bench.probe_points(prob)
+    assert pts.shape == (int(np.prod(prob.base[:dim])) * (order + 1) ** dim, dim)
+    lat_a = pts @ g + 7.0
+    d = bench.lat_difference(prob, lat_a, plain, lat_p)
+    assert d["probes"] == len(lat_a) and d["max_ms"] < 1e-12
+    d = bench.lat_difference(prob, lat_a + 0.25, plain, lat_p)
+    assert abs(d["mean_ms"] - 0.25) < 1e-12 and abs(d["max_ms"] - 0.25) < 1e-12
+    # the plain run never activated beyond a plane: adaptive probes next to it are not compared
+    lat_p2 = np.where(bench.probe_points(plain)[:, 0] < 0.25, lat_p, np.inf)
+    d = bench.lat_difference(prob, lat_a, plain, lat_p2)
+    assert 0 < d["probes"] < len(lat_a) and d["max_ms"] < 1e-12 and d["adaptive_only"] > 0

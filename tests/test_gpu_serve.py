@@ -37,7 +37,7 @@ def test_serving_loop_results_equal_alone():
 
     # a budget that holds about three of them at a time forces waiting and admission later
     fp = max(mdl.Batch(autotune=False).footprint(r.prob) for r in reqs)
-    srv = Server(budget_bytes=int(3.2 * fp), barriers_per_round=4, on_result=grab)
+    srv = Server(budget_bytes=int(3.2 * fp), barriers_per_round=4, autotune=False, on_result=grab)
     rep = srv.run(reqs, wall_limit_s=120.0, drain=True)
     srv.close()
     assert rep["completed"] == len(reqs) and rep["failed"] == 0
@@ -55,4 +55,45 @@ def test_serving_loop_results_equal_alone():
         assert np.array_equal(np.isfinite(la), np.isfinite(lb))
         if np.isfinite(la).any():
             assert np.abs(la[np.isfinite(la)] - lb[np.isfinite(la)]).max() <= 1e-6
+        g.close()
+
+
+@pytest.mark.parametrize("which", [0, 1, 2, 4])
+def test_completed_window_requests_fp64_match_oracle(which):
+    """The physics of the serving measurement on completed requests (workloads.completed_requests:
+    coarse meshes, AMR to depth 2, 3 LTS levels), on a patch of the request's roots: the FP64
+    adaptive run and the plain run of the plain loop (uniform finest mesh, global step) each
+    equal the FP64 oracle -- V to 1e-12 (mass-weighted), activation times to 1e-9 ms, the
+    adaptive meshes identical -- so the accuracies the measurement reports for the two arms are
+    those of the method, not of the kernels."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2310_07607_gb300 import build, mdl
+    from oracle import lts
+    from tests.helpers import forest_arrays, mass_rel_l2
+    import bench
+    build.build()
+    t, prob, h = W.completed_requests()[which]
+    patch = W.scaled(prob, (8, 8, 1) if prob.dim == 2 else (4, 2, 2)).replace(precision=64)
+    # the request's corner stimulus, a quarter of the patch wide
+    patch = patch.replace(stimuli=[W.Stimulus((0, 0, 0), tuple(0.25 * patch.extent[k] for k in range(3)),
+                                              1.0, 0.0, 1.0)])
+    for p in (patch, bench.plain_version(patch)):
+        o = lts.Sim(p)
+        g = mdl.Sim(p)
+        assert g.dt == o.dt
+        n = int(2.0 / o.dt)          # 2 ms: the stimulated front refines and spreads
+        for _ in range(n):
+            o.barrier()
+        g.step_barriers(n)
+        assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-12
+        la, lo = g.read_activation(), o.lat
+        assert np.array_equal(np.isfinite(la), np.isfinite(lo))
+        if np.isfinite(lo).any():
+            assert np.abs(la[np.isfinite(lo)] - lo[np.isfinite(lo)]).max() <= 1e-9
+        if p.amr_enabled:
+            lv, cc, _ = forest_arrays(o.forest)
+            r2, l2, c2, _ = g.read_mesh()
+            assert np.array_equal(l2, lv) and np.array_equal(c2, cc)
         g.close()

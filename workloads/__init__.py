@@ -258,9 +258,21 @@ def batch_instances(n: int = 64, seed: int = 4, min_e: float = 1e3, max_e: float
     return out
 
 
+# Refinement thresholds of the request generators per (dim, order), calibrated once on the
+# oracle: tau_refine about 1/20 of the largest level-0 spatial indicator on a developed front
+# (width 0.01 cm) at the generator's element size, so that a front reaches depth 2 within a
+# few barrier steps; tau_coarsen at the slabs' ratios (Q1 1/10, 2D Q2 1/100, 3D Q2 1/1000:
+# the indicator falls faster per refinement at Q2).
+SERVE_TAU = {(2, 1): (3e-8, 3e-9), (3, 1): (1.5e-10, 1.5e-11), (3, 2): (1e-9, 1e-12), (2, 2): (5e-8, 5e-10)}
+COMPLETED_TAU = {(2, 1): (2e-6, 2e-7), (3, 1): (5e-9, 5e-10), (3, 2): (4e-8, 4e-11), (2, 2): (5e-6, 5e-8)}
+
+
 def poisson_requests(rate: float = 20.0, duration: float = 60.0, seed: int = 5,
-                     min_e: float = 1e3, max_e: float = 2e5) -> List[Tuple[float, Problem, float]]:
-    """Poisson arrivals: (arrival_s, problem, horizon_ms)."""
+                     min_e: float = 1e3, max_e: float = 2e5,
+                     horizon: Tuple[float, float] = (100.0, 500.0), tau=None) -> List[Tuple[float, Problem, float]]:
+    """Poisson arrivals: (arrival_s, problem, horizon_ms); horizon is the range of the uniform
+    horizon draw, tau the refinement thresholds per (dim, order) (default SERVE_TAU)."""
+    tau = SERVE_TAU if tau is None else tau
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -282,13 +294,28 @@ def poisson_requests(rate: float = 20.0, duration: float = 60.0, seed: int = 5,
             hh = 0.015625 * order
             ext = (base[0] * hh, base[1] * hh, base[2] * hh)
         theta = float(rng.uniform(0.0, math.pi))
-        horizon = float(rng.uniform(100.0, 500.0))
+        t_end = float(rng.uniform(horizon[0], horizon[1]))
         corner = [0.0, 0.0, 0.0]
         size = [0.1 * ext[k] for k in range(3)]
         stim = Stimulus(tuple(corner), tuple(size), 1.0, 0.0, 1.0)
         p = Problem(dim=dim, order=order, extent=ext, base=base, sigma_l=1.2, sigma_t=0.4,
                     fibre=fibre_from_angle(theta), gamma=10.0 * order * order, stimuli=[stim],
                     dt_barrier=0.0, max_refine=2, n_lts_levels=3, tau_cell=0.5,
+                    tau_refine=tau[(dim, order)][0], tau_coarsen=tau[(dim, order)][1],
                     state_integrator=STATE_EXP, precision=32, amr_enabled=1, lts_enabled=1)
-        out.append((t, p, horizon))
+        out.append((t, p, t_end))
+    return out
+
+
+def completed_requests(rate: float = 3.0, duration: float = 20.0, seed: int = 6) -> List[Tuple[float, Problem, float]]:
+    """Requests that finish inside a serving window: the Poisson generator above with 100 to
+    2000 base elements, base elements 8x (2D) or 4x (3D) larger and 5-20 ms horizons (a few
+    thousand barrier steps each), arriving at `rate` per second for `duration` seconds."""
+    out = []
+    for t, p, h in poisson_requests(rate, duration, seed, min_e=1e2, max_e=2e3, horizon=(5.0, 20.0),
+                                    tau=COMPLETED_TAU):
+        f = 8.0 if p.dim == 2 else 4.0
+        ext = tuple(p.extent[k] * f if k < p.dim else p.extent[k] for k in range(3))
+        stim = dataclasses.replace(p.stimuli[0], hi=tuple(0.1 * ext[k] for k in range(3)))
+        out.append((t, p.replace(extent=ext, stimuli=[stim]), h))
     return out
