@@ -40,6 +40,7 @@ import numpy as np
 
 from . import basis, ionic
 from .forest import Forest
+from .mapped import MappedDisc
 from .sipg import Disc, eval_element
 
 
@@ -93,12 +94,15 @@ def gershgorin_cfl(Bown: np.ndarray, Mq: np.ndarray) -> float:
     return 1.0 / np.max(np.abs(L).sum(axis=1))
 
 
-def auto_dt_barrier(prob, disc: Disc) -> float:
-    """Largest 2^-k ms with b^CFL <= n_lts_levels - 1 for every admissible element class."""
+def auto_dt_barrier(prob, disc: Disc, cfl=None) -> float:
+    """Largest 2^-k ms with b^CFL <= n_lts_levels - 1 for every admissible element class
+    (on a mapped mesh, which does not adapt: for every element of the mesh, cfl)."""
     d = disc.dim
     wq = basis.node_weights(d, disc.p)
     cmin = math.inf
-    for level in range(prob.max_refine + 1):
+    if cfl is not None:
+        cmin = float(np.min(cfl))
+    for level in range(prob.max_refine + 1 if cfl is None else 0):
         choices = [0, 1] + ([2] if level > 0 else []) + ([3] if level < prob.max_refine else [])
         Mq = wq * np.prod(disc.forest.h(level) / 2.0)
         for cfg in itertools.product(choices, repeat=2 * d):
@@ -119,6 +123,9 @@ class Sim:
         self.forest = forest if forest is not None else Forest(prob.dim, prob.base, prob.max_refine,
                                                                prob.extent)
         self.B = prob.n_lts_levels - 1 if prob.lts_enabled else 0
+        self.mapped = getattr(prob, "geometry", 0) != 0
+        if self.mapped and prob.amr_enabled:
+            raise ValueError("mapped geometry: adaptive refinement is not supported")
         self._rebuild()
         n = self.disc.ne * self.disc.n_p
         self.V = np.zeros(n) if V0 is None else np.array(V0, dtype=np.float64)
@@ -129,7 +136,7 @@ class Sim:
         if prob.dt_barrier > 0:
             self.dt = float(prob.dt_barrier)
         else:
-            self.dt = auto_dt_barrier(prob, self.disc)
+            self.dt = auto_dt_barrier(prob, self.disc, self.cfl() if self.mapped else None)
         self._probes()
         self.lat = np.full(self.n_probe, np.inf)
         self._lat_initial()
@@ -147,7 +154,7 @@ class Sim:
 
     # ------------------------------------------------------------------
     def _rebuild(self):
-        self.disc = Disc(self.prob, self.forest)
+        self.disc = (MappedDisc if self.mapped else Disc)(self.prob, self.forest)
         self.A = self.disc.assemble()
         self._cfl = None
         self._stim_masks()

@@ -68,6 +68,8 @@ struct mdl_batch {
         size_t pin_cap = 0;
         // Uploaded records with the sweep graph captured for them.  Records change only when
         // a slot's state set or capacity does; two entries hold an adapting batch's two sets.
+        // A group of more than FUSED_MAX_SLOTS slots sweeps in chunks of that many, one
+        // launch sequence per chunk.
         struct Entry {
             std::vector<unsigned char> bytes;
             void* dev = nullptr;
@@ -75,7 +77,11 @@ struct mdl_batch {
             cudaGraphExec_t graph = nullptr;
             std::vector<long long> key;
             int64_t last = -1;
-        } entry[2];
+        };
+        struct Chunk {
+            Entry entry[2];
+        };
+        std::vector<Chunk> chunks;
         mdl::FusedShape shape{128, 256, 0};
         bool own = false;                         // tuned: each slot's own sweep
         int tuned = 0;                            // candidate rounds timed so far (-1: done)
@@ -90,10 +96,11 @@ struct mdl_batch {
     int64_t fused_rounds = 0, fused_launches = 0;
     ~mdl_batch() {
         for (auto& g : groups) {
-            for (auto& e : g.entry) {
-                if (e.graph) cudaGraphExecDestroy(e.graph);
-                if (e.dev) cudaFree(e.dev);
-            }
+            for (auto& c : g.chunks)
+                for (auto& e : c.entry) {
+                    if (e.graph) cudaGraphExecDestroy(e.graph);
+                    if (e.dev) cudaFree(e.dev);
+                }
             if (g.hpin) cudaFreeHost(g.hpin);
             if (g.t0) cudaEventDestroy(g.t0);
             if (g.t1) cudaEventDestroy(g.t1);
@@ -198,16 +205,21 @@ int candidate(const mdl_batch* b, const mdl_batch::Group& g) {
     return b->autotune && g.tuned >= 0 ? g.tuned / kRoundsPerCand : -1;
 }
 
-// The group's fused sweep of this round from its captured graph (uploading the records
-// and capturing first when they or the launch shape changed).
-int fused_group_sweep(mdl_batch* b, mdl_batch::Group& g, int n, int Bmax, int threads, int tile, int nsm) {
+// Chunk c of the group's fused sweep of this round (records host[0 .. n), already holding
+// their shifts) from its captured graph, uploading the records and capturing first when
+// they or the launch shape changed.  The group's pinned staging holds every chunk's records
+// at the chunk's own offset.
+int fused_group_sweep(mdl_batch* b, mdl_batch::Group& g, int c, const unsigned char* host, int n, int Bmax,
+                      int threads, int tile, int nsm) {
     const size_t bytes = mdl::fused_slot_bytes(g.precision);
     const size_t nb = (size_t)n * bytes;
+    if ((int)g.chunks.size() <= c) g.chunks.resize(c + 1);
+    mdl_batch::Group::Chunk& ch = g.chunks[c];
     mdl_batch::Group::Entry* E = nullptr;
-    for (auto& e : g.entry)
-        if (e.dev && e.bytes == g.host) E = &e;
+    for (auto& e : ch.entry)
+        if (e.dev && e.bytes.size() == nb && memcmp(e.bytes.data(), host, nb) == 0) E = &e;
     if (!E) {
-        E = g.entry[0].last <= g.entry[1].last ? &g.entry[0] : &g.entry[1];
+        E = ch.entry[0].last <= ch.entry[1].last ? &ch.entry[0] : &ch.entry[1];
         // the entry's buffer and the staging are idle once the group's stream is
         MDL_BCK(cudaStreamSynchronize(g.st));
         if (nb > E->cap) {
@@ -220,17 +232,18 @@ int fused_group_sweep(mdl_batch* b, mdl_batch::Group& g, int n, int Bmax, int th
             MDL_BCK(cudaMalloc(&E->dev, c));
             E->cap = c;
         }
-        if (nb > g.pin_cap) {
+        const size_t off = (size_t)c * mdl::FUSED_MAX_SLOTS * bytes;
+        if (off + nb > g.pin_cap) {
             if (g.hpin) cudaFreeHost(g.hpin);
             g.hpin = nullptr;
             g.pin_cap = 0;
-            const size_t c = std::max<size_t>(nb * 2, 16 * bytes);
-            MDL_BCK(cudaMallocHost((void**)&g.hpin, c));
-            g.pin_cap = c;
+            const size_t cp = std::max<size_t>((off + nb) * 2, 16 * bytes);
+            MDL_BCK(cudaMallocHost((void**)&g.hpin, cp));
+            g.pin_cap = cp;
         }
-        memcpy(g.hpin, g.host.data(), nb);
-        MDL_BCK(cudaMemcpyAsync(E->dev, g.hpin, nb, cudaMemcpyHostToDevice, g.st));
-        E->bytes = g.host;
+        memcpy(g.hpin + off, host, nb);
+        MDL_BCK(cudaMemcpyAsync(E->dev, g.hpin + off, nb, cudaMemcpyHostToDevice, g.st));
+        E->bytes.assign(host, host + nb);
     }
     E->last = b->fused_rounds;
     const int blocks = nsm * mdl::fused_blocks_per_sm(g.precision, g.cls, threads);
@@ -303,10 +316,6 @@ int fused_issue(mdl_batch* b, const std::vector<int>& run) {
         if (n == 0) continue;
         const int c = candidate(b, g);
         if (c < 0 && g.own) continue;
-        if (n > mdl::FUSED_MAX_SLOTS) {
-            b->err = "fused batch: too many slots in one group";
-            return MDL_E_ARG;
-        }
         if (!g.st) {
             MDL_BCK(cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking));
             MDL_BCK(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
@@ -335,15 +344,18 @@ int fused_issue(mdl_batch* b, const std::vector<int>& run) {
                 MDL_BCK(cudaStreamWaitEvent(g.st, b->sev[i], 0));
             }
         } else {
-            int Bmax = 0;
-            for (int i : g.members) Bmax = std::max(Bmax, Bs[i]);
             const size_t bytes = mdl::fused_slot_bytes(g.precision);
-            for (int k = 0; k < n; ++k)
-                mdl::fused_set_shift(g.host.data() + k * bytes, g.precision, Bmax - Bs[g.members[k]]);
             const int threads = c >= 0 ? kFusedShapes[c][0] : g.shape.threads;
             const int tile = c >= 0 ? kFusedShapes[c][1] : g.shape.tile;
-            const int rc = fused_group_sweep(b, g, n, Bmax, threads, tile, nsm);
-            if (rc) return rc;
+            for (int c0 = 0, ci = 0; c0 < n; c0 += mdl::FUSED_MAX_SLOTS, ++ci) {
+                const int nc = std::min(n - c0, mdl::FUSED_MAX_SLOTS);
+                int Bmax = 0;
+                for (int k = c0; k < c0 + nc; ++k) Bmax = std::max(Bmax, Bs[g.members[k]]);
+                for (int k = c0; k < c0 + nc; ++k)
+                    mdl::fused_set_shift(g.host.data() + k * bytes, g.precision, Bmax - Bs[g.members[k]]);
+                const int rc = fused_group_sweep(b, g, ci, g.host.data() + c0 * bytes, nc, Bmax, threads, tile, nsm);
+                if (rc) return rc;
+            }
         }
         if (c >= 0) MDL_BCK(cudaEventRecord(g.t1, g.st));
         MDL_BCK(cudaEventRecord(g.done, g.st));

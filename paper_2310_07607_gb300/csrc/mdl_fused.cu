@@ -39,9 +39,22 @@ __global__ void __launch_bounds__(256) k_tick_fused(const FusedSlot<R>* __restri
         sOff[s + 1] = (n + tile - 1) / tile;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        sOff[0] = 0;
-        for (int s = 0; s < nslot; ++s) sOff[s + 1] += sOff[s];
+    // prefix sums of the work items by warp 0, 32 slots at a time
+    if (threadIdx.x < 32) {
+        const int lane = (int)threadIdx.x;
+        int carry = 0;
+        for (int base = 0; base < nslot; base += 32) {
+            const int s = base + lane;
+            int v = s < nslot ? sOff[s + 1] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            if (s < nslot) sOff[s + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (lane == 0) sOff[0] = 0;
     }
     __syncthreads();
     // the values of the previous global tick are needed from here on

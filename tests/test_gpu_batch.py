@@ -223,3 +223,28 @@ def test_fused_tuner_picks_per_class_and_slots_finish(mdl):
     for s in slots:
         b.release(s)
     b.close()
+
+
+def test_fused_group_larger_than_one_launch(mdl):
+    """More slots of one class than one fused launch takes (256): the group sweeps in chunks,
+    each slot still gives the values it gives alone with the thread-per-element sweep."""
+    probs = [instance(2, 1, i % 5, amr=0).replace(base=(2, 2, 1), extent=(0.2, 0.15, 1.0)) for i in range(300)]
+    nbar = 4
+    b = mdl.Batch(autotune=False, fused=True)
+    slots = [b.admit(p, nbar * mdl.Sim(p).dt) for p in probs]
+    while b.step(barriers_per_slot=nbar) > 0:
+        pass
+    for i in (0, 255, 256, 299):
+        g = mdl.Sim(probs[i])
+        g.set_sweep_variant(mdl.SWEEP_THREAD)
+        g.step_barriers(nbar)
+        gb, state, rc = b.slot(slots[i])
+        assert state == mdl.SLOT_DONE and rc == 0 and gb.time()[1] == nbar
+        Va, Vb = g.read_V(), gb.read_V()
+        assert np.abs(Vb - Va).max() <= 1e-5 * max(np.abs(Va).max(), 1.0)
+        g.close()
+    _, (rounds, launches) = b.fused_info(32, 2, 1)
+    assert rounds == nbar and launches == nbar * 2 * 4      # two chunks, 2^2 ticks each
+    for s in slots:
+        b.release(s)
+    b.close()

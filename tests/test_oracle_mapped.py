@@ -1,0 +1,216 @@
+"""Oracle pins for the SIPG operator on mapped (curved) meshes: rigid motions reproduce the box
+operator, affine maps give the exact boundary-flux and volume identities of linear fields,
+the shell's mass is its exact volume, its operator is symmetric positive semi-definite with
+the constants as kernel, the azimuth's Dirichlet energy along a circumferential fibre is its
+closed form, and a radial manufactured solution converges at order p + 1."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import geometry, lts
+from oracle.forest import Forest
+from oracle.mapped import MappedDisc
+from oracle.sipg import Disc
+from tests.helpers import random_forest
+
+
+
+def rotation(dim):
+    a, b = 0.7, 0.4
+    R = np.array([[math.cos(a), -math.sin(a), 0.0], [math.sin(a), math.cos(a), 0.0], [0.0, 0.0, 1.0]])
+    if dim == 3:
+        R = R @ np.array([[1.0, 0.0, 0.0], [0.0, math.cos(b), -math.sin(b)], [0.0, math.sin(b), math.cos(b)]])
+    return R
+
+
+def box_problem(dim, p):
+    f = (0.6, 0.8, 0.0) if dim == 2 else (0.48, 0.64, 0.6)
+    return W.Problem(dim=dim, order=p, extent=(0.4, 0.3, 0.2), base=(3, 2, 2), sigma_l=1.2, sigma_t=0.4,
+                     fibre=f, gamma=10.0 * p * p)
+
+
+@pytest.mark.parametrize("hanging", [False, True])
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_rigid_motion_reproduces_the_box_operator(dim, p, hanging):
+    """x = R X + b with the fibre rotated along (f' = R f): the same operator and mass as the
+    box path, which is pinned against exact integration, on conforming and 2:1 meshes."""
+    prob = box_problem(dim, p)
+    R = rotation(dim)
+    f1 = R[:dim, :dim] @ np.array(prob.fibre[:dim])
+    pm = prob.replace(geometry=W.GEOMETRY_AFFINE, geo=tuple(R.ravel()) + (0.3, -0.2, 0.1),
+                      fibre=tuple(f1) + (0.0,) * (3 - dim))
+    f = random_forest(dim, prob.base, 2, prob.extent, steps=2, seed=3, tau=0.6) if hanging else \
+        Forest(dim, prob.base, 2, prob.extent)
+    d0, d1 = Disc(prob, f), MappedDisc(pm, f)
+    A0, A1 = d0.assemble(), d1.assemble()
+    assert abs(A0 - A1).max() <= 1e-13 * abs(A0).max()
+    assert np.allclose(d0.M, d1.M, rtol=1e-14, atol=0)
+    assert np.allclose(d1.node_coords(), d0.node_coords() @ R[:dim, :dim].T + np.array([0.3, -0.2, 0.1])[:dim])
+
+
+def shear(dim):
+    A = np.array([[1.3, 0.4, -0.2], [0.1, 0.9, 0.3], [0.25, -0.15, 1.1]])
+    return A
+
+
+def boundary_flux_exact(prob, A, g):
+    """sum over boundary faces of element e of (D g . n) |F|, per element, from the parallelogram
+    (parallelepiped face) geometry of the affine image of the box faces."""
+    d = prob.dim
+    Am = A[:d, :d]
+    from oracle.sipg import diffusion_tensor
+    D = diffusion_tensor(prob)
+    h = np.array(prob.extent[:d]) / np.array(prob.base[:d])
+    out = np.zeros(int(np.prod(prob.base[:d])))
+    for e in range(out.size):
+        c = np.array([(e // int(np.prod(prob.base[:k]))) % prob.base[k] for k in range(d)])
+        for k in range(d):
+            for side in (0, 1):
+                if (side == 0 and c[k] != 0) or (side == 1 and c[k] != prob.base[k] - 1):
+                    continue
+                t = [l for l in range(d) if l != k]
+                edges = [Am @ (h[l] * np.eye(d)[l]) for l in t]
+                if d == 2:
+                    e0 = edges[0]
+                    nrm = np.array([e0[1], -e0[0]])
+                else:
+                    nrm = np.cross(edges[0], edges[1])
+                area = np.linalg.norm(nrm)
+                nrm = nrm / area
+                outward = Am @ np.eye(d)[k] * (1.0 if side else -1.0)
+                if nrm @ outward < 0:
+                    nrm = -nrm
+                out[e] += (D @ g) @ nrm * area
+    return out
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_affine_map_linear_fields_exact_identities(dim, p):
+    """On an affine (sheared) mesh linear fields u = g.x, w = k.x lie in the space, so with
+    v piecewise constant a(u, v) = sum_e v_e (boundary flux of D g through e's outer faces)
+    and a(u, w) = g.D k |Omega|: the first checks the face normals, areas and consistency
+    terms, the second the volume term, both against plain geometry."""
+    prob = box_problem(dim, p).replace(geometry=W.GEOMETRY_AFFINE)
+    A = shear(dim)
+    prob = prob.replace(geo=tuple(A.ravel()) + (0.05, 0.1, -0.2))
+    disc = MappedDisc(prob, Forest(dim, prob.base, 0, prob.extent))
+    K = disc.assemble()
+    X = disc.node_coords()
+    rng = np.random.default_rng(1)
+    g = rng.normal(size=dim)
+    kk = rng.normal(size=dim)
+    u = X @ g
+    w = X @ kk
+    ve = rng.normal(size=disc.ne)
+    v = np.repeat(ve, disc.n_p)
+    lhs = v @ (K @ u)
+    rhs = ve @ boundary_flux_exact(prob, A, g)
+    assert abs(lhs - rhs) <= 1e-12 * (abs(rhs) + np.abs(ve).sum())
+    from oracle.sipg import diffusion_tensor
+    vol = abs(np.linalg.det(A[:dim, :dim])) * np.prod(prob.extent[:dim])
+    assert abs(w @ (K @ u) - g @ diffusion_tensor(prob) @ kk * vol) <= 1e-12 * vol
+    assert abs(disc.M.sum() - vol) <= 1e-13 * vol
+
+
+def shell(dim, p, base, inner=1.0, outer=1.5, ellipse=(1.0, 1.0)):
+    """Spherical (circular) shell sector: azimuth 0.3 .. 1.5 rad, polar angle 0.5 .. 2.3 rad."""
+    geo = (inner * ellipse[0], inner * ellipse[1], inner, outer * ellipse[0], outer * ellipse[1], outer,
+           0.3, 1.2, 0.5, 1.8)
+    return W.Problem(dim=dim, order=p, extent=(1.0, 1.0, 1.0), base=base, sigma_l=1.0, sigma_t=1.0,
+                     fibre=(1.0, 0.0, 0.0), gamma=10.0 * p * p, geometry=W.GEOMETRY_SHELL, geo=geo)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_shell_mass_is_the_sector_volume_and_operator_is_spsd(dim, p):
+    base = (8, 6, 4) if dim == 2 else (5, 4, 3)
+    prob = shell(dim, p, base)
+    disc = MappedDisc(prob, Forest(dim, base, 0, prob.extent))
+    ri, ro, dphi = 1.0, 1.5, 1.2
+    if dim == 2:
+        exact = 0.5 * (ro ** 2 - ri ** 2) * dphi
+    else:
+        exact = (ro ** 3 - ri ** 3) / 3.0 * (math.cos(0.5) - math.cos(2.3)) * dphi
+    tol = {(2, 1): 2e-3, (2, 2): 2e-5, (3, 1): 5e-3, (3, 2): 5e-5}[(dim, p)]
+    assert abs(disc.M.sum() - exact) <= tol * exact
+    K = disc.assemble()
+    Kd = K.toarray()
+    assert np.abs(Kd - Kd.T).max() <= 1e-13 * np.abs(Kd).max()
+    assert np.abs(Kd @ np.ones(Kd.shape[0])).max() <= 1e-12 * np.abs(Kd).max()
+    ev = np.linalg.eigvalsh(0.5 * (Kd + Kd.T))
+    assert ev[0] >= -1e-11 * ev[-1]
+    assert (ev < 1e-10 * ev[-1]).sum() == 1          # the constants only
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_circumferential_fibre_energy_of_the_azimuth(dim):
+    """u = azimuth is linear in the first reference coordinate, so it lies in the mapped space
+    and is continuous; with the fibre along the image of that axis, D grad(phi) = sigma_l
+    grad(phi) / (chi C_m) and a(u, u) = sigma_l/(chi C_m) int |grad phi|^2, in closed form:
+    dphi ln(r_o / r_i) (2D) and dphi (r_o - r_i) ln(tan(theta1/2) / tan(theta0/2)) (3D).
+    With the fibre radial-free but fixed in space, the value differs."""
+    base = (6, 5, 1) if dim == 2 else (6, 5, 4)
+    prob = shell(dim, 2, base).replace(sigma_l=2.0, sigma_t=0.5, fibre_ref=1)
+    disc = MappedDisc(prob, Forest(dim, base, 0, prob.extent))
+    K = disc.assemble()
+    Xr = disc.ref_coords()
+    u = 0.3 + Xr[:, 0] * 1.2
+    ri, ro = 1.0, 1.5
+    if dim == 2:
+        exact = 1.2 * math.log(ro / ri)
+    else:
+        exact = 1.2 * (ro - ri) * math.log(math.tan(2.3 / 2) / math.tan(0.5 / 2))
+    exact *= prob.sigma_l / (prob.chi * prob.cm)
+    assert abs(u @ (K @ u) - exact) <= 1e-4 * exact
+    other = MappedDisc(prob.replace(fibre_ref=0), Forest(dim, base, 0, prob.extent)).assemble()
+    assert abs(u @ (other @ u) - exact) >= 0.05 * exact
+
+
+def radial_error(dim, p, n):
+    """Steady Neumann problem -div(D grad u) = f on the shell sector with the radial solution
+    u(r) = cos(pi (r - r_i) / (r_o - r_i)) (zero normal flux on every side); returns the
+    mass-weighted L2 error of the discrete solution (both with zero mean)."""
+    base = (n, n, 1) if dim == 2 else (n, n, n)
+    prob = shell(dim, p, base)
+    disc = MappedDisc(prob, Forest(dim, base, 0, prob.extent))
+    K = disc.assemble().toarray()
+    X = disc.node_coords()
+    r = np.linalg.norm(X, axis=1)
+    ri, ro = 1.0, 1.5
+    w = math.pi / (ro - ri)
+    Dc = prob.sigma_l / (prob.chi * prob.cm)
+    u = np.cos(w * (r - ri))
+    up = -w * np.sin(w * (r - ri))
+    upp = -w * w * np.cos(w * (r - ri))
+    f = -Dc * (upp + (dim - 1) / r * up)
+    M = disc.M
+    rhs = M * f
+    rhs -= M * (rhs.sum() / M.sum())                        # compatible right-hand side
+    one = M / M.sum()
+    uh = np.linalg.solve(K + np.outer(M, one), rhs)      # zero M-weighted mean
+    ue = u - (M @ u) / M.sum()
+    uh = uh - (M @ uh) / M.sum()
+    return math.sqrt(M @ (uh - ue) ** 2) / math.sqrt(M @ ue ** 2)
+
+
+@pytest.mark.parametrize("dim,p,ns", [(2, 1, (6, 12)), (2, 2, (4, 8)), (3, 1, (3, 6)), (3, 2, (2, 4))])
+def test_radial_solution_converges_at_order_p_plus_one(dim, p, ns):
+    e0, e1 = radial_error(dim, p, ns[0]), radial_error(dim, p, ns[1])
+    rate = math.log(e0 / e1) / math.log(ns[1] / ns[0])
+    assert rate >= p + 1 - 0.3, (e0, e1, rate)
+
+
+def test_oracle_steps_a_mapped_problem_with_lts():
+    """Alg. 1 on a shell sector: one LTS level reproduces global forward Euler with the mapped
+    operator and mass bit for bit (the queue sweep is independent of the geometry)."""
+    prob = shell(2, 1, (6, 4, 1)).replace(ionic_model=0, sigma_l=1.2, sigma_t=0.4, fibre_ref=1,
+                                            dt_barrier=0.0, n_lts_levels=1, lts_enabled=0,
+                                            stimuli=[W.Stimulus((-2.0, -2.0, -2.0), (0.3, 2.0, 2.0), 1.0, 0.0, 1.0)])
+    o = lts.Sim(prob)
+    V0, v0 = o.V.copy(), o.v.copy()
+    for _ in range(20):
+        o.barrier()
+    V, v = lts.global_fe(prob, o.A, o.disc.M, V0, v0, o.dt, 20, lambda t: o.i_stim(t))
+    assert np.array_equal(V, o.V) and np.array_equal(v, o.v)
+    assert np.any(o.V != 0)

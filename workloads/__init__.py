@@ -29,6 +29,15 @@ AP_STANDARD = (8.0, 0.15, 0.002, 0.2, 0.3, 1.0)  # k, a, eps0, mu1, mu2, time_sc
 STATE_FE = 0
 STATE_EXP = 1
 
+# Geometry of the slab (Problem.geometry).  The forest always lives on the reference box
+# [0, extent_0] x [0, extent_1] (x [0, extent_2]); a map x = Phi(X) takes it to the physical
+# domain (the paper's curved ventricle meshes, Sec. 3.3, stand behind the shell).
+GEOMETRY_BOX = 0      # Phi = identity
+GEOMETRY_AFFINE = 1   # Phi(X) = A X + b, geo = (A row-major 3x3, b) (2D: the leading 2x2 block)
+GEOMETRY_SHELL = 2    # ellipsoidal shell sector, geo = (a_i, b_i, c_i, a_o, b_o, c_o, phi0, dphi,
+                      #   theta0, dtheta): X_0 -> azimuth, X_1 -> polar angle (2D: transmural),
+                      #   X_2 -> transmural, semi-axes linear from inner to outer surface
+
 
 @dataclass
 class Stimulus:
@@ -68,6 +77,9 @@ class Problem:
     precision: int = 64             # 32 or 64
     amr_enabled: int = 0
     lts_enabled: int = 0
+    geometry: int = 0               # 0 box, 1 affine map, 2 ellipsoidal shell sector (GEOMETRY_*)
+    geo: Tuple[float, ...] = ()     # parameters of the map (see the GEOMETRY_* constants)
+    fibre_ref: int = 0              # 1: fibre along the image of the first reference axis
 
     def replace(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)
