@@ -51,6 +51,26 @@ extern "C" {
 #define MDL_MAX_STIM      4
 #define MDL_MAX_REFINE    7
 
+/* Geometry (mdl_problem.geometry).  The forest lives on the reference box; the physical
+ * domain is its image under x = Phi(X).  Element maps are x(xi) = Phi(X_c + (xi + 1) h / 2),
+ * so elements are curved wherever Phi is; the SIPG terms (Eq. monodomain-primal-formulation,
+ * Eq. monodomain-numerical-flux) take the Jacobian, area weight, normal and normal extent of
+ * every GL point, and each element its own Gershgorin bound (Eq. cfl-monodomain).  A mapped
+ * geometry runs on the fixed root mesh: amr_enabled = 0 and max_refine = 0 (MDL_E_ARG
+ * otherwise), the thread-per-element sweep only, no mdl_upload_mesh.  Stimulus boxes and
+ * the fibre are in physical coordinates; probes stay the GL nodes of the roots.
+ *   MDL_GEOMETRY_BOX     Phi = identity (geo ignored)
+ *   MDL_GEOMETRY_AFFINE  Phi(X) = A X + b, geo = (A row-major 3x3, b[3]); 2D: leading 2x2, b[0..1]
+ *   MDL_GEOMETRY_SHELL   ellipsoidal shell sector, geo = (a_i, b_i, c_i, a_o, b_o, c_o, phi0,
+ *                        dphi, theta0, dtheta): azimuth phi = phi0 + dphi X_0 / L_0; 3D polar
+ *                        angle theta = theta0 + dtheta X_1 / L_1 inside (0, pi), transmural
+ *                        u = X_2 / L_2, x = (a sin(theta) cos(phi), b sin(theta) sin(phi),
+ *                        c cos(theta)); 2D u = X_1 / L_1, x = (a cos(phi), b sin(phi)); semi-axes
+ *                        a = a_i + u (a_o - a_i) etc., all growing (or all shrinking). */
+#define MDL_GEOMETRY_BOX    0
+#define MDL_GEOMETRY_AFFINE 1
+#define MDL_GEOMETRY_SHELL  2
+
 /* Box stimulus: I_stim = -amplitude at nodes inside [lo, hi] (inclusive, 1e-12
  * slack) for t0 <= t < t1 (Sec. 2, I' = I_ion + I_stim). */
 typedef struct mdl_stim {
@@ -84,6 +104,10 @@ typedef struct mdl_problem {
     int32_t precision;         /* 32 (FP32 bulk, FP64 reductions) or 64 */
     int32_t amr_enabled;       /* 0/1 */
     int32_t lts_enabled;       /* 0/1; 0 = every element takes one step per barrier */
+    int32_t geometry;          /* MDL_GEOMETRY_*: the map x = Phi(X) from the reference box
+                                  [0, extent] to the physical domain (curved meshes, Sec. 3.3) */
+    int32_t fibre_ref;         /* 1: fibre along the image DPhi e_0 of the first reference axis */
+    double  geo[12];           /* parameters of the map (see MDL_GEOMETRY_*) */
 } mdl_problem;
 
 typedef struct mdl_ctx mdl_ctx;

@@ -23,6 +23,7 @@ SOURCES = [
     "mdl_inst_3_1.cu",
     "mdl_inst_3_2.cu",
     "mdl_mesh.cpp",
+    "mdl_geometry.cpp",
     "mdl_tables.cpp",
     "mdl_noalloc.cu",
     "mdl_batch.cpp",

@@ -285,24 +285,34 @@ int fused_issue(mdl_batch* b, const std::vector<int>& run) {
     // own sweeps goes straight on with its sweep
     std::vector<int> Bs(b->slots.size(), 0);
     std::vector<int> begun;
+    std::vector<unsigned char> scratch;
     for (int i : run) {
         mdl_batch::Slot& s = b->slots[i];
         mdl_batch::Group& g = b->groups[s.group];
         const int c = candidate(b, g);
-        s.own = c >= 0 ? c == kOwnCand : g.own;
+        // a mapped slot always sweeps on its own and is no member of its group
+        const bool alone = s.ctx->impl->is_mapped();
+        s.own = alone || (c >= 0 ? c == kOwnCand : g.own);
         const size_t bytes = mdl::fused_slot_bytes(g.precision);
         const size_t off = g.host.size();
-        g.host.resize(off + bytes);
-        int rc = s.ctx->impl->fused_begin(g.host.data() + off, &Bs[i]);
-        if (!rc && s.own && c < 0) rc = s.ctx->impl->fused_own_sweep();
+        unsigned char* rec;
+        if (alone) {
+            scratch.resize(bytes);
+            rec = scratch.data();
+        } else {
+            g.host.resize(off + bytes);
+            rec = g.host.data() + off;
+        }
+        int rc = s.ctx->impl->fused_begin(rec, &Bs[i]);
+        if (!rc && s.own && (c < 0 || alone)) rc = s.ctx->impl->fused_own_sweep();
         if (rc) {
-            g.host.resize(off);
+            if (!alone) g.host.resize(off);
             s.state = MDL_SLOT_FAILED;
             s.rc = rc;
             continue;
         }
         MDL_BCK(cudaEventRecord(b->sev[i], (cudaStream_t)s.ctx->impl->stream_handle()));
-        g.members.push_back(i);
+        if (!alone) g.members.push_back(i);
         begun.push_back(i);
     }
     // per (precision, class) group, on the group's own stream (the groups' sweeps overlap):

@@ -8,6 +8,7 @@
 
 #include "../../include/mdl.h"
 #include "mdl_ctx.h"
+#include "mdl_geometry.h"
 #include "mdl_kernels.cuh"
 
 namespace mdl {
@@ -42,6 +43,9 @@ int check_problem(const mdl_problem* p, std::string* why) {
     double roots = 1.0;
     for (int k = 0; k < p->dim; ++k) roots *= p->base[k];
     if (roots * 27.0 > 2.0e9) { *why = "too many roots"; return MDL_E_ARG; }
+    if (p->fibre_ref != 0 && p->fibre_ref != 1) { *why = "fibre_ref must be 0 or 1"; return MDL_E_ARG; }
+    const char* gw = nullptr;
+    if (geo_check(*p, &gw) != MDL_OK) { *why = gw; return MDL_E_ARG; }
     return MDL_OK;
 }
 

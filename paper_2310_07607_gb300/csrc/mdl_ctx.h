@@ -52,6 +52,9 @@ public:
     virtual int fused_own_sweep() = 0;
     virtual int fused_finish() = 0;
     virtual bool replaying() const = 0;
+    // A mapped (curved) geometry: its sweep is always its own (the fused kernel has box
+    // elements only).
+    virtual bool is_mapped() const = 0;
     virtual void* stream_handle() const = 0;
     virtual int precision() const = 0;
     virtual int64_t device_bytes() const = 0;     // device memory held by the context

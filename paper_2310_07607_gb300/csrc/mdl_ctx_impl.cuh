@@ -33,6 +33,8 @@
 #include "mdl_ctx.h"
 #include "mdl_fused.h"
 #include "mdl_kernels.cuh"
+#include "mdl_geometry.h"
+#include "mdl_mapped.cuh"
 #include "mdl_mesh.h"
 #include "mdl_tables.h"
 #include "mdl_tc.cuh"
@@ -130,8 +132,10 @@ class Ctx : public CtxBase {
     DBuf<uint32_t> smask[MDL_MAX_STIM];
     DBuf<int8_t> pkind, pbits, lvl_ovr;
     DBuf<double> eta_t_ovr;
-    DBuf<double> mtab;   // FP64 GL mass w_q det J per (level, node)
+    DBuf<double> mtab;   // FP64 GL mass w_q det J per (level, node); mapped: per (element, node)
     DBuf<R> qvol, qface, qkelly;   // Q1 class blocks
+    bool mapped = false;           // curved mesh (mdl_geometry.h): fixed root mesh, own factors
+    DBuf<R> gvol, gface;           // its per-element geometric factors (mdl_mapped.cuh)
     DBuf<uint16_t> tcB;            // Q2 3D FP32: level-0 operator of the tensor-core sweep (FP16 hi/lo)
     float tc_unscale = 1.0f;       // 2^-t: undoes the scaling of the operator by 2^t
     DBuf<float> tcC;               // Q2 3D FP32: level-0 correction blocks of non-regular faces
@@ -213,6 +217,8 @@ class Ctx : public CtxBase {
         d.qvol = qvol.p;
         d.qface = qface.p;
         d.qkelly = qkelly.p;
+        d.gvol = gvol.p;
+        d.gface = gface.p;
         return d;
     }
 
@@ -467,6 +473,16 @@ class Ctx : public CtxBase {
                 stats.tick_launches += nt;
                 return MDL_OK;
             }
+            if (mapped) {
+                const int gm = (int)std::min<int64_t>(div_up(std::max<int64_t>(cap, 1), 128), (int64_t)nsm * 16);
+                for (int i = 0; i < nt; ++i) {
+                    ta.tick = i;
+                    MDL_CK(launch_kx(pdl && i > 0, (k_tick_mapped<R, DIM, P>), gm, 128, ta, T, ph));
+                    MDL_LAUNCHED();
+                    stats.tick_launches++;
+                }
+                return MDL_OK;
+            }
             const int lanes = (P == 1 && group_tick) ? NP : 1;
             const int gt = (int)std::min<int64_t>(div_up(std::max<int64_t>(cap, 1) * lanes, tick_threads),
                                                   (int64_t)nsm * tick_bpsm);
@@ -501,7 +517,7 @@ class Ctx : public CtxBase {
             int ex = 0;
             const double fr = frexp(dt, &ex);
             MDL_CK(launch_k((k_epilogue<R, DIM, P>), g256, 256, arrays(o), mtab.p, dt, 1.0 / dt,
-                            fr == 0.5 ? 1 : 0));
+                            fr == 0.5 ? 1 : 0, mapped ? 1 : 0));
         }
         MDL_LAUNCHED();
         return MDL_OK;
@@ -610,6 +626,7 @@ public:
         for (auto& m : smask) m.release();
         lvl_ovr.release(); eta_t_ovr.release(); meta.release(); mtab.release(); dT.release(); dph.release();
         qvol.release(); qface.release(); qkelly.release(); tcB.release(); tcC.release();
+        gvol.release(); gface.release();
         if (hmeta) cudaFreeHost(hmeta);
         for (auto e : evpool) cudaEventDestroy(e);
         if (st) cudaStreamDestroy(st);
@@ -617,13 +634,31 @@ public:
 
     int create(const mdl_problem& p) override {
         pb = p;
-        tensor_tick = tensor_capable;   // Q2 3D FP32: the tensor-core sweep is the default
+        mapped = pb.geometry != MDL_GEOMETRY_BOX;
+        // Q2 3D FP32: the tensor-core sweep is the default (box elements)
+        tensor_tick = tensor_capable && !mapped;
         B = pb.lts_enabled ? pb.n_lts_levels - 1 : 0;
         make_tables(P, &Td);
         make_phys(pb, Td, &phd);
         convert_tables<R>(Td, &T);
         convert_phys<R>(phd, &ph);
-        dt = pb.dt_barrier > 0 ? pb.dt_barrier : auto_dt_barrier(Td, phd, DIM, P, pb.max_refine, B);
+        MappedFactors mf;
+        if (mapped) {
+            const int rc = mapped_factors(pb, Td, &mf, &err);
+            if (rc) return rc;
+        }
+        if (pb.dt_barrier > 0) {
+            dt = pb.dt_barrier;
+        } else if (mapped) {
+            // the largest 2^-k ms with dt 2^-B below every element's bound (the mesh is fixed)
+            double cmin = INFINITY;
+            for (double c : mf.cfl) cmin = std::min(cmin, c);
+            int k = -20;
+            while (ldexp(1.0, -k - B) > cmin) ++k;
+            dt = ldexp(1.0, -k);
+        } else {
+            dt = auto_dt_barrier(Td, phd, DIM, P, pb.max_refine, B);
+        }
         int dev = 0;
         MDL_CK(cudaGetDevice(&dev));
         MDL_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -713,6 +748,7 @@ public:
         MDL_CK(dph.ensure(1));
         MDL_CK(cudaMemcpy(dT.p, &T, sizeof(Tables<R>), cudaMemcpyHostToDevice));
         MDL_CK(cudaMemcpy(dph.p, &ph, sizeof(Phys<R>), cudaMemcpyHostToDevice));
+        if (mapped) hm = mf.mass;
         MDL_CK(mtab.ensure(hm.size()));
         MDL_CK(cudaMemcpyAsync(mtab.p, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         MDL_CK(class_b.ensure(hcb.size()));
@@ -722,10 +758,44 @@ public:
         n_probe = mh.n() * NP;
         MDL_CK(lat.ensure(n_probe));
         MDL_CK(cudaStreamSynchronize(st));
-        return load_mesh(mh);
+        int rc = load_mesh(mh);
+        if (rc || !mapped) return rc;
+        return load_mapped(mf);
+    }
+
+    // Mapped meshes: the factors of the root mesh, each element's b^CFL from its own bound,
+    // and the stimulus masks of the physical node positions (replacing the box tables).
+    int load_mapped(const MappedFactors& mf) {
+        if (mf.ne != ne) {
+            err = "mapped geometry: factor count does not match the mesh";
+            return MDL_E_STATE;
+        }
+        std::vector<R> gv(mf.gvol.begin(), mf.gvol.end()), gf(mf.gface.begin(), mf.gface.end());
+        MDL_CK(gvol.ensure(gv.size()));
+        MDL_CK(gface.ensure(gf.size()));
+        MDL_CK(cudaMemcpyAsync(gvol.p, gv.data(), gv.size() * sizeof(R), cudaMemcpyHostToDevice, st));
+        MDL_CK(cudaMemcpyAsync(gface.p, gf.data(), gf.size() * sizeof(R), cudaMemcpyHostToDevice, st));
+        std::vector<uint8_t> hb((size_t)ne, 0);
+        if (pb.lts_enabled)
+            for (int64_t e = 0; e < ne; ++e) {
+                int b = b_from_bound(dt, mf.cfl[e]);
+                if (b < 0 || b > 15) b = 15;
+                hb[e] = (uint8_t)b;
+            }
+        MDL_CK(cudaMemcpyAsync(bcfl.p, hb.data(), hb.size(), cudaMemcpyHostToDevice, st));
+        for (int s = 0; s < pb.n_stim; ++s)
+            MDL_CK(cudaMemcpyAsync(smask[s].p, mf.smask[s].data(), mf.smask[s].size() * sizeof(uint32_t),
+                                   cudaMemcpyHostToDevice, st));
+        MDL_CK(cudaStreamSynchronize(st));
+        drop_graphs();
+        return MDL_OK;
     }
 
     int upload_mesh(int64_t n, const int32_t* rt, const int8_t* level, const int32_t* coords) override {
+        if (mapped) {
+            err = "upload_mesh: a mapped geometry runs on its root mesh";
+            return MDL_E_STATE;
+        }
         std::vector<Leaf> lv(n);
         for (int64_t i = 0; i < n; ++i) {
             lv[i].level = level[i];
@@ -938,6 +1008,10 @@ public:
             err = "set_sweep_variant: variant in {0, 1, 2, 3}";
             return MDL_E_ARG;
         }
+        if (mapped && variant != MDL_SWEEP_THREAD) {
+            err = "set_sweep_variant: a mapped geometry has the thread-per-element sweep only";
+            return MDL_E_ARG;
+        }
         if (variant == MDL_SWEEP_TENSOR && !tensor_capable) {
             err = "set_sweep_variant: the tensor-core sweep needs a Q2 3D FP32 context";
             return MDL_E_ARG;
@@ -1008,6 +1082,7 @@ public:
     }
 
     bool replaying() const override { return ovr_levels || ovr_eta_s || ovr_eta_t; }
+    bool is_mapped() const override { return mapped; }
 
     void* stream_handle() const override { return (void*)st; }
     int precision() const override { return sizeof(R) == 8 ? 64 : 32; }
@@ -1022,7 +1097,7 @@ public:
         add(Ia.cap + ga.cap, sizeof(R));
         add(acc.cap + eta_s.cap + lat.cap + partial.cap + scratch.cap + eta_t_ovr.cap + mtab.cap, 8);
         add(fscratch.cap, 4);
-        add(cview.cap, sizeof(R));
+        add(cview.cap + gvol.cap + gface.cap, sizeof(R));
         add(r.cap + c0.cap + class_b.cap + bcfl.cap + pkind.cap + pbits.cap + lvl_ovr.cap, 1);
         add(bcnt.cap + psrc.cap + nbr.cap + hang.cap + root.cap + order.cap + info.cap + loc.cap, 4);
         add(lkey.cap, 8);

@@ -87,6 +87,8 @@ struct DevArrays {
     const R* qvol;      // Q1 class blocks (see q1_blocks): volume, face, Kelly
     const R* qface;
     const R* qkelly;
+    const R* gvol;      // mapped meshes: per-element geometric factors (mdl_mapped.cuh)
+    const R* gface;
 };
 
 // Vector width for rows of NP values of type R: 16-byte loads when a row is a whole number
@@ -958,7 +960,7 @@ __global__ void k_eta_s(const DevArrays<R> d, const Tables<R> T, const Phys<R> p
 // check, per-block partial sums of int V = sum_q M_q V_q (FP64).
 template <typename R, int DIM, int P>
 __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const double* __restrict__ mtab,
-                                                 double dt, double inv_dt, int inv_dt_exact) {
+                                                 double dt, double inv_dt, int inv_dt_exact, int mass_per_elem) {
     pdl_enter();
     using S = Shape<DIM, P>;
     constexpr int NP = S::NP;
@@ -980,7 +982,8 @@ __global__ void __launch_bounds__(256) k_epilogue(const DevArrays<R> d, const do
         const R* Vc = (par ? d.V1 : d.V0) + (size_t)e * S::NPS;
         const R* w = d.v + (size_t)e * S::NPS;
         const int lev = (d.info[e] >> 24) & 15;
-        const double* Mq = mtab + lev * NP;
+        // GL masses: per (level, node) on box elements, per (element, node) on mapped ones
+        const double* Mq = mtab + (mass_per_elem ? (size_t)e * NP : (size_t)lev * NP);
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             const R x = Vc[q];

@@ -1,0 +1,227 @@
+// mdl_mapped.cuh -- the element step on curved (mapped) meshes: thread per element.
+//
+// The geometric factors of every element (mdl_geometry.h) are stored per GL point: at volume
+// node q the symmetric metric G_q and the mass M_q, at face point t the flux vector c, the
+// area weight dS and the penalty kappa.  The residual of element e (Eq. monodomain-primal-
+// formulation with the flux of Eq. monodomain-numerical-flux, all faces conforming):
+//   volume:  r_i += sum_q grad_xi psi_i(q) . G_q grad_xi u(q)
+//   face f:  at each point t, with the own trace u_o, the neighbour's trace u_n (its opposite
+//            face), flux = c . grad_xi u on each side and jump = u_o - u_n,
+//            r_i += dS [ (-(flux_o + flux_n)/2 + kappa jump) psi_i(t) - jump/2 c . grad_xi psi_i(t) ]
+// The pointwise update, RV-T term and probe check are those of the box elements with the
+// element's own GL mass M_q.
+#pragma once
+
+#include "mdl_kernels.cuh"
+
+namespace mdl {
+
+template <int DIM, int P>
+struct MapShape {
+    static constexpr int N1 = P + 1;
+    static constexpr int NP = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
+    static constexpr int NF = 2 * DIM;
+    static constexpr int NPF = DIM == 2 ? N1 : N1 * N1;
+    static constexpr int NS = DIM * (DIM + 1) / 2;
+    static constexpr int VPN = NS + 1;        // values per volume node: G, M
+    static constexpr int FPV = DIM + 2;       // values per face point: c, dS, kappa
+};
+
+// Entry (k, l) of the symmetric metric stored as (xx, yy, xy) or (xx, yy, zz, xy, xz, yz).
+template <int DIM>
+__device__ __forceinline__ int sym_index(int k, int l) {
+    if (k == l) return k;
+    if (DIM == 2) return 2;
+    const int a = k < l ? k : l, b = k < l ? l : k;
+    return a == 0 ? (b == 1 ? 3 : 4) : 5;
+}
+
+template <typename R, int DIM, int P>
+__device__ __forceinline__ void mapped_residual(const DevArrays<R>& d, const Tables<R>& T, int tick, int B, int e,
+                                                uint32_t inf, const R* u, R* r) {
+    using M = MapShape<DIM, P>;
+    constexpr int N1 = M::N1, NP = M::NP, NF = M::NF, NPF = M::NPF, VPN = M::VPN, FPV = M::FPV;
+    constexpr int NPS = Shape<DIM, P>::NPS;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r[q] = R(0);
+    // volume: flux G_q grad u at every node, then r_i = sum_k sum_m D1[m][a_k(i)] flux_k(node m of i's line)
+    {
+        const R* gv = d.gvol + (size_t)e * NP * VPN;
+        R fl[NP][DIM];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            R g[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                const int ak = digit<N1>(q, k);
+                R s = R(0);
+#pragma unroll
+                for (int m = 0; m < N1; ++m) s += T.D1[ak][m] * u[q + (m - ak) * stride<N1>(k)];
+                g[k] = s;
+            }
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                R s = R(0);
+#pragma unroll
+                for (int l = 0; l < DIM; ++l) s += gv[q * VPN + sym_index<DIM>(k, l)] * g[l];
+                fl[q][k] = s;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            R s = R(0);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                const int ak = digit<N1>(i, k);
+#pragma unroll
+                for (int m = 0; m < N1; ++m) s += T.D1[m][ak] * fl[i + (m - ak) * stride<N1>(k)][k];
+            }
+            r[i] = s;
+        }
+    }
+    // faces
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const int kind = (inf >> (4 * f)) & 3;
+        if (kind == 0) continue;
+        const int k = f >> 1, sd = f & 1;
+        R un[NP];
+        load_seen<R, NP, NPS>(d, tick, B, d.nbr[(size_t)e * NF + f], un);
+        const R* bs = sd ? T.bR : T.bL;
+        const R* ds = sd ? T.dR : T.dL;
+        const R* bn = sd ? T.bL : T.bR;
+        const R* dn = sd ? T.dL : T.dR;
+        int tg[2] = {0, 0};
+        {
+            int z = 0;
+#pragma unroll
+            for (int l = 0; l < DIM; ++l)
+                if (l != k) tg[z++] = l;
+        }
+        // traces and reference normal derivatives of both sides at the face points
+        R to[NPF], tn[NPF], go[NPF], gn[NPF];
+#pragma unroll
+        for (int t = 0; t < NPF; ++t) {
+            const int at0 = t % N1, at1 = t / N1;
+            int q0 = at0 * stride<N1>(tg[0]);
+            if (DIM == 3) q0 += at1 * stride<N1>(tg[1]);
+            R a = 0, b = 0, c = 0, g2 = 0;
+#pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                const int q = q0 + m * stride<N1>(k);
+                a += bs[m] * u[q];
+                c += ds[m] * u[q];
+                b += bn[m] * un[q];
+                g2 += dn[m] * un[q];
+            }
+            to[t] = a;
+            go[t] = c;
+            tn[t] = b;
+            gn[t] = g2;
+        }
+        const R* gf = d.gface + ((size_t)e * NF + f) * NPF * FPV;
+#pragma unroll
+        for (int t = 0; t < NPF; ++t) {
+            const int at[2] = {t % N1, t / N1};
+            const R* c = gf + t * FPV;
+            // c . grad_xi u on both sides: normal part + tangential derivatives of the traces
+            R flo = c[k] * go[t], fln = c[k] * gn[t];
+#pragma unroll
+            for (int z = 0; z < DIM - 1; ++z) {
+                const int st = z == 0 ? 1 : N1;            // face-point stride of tangent z
+                R so = 0, sn = 0;
+#pragma unroll
+                for (int a = 0; a < N1; ++a) {
+                    const int t2 = t + (a - at[z]) * st;
+                    so += T.D1[at[z]][a] * to[t2];
+                    sn += T.D1[at[z]][a] * tn[t2];
+                }
+                flo += c[tg[z]] * so;
+                fln += c[tg[z]] * sn;
+            }
+            const R dS = c[DIM], kap = c[DIM + 1];
+            const R jump = to[t] - tn[t];
+            const R A = dS * (R(-0.5) * (flo + fln) + kap * jump);
+            const R Bc = R(-0.5) * dS * jump;
+            int q0 = at[0] * stride<N1>(tg[0]);
+            if (DIM == 3) q0 += at[1] * stride<N1>(tg[1]);
+#pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                const int i = q0 + m * stride<N1>(k);
+                r[i] += A * bs[m] + Bc * c[k] * ds[m];
+#pragma unroll
+                for (int z = 0; z < DIM - 1; ++z) {
+                    const R w = Bc * c[tg[z]] * bs[m];
+#pragma unroll
+                    for (int a = 0; a < N1; ++a) r[i + (a - at[z]) * stride<N1>(tg[z])] += w * T.D1[at[z]][a];
+                }
+            }
+        }
+    }
+}
+
+// One element step of Alg. 1 on a mapped mesh (see tick_elem for the box elements).
+template <typename R, int DIM, int P>
+__device__ __forceinline__ void tick_elem_mapped(const TickArgs<R>& a, const Tables<R>& T, const Phys<R>& ph,
+                                                 int tick, int e) {
+    using M = MapShape<DIM, P>;
+    constexpr int NP = M::NP, VPN = M::VPN;
+    constexpr int NPS = Shape<DIM, P>::NPS;
+    const DevArrays<R>& d = a.d;
+    const uint8_t lvb = d.lvl[e];
+    const uint32_t inf = d.info[e];
+    const int b = lvb & 7, par = (lvb >> 3) & 1;
+    const int ke = tick >> (a.B - b);
+    const int cur = par ^ (ke & 1);
+    const R* Vc = (cur ? d.V1 : d.V0) + (size_t)e * NPS;
+    R* Vd = (cur ? d.V0 : d.V1) + (size_t)e * NPS;
+    R* vp = d.v + (size_t)e * NPS;
+    R u[NP], w[NP], r[NP], Ia[NP], ga[NP];
+    ld_dofs<R, NP, NPS>(Vc, u);
+    ld_dofs<R, NP, NPS>(vp, w);
+    mapped_residual<R, DIM, P>(d, T, tick, a.B, e, inf, u, r);
+    double acc0 = 0.0;
+    if (ke != 0) {
+        ld_dofs<R, NP, NPS>(d.Ia + (size_t)e * NPS, Ia);
+        ld_dofs<R, NP, NPS>(d.ga + (size_t)e * NPS, ga);
+        acc0 = d.acc[e];
+    }
+    bool stim = false;
+    for (int s = 0; s < a.stim.n; ++s) stim = stim || d.smask[s][e] != 0u;
+    const double dte_d = a.dte[b];
+    const R dte = a.dteR[b];
+    const R* gv = d.gvol + (size_t)e * NP * VPN;
+    R un[NP], wn[NP];
+    R term = R(0), vmax = R(0);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        R so = R(0), sm = R(0);
+        if (stim) dof_stim<R>(a, e, tick, dte_d, q, so, sm);
+        const R Mq = gv[q * VPN + VPN - 1];
+        term += dof_update<R>(ph, Mq, R(1) / Mq, ke, dte, so, sm, u[q], w[q], r[q], Ia[q], ga[q], un[q], wn[q]);
+        const R av = un[q] < R(0) ? -un[q] : un[q];
+        vmax = av > vmax ? av : vmax;
+    }
+    if (ke == 0 && b > 0) {
+        st_dofs<R, NP, NPS>(d.Ia + (size_t)e * NPS, Ia);
+        st_dofs<R, NP, NPS>(d.ga + (size_t)e * NPS, ga);
+    }
+    st_dofs<R, NP, NPS>(Vd, un);
+    st_dofs<R, NP, NPS>(vp, wn);
+    d.acc[e] = acc0 + dte_d * (double)term;
+    if ((inf & INFO_PENDING) && vmax >= ph.lat_gate) {
+        const int lev = (inf >> 24) & 15;
+        lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, tick_time(a, tick), dte_d);
+    }
+}
+
+template <typename R, int DIM, int P>
+__global__ void __launch_bounds__(128) k_tick_mapped(const TickArgs<R> a, const Tables<R> T, const Phys<R> ph) {
+    const int n_act = a.d.meta->nact[a.tick];
+    const bool bad = a.d.meta->err != 0;
+    pdl_enter();
+    if (bad) return;
+    for (int idx = (int)gtid(); idx < n_act; idx += (int)gstride()) tick_elem_mapped<R, DIM, P>(a, T, ph, a.tick, a.d.order[idx]);
+}
+
+}  // namespace mdl

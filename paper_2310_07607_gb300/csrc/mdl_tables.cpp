@@ -10,8 +10,6 @@
 
 namespace mdl {
 
-namespace {
-
 void gl_nodes(int p, double* x, double* w) {
     if (p == 1) {
         const double a = 1.0 / sqrt(3.0);
@@ -23,6 +21,8 @@ void gl_nodes(int p, double* x, double* w) {
         w[0] = 5.0 / 9.0; w[1] = 8.0 / 9.0; w[2] = 5.0 / 9.0;
     }
 }
+
+namespace {
 
 double lag(const double* x, int n, int j, double t) {
     double v = 1.0;

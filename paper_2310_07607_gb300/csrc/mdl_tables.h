@@ -10,6 +10,8 @@
 
 namespace mdl {
 
+// Nodes and weights of the (p+1)-point Gauss-Legendre rule on [-1, 1] (p = 1, 2).
+void gl_nodes(int p, double* x, double* w);
 // Basis tables of the (p+1)-point GL Lagrange basis (p = 1, 2), closed-form nodes.
 void make_tables(int p, Tables<double>* T);
 // Physics: D = (sigma_t I + (sigma_l - sigma_t) f f^T) / (chi C_m), per-level geometry,

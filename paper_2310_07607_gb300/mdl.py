@@ -50,6 +50,7 @@ class CProblem(C.Structure):
         ("act_threshold", C.c_double),
         ("state_integrator", C.c_int32), ("precision", C.c_int32),
         ("amr_enabled", C.c_int32), ("lts_enabled", C.c_int32),
+        ("geometry", C.c_int32), ("fibre_ref", C.c_int32), ("geo", C.c_double * 12),
     ]
 
 
@@ -182,6 +183,11 @@ def to_c(prob) -> CProblem:
     c.act_threshold = prob.act_threshold
     c.state_integrator, c.precision = prob.state_integrator, prob.precision
     c.amr_enabled, c.lts_enabled = prob.amr_enabled, prob.lts_enabled
+    c.geometry = int(getattr(prob, "geometry", 0))
+    c.fibre_ref = int(getattr(prob, "fibre_ref", 0))
+    geo = list(getattr(prob, "geo", ())) + [0.0] * 12
+    for i in range(12):
+        c.geo[i] = float(geo[i])
     return c
 
 
