@@ -7,7 +7,8 @@ indicator, 4 synchronous LTS levels, Aliev-Panfilov, transversely isotropic cond
 tensor cores.  The synthetic initial state is a planar excitation front at mid-slab;
 setup barriers let the AMR refine it to depth 3 (2.8M elements) before warm-up.
 `--workload slab2d` runs the 2D slab (2x2 cm, 256x256 Q1, AMR 3, LTS 4), `spiral2d` the
-temporal-adaptivity workload, `batch64` and `serve` the many-simulation workloads.
+temporal-adaptivity workload, `lv3d` the curved LV-like shell sector (mapped Q1 hexes,
+per-point geometric factors, LTS 4), `batch64` and `serve` the many-simulation workloads.
 
 A step is one barrier step of Alg. 1: eta^s, refine/coarsen (device forest bookkeeping),
 level assignment, all sweep ticks, eta^t, LAT, int V.  value = DOF-updates / s over the K
@@ -47,6 +48,7 @@ WORKLOADS = {
     "slab2d": (W.slab_2d_q1_256, 25.0, "<float,2,1>"),
     "slab3d": (W.slab_3d_q2, 17.6, "<float,3,2>"),
     "spiral2d": (W.spiral_2d_q1, 25.0, "<float,2,1>"),
+    "lv3d": (W.lv_3d_q1, 110.1, "<float,3,1>"),
 }
 SETUP_BARRIERS = 5
 # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum)
@@ -61,6 +63,9 @@ SETUP_BARRIERS = 5
 TRAFFIC_PER_LAUNCH = {
     ("slab2d", "k_tick<float,2,1>"): (10.354432e6 + 7 * (5.937920e6 + 5.938176e6) / 2.0) / 8.0,
 }
+# Mapped Q1 3D (lv3d): per element step the state 128 B, metadata and the RV-T accumulator
+# 49 B, and the element's geometric factors (8 nodes x 7 values + 6 faces x 4 points x 5
+# values, FP32) 704 B, over 8 DOFs: 110.1 B.
 # Algorithmic bytes per DOF-update of the fused sweep (Q1 2D, FP32, AP): V_old 4 + v 4 +
 # V_new 4 + v 4 = 16 B, plus per element step 2d neighbour ids + 4 B level/flags + the FP64
 # RV-T accumulator read-modify-write (36 B) over (p+1)^d = 4 DOFs.
@@ -141,6 +146,8 @@ def prob_order(factory):
 
 def workload_name(prob):
     b = prob.base
+    if getattr(prob, "geometry", 0):
+        return "lv3d_q1_%dx%dx%d_shell_lts%d_ap_fp32" % (b[0], b[1], b[2], prob.n_lts_levels)
     if prob.dim == 2 and not prob.amr_enabled:
         return "spiral2d_q1_%dx%d_lts%d_taucell_ap_fp32" % (b[0], b[1], prob.n_lts_levels)
     if prob.dim == 2:
@@ -194,7 +201,9 @@ def run_ours(args, rank, world):
     from paper_2310_07607_gb300 import build
     build.build()
     factory, alg_bytes, kname = WORKLOADS[args.workload]
-    if args.sweep == "group" and prob_order(factory) == 1:
+    if getattr(factory(), "geometry", 0):
+        kname = "k_tick_mapped" + kname
+    elif args.sweep == "group" and prob_order(factory) == 1:
         kname = "k_tick_group" + kname.replace(",1>", ">")
     elif args.sweep == "tensor" or (args.sweep == "default" and factory().order == 2 and factory().dim == 3):
         kname = "k_tick_tc<3,2>"
@@ -287,6 +296,8 @@ def run_ours(args, rank, world):
                                          if args.workload == "spiral2d" else
                                          "synthetic developed front, r=%.2f cm, width 0.01 cm" % (prob.extent[0] / 2.0)
                                          if prob.dim == 2 else
+                                         ("synthetic front at reference X_0=%.2f (a surface of constant azimuth), "
+                                          "width 0.012" % (prob.extent[0] / 2.0)) if getattr(prob, "geometry", 0) else
                                          "synthetic planar front at x=%.2f cm, width 0.012 cm" % (prob.extent[0] / 2.0)),
                        "l2": "512 MiB flush buffer written between timed steps",
                        "parallelism": "replicas" if world > 1 else "single"},

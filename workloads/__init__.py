@@ -158,6 +158,25 @@ SLAB3D_TAU = (1.0e-13, 1.0e-16)
 SLAB3D_T_END = 50.0
 
 
+def lv_3d_q1(base: Tuple[int, int, int] = (240, 96, 8)) -> Problem:
+    """LV-like curved slab (a stand-in for the paper's idealized left ventricle, Sec. 3.3):
+    an ellipsoidal shell sector with endocardial semi-axes (2.5, 2.5, 5.0) cm and epicardial
+    (3.5, 3.5, 6.0) cm, azimuth 0 .. 6 rad, polar angle 0.35 .. 1.9 rad (truncated below the
+    apex and past the equator), Q1 on 240 x 96 x 8 roots, fibres along the azimuth (3:1),
+    4 LTS levels from the per-element CFL bounds, the apical ring stimulated.  The reference
+    box has roughly the physical lengths (18 x 7.5 x 1 cm) so that reference and physical
+    element sizes are alike."""
+    geo = (2.5, 2.5, 5.0, 3.5, 3.5, 6.0, 0.0, 6.0, 0.35, 1.55)
+    return Problem(
+        dim=3, order=1, extent=(18.0, 7.5, 1.0), base=base,
+        sigma_l=1.2, sigma_t=0.4, fibre=(1.0, 0.0, 0.0), gamma=10.0,
+        stimuli=[Stimulus((-10.0, -10.0, 4.4), (10.0, 10.0, 10.0), 1.0, 0.0, 1.0)],
+        dt_barrier=0.0, max_refine=0, n_lts_levels=4,
+        tau_cell=0.5, dt_bar_cell=0.01, act_threshold=0.5, state_integrator=STATE_EXP,
+        precision=32, amr_enabled=0, lts_enabled=1,
+        geometry=GEOMETRY_SHELL, geo=geo, fibre_ref=1)
+
+
 def spiral_2d_q1(n: int = 80, h: float = 0.05) -> Problem:
     """Temporal adaptivity workload: a 2D Q1 square of n x n elements of size h (4x4 cm by
     default), isotropic 1.0 mS/cm, no AMR, 5 LTS levels, barrier step 0.1 ms and the
