@@ -62,6 +62,10 @@ SETUP_BARRIERS = 5
 # 2,736,960 elements by the elements due.
 TRAFFIC_PER_LAUNCH = {
     ("slab2d", "k_tick<float,2,1>"): (10.354432e6 + 7 * (5.937920e6 + 5.938176e6) / 2.0) / 8.0,
+    # curved LV-like slab at full size: the eight ticks of one barrier step
+    ("lv3d", "k_tick_mapped<float,3,1>"): 4.4873e7,
+    # 3D slab: the quarter slab's eight ticks, tick 0 and tick 4 scaled to the full slab
+    ("slab3d", "k_tick_tc<3,2>"): 1.9632e9,
 }
 # Mapped Q1 3D (lv3d): per element step the state 128 B, metadata and the RV-T accumulator
 # 49 B, and the element's geometric factors (8 nodes x 7 values + 6 faces x 4 points x 5
@@ -229,6 +233,11 @@ def run_ours(args, rank, world):
         V0, v0 = W.planar_front_state(X, PLANAR["x0"] * prob.extent[0] / 2.0, PLANAR["width"], PLANAR["tail"])
     sim.set_initial(V0, v0)
     sim.step_barriers(SETUP_BARRIERS)
+    # clocks are sampled from the warm-up on: nvidia-smi's start-up stalls the process's
+    # driver calls for a moment, which must not fall into the timed steps
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    time.sleep(0.5)
     sim.step_barriers(args.warmup)
     _, _, stream_ptr = sim.device_view(1)
     stream = torch.cuda.ExternalStream(stream_ptr)
@@ -236,11 +245,9 @@ def run_ours(args, rank, world):
     sim.reset_stats()
     sim.set_timing(True)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clk = ClockSampler(torch.cuda.current_device())
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clk.start()
     wall0 = time.perf_counter()
     for i in range(args.steps):
         with torch.cuda.stream(stream):
@@ -277,6 +284,12 @@ def run_ours(args, rank, world):
             "kernel": kname, "launches": st["tick_launches"],
             "avg_launch_us": round(st["sweep_ms"] * 1e3 / max(st["tick_launches"], 1), 3),
             "alg_bytes_per_dof_update": WORKLOADS[args.workload][1]}
+    if traffic:
+        # the same launches judged by their measured DRAM traffic (ncu, cold caches) instead of
+        # the algorithmic bytes
+        avg_s = st["sweep_ms"] / 1e3 / max(st["tick_launches"], 1)
+        roof["traffic_frac"] = round(traffic / avg_s / 1e9 / peak, 4)
+    roof["target"] = "0.6 of the HBM peak: not met"
     # end to end through the public API with host buffers: upload state, one barrier, read back
     e2e = run_e2e(sim, args, torch)
     out = None
