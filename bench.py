@@ -567,6 +567,12 @@ def completed_window(mdl, Request, Server, args, rate=3.0, arrivals_s=20.0, cap_
     reqs = mk()
     rep = srv.run(reqs, wall_limit_s=cap_s, drain=False)
     srv.close()
+    # capacity: the same requests all at once (the arrival-driven run is bound by the arrival
+    # rate; the plain loop, one request at a time, is saturated throughout its run)
+    srv = Server(budget_bytes=0, barriers_per_round=args.serve_round, autotune=True)
+    burst = srv.run([Request(rid=i, prob=p, horizon_ms=h, arrival_s=0.0) for i, (t, p, h) in enumerate(gen)],
+                    wall_limit_s=cap_s, drain=False)
+    srv.close()
     lat_p = {}
     plain = run_plain_loop(mdl, mk(), cap_s, keep=lat_p)
     per = []
@@ -604,6 +610,10 @@ def completed_window(mdl, Request, Server, args, rate=3.0, arrivals_s=20.0, cap_
                                                           "ttr_p99_s")},
         "sims_per_s_ratio_adaptive_over_plain": (rep["sims_per_s"] / plain["sims_per_s"]
                                                  if plain["sims_per_s"] > 0 else None),
+        "adaptive_fp32_batch_all_at_once": {k: burst[k] for k in ("completed", "wall_s", "sims_per_s", "ttr_p50_s",
+                                                                  "ttr_p99_s", "peak_resident")},
+        "capacity_ratio_adaptive_all_at_once_over_plain": (burst["sims_per_s"] / plain["sims_per_s"]
+                                                           if plain["sims_per_s"] > 0 else None),
         "accuracy": {
             "lat_adaptive_vs_plain_ms": {"requests": len(per), "median_of_mean": statistics.median(means)
                                          if means else None, "max_of_max": max(maxes) if maxes else None,
