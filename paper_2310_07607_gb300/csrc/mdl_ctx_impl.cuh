@@ -398,7 +398,8 @@ class Ctx : public CtxBase {
     int launch_phase(int ph_, int o) {
         const int g256 = persistent_blocks(256), g128 = persistent_blocks(128);
         if (ph_ == 0) {
-            MDL_CK(launch_k((k_eta_s<R, DIM, P>), g128, 128, arrays(o), T, ph));
+            if (mapped) MDL_CK(launch_k((k_eta_s_mapped<R, DIM, P>), g128, 128, arrays(o), T));
+            else MDL_CK(launch_k((k_eta_s<R, DIM, P>), g128, 128, arrays(o), T, ph));
             MDL_LAUNCHED();
             return MDL_OK;
         }
@@ -577,7 +578,9 @@ class Ctx : public CtxBase {
         const int o = cs;
         int rc;
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
-        if (pb.amr_enabled && !ovr_eta_s) {
+        // the spatial indicator: for the adaptation, and on a mapped mesh (which does not
+        // adapt) as the barrier's diagnostic
+        if ((pb.amr_enabled || mapped) && !ovr_eta_s) {
             if (timing && (e2 = next_event())) MDL_CK(cudaEventRecord(e2, st));
             if ((rc = run_phase(0, o, direct))) return rc;
             if (timing && (e3 = next_event())) MDL_CK(cudaEventRecord(e3, st));
@@ -1048,7 +1051,7 @@ public:
         fused_own = false;
         const int o = cs;
         int rc;
-        if (pb.amr_enabled && !ovr_eta_s && (rc = run_phase(0, o, direct))) return rc;
+        if ((pb.amr_enabled || mapped) && !ovr_eta_s && (rc = run_phase(0, o, direct))) return rc;
         if ((rc = run_phase(1, o, direct))) return rc;
         fused_cur = pb.amr_enabled ? (o ^ 1) : o;
         FusedSlot<R>* fs = static_cast<FusedSlot<R>*>(slot_record);

@@ -36,6 +36,73 @@ __device__ __forceinline__ int sym_index(int k, int l) {
     return a == 0 ? (b == 1 ? 3 : 4) : 5;
 }
 
+// Tangential axes of a normal-k face, increasing.
+template <int DIM>
+__device__ __forceinline__ void face_tangents(int k, int* tg) {
+    int z = 0;
+#pragma unroll
+    for (int l = 0; l < DIM; ++l)
+        if (l != k) tg[z++] = l;
+}
+
+// At the points t of face f = 2k + sd (sd = 1: the +k side), own and neighbour traces (to, tn)
+// and the normal fluxes c . grad_xi u of both sides (flo, fln): the normal derivative from
+// the 1D derivative values at the face, the tangential ones from the traces by the 1D
+// derivative matrix.  The neighbour is seen through its opposite face.
+template <typename R, int DIM, int P>
+__device__ __forceinline__ void mapped_face_fluxes(const Tables<R>& T, const R* u, const R* un, int k, int sd,
+                                                   const R* gf, R* to, R* tn, R* flo, R* fln) {
+    using M = MapShape<DIM, P>;
+    constexpr int N1 = M::N1, NPF = M::NPF, FPV = M::FPV;
+    const R* bs = sd ? T.bR : T.bL;
+    const R* ds = sd ? T.dR : T.dL;
+    const R* bn = sd ? T.bL : T.bR;
+    const R* dn = sd ? T.dL : T.dR;
+    int tg[2] = {0, 0};
+    face_tangents<DIM>(k, tg);
+    R go[NPF], gn[NPF];
+#pragma unroll
+    for (int t = 0; t < NPF; ++t) {
+        const int at0 = t % N1, at1 = t / N1;
+        int q0 = at0 * stride<N1>(tg[0]);
+        if (DIM == 3) q0 += at1 * stride<N1>(tg[1]);
+        R a = 0, b = 0, c = 0, g2 = 0;
+#pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            const int q = q0 + m * stride<N1>(k);
+            a += bs[m] * u[q];
+            c += ds[m] * u[q];
+            b += bn[m] * un[q];
+            g2 += dn[m] * un[q];
+        }
+        to[t] = a;
+        go[t] = c;
+        tn[t] = b;
+        gn[t] = g2;
+    }
+#pragma unroll
+    for (int t = 0; t < NPF; ++t) {
+        const int at[2] = {t % N1, t / N1};
+        const R* c = gf + t * FPV;
+        R fo = c[k] * go[t], fn = c[k] * gn[t];
+#pragma unroll
+        for (int z = 0; z < DIM - 1; ++z) {
+            const int st = z == 0 ? 1 : N1;            // face-point stride of tangent z
+            R so = 0, sn = 0;
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                const int t2 = t + (a - at[z]) * st;
+                so += T.D1[at[z]][a] * to[t2];
+                sn += T.D1[at[z]][a] * tn[t2];
+            }
+            fo += c[tg[z]] * so;
+            fn += c[tg[z]] * sn;
+        }
+        flo[t] = fo;
+        fln[t] = fn;
+    }
+}
+
 template <typename R, int DIM, int P>
 __device__ __forceinline__ void mapped_residual(const DevArrays<R>& d, const Tables<R>& T, int tick, int B, int e,
                                                 uint32_t inf, const R* u, R* r) {
@@ -89,59 +156,18 @@ __device__ __forceinline__ void mapped_residual(const DevArrays<R>& d, const Tab
         load_seen<R, NP, NPS>(d, tick, B, d.nbr[(size_t)e * NF + f], un);
         const R* bs = sd ? T.bR : T.bL;
         const R* ds = sd ? T.dR : T.dL;
-        const R* bn = sd ? T.bL : T.bR;
-        const R* dn = sd ? T.dL : T.dR;
         int tg[2] = {0, 0};
-        {
-            int z = 0;
-#pragma unroll
-            for (int l = 0; l < DIM; ++l)
-                if (l != k) tg[z++] = l;
-        }
-        // traces and reference normal derivatives of both sides at the face points
-        R to[NPF], tn[NPF], go[NPF], gn[NPF];
-#pragma unroll
-        for (int t = 0; t < NPF; ++t) {
-            const int at0 = t % N1, at1 = t / N1;
-            int q0 = at0 * stride<N1>(tg[0]);
-            if (DIM == 3) q0 += at1 * stride<N1>(tg[1]);
-            R a = 0, b = 0, c = 0, g2 = 0;
-#pragma unroll
-            for (int m = 0; m < N1; ++m) {
-                const int q = q0 + m * stride<N1>(k);
-                a += bs[m] * u[q];
-                c += ds[m] * u[q];
-                b += bn[m] * un[q];
-                g2 += dn[m] * un[q];
-            }
-            to[t] = a;
-            go[t] = c;
-            tn[t] = b;
-            gn[t] = g2;
-        }
+        face_tangents<DIM>(k, tg);
+        R to[NPF], tn[NPF], flo[NPF], fln[NPF];
         const R* gf = d.gface + ((size_t)e * NF + f) * NPF * FPV;
+        mapped_face_fluxes<R, DIM, P>(T, u, un, k, sd, gf, to, tn, flo, fln);
 #pragma unroll
         for (int t = 0; t < NPF; ++t) {
             const int at[2] = {t % N1, t / N1};
             const R* c = gf + t * FPV;
-            // c . grad_xi u on both sides: normal part + tangential derivatives of the traces
-            R flo = c[k] * go[t], fln = c[k] * gn[t];
-#pragma unroll
-            for (int z = 0; z < DIM - 1; ++z) {
-                const int st = z == 0 ? 1 : N1;            // face-point stride of tangent z
-                R so = 0, sn = 0;
-#pragma unroll
-                for (int a = 0; a < N1; ++a) {
-                    const int t2 = t + (a - at[z]) * st;
-                    so += T.D1[at[z]][a] * to[t2];
-                    sn += T.D1[at[z]][a] * tn[t2];
-                }
-                flo += c[tg[z]] * so;
-                fln += c[tg[z]] * sn;
-            }
             const R dS = c[DIM], kap = c[DIM + 1];
             const R jump = to[t] - tn[t];
-            const R A = dS * (R(-0.5) * (flo + fln) + kap * jump);
+            const R A = dS * (R(-0.5) * (flo[t] + fln[t]) + kap * jump);
             const R Bc = R(-0.5) * dS * jump;
             int q0 = at[0] * stride<N1>(tg[0]);
             if (DIM == 3) q0 += at[1] * stride<N1>(tg[1]);
@@ -212,6 +238,52 @@ __device__ __forceinline__ void tick_elem_mapped(const TickArgs<R>& a, const Tab
     if ((inf & INFO_PENDING) && vmax >= ph.lat_gate) {
         const int lev = (inf >> 24) & 15;
         lat_check<R, DIM, P>(d, T, ph, e, inf, lev, u, un, tick_time(a, tick), dte_d);
+    }
+}
+
+// Kelly-type spatial indicator (Eq. dg-error-estimate) on the mapped mesh, on the barrier-start
+// values: per interior face, with the flux jump J_t = (c . grad_xi u)_own - (c . grad_xi u)_nb,
+// the face area |F| = sum_t dS_t, h_F = |F|^(1/(d-1)) and the face map's Jacobian at the point
+// W_F(t) = dS_t / (reference GL weight of t): h_F / (2p) sum_t dS_t (W_F(t) J_t)^2.  Face-point
+// sums in the working precision, faces accumulated in FP64.
+template <typename R, int DIM, int P>
+__global__ void __launch_bounds__(128) k_eta_s_mapped(const DevArrays<R> d, const Tables<R> T) {
+    pdl_enter();
+    using M = MapShape<DIM, P>;
+    constexpr int N1 = M::N1, NP = M::NP, NF = M::NF, NPF = M::NPF, FPV = M::FPV;
+    constexpr int NPS = Shape<DIM, P>::NPS;
+    if (d.meta->err) return;
+    const int64_t ne = d.meta->ne;
+    for (int64_t e = gtid(); e < ne; e += gstride()) {
+        const uint32_t inf = d.info[e];
+        const int par = (d.lvl[e] >> 3) & 1;
+        R u[NP];
+        ld_dofs<R, NP, NPS>((par ? d.V1 : d.V0) + (size_t)e * NPS, u);
+        double acc = 0.0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const int kind = (inf >> (4 * f)) & 3;
+            if (kind == 0) continue;
+            const int nb = d.nbr[(size_t)e * NF + f];
+            R un[NP];
+            ld_dofs<R, NP, NPS>((((d.lvl[nb] >> 3) & 1) ? d.V1 : d.V0) + (size_t)nb * NPS, un);
+            const R* gf = d.gface + ((size_t)e * NF + f) * NPF * FPV;
+            R to[NPF], tn[NPF], flo[NPF], fln[NPF];
+            mapped_face_fluxes<R, DIM, P>(T, u, un, f >> 1, f & 1, gf, to, tn, flo, fln);
+            R area = R(0), sum = R(0);
+#pragma unroll
+            for (int t = 0; t < NPF; ++t) {
+                const R dS = gf[t * FPV + DIM];
+                const R wref = T.w[t % N1] * (DIM == 3 ? T.w[t / N1] : R(1));
+                const R WF = dS / wref;
+                const R jmp = WF * (flo[t] - fln[t]);
+                area += dS;
+                sum += dS * jmp * jmp;
+            }
+            const double hF = DIM == 3 ? sqrt((double)area) : (double)area;
+            acc += hF / (2.0 * P) * (double)sum;
+        }
+        d.eta_s[e] = sqrt(acc);
     }
 }
 

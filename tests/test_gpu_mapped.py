@@ -160,3 +160,30 @@ def test_mapped_slots_in_a_fused_batch_give_their_alone_values(mdl):
     assert np.array_equal(g.read_V(), Va)
     assert b.slot(s2)[1] == mdl.SLOT_DONE
     b.close()
+
+
+@pytest.mark.parametrize("dim,p,precision", [(2, 1, 64), (2, 2, 64), (3, 1, 64), (3, 2, 64), (3, 1, 32), (3, 2, 32)])
+def test_shell_kelly_indicator_matches_oracle(mdl, dim, p, precision):
+    """The spatial indicator on the mapped mesh, computed at the start of every barrier step:
+    after n steps it holds the indicator of the state n - 1 steps in (FP64 to 1e-10, FP32 with
+    FP64 face accumulation to 2e-3 of the largest value)."""
+    prob = shell_problem(dim, p, precision)
+    o = lts.Sim(prob.replace(precision=64))
+    V0, v0 = front(o, prob)
+    o.V, o.v = V0.copy(), v0.copy()
+    o._lat_initial()
+    g = mdl.Sim(prob)
+    g.set_initial(V0, v0)
+    nbar = 5
+    for _ in range(nbar - 1):
+        o.barrier()
+    want = o.disc.eta_s(o.V)
+    o.barrier()
+    g.step_barriers(nbar)
+    es, _ = g.read_indicators()
+    assert want.max() > 0
+    if precision == 64:
+        assert np.allclose(es, want, rtol=1e-10, atol=1e-14 * want.max())
+    else:
+        assert np.abs(es - want).max() <= 2e-3 * want.max()
+    g.close()

@@ -214,3 +214,37 @@ def test_oracle_steps_a_mapped_problem_with_lts():
     V, v = lts.global_fe(prob, o.A, o.disc.M, V0, v0, o.dt, 20, lambda t: o.i_stim(t))
     assert np.array_equal(V, o.V) and np.array_equal(v, o.v)
     assert np.any(o.V != 0)
+
+
+@pytest.mark.parametrize("hanging", [False, True])
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_rigid_motion_reproduces_the_box_kelly_indicator(dim, p, hanging):
+    """The mapped Kelly indicator under x = R X + b (fibre rotated along) equals the box
+    indicator, whose closed forms are pinned separately, on conforming and 2:1 meshes."""
+    prob = box_problem(dim, p)
+    R = rotation(dim)
+    f1 = R[:dim, :dim] @ np.array(prob.fibre[:dim])
+    pm = prob.replace(geometry=W.GEOMETRY_AFFINE, geo=tuple(R.ravel()) + (0.3, -0.2, 0.1),
+                      fibre=tuple(f1) + (0.0,) * (3 - dim))
+    f = random_forest(dim, prob.base, 2, prob.extent, steps=2, seed=3, tau=0.6) if hanging else \
+        Forest(dim, prob.base, 2, prob.extent)
+    d0, d1 = Disc(prob, f), MappedDisc(pm, f)
+    u = np.random.default_rng(2).normal(size=d0.ne * d0.n_p)
+    e0, e1 = d0.eta_s(u), d1.eta_s(u)
+    assert np.allclose(e1, e0, rtol=1e-11, atol=1e-14 * e0.max())
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (3, 2)])
+def test_kelly_indicator_vanishes_for_linear_fields_on_an_affine_mesh(dim, p):
+    """A linear field's flux D g is continuous, so every jump and the indicator vanish; a
+    field with a kink across one reference plane does not."""
+    prob = box_problem(dim, p).replace(geometry=W.GEOMETRY_AFFINE)
+    prob = prob.replace(geo=tuple(shear(dim).ravel()) + (0.05, 0.1, -0.2))
+    disc = MappedDisc(prob, Forest(dim, prob.base, 0, prob.extent))
+    X = disc.node_coords()
+    g = np.array([0.7, -1.1, 0.4][:dim])
+    es = disc.eta_s(X @ g)
+    assert es.max() <= 1e-12 * np.abs(X @ g).max()
+    kink = np.maximum(disc.ref_coords()[:, 0] - prob.extent[0] / prob.base[0], 0.0)
+    ek = disc.eta_s(kink)
+    assert ek.max() > 1e-10 and ek.max() > 1e4 * es.max()
