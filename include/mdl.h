@@ -177,7 +177,10 @@ int mdl_read_state(mdl_ctx* ctx, double* out, int64_t cap, int64_t* n);
  * precision of FP32 contexts; half the bytes of the FP64 calls).  mdl_set_initial_f32
  * behaves as mdl_set_initial.  mdl_read_fields_f32 writes V and the state variable (either
  * pointer may be NULL) at every DOF in leaf order with one gather and one synchronisation;
- * cap and *n are counted in DOFs per field. */
+ * cap and *n are counted in DOFs per field.  Page-locked host buffers mapped into the
+ * device's address space (cudaHostAlloc / cudaMallocHost, e.g. pinned framework tensors) are
+ * read or written by the layout kernel itself over the host link, with no staging copy;
+ * other host memory goes through one device copy.  The buffers are not retained. */
 int mdl_set_initial_f32(mdl_ctx* ctx, const float* V, const float* s, int64_t n_dof);
 int mdl_read_fields_f32(mdl_ctx* ctx, float* V, float* s, int64_t cap, int64_t* n);
 

@@ -1146,16 +1146,36 @@ public:
         return MDL_OK;
     }
 
+    // The device address of a page-locked host buffer mapped into the device's address space
+    // (cudaHostAlloc / pinned memory), or null for any other pointer (which is then staged
+    // through a device copy).
+    static const void* mapped_host(const void* p) {
+        if (!p) return nullptr;
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+    }
+
     int set_initial_f32(const float* V, const float* s, int64_t n_dof) override {
         if (n_dof != ne * NP || !V) {
             err = "set_initial_f32: n_dof must be n_elements * (p+1)^d";
             return MDL_E_ARG;
         }
-        MDL_CK(fscratch.ensure((size_t)2 * n_dof));
-        MDL_CK(cudaMemcpyAsync(fscratch.p, V, n_dof * sizeof(float), cudaMemcpyHostToDevice, st));
-        if (s) MDL_CK(cudaMemcpyAsync(fscratch.p + n_dof, s, n_dof * sizeof(float), cudaMemcpyHostToDevice, st));
-        k_scatter_initial<R, NP, NPS, float><<<div_up(ne * NPS, 256), 256, 0, st>>>(
-            arrays(cs), ne, fscratch.p, s ? fscratch.p + n_dof : nullptr);
+        // page-locked host buffers are read by the layout kernel itself over the host link;
+        // others go through one device copy first
+        const float* dV = static_cast<const float*>(mapped_host(V));
+        const float* dS = s ? static_cast<const float*>(mapped_host(s)) : nullptr;
+        if (!dV || (s && !dS)) {
+            MDL_CK(fscratch.ensure((size_t)2 * n_dof));
+            MDL_CK(cudaMemcpyAsync(fscratch.p, V, n_dof * sizeof(float), cudaMemcpyHostToDevice, st));
+            if (s) MDL_CK(cudaMemcpyAsync(fscratch.p + n_dof, s, n_dof * sizeof(float), cudaMemcpyHostToDevice, st));
+            dV = fscratch.p;
+            dS = s ? fscratch.p + n_dof : nullptr;
+        }
+        k_scatter_initial<R, NP, NPS, float><<<div_up(ne * NPS, 256), 256, 0, st>>>(arrays(cs), ne, dV, dS);
         MDL_LAUNCHED();
         MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
         k_lat_refresh<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(arrays(cs), T, ph, (double)nbar * dt, 1, 1);
@@ -1171,11 +1191,20 @@ public:
             err = "read_fields_f32: capacity too small";
             return MDL_E_ARG;
         }
-        MDL_CK(fscratch.ensure((size_t)2 * nd));
-        k_gather_f32<R, NP, NPS><<<div_up(nd, 256), 256, 0, st>>>(arrays(cs), ne, fscratch.p);
-        MDL_LAUNCHED();
-        if (V) MDL_CK(cudaMemcpyAsync(V, fscratch.p, nd * sizeof(float), cudaMemcpyDeviceToHost, st));
-        if (s) MDL_CK(cudaMemcpyAsync(s, fscratch.p + nd, nd * sizeof(float), cudaMemcpyDeviceToHost, st));
+        // page-locked host buffers are written by the layout kernel itself; others through a
+        // device copy
+        float* dV = V ? static_cast<float*>(const_cast<void*>(mapped_host(V))) : nullptr;
+        float* dS = s ? static_cast<float*>(const_cast<void*>(mapped_host(s))) : nullptr;
+        if ((V && !dV) || (s && !dS)) {
+            MDL_CK(fscratch.ensure((size_t)2 * nd));
+            k_gather_f32<R, NP, NPS><<<div_up(nd, 256), 256, 0, st>>>(arrays(cs), ne, fscratch.p, fscratch.p + nd);
+            MDL_LAUNCHED();
+            if (V) MDL_CK(cudaMemcpyAsync(V, fscratch.p, nd * sizeof(float), cudaMemcpyDeviceToHost, st));
+            if (s) MDL_CK(cudaMemcpyAsync(s, fscratch.p + nd, nd * sizeof(float), cudaMemcpyDeviceToHost, st));
+        } else {
+            k_gather_f32<R, NP, NPS><<<div_up(nd, 256), 256, 0, st>>>(arrays(cs), ne, dV, dS);
+            MDL_LAUNCHED();
+        }
         MDL_CK(cudaStreamSynchronize(st));
         return MDL_OK;
     }

@@ -1294,13 +1294,13 @@ __global__ void k_gather(const DevArrays<R> d, int64_t ne, int which, Out* out) 
 
 // V (current slot) and the state variable into one compact FP32 buffer [V | v].
 template <typename R, int NP, int NPS>
-__global__ void k_gather_f32(const DevArrays<R> d, int64_t ne, float* out) {
+__global__ void k_gather_f32(const DevArrays<R> d, int64_t ne, float* outV, float* outS) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= ne * NP) return;
     const int64_t e = i / NP, j = e * NPS + (i - e * NP);
     const int par = (d.lvl[e] >> 3) & 1;
-    out[i] = (float)((par ? d.V1 : d.V0)[j]);
-    out[ne * NP + i] = (float)d.v[j];
+    if (outV) outV[i] = (float)((par ? d.V1 : d.V0)[j]);
+    if (outS) outS[i] = (float)d.v[j];
 }
 
 // Set V (into slot 0, parity reset) and optionally v from compact FP64 or FP32 input; the
