@@ -124,8 +124,10 @@ class Sim:
                                                                prob.extent)
         self.B = prob.n_lts_levels - 1 if prob.lts_enabled else 0
         self.mapped = getattr(prob, "geometry", 0) != 0
-        if self.mapped and prob.amr_enabled:
-            raise ValueError("mapped geometry: adaptive refinement is not supported")
+        if self.mapped and prob.amr_enabled and not prob.dt_barrier > 0:
+            # the admissible elements of an adapting curved mesh are not a finite set of
+            # classes: the barrier step is the caller's
+            raise ValueError("mapped geometry with adaptation: dt_barrier must be given")
         self._rebuild()
         n = self.disc.ne * self.disc.n_p
         self.V = np.zeros(n) if V0 is None else np.array(V0, dtype=np.float64)
@@ -377,15 +379,27 @@ class Sim:
                 newv[ch[m]] = oldv[par[m]] @ phis[b].T
             eta_t[ch] = self.eta_t[par]
         pa = np.nonzero(kind == 2)[0]
+        new_disc = MappedDisc(self.prob, new_forest) if self.mapped else None
         if pa.size:
             kids = np.array([plan[i][1] for i in pa], dtype=np.int64)         # (npar, 2^d)
-            wc = wq / (2.0 ** d)                                              # child weights in parent measure
-            accV = np.zeros((pa.size, n_p)); accv = np.zeros((pa.size, n_p))
-            for b in range(1 << d):
-                accV += (wc[None, :] * oldV[kids[:, b]]) @ phis[b]
-                accv += (wc[None, :] * oldv[kids[:, b]]) @ phis[b]
-            newV[pa] = accV / wq[None, :]
-            newv[pa] = accv / wq[None, :]
+            if self.mapped:
+                # the children's GL masses against the parent's: M_p u_p = sum_c sum_qc M_c psi_p u_c
+                Mo = self.disc.M.reshape(-1, n_p)
+                Mn = new_disc.M.reshape(-1, n_p)
+                accV = np.zeros((pa.size, n_p)); accv = np.zeros((pa.size, n_p))
+                for b in range(1 << d):
+                    accV += (Mo[kids[:, b]] * oldV[kids[:, b]]) @ phis[b]
+                    accv += (Mo[kids[:, b]] * oldv[kids[:, b]]) @ phis[b]
+                newV[pa] = accV / Mn[pa]
+                newv[pa] = accv / Mn[pa]
+            else:
+                wc = wq / (2.0 ** d)                                          # child weights in parent measure
+                accV = np.zeros((pa.size, n_p)); accv = np.zeros((pa.size, n_p))
+                for b in range(1 << d):
+                    accV += (wc[None, :] * oldV[kids[:, b]]) @ phis[b]
+                    accv += (wc[None, :] * oldv[kids[:, b]]) @ phis[b]
+                newV[pa] = accV / wq[None, :]
+                newv[pa] = accv / wq[None, :]
             eta_t[pa] = self.eta_t[kids].mean(axis=1)
         self.forest = new_forest
         self._rebuild()

@@ -248,3 +248,48 @@ def test_kelly_indicator_vanishes_for_linear_fields_on_an_affine_mesh(dim, p):
     kink = np.maximum(disc.ref_coords()[:, 0] - prob.extent[0] / prob.base[0], 0.0)
     ek = disc.eta_s(kink)
     assert ek.max() > 1e-10 and ek.max() > 1e4 * es.max()
+
+
+def test_mapped_adaptation_conserves_the_integral_and_matches_the_box_under_rigid_motion():
+    """Alg. 1 with refinement and coarsening on a mapped mesh: (a) under a rigid motion (fibre
+    rotated along) the run is the box run -- the same meshes, levels and values to rounding --
+    and (b) on the shell, coarsening by the mass-weighted projection keeps the integral of V
+    (pure diffusion, no stimulus: the operator conserves it too)."""
+    dim, p = 2, 1
+    prob = box_problem(dim, p).replace(max_refine=2, n_lts_levels=3, lts_enabled=1, amr_enabled=1,
+                                       tau_refine=0.8, tau_coarsen=0.2, dt_barrier=2.0 ** -12,
+                                       state_integrator=W.STATE_EXP)
+    R = rotation(dim)
+    f1 = R[:dim, :dim] @ np.array(prob.fibre[:dim])
+    pm = prob.replace(geometry=W.GEOMETRY_AFFINE, geo=tuple(R.ravel()) + (0.3, -0.2, 0.1),
+                      fibre=tuple(f1) + (0.0,) * (3 - dim))
+    ob, om = lts.Sim(prob), lts.Sim(pm)
+    X = ob.disc.node_coords()
+    V0, v0 = W.front_state(X, (0, 0, 0), 0.15, 0.02, tail=0.05)
+    for o in (ob, om):
+        o.V, o.v = V0.copy(), v0.copy()
+    rng = np.random.default_rng(5)
+    for step in range(4):
+        eta = rng.uniform(0, 1, ob.disc.ne)
+        for o in (ob, om):
+            newf, plan = o.forest.adapt(eta, prob.tau_refine, prob.tau_coarsen)
+            o.transfer(newf, plan)
+            lev = o.assign_levels(o.eta_t)
+            o.eta_t = o.sweep(lev)
+            o.barrier_count += 1
+        assert ob.forest.leaves == om.forest.leaves
+        assert np.allclose(om.V, ob.V, rtol=0, atol=1e-12 * np.abs(ob.V).max())
+    # (b) shell, pure diffusion: the integral survives refinement and coarsening
+    sp = shell(2, 2, (6, 4, 1)).replace(ionic_model=-1, max_refine=2, n_lts_levels=1, amr_enabled=1,
+                                        tau_refine=0.8, tau_coarsen=0.3, dt_barrier=2.0 ** -14)
+    o = lts.Sim(sp)
+    o.V = np.cos(3.0 * o.disc.node_coords()[:, 0]) + 0.5
+    I0 = o.disc.M @ o.V
+    for step in range(5):
+        eta = rng.uniform(0, 1, o.disc.ne)
+        newf, plan = o.forest.adapt(eta, sp.tau_refine, sp.tau_coarsen)
+        o.transfer(newf, plan)
+        assert abs(o.disc.M @ o.V - I0) <= 1e-12 * abs(I0)
+        o.eta_t = o.sweep(o.assign_levels(o.eta_t))
+        o.barrier_count += 1
+    assert abs(o.disc.M @ o.V - I0) <= 1e-11 * abs(I0)
