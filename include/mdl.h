@@ -56,9 +56,13 @@ extern "C" {
  * so elements are curved wherever Phi is; the SIPG terms (Eq. monodomain-primal-formulation,
  * Eq. monodomain-numerical-flux) take the Jacobian, area weight, normal and normal extent of
  * every GL point, and each element its own Gershgorin bound (Eq. cfl-monodomain).  A mapped
- * geometry runs on the fixed root mesh: amr_enabled = 0 and max_refine = 0 (MDL_E_ARG
- * otherwise), the thread-per-element sweep only, no mdl_upload_mesh.  Stimulus boxes and
- * the fibre are in physical coordinates; probes stay the GL nodes of the roots.
+ * geometry adapts like a box slab (hanging faces integrated at the finer side's points; the
+ * restriction weighted by the elements' own GL masses) but needs dt_barrier > 0 when it
+ * adapts (MDL_E_ARG otherwise: an adapting curved mesh has no finite set of element classes
+ * to bound the step by); it runs the thread-per-element sweep only and takes no
+ * mdl_upload_mesh.  Its factors are recomputed on the device for every element whose face
+ * kinds change.  Stimulus boxes and the fibre are in physical coordinates; probes stay the
+ * GL nodes of the roots.
  *   MDL_GEOMETRY_BOX     Phi = identity (geo ignored)
  *   MDL_GEOMETRY_AFFINE  Phi(X) = A X + b, geo = (A row-major 3x3, b[3]); 2D: leading 2x2, b[0..1]
  *   MDL_GEOMETRY_SHELL   ellipsoidal shell sector, geo = (a_i, b_i, c_i, a_o, b_o, c_o, phi0,

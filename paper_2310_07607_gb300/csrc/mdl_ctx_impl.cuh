@@ -94,8 +94,16 @@ class Ctx : public CtxBase {
         DBuf<double> eta_t;
         DBuf<uint8_t> lvl;
         DBuf<int4> coord;
+        // mapped meshes: each element's geometric factors, GL masses, signature (face kinds,
+        // level, b^CFL) and stimulus masks, which follow the element through adaptations
+        DBuf<R> gvol, gface;
+        DBuf<double> mq;
+        DBuf<uint32_t> fsig;
+        DBuf<uint32_t> fsm[MDL_MAX_STIM];
         void release() {
             V0.release(); V1.release(); v.release(); eta_t.release(); lvl.release(); coord.release();
+            gvol.release(); gface.release(); mq.release(); fsig.release();
+            for (auto& m : fsm) m.release();
         }
     };
 
@@ -134,8 +142,8 @@ class Ctx : public CtxBase {
     DBuf<double> eta_t_ovr;
     DBuf<double> mtab;   // FP64 GL mass w_q det J per (level, node); mapped: per (element, node)
     DBuf<R> qvol, qface, qkelly;   // Q1 class blocks
-    bool mapped = false;           // curved mesh (mdl_geometry.h): fixed root mesh, own factors
-    DBuf<R> gvol, gface;           // its per-element geometric factors (mdl_mapped.cuh)
+    bool mapped = false;           // curved mesh (mdl_geometry.h): per-element factors in the sets
+    MapArgs margs{};               // its map, diffusion, GL nodes and stimulus boxes for k_mapped_factors
     DBuf<uint16_t> tcB;            // Q2 3D FP32: level-0 operator of the tensor-core sweep (FP16 hi/lo)
     float tc_unscale = 1.0f;       // 2^-t: undoes the scaling of the operator by 2^t
     DBuf<float> tcC;               // Q2 3D FP32: level-0 correction blocks of non-regular faces
@@ -217,13 +225,17 @@ class Ctx : public CtxBase {
         d.qvol = qvol.p;
         d.qface = qface.p;
         d.qkelly = qkelly.p;
-        d.gvol = gvol.p;
-        d.gface = gface.p;
+        d.gvol = x.gvol.p;
+        d.gface = x.gface.p;
+        d.mq = mapped ? x.mq.p : nullptr;
         return d;
     }
 
     // ------------------------------------------------------------------
     // Allocation.  Growing keeps the current set's contents.
+    static constexpr int MAP_VOL = NP * (DIM * (DIM + 1) / 2 + 1);      // factor values per element
+    static constexpr int MAP_FACE = NF * (DIM == 2 ? N1 : N1 * N1) * (DIM + 2);
+
     int alloc_set(Set& x, int64_t c) {
         MDL_CK(x.V0.ensure((size_t)c * NPS));
         MDL_CK(x.V1.ensure((size_t)c * NPS));
@@ -231,6 +243,13 @@ class Ctx : public CtxBase {
         MDL_CK(x.eta_t.ensure(c));
         MDL_CK(x.lvl.ensure(c));
         MDL_CK(x.coord.ensure(c));
+        if (mapped) {
+            MDL_CK(x.gvol.ensure((size_t)c * MAP_VOL));
+            MDL_CK(x.gface.ensure((size_t)c * MAP_FACE));
+            MDL_CK(x.mq.ensure((size_t)c * NP));
+            MDL_CK(x.fsig.ensure(c));
+            for (int s = 0; s < pb.n_stim; ++s) MDL_CK(x.fsm[s].ensure(c));
+        }
         return MDL_OK;
     }
 
@@ -284,6 +303,10 @@ class Ctx : public CtxBase {
 #define MDL_GROW(buf, per) if ((rc = grow_copy(buf, (size_t)c * (per), (size_t)ne * (per)))) return rc
         MDL_GROW(x.V0, NPS); MDL_GROW(x.V1, NPS); MDL_GROW(x.v, NPS); MDL_GROW(x.eta_t, 1);
         MDL_GROW(x.lvl, 1); MDL_GROW(x.coord, 1);
+        if (mapped) {
+            MDL_GROW(x.gvol, MAP_VOL); MDL_GROW(x.gface, MAP_FACE); MDL_GROW(x.mq, NP); MDL_GROW(x.fsig, 1);
+            for (int s = 0; s < pb.n_stim; ++s) MDL_GROW(x.fsm[s], 1);
+        }
         MDL_GROW(bcfl, 1); MDL_GROW(info, 1); MDL_GROW(loc, 1); MDL_GROW(nbr, NF); MDL_GROW(hang, NF * NSUB);
         MDL_GROW(root, 1); MDL_GROW(order, 1); MDL_GROW(lkey, 1);
         for (int s = 0; s < pb.n_stim; ++s) MDL_GROW(smask[s], 1);
@@ -430,6 +453,17 @@ class Ctx : public CtxBase {
                 DevArrays<R> od = arrays(o);
                 int rc = build_tables(n, 0);
                 if (rc) return rc;
+                if (mapped) {
+                    // factors of the new set: copied for elements kept with the same face kinds,
+                    // computed for the rest (every barrier: the sets alternate)
+                    MDL_CK(launch_k((k_mapped_factors<R, DIM, P>), persistent_blocks(64), 64, sn.coord.p, info.p,
+                                    margs, Td, sn.gvol.p, sn.gface.p, sn.mq.p, sn.fsig.p, sn.fsm[0].p, sn.fsm[1].p,
+                                    sn.fsm[2].p, sn.fsm[3].p, bcfl.p, smask[0].p, smask[1].p, smask[2].p,
+                                    smask[3].p, so.gvol.p, so.gface.p, so.mq.p, so.fsig.p, so.fsm[0].p,
+                                    so.fsm[1].p, so.fsm[2].p, so.fsm[3].p, (const int8_t*)pkind.p,
+                                    (const int32_t*)psrc.p, meta.p));
+                    MDL_LAUNCHED();
+                }
                 MDL_CK(launch_k((k_transfer<R, DIM, P>), g128, 128, od, arrays(n), pkind.p, psrc.p, pbits.p, T));
                 MDL_LAUNCHED();
                 MDL_CK(launch_k((k_lat_refresh<R, DIM, P>), g128, 128, arrays(n), T, ph, 0.0, 0, 0));
@@ -517,8 +551,8 @@ class Ctx : public CtxBase {
         {
             int ex = 0;
             const double fr = frexp(dt, &ex);
-            MDL_CK(launch_k((k_epilogue<R, DIM, P>), g256, 256, arrays(o), mtab.p, dt, 1.0 / dt,
-                            fr == 0.5 ? 1 : 0, mapped ? 1 : 0));
+            MDL_CK(launch_k((k_epilogue<R, DIM, P>), g256, 256, arrays(o), mapped ? sets[o].mq.p : mtab.p, dt,
+                            1.0 / dt, fr == 0.5 ? 1 : 0, mapped ? 1 : 0));
         }
         MDL_LAUNCHED();
         return MDL_OK;
@@ -629,7 +663,6 @@ public:
         for (auto& m : smask) m.release();
         lvl_ovr.release(); eta_t_ovr.release(); meta.release(); mtab.release(); dT.release(); dph.release();
         qvol.release(); qface.release(); qkelly.release(); tcB.release(); tcC.release();
-        gvol.release(); gface.release();
         if (hmeta) cudaFreeHost(hmeta);
         for (auto e : evpool) cudaEventDestroy(e);
         if (st) cudaStreamDestroy(st);
@@ -751,7 +784,6 @@ public:
         MDL_CK(dph.ensure(1));
         MDL_CK(cudaMemcpy(dT.p, &T, sizeof(Tables<R>), cudaMemcpyHostToDevice));
         MDL_CK(cudaMemcpy(dph.p, &ph, sizeof(Phys<R>), cudaMemcpyHostToDevice));
-        if (mapped) hm = mf.mass;
         MDL_CK(mtab.ensure(hm.size()));
         MDL_CK(cudaMemcpyAsync(mtab.p, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         MDL_CK(class_b.ensure(hcb.size()));
@@ -766,29 +798,33 @@ public:
         return load_mapped(mf);
     }
 
-    // Mapped meshes: the factors of the root mesh, each element's b^CFL from its own bound,
-    // and the stimulus masks of the physical node positions (replacing the box tables).
+    // Mapped meshes: the factors, GL masses, b^CFL and stimulus masks of every element of the
+    // current mesh, computed on the device (replacing the box tables of the mesh build).
     int load_mapped(const MappedFactors& mf) {
         if (mf.ne != ne) {
             err = "mapped geometry: factor count does not match the mesh";
             return MDL_E_STATE;
         }
-        std::vector<R> gv(mf.gvol.begin(), mf.gvol.end()), gf(mf.gface.begin(), mf.gface.end());
-        MDL_CK(gvol.ensure(gv.size()));
-        MDL_CK(gface.ensure(gf.size()));
-        MDL_CK(cudaMemcpyAsync(gvol.p, gv.data(), gv.size() * sizeof(R), cudaMemcpyHostToDevice, st));
-        MDL_CK(cudaMemcpyAsync(gface.p, gf.data(), gf.size() * sizeof(R), cudaMemcpyHostToDevice, st));
-        std::vector<uint8_t> hb((size_t)ne, 0);
-        if (pb.lts_enabled)
-            for (int64_t e = 0; e < ne; ++e) {
-                int b = b_from_bound(dt, mf.cfl[e]);
-                if (b < 0 || b > 15) b = 15;
-                hb[e] = (uint8_t)b;
-            }
-        MDL_CK(cudaMemcpyAsync(bcfl.p, hb.data(), hb.size(), cudaMemcpyHostToDevice, st));
+        margs.g = geo_args(pb);
+        double wg[3];
+        gl_nodes(P, margs.xg, wg);
+        for (int k = 0; k < 3; ++k) margs.h0[k] = k < DIM ? pb.extent[k] / pb.base[k] : 1.0;
+        margs.nstim = pb.n_stim;
         for (int s = 0; s < pb.n_stim; ++s)
-            MDL_CK(cudaMemcpyAsync(smask[s].p, mf.smask[s].data(), mf.smask[s].size() * sizeof(uint32_t),
-                                   cudaMemcpyHostToDevice, st));
+            for (int k = 0; k < 3; ++k) {
+                margs.slo[s][k] = pb.stim[s].lo[k] - 1e-12;
+                margs.shi[s][k] = pb.stim[s].hi[k] + 1e-12;
+            }
+        margs.dt = dt;
+        margs.B = B;
+        margs.lts = pb.lts_enabled;
+        Set& x = sets[cs];
+        const int nb = (int)std::min<int64_t>(div_up(std::max<int64_t>(ne, 1), 64), (int64_t)nsm * 8);
+        k_mapped_factors<R, DIM, P><<<nb, 64, 0, st>>>(
+            x.coord.p, info.p, margs, Td, x.gvol.p, x.gface.p, x.mq.p, x.fsig.p, x.fsm[0].p, x.fsm[1].p,
+            x.fsm[2].p, x.fsm[3].p, bcfl.p, smask[0].p, smask[1].p, smask[2].p, smask[3].p, nullptr, nullptr, nullptr,
+            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, meta.p);
+        MDL_LAUNCHED();
         MDL_CK(cudaStreamSynchronize(st));
         drop_graphs();
         return MDL_OK;
@@ -1100,7 +1136,13 @@ public:
         add(Ia.cap + ga.cap, sizeof(R));
         add(acc.cap + eta_s.cap + lat.cap + partial.cap + scratch.cap + eta_t_ovr.cap + mtab.cap, 8);
         add(fscratch.cap, 4);
-        add(cview.cap + gvol.cap + gface.cap, sizeof(R));
+        add(cview.cap, sizeof(R));
+        for (const auto& x : sets) {
+            add(x.gvol.cap + x.gface.cap, sizeof(R));
+            add(x.mq.cap, 8);
+            add(x.fsig.cap, 4);
+            for (const auto& m : x.fsm) add(m.cap, 4);
+        }
         add(r.cap + c0.cap + class_b.cap + bcfl.cap + pkind.cap + pbits.cap + lvl_ovr.cap, 1);
         add(bcnt.cap + psrc.cap + nbr.cap + hang.cap + root.cap + order.cap + info.cap + loc.cap, 4);
         add(lkey.cap, 8);

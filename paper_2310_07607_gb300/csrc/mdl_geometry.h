@@ -29,8 +29,12 @@
 
 #include "../../include/mdl.h"
 #include "mdl_element.cuh"
+#include "mdl_geofactors.cuh"
 
 namespace mdl {
+
+// The problem's geometry and diffusion as plain values for geo_eval / geo_element.
+GeoArgs geo_args(const mdl_problem& p);
 
 // x = Phi(X) and J = DPhi(X) (J[i][j] = d x_i / d X_j) of the problem's map; 3D layout,
 // 2D uses the leading 2 x 2 block.

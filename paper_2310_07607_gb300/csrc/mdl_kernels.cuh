@@ -89,6 +89,7 @@ struct DevArrays {
     const R* qkelly;
     const R* gvol;      // mapped meshes: per-element geometric factors (mdl_mapped.cuh)
     const R* gface;
+    const double* mq;   // mapped meshes: per-element GL masses (null on boxes)
 };
 
 // Vector width for rows of NP values of type R: 16-byte loads when a row is a whole number
@@ -1478,9 +1479,15 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
             const R* wo = o.v + (size_t)ch * NPS;
             et += o.eta_t[ch];
             for (int qc = 0; qc < NP; ++qc) {
+                // the child's GL weight in the parent's measure; on a mapped mesh the child's
+                // own GL mass (divided by the parent's below)
                 R wc = R(1);
+                if (o.mq) {
+                    wc = (R)o.mq[(size_t)ch * NP + qc];
+                } else {
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) wc *= T.w[digit<N1>(qc, k)] * R(0.5);
+                    for (int k = 0; k < DIM; ++k) wc *= T.w[digit<N1>(qc, k)] * R(0.5);
+                }
                 const R xv = wc * Vo[qc], xw = wc * wo[qc];
 #pragma unroll
                 for (int q = 0; q < NP; ++q) {
@@ -1495,8 +1502,12 @@ __global__ void k_transfer(const DevArrays<R> o, DevArrays<R> n, const int8_t* p
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             R wq = R(1);
+            if (n.mq) {
+                wq = (R)n.mq[(size_t)i * NP + q];
+            } else {
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) wq *= T.w[digit<N1>(q, k)];
+                for (int k = 0; k < DIM; ++k) wq *= T.w[digit<N1>(q, k)];
+            }
             Vn[q] = a[q] / wq;
             wn[q] = c[q] / wq;
         }

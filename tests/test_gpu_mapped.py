@@ -187,3 +187,45 @@ def test_shell_kelly_indicator_matches_oracle(mdl, dim, p, precision):
     else:
         assert np.abs(es - want).max() <= 2e-3 * want.max()
     g.close()
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_shell_adaptation_replay_matches_oracle(mdl, dim, p):
+    """Adaptation on the curved shell (2:1 meshes with hanging faces): with the oracle's random
+    indicators replayed, four barrier steps of refinement and coarsening give the same meshes
+    and LTS levels (the device recomputes the factors and each element's bound where the face
+    kinds change), V to 1e-12 (the hanging-face terms and the mass-weighted restriction); then
+    the device's own indicator on the adapted mesh equals the oracle's to 1e-10."""
+    from tests.helpers import forest_arrays
+    base = shell_problem(dim, p, 64, base=(6, 4, 1) if dim == 2 else (4, 3, 2))
+    dt0 = lts.Sim(base).dt
+    prob = base.replace(max_refine=2, amr_enabled=1, tau_refine=0.7, tau_coarsen=0.3, dt_barrier=dt0 / 32)
+    o = lts.Sim(prob)
+    V0, v0 = front(o, prob)
+    o.V, o.v = V0.copy(), v0.copy()
+    o._lat_initial()
+    g = mdl.Sim(prob)
+    g.set_initial(V0, v0)
+    rng = np.random.default_rng(dim * 10 + p)
+    hanging = False
+    for step in range(4):
+        eta = rng.uniform(0, 1, o.disc.ne)
+        g.set_indicators(eta_s=eta)
+        newf, plan = o.forest.adapt(eta, prob.tau_refine, prob.tau_coarsen)
+        o.transfer(newf, plan)
+        lev = o.assign_levels(o.eta_t)
+        o.eta_t = o.sweep(lev)
+        o.barrier_count += 1
+        g.step_barriers(1)
+        r2, l2, c2, b2 = g.read_mesh()
+        lvo, cco, _ = forest_arrays(o.forest)
+        assert np.array_equal(l2, lvo) and np.array_equal(c2, cco)
+        assert np.array_equal(b2, lev)
+        assert mass_rel_l2(o.disc.M, g.read_V(), o.V) <= 1e-12, step
+        hanging = hanging or (l2.max() > l2.min())
+    assert hanging
+    want = o.disc.eta_s(o.V)
+    g.step_barriers(1)
+    es, _ = g.read_indicators()
+    assert np.allclose(es, want, rtol=1e-10, atol=1e-14 * want.max())
+    g.close()
