@@ -8,7 +8,8 @@ tensor cores.  The synthetic initial state is a planar excitation front at mid-s
 setup barriers let the AMR refine it to depth 3 (2.8M elements) before warm-up.
 `--workload slab2d` runs the 2D slab (2x2 cm, 256x256 Q1, AMR 3, LTS 4), `spiral2d` the
 temporal-adaptivity workload, `lv3d` the curved LV-like shell sector (mapped Q1 hexes,
-per-point geometric factors, LTS 4), `batch64` and `serve` the many-simulation workloads.
+per-point geometric factors, LTS 4; `lv3d_amr` with octree adaptation to depth 2), `batch64` and
+`serve` the many-simulation workloads.
 
 A step is one barrier step of Alg. 1: eta^s, refine/coarsen (device forest bookkeeping),
 level assignment, all sweep ticks, eta^t, LAT, int V.  value = DOF-updates / s over the K
@@ -49,6 +50,7 @@ WORKLOADS = {
     "slab3d": (W.slab_3d_q2, 17.6, "<float,3,2>"),
     "spiral2d": (W.spiral_2d_q1, 25.0, "<float,2,1>"),
     "lv3d": (W.lv_3d_q1, 110.1, "<float,3,1>"),
+    "lv3d_amr": (W.lv_3d_q1_amr, 110.1, "<float,3,1>"),
 }
 SETUP_BARRIERS = 5
 # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum)
@@ -151,7 +153,9 @@ def prob_order(factory):
 def workload_name(prob):
     b = prob.base
     if getattr(prob, "geometry", 0):
-        return "lv3d_q1_%dx%dx%d_shell_lts%d_ap_fp32" % (b[0], b[1], b[2], prob.n_lts_levels)
+        return "lv3d_q1_%dx%dx%d_shell%s_lts%d_ap_fp32" % (b[0], b[1], b[2],
+                                                           "_amr%d" % prob.max_refine if prob.amr_enabled else "",
+                                                           prob.n_lts_levels)
     if prob.dim == 2 and not prob.amr_enabled:
         return "spiral2d_q1_%dx%d_lts%d_taucell_ap_fp32" % (b[0], b[1], prob.n_lts_levels)
     if prob.dim == 2:

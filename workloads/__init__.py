@@ -177,6 +177,17 @@ def lv_3d_q1(base: Tuple[int, int, int] = (240, 96, 8)) -> Problem:
         geometry=GEOMETRY_SHELL, geo=geo, fibre_ref=1)
 
 
+def lv_3d_q1_amr(base: Tuple[int, int, int] = (120, 48, 4)) -> Problem:
+    """The LV-like shell sector of lv_3d_q1 on half as many roots per direction with octree
+    adaptation to depth 2 (the finest elements as in lv_3d_q1 at 4x its resolution): the
+    paper's idealized LV runs adapt (Sec. 3.3).  An adapting curved mesh takes its barrier step
+    from the caller: 2^-6 ms, where the depth-2 elements need the 4 LTS levels (the root mesh
+    alone allows 2^-2 ms).  Thresholds as the completed-request generator's 3D Q1 class
+    (similar element size)."""
+    return lv_3d_q1(base).replace(max_refine=2, amr_enabled=1, dt_barrier=2.0 ** -6,
+                                  tau_refine=COMPLETED_TAU[(3, 1)][0], tau_coarsen=COMPLETED_TAU[(3, 1)][1])
+
+
 def spiral_2d_q1(n: int = 80, h: float = 0.05) -> Problem:
     """Temporal adaptivity workload: a 2D Q1 square of n x n elements of size h (4x4 cm by
     default), isotropic 1.0 mS/cm, no AMR, 5 LTS levels, barrier step 0.1 ms and the
