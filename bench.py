@@ -326,6 +326,7 @@ def run_ours(args, rank, world):
                 "sweep": st["sweep_ms"] / args.steps, "eta_s": st["indicator_ms"] / args.steps,
                 "amr_host": st["amr_host_ms"] / args.steps, "mesh_upload_transfer": st["transfer_ms"] / args.steps},
             "amr_rebuilds": st["amr_rebuilds"],
+            **({"factor_updates_per_step": st["factor_updates"] / args.steps} if prob.geometry else {}),
             "sweep_only_dof_updates_per_s": st["dof_updates"] / sweep_s if sweep_s > 0 else None,
             # host clock around the same K steps: each step also holds the L2 flush and the
             # library's end-of-call synchronisation (one read of the device bookkeeping)

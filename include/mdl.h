@@ -132,6 +132,8 @@ typedef struct mdl_stats {
     double  integral_V;        /* last FP64 integral of V over the domain */
     int64_t n_elements;        /* current leaf count */
     int64_t level_counts[8];   /* elements per LTS level b in the last barrier */
+    int64_t factor_updates;    /* curved meshes: elements whose geometric factors were computed
+                                  (at creation and after each adaptation; kept elements copy theirs) */
 } mdl_stats;
 
 /* Create a context: base grid of roots, V = v = 0 (rest), t = 0.

@@ -196,6 +196,7 @@ static __global__ void k_scan_top(int64_t* bsum, DevMeta* m, int64_t cap) {
             m->ne_new = ne;          // old count, read by the emit pass
             m->ne = carry;
             m->cur_set ^= 1u;
+            m->nfac = 0u;
             if (m->changed) m->rebuilds++;
         }
     }

@@ -84,9 +84,10 @@ int64_t estimate_footprint(const mdl_problem& p) {
     const int64_t shared = 2 * np * r + 8 + 8 + 1 + 1 + 8 + 1 + 1 + 4 + 4;
     int64_t tables = 1 + 4 + 4 + 4 * nf + 4 * nf * nsub + 4 + 4 + 4 * p.n_stim + 8;
     if (p.geometry != MDL_GEOMETRY_BOX) {
-        // per set: geometric factors, GL masses, signature and stimulus masks of every element
+        // per set: geometric factors, GL masses, signature and stimulus masks of every element;
+        // the list of elements whose factors an adaptation recomputes
         const int64_t npf = d == 2 ? n1 : n1 * n1;
-        tables += 2 * ((np0 * (d * (d + 1) / 2 + 1) + nf * npf * (d + 2)) * r + np0 * 8 + 4 + 4 * p.n_stim);
+        tables += 2 * ((np0 * (d * (d + 1) / 2 + 1) + nf * npf * (d + 2)) * r + np0 * 8 + 4 + 4 * p.n_stim) + 4;
     }
     return cap * (2 * per_set + shared + tables) + roots * np0 * 8 + (1 << 20);
 }

@@ -139,6 +139,7 @@ class Ctx : public CtxBase {
     DBuf<int32_t> nbr, hang, root, order;
     DBuf<uint32_t> smask[MDL_MAX_STIM];
     DBuf<int8_t> pkind, pbits, lvl_ovr;
+    DBuf<int32_t> ftodo;   // curved meshes: elements whose factors an adaptation recomputes
     DBuf<double> eta_t_ovr;
     DBuf<double> mtab;   // FP64 GL mass w_q det J per (level, node); mapped: per (element, node)
     DBuf<R> qvol, qface, qkelly;   // Q1 class blocks
@@ -278,6 +279,7 @@ class Ctx : public CtxBase {
         MDL_CK(pkind.ensure(c));
         MDL_CK(pbits.ensure(c));
         MDL_CK(psrc.ensure(c));
+        if (mapped) MDL_CK(ftodo.ensure(c));
         MDL_CK(partial.ensure((size_t)nsm * 16 + 1024));
         return MDL_OK;
     }
@@ -315,7 +317,7 @@ class Ctx : public CtxBase {
         sets[cs ^ 1].release();
         if ((rc = alloc_set(sets[cs ^ 1], c))) return rc;
         Ia.release(); ga.release(); acc.release(); r.release(); c0.release();
-        bsum.release(); bcnt.release(); pkind.release(); pbits.release(); psrc.release();
+        bsum.release(); bcnt.release(); pkind.release(); pbits.release(); psrc.release(); ftodo.release();
         if ((rc = alloc_shared(c))) return rc;
         if (lvl_ovr.p && (rc = grow_copy(lvl_ovr, (size_t)c, (size_t)ne))) return rc;
         if (eta_t_ovr.p && (rc = grow_copy(eta_t_ovr, (size_t)c, (size_t)ne))) return rc;
@@ -336,6 +338,7 @@ class Ctx : public CtxBase {
         stats.element_updates = hmeta->elem_updates;
         stats.dof_updates = hmeta->elem_updates * NP;
         stats.amr_rebuilds = hmeta->rebuilds;
+        stats.factor_updates = hmeta->fac_updates;
         for (int b = 0; b < 8; ++b) stats.level_counts[b] = hmeta->cnt[b];
         return MDL_OK;
     }
@@ -456,12 +459,16 @@ class Ctx : public CtxBase {
                 if (mapped) {
                     // factors of the new set: copied for elements kept with the same face kinds,
                     // computed for the rest (every barrier: the sets alternate)
-                    MDL_CK(launch_k((k_mapped_factors<R, DIM, P>), persistent_blocks(64), 64, sn.coord.p, info.p,
-                                    margs, Td, sn.gvol.p, sn.gface.p, sn.mq.p, sn.fsig.p, sn.fsm[0].p, sn.fsm[1].p,
-                                    sn.fsm[2].p, sn.fsm[3].p, bcfl.p, smask[0].p, smask[1].p, smask[2].p,
-                                    smask[3].p, so.gvol.p, so.gface.p, so.mq.p, so.fsig.p, so.fsm[0].p,
-                                    so.fsm[1].p, so.fsm[2].p, so.fsm[3].p, (const int8_t*)pkind.p,
-                                    (const int32_t*)psrc.p, meta.p));
+                    MDL_CK(launch_k((k_mapped_keep<R, DIM, P>), persistent_blocks(256), 256, info.p, margs.nstim,
+                                    sn.gvol.p, sn.gface.p, sn.mq.p, sn.fsig.p, sn.fsm[0].p, sn.fsm[1].p, sn.fsm[2].p,
+                                    sn.fsm[3].p, bcfl.p, smask[0].p, smask[1].p, smask[2].p, smask[3].p, so.gvol.p,
+                                    so.gface.p, so.mq.p, so.fsig.p, so.fsm[0].p, so.fsm[1].p, so.fsm[2].p,
+                                    so.fsm[3].p, (const int8_t*)pkind.p, (const int32_t*)psrc.p, ftodo.p, meta.p));
+                    MDL_LAUNCHED();
+                    MDL_CK(launch_k((k_mapped_factors<R, DIM, P>), nsm * 8, 64, sn.coord.p, info.p, margs, Td,
+                                    sn.gvol.p, sn.gface.p, sn.mq.p, sn.fsig.p, sn.fsm[0].p, sn.fsm[1].p, sn.fsm[2].p,
+                                    sn.fsm[3].p, bcfl.p, smask[0].p, smask[1].p, smask[2].p, smask[3].p,
+                                    (const int32_t*)ftodo.p, meta.p));
                     MDL_LAUNCHED();
                 }
                 MDL_CK(launch_k((k_transfer<R, DIM, P>), g128, 128, od, arrays(n), pkind.p, psrc.p, pbits.p, T));
@@ -819,11 +826,16 @@ public:
         margs.B = B;
         margs.lts = pb.lts_enabled;
         Set& x = sets[cs];
-        const int nb = (int)std::min<int64_t>(div_up(std::max<int64_t>(ne, 1), 64), (int64_t)nsm * 8);
-        k_mapped_factors<R, DIM, P><<<nb, 64, 0, st>>>(
+        MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, nfac), 0, sizeof(unsigned int), st));
+        const int nb = (int)std::min<int64_t>(div_up(std::max<int64_t>(ne, 1), 256), (int64_t)nsm * 8);
+        k_mapped_keep<R, DIM, P><<<nb, 256, 0, st>>>(
+            info.p, margs.nstim, x.gvol.p, x.gface.p, x.mq.p, x.fsig.p, x.fsm[0].p, x.fsm[1].p, x.fsm[2].p,
+            x.fsm[3].p, bcfl.p, smask[0].p, smask[1].p, smask[2].p, smask[3].p, nullptr, nullptr, nullptr, nullptr,
+            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, ftodo.p, meta.p);
+        MDL_LAUNCHED();
+        k_mapped_factors<R, DIM, P><<<nsm * 8, 64, 0, st>>>(
             x.coord.p, info.p, margs, Td, x.gvol.p, x.gface.p, x.mq.p, x.fsig.p, x.fsm[0].p, x.fsm[1].p,
-            x.fsm[2].p, x.fsm[3].p, bcfl.p, smask[0].p, smask[1].p, smask[2].p, smask[3].p, nullptr, nullptr, nullptr,
-            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, meta.p);
+            x.fsm[2].p, x.fsm[3].p, bcfl.p, smask[0].p, smask[1].p, smask[2].p, smask[3].p, ftodo.p, meta.p);
         MDL_LAUNCHED();
         MDL_CK(cudaStreamSynchronize(st));
         drop_graphs();
@@ -1144,7 +1156,7 @@ public:
             for (const auto& m : x.fsm) add(m.cap, 4);
         }
         add(r.cap + c0.cap + class_b.cap + bcfl.cap + pkind.cap + pbits.cap + lvl_ovr.cap, 1);
-        add(bcnt.cap + psrc.cap + nbr.cap + hang.cap + root.cap + order.cap + info.cap + loc.cap, 4);
+        add(bcnt.cap + psrc.cap + ftodo.cap + nbr.cap + hang.cap + root.cap + order.cap + info.cap + loc.cap, 4);
         add(lkey.cap, 8);
         for (const auto& m : smask) add(m.cap, 4);
         add(bsum.cap, 8);
@@ -1333,7 +1345,7 @@ public:
         return MDL_OK;
     }
     int reset_stats() override {
-        MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, elem_updates), 0, 2 * sizeof(int64_t), st));
+        MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, elem_updates), 0, 3 * sizeof(int64_t), st));
         MDL_CK(cudaStreamSynchronize(st));
         stats = mdl_stats{};
         stats.n_elements = ne;

@@ -46,7 +46,9 @@ struct DevMeta {
     int32_t nact[128];       // due elements per tick
     int64_t elem_updates;    // accumulated element steps
     int64_t rebuilds;        // barriers whose mesh changed
+    int64_t fac_updates;     // curved meshes: elements whose factors were computed
     double integral;         // FP64 int V after the last barrier
+    unsigned int nfac;       // curved meshes: elements whose factors the adaptation recomputes
 };
 
 constexpr unsigned ERR_NONFINITE = 1u, ERR_CFL = 2u, ERR_CAPACITY = 4u, ERR_MESH = 8u;

@@ -473,28 +473,304 @@ __device__ __forceinline__ int b_from_bound_dev(double dt, double bound) {
     return 15;
 }
 
-// Every element's geometric factors, GL masses, signature (face kinds in bits 0-11, b^CFL in
-// bits 16-19) and stimulus masks on the current mesh, and the shared b^CFL and mask tables.  An
-// element kept by the adaptation (pkind 0) with the face kinds it had takes its old values
-// (source psrc in the old set); the others are computed in FP64 (geo_element, shared with the
-// host).  Without an old set (o* null) every element is computed.
+// Factors of the current mesh after an adaptation, part 1.  An element kept by the adaptation
+// (pkind 0) with the face kinds it had takes its old factors, GL masses, signature (face kinds
+// in bits 0-11, level in bits 12-15, b^CFL in bits 16-19) and stimulus masks (source psrc in the
+// old set); a warp walks 32 consecutive elements and copies each kept element's factor rows with
+// its lanes (coalesced).  Every other element is appended to `todo` (count m->nfac, zeroed by
+// the scan that commits the new mesh) for k_mapped_factors.  Without an old set (o* null)
+// every element is appended.
 template <typename R, int DIM, int P>
-__global__ void __launch_bounds__(64) k_mapped_factors(
-        const int4* coord, const uint32_t* info, const MapArgs a, const Tables<double> Td, R* gvol, R* gface,
-        double* mass, uint32_t* fsig, uint32_t* f0, uint32_t* f1, uint32_t* f2, uint32_t* f3, uint8_t* bcfl,
-        uint32_t* sm0, uint32_t* sm1, uint32_t* sm2, uint32_t* sm3, const R* ogvol, const R* ogface,
-        const double* omass, const uint32_t* ofsig, const uint32_t* of0, const uint32_t* of1, const uint32_t* of2,
-        const uint32_t* of3, const int8_t* pkind, const int32_t* psrc, DevMeta* m) {
+__global__ void __launch_bounds__(256) k_mapped_keep(
+        const uint32_t* info, const int nstim, R* gvol, R* gface, double* mass, uint32_t* fsig, uint32_t* f0,
+        uint32_t* f1, uint32_t* f2, uint32_t* f3, uint8_t* bcfl, uint32_t* sm0, uint32_t* sm1, uint32_t* sm2,
+        uint32_t* sm3, const R* ogvol, const R* ogface, const double* omass, const uint32_t* ofsig,
+        const uint32_t* of0, const uint32_t* of1, const uint32_t* of2, const uint32_t* of3, const int8_t* pkind,
+        const int32_t* psrc, int32_t* todo, DevMeta* m) {
     pdl_enter();
     using M = MapShape<DIM, P>;
-    constexpr int NP = M::NP, NF = M::NF, NPF = M::NPF, VPN = M::VPN, FPV = M::FPV;
-    constexpr int NV = NP * VPN, NFV = NF * NPF * FPV;
+    constexpr int NP = M::NP, NF = M::NF;
+    constexpr int NV = NP * M::VPN, NFV = NF * M::NPF * M::FPV;
     if (m->err) return;
     uint32_t* smask[4] = {sm0, sm1, sm2, sm3};
     uint32_t* fsm[4] = {f0, f1, f2, f3};
     const uint32_t* ofsm[4] = {of0, of1, of2, of3};
     const int64_t ne = m->ne;
-    for (int64_t e = gtid(); e < ne; e += gstride()) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarp = gstride() >> 5;
+    for (int64_t base = (gtid() >> 5) * 32; base < ne; base += nwarp * 32) {
+        const int64_t e = base + lane;
+        bool keep = false;
+        int64_t o = 0;
+        if (e < ne && ofsig) {
+            const uint32_t inf = info[e];
+            uint32_t kbits = 0;
+            for (int f = 0; f < NF; ++f) kbits |= ((inf >> (4 * f)) & 3u) << (2 * f);
+            if (pkind[e] == 0) {
+                o = psrc[e];
+                const uint32_t sg = ofsig[o];
+                keep = (sg & 0xfffu) == kbits;
+                if (keep) {
+                    fsig[e] = sg;
+                    bcfl[e] = (uint8_t)((sg >> 16) & 15u);
+                    for (int s = 0; s < nstim; ++s) smask[s][e] = fsm[s][e] = ofsm[s][o];
+                }
+            }
+        }
+        const unsigned need = __ballot_sync(0xffffffffu, e < ne && !keep);
+        if (need) {
+            int slot = 0;
+            if (lane == 0) slot = (int)atomicAdd(&m->nfac, (unsigned)__popc(need));
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if ((need >> lane) & 1u) todo[slot + __popc(need & ((1u << lane) - 1u))] = (int32_t)e;
+        }
+        for (unsigned kept = __ballot_sync(0xffffffffu, keep); kept; kept &= kept - 1u) {
+            const int l = __ffs(kept) - 1;
+            const int64_t ek = base + l, ok = __shfl_sync(0xffffffffu, o, l);
+            for (int i = lane; i < NV; i += 32) gvol[(size_t)ek * NV + i] = ogvol[(size_t)ok * NV + i];
+            for (int i = lane; i < NFV; i += 32) gface[(size_t)ek * NFV + i] = ogface[(size_t)ok * NFV + i];
+            for (int i = lane; i < NP; i += 32) mass[(size_t)ek * NP + i] = omass[(size_t)ok * NP + i];
+        }
+    }
+}
+
+// One element's factors computed by a whole warp: the arithmetic of geo_element, with the lanes
+// over the element's GL points (map, metric, face factors; chunks of 32 points) and over the
+// entries of its own block B (registers; every entry summed over the points in geo_element's
+// order).  FP64 issues at a small fraction of the FP32 rate on this GPU, so one element's
+// instructions are spread over 32 lanes rather than run by one.
+template <int DIM, int P>
+struct GeoWarp {
+    static constexpr int N1 = P + 1;
+    static constexpr int NP = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
+    static constexpr int NF = 2 * DIM, NPF = DIM == 2 ? N1 : N1 * N1, NSUB = 1 << (DIM - 1);
+    static constexpr int NS = DIM * (DIM + 1) / 2, VPN = NS + 1, FPV = DIM + 2;
+    static constexpr int CH = 32;                   // points per chunk (one per lane)
+    static constexpr int PS = 2 * NP + 2;           // doubles per point: psi, c.grad psi, dS, kappa (face);
+                                                    // the metric K (volume node)
+    static constexpr int NE = (NP * NP + 31) / 32;  // block entries per lane
+    static_assert(PS >= DIM * DIM && CH * PS >= NP * NP, "point record too small");
+};
+
+// Returns the Gershgorin bound (every lane); writes the element's volume factors and GL masses
+// (gvol, gface, mass: the element's rows) and returns its stimulus masks in sk (every lane).
+// spt: CH * PS doubles and sm: NP doubles of shared memory owned by the warp.
+template <typename R, int DIM, int P>
+__device__ double geo_element_warp(const GeoArgs& g, const Tables<double>& T, const double* xg, const double* h0,
+                                   int lev, const int* cc, const int* kinds, int nstim, const double (*slo)[3],
+                                   const double (*shi)[3], double* spt, double* sm, R* gvol, R* gface, double* mass,
+                                   uint32_t* sk) {
+    using W = GeoWarp<DIM, P>;
+    constexpr int N1 = W::N1, NP = W::NP, NF = W::NF, NPF = W::NPF, NS = W::NS, VPN = W::VPN, FPV = W::FPV;
+    constexpr int CH = W::CH, PS = W::PS, NE = W::NE;
+    const int lane = threadIdx.x & 31;
+    double h[3] = {1.0, 1.0, 1.0}, Xc[3] = {0.0, 0.0, 0.0};
+    const double sc = 1.0 / (double)(1 << lev);
+    for (int k = 0; k < DIM; ++k) {
+        h[k] = h0[k] * sc;
+        Xc[k] = cc[k] * h[k];
+    }
+    // points: the NP volume nodes, then per face with a neighbour its GL points (kind 3: the
+    // finer neighbours' points, subface outer)
+    int off[NF + 1];
+    off[0] = NP;
+    for (int f = 0; f < NF; ++f) off[f + 1] = off[f] + (kinds[f] ? NPF * (kinds[f] == 3 ? W::NSUB : 1) : 0);
+    const int npt = off[NF];
+    for (int f = 0; f < NF; ++f)
+        if (kinds[f] == 0 || kinds[f] == 3)
+            for (int i = lane; i < NPF * FPV; i += 32) gface[f * NPF * FPV + i] = (R)0;
+    uint32_t mk[MDL_MAX_STIM] = {0u, 0u, 0u, 0u};
+    double bacc[NE];
+#pragma unroll
+    for (int u = 0; u < NE; ++u) bacc[u] = 0.0;
+    for (int c0 = 0; c0 < npt; c0 += CH) {
+        const int p = c0 + lane;
+        double* rec = spt + lane * PS;
+        if (p < NP) {
+            const int q = p;
+            double X[3] = {0.0, 0.0, 0.0}, x[3], J[3][3], Ji[3][3], D[3][3];
+            double Wq = 1.0;
+            for (int k = 0; k < DIM; ++k) {
+                const int a = digit<N1>(q, k);
+                X[k] = Xc[k] + (xg[a] + 1.0) * 0.5 * h[k];
+                Wq *= T.w[a] * h[k] * 0.5;
+            }
+            geo_eval(g, X, x, J);
+            const double det = geo_inverse(DIM, J, Ji);
+            geo_tensor(g, J, D);
+            double K[3][3];
+            for (int i = 0; i < DIM; ++i)
+                for (int j = 0; j < DIM; ++j) {
+                    double s = 0.0;
+                    for (int a = 0; a < DIM; ++a)
+                        for (int b = 0; b < DIM; ++b) s += Ji[i][a] * D[a][b] * Ji[j][b];
+                    K[i][j] = Wq * fabs(det) * (2.0 / h[i]) * s * (2.0 / h[j]);
+                    rec[i * DIM + j] = K[i][j];
+                }
+            R* gv = gvol + q * VPN;
+            if (DIM == 2) {
+                gv[0] = (R)K[0][0]; gv[1] = (R)K[1][1]; gv[2] = (R)K[0][1];
+            } else {
+                gv[0] = (R)K[0][0]; gv[1] = (R)K[1][1]; gv[2] = (R)K[2][2];
+                gv[3] = (R)K[0][1]; gv[4] = (R)K[0][2]; gv[5] = (R)K[1][2];
+            }
+            const double mq = Wq * fabs(det);
+            mass[q] = mq;
+            gv[NS] = (R)mq;
+            sm[q] = mq;
+            for (int s = 0; s < nstim; ++s) {
+                bool in = true;
+                for (int k = 0; k < DIM; ++k) in = in && x[k] >= slo[s][k] && x[k] <= shi[s][k];
+                if (in) mk[s] |= 1u << q;
+            }
+        } else if (p < npt) {
+            int f = 0;
+            while (off[f + 1] <= p) ++f;
+            const int kind = kinds[f], r = p - off[f], sb = r / NPF, t = r - sb * NPF;
+            const int k = f >> 1, sd = f & 1;
+            const double sgn = sd ? 1.0 : -1.0;
+            int tg[2] = {0, 0}, nt = 0;
+            for (int l = 0; l < DIM; ++l)
+                if (l != k) tg[nt++] = l;
+            const double* bs = sd ? T.bR : T.bL;
+            const double* ds = sd ? T.dR : T.dL;
+            const double pen = kind == 2 ? 0.75 : (kind == 3 ? 1.5 : 1.0);   // (1 + h_own / h_nb) / 2
+            const int at[2] = {t % N1, t / N1};
+            double X[3] = {0.0, 0.0, 0.0};
+            double Wt = 1.0;
+            double xi_t[2] = {0.0, 0.0};
+            X[k] = Xc[k] + (sd ? h[k] : 0.0);
+            for (int z = 0; z < nt; ++z) {
+                const int l = tg[z];
+                if (kind == 3) {
+                    const int bit = (sb >> z) & 1;
+                    const double xf = (xg[at[z]] + 2.0 * bit - 1.0) * 0.5;
+                    X[l] = Xc[l] + (xf + 1.0) * 0.5 * h[l];
+                    Wt *= T.w[at[z]] * h[l] * 0.25;
+                    xi_t[z] = xf;
+                } else {
+                    X[l] = Xc[l] + (xg[at[z]] + 1.0) * 0.5 * h[l];
+                    Wt *= T.w[at[z]] * h[l] * 0.5;
+                    xi_t[z] = xg[at[z]];
+                }
+            }
+            double c[3] = {0.0, 0.0, 0.0}, adet = 0.0, ln = 0.0, nDn = 0.0;
+            geo_face_point(g, X, h, k, sgn, c, &adet, &ln, &nDn);
+            const double dS = Wt * adet * ln;
+            const double kap = g.gamma * nDn * ln / h[k] * pen;
+            if (sb == 0 && kind != 3) {
+                R* gf = gface + (f * NPF + t) * FPV;
+                for (int i = 0; i < DIM; ++i) gf[i] = (R)c[i];
+                gf[DIM] = (R)dS;
+                gf[DIM + 1] = (R)kap;
+            }
+            double lt[2][3], dlt[2][3];
+            for (int z = 0; z < nt; ++z) geo_lagrange<N1>(xg, xi_t[z], lt[z], dlt[z]);
+            for (int i = 0; i < NP; ++i) {
+                const int ak = digit<N1>(i, k);
+                double tv = 1.0;
+                for (int z = 0; z < nt; ++z) tv *= lt[z][digit<N1>(i, tg[z])];
+                double cgi = c[k] * ds[ak] * tv;
+                for (int z = 0; z < nt; ++z) {
+                    double dz = bs[ak] * dlt[z][digit<N1>(i, tg[z])];
+                    for (int z2 = 0; z2 < nt; ++z2)
+                        if (z2 != z) dz *= lt[z2][digit<N1>(i, tg[z2])];
+                    cgi += c[tg[z]] * dz;
+                }
+                rec[i] = bs[ak] * tv;
+                rec[NP + i] = cgi;
+            }
+            rec[2 * NP] = dS;
+            rec[2 * NP + 1] = kap;
+        }
+        __syncwarp();
+        // block entries (i, j) = (ent / NP, ent % NP), ent = lane + 32 u, summed over the chunk's points
+        const int pe = min(CH, npt - c0);
+        for (int pp = 0; pp < pe; ++pp) {
+            const double* d = spt + pp * PS;
+            if (c0 + pp < NP) {
+                // volume node q: B_ij += g_i^T K g_j, g_i = grad psi_i at q (nonzero when i and q
+                // differ in at most one digit k: D1[q_k][i_k] there)
+                const int q = c0 + pp;
+#pragma unroll
+                for (int u = 0; u < NE; ++u) {
+                    const int ent = lane + 32 * u;
+                    if (ent >= NP * NP) continue;
+                    const int i = ent / NP, j = ent - (ent / NP) * NP;
+                    int di = 0, ki = 0, dj = 0, kj = 0;
+                    for (int k = 0; k < DIM; ++k) {
+                        if (digit<N1>(i, k) != digit<N1>(q, k)) { ++di; ki = k; }
+                        if (digit<N1>(j, k) != digit<N1>(q, k)) { ++dj; kj = k; }
+                    }
+                    if (di > 1 || dj > 1) continue;
+                    double s = bacc[u];
+                    for (int k = 0; k < DIM; ++k) {
+                        if (di == 1 && k != ki) continue;
+                        const double gik = T.D1[digit<N1>(q, k)][digit<N1>(i, k)];
+                        for (int l = 0; l < DIM; ++l) {
+                            if (dj == 1 && l != kj) continue;
+                            s += gik * d[k * DIM + l] * T.D1[digit<N1>(q, l)][digit<N1>(j, l)];
+                        }
+                    }
+                    bacc[u] = s;
+                }
+            } else {
+                const double dS = d[2 * NP], kap = d[2 * NP + 1];
+#pragma unroll
+                for (int u = 0; u < NE; ++u) {
+                    const int ent = lane + 32 * u;
+                    if (ent >= NP * NP) continue;
+                    const int i = ent / NP, j = ent - (ent / NP) * NP;
+                    const double pi = d[i], ci = d[NP + i];
+                    if (pi == 0.0 && ci == 0.0) continue;
+                    bacc[u] += dS * (-0.5 * d[NP + j] * pi - 0.5 * ci * d[j] + kap * pi * d[j]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // Gershgorin: max_i sum_j |B_ij| / M_i
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+        const int ent = lane + 32 * u;
+        if (ent < NP * NP) spt[ent] = fabs(bacc[u]);
+    }
+    __syncwarp();
+    double mx = 0.0;
+    if (lane < NP) {
+        double row = 0.0;
+        for (int j = 0; j < NP; ++j) row += spt[lane * NP + j];
+        mx = row / sm[lane];
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int s = 0; s < nstim; ++s) sk[s] = __reduce_or_sync(0xffffffffu, mk[s]);
+    __syncwarp();
+    return 1.0 / mx;
+}
+
+// Part 2: the factors of the listed elements (todo[0 .. m->nfac)), one warp per element
+// (geo_element_warp), with their b^CFL, signature and stimulus masks.  List entry j goes to
+// warp j mod (number of warps), the warps numbered block-fastest, so that a run of neighbouring
+// elements (a refined patch) spreads over every SM.
+template <typename R, int DIM, int P>
+__global__ void __launch_bounds__(64) k_mapped_factors(
+        const int4* coord, const uint32_t* info, const MapArgs a, const Tables<double> Td, R* gvol, R* gface,
+        double* mass, uint32_t* fsig, uint32_t* f0, uint32_t* f1, uint32_t* f2, uint32_t* f3, uint8_t* bcfl,
+        uint32_t* sm0, uint32_t* sm1, uint32_t* sm2, uint32_t* sm3, const int32_t* todo, DevMeta* m) {
+    pdl_enter();
+    using W = GeoWarp<DIM, P>;
+    constexpr int NP = W::NP, NF = W::NF;
+    constexpr int NV = NP * W::VPN, NFV = NF * W::NPF * W::FPV;
+    __shared__ double s_pt[2][W::CH * W::PS];
+    __shared__ double s_m[2][NP];
+    if (m->err) return;
+    uint32_t* smask[4] = {sm0, sm1, sm2, sm3};
+    uint32_t* fsm[4] = {f0, f1, f2, f3};
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n = m->nfac;
+    if (blockIdx.x == 0 && threadIdx.x == 0) m->fac_updates += n;
+    for (int64_t j = blockIdx.x + (int64_t)gridDim.x * wib; j < n; j += 2 * (int64_t)gridDim.x) {
+        const int64_t e = todo[j];
         const int4 c4 = coord[e];
         const uint32_t inf = info[e];
         uint32_t kbits = 0;
@@ -503,29 +779,17 @@ __global__ void __launch_bounds__(64) k_mapped_factors(
             kinds[f] = (inf >> (4 * f)) & 3;
             kbits |= (uint32_t)kinds[f] << (2 * f);
         }
-        if (ofsig && pkind[e] == 0 && (ofsig[psrc[e]] & 0xfffu) == kbits) {
-            const int64_t o = psrc[e];
-            for (int i = 0; i < NV; ++i) gvol[(size_t)e * NV + i] = ogvol[(size_t)o * NV + i];
-            for (int i = 0; i < NFV; ++i) gface[(size_t)e * NFV + i] = ogface[(size_t)o * NFV + i];
-            for (int q = 0; q < NP; ++q) mass[(size_t)e * NP + q] = omass[(size_t)o * NP + q];
-            const uint32_t sg = ofsig[o];
-            fsig[e] = sg;
-            bcfl[e] = (uint8_t)((sg >> 16) & 15u);
-            for (int s = 0; s < a.nstim; ++s) smask[s][e] = fsm[s][e] = ofsm[s][o];
-            continue;
-        }
         const int cc[3] = {c4.x, c4.y, c4.z};
-        double gv[NV], gf[NFV], ms[NP], Bs[NP * NP];
         uint32_t sk[MDL_MAX_STIM] = {0u, 0u, 0u, 0u};
-        const double cfl = geo_element<DIM, P>(a.g, Td, a.xg, a.h0, c4.w, cc, kinds, a.nstim, a.slo, a.shi, gv, gf,
-                                               ms, sk, Bs);
-        for (int i = 0; i < NV; ++i) gvol[(size_t)e * NV + i] = (R)gv[i];
-        for (int i = 0; i < NFV; ++i) gface[(size_t)e * NFV + i] = (R)gf[i];
-        for (int q = 0; q < NP; ++q) mass[(size_t)e * NP + q] = ms[q];
-        const int b = a.lts ? b_from_bound_dev(a.dt, cfl) : 0;
-        bcfl[e] = (uint8_t)b;
-        fsig[e] = kbits | ((uint32_t)c4.w << 12) | ((uint32_t)b << 16);
-        for (int s = 0; s < a.nstim; ++s) smask[s][e] = fsm[s][e] = sk[s];
+        const double cfl = geo_element_warp<R, DIM, P>(a.g, Td, a.xg, a.h0, c4.w, cc, kinds, a.nstim, a.slo, a.shi,
+                                                       s_pt[wib], s_m[wib], gvol + (size_t)e * NV,
+                                                       gface + (size_t)e * NFV, mass + (size_t)e * NP, sk);
+        if (lane == 0) {
+            const int b = a.lts ? b_from_bound_dev(a.dt, cfl) : 0;
+            bcfl[e] = (uint8_t)b;
+            fsig[e] = kbits | ((uint32_t)c4.w << 12) | ((uint32_t)b << 16);
+            for (int s = 0; s < a.nstim; ++s) smask[s][e] = fsm[s][e] = sk[s];
+        }
     }
 }
 

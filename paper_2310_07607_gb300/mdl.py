@@ -61,7 +61,7 @@ class CStats(C.Structure):
         ("sweep_ms", C.c_double), ("timed_barriers", C.c_int64), ("indicator_ms", C.c_double),
         ("amr_host_ms", C.c_double),
         ("transfer_ms", C.c_double), ("integral_V", C.c_double),
-        ("n_elements", C.c_int64), ("level_counts", C.c_int64 * 8),
+        ("n_elements", C.c_int64), ("level_counts", C.c_int64 * 8), ("factor_updates", C.c_int64),
     ]
 
 
