@@ -28,10 +28,21 @@ namespace mdl {
 struct GeoArgs {
     int dim, geometry, fibre_ref;
     double extent[3];
+    double iext[3];           // 1 / extent
     double geo[12];
     double f0[3];             // normalised fibre (fibre_ref = 0)
     double sig_l, sig_t, chi_cm, gamma;
 };
+
+// sin and cos of one angle (the device computes both from one argument reduction).
+MDL_HD void geo_sincos(double a, double* s, double* c) {
+#ifdef __CUDA_ARCH__
+    sincos(a, s, c);
+#else
+    *s = sin(a);
+    *c = cos(a);
+#endif
+}
 
 // x = Phi(X) and J = DPhi(X) (J[i][j] = d x_i / d X_j), 3D layout (2D: leading 2 x 2 block).
 MDL_HD void geo_eval(const GeoArgs& g, const double X[3], double x[3], double J[3][3]) {
@@ -54,60 +65,66 @@ MDL_HD void geo_eval(const GeoArgs& g, const double X[3], double x[3], double J[
     if (g.geometry != MDL_GEOMETRY_SHELL) return;
     const double ai = p[0], bi = p[1], ci = p[2], ao = p[3], bo = p[4], co = p[5];
     const double p0 = p[6], dp = p[7], t0 = p[8], dt = p[9];
-    const double az = p0 + X[0] / g.extent[0] * dp;
-    const double sp = sin(az), cp = cos(az);
+    // (products by the inverse extents: FP64 division is a long instruction sequence)
+    const double e0 = g.iext[0], e1 = g.iext[1], e2 = g.iext[2];
+    const double az = p0 + X[0] * e0 * dp;
+    double sp, cp;
+    geo_sincos(az, &sp, &cp);
     if (d == 2) {
-        const double u = X[1] / g.extent[1];
+        const double u = X[1] * e1;
         const double a = ai + u * (ao - ai), b = bi + u * (bo - bi);
         x[0] = a * cp;
         x[1] = b * sp;
-        J[0][0] = -a * sp * dp / g.extent[0];
-        J[1][0] = b * cp * dp / g.extent[0];
-        J[0][1] = (ao - ai) * cp / g.extent[1];
-        J[1][1] = (bo - bi) * sp / g.extent[1];
+        J[0][0] = -a * sp * dp * e0;
+        J[1][0] = b * cp * dp * e0;
+        J[0][1] = (ao - ai) * cp * e1;
+        J[1][1] = (bo - bi) * sp * e1;
         return;
     }
-    const double th = t0 + X[1] / g.extent[1] * dt;
-    const double st = sin(th), ct = cos(th);
-    const double u = X[2] / g.extent[2];
+    const double th = t0 + X[1] * e1 * dt;
+    double st, ct;
+    geo_sincos(th, &st, &ct);
+    const double u = X[2] * e2;
     const double a = ai + u * (ao - ai), b = bi + u * (bo - bi), c = ci + u * (co - ci);
     x[0] = a * st * cp;
     x[1] = b * st * sp;
     x[2] = c * ct;
-    J[0][0] = -a * st * sp * dp / g.extent[0];
-    J[1][0] = b * st * cp * dp / g.extent[0];
+    J[0][0] = -a * st * sp * dp * e0;
+    J[1][0] = b * st * cp * dp * e0;
     J[2][0] = 0.0;
-    J[0][1] = a * ct * cp * dt / g.extent[1];
-    J[1][1] = b * ct * sp * dt / g.extent[1];
-    J[2][1] = -c * st * dt / g.extent[1];
-    J[0][2] = (ao - ai) * st * cp / g.extent[2];
-    J[1][2] = (bo - bi) * st * sp / g.extent[2];
-    J[2][2] = (co - ci) * ct / g.extent[2];
+    J[0][1] = a * ct * cp * dt * e1;
+    J[1][1] = b * ct * sp * dt * e1;
+    J[2][1] = -c * st * dt * e1;
+    J[0][2] = (ao - ai) * st * cp * e2;
+    J[1][2] = (bo - bi) * st * sp * e2;
+    J[2][2] = (co - ci) * ct * e2;
 }
 
 // Inverse and determinant of the leading d x d block.
 MDL_HD double geo_inverse(int d, const double J[3][3], double Ji[3][3]) {
     if (d == 2) {
         const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-        Ji[0][0] = J[1][1] / det;
-        Ji[0][1] = -J[0][1] / det;
-        Ji[1][0] = -J[1][0] / det;
-        Ji[1][1] = J[0][0] / det;
+        const double id = 1.0 / det;
+        Ji[0][0] = J[1][1] * id;
+        Ji[0][1] = -J[0][1] * id;
+        Ji[1][0] = -J[1][0] * id;
+        Ji[1][1] = J[0][0] * id;
         return det;
     }
     const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
     const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
     const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
     const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-    Ji[0][0] = c00 / det;
-    Ji[1][0] = c01 / det;
-    Ji[2][0] = c02 / det;
-    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
-    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
-    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
-    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
-    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
-    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    const double id = 1.0 / det;
+    Ji[0][0] = c00 * id;
+    Ji[1][0] = c01 * id;
+    Ji[2][0] = c02 * id;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
     return det;
 }
 
@@ -121,8 +138,9 @@ MDL_HD void geo_tensor(const GeoArgs& g, const double J[3][3], double D[3][3]) {
         l = sqrt(l);
         for (int i = 0; i < 3; ++i) f[i] = i < d ? J[i][0] / l : 0.0;
     }
+    const double ic = 1.0 / g.chi_cm;
     for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) D[i][j] = ((i == j ? g.sig_t : 0.0) + (g.sig_l - g.sig_t) * f[i] * f[j]) / g.chi_cm;
+        for (int j = 0; j < 3; ++j) D[i][j] = ((i == j ? g.sig_t : 0.0) + (g.sig_l - g.sig_t) * f[i] * f[j]) * ic;
 }
 
 // The 1D Lagrange basis of the (p+1) GL nodes xg at t, and its derivative.
@@ -157,9 +175,9 @@ MDL_HD void geo_face_point(const GeoArgs& g, const double X[3], const double* h,
         m[i] = Ji[k][i];
         l2 += m[i] * m[i];
     }
-    const double l = sqrt(l2);
+    const double l = sqrt(l2), il = 1.0 / l;
     double n[3] = {0.0, 0.0, 0.0}, Dn[3] = {0.0, 0.0, 0.0}, q = 0.0;
-    for (int i = 0; i < d; ++i) n[i] = sgn * m[i] / l;
+    for (int i = 0; i < d; ++i) n[i] = sgn * m[i] * il;
     for (int i = 0; i < d; ++i) {
         for (int j = 0; j < d; ++j) Dn[i] += D[i][j] * n[j];
         q += n[i] * Dn[i];
@@ -167,7 +185,7 @@ MDL_HD void geo_face_point(const GeoArgs& g, const double X[3], const double* h,
     for (int i = 0; i < d; ++i) {
         double s = 0.0;
         for (int j = 0; j < d; ++j) s += Ji[i][j] * Dn[j];
-        c[i] = s * 2.0 / h[i];
+        c[i] = s * (2.0 / h[i]);
     }
     *adet = fabs(det);
     *ln = l;
@@ -185,11 +203,12 @@ MDL_HD double geo_element(const GeoArgs& g, const Tables<double>& T, const doubl
     constexpr int N1 = P + 1;
     constexpr int NP = DIM == 2 ? N1 * N1 : N1 * N1 * N1, NF = 2 * DIM, NPF = DIM == 2 ? N1 : N1 * N1;
     constexpr int NS = DIM * (DIM + 1) / 2, VPN = NS + 1, FPV = DIM + 2;
-    double h[3] = {1.0, 1.0, 1.0}, Xc[3] = {0.0, 0.0, 0.0};
+    double h[3] = {1.0, 1.0, 1.0}, Xc[3] = {0.0, 0.0, 0.0}, s2h[3] = {2.0, 2.0, 2.0};
     const double sc = 1.0 / (double)(1 << lev);
     for (int k = 0; k < DIM; ++k) {
         h[k] = h0[k] * sc;
         Xc[k] = cc[k] * h[k];
+        s2h[k] = 2.0 / h[k];
     }
     for (int i = 0; i < NP * NP; ++i) B[i] = 0.0;
     for (int s = 0; s < nstim; ++s) smask[s] = 0u;
@@ -211,7 +230,7 @@ MDL_HD double geo_element(const GeoArgs& g, const Tables<double>& T, const doubl
                 double s = 0.0;
                 for (int a = 0; a < DIM; ++a)
                     for (int b = 0; b < DIM; ++b) s += Ji[i][a] * D[a][b] * Ji[j][b];
-                K[i][j] = W * fabs(det) * (2.0 / h[i]) * s * (2.0 / h[j]);
+                K[i][j] = W * fabs(det) * s2h[i] * s * s2h[j];
             }
         double* gv = gvol + q * VPN;
         if (DIM == 2) {

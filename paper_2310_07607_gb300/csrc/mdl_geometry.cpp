@@ -15,7 +15,10 @@ GeoArgs geo_args(const mdl_problem& p) {
     g.dim = p.dim;
     g.geometry = p.geometry;
     g.fibre_ref = p.fibre_ref;
-    for (int k = 0; k < 3; ++k) g.extent[k] = p.extent[k];
+    for (int k = 0; k < 3; ++k) {
+        g.extent[k] = p.extent[k];
+        g.iext[k] = p.extent[k] != 0.0 ? 1.0 / p.extent[k] : 0.0;
+    }
     for (int i = 0; i < 12; ++i) g.geo[i] = p.geo[i];
     double f0[3] = {p.fibre[0], p.fibre[1], p.dim == 3 ? p.fibre[2] : 0.0};
     double nf0 = 0.0;

@@ -564,11 +564,12 @@ __device__ double geo_element_warp(const GeoArgs& g, const Tables<double>& T, co
     constexpr int N1 = W::N1, NP = W::NP, NF = W::NF, NPF = W::NPF, NS = W::NS, VPN = W::VPN, FPV = W::FPV;
     constexpr int CH = W::CH, PS = W::PS, NE = W::NE;
     const int lane = threadIdx.x & 31;
-    double h[3] = {1.0, 1.0, 1.0}, Xc[3] = {0.0, 0.0, 0.0};
+    double h[3] = {1.0, 1.0, 1.0}, Xc[3] = {0.0, 0.0, 0.0}, s2h[3] = {2.0, 2.0, 2.0};
     const double sc = 1.0 / (double)(1 << lev);
     for (int k = 0; k < DIM; ++k) {
         h[k] = h0[k] * sc;
         Xc[k] = cc[k] * h[k];
+        s2h[k] = 2.0 / h[k];
     }
     // points: the NP volume nodes, then per face with a neighbour its GL points (kind 3: the
     // finer neighbours' points, subface outer)
@@ -604,7 +605,7 @@ __device__ double geo_element_warp(const GeoArgs& g, const Tables<double>& T, co
                     double s = 0.0;
                     for (int a = 0; a < DIM; ++a)
                         for (int b = 0; b < DIM; ++b) s += Ji[i][a] * D[a][b] * Ji[j][b];
-                    K[i][j] = Wq * fabs(det) * (2.0 / h[i]) * s * (2.0 / h[j]);
+                    K[i][j] = Wq * fabs(det) * s2h[i] * s * s2h[j];
                     rec[i * DIM + j] = K[i][j];
                 }
             R* gv = gvol + q * VPN;
