@@ -245,7 +245,8 @@ int mdl_set_tick_shape(mdl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
  *   MDL_SWEEP_GROUP   Q1 only: (p+1)^d lanes per element, one lane per face and per DOF,
  *                     one launch per tick (Q2 contexts use MDL_SWEEP_THREAD);
  *   MDL_SWEEP_COOP    every tick and the barrier epilogue in one cooperative launch with
- *                     grid-wide barriers between ticks;
+ *                     grid-wide barriers between ticks (bounded waits: one that gives up
+ *                     makes the stepping call return MDL_E_TIMEOUT);
  *   MDL_SWEEP_TENSOR  Q2 3D FP32 contexts only (their default): per tile of 64 due
  *                     elements the SIPG residual of elements with same-level neighbours is
  *                     one tcgen05 tensor-core product of the gathered element and face-

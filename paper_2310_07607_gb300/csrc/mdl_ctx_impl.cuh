@@ -510,6 +510,7 @@ class Ctx : public CtxBase {
                 attr[0].val.cooperative = 1;
                 cfg.attrs = attr;
                 cfg.numAttrs = 1;
+                MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, gbar), 0, sizeof(unsigned int), st));
                 MDL_CK(cudaLaunchKernelEx(&cfg, k_sweep<R, DIM, P>, ta, T, ph, (const double*)mtab.p));
                 MDL_LAUNCHED();
                 stats.tick_launches += nt;
@@ -968,8 +969,8 @@ public:
                 MDL_CK(cudaStreamSynchronize(st));
                 return MDL_E_CFL;
             }
-            if (e & tc::ERR_TIMEOUT) {
-                err = "a bounded wait of the tensor-core sweep gave up";
+            if (e & ERR_WAIT) {
+                err = "a bounded wait of the sweep gave up (tensor-core mbarrier or cooperative grid barrier)";
                 return MDL_E_TIMEOUT;
             }
             if (e & ERR_MESH) {
@@ -1029,8 +1030,8 @@ public:
             MDL_CK(cudaStreamSynchronize(st));
             return MDL_E_CFL;
         }
-        if (e & tc::ERR_TIMEOUT) {
-            err = "a bounded wait of the tensor-core sweep gave up";
+        if (e & ERR_WAIT) {
+            err = "a bounded wait of the sweep gave up (tensor-core mbarrier or cooperative grid barrier)";
             return MDL_E_TIMEOUT;
         }
         if (e & ERR_MESH) {

@@ -17,7 +17,6 @@
 //   lat     [n_probe]  FP64 activation time per probe (+INF pending)
 #pragma once
 
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -49,9 +48,11 @@ struct DevMeta {
     int64_t fac_updates;     // curved meshes: elements whose factors were computed
     double integral;         // FP64 int V after the last barrier
     unsigned int nfac;       // curved meshes: elements whose factors the adaptation recomputes
+    unsigned int gbar;       // cooperative sweep: arrivals at its grid barriers (zeroed before each launch)
 };
 
-constexpr unsigned ERR_NONFINITE = 1u, ERR_CFL = 2u, ERR_CAPACITY = 4u, ERR_MESH = 8u;
+// ERR_WAIT: a bounded wait of a kernel gave up (tensor-core mbarrier, cooperative grid barrier)
+constexpr unsigned ERR_NONFINITE = 1u, ERR_CFL = 2u, ERR_CAPACITY = 4u, ERR_MESH = 8u, ERR_WAIT = 16u;
 
 // Programmatic dependent launch: wait until the preceding grid on the stream has completed
 // and its writes are visible, then let the following grid be scheduled.  Each kernel of a
@@ -1212,6 +1213,29 @@ __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const P
     }
 }
 
+// Grid-wide barrier number `round` (1, 2, ...) of a cooperative launch (every block resident):
+// each block's thread 0 counts its arrival in m->gbar (zeroed before the launch) and waits,
+// with a bounded number of polls, until every block of the round has arrived.  A wait that
+// gives up sets ERR_WAIT (the host reports it) and lets the block go on: no hang.
+__device__ __forceinline__ void grid_barrier(DevMeta* m, unsigned round) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned target = round * gridDim.x;
+        __threadfence();
+        atomicAdd(&m->gbar, 1u);
+        uint32_t it = 0;
+        while (*(volatile unsigned*)&m->gbar < target) {
+            if (++it > (1u << 24)) {   // ~1 s of polls
+                atomicOr(&m->err, ERR_WAIT);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
 // The whole sweep of a barrier in one cooperative launch: every tick of Alg. 1 with a
 // grid-wide barrier between ticks (the Jacobi reading needs all of tick i before tick
 // i+1), then the epilogue with a fixed-order final reduction by block 0.  The grid is
@@ -1223,11 +1247,10 @@ __global__ void __launch_bounds__(256) k_sweep(const TickArgs<R> a, const Tables
     constexpr int NP = S::NP;
     const DevArrays<R>& d = a.d;
     if (d.meta->err) return;             // uniform: nothing below changes err before the end
-    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
     const int nt = 1 << a.B;
     for (int i = 0; i < nt; ++i) {
         tick_work<R, DIM, P>(a, T, ph, i);
-        grid.sync();
+        grid_barrier(d.meta, (unsigned)(i + 1));
     }
     __shared__ double red[256];
     const int64_t ne = d.meta->ne;
@@ -1260,7 +1283,7 @@ __global__ void __launch_bounds__(256) k_sweep(const TickArgs<R> a, const Tables
         __syncthreads();
     }
     if (threadIdx.x == 0) d.partial[blockIdx.x] = red[0];
-    grid.sync();
+    grid_barrier(d.meta, (unsigned)(nt + 1));
     if (blockIdx.x != 0) return;
     double s3 = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s3 += d.partial[i];

@@ -88,7 +88,7 @@ constexpr int SMEM_BYTES = OFF_TMEM + 16 + 1024;      // + alignment slack of th
 static_assert(OFF_UHI % 1024 == 0 && OFF_ULO % 1024 == 0 && OFF_BLO % 1024 == 0, "operand alignment");
 static_assert(2 * (SMEM_BYTES + 1024) <= 228 * 1024, "two CTAs per SM");
 
-constexpr unsigned ERR_TIMEOUT = 16u;                 // a bounded wait of the sweep gave up
+constexpr unsigned ERR_TIMEOUT = ERR_WAIT;            // a bounded wait of the sweep gave up
 constexpr uint32_t WAIT_LIMIT = 1u << 26;             // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
