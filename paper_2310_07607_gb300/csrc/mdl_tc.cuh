@@ -242,12 +242,13 @@ __device__ __forceinline__ float block_row_dot(const float* __restrict__ row, co
 //      power-of-two scale and the FP16 hi/lo terms in the swizzled operand layout
 //   2  one thread of warp 0 issues the MMAs and commits to an mbarrier
 //   3  while they run: corrections of non-regular faces (warps 1-7, warp per element, lane =
-//      row) and the loads of the pointwise step, item by item (element, DOF)
+//      row) and the loads of the pointwise step: thread 4 i + p takes DOFs p + 4 m of element i
 //   4  warps 0-3: D row -> scaled residual in shared memory
-//   5  the pointwise step of every item with coalesced stores: straight-line
-//      (dof_update_ap) for a tile without stimulus or padding rows, else dof_update
-//   6  per element (four threads each): the RV-T accumulation; a due probe check is recorded
-//      and run by threads 64..127 during the next tile's metadata step (or after the last)
+//   5  the pointwise step of the thread's DOFs (element metadata read once per thread):
+//      straight-line (dof_update_ap) for a tile without stimulus or padding rows, else
+//      dof_update; the element's RV-T sum and max |V_new| over its four threads by shuffles,
+//      the accumulation; a due probe check is recorded and run by threads 64..127 during the
+//      next tile's metadata step (or after the last)
 // unscale = 2^-t undoes the scaling of B by 2^t; each row's scale of y is undone by 2^-sc.
 template <int DIM, int P>
 __global__ void __launch_bounds__(tc::THREADS, 2)
@@ -553,20 +554,23 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             }
         }
 
-        // item = (element i, DOF q), i = it / 27: the loads of every item of the thread
-        constexpr int NIT = (M * NP + THREADS - 1) / THREADS;
+        // element i = tid / 4, DOFs q = p + 4 m (p = tid % 4): the loads of the thread's DOFs
+        constexpr int NIT = (NP + 3) / 4;
         float u[NIT], w[NIT], Ia[NIT], ga[NIT];
-#pragma unroll
-        for (int m = 0; m < NIT; ++m) {
-            const int it = tid + m * THREADS;
-            const int i = min(it / NP, M - 1), q = it - (it / NP) * NP;
+        {
+            const int i = tid >> 2, p = tid & 3;
             const int e = sE[i], es = e >= 0 ? e : 0;
             const int ke = tick >> (B - (sLv[i] & 7));
-            const bool need = it < M * NP && e >= 0 && ke != 0;
-            u[m] = __ldg(sPtr[i] + q);
-            w[m] = d.v[(size_t)es * NPS + q];
-            Ia[m] = need ? d.Ia[(size_t)es * NPS + q] : 0.0f;
-            ga[m] = need ? d.ga[(size_t)es * NPS + q] : 0.0f;
+            const bool need = e >= 0 && ke != 0;
+            const float* up = sPtr[i];
+#pragma unroll
+            for (int m = 0; m < NIT; ++m) {
+                const int q = min(p + 4 * m, NP - 1);
+                u[m] = __ldg(up + q);
+                w[m] = d.v[(size_t)es * NPS + q];
+                Ia[m] = need ? d.Ia[(size_t)es * NPS + q] : 0.0f;
+                ga[m] = need ? d.ga[(size_t)es * NPS + q] : 0.0f;
+            }
         }
         // thread 4 i: the RV-T accumulator of element i, needed at the end of the tile (ke != 0)
         double acc0 = 0.0;
@@ -605,98 +609,72 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             fetch_lvn(e_next, nxr, nlo, nhi);
         }
 
-        // ---- 5: item updates (dof_update) with coalesced stores; the RV-T terms and both
-        //      values go to shared memory (the operand bytes, free once the MMA completed)
-        //      A tile without stimulus and without padding rows, under the Aliev-Panfilov model
-        //      with the exponential state step, takes the straight-line form (dof_update_ap),
-        //      so that the items of a thread interleave; any other tile the general one.  Every
-        //      element is at its first step of the barrier exactly at tick 0.
-        auto fast_items = [&](auto first) {
-            constexpr bool FIRST = decltype(first)::value;
-            float* sT = reinterpret_cast<float*>(sm + OFF_UHI);
-            float* sUo = sT + M * NP;
-            float* sUn = sUo + M * NP;
-#pragma unroll
-            for (int m = 0; m < NIT; ++m) {
-                const int it0 = tid + m * THREADS;
-                const bool in = it0 < M * NP;
-                const int it = in ? it0 : M * NP - 1;
-                const int i = it / NP, q = it - i * NP;
-                const int lev = (sInf[i] >> 24) & 15;
-                const float cr = sCorr[i * RST + q];
-                const float r = sR[i * RST + q] + (sIrr[i] ? cr : 0.0f);
-                float un, wn;
-                const float term = dof_update_ap<FIRST>(ph, sMq[lev * NP + q], sMinv[lev * NP + q],
-                                                        sDte[sLv[i] & 7], u[m], w[m], r, Ia[m], ga[m], un, wn);
-                if (in) {
-                    const_cast<float*>(sPtrO[i])[q] = un;
-                    d.v[(size_t)sE[i] * NPS + q] = wn;
-                    if (FIRST && (sLv[i] & 7) > 0) {
-                        d.Ia[(size_t)sE[i] * NPS + q] = Ia[m];
-                        d.ga[(size_t)sE[i] * NPS + q] = ga[m];
-                    }
-                    sT[it] = term;
-                    sUo[it] = u[m];
-                    sUn[it] = un;
-                }
-            }
-        };
-        if (fast) {
-            if (tick == 0) fast_items(std::true_type{});
-            else fast_items(std::false_type{});
-        } else {
-            float* sT = reinterpret_cast<float*>(sm + OFF_UHI);
-            float* sUo = sT + M * NP;
-            float* sUn = sUo + M * NP;
-#pragma unroll
-            for (int m = 0; m < NIT; ++m) {
-                const int it = tid + m * THREADS;
-                if (it >= M * NP) continue;
-                const int i = it / NP, q = it - i * NP;
-                const int e = sE[i];
-                float term = 0.0f, un = 0.0f;
-                if (e >= 0) {
-                    const uint32_t inf = sInf[i];
-                    const int b = sLv[i] & 7, ke = tick >> (B - b), lev = (inf >> 24) & 15;
-                    float so = 0.0f, smd = 0.0f;
-                    if (inf & INFO_STIM) dof_stim<float>(a, e, tick, a.dte[b], q, so, smd);
-                    const float r = sR[i * RST + q] + (sIrr[i] ? sCorr[i * RST + q] : 0.0f);
-                    float wn;
-                    term = dof_update<float>(ph, sMq[lev * NP + q], sMinv[lev * NP + q], ke, a.dteR[b], so, smd, u[m],
-                                             w[m], r, Ia[m], ga[m], un, wn);
-                    const size_t o = (size_t)e * NPS + q;
-                    const_cast<float*>(sPtrO[i])[q] = un;
-                    d.v[o] = wn;
-                    if (ke == 0 && b > 0) {
-                        d.Ia[o] = Ia[m];
-                        d.ga[o] = ga[m];
-                    }
-                }
-                sT[it] = term;
-                sUo[it] = u[m];
-                sUn[it] = un;
-            }
-        }
-        __syncthreads();
-        if (tid < M) {
-            sNx[7 * M + tid] = nxr[7] | (int)(nlo << 8);
-            sNx2[tid] = nhi;
-        }
+        // ---- 5: the pointwise step of element i = tid / 4, DOFs q = p + 4 m; the RV-T sum and
+        //      max |V_new| of its four threads by shuffles, the accumulation and the record of a
+        //      due probe check (the values before and after the step of elements with a pending
+        //      probe go to shared memory for it)
         {
-            // ---- 6: per element i (threads 4 i .. 4 i + 3, DOFs q = p mod 4): RV-T sum and
-            //      max |V_new|, the accumulation, and the record of a due probe check (run with
-            //      the next tile's metadata)
-            const int i = tid >> 2, p = tid & 3, e = sE[i];
-            const float* sT = reinterpret_cast<const float*>(sm + OFF_UHI);
-            const float* sUo = sT + M * NP;
-            const float* sUn = sUo + M * NP;
+            const int i = tid >> 2, p = tid & 3;
+            const int e = sE[i];
+            const uint32_t inf = sInf[i];
+            const int b = sLv[i] & 7, lev = (inf >> 24) & 15, ke = tick >> (B - b);
+            const bool irr = sIrr[i] != 0, pend = (inf & INFO_PENDING) != 0;
+            float* vrow = const_cast<float*>(sPtrO[i]);
+            float* sUo = reinterpret_cast<float*>(sm + OFF_UHI) + M * NP;
+            float* sUn = sUo + M * NP;
             float term = 0.0f, vmax = 0.0f;
+            auto fast_dofs = [&](auto first) {
+                constexpr bool FIRST = decltype(first)::value;
+                const float dte = sDte[b];
 #pragma unroll
-            for (int j = 0; j < (NP + 3) / 4; ++j) {
-                const int q = p + 4 * j;
-                if (q < NP) {
-                    term += sT[i * NP + q];
-                    vmax = fmaxf(vmax, fabsf(sUn[i * NP + q]));
+                for (int m = 0; m < NIT; ++m) {
+                    const int q = p + 4 * m;
+                    if (q < NP) {
+                        const float r = sR[i * RST + q] + (irr ? sCorr[i * RST + q] : 0.0f);
+                        float un, wn;
+                        term += dof_update_ap<FIRST>(ph, sMq[lev * NP + q], sMinv[lev * NP + q], dte, u[m], w[m], r,
+                                                     Ia[m], ga[m], un, wn);
+                        vmax = fmaxf(vmax, fabsf(un));
+                        vrow[q] = un;
+                        d.v[(size_t)e * NPS + q] = wn;
+                        if (FIRST && b > 0) {
+                            d.Ia[(size_t)e * NPS + q] = Ia[m];
+                            d.ga[(size_t)e * NPS + q] = ga[m];
+                        }
+                        if (pend) {
+                            sUo[i * NP + q] = u[m];
+                            sUn[i * NP + q] = un;
+                        }
+                    }
+                }
+            };
+            if (fast) {
+                if (tick == 0) fast_dofs(std::true_type{});
+                else fast_dofs(std::false_type{});
+            } else if (e >= 0) {
+#pragma unroll
+                for (int m = 0; m < NIT; ++m) {
+                    const int q = p + 4 * m;
+                    if (q < NP) {
+                        float so = 0.0f, smd = 0.0f;
+                        if (inf & INFO_STIM) dof_stim<float>(a, e, tick, a.dte[b], q, so, smd);
+                        const float r = sR[i * RST + q] + (irr ? sCorr[i * RST + q] : 0.0f);
+                        float un, wn;
+                        term += dof_update<float>(ph, sMq[lev * NP + q], sMinv[lev * NP + q], ke, a.dteR[b], so, smd,
+                                                  u[m], w[m], r, Ia[m], ga[m], un, wn);
+                        vmax = fmaxf(vmax, fabsf(un));
+                        const size_t o = (size_t)e * NPS + q;
+                        vrow[q] = un;
+                        d.v[o] = wn;
+                        if (ke == 0 && b > 0) {
+                            d.Ia[o] = Ia[m];
+                            d.ga[o] = ga[m];
+                        }
+                        if (pend) {
+                            sUo[i * NP + q] = u[m];
+                            sUn[i * NP + q] = un;
+                        }
+                    }
                 }
             }
             term += __shfl_xor_sync(0xffffffffu, term, 1);
@@ -704,13 +682,15 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             term += __shfl_xor_sync(0xffffffffu, term, 2);
             vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 2));
             if (p == 0) {
-                const uint32_t inf = sInf[i];
-                const int b = sLv[i] & 7;
                 if (e >= 0) d.acc[e] = acc0 + a.dte[b] * (double)term;
-                sChkE[i] = (e >= 0 && (inf & INFO_PENDING) && vmax >= ph.lat_gate) ? e : -1;
+                sChkE[i] = (e >= 0 && pend && vmax >= ph.lat_gate) ? e : -1;
                 sChkInf[i] = inf;
                 sChkB[i] = b;
             }
+        }
+        if (tid < M) {
+            sNx[7 * M + tid] = nxr[7] | (int)(nlo << 8);
+            sNx2[tid] = nhi;
         }
         __syncthreads();
     }
