@@ -66,22 +66,19 @@ constexpr int OFF_R = OFF_ULO + U_BYTES;              // float [M][RST] scaled r
 constexpr int OFF_SCR = OFF_R + M * RST * 4;          // float [8 warps][2][32] per-warp scratch
 constexpr int OFF_PTR = OFF_SCR + 8 * 2 * 32 * 4;     // const float* [8][M]: row of slot s (seen value)
 constexpr int OFF_PTRO = OFF_PTR + M * 8 * 8;         // const float* [8][M]: other V slot (interpolation)
-constexpr int OFF_E = OFF_PTRO + M * 8 * 8;           // int32 element id (-1: padding row)
-constexpr int OFF_INF = OFF_E + M * 4;                // uint32 face info
-constexpr int OFF_NB = OFF_INF + M * 4;               // int32 [6][M] face neighbours
+constexpr int OFF_E = OFF_PTRO + M * 8 * 8;           // int32 [2][M] element id (-1: padding row)
+constexpr int OFF_INF = OFF_E + 2 * M * 4;            // uint32 [2][M] face info
+constexpr int OFF_NB = OFF_INF + 2 * M * 4;           // int32 [6][M] face neighbours
 constexpr int OFF_TH = OFF_NB + M * 6 * 4;            // float [8][M] time-interpolation weight
 constexpr int OFF_RS = OFF_TH + M * 8 * 4;            // float 2^-sc: undoes the row's operand scale
 constexpr int OFF_C = OFF_RS + M * 4;                 // float operand mean c of the row
-constexpr int OFF_LV = OFF_C + M * 4;                 // uint8 level byte
-constexpr int OFF_LIVE = OFF_LV + M;                  // uint8 bit s: slot s holds values
+constexpr int OFF_LV = OFF_C + M * 4;                 // uint8 [2][M] level byte
+constexpr int OFF_LIVE = OFF_LV + 2 * M;              // uint8 bit s: slot s holds values
 constexpr int OFF_INTP = OFF_LIVE + M;                // uint8 bit s: slot s is interpolated in time
-constexpr int OFF_IRR = OFF_INTP + M;                 // uint8 element has a non-regular face
-constexpr int OFF_CORR = ((OFF_IRR + M + 15) / 16) * 16;  // float [M][RST] residual corrections
-constexpr int OFF_NX = OFF_CORR + M * RST * 4;        // next tile: int32 [8][M] = info, nbr[6], lvl | lvn[f] << 8 (f < 3)
-constexpr int OFF_NX2 = OFF_NX + M * 8 * 4;           // next tile: uint32 [M] lvn[f] for f >= 3
-constexpr int OFF_MTAB = OFF_NX2 + M * 4;             // float [8][27] GL mass, [8][27] inverse, [8] dt_e
-constexpr int OFF_CHK = OFF_MTAB + (2 * 8 * NP + 8) * 4;   // int32 [3][M]: probe checks deferred to the next tile
-constexpr int OFF_MBAR = ((OFF_CHK + 3 * M * 4 + 7) / 8) * 8;
+constexpr int OFF_IRR = OFF_INTP + M;                 // uint8 [2][M] element has a non-regular face
+constexpr int OFF_CORR = ((OFF_IRR + 2 * M + 15) / 16) * 16;  // float [M][RST] residual corrections
+constexpr int OFF_MTAB = OFF_CORR + M * RST * 4;      // float [8][27] GL mass, [8][27] inverse, [8] dt_e
+constexpr int OFF_MBAR = ((OFF_MTAB + (2 * 8 * NP + 8) * 4 + 7) / 8) * 8;
 constexpr int OFF_FLAG = OFF_MBAR + 8;
 constexpr int OFF_TMEM = OFF_FLAG + 8;
 constexpr int SMEM_BYTES = OFF_TMEM + 16 + 1024;      // + alignment slack of the dynamic base
@@ -262,25 +259,20 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
     float* sScr = reinterpret_cast<float*>(sm + OFF_SCR);
     const float** sPtr = reinterpret_cast<const float**>(sm + OFF_PTR);
     const float** sPtrO = reinterpret_cast<const float**>(sm + OFF_PTRO);
-    int* sE = reinterpret_cast<int*>(sm + OFF_E);
-    uint32_t* sInf = reinterpret_cast<uint32_t*>(sm + OFF_INF);
+    int* const bE = reinterpret_cast<int*>(sm + OFF_E);          // [2][M]: this tile's and the next's
+    uint32_t* const bInf = reinterpret_cast<uint32_t*>(sm + OFF_INF);
     int* sNb = reinterpret_cast<int*>(sm + OFF_NB);
     float* sTh = reinterpret_cast<float*>(sm + OFF_TH);
     float* sRs = reinterpret_cast<float*>(sm + OFF_RS);
     float* sC = reinterpret_cast<float*>(sm + OFF_C);
-    uint8_t* sLv = sm + OFF_LV;
+    uint8_t* const bLv = sm + OFF_LV;
     uint8_t* sLive = sm + OFF_LIVE;
     uint8_t* sIntp = sm + OFF_INTP;
-    uint8_t* sIrr = sm + OFF_IRR;
+    uint8_t* const bIrr = sm + OFF_IRR;
     float* sCorr = reinterpret_cast<float*>(sm + OFF_CORR);
-    int* sNx = reinterpret_cast<int*>(sm + OFF_NX);
-    uint32_t* sNx2 = reinterpret_cast<uint32_t*>(sm + OFF_NX2);
     float* sMq = reinterpret_cast<float*>(sm + OFF_MTAB);
     float* sMinv = sMq + 8 * NP;
     float* sDte = sMinv + 8 * NP;
-    int* sChkE = reinterpret_cast<int*>(sm + OFF_CHK);      // element whose probe check is due, or -1
-    uint32_t* sChkInf = reinterpret_cast<uint32_t*>(sChkE + M);
-    int* sChkB = sChkE + 2 * M;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + OFF_MBAR);
     unsigned* sFlag = reinterpret_cast<unsigned*>(sm + OFF_FLAG);
     uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + OFF_TMEM);
@@ -302,7 +294,6 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
         sMinv[i] = ph.Minv[l][q];
     }
     if (tid < 8) sDte[tid] = a.dteR[tid];
-    if (tid < M) sChkE[tid] = -1;
     if (warp == 0) tmem_alloc(sTmem, TMEM_COLS);
     if (tid == 0) {
         mbar_init(mbar, 1);
@@ -317,14 +308,17 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
     // due count and element order are fixed during the sweep
     const int n_act = d.meta->nact[tick];
     const int ntiles = (n_act + M - 1) / M;
-    int e_next = -1;
-    if (tid < M && (int)blockIdx.x * M + tid < n_act) e_next = d.order[blockIdx.x * M + tid];
+    const int G = (int)gridDim.x;
+    int e_cur = -1, e_next = -1;   // threads 0..63: element of this CTA's first tile, of the next one
+    if (tid < M && (int)blockIdx.x * M + tid < n_act) e_cur = d.order[blockIdx.x * M + tid];
+    if (tid < M && ((int)blockIdx.x + G) * M + tid < n_act) e_next = d.order[(blockIdx.x + G) * M + tid];
     pdl_enter();
     uint32_t parity = 0;
     bool ok = d.meta->err == 0;
-    // Metadata of a tile's element (threads 0..63) is fetched one tile ahead: the ids when a
-    // tile starts, their level bytes, face info and neighbours while its gather runs, the
-    // neighbours' level bytes while its pointwise step runs (kept in sNx / sNx2).
+    // Metadata of a tile's element (threads 0..63) is fetched one tile ahead: its face info,
+    // neighbours and level byte while the previous tile's gather and MMAs run, the neighbours'
+    // level bytes while its pointwise step runs, and the tile's records are built at the end of
+    // that step (the records read by phases 2 and 5 are double-buffered).
     auto fetch_raw = [&](int e, int* nx) {
         const int es = e >= 0 ? e : 0;
         nx[0] = e >= 0 ? (int)d.info[es] : 0;
@@ -347,87 +341,69 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             else hi |= v << (8 * (f - 3));
         }
     };
+    // The records of element e (row tid of a tile) from its raw metadata: per operand slot the row
+    // holding the value the element sees (Alg. 1: a coarser LTS neighbour mid-interval is seen
+    // through the linear interpolant of its last step), the interpolation weights, live and
+    // interpolated slots; into buffer nb of the double-buffered records.  Returns whether the
+    // element needs the general pointwise step (padding row or stimulus).
+    auto build_meta = [&](int e, const int* nx, uint32_t lo, uint32_t hi, int nb) -> bool {
+        const int es = e >= 0 ? e : 0;                    // any valid row for padding slots
+        uint8_t live = 0, intp = 0;
+        const uint32_t inf = (uint32_t)nx[0];
+        const uint8_t lv = (uint8_t)(nx[7] & 255);
+        const int b = lv & 7, par = (lv >> 3) & 1;
+        const int cur = par ^ ((tick >> (B - b)) & 1);
+        sPtr[tid] = (cur ? d.V1 : d.V0) + (size_t)es * NPS;
+        sPtrO[tid] = (cur ? d.V0 : d.V1) + (size_t)es * NPS;   // slot 0: the row the step writes
+        sTh[tid] = 0.0f;
+        if (e >= 0) live = 1;
+        bool irr = false;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const uint32_t lvn = (f < 3 ? (lo >> (8 * f)) : (hi >> (8 * (f - 3)))) & 255u;
+            const bool same = e >= 0 && ((inf >> (4 * f)) & 3) == 1;
+            const int sh = B - (int)(lvn & 7), pn = (lvn >> 3) & 1;
+            const int j = tick >> sh, rem = same ? (tick & ((1 << sh) - 1)) : 0;
+            const int nw = pn ^ ((j + (rem ? 1 : 0)) & 1);
+            const size_t o = (size_t)(same ? nx[1 + f] : es) * NPS;
+            sPtr[(1 + f) * M + tid] = (nw ? d.V1 : d.V0) + o;
+            sPtrO[(1 + f) * M + tid] = (nw ? d.V0 : d.V1) + o;
+            sTh[(1 + f) * M + tid] = rem ? (float)rem * pow2_neg<float>(sh) : 0.0f;
+            if (same) live |= (uint8_t)(2u << f);
+            if (rem) intp |= (uint8_t)(2u << f);
+            irr = irr || (((inf >> (4 * f)) & 3) != 1);
+            sNb[f * M + tid] = nx[1 + f];
+        }
+        bE[nb * M + tid] = e;
+        bInf[nb * M + tid] = inf;
+        bLv[nb * M + tid] = lv;
+        bIrr[nb * M + tid] = (e >= 0 && irr) ? 1 : 0;
+        sLive[tid] = live;
+        sIntp[tid] = intp;
+        return e < 0 || (inf & INFO_STIM);
+    };
+    bool slow0 = false;
     if (tid < M && (int)blockIdx.x < ntiles) {
         int nx[8];
-        fetch_raw(e_next, nx);
         uint32_t lo, hi;
-        fetch_lvn(e_next, nx, lo, hi);
-        nx[7] |= (int)(lo << 8);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sNx[k * M + tid] = nx[k];
-        sNx2[tid] = hi;
+        fetch_raw(e_cur, nx);
+        fetch_lvn(e_cur, nx, lo, hi);
+        slow0 = build_meta(e_cur, nx, lo, hi, 0);
     }
+    // a tile without padding rows or stimulus, under the Aliev-Panfilov model with the
+    // exponential state step, takes the straight-line pointwise step (phase 5)
+    const bool ap_exp = ph.ionic == 0 && ph.integrator == 1;
+    bool fast = !__syncthreads_or(slow0) && ap_exp;
     const double t_tick = tick_time(a, tick);
-    auto run_checks = [&]() {
-        if (tid >= M && tid < 2 * M) {
-            const int i = tid - M, e = sChkE[i];
-            if (e >= 0) {
-                const float* sUo = reinterpret_cast<const float*>(sm + OFF_UHI) + M * NP;
-                const uint32_t inf = sChkInf[i];
-                lat_check<float, DIM, P>(d, T, ph, e, inf, (inf >> 24) & 15, sUo + i * NP, sUo + M * NP + i * NP,
-                                         t_tick, a.dte[sChkB[i]]);
-                sChkE[i] = -1;
-            }
-        }
-    };
     int nxr[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // threads 0..63: next tile's raw metadata in flight
     uint32_t nlo = 0u, nhi = 0u;
+    int buf = 0;                             // buffer of this tile's records
 
     for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
-        // the previous tile's probe checks (threads 64..127, element tid - 64) run while threads
-        // 0..63 fetch this tile's metadata: they read only the check records and the values
-        // before and after the step, which phase 1 overwrites after the barrier below
-        run_checks();
-        // ---- 0: metadata (threads 0..63, one element each)
-        bool slow = false;   // the element needs the general pointwise step (see phase 5)
-        if (tid < M) {
-            const int e = e_next;
-            const int idx_n = (t + (int)gridDim.x) * M + tid;
-            e_next = idx_n < n_act ? d.order[idx_n] : -1;
-            const int es = e >= 0 ? e : 0;                    // any valid row for padding slots
-            uint8_t live = 0, intp = 0;
-            const uint32_t inf = (uint32_t)sNx[tid];
-            int nbf[6];
-#pragma unroll
-            for (int f = 0; f < 6; ++f) nbf[f] = sNx[(1 + f) * M + tid];
-            const uint32_t w7 = (uint32_t)sNx[7 * M + tid], w8 = sNx2[tid];
-            const uint8_t lv = (uint8_t)(w7 & 255u);
-            uint8_t lvn[6];
-#pragma unroll
-            for (int f = 0; f < 6; ++f) lvn[f] = (uint8_t)((f < 3 ? (w7 >> (8 * (f + 1))) : (w8 >> (8 * (f - 3)))) & 255u);
-            const int b = lv & 7, par = (lv >> 3) & 1;
-            const int cur = par ^ ((tick >> (B - b)) & 1);
-            sPtr[tid] = (cur ? d.V1 : d.V0) + (size_t)es * NPS;
-            sPtrO[tid] = (cur ? d.V0 : d.V1) + (size_t)es * NPS;   // slot 0: the row the step writes
-            sTh[tid] = 0.0f;
-            if (e >= 0) live = 1;
-#pragma unroll
-            for (int f = 0; f < 6; ++f) {
-                const bool same = e >= 0 && ((inf >> (4 * f)) & 3) == 1;
-                const int sh = B - (lvn[f] & 7), pn = (lvn[f] >> 3) & 1;
-                const int j = tick >> sh, rem = same ? (tick & ((1 << sh) - 1)) : 0;
-                const int nw = pn ^ ((j + (rem ? 1 : 0)) & 1);
-                const size_t o = (size_t)(same ? nbf[f] : es) * NPS;
-                sPtr[(1 + f) * M + tid] = (nw ? d.V1 : d.V0) + o;
-                sPtrO[(1 + f) * M + tid] = (nw ? d.V0 : d.V1) + o;
-                sTh[(1 + f) * M + tid] = rem ? (float)rem * pow2_neg<float>(sh) : 0.0f;
-                if (same) live |= (uint8_t)(2u << f);
-                if (rem) intp |= (uint8_t)(2u << f);
-            }
-            bool irr = false;
-#pragma unroll
-            for (int f = 0; f < 6; ++f) irr = irr || (((inf >> (4 * f)) & 3) != 1);
-            sE[tid] = e;
-            sInf[tid] = inf;
-            sLv[tid] = lv;
-            sLive[tid] = live;
-            sIntp[tid] = intp;
-            sIrr[tid] = (e >= 0 && irr) ? 1 : 0;
-#pragma unroll
-            for (int f = 0; f < 6; ++f) sNb[f * M + tid] = nbf[f];
-            slow = e < 0 || (inf & INFO_STIM);
-        }
-        const bool fast = !__syncthreads_or(slow) && ph.ionic == 0 && ph.integrator == 1;
+        int* const sE = bE + buf * M;
+        uint32_t* const sInf = bInf + buf * M;
+        uint8_t* const sLv = bLv + buf * M;
+        uint8_t* const sIrr = bIrr + buf * M;
 
         // ---- 1: gather, mean shift, FP16 split (warp w: rows 8 w .. 8 w + 7; lane = 4 ii + kk:
         //      row ii, column pairs k = 2 kk + 8 jj + {0, 1})
@@ -603,11 +579,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             break;
         }
 
-        if (tid < M) {
-#pragma unroll
-            for (int k = 0; k < 7; ++k) sNx[k * M + tid] = nxr[k];
-            fetch_lvn(e_next, nxr, nlo, nhi);
-        }
+        if (tid < M) fetch_lvn(e_next, nxr, nlo, nhi);
 
         // ---- 5: the pointwise step of element i = tid / 4, DOFs q = p + 4 m; the RV-T sum and
         //      max |V_new| of its four threads by shuffles, the accumulation and the record of a
@@ -619,7 +591,8 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             const uint32_t inf = sInf[i];
             const int b = sLv[i] & 7, lev = (inf >> 24) & 15, ke = tick >> (B - b);
             const bool irr = sIrr[i] != 0, pend = (inf & INFO_PENDING) != 0;
-            float* vrow = const_cast<float*>(sPtrO[i]);
+            const int par = (sLv[i] >> 3) & 1, cur = par ^ (ke & 1);
+            float* vrow = (cur ? d.V0 : d.V1) + (size_t)(e >= 0 ? e : 0) * NPS;   // the row the step writes
             float* sUo = reinterpret_cast<float*>(sm + OFF_UHI) + M * NP;
             float* sUn = sUo + M * NP;
             float term = 0.0f, vmax = 0.0f;
@@ -681,20 +654,23 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 1));
             term += __shfl_xor_sync(0xffffffffu, term, 2);
             vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 2));
+            __syncwarp();   // the element's values before and after the step, for its probe check
             if (p == 0) {
                 if (e >= 0) d.acc[e] = acc0 + a.dte[b] * (double)term;
-                sChkE[i] = (e >= 0 && pend && vmax >= ph.lat_gate) ? e : -1;
-                sChkInf[i] = inf;
-                sChkB[i] = b;
+                if (e >= 0 && pend && vmax >= ph.lat_gate)
+                    lat_check<float, DIM, P>(d, T, ph, e, inf, lev, sUo + i * NP, sUn + i * NP, t_tick, a.dte[b]);
             }
         }
+        // the next tile's records (threads 0..63), then the next tile's element ids
+        bool slow = false;
         if (tid < M) {
-            sNx[7 * M + tid] = nxr[7] | (int)(nlo << 8);
-            sNx2[tid] = nhi;
+            slow = build_meta(e_next, nxr, nlo, nhi, buf ^ 1);
+            const int idx_n = (t + 2 * G) * M + tid;
+            e_next = idx_n < n_act ? d.order[idx_n] : -1;
         }
-        __syncthreads();
+        fast = !__syncthreads_or(slow) && ap_exp;
+        buf ^= 1;
     }
-    if (ok) run_checks();   // the last tile's
     if (*sFlag) {
         // a wait gave up: give the MMAs in flight one more bounded wait before freeing TMEM
         if (tid == 0) mbar_wait(mbar, parity ^ 1u);
