@@ -63,7 +63,8 @@ SETUP_BARRIERS = 5
 # ticks 1-7, the same level-1 and level-3 elements at tick 4), tick 0 scaled to the full slab's
 # 2,736,960 elements by the elements due.
 TRAFFIC_PER_LAUNCH = {
-    ("slab2d", "k_tick<float,2,1>"): (10.354432e6 + 7 * (5.937920e6 + 5.938176e6) / 2.0) / 8.0,
+    # 2D slab: the eight ticks of one barrier step
+    ("slab2d", "k_tick<float,2,1>"): 6.6640e6,
     # curved LV-like slab at full size: the eight ticks of one barrier step
     ("lv3d", "k_tick_mapped<float,3,1>"): 4.4873e7,
     # 3D slab: the quarter slab's eight ticks, tick 0 and tick 4 scaled to the full slab
