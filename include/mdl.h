@@ -364,6 +364,17 @@ int mdl_integral_noalloc(int32_t dim, int32_t order, const double* extent, const
                          double* out_dev, void* stream);
 const char* mdl_noalloc_last_error(void);
 
+/* Self-test of the bounded device waits (failure detection without a GPU fault).  The
+ * tensor-core sweep waits on an mbarrier for its MMAs and the cooperative sweep on a grid
+ * barrier between ticks; a wait that runs out of polls records an error and returns, and the
+ * stepping call reports MDL_E_TIMEOUT.  This runs one block of the same wait on a phase or a
+ * count that nothing completes, on the current device: which = 0 the grid barrier (its
+ * production limit, ~1 s), which = 1 the mbarrier wait (2^16 polls).  *status receives the code
+ * a stepping call would return (MDL_E_TIMEOUT when the wait gave up as designed), *elapsed_ms
+ * (may be null) the host time of the call.  Returns MDL_OK, MDL_E_ARG (which not 0 or 1, null
+ * status) or MDL_E_CUDA; the device stays usable. */
+int mdl_selftest_wait(int32_t which, int32_t* status, double* elapsed_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,7 @@ SOURCES = [
     "mdl_noalloc.cu",
     "mdl_batch.cpp",
     "mdl_fused.cu",
+    "mdl_selftest.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1215,9 +1215,11 @@ __global__ void __launch_bounds__(256) k_tick_group(const TickArgs<R> a, const P
 
 // Grid-wide barrier number `round` (1, 2, ...) of a cooperative launch (every block resident):
 // each block's thread 0 counts its arrival in m->gbar (zeroed before the launch) and waits,
-// with a bounded number of polls, until every block of the round has arrived.  A wait that
-// gives up sets ERR_WAIT (the host reports it) and lets the block go on: no hang.
-__device__ __forceinline__ void grid_barrier(DevMeta* m, unsigned round) {
+// with at most `limit` polls 64 ns apart (~1 s by default), until every block of the round has
+// arrived.  A wait that gives up sets ERR_WAIT (the host reports it) and lets the block go on:
+// no hang.
+constexpr uint32_t GRID_WAIT_LIMIT = 1u << 24;
+__device__ __forceinline__ void grid_barrier(DevMeta* m, unsigned round, uint32_t limit = GRID_WAIT_LIMIT) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned target = round * gridDim.x;
@@ -1225,7 +1227,7 @@ __device__ __forceinline__ void grid_barrier(DevMeta* m, unsigned round) {
         atomicAdd(&m->gbar, 1u);
         uint32_t it = 0;
         while (*(volatile unsigned*)&m->gbar < target) {
-            if (++it > (1u << 24)) {   // ~1 s of polls
+            if (++it > limit) {
                 atomicOr(&m->err, ERR_WAIT);
                 break;
             }

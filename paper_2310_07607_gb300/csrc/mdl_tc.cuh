@@ -150,9 +150,10 @@ __device__ __forceinline__ bool mbar_test(uint64_t* mbar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase of the given parity; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
-    for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
+// Bounded wait for the phase of the given parity (at most `limit` polls); false if it did not
+// complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit = WAIT_LIMIT) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_test(mbar, parity)) return true;
     return false;
 }

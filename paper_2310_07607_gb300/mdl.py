@@ -71,6 +71,7 @@ EXPORTS = [
     "mdl_read_state", "mdl_read_activation", "mdl_read_mesh", "mdl_read_faces",
     "mdl_read_indicators", "mdl_get_stats", "mdl_reset_stats", "mdl_set_timing",
     "mdl_device_view", "mdl_last_error", "mdl_destroy", "mdl_version", "mdl_integral_noalloc",
+    "mdl_selftest_wait",
     "mdl_noalloc_last_error", "mdl_set_tick_shape", "mdl_set_sweep_variant", "mdl_set_sweep_blocks", "mdl_batch_create", "mdl_batch_footprint",
     "mdl_batch_admit", "mdl_batch_step", "mdl_batch_poll", "mdl_batch_slot", "mdl_batch_release",
     "mdl_batch_usage", "mdl_batch_shape", "mdl_batch_last_error", "mdl_batch_destroy",
@@ -122,6 +123,7 @@ def load(path: Optional[str] = None):
     lib.mdl_destroy.restype = None
     lib.mdl_version.restype = C.c_char_p
     lib.mdl_integral_noalloc.argtypes = [C.c_int32, C.c_int32, vp, vp, C.c_int32, vp, vp, i64, vp, vp]
+    lib.mdl_selftest_wait.argtypes = [C.c_int32, C.POINTER(C.c_int32), dp]
     lib.mdl_noalloc_last_error.restype = C.c_char_p
     i32p = C.POINTER(C.c_int32)
     lib.mdl_set_tick_shape.argtypes = [vp, C.c_int32, C.c_int32]
@@ -390,6 +392,19 @@ def integral_noalloc(prob, V_dev: int, level_dev: int, n_e: int, out_dev: int, s
                                   C.c_void_p(out_dev), C.c_void_p(stream))
     if rc != 0:
         raise MdlError(rc, lib.mdl_noalloc_last_error().decode())
+
+
+def selftest_wait(which: int, lib=None):
+    """Run one bounded device wait on a phase or count nothing completes (mdl_selftest_wait):
+    which 0 the cooperative sweep's grid barrier, 1 the tensor-core sweep's mbarrier wait.
+    Returns (status, elapsed_ms); status is MDL_E_TIMEOUT (-6) when the wait gave up."""
+    lib = lib or load()
+    st = C.c_int32(0)
+    ms = C.c_double(0.0)
+    rc = lib.mdl_selftest_wait(int(which), C.byref(st), C.byref(ms))
+    if rc != 0:
+        raise MdlError(rc, "mdl_selftest_wait failed")
+    return st.value, ms.value
 
 
 class Batch:
