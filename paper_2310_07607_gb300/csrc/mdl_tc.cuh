@@ -65,11 +65,11 @@ constexpr int OFF_ULO = OFF_UHI + U_BYTES;
 constexpr int OFF_R = OFF_ULO + U_BYTES;              // float [M][RST] scaled residual
 constexpr int OFF_SCR = OFF_R + M * RST * 4;          // float [8 warps][2][32] per-warp scratch
 constexpr int OFF_PTR = OFF_SCR + 8 * 2 * 32 * 4;     // const float* [8][M]: row of slot s (seen value)
-constexpr int OFF_PTRO = OFF_PTR + M * 8 * 8;         // const float* [8][M]: other V slot (interpolation)
+constexpr int OFF_PTRO = OFF_PTR + M * 8 * 8;         // const float* [8][M]: other V slot (interpolated slots only)
 constexpr int OFF_E = OFF_PTRO + M * 8 * 8;           // int32 [2][M] element id (-1: padding row)
 constexpr int OFF_INF = OFF_E + 2 * M * 4;            // uint32 [2][M] face info
 constexpr int OFF_NB = OFF_INF + 2 * M * 4;           // int32 [6][M] face neighbours
-constexpr int OFF_TH = OFF_NB + M * 6 * 4;            // float [8][M] time-interpolation weight
+constexpr int OFF_TH = OFF_NB + M * 6 * 4;            // float [8][M] time-interpolation weight (interpolated slots only)
 constexpr int OFF_RS = OFF_TH + M * 8 * 4;            // float 2^-sc: undoes the row's operand scale
 constexpr int OFF_C = OFF_RS + M * 4;                 // float operand mean c of the row
 constexpr int OFF_LV = OFF_C + M * 4;                 // uint8 [2][M] level byte
@@ -355,8 +355,6 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
         const int b = lv & 7, par = (lv >> 3) & 1;
         const int cur = par ^ ((tick >> (B - b)) & 1);
         sPtr[tid] = (cur ? d.V1 : d.V0) + (size_t)es * NPS;
-        sPtrO[tid] = (cur ? d.V0 : d.V1) + (size_t)es * NPS;   // slot 0: the row the step writes
-        sTh[tid] = 0.0f;
         if (e >= 0) live = 1;
         bool irr = false;
 #pragma unroll
@@ -368,8 +366,10 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
             const int nw = pn ^ ((j + (rem ? 1 : 0)) & 1);
             const size_t o = (size_t)(same ? nx[1 + f] : es) * NPS;
             sPtr[(1 + f) * M + tid] = (nw ? d.V1 : d.V0) + o;
-            sPtrO[(1 + f) * M + tid] = (nw ? d.V0 : d.V1) + o;
-            sTh[(1 + f) * M + tid] = rem ? (float)rem * pow2_neg<float>(sh) : 0.0f;
+            if (rem) {
+                sPtrO[(1 + f) * M + tid] = (nw ? d.V0 : d.V1) + o;
+                sTh[(1 + f) * M + tid] = (float)rem * pow2_neg<float>(sh);
+            }
             if (same) live |= (uint8_t)(2u << f);
             if (rem) intp |= (uint8_t)(2u << f);
             irr = irr || (((inf >> (4 * f)) & 3) != 1);
