@@ -94,3 +94,41 @@ def test_integral_noalloc_levels_up_to_seven_and_out_of_range(dim, order):
     mdl.integral_noalloc(prob, Vd.data_ptr(), lev.data_ptr(), n_e, out.data_ptr(), 0)
     torch.cuda.synchronize()
     assert np.isnan(out.item())
+
+
+def test_integral_noalloc_captured_in_a_graph():
+    """After a first call outside any capture, the call is captured into a CUDA graph on a side
+    stream and replayed; each replay reads the field as it is then (no allocation in between)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from oracle import basis
+    from paper_2310_07607_gb300 import build, mdl
+    build.build()
+    prob = W.Problem(dim=2, order=1, extent=(0.4, 0.3, 1.0), base=(4, 3, 1), precision=64)
+    rng = np.random.default_rng(12)
+    n_e, n_p = 2000, 4
+    level = rng.integers(0, 8, n_e).astype(np.int8)
+    V = rng.standard_normal(n_e * n_p)
+    wq = basis.node_weights(2, 1)
+    h = np.array([[prob.extent[k] / (prob.base[k] * 2.0 ** l) for k in range(2)] for l in range(8)])
+    m = (np.prod(h / 2.0, axis=1)[level][:, None] * wq[None, :]).reshape(-1)
+    ref, scale = float(np.sum(m * V)), float(np.sum(np.abs(m * V)))
+    Vd = torch.tensor(V, dtype=torch.float64, device="cuda")
+    lev = torch.tensor(level, dtype=torch.int8, device="cuda")
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    mdl.integral_noalloc(prob, Vd.data_ptr(), lev.data_ptr(), n_e, out.data_ptr(), 0)
+    torch.cuda.synchronize()
+    assert abs(out.item() - ref) <= 1e-12 * scale
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        mdl.integral_noalloc(prob, Vd.data_ptr(), lev.data_ptr(), n_e, out.data_ptr(), side.cuda_stream)
+    for factor in (1.0, -2.5):
+        Vd.copy_(torch.tensor(V * factor, dtype=torch.float64, device="cuda"))
+        out.fill_(float("nan"))
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert abs(out.item() - factor * ref) <= 1e-12 * abs(factor) * scale, (factor, out.item())
