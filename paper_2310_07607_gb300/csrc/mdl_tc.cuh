@@ -231,22 +231,22 @@ __device__ __forceinline__ float block_row_dot(const float* __restrict__ row, co
 
 // One tick of Alg. 1 for a Q2 3D FP32 context with the element residual on the tensor
 // cores.  Persistent, two CTAs per SM (each hides the other's memory latency), each CTA
-// walking tiles of 64 due elements:
-//   0  threads 0..63: metadata of the tile's elements and, per operand slot, the row that
-//      holds the value the element sees (Alg. 1: a coarser LTS neighbour mid-interval is
-//      seen through the linear interpolant of its last step); next tile's ids prefetched
+// walking tiles of 64 due elements (the first tile's records are built before the loop):
 //   1  warp w = 8-row group w, lane = 4 ii + kk: row ii, column pairs k = 2 kk + 8 jj +
 //      {0, 1}; all loads issued at once, then the row mean c, y = x - c, the row's
 //      power-of-two scale and the FP16 hi/lo terms in the swizzled operand layout
-//   2  one thread of warp 0 issues the MMAs and commits to an mbarrier
+//   2  one thread of warp 0 issues the MMAs and commits to an mbarrier; threads 0..63 fetch
+//      the next tile's face info, neighbours and level bytes
 //   3  while they run: corrections of non-regular faces (warps 1-7, warp per element, lane =
 //      row) and the loads of the pointwise step: thread 4 i + p takes DOFs p + 4 m of element i
 //   4  warps 0-3: D row -> scaled residual in shared memory
 //   5  the pointwise step of the thread's DOFs (element metadata read once per thread):
 //      straight-line (dof_update_ap) for a tile without stimulus or padding rows, else
 //      dof_update; the element's RV-T sum and max |V_new| over its four threads by shuffles,
-//      the accumulation; a due probe check is recorded and run by threads 64..127 during the
-//      next tile's metadata step (or after the last)
+//      the accumulation and a due probe check; then threads 0..63 build the next tile's
+//      records: per operand slot the row that holds the value the element sees (Alg. 1: a
+//      coarser LTS neighbour mid-interval is seen through the linear interpolant of its last
+//      step), the interpolation weights, live and interpolated slots
 // unscale = 2^-t undoes the scaling of B by 2^t; each row's scale of y is undone by 2^-sc.
 template <int DIM, int P>
 __global__ void __launch_bounds__(tc::THREADS, 2)
