@@ -1204,6 +1204,7 @@ public:
     // The device address of a page-locked host buffer mapped into the device's address space
     // (cudaHostAlloc / pinned memory), or null for any other pointer (which is then staged
     // through a device copy).
+    static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }   // null counts as aligned
     static const void* mapped_host(const void* p) {
         if (!p) return nullptr;
         cudaPointerAttributes a{};
@@ -1230,7 +1231,12 @@ public:
             dV = fscratch.p;
             dS = s ? fscratch.p + n_dof : nullptr;
         }
-        k_scatter_initial<R, NP, NPS, float><<<div_up(ne * NPS, 256), 256, 0, st>>>(arrays(cs), ne, dV, dS);
+        if (dV != fscratch.p && aligned16(dV) && aligned16(dS)) {
+            const int64_t nt = std::max<int64_t>(div_up(n_dof, 4), ne);
+            k_scatter_initial_x4<R, NP, NPS><<<div_up(nt, 256), 256, 0, st>>>(arrays(cs), ne, dV, dS);
+        } else {
+            k_scatter_initial<R, NP, NPS, float><<<div_up(ne * NPS, 256), 256, 0, st>>>(arrays(cs), ne, dV, dS);
+        }
         MDL_LAUNCHED();
         MDL_CK(cudaMemsetAsync((char*)meta.p + offsetof(DevMeta, err), 0, sizeof(unsigned int), st));
         k_lat_refresh<R, DIM, P><<<persistent_blocks(128), 128, 0, st>>>(arrays(cs), T, ph, (double)nbar * dt, 1, 1);
@@ -1256,6 +1262,9 @@ public:
             MDL_LAUNCHED();
             if (V) MDL_CK(cudaMemcpyAsync(V, fscratch.p, nd * sizeof(float), cudaMemcpyDeviceToHost, st));
             if (s) MDL_CK(cudaMemcpyAsync(s, fscratch.p + nd, nd * sizeof(float), cudaMemcpyDeviceToHost, st));
+        } else if (aligned16(dV) && aligned16(dS)) {
+            k_gather_f32x4<R, NP, NPS><<<div_up(div_up(nd, 4), 256), 256, 0, st>>>(arrays(cs), ne, dV, dS);
+            MDL_LAUNCHED();
         } else {
             k_gather_f32<R, NP, NPS><<<div_up(nd, 256), 256, 0, st>>>(arrays(cs), ne, dV, dS);
             MDL_LAUNCHED();

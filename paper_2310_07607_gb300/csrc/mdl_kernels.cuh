@@ -1331,6 +1331,74 @@ __global__ void k_gather_f32(const DevArrays<R> d, int64_t ne, float* outV, floa
     if (outS) outS[i] = (float)d.v[j];
 }
 
+// The same for page-locked host buffers read or written over the host link: four consecutive
+// compact values per thread as one 16-byte access (buffers 16-byte aligned; the last partial
+// group value by value), which keeps more bytes in flight per request than 4-byte accesses.
+template <typename R, int NP, int NPS>
+__global__ void k_gather_f32x4(const DevArrays<R> d, int64_t ne, float* outV, float* outS) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, n = ne * NP, i0 = 4 * t;
+    if (i0 >= n) return;
+    float va[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sa[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t i = i0 + k;
+        if (i < n) {
+            const int64_t e = i / NP, j = e * NPS + (i - e * NP);
+            const int par = (d.lvl[e] >> 3) & 1;
+            va[k] = (float)((par ? d.V1 : d.V0)[j]);
+            sa[k] = (float)d.v[j];
+        }
+    }
+    if (i0 + 3 < n) {
+        if (outV) reinterpret_cast<float4*>(outV)[t] = make_float4(va[0], va[1], va[2], va[3]);
+        if (outS) reinterpret_cast<float4*>(outS)[t] = make_float4(sa[0], sa[1], sa[2], sa[3]);
+    } else {
+        for (int k = 0; i0 + k < n; ++k) {
+            if (outV) outV[i0 + k] = va[k];
+            if (outS) outS[i0 + k] = sa[k];
+        }
+    }
+}
+
+template <typename R, int NP, int NPS>
+__global__ void k_scatter_initial_x4(DevArrays<R> d, int64_t ne, const float* V, const float* w) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, n = ne * NP, i0 = 4 * t;
+    if (i0 < n) {
+        float va[4] = {0.0f, 0.0f, 0.0f, 0.0f}, wa[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (i0 + 3 < n) {
+            const float4 a = reinterpret_cast<const float4*>(V)[t];
+            va[0] = a.x; va[1] = a.y; va[2] = a.z; va[3] = a.w;
+            if (w) {
+                const float4 b = reinterpret_cast<const float4*>(w)[t];
+                wa[0] = b.x; wa[1] = b.y; wa[2] = b.z; wa[3] = b.w;
+            }
+        } else {
+            for (int k = 0; i0 + k < n; ++k) {
+                va[k] = V[i0 + k];
+                if (w) wa[k] = w[i0 + k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k;
+            if (i < n) {
+                const int64_t e = i / NP, j = e * NPS + (i - e * NP);
+                d.V0[j] = (R)va[k];
+                if (w) d.v[j] = (R)wa[k];
+            }
+        }
+    }
+    // element t: the pad values of its padded rows, and its level byte's parity reset
+    if (t < ne) {
+#pragma unroll
+        for (int q = NP; q < NPS; ++q) {
+            d.V0[t * NPS + q] = R(0);
+            if (w) d.v[t * NPS + q] = R(0);
+        }
+        d.lvl[t] &= 7;
+    }
+}
+
 // Set V (into slot 0, parity reset) and optionally v from compact FP64 or FP32 input; the
 // pad values of padded rows are set to 0.
 template <typename R, int NP, int NPS, typename In>

@@ -572,9 +572,10 @@ def test_fp32_field_transfers_match_fp64_calls(mdl):
 def test_fp32_field_transfers_through_pinned_buffers(mdl):
     """Page-locked host buffers are read and written by the layout kernels directly (no staging
     copy): the same stored and returned values as with ordinary host arrays, bit for bit, on
-    the padded Q2 3D rows and on Q1 2D."""
+    the padded Q2 3D rows and on Q1 2D; 81 values (a partial group of four at the end) too."""
     import torch
     for prob in (W.scaled(W.slab_3d_q2(), (3, 2, 2)).replace(amr_enabled=0, max_refine=0),
+                 W.scaled(W.slab_3d_q2(), (3, 1, 1)).replace(amr_enabled=0, max_refine=0),
                  W.slab_2d_q1_256().replace(base=(12, 10, 1), extent=(12 * 2.0 / 256, 10 * 2.0 / 256, 1.0),
                                             amr_enabled=0, max_refine=0)):
         a, b = mdl.Sim(prob), mdl.Sim(prob)
