@@ -779,8 +779,15 @@ public:
             std::vector<uint16_t> hb;
             const int t = q2_tensor_blocks(Td, phd, &hb);
             tc_unscale = (float)ldexp(1.0, -t);
-            MDL_CK(tcB.ensure(hb.size()));
-            MDL_CK(cudaMemcpy(tcB.p, hb.data(), hb.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+            // as the image of the kernel's swizzled shared-memory operand (B_hi, then B_lo)
+            std::vector<uint16_t> img((size_t)2 * tc::B_BYTES / 2, 0);
+            for (int part = 0; part < 2; ++part)
+                for (int n = 0; n < tc::N; ++n)
+                    for (int k = 0; k < tc::K; ++k)
+                        img[((size_t)part * tc::B_BYTES + tc::sw128h(n, k, tc::N)) / 2] =
+                            hb[((size_t)part * tc::N + n) * tc::K + k];
+            MDL_CK(tcB.ensure(img.size()));
+            MDL_CK(cudaMemcpy(tcB.p, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
             std::vector<float> hc;
             q2_correction_blocks(Td, phd, &hc);
             MDL_CK(tcC.ensure(hc.size()));

@@ -91,7 +91,7 @@ constexpr uint32_t WAIT_LIMIT = 1u << 26;             // mbarrier polls before g
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Byte offset of FP16 element (row, k) in a 128-byte swizzled K-major operand of `rows` rows.
-__device__ __forceinline__ uint32_t sw128h(int row, int k, int rows) {
+__host__ __device__ __forceinline__ uint32_t sw128h(int row, int k, int rows) {
     return (uint32_t)((k >> 6) * rows * 128 + (row >> 3) * 1024 + (row & 7) * 128 +
                       ((((k >> 3) & 7) ^ (row & 7)) << 4) + ((k & 7) << 1));
 }
@@ -283,10 +283,10 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
     const int tick = a.tick, B = a.B;
 
     // --- set-up that reads nothing the previous tick writes (before the dependent wait)
-    for (int i = tid; i < 2 * N * K; i += THREADS) {
-        const int part = i / (N * K), rem = i - part * (N * K), n = rem / K, k = rem - n * K;
-        *reinterpret_cast<uint16_t*>(sm + (part ? OFF_BLO : OFF_BHI) + sw128h(n, k, N)) = Bg[i];
-    }
+    // the operator's FP16 terms, stored in global memory as the image of their swizzled shared-
+    // memory layout (B_hi then B_lo): a straight 16-byte copy
+    for (int i = tid; i < 2 * B_BYTES / 16; i += THREADS)
+        reinterpret_cast<uint4*>(sm + OFF_BHI)[i] = __ldg(reinterpret_cast<const uint4*>(Bg) + i);
     // per (level, node) GL mass and its inverse: lanes read different nodes, which kernel-
     // parameter arrays would serve one address at a time
     for (int i = tid; i < 8 * NP; i += THREADS) {
