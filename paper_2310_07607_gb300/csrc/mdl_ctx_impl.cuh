@@ -531,8 +531,11 @@ class Ctx : public CtxBase {
                                                   (int64_t)nsm * tick_bpsm);
             if constexpr (tensor_capable) {
                 if (tensor_tick) {
-                    // persistent: two blocks per SM walk the tiles of 64 due elements
-                    const int nblk = sweep_blocks > 0 ? std::min(sweep_blocks, 2 * nsm) : 2 * nsm;
+                    // persistent: two blocks per SM walk the tiles of 64 due elements; no more
+                    // blocks than the capacity has tiles (a small instance leaves the other SMs
+                    // to the batch's other slots)
+                    const int nfit = (int)std::min<int64_t>(div_up(std::max<int64_t>(cap, 1), tc::M), 2 * nsm);
+                    const int nblk = sweep_blocks > 0 ? std::min(sweep_blocks, 2 * nsm) : nfit;
                     for (int i = 0; i < nt; ++i) {
                         ta.tick = i;
                         MDL_CK(launch_kxs(pdl && i > 0, (size_t)tc::SMEM_BYTES, (k_tick_tc<DIM, P>), nblk, tc::THREADS,
