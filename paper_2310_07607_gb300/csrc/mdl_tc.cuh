@@ -313,9 +313,6 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
     int e_cur = -1, e_next = -1;   // threads 0..63: element of this CTA's first tile, of the next one
     if (tid < M && (int)blockIdx.x * M + tid < n_act) e_cur = d.order[blockIdx.x * M + tid];
     if (tid < M && ((int)blockIdx.x + G) * M + tid < n_act) e_next = d.order[(blockIdx.x + G) * M + tid];
-    pdl_enter();
-    uint32_t parity = 0;
-    bool ok = d.meta->err == 0;
     // Metadata of a tile's element (threads 0..63) is fetched one tile ahead: its face info,
     // neighbours and level byte while the previous tile's gather and MMAs run, the neighbours'
     // level bytes while its pointwise step runs, and the tile's records are built at the end of
@@ -395,6 +392,11 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
     // exponential state step, takes the straight-line pointwise step (phase 5)
     const bool ap_exp = ph.ionic == 0 && ph.integrator == 1;
     bool fast = !__syncthreads_or(slow0) && ap_exp;
+    // everything above reads only what is fixed during the sweep (order, due counts, face info,
+    // neighbours, level bytes): it overlaps the previous tick's tail; the values from here on
+    pdl_enter();
+    uint32_t parity = 0;
+    bool ok = d.meta->err == 0;
     const double t_tick = tick_time(a, tick);
     int nxr[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // threads 0..63: next tile's raw metadata in flight
     uint32_t nlo = 0u, nhi = 0u;
