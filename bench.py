@@ -68,7 +68,7 @@ TRAFFIC_PER_LAUNCH = {
     # curved LV-like slab at full size: the eight ticks of one barrier step
     ("lv3d", "k_tick_mapped<float,3,1>"): 4.4873e7,
     # 3D slab: the quarter slab's eight ticks, tick 0 and tick 4 scaled to the full slab
-    ("slab3d", "k_tick_tc<3,2>"): 1.9599e9,
+    ("slab3d", "k_tick_tc<3,2>"): 1.9601e9,
 }
 # Mapped Q1 3D (lv3d): per element step the state 128 B, metadata and the RV-T accumulator
 # 49 B, and the element's geometric factors (8 nodes x 7 values + 6 faces x 4 points x 5
