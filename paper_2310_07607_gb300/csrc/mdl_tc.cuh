@@ -281,6 +281,11 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
     const DevArrays<float>& d = a.d;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tick = a.tick, B = a.B;
+    // due count and element order are fixed during the sweep; a block without a tile of this
+    // tick skips the set-up and leaves its SM to other work (a small instance's fine ticks)
+    const int n_act = d.meta->nact[tick];
+    const int ntiles = (n_act + M - 1) / M;
+    if ((int)blockIdx.x >= ntiles) return;
 
     // --- set-up that reads nothing the previous tick writes (before the dependent wait)
     // the operator's FP16 terms, stored in global memory as the image of their swizzled shared-
@@ -306,9 +311,6 @@ __global__ void __launch_bounds__(tc::THREADS, 2)
     __syncthreads();
     fence_after();
     const uint32_t tmem = *sTmem;
-    // due count and element order are fixed during the sweep
-    const int n_act = d.meta->nact[tick];
-    const int ntiles = (n_act + M - 1) / M;
     const int G = (int)gridDim.x;
     int e_cur = -1, e_next = -1;   // threads 0..63: element of this CTA's first tile, of the next one
     if (tid < M && (int)blockIdx.x * M + tid < n_act) e_cur = d.order[blockIdx.x * M + tid];
